@@ -1,0 +1,933 @@
+// Plain CPU oracle of one UGKWP time step on a tetrahedral mesh.
+//
+// TEST INFRASTRUCTURE ONLY -- see ugkwp_oracle.h.  Written for a reader who
+// checks it against the paper (Chen, Zhu, Xu, "A three-dimensional unified
+// gas-kinetic wave-particle solver for flow computation in all regimes",
+// arXiv 2007.13091): every step cites the section or equation it follows.
+// It is single-threaded FP64 (particle state optionally binary32, "mixed"),
+// keeps particles in a plain std::vector and runs the steps of the method in
+// the order of the particle evolution procedure of Sec. 2.2:
+//
+//   a1  primitives and relaxation time per cell            (Sec. 2, tau = mu/p)
+//   a2  time step                                          (Sec. 2.4 (a))
+//   a5  sampling of the collisionless hydrodynamic particles (Sec. 2.4 (b))
+//   a6  free-transport time of the remaining particles     (Eq. t_f)
+//   a7  ballistic streaming with face-by-face tet tracking (Sec. 2.2)
+//   a8  particle flux by counting                          (Eq. F^{fr,p})
+//   a9  removal of collisional and exited particles        (Sec. 2.2 step 4)
+//   a4  wave flux F^eq + F^{fr,wave} per face              (Sec. 2.1, 2.3, 2.4 (d),(e))
+//   a10 conservative update of W                           (Eq. update_macro_variables)
+//
+// Readings where the paper is silent are listed in the repository design
+// notes; each is marked "reading:" below.
+#include "ugkwp_oracle.h"
+#include "omath.hpp"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+namespace orc {
+
+static const double PI = 3.14159265358979323846;
+
+// ------------------------------------------------------------------ ids, tags
+// Particle id: (step born : 24 | cell born : 24 | index in cell : 16).
+static inline uint64_t make_id(uint64_t step, uint64_t cell, uint64_t k) {
+    return (step << 40) | (cell << 16) | k;
+}
+static inline uint64_t id_step(uint64_t id) { return id >> 40; }
+// Random-number purposes (third counter word).
+enum { TAG_TF = 1, TAG_SVEL = 2, TAG_SPOS = 3, TAG_WALL = 4 };
+
+static inline Ctr4 draw(uint64_t seed, uint64_t a, uint64_t b, uint64_t tag, uint64_t idx) {
+    Ctr4 c; c.v[0] = a; c.v[1] = b; c.v[2] = tag; c.v[3] = idx;
+    return philox4x64_10(c, seed, 0);
+}
+
+// ------------------------------------------------------------- small vectors
+static inline double dot3(const double* a, const double* b) { return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]; }
+static inline void cross3(const double* a, const double* b, double* c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// ------------------------------------------------------------------ geometry
+struct Geom {
+    int nn = 0, nc = 0, nf = 0, nbf = 0;
+    std::vector<double> xyz;          // [3*nn] node-major (x,y,z per node)
+    std::vector<int32_t> tet;         // [4*nc]
+    std::vector<int32_t> tet_face;    // [4*nc] face opposite local node k
+    std::vector<int8_t> tet_sign;     // [4*nc] +1 if the tet owns the face
+    std::vector<int32_t> f_owner, f_nbr, f_owner_k, f_nbr_k, f_bc;
+    std::vector<double> f_n, f_area, f_c, f_d, f_t1, f_t2;  // [3*nf] or [nf]
+    std::vector<double> vol, cen, dS;                      // [nc], [3*nc], [3*nc]
+};
+
+static bool build_geometry(Geom& g, int nn, const double* xyz, int nc, const int32_t* tets,
+                           int nbf, const int32_t* bf, const int32_t* btag, int n_bc, std::string& err) {
+    g.nn = nn; g.nc = nc;
+    g.xyz.assign(xyz, xyz + 3 * (size_t)nn);
+    g.tet.assign(tets, tets + 4 * (size_t)nc);
+    g.tet_face.assign(4 * (size_t)nc, -1);
+    g.tet_sign.assign(4 * (size_t)nc, 0);
+    g.vol.resize(nc); g.cen.resize(3 * (size_t)nc); g.dS.resize(3 * (size_t)nc);
+    auto P = [&](int node) { return &g.xyz[3 * (size_t)node]; };
+    for (int i = 0; i < nc; ++i) {
+        for (int k = 0; k < 4; ++k) {
+            int v = g.tet[4 * i + k];
+            if (v < 0 || v >= nn) { err = "tet node index out of range"; return false; }
+        }
+        const double *p0 = P(g.tet[4 * i]), *p1 = P(g.tet[4 * i + 1]), *p2 = P(g.tet[4 * i + 2]), *p3 = P(g.tet[4 * i + 3]);
+        double a[3], b[3], c[3], bxc[3];
+        for (int d = 0; d < 3; ++d) { a[d] = p1[d] - p0[d]; b[d] = p2[d] - p0[d]; c[d] = p3[d] - p0[d]; }
+        cross3(b, c, bxc);
+        double V = dot3(a, bxc) / 6.0;
+        if (!(V > 0.0)) { err = "tet " + std::to_string(i) + " has non-positive volume"; return false; }
+        g.vol[i] = V;
+        for (int d = 0; d < 3; ++d) g.cen[3 * i + d] = (((p0[d] + p1[d]) + p2[d]) + p3[d]) * 0.25;
+    }
+    // Face matching on sorted node triples; faces numbered by first appearance.
+    std::map<std::array<int, 3>, int> fmap;
+    for (int i = 0; i < nc; ++i) {
+        for (int k = 0; k < 4; ++k) {
+            std::array<int, 3> key;
+            int j = 0;
+            for (int l = 0; l < 4; ++l) if (l != k) key[j++] = g.tet[4 * i + l];
+            std::sort(key.begin(), key.end());
+            auto it = fmap.find(key);
+            if (it == fmap.end()) {
+                int f = (int)g.f_owner.size();
+                fmap[key] = f;
+                g.f_owner.push_back(i); g.f_owner_k.push_back(k);
+                g.f_nbr.push_back(-1); g.f_nbr_k.push_back(-1);
+                g.tet_face[4 * i + k] = f; g.tet_sign[4 * i + k] = 1;
+            } else {
+                int f = it->second;
+                if (g.f_nbr[f] >= 0) { err = "face shared by more than two tets"; return false; }
+                g.f_nbr[f] = i; g.f_nbr_k[f] = k;
+                g.tet_face[4 * i + k] = f; g.tet_sign[4 * i + k] = -1;
+            }
+        }
+    }
+    int nf = (int)g.f_owner.size();
+    g.nf = nf;
+    g.f_bc.assign(nf, -1);
+    for (int b = 0; b < nbf; ++b) {
+        std::array<int, 3> key = {bf[3 * b], bf[3 * b + 1], bf[3 * b + 2]};
+        std::sort(key.begin(), key.end());
+        auto it = fmap.find(key);
+        if (it == fmap.end()) { err = "boundary face " + std::to_string(b) + " is not a tet face"; return false; }
+        int f = it->second;
+        if (g.f_nbr[f] >= 0) { err = "boundary face " + std::to_string(b) + " is interior"; return false; }
+        if (btag[b] < 0 || btag[b] >= n_bc) { err = "boundary tag out of range"; return false; }
+        if (g.f_bc[f] >= 0) { err = "boundary face listed twice"; return false; }
+        g.f_bc[f] = btag[b];
+    }
+    g.nbf = 0;
+    for (int f = 0; f < nf; ++f) {
+        if (g.f_nbr[f] < 0) {
+            if (g.f_bc[f] < 0) { err = "unmatched face " + std::to_string(f) + " has no boundary tag"; return false; }
+            g.nbf++;
+        }
+    }
+    // Face geometry: normal from the cross product of the sorted triple, turned
+    // to point out of the owner; centroid; plane offset d = n . centroid.
+    g.f_n.resize(3 * (size_t)nf); g.f_area.resize(nf); g.f_c.resize(3 * (size_t)nf); g.f_d.resize(nf);
+    g.f_t1.resize(3 * (size_t)nf); g.f_t2.resize(3 * (size_t)nf);
+    for (int f = 0; f < nf; ++f) {
+        int o = g.f_owner[f], k = g.f_owner_k[f];
+        int tri[3], j = 0;
+        for (int l = 0; l < 4; ++l) if (l != k) tri[j++] = g.tet[4 * o + l];
+        std::sort(tri, tri + 3);
+        const double *pa = P(tri[0]), *pb = P(tri[1]), *pc = P(tri[2]), *po = P(g.tet[4 * o + k]);
+        double e1[3], e2[3], N[3], w[3];
+        for (int d = 0; d < 3; ++d) { e1[d] = pb[d] - pa[d]; e2[d] = pc[d] - pa[d]; w[d] = po[d] - pa[d]; }
+        cross3(e1, e2, N);
+        double s = dot3(N, w);
+        if (s == 0.0) { err = "degenerate face"; return false; }
+        if (s > 0.0) { N[0] = -N[0]; N[1] = -N[1]; N[2] = -N[2]; }
+        double len = std::sqrt(dot3(N, N));
+        double* n = &g.f_n[3 * (size_t)f];
+        for (int d = 0; d < 3; ++d) n[d] = N[d] / len;
+        g.f_area[f] = 0.5 * len;
+        double* c = &g.f_c[3 * (size_t)f];
+        for (int d = 0; d < 3; ++d) c[d] = ((pa[d] + pb[d]) + pc[d]) / 3.0;
+        g.f_d[f] = dot3(n, c);
+        // Tangent basis: t1 = (e_a x n)/|e_a x n| with a the axis of smallest |n_a|.
+        int a = 0;
+        for (int d = 1; d < 3; ++d) if (std::fabs(n[d]) < std::fabs(n[a])) a = d;
+        double ea[3] = {0.0, 0.0, 0.0}; ea[a] = 1.0;
+        double t1[3], t2[3];
+        cross3(ea, n, t1);
+        double l1 = std::sqrt(dot3(t1, t1));
+        for (int d = 0; d < 3; ++d) t1[d] = t1[d] / l1;
+        cross3(n, t1, t2);
+        for (int d = 0; d < 3; ++d) { g.f_t1[3 * (size_t)f + d] = t1[d]; g.f_t2[3 * (size_t)f + d] = t2[d]; }
+    }
+    // Projected areas (Sec. 2.4 (a)): dS^x = 1/2 sum_j |S^x_ij| with S = |S| n.
+    for (int i = 0; i < nc; ++i) {
+        for (int d = 0; d < 3; ++d) {
+            double acc = 0.0;
+            for (int k = 0; k < 4; ++k) {
+                int f = g.tet_face[4 * i + k];
+                acc = acc + std::fabs(g.f_n[3 * (size_t)f + d] * g.f_area[f]);
+            }
+            g.dS[3 * i + d] = 0.5 * acc;
+        }
+    }
+    return true;
+}
+
+// ------------------------------------------------------------- primitives
+// Sec. 2: W = (rho, rho U, rho E), rho E = 1/2 rho |U|^2 + (3+K)/2 p with K = 0,
+// p = rho R T, lambda = 1/(2RT).
+struct Prim { double rho, U[3], p, T, lam; };
+static inline Prim prim_of(const double* W, double R) {
+    Prim s;
+    s.rho = W[0];
+    for (int d = 0; d < 3; ++d) s.U[d] = W[1 + d] / s.rho;
+    double U2 = (s.U[0] * s.U[0] + s.U[1] * s.U[1]) + s.U[2] * s.U[2];
+    s.p = (W[4] - 0.5 * (s.rho * U2)) / 1.5;
+    s.T = s.p / (s.rho * R);
+    s.lam = s.rho / (2.0 * s.p);
+    return s;
+}
+
+// tau = mu_ref / p (T / T_ref)^omega  (Eq. tau_via_T_ref), with the power written
+// as exp(omega log(T/T_ref)) through the bit-reproducible exp_d/log_d.
+static inline double tau_cell(const Prim& s, const orc_params& P) {
+    return (P.mu_ref / s.p) * exp_d(P.omega * log_d(s.T / P.T_ref));
+}
+
+// ------------------------------------------------------- time coefficients
+// q1..q5 = int_0^dt c1..c5 dt (Sec. 2.1) and the free-transport coefficients of
+// the collisional wave (Sec. 2.3): a4 = q4 - dt e^{-dt/tau}, a5 = q5 + dt^2/2 e^{-dt/tau}.
+// For x = dt/tau < 1 each is tau^p times a power series in x whose k-th
+// coefficient follows from expanding e^{-x}; otherwise the closed forms are used.
+static void qcoef(double dt, double tau, double q[7]) {
+    double x = dt / tau;
+    if (x < 1.0) {
+        double s[7] = {0, 0, 0, 0, 0, 0, 0};
+        double term = 1.0;  // x^k / k!
+        for (int k = 1; k <= 30; ++k) {
+            term = term * x / (double)k;
+            double sg = (k % 2 == 0) ? 1.0 : -1.0;  // (-1)^k
+            if (k >= 2) s[0] += sg * term;                                   // q1/tau
+            if (k >= 3) s[1] += -sg * (double)(2 - k) * term;                // q2/tau^2
+            if (k >= 3) s[2] += -sg * term;                                  // q3/tau^2
+            s[3] += -sg * term;                                              // q4/tau
+            if (k >= 2) s[4] += -sg * (double)(k - 1) * term;                // q5/tau^2
+            if (k >= 2) s[5] += -sg * (double)(1 - k) * term;                // a4/tau
+            if (k >= 3) s[6] += sg * 0.5 * (double)((k - 1) * (k - 2)) * term;  // a5/tau^2
+        }
+        double t2 = tau * tau;
+        q[0] = tau * s[0]; q[1] = t2 * s[1]; q[2] = t2 * s[2]; q[3] = tau * s[3];
+        q[4] = t2 * s[4]; q[5] = tau * s[5]; q[6] = t2 * s[6];
+    } else {
+        double e = std::exp(-x);
+        double ph = -std::expm1(-x);  // 1 - e^{-x}
+        q[0] = dt - tau * ph;
+        q[1] = 2.0 * tau * tau * ph - tau * dt - tau * dt * e;
+        q[2] = 0.5 * dt * dt - tau * dt + tau * tau * ph;
+        q[3] = tau * ph;
+        q[4] = tau * dt * e - tau * tau * ph;
+        q[5] = q[3] - dt * e;
+        q[6] = q[4] + 0.5 * dt * dt * e;
+    }
+}
+
+// ------------------------------------------------------ Maxwellian moments
+// Moments <u_n^k>, k = 0..4, of the normalised 1D Maxwellian in the normal
+// direction over u_n > 0 (half = +1), u_n < 0 (half = -1) or all u_n (half = 0),
+// by the recurrence <u^{k+2}> = Un <u^{k+1}> + (k+1)/(2 lambda) <u^k>.
+static void un_moments(double Un, double lam, int half, double M[5]) {
+    if (half == 0) {
+        M[0] = 1.0; M[1] = Un;
+    } else {
+        double a = std::sqrt(lam) * Un;
+        double edge = 0.5 * std::exp(-lam * Un * Un) / std::sqrt(PI * lam);
+        if (half > 0) { M[0] = 0.5 * std::erfc(-a); M[1] = Un * M[0] + edge; }
+        else          { M[0] = 0.5 * std::erfc(a);  M[1] = Un * M[0] - edge; }
+    }
+    for (int k = 0; k < 3; ++k) M[k + 2] = Un * M[k + 1] + (double)(k + 1) / (2.0 * lam) * M[k];
+}
+
+// H = int g psi du and G = int u_n g psi du over the half space, for a unit-density
+// Maxwellian with velocity U = Un n + Ut and lambda; psi = (1, u, |u|^2/2), K = 0.
+static void half_moments(double Un, const double* Ut, const double* n, double lam, int half,
+                         double H[5], double G[5]) {
+    double M[5];
+    un_moments(Un, lam, half, M);
+    double Ut2 = (Ut[0] * Ut[0] + Ut[1] * Ut[1]) + Ut[2] * Ut[2];
+    double tv = Ut2 + 1.0 / lam;  // <|u_t|^2> of the two tangential directions
+    H[0] = M[0];
+    G[0] = M[1];
+    for (int d = 0; d < 3; ++d) {
+        H[1 + d] = M[1] * n[d] + M[0] * Ut[d];
+        G[1 + d] = M[2] * n[d] + M[1] * Ut[d];
+    }
+    H[4] = 0.5 * (M[2] + M[0] * tv);
+    G[4] = 0.5 * (M[3] + M[1] * tv);
+}
+
+struct FaceState { double rho, rhoh, Un, Ut[3], lam, p, T; };
+static FaceState face_state(const double* W, double rhoh, const double* n, double R) {
+    Prim s = prim_of(W, R);
+    FaceState f;
+    f.rho = s.rho; f.rhoh = rhoh; f.lam = s.lam; f.p = s.p; f.T = s.T;
+    f.Un = dot3(s.U, n);
+    for (int d = 0; d < 3; ++d) f.Ut[d] = s.U[d] - f.Un * n[d];
+    return f;
+}
+
+// ---------------------------------------------------------------- face flux
+// Time-integrated flux per unit area through a face with unit normal n (L -> R):
+//   F = F^eq + F^{fr,wave}
+//   F^eq       = int u.n (q1 g0) psi du                    (Eq. macroscopic fluxes,
+//                first order: g_x = g_t = 0)
+//   F^{fr,wave}= int u.n [(q4 - dt e^{-dt/tau}) g0^h] psi du   (Sec. 2.3, g_x^h = 0)
+// with W0 = int_{u.n>0} g_L psi + int_{u.n<0} g_R psi (compatibility condition,
+// Sec. 2.1) and reading: g0^h is the upwind hydrodynamic Maxwellian
+// (rho^h_L/rho_L) g_L for u.n >= 0 and (rho^h_R/rho_R) g_R for u.n < 0.
+// Face relaxation time (Sec. 2.4 (d)): tau = mu(T0)/p0 + C2 |pL-pR|/|pL+pR| dt.
+// ghost_hydro: the R side is a far-field ghost that emits no particles, so its
+// incoming half carries the full UGKS free-transport coefficient q4.
+static void interior_flux(const FaceState& L, const FaceState& Rs, bool ghost_hydro,
+                          const double* n, double dt, const orc_params& P, double F[5]) {
+    double HL[5], GL[5], HR[5], GR[5];
+    half_moments(L.Un, L.Ut, n, L.lam, +1, HL, GL);
+    half_moments(Rs.Un, Rs.Ut, n, Rs.lam, -1, HR, GR);
+    double W0[5];
+    for (int q = 0; q < 5; ++q) W0[q] = L.rho * HL[q] + Rs.rho * HR[q];
+    Prim s0 = prim_of(W0, P.R);
+    double tau = P.mu_ref * std::pow(s0.T / P.T_ref, P.omega) / s0.p
+               + P.C2 * std::fabs(L.p - Rs.p) / std::fabs(L.p + Rs.p) * dt;
+    double q[7];
+    qcoef(dt, tau, q);
+    double Un0 = dot3(s0.U, n), Ut0[3];
+    for (int d = 0; d < 3; ++d) Ut0[d] = s0.U[d] - Un0 * n[d];
+    double H0[5], G0[5];
+    half_moments(Un0, Ut0, n, s0.lam, 0, H0, G0);
+    double cR = ghost_hydro ? q[3] : q[5];
+    for (int k = 0; k < 5; ++k)
+        F[k] = q[0] * (s0.rho * G0[k]) + q[5] * (L.rhoh * GL[k]) + cR * (Rs.rhoh * GR[k]);
+}
+
+// Diffuse isothermal wall (Sec. 2.4 (e)), n pointing from the gas into the wall.
+// Incoming half: the interior state as g0 and f0 with the cell's tau; emitted
+// half: the wall Maxwellian g_w(T_w, U_w) over the whole step with rho_w from
+// zero net mass flux of the wave (reading: particles reflect individually).
+static void wall_flux(const FaceState& L, double tau, const orc_bc& bc, const double* n,
+                      double dt, const orc_params& P, double F[5]) {
+    double q[7];
+    qcoef(dt, tau, q);
+    double HL[5], GL[5];
+    half_moments(L.Un, L.Ut, n, L.lam, +1, HL, GL);
+    double Gin[5];
+    for (int k = 0; k < 5; ++k) Gin[k] = q[0] * (L.rho * GL[k]) + q[5] * (L.rhoh * GL[k]);
+    double lamw = 1.0 / (2.0 * P.R * bc.T_w);
+    double Uwn = dot3(bc.U_w, n), Uwt[3];
+    for (int d = 0; d < 3; ++d) Uwt[d] = bc.U_w[d] - Uwn * n[d];
+    double Hw[5], Gw[5];
+    half_moments(Uwn, Uwt, n, lamw, -1, Hw, Gw);
+    double rhow = -Gin[0] / (dt * Gw[0]);
+    for (int k = 0; k < 5; ++k) F[k] = Gin[k] + dt * rhow * Gw[k];
+}
+
+static void boundary_flux(const double* WL, double rhohL, double tauL, const orc_bc& bc,
+                          const double* n, double dt, const orc_params& P, double F[5]) {
+    FaceState L = face_state(WL, rhohL, n, P.R);
+    if (bc.type == ORC_BC_DIFFUSE_WALL) { wall_flux(L, tauL, bc, n, dt, P, F); return; }
+    if (bc.type == ORC_BC_SPECULAR) {
+        // Mirror ghost: same state with the normal velocity reversed.  Only the
+        // normal momentum flux survives; mass, energy and shear are zero.
+        FaceState Rg = L; Rg.Un = -L.Un;
+        double Ff[5];
+        interior_flux(L, Rg, false, n, dt, P, Ff);
+        double fn = dot3(&Ff[1], n);
+        F[0] = 0.0; F[4] = 0.0;
+        for (int d = 0; d < 3; ++d) F[1 + d] = fn * n[d];
+        return;
+    }
+    // Far field: inflow ghost = prescribed state, outflow ghost = interior state;
+    // both all-hydrodynamic and emitting no particles (reading).
+    FaceState Rg = (bc.type == ORC_BC_INFLOW) ? face_state(bc.W_in, bc.W_in[0], n, P.R) : L;
+    Rg.rhoh = Rg.rho;
+    interior_flux(L, Rg, true, n, dt, P, F);
+}
+
+// ------------------------------------------------------------ particles
+template <class Real> struct Part { uint64_t id; int32_t cell; Real x[3]; Real u[3]; double m; };
+
+template <class Real> struct Planes {
+    std::vector<Real> n;  // [4*nc][3]
+    std::vector<Real> d;  // [4*nc]
+    std::vector<int32_t> nb;  // [4*nc]: (tet << 2 | local face) or -1 - face for boundary
+    void build(const Geom& g) {
+        n.resize(12 * (size_t)g.nc); d.resize(4 * (size_t)g.nc); nb.resize(4 * (size_t)g.nc);
+        for (int i = 0; i < g.nc; ++i)
+            for (int k = 0; k < 4; ++k) {
+                int f = g.tet_face[4 * i + k];
+                int sg = g.tet_sign[4 * i + k];
+                for (int c = 0; c < 3; ++c) {
+                    Real v = (Real)g.f_n[3 * (size_t)f + c];
+                    n[12 * (size_t)i + 3 * k + c] = sg > 0 ? v : -v;
+                }
+                Real dv = (Real)g.f_d[f];
+                d[4 * (size_t)i + k] = sg > 0 ? dv : -dv;
+                if (g.f_nbr[f] < 0) nb[4 * (size_t)i + k] = -1 - f;
+                else if (sg > 0) nb[4 * (size_t)i + k] = (g.f_nbr[f] << 2) | g.f_nbr_k[f];
+                else nb[4 * (size_t)i + k] = (g.f_owner[f] << 2) | g.f_owner_k[f];
+            }
+    }
+};
+
+struct TrackOut { int status; int cell; int ncross; int nwall; };
+enum { ST_COLL = 1, ST_EXIT = 2, ST_LOST = 4 };
+
+// Ballistic streaming x* = x + u t (Sec. 2.2) through the tets.  The particle
+// follows the ray x0 + u (t - t0); in its tet the exit face is the one with
+// u.n > 0 and the smallest crossing time (ties: lowest local face; the face it
+// entered through, or last reflected from, is skipped).  Interior faces hand
+// the ray to the neighbour unchanged; walls restart it at the hit point.
+template <class Real>
+static TrackOut track(const Geom& g, const Planes<Real>& pl, const orc_params& P,
+                      Part<Real>& pt, Real t_end, uint64_t step) {
+    TrackOut o = {0, pt.cell, 0, 0};
+    int tet = pt.cell, last = -1;
+    Real x0[3] = {pt.x[0], pt.x[1], pt.x[2]};
+    Real u[3] = {pt.u[0], pt.u[1], pt.u[2]};
+    Real t0 = 0;
+    for (;;) {
+        int best = -1;
+        Real sbest = 0;
+        for (int k = 0; k < 4; ++k) {
+            if (k == last) continue;
+            const Real* nk = &pl.n[12 * (size_t)tet + 3 * k];
+            Real un = (u[0] * nk[0] + u[1] * nk[1]) + u[2] * nk[2];
+            if (un > (Real)0) {
+                Real xn = (x0[0] * nk[0] + x0[1] * nk[1]) + x0[2] * nk[2];
+                Real s = (pl.d[4 * (size_t)tet + k] - xn) / un;
+                if (best < 0 || s < sbest) { best = k; sbest = s; }
+            }
+        }
+        Real rem = t_end - t0;
+        if (best < 0 || sbest >= rem) {
+            for (int c = 0; c < 3; ++c) pt.x[c] = x0[c] + u[c] * rem;
+            break;
+        }
+        if (sbest < (Real)0) sbest = 0;
+        o.ncross++;
+        if (o.ncross > P.max_crossings) {
+            o.status |= ST_LOST;
+            for (int c = 0; c < 3; ++c) pt.x[c] = x0[c];
+            break;
+        }
+        int code = pl.nb[4 * (size_t)tet + best];
+        if (code >= 0) { tet = code >> 2; last = code & 3; continue; }
+        int f = -1 - code;
+        const orc_bc& bc = P.bc[g.f_bc[f]];
+        if (bc.type == ORC_BC_INFLOW || bc.type == ORC_BC_OUTFLOW) { o.status |= ST_EXIT; break; }
+        Real xh[3];
+        for (int c = 0; c < 3; ++c) xh[c] = x0[c] + u[c] * sbest;
+        if (bc.type == ORC_BC_SPECULAR) {
+            const Real* nk = &pl.n[12 * (size_t)tet + 3 * best];
+            Real un = (u[0] * nk[0] + u[1] * nk[1]) + u[2] * nk[2];
+            Real two = un + un;
+            for (int c = 0; c < 3; ++c) u[c] = u[c] - two * nk[c];
+        } else {
+            // Diffuse re-emission with full accommodation (reading): flux-weighted
+            // normal speed sqrt(-2 R T_w ln eta), Gaussian tangential components.
+            Ctr4 r = draw(P.seed, pt.id, step, TAG_WALL, (uint64_t)o.nwall);
+            double vn = std::sqrt(-2.0 * P.R * bc.T_w * log_d(u01_d(r.v[0])));
+            double rad = std::sqrt(-2.0 * log_d(u01_d(r.v[1])));
+            double sn, cs;
+            sincos2pi_d(u01_d(r.v[2]), &sn, &cs);
+            double sw = std::sqrt(P.R * bc.T_w);
+            const double* n = &g.f_n[3 * (size_t)f];
+            const double* t1 = &g.f_t1[3 * (size_t)f];
+            const double* t2 = &g.f_t2[3 * (size_t)f];
+            double v1 = dot3(bc.U_w, t1) + sw * (rad * cs);
+            double v2 = dot3(bc.U_w, t2) + sw * (rad * sn);
+            for (int c = 0; c < 3; ++c) u[c] = (Real)(((-vn) * n[c] + v1 * t1[c]) + v2 * t2[c]);
+            o.nwall++;
+        }
+        for (int c = 0; c < 3; ++c) x0[c] = xh[c];
+        t0 = t0 + sbest;
+        last = best;
+    }
+    o.cell = tet;
+    for (int c = 0; c < 3; ++c) pt.u[c] = u[c];
+    return o;
+}
+
+// Fixed-point image of phi = m (1, u, |u|^2/2) (Sec. 2.2, Eq. W^p): each
+// component scaled by its power-of-two quantum 2^e and rounded to nearest even.
+template <class Real>
+static bool phi_fixed(const Part<Real>& pt, const int* e, int64_t q[5]) {
+    double u0 = (double)pt.u[0], u1 = (double)pt.u[1], u2 = (double)pt.u[2];
+    double m = pt.m;
+    double phi[5] = {m, m * u0, m * u1, m * u2, 0.5 * (m * ((u0 * u0 + u1 * u1) + u2 * u2))};
+    bool ok = true;
+    for (int k = 0; k < 5; ++k) {
+        double v = std::ldexp(phi[k], -e[k]);
+        if (!(std::fabs(v) < 0x1p62)) { ok = false; v = 0.0; }
+        q[k] = std::llrint(v);
+    }
+    return ok;
+}
+
+// ------------------------------------------------------------ simulation
+struct SimBase {
+    Geom g;
+    orc_params P;
+    std::vector<double> W;  // [5][nc]
+    int64_t step = 0;
+    double t = 0.0;
+    int e[5] = {0, 0, 0, 0, 0};
+    // diagnostics of the last step
+    double dt = 0.0;
+    std::vector<double> tau, rhoh, msam, F;
+    std::vector<int64_t> nsam, pflux, smass, scount;
+    int64_t counters[7] = {0, 0, 0, 0, 0, 0, 0};
+    virtual ~SimBase() {}
+    virtual int64_t n_particles() const = 0;
+    virtual int do_step(std::string& err) = 0;
+    virtual void get_particles(uint64_t*, int32_t*, double*, double*, double*) const = 0;
+    virtual bool set_particles(int64_t, const uint64_t*, const int32_t*, const double*, const double*,
+                               const double*, std::string&) = 0;
+    virtual int track_one(uint64_t, int32_t, double*, double*, double, double, int64_t, int32_t*, int32_t*) const = 0;
+};
+
+template <class Real> struct Sim : SimBase {
+    Planes<Real> pl;
+    std::vector<Part<Real>> parts;
+
+    int64_t n_particles() const override { return (int64_t)parts.size(); }
+
+    int do_step(std::string& err) override {
+        const int nc = g.nc, nf = g.nf;
+        const orc_params& p = P;
+        // ---- a1: primitives and relaxation time; W^h density = W - W^p (Sec. 2.2)
+        std::vector<Prim> pr(nc);
+        tau.assign(nc, 0.0); rhoh.assign(nc, 0.0);
+        std::vector<int64_t> mass_q(nc, 0), nleft(nc, 0);
+        for (const auto& pt : parts) {
+            int64_t q[5];
+            phi_fixed(pt, e, q);
+            mass_q[pt.cell] += q[0];
+            nleft[pt.cell] += 1;
+        }
+        std::vector<double> rho_p(nc);
+        for (int i = 0; i < nc; ++i) {
+            double Wi[5];
+            for (int k = 0; k < 5; ++k) Wi[k] = W[(size_t)k * nc + i];
+            pr[i] = prim_of(Wi, p.R);
+            if (!(pr[i].rho > 0.0) || !(pr[i].p > 0.0) || !std::isfinite(pr[i].p)) {
+                err = "non-positive density or pressure in cell " + std::to_string(i);
+                return -9;
+            }
+            tau[i] = tau_cell(pr[i], p);
+            rho_p[i] = std::ldexp((double)mass_q[i], e[0]) / g.vol[i];
+            rhoh[i] = pr[i].rho - rho_p[i];
+        }
+        // ---- a2: time step (Sec. 2.4 (a)), c = 3 sqrt(RT)
+        double rmin = HUGE_VAL;
+        for (int i = 0; i < nc; ++i) {
+            double c = 3.0 * std::sqrt(p.R * pr[i].T);
+            double lam = ((std::fabs(pr[i].U[0]) + c) * g.dS[3 * i] + (std::fabs(pr[i].U[1]) + c) * g.dS[3 * i + 1])
+                       + (std::fabs(pr[i].U[2]) + c) * g.dS[3 * i + 2];
+            double r = g.vol[i] / lam;
+            if (r < rmin) rmin = r;
+        }
+        dt = p.CFL * rmin;
+        // ---- a5: sample the collisionless part of the hydrodynamic wave
+        // (Sec. 2.4 (b)): rho^hp = e^{-dt/tau} rho^h, m_ref, N_sam, m_sam; pairs
+        // u = U +/- sqrt(RT) X, X ~ N(0, I); x uniform in the tet.
+        nsam.assign(nc, 0); msam.assign(nc, 0.0);
+        const size_t n_old = parts.size();
+        int64_t n_sampled = 0;
+        for (int i = 0; i < nc; ++i) {
+            double ex = exp_d(-(dt / tau[i]));
+            double rh = rhoh[i] > 0.0 ? rhoh[i] : 0.0;  // reading: clamp noise-negative rho^h
+            double rhp = ex * rh;
+            double Mhp = rhp * g.vol[i];
+            if (!(Mhp > (pr[i].rho * g.vol[i]) * 0x1p-30)) continue;  // reading: below noise floor
+            double mref = ((rho_p[i] + rhp) * g.vol[i]) / (double)p.N_ref;
+            int64_t ns = 2 * (int64_t)std::ceil(Mhp / (2.0 * mref));
+            int64_t need = (int64_t)p.N_min - nleft[i];
+            if (need > ns) ns = need + (need & 1);
+            if (ns > 65534) { err = "more than 65534 particles sampled in one cell"; return -6; }
+            double ms = Mhp / (double)ns;
+            nsam[i] = ns; msam[i] = ms;
+            double sig = std::sqrt(p.R * pr[i].T);
+            const double *p0 = &g.xyz[3 * (size_t)g.tet[4 * i]], *p1 = &g.xyz[3 * (size_t)g.tet[4 * i + 1]];
+            const double *p2 = &g.xyz[3 * (size_t)g.tet[4 * i + 2]], *p3 = &g.xyz[3 * (size_t)g.tet[4 * i + 3]];
+            for (int64_t j = 0; j < ns / 2; ++j) {
+                uint64_t ida = make_id((uint64_t)step, (uint64_t)i, (uint64_t)(2 * j));
+                Ctr4 r = draw(p.seed, ida, (uint64_t)step, TAG_SVEL, 0);
+                double X[3], sn, cs;
+                double rad = std::sqrt(-2.0 * log_d(u01_d(r.v[0])));
+                sincos2pi_d(u01_d(r.v[1]), &sn, &cs);
+                X[0] = rad * cs; X[1] = rad * sn;
+                rad = std::sqrt(-2.0 * log_d(u01_d(r.v[2])));
+                sincos2pi_d(u01_d(r.v[3]), &sn, &cs);
+                X[2] = rad * cs;
+                for (int side = 0; side < 2; ++side) {
+                    Part<Real> pt;
+                    pt.id = ida + (uint64_t)side;
+                    pt.cell = i;
+                    pt.m = ms;
+                    for (int c = 0; c < 3; ++c)
+                        pt.u[c] = (Real)(side == 0 ? pr[i].U[c] + sig * X[c] : pr[i].U[c] - sig * X[c]);
+                    // Uniform point in the tet: cube -> prism -> tet folding
+                    // (Rocchini and Cignoni, J. Graphics Tools 5(4), 2000).
+                    Ctr4 rp = draw(p.seed, pt.id, (uint64_t)step, TAG_SPOS, 0);
+                    double a = u01_d(rp.v[0]), b = u01_d(rp.v[1]), cc = u01_d(rp.v[2]);
+                    if (a + b > 1.0) { a = 1.0 - a; b = 1.0 - b; }
+                    if (b + cc > 1.0) { double tmp = cc; cc = 1.0 - a - b; b = 1.0 - tmp; }
+                    else if (a + b + cc > 1.0) { double tmp = cc; cc = a + b + cc - 1.0; a = 1.0 - b - tmp; }
+                    for (int c = 0; c < 3; ++c) {
+                        double e1 = p1[c] - p0[c], e2 = p2[c] - p0[c], e3 = p3[c] - p0[c];
+                        pt.x[c] = (Real)(p0[c] + ((a * e1 + b * e2) + cc * e3));
+                    }
+                    parts.push_back(pt);
+                }
+            }
+            n_sampled += ns;
+        }
+        // ---- a6..a9: free-transport time (Eq. t_f), streaming, counting flux
+        // F^{fr,p}_i = sum_{end in i} phi - sum_{start in i} phi (Sec. 2.3),
+        // removal of collisional (t_f < dt) and exited particles (Sec. 2.2).
+        pflux.assign(5 * (size_t)nc, 0);
+        smass.assign(nc, 0); scount.assign(nc, 0);
+        const Real dtR = (Real)dt;
+        std::vector<Part<Real>> kept;
+        kept.reserve(parts.size());
+        int64_t ncoll = 0, nexit = 0, nlost = 0, ncross = 0, nwall = 0;
+        bool overflow = false;
+        for (size_t k = 0; k < parts.size(); ++k) {
+            Part<Real> pt = parts[k];
+            int64_t q0[5], q1[5];
+            overflow |= !phi_fixed(pt, e, q0);
+            const int c0 = pt.cell;
+            Real t_end = dtR;
+            bool coll = false;
+            if (k < n_old) {
+                Ctr4 r = draw(p.seed, pt.id, (uint64_t)step, TAG_TF, 0);
+                Real tf;
+                if (sizeof(Real) == 8) tf = (Real)(-((double)tau[c0] * log_d(u01_d(r.v[0]))));
+                else tf = (Real)(-((float)tau[c0] * log_f(u01_f(r.v[0]))));
+                if (tf < dtR) { coll = true; t_end = tf; }
+            }
+            TrackOut o = track<Real>(g, pl, p, pt, t_end, (uint64_t)step);
+            ncross += o.ncross; nwall += o.nwall;
+            for (int c = 0; c < 5; ++c) pflux[(size_t)c * nc + c0] -= q0[c];
+            if (o.status & ST_EXIT) { nexit++; continue; }
+            if (o.status & ST_LOST) nlost++;
+            pt.cell = o.cell;
+            overflow |= !phi_fixed(pt, e, q1);
+            for (int c = 0; c < 5; ++c) pflux[(size_t)c * nc + o.cell] += q1[c];
+            if (coll && !(o.status & ST_LOST)) { ncoll++; continue; }
+            smass[o.cell] += q1[0];
+            scount[o.cell] += 1;
+            kept.push_back(pt);
+        }
+        counters[0] = (int64_t)parts.size(); counters[1] = ncoll; counters[2] = nexit;
+        counters[3] = nlost; counters[4] = ncross; counters[5] = nwall; counters[6] = n_sampled;
+        parts.swap(kept);
+        // ---- a4: wave flux per face from W^n and rho^{h,n}
+        F.assign(5 * (size_t)nf, 0.0);
+        for (int f = 0; f < nf; ++f) {
+            const double* n = &g.f_n[3 * (size_t)f];
+            int o = g.f_owner[f], nb = g.f_nbr[f];
+            double WL[5], Fv[5];
+            for (int k = 0; k < 5; ++k) WL[k] = W[(size_t)k * nc + o];
+            if (nb >= 0) {
+                double WR[5];
+                for (int k = 0; k < 5; ++k) WR[k] = W[(size_t)k * nc + nb];
+                FaceState L = face_state(WL, rhoh[o], n, p.R), Rs = face_state(WR, rhoh[nb], n, p.R);
+                interior_flux(L, Rs, false, n, dt, p, Fv);
+            } else {
+                boundary_flux(WL, rhoh[o], tau[o], p.bc[g.f_bc[f]], n, dt, p, Fv);
+            }
+            for (int k = 0; k < 5; ++k) F[(size_t)k * nf + f] = Fv[k];
+        }
+        // ---- a10: W^{n+1} = W^n - 1/|Omega| sum_j (F^eq + F^{fr,wave}) |S| + F^{fr,p}/|Omega|
+        for (int i = 0; i < nc; ++i) {
+            for (int q = 0; q < 5; ++q) {
+                double s = 0.0;
+                for (int k = 0; k < 4; ++k) {
+                    int f = g.tet_face[4 * i + k];
+                    double v = F[(size_t)q * nf + f] * g.f_area[f];
+                    s = s + (g.tet_sign[4 * i + k] > 0 ? v : -v);
+                }
+                double fp = std::ldexp((double)pflux[(size_t)q * nc + i], e[q]);
+                double& Wq = W[(size_t)q * nc + i];
+                Wq = (Wq - s / g.vol[i]) + fp / g.vol[i];
+            }
+        }
+        step += 1;
+        t += dt;
+        if (overflow) { err = "fixed-point overflow"; return -8; }
+        if (nlost) { err = std::to_string(nlost) + " particles exceeded max_crossings"; return -7; }
+        return 0;
+    }
+
+    void get_particles(uint64_t* id, int32_t* cell, double* x, double* u, double* m) const override {
+        size_t n = parts.size();
+        for (size_t k = 0; k < n; ++k) {
+            const auto& pt = parts[k];
+            if (id) id[k] = pt.id;
+            if (cell) cell[k] = pt.cell;
+            for (int c = 0; c < 3; ++c) {
+                if (x) x[c * n + k] = (double)pt.x[c];
+                if (u) u[c * n + k] = (double)pt.u[c];
+            }
+            if (m) m[k] = pt.m;
+        }
+    }
+
+    bool set_particles(int64_t n, const uint64_t* id, const int32_t* cell, const double* x,
+                       const double* u, const double* m, std::string& err) override {
+        parts.resize((size_t)n);
+        for (int64_t k = 0; k < n; ++k) {
+            Part<Real>& pt = parts[(size_t)k];
+            pt.id = id[k]; pt.cell = cell[k]; pt.m = m[k];
+            if (pt.cell < 0 || pt.cell >= g.nc) { err = "particle cell out of range"; return false; }
+            for (int c = 0; c < 3; ++c) {
+                pt.x[c] = (Real)x[c * n + k];
+                pt.u[c] = (Real)u[c * n + k];
+                if ((double)pt.x[c] != x[c * n + k] || (double)pt.u[c] != u[c * n + k]) {
+                    err = "particle state not representable in the particle precision"; return false;
+                }
+            }
+        }
+        return true;
+    }
+
+    int track_one(uint64_t id, int32_t cell, double* io_x, double* io_u, double tau_c, double dtv,
+                  int64_t stp, int32_t* cell_out, int32_t* nc_out) const override {
+        Part<Real> pt;
+        pt.id = id; pt.cell = cell; pt.m = 1.0;
+        for (int c = 0; c < 3; ++c) { pt.x[c] = (Real)io_x[c]; pt.u[c] = (Real)io_u[c]; }
+        const Real dtR = (Real)dtv;
+        Real t_end = dtR;
+        int st = 0;
+        if (id_step(id) != (uint64_t)stp) {
+            Ctr4 r = draw(P.seed, id, (uint64_t)stp, TAG_TF, 0);
+            Real tf;
+            if (sizeof(Real) == 8) tf = (Real)(-(tau_c * log_d(u01_d(r.v[0]))));
+            else tf = (Real)(-((float)tau_c * log_f(u01_f(r.v[0]))));
+            if (tf < dtR) { st |= ST_COLL; t_end = tf; }
+        }
+        TrackOut o = track<Real>(g, pl, P, pt, t_end, (uint64_t)stp);
+        for (int c = 0; c < 3; ++c) { io_x[c] = (double)pt.x[c]; io_u[c] = (double)pt.u[c]; }
+        *cell_out = o.cell;
+        *nc_out = o.ncross;
+        return st | o.status;
+    }
+};
+
+// Fixed-point quanta 2^e_q (reading): e_q = ceil(log2 B_q) - 50 with
+// B_mass = max_i rho_i |Omega_i|, B_mom = B_mass c, B_E = B_mass c^2 / 2 and
+// c = max over cells and boundary states of |U| + 5 sqrt(RT).
+static int ceil_log2(double b) {
+    int ex;
+    double mant = std::frexp(b, &ex);
+    return mant == 0.5 ? ex - 1 : ex;
+}
+static void scale_exponents(const Geom& g, const orc_params& P, const std::vector<double>& W, int e[5]) {
+    double bm = 0.0, cmax = 0.0;
+    int nc = g.nc;
+    for (int i = 0; i < nc; ++i) {
+        double Wi[5];
+        for (int k = 0; k < 5; ++k) Wi[k] = W[(size_t)k * nc + i];
+        Prim s = prim_of(Wi, P.R);
+        double mass = s.rho * g.vol[i];
+        if (mass > bm) bm = mass;
+        double c = std::sqrt(dot3(s.U, s.U)) + 5.0 * std::sqrt(P.R * s.T);
+        if (c > cmax) cmax = c;
+    }
+    for (int b = 0; b < P.n_bc; ++b) {
+        const orc_bc& bc = P.bc[b];
+        if (bc.type == ORC_BC_DIFFUSE_WALL) {
+            double c = std::sqrt(dot3(bc.U_w, bc.U_w)) + 5.0 * std::sqrt(P.R * bc.T_w);
+            if (c > cmax) cmax = c;
+        } else if (bc.type == ORC_BC_INFLOW) {
+            Prim s = prim_of(bc.W_in, P.R);
+            double c = std::sqrt(dot3(s.U, s.U)) + 5.0 * std::sqrt(P.R * s.T);
+            if (c > cmax) cmax = c;
+        }
+    }
+    e[0] = ceil_log2(bm) - 50;
+    e[1] = e[2] = e[3] = ceil_log2(bm * cmax) - 50;
+    e[4] = ceil_log2(bm * cmax * cmax * 0.5) - 50;
+}
+
+}  // namespace orc
+
+using namespace orc;
+
+struct orc_sim { SimBase* s; };
+
+static void set_err(char* err, int32_t len, const std::string& msg) {
+    if (err && len > 0) { std::snprintf(err, (size_t)len, "%s", msg.c_str()); }
+}
+
+extern "C" {
+
+void orc_math_d(int which, const double* x, double* y, int64_t n) {
+    for (int64_t k = 0; k < n; ++k) {
+        double s, c;
+        switch (which) {
+            case 0: y[k] = exp_d(x[k]); break;
+            case 1: y[k] = log_d(x[k]); break;
+            case 2: sincos2pi_d(x[k], &s, &c); y[k] = s; break;
+            default: sincos2pi_d(x[k], &s, &c); y[k] = c; break;
+        }
+    }
+}
+
+void orc_math_logf(const float* x, float* y, int64_t n) {
+    for (int64_t k = 0; k < n; ++k) y[k] = log_f(x[k]);
+}
+
+void orc_philox(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+    Ctr4 c;
+    for (int k = 0; k < 4; ++k) c.v[k] = ctr[k];
+    Ctr4 r = philox4x64_10(c, key[0], key[1]);
+    for (int k = 0; k < 4; ++k) out[k] = r.v[k];
+}
+
+void orc_qcoef(double dt, double tau, double q[7]) { qcoef(dt, tau, q); }
+
+void orc_maxwell_moments(const double U[3], double lam, const double n[3], int half,
+                         double H[5], double G[5]) {
+    double Un = dot3(U, n), Ut[3];
+    for (int d = 0; d < 3; ++d) Ut[d] = U[d] - Un * n[d];
+    half_moments(Un, Ut, n, lam, half, H, G);
+}
+
+int orc_face_flux(const orc_params* p, int kind, const double WL[5], double rhohL,
+                  const double WR[5], double rhohR, const double n[3], double dt,
+                  double tau_wall, const orc_bc* bc, double F[5]) {
+    if (kind == 0) {
+        FaceState L = face_state(WL, rhohL, n, p->R), R = face_state(WR, rhohR, n, p->R);
+        interior_flux(L, R, false, n, dt, *p, F);
+        return 0;
+    }
+    if (!bc) return -1;
+    boundary_flux(WL, rhohL, tau_wall, *bc, n, dt, *p, F);
+    return 0;
+}
+
+orc_sim* orc_create(const orc_params* p, int32_t n_nodes, const double* xyz,
+                    int32_t n_tets, const int32_t* tets, int32_t n_bfaces,
+                    const int32_t* bfaces, const int32_t* btags, const double* W0,
+                    char* err, int32_t errlen) {
+    std::string e;
+    if (p->order != 1) { set_err(err, errlen, "only first-order reconstruction is implemented"); return nullptr; }
+    if (p->n_bc < 0 || p->n_bc > 16) { set_err(err, errlen, "n_bc out of range"); return nullptr; }
+    if (n_tets >= (1 << 24)) { set_err(err, errlen, "too many tets for the particle id layout"); return nullptr; }
+    SimBase* s = nullptr;
+    if (p->precision == ORC_MIXED) s = new Sim<float>(); else s = new Sim<double>();
+    s->P = *p;
+    if (!build_geometry(s->g, n_nodes, xyz, n_tets, tets, n_bfaces, bfaces, btags, p->n_bc, e)) {
+        delete s; set_err(err, errlen, e); return nullptr;
+    }
+    if (p->precision == ORC_MIXED) static_cast<Sim<float>*>(s)->pl.build(s->g);
+    else static_cast<Sim<double>*>(s)->pl.build(s->g);
+    s->W.assign(W0, W0 + 5 * (size_t)n_tets);
+    scale_exponents(s->g, s->P, s->W, s->e);
+    orc_sim* h = new orc_sim;
+    h->s = s;
+    return h;
+}
+
+void orc_free(orc_sim* h) {
+    if (!h) return;
+    delete h->s;
+    delete h;
+}
+
+int orc_step(orc_sim* h, char* err, int32_t errlen) {
+    std::string e;
+    int rc = h->s->do_step(e);
+    if (rc) set_err(err, errlen, e);
+    return rc;
+}
+
+void orc_sizes(const orc_sim* h, int64_t out[5]) {
+    out[0] = h->s->g.nc; out[1] = h->s->g.nf; out[2] = h->s->g.nbf;
+    out[3] = h->s->n_particles(); out[4] = h->s->step;
+}
+
+int orc_geometry(const orc_sim* h, int which, double* out) {
+    const Geom& g = h->s->g;
+    int nc = g.nc, nf = g.nf;
+    switch (which) {
+        case 0: for (int i = 0; i < nc; ++i) out[i] = g.vol[i]; return 0;
+        case 1: for (int i = 0; i < nc; ++i) for (int d = 0; d < 3; ++d) out[(size_t)d * nc + i] = g.cen[3 * i + d]; return 0;
+        case 2: for (int f = 0; f < nf; ++f) for (int d = 0; d < 3; ++d) out[(size_t)d * nf + f] = g.f_n[3 * (size_t)f + d]; return 0;
+        case 3: for (int f = 0; f < nf; ++f) out[f] = g.f_area[f]; return 0;
+        case 4: for (int f = 0; f < nf; ++f) out[f] = g.f_owner[f]; return 0;
+        case 5: for (int f = 0; f < nf; ++f) out[f] = g.f_nbr[f]; return 0;
+        case 6: for (int i = 0; i < nc; ++i) for (int d = 0; d < 3; ++d) out[(size_t)d * nc + i] = g.dS[3 * i + d]; return 0;
+        case 7: for (int f = 0; f < nf; ++f) out[f] = g.f_d[f]; return 0;
+        default: return -1;
+    }
+}
+
+void orc_get_state(const orc_sim* h, double* W, uint64_t* id, int32_t* cell,
+                   double* x, double* u, double* m, int64_t* scal, double* t) {
+    const SimBase* s = h->s;
+    if (W) std::memcpy(W, s->W.data(), s->W.size() * sizeof(double));
+    s->get_particles(id, cell, x, u, m);
+    if (scal) { scal[0] = s->step; for (int k = 0; k < 5; ++k) scal[1 + k] = s->e[k]; }
+    if (t) *t = s->t;
+}
+
+int orc_set_state(orc_sim* h, const double* W, int64_t n, const uint64_t* id,
+                  const int32_t* cell, const double* x, const double* u, const double* m,
+                  const int64_t* scal, double t, char* err, int32_t errlen) {
+    SimBase* s = h->s;
+    std::string e;
+    if (!s->set_particles(n, id, cell, x, u, m, e)) { set_err(err, errlen, e); return -1; }
+    std::memcpy(s->W.data(), W, s->W.size() * sizeof(double));
+    s->step = scal[0];
+    for (int k = 0; k < 5; ++k) s->e[k] = (int)scal[1 + k];
+    s->t = t;
+    return 0;
+}
+
+int orc_last(const orc_sim* h, int which, void* out) {
+    const SimBase* s = h->s;
+    switch (which) {
+        case 0: *(double*)out = s->dt; return 0;
+        case 1: std::memcpy(out, s->tau.data(), s->tau.size() * 8); return 0;
+        case 2: std::memcpy(out, s->rhoh.data(), s->rhoh.size() * 8); return 0;
+        case 3: std::memcpy(out, s->nsam.data(), s->nsam.size() * 8); return 0;
+        case 4: std::memcpy(out, s->msam.data(), s->msam.size() * 8); return 0;
+        case 5: std::memcpy(out, s->F.data(), s->F.size() * 8); return 0;
+        case 6: std::memcpy(out, s->pflux.data(), s->pflux.size() * 8); return 0;
+        case 7: std::memcpy(out, s->smass.data(), s->smass.size() * 8); return 0;
+        case 8: std::memcpy(out, s->scount.data(), s->scount.size() * 8); return 0;
+        case 9: std::memcpy(out, s->counters, sizeof(s->counters)); return 0;
+        default: return -1;
+    }
+}
+
+int orc_track_one(const orc_sim* h, uint64_t id, int32_t cell, double* io_x, double* io_u,
+                  double tau_cell_v, double dt, int64_t step, int32_t* cell_out, int32_t* ncross) {
+    return h->s->track_one(id, cell, io_x, io_u, tau_cell_v, dt, step, cell_out, ncross);
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+/* Plain CPU oracle of one UGKWP time step (arXiv 2007.13091, Sec. 2).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the slow, obviously correct
+ * reference that the CUDA path is checked against.  Only tests/,
+ * __graft_entry__.smoke() and bench.py's CPU-baseline leg may load it; the
+ * product (the ugkwp C-ABI library) never links, loads or calls it, and it
+ * shares no code, header or constant with that library.
+ *
+ * Arrays of per-cell quantities are structure-of-arrays: component q of cell
+ * i is at [q * n_cells + i].  Particle arrays are indexed by particle; vector
+ * quantities are [component * n + k].
+ */
+#ifndef UGKWP_ORACLE_H
+#define UGKWP_ORACLE_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_BC_DIFFUSE_WALL = 1, ORC_BC_SPECULAR = 2, ORC_BC_INFLOW = 3, ORC_BC_OUTFLOW = 4 };
+enum { ORC_FP64 = 0, ORC_MIXED = 1 };
+
+typedef struct {
+    int32_t type;      /* ORC_BC_* */
+    int32_t pad_;
+    double T_w;        /* wall temperature (diffuse wall) */
+    double U_w[3];     /* wall velocity (diffuse wall), tangential */
+    double W_in[5];    /* conservative state of the far field (inflow) */
+} orc_bc;
+
+typedef struct {
+    double R, mu_ref, T_ref, omega, CFL, C2;
+    int32_t order, N_ref, N_min, precision, max_crossings, n_bc;
+    uint64_t seed;
+    orc_bc bc[16];
+} orc_params;
+
+typedef struct orc_sim orc_sim;
+
+/* ---- elementary pins ---------------------------------------------------- */
+/* which: 0 exp_d, 1 log_d, 2 sin(2 pi x), 3 cos(2 pi x) */
+void orc_math_d(int which, const double* x, double* y, int64_t n);
+void orc_math_logf(const float* x, float* y, int64_t n);
+void orc_philox(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+/* q1..q5, then the two free-transport coefficients of the collisional wave:
+ * a4 = q4 - dt e^{-dt/tau}, a5 = q5 + dt^2/2 e^{-dt/tau}. */
+void orc_qcoef(double dt, double tau, double q[7]);
+/* Moments of a unit-density Maxwellian (U, lambda) with K = 0, normal n:
+ * H[5] = int_{half} g psi du, G[5] = int_{half} u.n g psi du,
+ * half = +1 (u.n > 0), -1 (u.n < 0) or 0 (all u). */
+void orc_maxwell_moments(const double U[3], double lam, const double n[3], int half,
+                         double H[5], double G[5]);
+/* Time-integrated wave flux of one face (F^eq + F^{fr,wave}, per unit area,
+ * normal from L to R).  kind: 0 interior, or an ORC_BC_* type with the ghost
+ * built from WL (and bc).  rhoh = hydrodynamic density rho^h of each side. */
+int orc_face_flux(const orc_params* p, int kind, const double WL[5], double rhohL,
+                  const double WR[5], double rhohR, const double n[3], double dt,
+                  double tau_wall, const orc_bc* bc, double F[5]);
+
+/* ---- simulation --------------------------------------------------------- */
+orc_sim* orc_create(const orc_params* p, int32_t n_nodes, const double* xyz,
+                    int32_t n_tets, const int32_t* tets, int32_t n_bfaces,
+                    const int32_t* bfaces, const int32_t* btags, const double* W0,
+                    char* err, int32_t errlen);
+void orc_free(orc_sim* s);
+int orc_step(orc_sim* s, char* err, int32_t errlen);
+
+/* sizes: [n_cells, n_faces, n_boundary_faces, n_particles, step] */
+void orc_sizes(const orc_sim* s, int64_t out[5]);
+/* Geometry (which): 0 vol[nc], 1 centroid[3][nc], 2 face normal[3][nf],
+ * 3 face area[nf], 4 face owner (as double)[nf], 5 face neighbour (-1 boundary)[nf],
+ * 6 dS[3][nc], 7 face plane offset d[nf] */
+int orc_geometry(const orc_sim* s, int which, double* out);
+/* State export.  Any pointer may be NULL.  scal = [step, e_0..e_4] (int64),
+ * t = simulation time. */
+void orc_get_state(const orc_sim* s, double* W, uint64_t* id, int32_t* cell,
+                   double* x, double* u, double* m, int64_t* scal, double* t);
+/* State import (teacher forcing).  Positions/velocities must be exactly
+ * representable in the particle precision. */
+int orc_set_state(orc_sim* s, const double* W, int64_t n, const uint64_t* id,
+                  const int32_t* cell, const double* x, const double* u, const double* m,
+                  const int64_t* scal, double t, char* err, int32_t errlen);
+/* Diagnostics of the last step (which):
+ *  0 dt (1 value), 1 tau[nc], 2 rho_h[nc] (before sampling), 3 n_sam[nc],
+ *  4 m_sam[nc], 5 wave flux F[5][nf], 6 particle flux F^{fr,p}[5][nc] (fixed point,
+ *  int64 written as raw 8 bytes), 7 survivor mass sum[nc] (int64 raw),
+ *  8 survivor count[nc], 9 counters [n_tracked, n_collided, n_exited, n_lost,
+ *  n_crossings, n_wall_hits, n_sampled] */
+int orc_last(const orc_sim* s, int which, void* out);
+
+/* Track one particle with the simulation's mesh and parameters (sampled checks
+ * at sizes where a whole oracle step would be slow).  io_x/io_u are [3];
+ * the particle precision follows the simulation.  Returns the status bits
+ * 1 collided, 2 exited, 4 lost; *cell_out the end tet; *ncross the crossings. */
+int orc_track_one(const orc_sim* s, uint64_t id, int32_t cell, double* io_x, double* io_u,
+                  double tau_cell, double dt, int64_t step, int32_t* cell_out, int32_t* ncross);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,265 @@
+"""Seeded synthetic workloads shaped like the paper's test cases.
+
+Input generation only: tetrahedral meshes (structured hexahedra split into six
+tets, optional grading, node jitter and carving), initial conservative states
+and gas parameters.  None of the UGKWP arithmetic lives here; both the CUDA
+path and the CPU oracle consume exactly these arrays and dicts.
+
+Conventions
+-----------
+* mesh = {"nodes": [nn,3] f64, "tets": [nc,4] i32 (positive volume),
+  "bfaces": [nb,3] i32, "btags": [nb] i32 (index into params["bc"])}
+* W0 = [5, nc] f64 conservative state (rho, rho U, rho E) with
+  rho E = 1/2 rho |U|^2 + 3/2 p (monatomic, K = 0), R = 1.
+* params = dict with R, mu_ref, T_ref, omega, CFL, C2, order, N_ref, N_min,
+  precision ('fp64' | 'mixed'), seed, max_crossings, bc (list of dicts with
+  type 'wall' | 'specular' | 'farfield' (alias 'inflow') | 'outflow', T_w,
+  U_w, W_in) and
+  particle_capacity (device buffers).
+"""
+import math
+
+import numpy as np
+
+GAMMA = 5.0 / 3.0
+
+# The six tets of the Kuhn split of a unit hex share its main diagonal; tet
+# (a,b,c) walks 000 -> e_a -> e_a+e_b -> 111.  Using the same diagonal in every
+# hex makes the split conforming across hex faces.
+_PERMS = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+
+
+def _hex_corner_offsets():
+    tets = []
+    for a, b, c in _PERMS:
+        p0 = (0, 0, 0)
+        p1 = [0, 0, 0]
+        p1[a] = 1
+        p2 = list(p1)
+        p2[b] = 1
+        tets.append([p0, tuple(p1), tuple(p2), (1, 1, 1)])
+    return np.array(tets, dtype=np.int64)  # [6, 4, 3]
+
+
+def structured_tet_mesh(xs, ys, zs, keep=None):
+    """Tet mesh of the tensor grid xs x ys x zs (each hex -> 6 Kuhn tets).
+
+    keep: optional bool array [nx, ny, nz]; hexes with False are removed.
+    Returns (nodes, tets, bfaces, where) with where in 0..5 for the box sides
+    x-, x+, y-, y+, z-, z+ and 6 for faces exposed by removed hexes.
+    """
+    xs, ys, zs = (np.asarray(v, dtype=np.float64) for v in (xs, ys, zs))
+    nx, ny, nz = len(xs) - 1, len(ys) - 1, len(zs) - 1
+    if keep is None:
+        keep = np.ones((nx, ny, nz), dtype=bool)
+    hi, hj, hk = np.nonzero(keep)
+    off = _hex_corner_offsets()
+    I = hi[:, None, None] + off[None, :, :, 0]
+    J = hj[:, None, None] + off[None, :, :, 1]
+    K = hk[:, None, None] + off[None, :, :, 2]
+    gid = (I * (ny + 1) + J) * (nz + 1) + K  # [nh, 6, 4]
+    tets = gid.reshape(-1, 4)
+    used, inv = np.unique(tets, return_inverse=True)
+    tets = inv.reshape(-1, 4).astype(np.int64)
+    gi = used // ((ny + 1) * (nz + 1))
+    gj = (used // (nz + 1)) % (ny + 1)
+    gk = used % (nz + 1)
+    nodes = np.stack([xs[gi], ys[gj], zs[gk]], axis=1)
+    vol = _volumes(nodes, tets)
+    neg = vol < 0
+    tets[neg] = tets[neg][:, [0, 1, 3, 2]]
+    bfaces = boundary_faces(tets)
+    where = np.full(len(bfaces), 6, dtype=np.int32)
+    p = nodes[bfaces]  # [nb, 3, 3]
+    for axis, (lo, hi_) in enumerate(((xs[0], xs[-1]), (ys[0], ys[-1]), (zs[0], zs[-1]))):
+        where[np.all(p[:, :, axis] == lo, axis=1)] = 2 * axis
+        where[np.all(p[:, :, axis] == hi_, axis=1)] = 2 * axis + 1
+    return nodes, tets.astype(np.int32), bfaces.astype(np.int32), where
+
+
+def _volumes(nodes, tets):
+    p = nodes[tets]
+    a, b, c = p[:, 1] - p[:, 0], p[:, 2] - p[:, 0], p[:, 3] - p[:, 0]
+    return np.einsum("ij,ij->i", a, np.cross(b, c)) / 6.0
+
+
+def boundary_faces(tets):
+    """Faces (node triples) that belong to exactly one tet."""
+    tets = np.asarray(tets, dtype=np.int64)
+    f = tets[:, [[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]]].reshape(-1, 3)
+    s = np.sort(f, axis=1)
+    n = int(tets.max()) + 1
+    key = (s[:, 0] * n + s[:, 1]) * n + s[:, 2]
+    _, first, counts = np.unique(key, return_index=True, return_counts=True)
+    return f[first[counts == 1]]
+
+
+def jitter(nodes, tets, bfaces, amount, spacing, seed, min_ratio=0.2):
+    """Move interior nodes by amount * spacing * U(-1,1)^3, keeping every tet
+    volume above min_ratio of its unjittered volume (offending nodes are pulled
+    back by halving their displacement)."""
+    rng = np.random.default_rng(seed)
+    nodes = np.asarray(nodes, dtype=np.float64)
+    v0 = _volumes(nodes, tets)
+    interior = np.ones(len(nodes), dtype=bool)
+    interior[np.unique(bfaces)] = False
+    h = np.asarray(spacing, dtype=np.float64)
+    h = h[:, None] if h.ndim == 1 else h
+    disp = rng.uniform(-1.0, 1.0, size=nodes.shape) * amount * h
+    disp[~interior] = 0.0
+    for _ in range(60):
+        trial = nodes + disp
+        bad = _volumes(trial, tets) < min_ratio * v0
+        if not bad.any():
+            return trial
+        disp[np.unique(tets[bad])] *= 0.5
+    return nodes
+
+
+def conservative(rho, U, p):
+    rho = np.asarray(rho, dtype=np.float64)
+    U = np.asarray(U, dtype=np.float64)
+    p = np.asarray(p, dtype=np.float64)
+    U = np.broadcast_to(U, rho.shape + (3,)) if U.ndim == 1 else U
+    W = np.empty((5,) + rho.shape)
+    W[0] = rho
+    W[1:4] = np.moveaxis(rho[..., None] * U, -1, 0)
+    W[4] = 0.5 * rho * np.sum(U * U, axis=-1) + 1.5 * p
+    return W
+
+
+def mu_ref_vhs(Kn, omega, rho_ref=1.0, T_ref=1.0, L=1.0, R=1.0):
+    """Reference viscosity giving the VHS mean free path Kn*L at (rho_ref, T_ref):
+    lambda = 2(5-2w)(7-2w)/15 * mu / (rho sqrt(2 pi R T))."""
+    return 15.0 * rho_ref * Kn * L * math.sqrt(2.0 * math.pi * R * T_ref) / (
+        2.0 * (5.0 - 2.0 * omega) * (7.0 - 2.0 * omega))
+
+
+def centroids(nodes, tets):
+    return nodes[tets].mean(axis=1)
+
+
+def _params(Kn, omega, CFL, N_ref, precision, seed, bc, C2=0.0, N_min=0, capacity=None,
+            n_cells=None, max_crossings=1000):
+    cap = capacity if capacity is not None else int(3 * N_ref * n_cells + 4096)
+    return {"R": 1.0, "mu_ref": mu_ref_vhs(Kn, omega), "T_ref": 1.0, "omega": omega, "CFL": CFL,
+            "C2": C2, "order": 1, "N_ref": N_ref, "N_min": N_min, "precision": precision,
+            "seed": seed, "max_crossings": max_crossings, "bc": bc, "particle_capacity": cap,
+            "Kn": Kn}
+
+
+def shock_tube(nx=100, ny=4, nz=4, Kn=1e-2, N_ref=50, precision="fp64", CFL=0.5, seed=1,
+               omega=0.81, C2=0.0, length=1.0, width=0.04):
+    """3D Sod tube [0,1] x [0,0.04]^2: left rho=1, p=1; right rho=0.125, p=0.1;
+    far-field (outflow) ends, specular side walls."""
+    xs = np.linspace(0.0, length, nx + 1)
+    ys = np.linspace(0.0, width, ny + 1)
+    zs = np.linspace(0.0, width, nz + 1)
+    nodes, tets, bf, where = structured_tet_mesh(xs, ys, zs)
+    btags = np.where(where <= 1, where, 2).astype(np.int32)
+    c = centroids(nodes, tets)
+    left = c[:, 0] < 0.5 * length
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    W0 = conservative(rho, np.zeros(3), p)
+    # far-field ends hold the undisturbed left and right states
+    WL = conservative(np.array(1.0), np.zeros(3), np.array(1.0))
+    WR = conservative(np.array(0.125), np.zeros(3), np.array(0.1))
+    bc = [{"type": "farfield", "W_in": tuple(float(v) for v in WL)},
+          {"type": "farfield", "W_in": tuple(float(v) for v in WR)}, {"type": "specular"}]
+    params = _params(Kn, omega, CFL, N_ref, precision, seed, bc, C2=C2, n_cells=len(tets))
+    return {"name": f"shock_tube_{nx}x{ny}x{nz}", "mesh": {"nodes": nodes, "tets": tets, "bfaces": bf,
+            "btags": btags}, "W0": W0, "params": params}
+
+
+def cavity(n=24, Kn=0.075, N_ref=100, precision="mixed", CFL=0.5, seed=2, omega=0.81, lid_mach=0.16):
+    """Lid-driven cubic cavity: unit cube, all walls diffuse at T0 = 1, the z = 1
+    lid moving at U = (lid_mach sqrt(gamma R T0), 0, 0); gas at rest, rho = 1."""
+    xs = np.linspace(0.0, 1.0, n + 1)
+    nodes, tets, bf, where = structured_tet_mesh(xs, xs, xs)
+    btags = (where == 5).astype(np.int32)
+    W0 = conservative(np.ones(len(tets)), np.zeros(3), np.ones(len(tets)))
+    Ulid = lid_mach * math.sqrt(GAMMA)
+    bc = [{"type": "wall", "T_w": 1.0, "U_w": (0.0, 0.0, 0.0)},
+          {"type": "wall", "T_w": 1.0, "U_w": (Ulid, 0.0, 0.0)}]
+    params = _params(Kn, omega, CFL, N_ref, precision, seed, bc, n_cells=len(tets))
+    return {"name": f"cavity_{n}^3", "mesh": {"nodes": nodes, "tets": tets, "bfaces": bf, "btags": btags},
+            "W0": W0, "params": params}
+
+
+def graded_axis(lo, hi, c_lo, c_hi, h0, growth, h_max=None):
+    """Coordinates over [lo, hi] with uniform spacing h0 on [c_lo, c_hi] and
+    spacing growing geometrically by `growth` away from it (capped at h_max)."""
+    core = np.linspace(c_lo, c_hi, int(round((c_hi - c_lo) / h0)) + 1)
+    right, left = [], []
+    h, x = h0, c_hi
+    while x < hi - 1e-12:
+        h = h * growth if h_max is None else min(h * growth, h_max)
+        x = min(x + h, hi)
+        if hi - x < 0.3 * h:
+            x = hi
+        right.append(x)
+    h, x = h0, c_lo
+    while x > lo + 1e-12:
+        h = h * growth if h_max is None else min(h * growth, h_max)
+        x = max(x - h, lo)
+        if x - lo < 0.3 * h:
+            x = lo
+        left.append(x)
+    return np.concatenate([np.array(left[::-1]), core, np.array(right)])
+
+
+def cube_flow(h0=0.05, growth=1.5, Kn=0.1, mach=4.0, N_ref=200, precision="mixed", CFL=0.5, seed=3,
+              omega=0.81, jitter_amount=0.1, h_max=None):
+    """Hypersonic flow past a unit cube [-0.5,0.5]^3 in the box [-6,10] x [-6,6]^2:
+    graded hexes (growth from the cube), Kuhn tets, jittered interior nodes;
+    far-field free stream (Maxwellian at Ma `mach`) on all box sides (tag 0 at
+    x = -6, tag 1 elsewhere), diffuse cube wall at T_w = T_inf (tag 2)."""
+    xs = graded_axis(-6.0, 10.0, -0.5, 0.5, h0, growth, h_max)
+    ys = graded_axis(-6.0, 6.0, -0.5, 0.5, h0, growth, h_max)
+    zs = ys
+    cx, cy, cz = (0.5 * (a[1:] + a[:-1]) for a in (xs, ys, zs))
+    inside = (np.abs(cx)[:, None, None] < 0.5) & (np.abs(cy)[None, :, None] < 0.5) & (np.abs(cz)[None, None, :] < 0.5)
+    nodes, tets, bf, where = structured_tet_mesh(xs, ys, zs, keep=~inside)
+    # local spacing per node: the smaller adjacent interval along each axis
+    def local_h(a, v):
+        d = np.diff(a)
+        hl = np.concatenate([[d[0]], d])
+        hr = np.concatenate([d, [d[-1]]])
+        idx = np.searchsorted(a, v)
+        idx = np.clip(idx, 0, len(a) - 1)
+        return np.minimum(hl[idx], hr[idx])
+    h = np.minimum(np.minimum(local_h(xs, nodes[:, 0]), local_h(ys, nodes[:, 1])), local_h(zs, nodes[:, 2]))
+    if jitter_amount > 0:
+        nodes = jitter(nodes, tets, bf, jitter_amount, h, seed)
+    btags = np.where(where == 0, 0, np.where(where == 6, 2, 1)).astype(np.int32)
+    Uinf = mach * math.sqrt(GAMMA)
+    W_in = conservative(np.array(1.0), np.array([Uinf, 0.0, 0.0]), np.array(1.0))
+    W0 = conservative(np.ones(len(tets)), np.array([Uinf, 0.0, 0.0]), np.ones(len(tets)))
+    bc = [{"type": "farfield", "W_in": tuple(float(v) for v in W_in)},
+          {"type": "farfield", "W_in": tuple(float(v) for v in W_in)},
+          {"type": "wall", "T_w": 1.0, "U_w": (0.0, 0.0, 0.0)}]
+    params = _params(Kn, omega, CFL, N_ref, precision, seed, bc, n_cells=len(tets))
+    return {"name": f"cube_ma{mach:g}_{len(tets)}tets", "mesh": {"nodes": nodes, "tets": tets, "bfaces": bf,
+            "btags": btags}, "W0": W0, "params": params}
+
+
+def uniform_box(n=(3, 3, 3), size=(1.0, 1.0, 1.0), rho=1.0, U=(0.0, 0.0, 0.0), p=1.0, Kn=0.1, N_ref=20,
+                precision="fp64", CFL=0.5, seed=7, bc_type="specular", T_w=1.0, omega=0.81,
+                jitter_amount=0.0):
+    """Box of n hexes (x 6 tets), one boundary condition on all sides, uniform gas."""
+    xs, ys, zs = (np.linspace(0.0, s, k + 1) for k, s in zip(n, size))
+    nodes, tets, bf, where = structured_tet_mesh(xs, ys, zs)
+    if jitter_amount > 0:
+        h = min(s / k for k, s in zip(n, size))
+        nodes = jitter(nodes, tets, bf, jitter_amount, h, seed)
+    btags = np.zeros(len(bf), dtype=np.int32)
+    W0 = conservative(np.full(len(tets), rho), np.asarray(U, dtype=np.float64), np.full(len(tets), p))
+    b = {"type": bc_type}
+    if bc_type == "wall":
+        b.update(T_w=T_w, U_w=(0.0, 0.0, 0.0))
+    if bc_type in ("inflow", "farfield"):
+        b.update(W_in=tuple(float(v) for v in conservative(np.array(rho), np.asarray(U, float), np.array(p))))
+    params = _params(Kn, omega, CFL, N_ref, precision, seed, [b], n_cells=len(tets))
+    return {"name": "uniform_box", "mesh": {"nodes": nodes, "tets": tets, "bfaces": bf, "btags": btags},
+            "W0": W0, "params": params}
