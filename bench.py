@@ -1,0 +1,358 @@
+"""Benchmark of the UGKWP step on one GB300 (one JSON line on stdout).
+
+Workload: the lid-driven cubic cavity (24^3 hexes x 6 = 82,944 tets, argon-like
+VHS gas, Kn 0.075, diffuse walls, lid Mach 0.16, 100 reference particles per
+cell, ~8.3e6 particles), MIXED precision (binary32 particles, binary64 cells,
+int64 fixed-point particle flux).  A step is one full UGKWP time step.
+
+  value      particle-moves/s, device time (CUDA events on the library's stream)
+  roofline   the tracking kernel (a6-a9) against the measured HBM copy bandwidth
+  fp64       the same workload with binary64 particles
+  field_error MIXED vs FP64 after a fixed number of steps, with the Monte-Carlo
+             noise floor (two FP64 runs with different seeds)
+  e2e        per step: state import from host buffers, step, W back to host
+  cpu_baseline the CPU oracle (single thread) on a bounded sample
+
+Multi-GPU: replicas only (each rank runs its own simulation; value = all
+ranks' moves / max time).  --impl reference times the CPU oracle instead.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-moves/s & cell-steps/s on 1 GB300: mixed vs FP64 at fixed error"
+UNIT = "particle-moves/s"
+# minimum bytes the tracking kernel moves (MIXED / FP64): read the particle
+# record (x, u, m, cell, id) and write back position and cell
+TRACK_BYTES_PER_MOVE = {"mixed": 44 + 16, "fp64": 68 + 28}
+# per cell and step: tracking record (planes + neighbours) and tau
+TRACK_BYTES_PER_CELL = {"mixed": 80 + 8, "fp64": 144 + 8}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload(precision, seed=None):
+    from paper_2007_13091_gb300 import workloads as wl
+    cfg = wl.cavity(n=24, Kn=0.075, N_ref=100, precision=precision)
+    if seed is not None:
+        cfg["params"]["seed"] = seed
+    return cfg
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, busy_fraction_min=0.0):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                if self.uuid and parts[0] != self.uuid:
+                    continue
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def time_steps(sim, steps, warmup, ws, timing=True):
+    """Device time of `steps` steps after `warmup`; returns (ms, moves, launches, kernel ms)."""
+    import torch
+    from paper_2007_13091_gb300 import ugkwp
+    sim.step(warmup)
+    st0 = sim.step(0, stats=True)
+    ms0, l0 = ugkwp.ugkwp_timing_read(sim.handle)
+    ugkwp.ugkwp_timing_enable(sim.handle, timing)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(sim.stream)
+    sim.step(steps)
+    e1.record(sim.stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    ugkwp.ugkwp_timing_enable(sim.handle, False)
+    kms, l1 = ugkwp.ugkwp_timing_read(sim.handle)
+    st1 = sim.step(0, stats=True)
+    moves = st1["n_moves_total"] - st0["n_moves_total"]
+    launches = sum(l1.values()) - sum(l0.values())
+    return ms, moves, launches, kms, st1
+
+
+def field_error(steps, device):
+    """Per-field relative L2 of MIXED vs FP64 after `steps` steps from the same
+    initial state and seed, and the FP64 seed-to-seed noise floor."""
+    from paper_2007_13091_gb300 import ugkwp
+
+    def prim(precision, seed):
+        cfg = workload(precision, seed)
+        sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device)
+        sim.step(steps)
+        P = sim.moments(ugkwp.PRIM)
+        sim.close()
+        rho, U, T = P[0], P[1:4], P[4]
+        return {"rho": rho, "U": U, "T": T, "p": rho * T}
+
+    a, b, c = prim("mixed", 2), prim("fp64", 2), prim("fp64", 1002)
+
+    def rel(x, y):
+        return float(np.linalg.norm(x - y) / np.linalg.norm(y))
+    # velocity error relative to the lid speed scale (the cavity starts at rest)
+    ulid = 0.16 * math.sqrt(5.0 / 3.0)
+    uerr = lambda x, y: float(np.linalg.norm(x - y) / (ulid * math.sqrt(y.shape[1])))
+    err = {k: rel(a[k], b[k]) for k in ("rho", "T", "p")}
+    err["U"] = uerr(a["U"], b["U"])
+    floor = {k: rel(c[k], b[k]) for k in ("rho", "T", "p")}
+    floor["U"] = uerr(c["U"], b["U"])
+    return {"steps": steps, "mixed_vs_fp64": err, "noise_floor_fp64_seed": floor}
+
+
+def e2e(cfg, steps, device):
+    """Per step through the C-ABI with host buffers: import the state from host
+    arrays, one step, read W back to host memory."""
+    import torch
+    from paper_2007_13091_gb300 import ugkwp
+    sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device)
+    sim.step(2)
+    state = sim.state()
+    n = state["id"].size
+    h2d = state["W"].nbytes + state["id"].nbytes + state["cell"].nbytes + state["x"].nbytes + \
+        state["u"].nbytes + state["m"].nbytes
+    d2h = state["W"].nbytes
+    torch.cuda.synchronize()
+    moves = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.set_state(state)
+        st = sim.step(1, stats=True)
+        moves += st["n_tracked"]
+        sim.moments(ugkwp.W)
+    t1 = time.perf_counter()
+    sim.close()
+    return {"value": moves / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "steps": steps, "particles": int(n)}
+
+
+def cpu_baseline(steps):
+    """The CPU oracle (single thread) on the same workload: one untimed step
+    samples the particle population, then `steps` timed steps."""
+    import oracle
+    cfg = workload("mixed")
+    s = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    s.step()
+    moves = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.step()
+        moves += s.last("counters")["n_tracked"]
+    t1 = time.perf_counter()
+    return {"value": moves / (t1 - t0), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"cavity 24^3x6 tets, N_ref 100, MIXED: {steps} oracle steps after one sampling step "
+                      f"({moves} particle moves, {t1 - t0:.1f} s)",
+            "cell_steps_per_s": len(cfg["mesh"]["tets"]) * steps / (t1 - t0)}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    steps = max(1, min(args.steps, 4))
+    warm = max(1, min(args.warmup, 1))
+    import oracle
+    cfg = workload("mixed")
+    s = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    s.step(warm)
+    moves = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.step()
+        moves += s.last("counters")["n_tracked"]
+    dt = time.perf_counter() - t0
+    v = moves / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
+            "warmup": warm, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 cells / f32 particles (oracle)", "data": "synthetic",
+            "config": {"workload": "lid-driven cavity 24^3 hexes x 6 = 82944 tets, Kn 0.075, N_ref 100, MIXED",
+                       "sample": f"{steps} of the requested {args.steps} steps (CPU oracle, single thread)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{steps} oracle steps after {warm} warm-up step(s), {moves} moves"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ugkwp", choices=["ugkwp", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-extras", action="store_true", help="skip FP64, field error, e2e and CPU baseline")
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    device = f"cuda:{local}"
+    from paper_2007_13091_gb300 import ugkwp
+    ugkwp.lib()
+    stream = torch.cuda.Stream(device=device)
+    cfg = workload(args.precision)
+    nc = len(cfg["mesh"]["tets"])
+    sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=stream)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    with ClockSampler(uuid) as clk:
+        ms, moves, launches, kms, st = time_steps(sim, args.steps, args.warmup, ws)
+    clocks = clk.summary()
+    ms_max = reduce_max(ms, ws)
+    moves_all = reduce_sum(moves, ws)
+    value = moves_all / (ms_max * 1e-3)
+    cell_steps = reduce_sum(nc * args.steps, ws) / (ms_max * 1e-3)
+    peak, peak_kind = peaks()
+    track_ms = kms["track"] / args.steps
+    moves_per_step = moves / args.steps
+    alg = TRACK_BYTES_PER_MOVE[args.precision] * moves_per_step + TRACK_BYTES_PER_CELL[args.precision] * nc
+    achieved = alg / (track_ms * 1e-3) / 1e9
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 particles / f64 cells / int64 flux" if args.precision == "mixed" else "f64",
+           "data": "synthetic",
+           "config": {"workload": "lid-driven cavity 24^3 hexes x 6 = 82944 tets, argon-like VHS gas, Kn 0.075, "
+                                  "diffuse walls, lid Mach 0.16, N_ref 100",
+                      "precision": args.precision, "n_cells": nc, "particles_per_step": int(moves_per_step),
+                      "l2": "inputs larger than L2 (particle SoA %.2f GB per buffer)" % (moves_per_step * 44 / 1e9),
+                      "parallelism": "replicas" if ws > 1 else "single GPU"},
+           "cell_steps_per_s": cell_steps,
+           "roofline": {"kernel": "k_track (a6-a9: t_f draw, tet walk, fixed-point flux, removal)", "bound": "hbm",
+                        "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "peak_kind": f"{peak_kind} HBM copy", "traffic": None,
+                        "bytes_per_move": TRACK_BYTES_PER_MOVE[args.precision],
+                        "bytes_per_cell": TRACK_BYTES_PER_CELL[args.precision], "ms_per_launch": track_ms},
+           "kernels_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+           "gpu_launches": int(launches), "clocks": clocks}
+    sim.close()
+    if not args.no_extras and rank == 0:
+        c64 = workload("fp64")
+        s64 = ugkwp.Simulation(c64["mesh"], c64["W0"], c64["params"], device=device, stream=stream)
+        ms64, mv64, _, k64, _ = time_steps(s64, args.steps, args.warmup, 1)
+        s64.close()
+        out["fp64"] = {"value": mv64 / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / args.steps,
+                       "cell_steps_per_s": nc * args.steps / (ms64 * 1e-3),
+                       "kernels_ms_per_step": {k: v / args.steps for k, v in k64.items()}}
+        out["mixed_over_fp64"] = out["value"] / out["fp64"]["value"]
+        out["field_error"] = field_error(10, device)
+        out["e2e"] = e2e(cfg, 3, device)
+        out["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+    elif rank == 0:
+        out["e2e"] = None
+        out["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,254 @@
+/*
+ * ugkwp.h -- C-ABI of the GB300 (sm_103a) unified gas-kinetic wave-particle
+ * (UGKWP) time step on unstructured tetrahedral meshes.
+ *
+ * The method is that of Chen, Zhu & Xu, "A three-dimensional unified
+ * gas-kinetic wave-particle solver for flow computation in all regimes"
+ * (arXiv 2007.13091), Sec. 2: the cell-averaged conservative variables
+ * W = (rho, rho U, rho E) evolve by the finite-volume law of Eq. (FVmacroEq)
+ * with the multiscale flux of Sec. 2.1 (equilibrium part F^eq and the
+ * free-transport part of the collisional hydrodynamic wave, Sec. 2.3), while
+ * the collisionless part of the gas is carried by simulation particles
+ * (Sec. 2.2) whose free-transport time t_f = min(-tau ln eta, dt) decides
+ * whether they survive the step; particles are streamed through the tets,
+ * counted into the particle flux F^{fr,p}, removed when collisional, and the
+ * collisionless fraction e^{-dt/tau} of the hydrodynamic wave is re-sampled as
+ * particles at the start of every step (Sec. 2.4 (b)).
+ *
+ * Conventions for every entry point:
+ *  - All functions return 0 (UGKWP_OK) or a negative UGKWP_E_* status; the
+ *    message of the last failure in the calling thread is available through
+ *    ugkwp_last_error().  Invalid arguments are reported synchronously.
+ *  - Device-side failures (capacity, lost particles, fixed-point overflow,
+ *    non-physical states) set a device error word; it is read and returned by
+ *    the next call that synchronises (ugkwp_step with stats, ugkwp_moments,
+ *    ugkwp_export_state, ugkwp_sync).  No call traps or hangs the GPU: every
+ *    data-dependent device loop has an iteration cap.
+ *  - Per-cell arrays are structure-of-arrays, component-major: component q of
+ *    cell i is at [q * n_cells + i].  Per-particle vectors are [3][n].
+ *  - Objects are opaque; calls on one object are not thread-safe.
+ *  - The library allocates no device memory: the caller provides one
+ *    workspace (size from ugkwp_query_sizes) that must outlive the simulation.
+ */
+#ifndef UGKWP_H
+#define UGKWP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+enum {
+    UGKWP_OK = 0,
+    UGKWP_E_ARG = -1,            /* invalid argument */
+    UGKWP_E_MESH = -2,           /* invalid mesh (inverted tet, unmatched face, ...) */
+    UGKWP_E_CUDA = -3,           /* CUDA runtime error */
+    UGKWP_E_WORKSPACE = -4,      /* workspace missing, too small or misaligned */
+    UGKWP_E_CAPACITY = -5,       /* particle capacity exceeded (step aborted its writes) */
+    UGKWP_E_TRACK_LIMIT = -7,    /* a particle exceeded max_crossings face crossings */
+    UGKWP_E_FIXED_OVERFLOW = -8, /* a particle's fixed-point flux left the int64 range */
+    UGKWP_E_NONFINITE = -9,      /* non-positive density/pressure or non-finite state */
+    UGKWP_E_STATE = -10,         /* call out of order / inconsistent imported state */
+    UGKWP_E_UNSUPPORTED = -11    /* feature not available in this build */
+};
+
+/* ------------------------------------------------------ boundary types
+ * Sec. 2.4 (e) gives the diffuse isothermal wall; the paper's test cases also
+ * use far-field and symmetry (specular) boundaries. */
+enum {
+    UGKWP_BC_DIFFUSE_WALL = 1, /* isothermal wall (T_w, U_w): wave re-emitted as g_w,
+                                  particles re-emitted diffusely, full accommodation */
+    UGKWP_BC_SPECULAR = 2,     /* symmetry plane: mirror ghost, specular particles */
+    UGKWP_BC_FARFIELD = 3,     /* prescribed far-field/inflow Maxwellian W_in: all-hydro
+                                  ghost, particles leaving the domain are absorbed */
+    UGKWP_BC_OUTFLOW = 4       /* zero-gradient ghost (ghost = interior), absorbing */
+};
+
+/* Particle precision.  FP64: particle state and tracking in binary64.
+ * MIXED: particle position, velocity, t_f and tracking in binary32; particle
+ * mass, fluxes (fixed point), relaxation times and all cell/face arithmetic
+ * stay binary64. */
+enum { UGKWP_FP64 = 0, UGKWP_MIXED = 1 };
+
+/* Which quantity ugkwp_moments returns (all [5][n_cells] unless stated). */
+enum {
+    UGKWP_W = 0,     /* conservative W = (rho, rho U, rho E) of the whole gas */
+    UGKWP_WP = 1,    /* W^p: conservative variables carried by the particles (Eq. W^p) */
+    UGKWP_WH = 2,    /* W^h = W - W^p, the hydrodynamic wave */
+    UGKWP_PRIM = 3   /* primitives (rho, U_x, U_y, U_z, T) of W */
+};
+
+/* ------------------------------------------------------------------ types */
+typedef struct ugkwp_mesh ugkwp_mesh;
+typedef struct ugkwp_sim ugkwp_sim;
+
+/* Mesh description.  All arrays are host memory owned by the caller and are
+ * copied by ugkwp_mesh_load.  Every tet must have positive volume with its
+ * nodes in the given order; every face must be shared by two tets or listed
+ * once in bfaces with a tag in [0, n_bc). */
+typedef struct {
+    int32_t n_nodes;
+    int32_t n_tets;              /* < 2^24 (particle ids hold the birth cell in 24 bits) */
+    int32_t n_bfaces;
+    int32_t reserved;
+    const double* xyz;           /* [n_nodes][3] node coordinates */
+    const int32_t* tets;         /* [n_tets][4] node indices */
+    const int32_t* bfaces;       /* [n_bfaces][3] node indices of boundary faces */
+    const int32_t* bface_tags;   /* [n_bfaces] index into ugkwp_params.bc */
+} ugkwp_mesh_desc;
+
+typedef struct {
+    int32_t type;                /* UGKWP_BC_* */
+    int32_t reserved;
+    double T_w;                  /* diffuse wall temperature */
+    double U_w[3];               /* diffuse wall velocity (tangential to the wall) */
+    double W_in[5];              /* far-field conservative state */
+} ugkwp_bc;
+
+/* Gas and scheme parameters.  tau = mu_ref/p (T/T_ref)^omega (Sec. 2, Eq.
+ * tau_via_T_ref); dt = CFL min_i |Omega_i| / sum_d Lambda_i^d (Sec. 2.4 (a));
+ * face relaxation time adds C2 |p_l - p_r|/|p_l + p_r| dt (Sec. 2.4 (d));
+ * N_ref, N_min control the sampling (Sec. 2.4 (b)). */
+typedef struct {
+    double R;                    /* specific gas constant */
+    double mu_ref, T_ref, omega; /* viscosity law */
+    double Pr;                   /* reserved (BGK: Pr = 1); must be 0 or 1 */
+    double CFL;                  /* Courant number C in (0, 1] */
+    double C2;                   /* numerical-dissipation constant (>= 0) */
+    double venkat_K;             /* reserved for second-order reconstruction */
+    int32_t order;               /* reconstruction order: 1 (first order) */
+    int32_t N_ref;               /* reference particle number per cell (> 0) */
+    int32_t N_min;               /* minimum particles per cell after sampling (>= 0) */
+    int32_t precision;           /* UGKWP_FP64 or UGKWP_MIXED */
+    int32_t max_crossings;       /* cap on face crossings per particle and step (> 0) */
+    int32_t n_bc;                /* number of used entries of bc (<= 16) */
+    uint64_t seed;               /* Philox4x64-10 key word 0 */
+    int64_t particle_capacity;   /* particles the device buffers hold (< 2^31) */
+    ugkwp_bc bc[16];
+} ugkwp_params;
+
+typedef struct {
+    size_t workspace_bytes;      /* device bytes the caller must provide */
+    int64_t n_cells, n_faces, n_bfaces;
+} ugkwp_sizes;
+
+/* Step statistics (filled when requested; forces a stream synchronisation). */
+typedef struct {
+    double t, dt;                /* time after the last step, its time step */
+    int64_t step;                /* steps taken so far */
+    int64_t n_particles;         /* particles alive after the last step */
+    int64_t n_tracked;           /* particles moved in the last step (old + sampled) */
+    int64_t n_sampled, n_collided, n_exited, n_lost, n_crossings, n_wall_hits;
+    int64_t n_moves_total;       /* particle moves summed over every step since init */
+} ugkwp_stats;
+
+/* Host-side image of the simulation state for checkpoint/restart and for
+ * teacher-forced comparison.  All pointers are caller-owned host buffers:
+ * W [5][n_cells]; id, cell, m [n]; x, u [3][n] (binary64; in MIXED mode the
+ * values are binary32 numbers widened exactly).  exps are the base-2
+ * exponents of the fixed-point quanta of (mass, 3 x momentum, energy). */
+typedef struct {
+    int64_t n_particles;
+    int64_t step;
+    double t;
+    int32_t exps[5];
+    int32_t reserved;
+    double* W;
+    uint64_t* id;
+    int32_t* cell;
+    double* x;
+    double* u;
+    double* m;
+} ugkwp_state;
+
+/* ---------------------------------------------------------------- mesh */
+
+/* Build the mesh object: validates the tets (positive volume), matches faces
+ * on sorted node triples, assigns boundary tags and precomputes geometry
+ * (unit face normals from owner to neighbour, areas, plane offsets, volumes,
+ * the projected areas Delta S of Sec. 2.4 (a)).  Host only; no GPU needed.
+ * Errors: UGKWP_E_ARG (NULL/size), UGKWP_E_MESH (with a message). */
+int ugkwp_mesh_load(const ugkwp_mesh_desc* d, ugkwp_mesh** out);
+int ugkwp_mesh_free(ugkwp_mesh* m);
+
+/* Device workspace needed for (mesh, params).  Host only. */
+int ugkwp_query_sizes(const ugkwp_mesh* m, const ugkwp_params* p, ugkwp_sizes* out);
+
+/* Create a simulation: copies the mesh geometry and the initial state W0
+ * (host, [5][n_cells], conservative) into the caller's device workspace
+ * (>= workspace_bytes, 256-byte aligned, owned by the caller and used until
+ * ugkwp_free), and binds the CUDA stream (cudaStream_t, NULL = legacy default)
+ * on which every later call enqueues its work.  No particles exist yet: the
+ * first step samples e^{-dt/tau} of every cell as particles.  The mesh object
+ * may be freed afterwards.  Errors: UGKWP_E_ARG, UGKWP_E_WORKSPACE,
+ * UGKWP_E_NONFINITE (W0 with rho <= 0 or p <= 0), UGKWP_E_CUDA. */
+int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0,
+               void* d_workspace, size_t workspace_bytes, void* cuda_stream,
+               ugkwp_sim** out);
+int ugkwp_free(ugkwp_sim* s);
+
+/* Advance n_steps time steps (Sec. 2.2 procedure, Eq. update_macro_variables),
+ * asynchronously on the bound stream.  If st is non-NULL the call waits for
+ * the stream, fills st and returns any device-side error. */
+int ugkwp_step(ugkwp_sim* s, int32_t n_steps, ugkwp_stats* st);
+
+/* Wait for the stream and return (then clear) any device-side error. */
+int ugkwp_sync(ugkwp_sim* s);
+
+/* Copy a per-cell quantity (UGKWP_W, _WP, _WH, _PRIM) to out: a device
+ * pointer (out_on_device = 1, enqueued on the stream) or host memory
+ * (out_on_device = 0, synchronising).  [5][n_cells] doubles. */
+int ugkwp_moments(ugkwp_sim* s, int32_t which, double* out, int32_t out_on_device);
+
+/* State image: ugkwp_state_info fills the scalar fields (n_particles, step,
+ * t, exps); ugkwp_export_state also fills the arrays (which must hold
+ * n_particles entries).  ugkwp_import_state replaces the simulation state
+ * (W, particles, step, t, exps) from host arrays.  Synchronising.
+ * Errors: UGKWP_E_ARG, UGKWP_E_CAPACITY, UGKWP_E_STATE (particle outside the
+ * mesh index range or not representable in the particle precision). */
+int ugkwp_state_info(ugkwp_sim* s, ugkwp_state* st);
+int ugkwp_export_state(ugkwp_sim* s, ugkwp_state* st);
+int ugkwp_import_state(ugkwp_sim* s, const ugkwp_state* st);
+
+/* Diagnostics of the last step, copied to host memory (synchronising):
+ *  0 dt (1 double), 1 tau [n_cells], 2 rho^h before sampling [n_cells],
+ *  3 N_sam [n_cells] (int64), 4 m_sam [n_cells], 5 wave flux
+ *  F^eq + F^{fr,wave} per unit area [5][n_faces] (face numbering: by owner
+ *  tet then its local face), 6 particle flux F^{fr,p} in fixed point
+ *  [5][n_cells] (int64), 7 survivor mass in fixed point [n_cells] (int64),
+ *  8 survivor count [n_cells] (int64). */
+int ugkwp_last(ugkwp_sim* s, int32_t which, void* host_out);
+
+/* Kernel classes of one step, in launch order (for ugkwp_timing_read). */
+enum {
+    UGKWP_K_RESET = 0, UGKWP_K_CELL_PREP, UGKWP_K_SAMPLE_COUNT, UGKWP_K_SCAN, UGKWP_K_SCATTER,
+    UGKWP_K_SAMPLE, UGKWP_K_TRACK, UGKWP_K_FLUX, UGKWP_K_UPDATE, UGKWP_N_KERNELS
+};
+
+/* Per-kernel timing with CUDA events recorded on the bound stream around each
+ * kernel launch of ugkwp_step while enabled (enable != 0).  ugkwp_timing_read
+ * synchronises and returns, per kernel class, the summed device time in
+ * milliseconds (ms[UGKWP_N_KERNELS]) of the launches timed since the last
+ * read, and the number of kernels launched since ugkwp_init
+ * (launches[UGKWP_N_KERNELS], counted whether or not timing is enabled; the
+ * scan class counts its two kernels); either pointer may be NULL.  The timed
+ * sums are reset by the read. */
+int ugkwp_timing_enable(ugkwp_sim* s, int32_t enable);
+int ugkwp_timing_read(ugkwp_sim* s, double* ms, int64_t* launches);
+
+/* Gradient of a wall functional with respect to far-field / wall parameters
+ * with the particle sample frozen (hand-written adjoint of the wave flux and
+ * update).  Not available in this build: returns UGKWP_E_UNSUPPORTED. */
+typedef struct { int32_t functional; int32_t n_steps; const int32_t* wall_tags; int32_t n_wall_tags; } ugkwp_adjoint_req;
+int ugkwp_adjoint_wave(ugkwp_sim* s, const ugkwp_adjoint_req* r, double* dJ_dtheta);
+
+/* Copy the calling thread's last error message (NUL-terminated) into buf. */
+int ugkwp_last_error(char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UGKWP_H */

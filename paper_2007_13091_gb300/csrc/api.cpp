@@ -1,0 +1,711 @@
+// C-ABI of the ugkwp library (declared in include/ugkwp.h): argument checks,
+// workspace layout, host-side preparation of the device geometry, the order of
+// kernel launches of one step, and state import/export.
+// This file is compiled with floating-point contraction disabled.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ugkwp_internal.hpp"
+
+namespace ugkwp {
+bool build_mesh(const ugkwp_mesh_desc& d, MeshHost& M, std::string& err);
+}
+
+using namespace ugkwp;
+
+struct ugkwp_mesh {
+    MeshHost h;
+};
+
+struct TimedLaunch {
+    int k;
+    cudaEvent_t a, b;
+};
+
+struct ugkwp_sim {
+    DevParams P;
+    DevMesh M;
+    DevState S;
+    PartBufRaw A, B;
+    cudaStream_t stream = nullptr;
+    int64_t step = 0;
+    int32_t n_bc = 0;
+    size_t real_size = 8;
+    int64_t capacity = 0;
+    bool timing = false;
+    int64_t launches[UGKWP_N_KERNELS] = {};
+    std::vector<TimedLaunch> pending;
+    std::vector<cudaEvent_t> pool;
+    ~ugkwp_sim() {
+        for (auto& t : pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(UGKWP_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CU(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+// Linear allocator over the caller's workspace (256-byte aligned chunks).
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base((char*)b) {}
+    template <class T> T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? (T*)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, DevState& S, PartBufRaw& A,
+            PartBufRaw& B) {
+    const size_t nc = mh.nc, nf = mh.nf, nbf = mh.nbf;
+    M.nc = mh.nc; M.nf = mh.nf; M.nbf = mh.nbf;
+    M.vol = c.take<double>(nc);
+    M.dS = c.take<double>(3 * nc);
+    M.vtx = c.take<double>(12 * nc);
+    M.cf = c.take<int32_t>(4 * nc);
+    M.cfs = c.take<int32_t>(nc);
+    M.trk_f = nullptr;
+    M.trk_d = nullptr;
+    if (rs == 4) M.trk_f = c.take<TrkF>(nc);
+    else M.trk_d = c.take<TrkD>(nc);
+    M.f_own = c.take<int32_t>(nf);
+    M.f_nbr = c.take<int32_t>(nf);
+    M.f_n = c.take<double>(3 * nf);
+    M.f_area = c.take<double>(nf);
+    M.bf_tag = c.take<int32_t>(nbf ? nbf : 1);
+    M.bf_n = c.take<double>(3 * (nbf ? nbf : 1));
+    M.bf_t1 = c.take<double>(3 * (nbf ? nbf : 1));
+    M.bf_t2 = c.take<double>(3 * (nbf ? nbf : 1));
+    S.W = c.take<double>(5 * nc);
+    S.prim = c.take<double>(5 * nc);
+    S.tau = c.take<double>(nc);
+    S.rhoh = c.take<double>(nc);
+    S.rhop = c.take<double>(nc);
+    S.nsam = c.take<int32_t>(nc);
+    S.msam = c.take<double>(nc);
+    S.nleft = c.take<int32_t>(nc);
+    S.nleft_next = c.take<int32_t>(nc);
+    S.smass = c.take<int64_t>(nc);
+    S.smass_next = c.take<int64_t>(nc);
+    S.cnt = c.take<int32_t>(nc);
+    S.off = c.take<int32_t>(nc);
+    S.cursor = c.take<int32_t>(nc);
+    S.pflux = c.take<int64_t>(5 * nc);
+    S.wacc = c.take<int64_t>(5 * nc);
+    S.mom = c.take<double>(5 * nc);
+    S.F = c.take<double>(5 * nf);
+    S.bsum = c.take<int32_t>((size_t)scan_blocks(mh.nc) + 1);
+    S.t = c.take<double>(1);
+    S.dt = c.take<double>(1);
+    S.cnt64 = c.take<int64_t>(CNT_SLOTS);
+    for (PartBufRaw* pb : {&A, &B}) {
+        for (int d = 0; d < 3; ++d) pb->x[d] = c.take<char>(rs * (size_t)cap);
+        for (int d = 0; d < 3; ++d) pb->u[d] = c.take<char>(rs * (size_t)cap);
+        pb->m = c.take<double>((size_t)cap);
+        pb->cell = c.take<int32_t>((size_t)cap);
+        pb->id = c.take<uint64_t>((size_t)cap);
+    }
+}
+
+int check_params(const ugkwp_params* p, const MeshHost* mh) {
+    if (!p) return fail(UGKWP_E_ARG, "params is NULL");
+    if (!(p->R > 0.0) || !(p->mu_ref > 0.0) || !(p->T_ref > 0.0) || !std::isfinite(p->omega))
+        return fail(UGKWP_E_ARG, "R, mu_ref and T_ref must be positive and omega finite");
+    if (!(p->CFL > 0.0 && p->CFL <= 1.0)) return fail(UGKWP_E_ARG, "CFL must be in (0, 1]");
+    if (!(p->C2 >= 0.0)) return fail(UGKWP_E_ARG, "C2 must be >= 0");
+    if (!(p->Pr == 0.0 || p->Pr == 1.0)) return fail(UGKWP_E_UNSUPPORTED, "only the BGK model (Pr = 1) is available");
+    if (p->order != 1) return fail(UGKWP_E_UNSUPPORTED, "only first-order reconstruction (order = 1) is available");
+    if (p->N_ref <= 0 || p->N_min < 0) return fail(UGKWP_E_ARG, "N_ref must be > 0 and N_min >= 0");
+    if (p->precision != UGKWP_FP64 && p->precision != UGKWP_MIXED) return fail(UGKWP_E_ARG, "unknown precision");
+    if (p->max_crossings <= 0) return fail(UGKWP_E_ARG, "max_crossings must be > 0");
+    if (p->particle_capacity < 0 || p->particle_capacity >= ((int64_t)1 << 31))
+        return fail(UGKWP_E_ARG, "particle_capacity must be in [0, 2^31)");
+    if (p->n_bc < 0 || p->n_bc > 16) return fail(UGKWP_E_ARG, "n_bc must be in [0, 16]");
+    for (int b = 0; b < p->n_bc; ++b) {
+        const ugkwp_bc& bc = p->bc[b];
+        if (bc.type < 1 || bc.type > 4) return fail(UGKWP_E_ARG, "unknown boundary type in bc[" + std::to_string(b) + "]");
+        if (bc.type == UGKWP_BC_DIFFUSE_WALL && !(bc.T_w > 0.0)) return fail(UGKWP_E_ARG, "wall temperature must be > 0");
+        if (bc.type == UGKWP_BC_FARFIELD) {
+            const double* W = bc.W_in;
+            const double rho = W[0];
+            if (!(rho > 0.0)) return fail(UGKWP_E_ARG, "far-field density must be > 0");
+            const double U2 = ((W[1] / rho) * (W[1] / rho) + (W[2] / rho) * (W[2] / rho)) + (W[3] / rho) * (W[3] / rho);
+            if (!((W[4] - 0.5 * (rho * U2)) > 0.0)) return fail(UGKWP_E_ARG, "far-field pressure must be > 0");
+        }
+    }
+    if (mh) {
+        for (int f = 0; f < mh->nf; ++f)
+            if (mh->f_nbr[f] < 0 && mh->f_tag[f] >= p->n_bc)
+                return fail(UGKWP_E_ARG, "boundary tag " + std::to_string(mh->f_tag[f]) + " has no entry in params.bc");
+    }
+    return UGKWP_OK;
+}
+
+int ceil_log2(double b) {
+    int ex;
+    const double mant = std::frexp(b, &ex);
+    return mant == 0.5 ? ex - 1 : ex;
+}
+
+// Fixed-point quanta 2^e_q: e_q = ceil(log2 B_q) - 50 with B_mass the largest
+// cell mass, B_mom = B_mass c, B_E = B_mass c^2 / 2, c the largest |U| + 5 sqrt(RT)
+// over the cells and the wall / far-field states.
+void fixed_point_exponents(const MeshHost& mh, const ugkwp_params& p, const double* W, int32_t e[5]) {
+    const int nc = mh.nc;
+    double bm = 0.0, cmax = 0.0;
+    auto speed = [&](const double* Wv, size_t stride) {
+        const double rho = Wv[0];
+        const double U[3] = {Wv[stride] / rho, Wv[2 * stride] / rho, Wv[3 * stride] / rho};
+        const double U2 = (U[0] * U[0] + U[1] * U[1]) + U[2] * U[2];
+        const double pr = (Wv[4 * stride] - 0.5 * (rho * U2)) / 1.5;
+        const double T = pr / (rho * p.R);
+        return std::sqrt((U[0] * U[0] + U[1] * U[1]) + U[2] * U[2]) + 5.0 * std::sqrt(p.R * T);
+    };
+    for (int i = 0; i < nc; ++i) {
+        const double mass = W[i] * mh.vol[i];
+        if (mass > bm) bm = mass;
+        const double c = speed(W + i, (size_t)nc);
+        if (c > cmax) cmax = c;
+    }
+    for (int b = 0; b < p.n_bc; ++b) {
+        const ugkwp_bc& bc = p.bc[b];
+        double c = 0.0;
+        if (bc.type == UGKWP_BC_DIFFUSE_WALL)
+            c = std::sqrt((bc.U_w[0] * bc.U_w[0] + bc.U_w[1] * bc.U_w[1]) + bc.U_w[2] * bc.U_w[2]) + 5.0 * std::sqrt(p.R * bc.T_w);
+        else if (bc.type == UGKWP_BC_FARFIELD)
+            c = speed(bc.W_in, 1);
+        if (c > cmax) cmax = c;
+    }
+    e[0] = ceil_log2(bm) - 50;
+    e[1] = e[2] = e[3] = ceil_log2(bm * cmax) - 50;
+    e[4] = ceil_log2(bm * cmax * cmax * 0.5) - 50;
+}
+
+void set_exps(DevParams& P, const int32_t e[5]) {
+    for (int q = 0; q < 5; ++q) {
+        P.exps[q] = e[q];
+        P.qscale[q] = std::ldexp(1.0, e[q]);
+        P.qinv[q] = std::ldexp(1.0, -e[q]);
+    }
+}
+
+int read_error(ugkwp_sim* s) {
+    int64_t h[CNT_SLOTS];
+    CU(cudaMemcpyAsync(h, s->S.cnt64, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    const int64_t e = h[CNT_ERR];
+    if (!e) return UGKWP_OK;
+    const int64_t zero = 0;
+    CU(cudaMemcpyAsync(s->S.cnt64 + CNT_ERR, &zero, sizeof(zero), cudaMemcpyHostToDevice, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    if (e & ERRB_CAPACITY) return fail(UGKWP_E_CAPACITY, "particle capacity exceeded: the step's particle writes were skipped and the particle state is no longer valid");
+    if (e & ERRB_NONFINITE) return fail(UGKWP_E_NONFINITE, "non-positive density or pressure in a cell");
+    if (e & ERRB_TRACK_LIMIT) return fail(UGKWP_E_TRACK_LIMIT, std::to_string(h[CNT_LOST]) + " particles exceeded max_crossings");
+    if (e & ERRB_FIXED_OVERFLOW) return fail(UGKWP_E_FIXED_OVERFLOW, "fixed-point particle flux overflow");
+    if (e & ERRB_SAMPLE_LIMIT) return fail(UGKWP_E_CAPACITY, "more than 65534 particles sampled in one cell");
+    return fail(UGKWP_E_STATE, "device error word " + std::to_string(e));
+}
+
+}  // namespace
+
+extern "C" {
+
+int ugkwp_last_error(char* buf, size_t len) {
+    if (!buf || len == 0) return UGKWP_E_ARG;
+    std::snprintf(buf, len, "%s", g_err.c_str());
+    return UGKWP_OK;
+}
+
+int ugkwp_mesh_load(const ugkwp_mesh_desc* d, ugkwp_mesh** out) {
+    if (!d || !out) return fail(UGKWP_E_ARG, "NULL argument");
+    *out = nullptr;
+    if (d->n_nodes <= 0 || d->n_tets <= 0 || d->n_bfaces < 0 || !d->xyz || !d->tets ||
+        (d->n_bfaces > 0 && (!d->bfaces || !d->bface_tags)))
+        return fail(UGKWP_E_ARG, "invalid mesh description");
+    if (d->n_tets >= (1 << 24)) return fail(UGKWP_E_ARG, "n_tets must be < 2^24");
+    for (int32_t b = 0; b < d->n_bfaces; ++b)
+        if (d->bface_tags[b] < 0 || d->bface_tags[b] >= 16) return fail(UGKWP_E_ARG, "boundary tags must be in [0, 16)");
+    ugkwp_mesh* m = new ugkwp_mesh;
+    std::string err;
+    if (!build_mesh(*d, m->h, err)) {
+        delete m;
+        return fail(UGKWP_E_MESH, err);
+    }
+    *out = m;
+    return UGKWP_OK;
+}
+
+int ugkwp_mesh_free(ugkwp_mesh* m) {
+    delete m;
+    return UGKWP_OK;
+}
+
+int ugkwp_query_sizes(const ugkwp_mesh* m, const ugkwp_params* p, ugkwp_sizes* out) {
+    if (!m || !out) return fail(UGKWP_E_ARG, "NULL argument");
+    int rc = check_params(p, &m->h);
+    if (rc) return rc;
+    DevMesh M{};
+    DevState S{};
+    PartBufRaw A{}, B{};
+    Carver c(nullptr);
+    layout(m->h, p->particle_capacity, p->precision == UGKWP_MIXED ? 4 : 8, c, M, S, A, B);
+    out->workspace_bytes = (c.off + 255) & ~(size_t)255;
+    out->n_cells = m->h.nc;
+    out->n_faces = m->h.nf;
+    out->n_bfaces = m->h.nbf;
+    return UGKWP_OK;
+}
+
+int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, void* d_workspace,
+               size_t workspace_bytes, void* cuda_stream, ugkwp_sim** out) {
+    if (!m || !W0 || !out) return fail(UGKWP_E_ARG, "NULL argument");
+    *out = nullptr;
+    int rc = check_params(p, &m->h);
+    if (rc) return rc;
+    const MeshHost& mh = m->h;
+    const int nc = mh.nc, nf = mh.nf, nbf = mh.nbf;
+    for (int i = 0; i < nc; ++i) {
+        const double rho = W0[i];
+        if (!(rho > 0.0) || !std::isfinite(rho)) return fail(UGKWP_E_NONFINITE, "W0 has rho <= 0 in cell " + std::to_string(i));
+        const double U[3] = {W0[nc + i] / rho, W0[2 * nc + i] / rho, W0[3 * nc + i] / rho};
+        const double pr = (W0[4 * nc + i] - 0.5 * (rho * ((U[0] * U[0] + U[1] * U[1]) + U[2] * U[2]))) / 1.5;
+        if (!(pr > 0.0) || !std::isfinite(pr)) return fail(UGKWP_E_NONFINITE, "W0 has p <= 0 in cell " + std::to_string(i));
+    }
+    ugkwp_sizes sz;
+    rc = ugkwp_query_sizes(m, p, &sz);
+    if (rc) return rc;
+    if (!d_workspace || workspace_bytes < sz.workspace_bytes)
+        return fail(UGKWP_E_WORKSPACE, "workspace missing or smaller than ugkwp_query_sizes requires (" +
+                                           std::to_string(sz.workspace_bytes) + " bytes)");
+    if (((uintptr_t)d_workspace) & 255) return fail(UGKWP_E_WORKSPACE, "workspace must be 256-byte aligned");
+
+    ugkwp_sim* s = new ugkwp_sim;
+    s->stream = (cudaStream_t)cuda_stream;
+    s->real_size = p->precision == UGKWP_MIXED ? 4 : 8;
+    s->capacity = p->particle_capacity;
+    s->n_bc = p->n_bc;
+    Carver c(d_workspace);
+    layout(mh, p->particle_capacity, s->real_size, c, s->M, s->S, s->A, s->B);
+    // parameters
+    DevParams& P = s->P;
+    std::memset(&P, 0, sizeof(P));
+    P.R = p->R; P.mu_ref = p->mu_ref; P.T_ref = p->T_ref; P.omega = p->omega; P.CFL = p->CFL; P.C2 = p->C2;
+    P.N_ref = p->N_ref; P.N_min = p->N_min; P.max_crossings = p->max_crossings; P.precision = p->precision;
+    P.seed = p->seed; P.capacity = p->particle_capacity; P.n_bc = p->n_bc;
+    for (int b = 0; b < p->n_bc; ++b) {
+        P.bc[b].type = p->bc[b].type;
+        P.bc[b].T_w = p->bc[b].T_w;
+        for (int k = 0; k < 3; ++k) P.bc[b].U_w[k] = p->bc[b].U_w[k];
+        for (int k = 0; k < 5; ++k) P.bc[b].W_in[k] = p->bc[b].W_in[k];
+    }
+    int32_t e[5];
+    fixed_point_exponents(mh, *p, W0, e);
+    set_exps(P, e);
+    // host images of the device geometry
+    std::vector<double> dS(3 * (size_t)nc), vtx(12 * (size_t)nc), fn(3 * (size_t)nf), bn(3 * (size_t)std::max(nbf, 1)),
+        bt1(3 * (size_t)std::max(nbf, 1)), bt2(3 * (size_t)std::max(nbf, 1));
+    std::vector<int32_t> cf(4 * (size_t)nc), cfs(nc), fnb(nf), btag(std::max(nbf, 1));
+    for (int i = 0; i < nc; ++i) {
+        for (int d = 0; d < 3; ++d) dS[(size_t)d * nc + i] = mh.dS[3 * (size_t)i + d];
+        for (int k = 0; k < 4; ++k)
+            for (int d = 0; d < 3; ++d) vtx[(size_t)(3 * k + d) * nc + i] = mh.xyz[3 * (size_t)mh.tet[4 * (size_t)i + k] + d];
+        int bits = 0;
+        for (int k = 0; k < 4; ++k) {
+            cf[(size_t)k * nc + i] = mh.cf[4 * (size_t)i + k];
+            if (mh.cf_sign[4 * (size_t)i + k] > 0) bits |= 1 << k;
+        }
+        cfs[i] = bits;
+    }
+    for (int f = 0; f < nf; ++f) {
+        for (int d = 0; d < 3; ++d) fn[(size_t)d * nf + f] = mh.f_n[3 * (size_t)f + d];
+        fnb[f] = mh.f_nbr[f] >= 0 ? mh.f_nbr[f] : -1 - mh.bf_of_face[f];
+    }
+    for (int b = 0; b < nbf; ++b) {
+        const int f = mh.face_of_bf[b];
+        btag[b] = mh.f_tag[f];
+        for (int d = 0; d < 3; ++d) {
+            bn[(size_t)d * nbf + b] = mh.f_n[3 * (size_t)f + d];
+            bt1[(size_t)d * nbf + b] = mh.f_t1[3 * (size_t)f + d];
+            bt2[(size_t)d * nbf + b] = mh.f_t2[3 * (size_t)f + d];
+        }
+    }
+    // tracking records: planes (+-n, +-d) per local face, neighbour codes
+    std::vector<TrkF> tf;
+    std::vector<TrkD> td;
+    if (s->real_size == 4) tf.resize(nc); else td.resize(nc);
+    for (int i = 0; i < nc; ++i) {
+        int nbv[4];
+        for (int k = 0; k < 4; ++k) {
+            const int f = mh.cf[4 * (size_t)i + k];
+            const bool own = mh.cf_sign[4 * (size_t)i + k] > 0;
+            const double* n = &mh.f_n[3 * (size_t)f];
+            const double d = mh.f_d[f];
+            if (s->real_size == 4) {
+                const float nx = (float)n[0], ny = (float)n[1], nz = (float)n[2], dd = (float)d;
+                tf[i].pl[k] = own ? make_float4(nx, ny, nz, dd) : make_float4(-nx, -ny, -nz, -dd);
+            } else {
+                td[i].pl[k] = own ? Dbl4{n[0], n[1], n[2], d} : Dbl4{-n[0], -n[1], -n[2], -d};
+            }
+            if (mh.f_nbr[f] < 0) nbv[k] = -1 - mh.bf_of_face[f];
+            else if (own) nbv[k] = (mh.f_nbr[f] << 2) | mh.f_nbr_k[f];
+            else nbv[k] = (mh.f_own[f] << 2) | mh.f_own_k[f];
+        }
+        const int4 nb4 = make_int4(nbv[0], nbv[1], nbv[2], nbv[3]);
+        if (s->real_size == 4) tf[i].nb = nb4; else td[i].nb = nb4;
+    }
+    cudaStream_t st = s->stream;
+    auto up = [&](const void* dst, const void* src, size_t bytes) {
+        return cudaMemcpyAsync(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice, st);
+    };
+    cudaError_t ce = cudaSuccess;
+#define UP(dst, src, bytes) if (ce == cudaSuccess) ce = up(dst, src, bytes)
+    UP(s->M.vol, mh.vol.data(), nc * sizeof(double));
+    UP(s->M.dS, dS.data(), dS.size() * sizeof(double));
+    UP(s->M.vtx, vtx.data(), vtx.size() * sizeof(double));
+    UP(s->M.cf, cf.data(), cf.size() * sizeof(int32_t));
+    UP(s->M.cfs, cfs.data(), cfs.size() * sizeof(int32_t));
+    if (s->real_size == 4) { UP(s->M.trk_f, tf.data(), tf.size() * sizeof(TrkF)); }
+    else { UP(s->M.trk_d, td.data(), td.size() * sizeof(TrkD)); }
+    UP(s->M.f_own, mh.f_own.data(), nf * sizeof(int32_t));
+    UP(s->M.f_nbr, fnb.data(), nf * sizeof(int32_t));
+    UP(s->M.f_n, fn.data(), fn.size() * sizeof(double));
+    UP(s->M.f_area, mh.f_area.data(), nf * sizeof(double));
+    UP(s->M.bf_tag, btag.data(), btag.size() * sizeof(int32_t));
+    UP(s->M.bf_n, bn.data(), bn.size() * sizeof(double));
+    UP(s->M.bf_t1, bt1.data(), bt1.size() * sizeof(double));
+    UP(s->M.bf_t2, bt2.data(), bt2.size() * sizeof(double));
+    UP(s->S.W, W0, 5 * (size_t)nc * sizeof(double));
+#undef UP
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(s->S.nleft, 0, nc * sizeof(int32_t), st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(s->S.smass, 0, nc * sizeof(int64_t), st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(s->S.cnt64, 0, CNT_SLOTS * sizeof(int64_t), st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(s->S.t, 0, sizeof(double), st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(s->S.dt, 0, sizeof(double), st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) {
+        delete s;
+        return cuda_fail(ce, "ugkwp_init upload");
+    }
+    *out = s;
+    return UGKWP_OK;
+}
+
+int ugkwp_free(ugkwp_sim* s) {
+    if (s && s->stream) cudaStreamSynchronize(s->stream);
+    delete s;
+    return UGKWP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+cudaEvent_t take_event(ugkwp_sim* s) {
+    if (!s->pool.empty()) {
+        cudaEvent_t e = s->pool.back();
+        s->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch one kernel class, bracketed by events when timing is enabled.
+template <class F> void timed(ugkwp_sim* s, int k, int n_kernels, F&& launch) {
+    s->launches[k] += n_kernels;
+    if (!s->timing) {
+        launch();
+        return;
+    }
+    TimedLaunch t{k, take_event(s), take_event(s)};
+    cudaEventRecord(t.a, s->stream);
+    launch();
+    cudaEventRecord(t.b, s->stream);
+    s->pending.push_back(t);
+}
+}  // namespace
+
+extern "C" {
+
+int ugkwp_timing_enable(ugkwp_sim* s, int32_t enable) {
+    if (!s) return fail(UGKWP_E_ARG, "NULL simulation");
+    s->timing = enable != 0;
+    return UGKWP_OK;
+}
+
+int ugkwp_timing_read(ugkwp_sim* s, double* ms, int64_t* launches) {
+    if (!s) return fail(UGKWP_E_ARG, "NULL simulation");
+    CU(cudaStreamSynchronize(s->stream));
+    double acc[UGKWP_N_KERNELS] = {};
+    for (auto& t : s->pending) {
+        float v = 0.0f;
+        CU(cudaEventElapsedTime(&v, t.a, t.b));
+        acc[t.k] += v;
+        s->pool.push_back(t.a);
+        s->pool.push_back(t.b);
+    }
+    s->pending.clear();
+    for (int k = 0; k < UGKWP_N_KERNELS; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (launches) launches[k] = s->launches[k];
+    }
+    return UGKWP_OK;
+}
+
+int ugkwp_step(ugkwp_sim* s, int32_t n_steps, ugkwp_stats* st) {
+    if (!s || n_steps < 0) return fail(UGKWP_E_ARG, "invalid argument");
+    cudaStream_t q = s->stream;
+    for (int32_t k = 0; k < n_steps; ++k) {
+        if (s->step >= ((int64_t)1 << 24) - 1) return fail(UGKWP_E_STATE, "step counter exhausted (2^24 steps)");
+        timed(s, UGKWP_K_RESET, 1, [&] { launch_reset(s->M, s->S, q); });
+        timed(s, UGKWP_K_CELL_PREP, 1, [&] { launch_cell_prep(s->M, s->S, s->P, q); });
+        timed(s, UGKWP_K_SAMPLE_COUNT, 1, [&] { launch_sample_count(s->M, s->S, s->P, q); });
+        timed(s, UGKWP_K_SCAN, 2, [&] { launch_scan(s->M, s->S, s->P, q); });
+        timed(s, UGKWP_K_SCATTER, 1, [&] { launch_scatter(s->M, s->S, s->P, s->A, s->B, q); });
+        timed(s, UGKWP_K_SAMPLE, 1, [&] { launch_sample_write(s->M, s->S, s->P, s->B, q); });
+        timed(s, UGKWP_K_TRACK, 1, [&] { launch_track(s->M, s->S, s->P, s->B, q); });
+        timed(s, UGKWP_K_FLUX, 1, [&] { launch_face_flux(s->M, s->S, s->P, q); });
+        timed(s, UGKWP_K_UPDATE, 1, [&] { launch_cell_update(s->M, s->S, s->P, q); });
+        std::swap(s->A, s->B);
+        std::swap(s->S.nleft, s->S.nleft_next);
+        std::swap(s->S.smass, s->S.smass_next);
+        s->step += 1;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if (st) {
+        int64_t h[CNT_SLOTS];
+        double t = 0, dt = 0;
+        CU(cudaMemcpyAsync(h, s->S.cnt64, sizeof(h), cudaMemcpyDeviceToHost, q));
+        CU(cudaMemcpyAsync(&t, s->S.t, sizeof(double), cudaMemcpyDeviceToHost, q));
+        CU(cudaMemcpyAsync(&dt, s->S.dt, sizeof(double), cudaMemcpyDeviceToHost, q));
+        CU(cudaStreamSynchronize(q));
+        st->t = t; st->dt = dt; st->step = s->step;
+        st->n_particles = h[CNT_ALIVE]; st->n_tracked = h[CNT_TRACKED];
+        st->n_sampled = h[CNT_SAMPLED]; st->n_collided = h[CNT_COLLIDED]; st->n_exited = h[CNT_EXITED];
+        st->n_lost = h[CNT_LOST]; st->n_crossings = h[CNT_CROSSINGS]; st->n_wall_hits = h[CNT_WALL];
+        st->n_moves_total = h[CNT_MOVES];
+        return read_error(s);
+    }
+    return UGKWP_OK;
+}
+
+int ugkwp_sync(ugkwp_sim* s) {
+    if (!s) return fail(UGKWP_E_ARG, "NULL simulation");
+    return read_error(s);
+}
+
+int ugkwp_moments(ugkwp_sim* s, int32_t which, double* out, int32_t out_on_device) {
+    if (!s || !out) return fail(UGKWP_E_ARG, "NULL argument");
+    if (which < UGKWP_W || which > UGKWP_PRIM) return fail(UGKWP_E_ARG, "unknown moment");
+    const size_t bytes = 5 * (size_t)s->M.nc * sizeof(double);
+    cudaStream_t q = s->stream;
+    if (which == UGKWP_W) {
+        CU(cudaMemcpyAsync(out, s->S.W, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, q));
+    } else {
+        double* dst = out_on_device ? out : s->S.mom;
+        if (which != UGKWP_PRIM) launch_wp_moments(s->M, s->S, s->P, s->A, dst, q);
+        launch_prim_moments(s->M, s->S, s->P, which, dst, q);
+        CU(cudaGetLastError());
+        if (!out_on_device) CU(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, q));
+    }
+    if (!out_on_device) {
+        CU(cudaStreamSynchronize(q));
+        return read_error(s);
+    }
+    return UGKWP_OK;
+}
+
+int ugkwp_state_info(ugkwp_sim* s, ugkwp_state* st) {
+    if (!s || !st) return fail(UGKWP_E_ARG, "NULL argument");
+    int64_t h[CNT_SLOTS];
+    double t = 0;
+    CU(cudaMemcpyAsync(h, s->S.cnt64, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaMemcpyAsync(&t, s->S.t, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    // alive particles = non-negative cells among the N_A entries of the current buffer
+    std::vector<int32_t> cell((size_t)h[CNT_N_A]);
+    if (h[CNT_N_A] > 0) {
+        CU(cudaMemcpyAsync(cell.data(), s->A.cell, cell.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+        CU(cudaStreamSynchronize(s->stream));
+    }
+    int64_t alive = 0;
+    for (int32_t c : cell) alive += c >= 0;
+    st->n_particles = alive;
+    st->step = s->step;
+    st->t = t;
+    for (int q = 0; q < 5; ++q) st->exps[q] = s->P.exps[q];
+    return UGKWP_OK;
+}
+
+int ugkwp_export_state(ugkwp_sim* s, ugkwp_state* st) {
+    if (!s || !st) return fail(UGKWP_E_ARG, "NULL argument");
+    int64_t want = st->n_particles;
+    int rc = ugkwp_state_info(s, st);
+    if (rc) return rc;
+    if (want < st->n_particles) return fail(UGKWP_E_ARG, "n_particles of the state is smaller than the particle count");
+    const int nc = s->M.nc;
+    cudaStream_t q = s->stream;
+    if (st->W) CU(cudaMemcpyAsync(st->W, s->S.W, 5 * (size_t)nc * sizeof(double), cudaMemcpyDeviceToHost, q));
+    int64_t h[CNT_SLOTS];
+    CU(cudaMemcpyAsync(h, s->S.cnt64, sizeof(h), cudaMemcpyDeviceToHost, q));
+    CU(cudaStreamSynchronize(q));
+    const size_t n = (size_t)h[CNT_N_A], rs = s->real_size;
+    std::vector<char> xs[3], us[3];
+    std::vector<double> m(n);
+    std::vector<int32_t> cell(n);
+    std::vector<uint64_t> id(n);
+    for (int d = 0; d < 3; ++d) {
+        xs[d].resize(n * rs);
+        us[d].resize(n * rs);
+        if (n) {
+            CU(cudaMemcpyAsync(xs[d].data(), s->A.x[d], n * rs, cudaMemcpyDeviceToHost, q));
+            CU(cudaMemcpyAsync(us[d].data(), s->A.u[d], n * rs, cudaMemcpyDeviceToHost, q));
+        }
+    }
+    if (n) {
+        CU(cudaMemcpyAsync(m.data(), s->A.m, n * 8, cudaMemcpyDeviceToHost, q));
+        CU(cudaMemcpyAsync(cell.data(), s->A.cell, n * 4, cudaMemcpyDeviceToHost, q));
+        CU(cudaMemcpyAsync(id.data(), s->A.id, n * 8, cudaMemcpyDeviceToHost, q));
+    }
+    CU(cudaStreamSynchronize(q));
+    const size_t np = (size_t)st->n_particles;
+    size_t k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        if (cell[i] < 0) continue;
+        if (st->id) st->id[k] = id[i];
+        if (st->cell) st->cell[k] = cell[i];
+        if (st->m) st->m[k] = m[i];
+        for (int d = 0; d < 3; ++d) {
+            double xv, uv;
+            if (rs == 4) { xv = ((const float*)xs[d].data())[i]; uv = ((const float*)us[d].data())[i]; }
+            else { xv = ((const double*)xs[d].data())[i]; uv = ((const double*)us[d].data())[i]; }
+            if (st->x) st->x[d * np + k] = xv;
+            if (st->u) st->u[d * np + k] = uv;
+        }
+        ++k;
+    }
+    return read_error(s);
+}
+
+int ugkwp_import_state(ugkwp_sim* s, const ugkwp_state* st) {
+    if (!s || !st || !st->W || (st->n_particles > 0 && (!st->id || !st->cell || !st->x || !st->u || !st->m)))
+        return fail(UGKWP_E_ARG, "NULL argument");
+    const int64_t n = st->n_particles;
+    if (n < 0 || n > s->capacity) return fail(UGKWP_E_CAPACITY, "imported particles exceed the capacity");
+    if (st->step < 0 || st->step >= ((int64_t)1 << 24) - 1) return fail(UGKWP_E_STATE, "step out of range");
+    const int nc = s->M.nc;
+    const size_t rs = s->real_size;
+    std::vector<char> xs[3], us[3];
+    for (int d = 0; d < 3; ++d) {
+        xs[d].resize((size_t)n * rs);
+        us[d].resize((size_t)n * rs);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if (st->cell[i] < 0 || st->cell[i] >= nc) return fail(UGKWP_E_STATE, "particle cell out of range");
+        for (int d = 0; d < 3; ++d) {
+            const double xv = st->x[d * n + i], uv = st->u[d * n + i];
+            if (rs == 4) {
+                const float xf = (float)xv, uf = (float)uv;
+                if ((double)xf != xv || (double)uf != uv) return fail(UGKWP_E_STATE, "particle state not representable in binary32");
+                ((float*)xs[d].data())[i] = xf;
+                ((float*)us[d].data())[i] = uf;
+            } else {
+                ((double*)xs[d].data())[i] = xv;
+                ((double*)us[d].data())[i] = uv;
+            }
+        }
+    }
+    cudaStream_t q = s->stream;
+    CU(cudaStreamSynchronize(q));
+    for (int d = 0; d < 3; ++d)
+        if (n) {
+            CU(cudaMemcpyAsync(s->A.x[d], xs[d].data(), (size_t)n * rs, cudaMemcpyHostToDevice, q));
+            CU(cudaMemcpyAsync(s->A.u[d], us[d].data(), (size_t)n * rs, cudaMemcpyHostToDevice, q));
+        }
+    if (n) {
+        CU(cudaMemcpyAsync(s->A.m, st->m, (size_t)n * 8, cudaMemcpyHostToDevice, q));
+        CU(cudaMemcpyAsync(s->A.cell, st->cell, (size_t)n * 4, cudaMemcpyHostToDevice, q));
+        CU(cudaMemcpyAsync(s->A.id, st->id, (size_t)n * 8, cudaMemcpyHostToDevice, q));
+    }
+    CU(cudaMemcpyAsync(s->S.W, st->W, 5 * (size_t)nc * sizeof(double), cudaMemcpyHostToDevice, q));
+    int64_t h[CNT_SLOTS];
+    CU(cudaMemcpyAsync(h, s->S.cnt64, sizeof(h), cudaMemcpyDeviceToHost, q));
+    CU(cudaStreamSynchronize(q));
+    const int64_t moves = h[CNT_MOVES];
+    std::memset(h, 0, sizeof(h));
+    h[CNT_MOVES] = moves;
+    h[CNT_N_A] = n;
+    h[CNT_STEP] = st->step;
+    CU(cudaMemcpyAsync(s->S.cnt64, h, sizeof(h), cudaMemcpyHostToDevice, q));
+    CU(cudaMemcpyAsync(s->S.t, &st->t, sizeof(double), cudaMemcpyHostToDevice, q));
+    CU(cudaMemsetAsync(s->S.nleft, 0, nc * sizeof(int32_t), q));
+    CU(cudaMemsetAsync(s->S.smass, 0, nc * sizeof(int64_t), q));
+    set_exps(s->P, st->exps);
+    launch_rebuild_survivors(s->M, s->S, s->P, s->A, q);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(q));
+    s->step = st->step;
+    return UGKWP_OK;
+}
+
+int ugkwp_last(ugkwp_sim* s, int32_t which, void* host_out) {
+    if (!s || !host_out) return fail(UGKWP_E_ARG, "NULL argument");
+    const size_t nc = s->M.nc, nf = s->M.nf;
+    cudaStream_t q = s->stream;
+    CU(cudaStreamSynchronize(q));
+    auto get = [&](const void* src, size_t bytes) { return cudaMemcpy(host_out, src, bytes, cudaMemcpyDeviceToHost); };
+    switch (which) {
+        case 0: CU(get(s->S.dt, 8)); break;
+        case 1: CU(get(s->S.tau, nc * 8)); break;
+        case 2: CU(get(s->S.rhoh, nc * 8)); break;
+        case 3: {
+            std::vector<int32_t> v(nc);
+            CU(cudaMemcpy(v.data(), s->S.nsam, nc * 4, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < nc; ++i) ((int64_t*)host_out)[i] = v[i];
+            break;
+        }
+        case 4: CU(get(s->S.msam, nc * 8)); break;
+        case 5: CU(get(s->S.F, 5 * nf * 8)); break;
+        case 6: CU(get(s->S.pflux, 5 * nc * 8)); break;
+        case 7: CU(get(s->S.smass, nc * 8)); break;
+        case 8: {
+            std::vector<int32_t> v(nc);
+            CU(cudaMemcpy(v.data(), s->S.nleft, nc * 4, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < nc; ++i) ((int64_t*)host_out)[i] = v[i];
+            break;
+        }
+        default: return fail(UGKWP_E_ARG, "unknown diagnostic");
+    }
+    return UGKWP_OK;
+}
+
+int ugkwp_adjoint_wave(ugkwp_sim* s, const ugkwp_adjoint_req* r, double* dJ_dtheta) {
+    (void)s; (void)r; (void)dJ_dtheta;
+    return fail(UGKWP_E_UNSUPPORTED, "the adjoint of the wave flux is not available in this build");
+}
+
+}  // extern "C"

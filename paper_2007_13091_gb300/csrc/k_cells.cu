@@ -1,0 +1,332 @@
+// Per-cell kernels of the UGKWP step: primitives, relaxation time and the
+// time-step reduction (a1, a2), hydro-particle counts (a5), the exclusive scan
+// that lays out the next particle buffer (a11), and the conservative update
+// (a10).  Compiled with --fmad=false: tau, dt, N_sam and m_sam decide integer
+// outcomes of the particle path and must be reproducible bit for bit.
+#include <cfloat>
+
+#include "dmath.cuh"
+#include "ugkwp_internal.hpp"
+
+namespace ugkwp {
+
+namespace {
+
+__device__ __forceinline__ void set_err(const DevState& s, int32_t bits) {
+    atomicOr(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_ERR]), (unsigned long long)bits);
+}
+
+// Inclusive scan of one int per thread over a block of SCAN_BLOCK threads.
+__device__ __forceinline__ int block_scan_incl(int v, int* sh_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    if (lane == 31) sh_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int w = (lane < (int)(blockDim.x >> 5)) ? sh_warp[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += o;
+        }
+        sh_warp[lane] = w;
+    }
+    __syncthreads();
+    return v + (warp > 0 ? sh_warp[warp - 1] : 0);
+}
+
+__global__ void k_reset(DevMesh m, DevState s) {
+    const int nc = m.nc;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 5LL * nc; i += stride) {
+        s.pflux[i] = 0;
+        if (i < nc) {
+            s.nleft_next[i] = 0;
+            s.smass_next[i] = 0;
+            s.cursor[i] = 0;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        s.cnt64[CNT_SAMPLED] = 0;
+        s.cnt64[CNT_COLLIDED] = 0;
+        s.cnt64[CNT_EXITED] = 0;
+        s.cnt64[CNT_LOST] = 0;
+        s.cnt64[CNT_CROSSINGS] = 0;
+        s.cnt64[CNT_WALL] = 0;
+        s.cnt64[CNT_ALIVE] = 0;
+        s.cnt64[CNT_TRACKED] = 0;
+        s.cnt64[CNT_DT_BITS] = 0x7ff0000000000000LL;  // +inf
+    }
+}
+
+// a1 + a2: primitives, tau = mu_ref/p (T/T_ref)^omega, rho^p from the survivors'
+// fixed-point mass, rho^h = rho - rho^p, and min_i |Omega_i| / sum_d Lambda_i^d.
+__global__ void k_cell_prep(DevMesh m, DevState s, DevParams p) {
+    const int nc = m.nc;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double r = __longlong_as_double(0x7ff0000000000000LL);
+    if (i < nc) {
+        const double rho = s.W[i];
+        const double Ux = s.W[nc + i] / rho, Uy = s.W[2 * nc + i] / rho, Uz = s.W[3 * nc + i] / rho;
+        const double U2 = (Ux * Ux + Uy * Uy) + Uz * Uz;
+        const double pr = (s.W[4 * nc + i] - 0.5 * (rho * U2)) / 1.5;
+        const double T = pr / (rho * p.R);
+        double tau = 1.0;
+        if (!(rho > 0.0) || !(pr > 0.0) || !isfinite(pr)) {
+            set_err(s, ERRB_NONFINITE);
+        } else {
+            tau = (p.mu_ref / pr) * dm::d_exp(p.omega * dm::d_log(T / p.T_ref));
+            const double c = 3.0 * sqrt(p.R * T);
+            const double lam = ((fabs(Ux) + c) * m.dS[i] + (fabs(Uy) + c) * m.dS[nc + i]) + (fabs(Uz) + c) * m.dS[2 * nc + i];
+            r = m.vol[i] / lam;
+        }
+        const double rhop = ((double)s.smass[i] * p.qscale[0]) / m.vol[i];
+        s.prim[i] = rho;
+        s.prim[nc + i] = Ux;
+        s.prim[2 * nc + i] = Uy;
+        s.prim[3 * nc + i] = Uz;
+        s.prim[4 * nc + i] = T;
+        s.tau[i] = tau;
+        s.rhop[i] = rhop;
+        s.rhoh[i] = rho - rhop;
+    }
+    // block minimum, then one atomic on the ordered bit pattern (r > 0)
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) r = fmin(r, __shfl_xor_sync(0xffffffffu, r, d));
+    __shared__ double sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : __longlong_as_double(0x7ff0000000000000LL);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, d));
+        if (threadIdx.x == 0 && v < __longlong_as_double(0x7ff0000000000000LL) && v > 0.0)
+            atomicMin(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_DT_BITS]),
+                      (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+// a5 counts: rho^hp = e^{-dt/tau} rho^h, m_ref = (rho^p + rho^hp)|Omega|/N_ref,
+// N_sam = 2 ceil(rho^hp |Omega| / (2 m_ref)), N_sam >= N_min - N_left,
+// m_sam = rho^hp |Omega| / N_sam (Sec. 2.4 (b)).  Also the per-block sums of
+// the next buffer's per-cell counts.
+__global__ void k_sample_count(DevMesh m, DevState s, DevParams p) {
+    __shared__ int shw[32];
+    const int nc = m.nc;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double dt = p.CFL * __longlong_as_double(s.cnt64[CNT_DT_BITS]);
+    int count = 0;
+    if (i < nc) {
+        const double vol = m.vol[i];
+        const double ex = dm::d_exp(-(dt / s.tau[i]));
+        const double rh = s.rhoh[i] > 0.0 ? s.rhoh[i] : 0.0;
+        const double rhp = ex * rh;
+        const double Mhp = rhp * vol;
+        long long ns = 0;
+        double ms = 0.0;
+        if (Mhp > (s.prim[i] * vol) * 0x1p-30) {
+            const double mref = ((s.rhop[i] + rhp) * vol) / (double)p.N_ref;
+            ns = 2 * (long long)ceil(Mhp / (2.0 * mref));
+            const long long need = (long long)p.N_min - (long long)s.nleft[i];
+            if (need > ns) ns = need + (need & 1);
+            if (ns > 65534) {
+                set_err(s, ERRB_SAMPLE_LIMIT);
+                ns = 0;
+            } else {
+                ms = Mhp / (double)ns;
+            }
+        }
+        s.nsam[i] = (int)ns;
+        s.msam[i] = ms;
+        count = s.nleft[i] + (int)ns;
+        s.cnt[i] = count;
+    }
+    const int incl = block_scan_incl(count, shw);
+    if (threadIdx.x == blockDim.x - 1) s.bsum[blockIdx.x] = incl;
+    if (i == 0) s.dt[0] = dt;
+}
+
+// Exclusive scan of the block sums (one block), the total and the capacity check.
+__global__ void k_scan_bsum(DevState s, DevParams p, int nb) {
+    __shared__ int shw[32];
+    __shared__ long long carry_sh;
+    if (threadIdx.x == 0) carry_sh = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += blockDim.x) {
+        const int j = base + threadIdx.x;
+        const int v = j < nb ? s.bsum[j] : 0;
+        const int incl = block_scan_incl(v, shw);
+        const long long carry = carry_sh;
+        if (j < nb) s.bsum[j] = (int)(carry + incl - v);
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry_sh = carry + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const long long total = carry_sh;
+        s.cnt64[CNT_N_B] = total;
+        if (total > p.capacity) {
+            set_err(s, ERRB_CAPACITY);
+            s.cnt64[CNT_N_B] = 0;
+        }
+    }
+}
+
+__global__ void k_scan_apply(DevMesh m, DevState s) {
+    __shared__ int shw[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = i < m.nc ? s.cnt[i] : 0;
+    const int incl = block_scan_incl(v, shw);
+    if (i < m.nc) s.off[i] = s.bsum[blockIdx.x] + incl - v;
+}
+
+// a10: W^{n+1} = W^n - 1/|Omega| sum_k (+-F_k |S_k|) + F^{fr,p}/|Omega|, faces
+// gathered in local order 0..3 (Eq. update_macro_variables).
+__global__ void k_cell_update(DevMesh m, DevState s, DevParams p) {
+    const int nc = m.nc, nf = m.nf;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        s.t[0] = s.t[0] + s.dt[0];
+        s.cnt64[CNT_STEP] += 1;
+        s.cnt64[CNT_N_A] = s.cnt64[CNT_N_B];  // the tracked buffer becomes the current one
+    }
+    if (i >= nc) return;
+    int f[4];
+    const int own = m.cfs[i];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) f[k] = m.cf[k * nc + i];
+    const double vol = m.vol[i];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double v = s.F[(size_t)q * nf + f[k]] * m.f_area[f[k]];
+            acc = acc + (((own >> k) & 1) ? v : -v);
+        }
+        const double fp = (double)s.pflux[(size_t)q * nc + i] * p.qscale[q];
+        double& w = s.W[(size_t)q * nc + i];
+        w = (w - acc / vol) + fp / vol;
+    }
+}
+
+template <class Real>
+__global__ void k_rebuild(DevMesh m, DevState s, DevParams p, PartBufRaw a) {
+    const long long n = s.cnt64[CNT_N_A];
+    const int32_t* cell = a.cell;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int c = cell[i];
+        if (c < 0) continue;
+        atomicAdd(&s.nleft[c], 1);
+        const long long q = __double2ll_rn(a.m[i] * p.qinv[0]);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&s.smass[c]), (unsigned long long)q);
+    }
+}
+
+template <class Real>
+__global__ void k_wp_acc(DevMesh m, DevState s, DevParams p, PartBufRaw a) {
+    const long long n = s.cnt64[CNT_N_A];
+    const int nc = m.nc;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const Real* ux = (const Real*)a.u[0];
+    const Real* uy = (const Real*)a.u[1];
+    const Real* uz = (const Real*)a.u[2];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int c = a.cell[i];
+        if (c < 0) continue;
+        const double u0 = (double)ux[i], u1 = (double)uy[i], u2 = (double)uz[i], mm = a.m[i];
+        const double phi[5] = {mm, mm * u0, mm * u1, mm * u2, 0.5 * (mm * ((u0 * u0 + u1 * u1) + u2 * u2))};
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&s.wacc[(size_t)q * nc + c]),
+                      (unsigned long long)__double2ll_rn(phi[q] * p.qinv[q]));
+    }
+}
+
+__global__ void k_zero_wacc(DevMesh m, DevState s) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 5LL * m.nc; i += stride) s.wacc[i] = 0;
+}
+
+// which: 1 = W^p, 2 = W^h = W - W^p
+__global__ void k_wp_out(DevMesh m, DevState s, DevParams p, int which, double* out) {
+    const int nc = m.nc;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const double wp = ((double)s.wacc[(size_t)q * nc + i] * p.qscale[q]) / m.vol[i];
+        out[(size_t)q * nc + i] = which == 1 ? wp : s.W[(size_t)q * nc + i] - wp;
+    }
+}
+
+__global__ void k_prim_out(DevMesh m, DevState s, DevParams p, double* out) {
+    const int nc = m.nc;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const double rho = s.W[i];
+    const double Ux = s.W[nc + i] / rho, Uy = s.W[2 * nc + i] / rho, Uz = s.W[3 * nc + i] / rho;
+    const double U2 = (Ux * Ux + Uy * Uy) + Uz * Uz;
+    const double pr = (s.W[4 * nc + i] - 0.5 * (rho * U2)) / 1.5;
+    out[i] = rho;
+    out[nc + i] = Ux;
+    out[2 * nc + i] = Uy;
+    out[3 * nc + i] = Uz;
+    out[4 * nc + i] = pr / (rho * p.R);
+}
+
+inline int cdiv(long long a, int b) { return (int)((a + b - 1) / b); }
+
+}  // namespace
+
+int particle_grid() {
+    static int g = 0;
+    if (!g) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+        g = sms * 8;
+    }
+    return g;
+}
+
+void launch_reset(const DevMesh& m, const DevState& s, cudaStream_t st) {
+    k_reset<<<cdiv(5LL * m.nc, 256) < 4096 ? cdiv(5LL * m.nc, 256) : 4096, 256, 0, st>>>(m, s);
+}
+void launch_cell_prep(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
+    k_cell_prep<<<cdiv(m.nc, 256), 256, 0, st>>>(m, s, p);
+}
+void launch_sample_count(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
+    k_sample_count<<<scan_blocks(m.nc), SCAN_BLOCK, 0, st>>>(m, s, p);
+}
+void launch_scan(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
+    k_scan_bsum<<<1, SCAN_BLOCK, 0, st>>>(s, p, scan_blocks(m.nc));
+    k_scan_apply<<<scan_blocks(m.nc), SCAN_BLOCK, 0, st>>>(m, s);
+}
+void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
+    k_cell_update<<<cdiv(m.nc, 256), 256, 0, st>>>(m, s, p);
+}
+void launch_rebuild_survivors(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
+                              cudaStream_t st) {
+    if (p.precision == UGKWP_MIXED) k_rebuild<float><<<particle_grid(), 256, 0, st>>>(m, s, p, a);
+    else k_rebuild<double><<<particle_grid(), 256, 0, st>>>(m, s, p, a);
+}
+void launch_wp_moments(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
+                       double* out, cudaStream_t st) {
+    k_zero_wacc<<<cdiv(5LL * m.nc, 256), 256, 0, st>>>(m, s);
+    if (p.precision == UGKWP_MIXED) k_wp_acc<float><<<particle_grid(), 256, 0, st>>>(m, s, p, a);
+    else k_wp_acc<double><<<particle_grid(), 256, 0, st>>>(m, s, p, a);
+    (void)out;
+}
+void launch_prim_moments(const DevMesh& m, const DevState& s, const DevParams& p, int which, double* out,
+                         cudaStream_t st) {
+    if (which == UGKWP_PRIM) k_prim_out<<<cdiv(m.nc, 256), 256, 0, st>>>(m, s, p, out);
+    else k_wp_out<<<cdiv(m.nc, 256), 256, 0, st>>>(m, s, p, which, out);
+}
+
+}  // namespace ugkwp

@@ -1,0 +1,394 @@
+// Particle kernels of the UGKWP step, templated on the particle precision
+// (double: FP64 mode; float: MIXED mode).  Compiled with --fmad=false so that
+// every particle trajectory and fixed-point flux is reproducible bit for bit.
+//
+//   k_scatter       a11: survivors of the last step -> cell-sorted slots of the
+//                   next buffer (warp-aggregated slot reservation per cell).
+//   k_sample_write  a5: N_sam hydro particles per cell, in pairs U +/- sqrt(RT) X
+//                   with X ~ N(0, I) (Box-Muller), uniform in the tet.
+//   k_track         a6-a9: t_f = min(-tau ln eta, dt), face-by-face streaming,
+//                   boundary interaction, fixed-point particle flux, removal.
+#include "dmath.cuh"
+#include "ugkwp_internal.hpp"
+
+namespace ugkwp {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+enum : unsigned long long { TAG_TF = 1, TAG_SVEL = 2, TAG_SPOS = 3, TAG_WALL = 4 };
+
+__device__ __forceinline__ void set_err(const DevState& s, int32_t bits) {
+    atomicOr(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_ERR]), (unsigned long long)bits);
+}
+
+__device__ __forceinline__ unsigned long long make_id(long long step, int cell, int k) {
+    return ((unsigned long long)step << 40) | ((unsigned long long)cell << 16) | (unsigned long long)k;
+}
+
+template <class Real> __device__ __forceinline__ PartView<Real> view(const PartBufRaw& r) {
+    PartView<Real> v;
+    for (int c = 0; c < 3; ++c) {
+        v.x[c] = (Real*)r.x[c];
+        v.u[c] = (Real*)r.u[c];
+    }
+    v.m = r.m;
+    v.cell = r.cell;
+    v.id = r.id;
+    return v;
+}
+
+// ------------------------------------------------------------------ scatter
+template <class Real>
+__global__ void __launch_bounds__(256) k_scatter(DevState s, PartBufRaw ar, PartBufRaw br) {
+    if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
+    const PartView<Real> a = view<Real>(ar), b = view<Real>(br);
+    const long long n = s.cnt64[CNT_N_A];
+    const int lane = threadIdx.x & 31;
+    const long long wstride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += wstride) {
+        const long long i = base + lane;
+        const int c = i < n ? a.cell[i] : -1;
+        const unsigned grp = __match_any_sync(FULL, c);
+        if (c >= 0) {
+            const int leader = __ffs(grp) - 1;
+            const int rank = __popc(grp & ((1u << lane) - 1u));
+            int slot0 = 0;
+            if (lane == leader) slot0 = atomicAdd(&s.cursor[c], __popc(grp));
+            slot0 = __shfl_sync(grp, slot0, leader);
+            const long long j = (long long)s.off[c] + slot0 + rank;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                b.x[d][j] = a.x[d][i];
+                b.u[d][j] = a.u[d][i];
+            }
+            b.m[j] = a.m[i];
+            b.cell[j] = c;
+            b.id[j] = a.id[i];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ sampling
+template <class Real>
+__global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, DevParams p, PartBufRaw br) {
+    if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
+    const PartView<Real> b = view<Real>(br);
+    const int nc = m.nc;
+    const int cell = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (cell >= nc) return;
+    const int ns = s.nsam[cell];
+    if (ns == 0) return;
+    const long long step = s.cnt64[CNT_STEP];
+    const double ms = s.msam[cell];
+    const double U[3] = {s.prim[nc + cell], s.prim[2 * nc + cell], s.prim[3 * nc + cell]};
+    const double sig = sqrt(p.R * s.prim[4 * nc + cell]);
+    double P0[3], E1[3], E2[3], E3[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        P0[c] = m.vtx[(size_t)c * nc + cell];
+        E1[c] = m.vtx[(size_t)(3 + c) * nc + cell] - P0[c];
+        E2[c] = m.vtx[(size_t)(6 + c) * nc + cell] - P0[c];
+        E3[c] = m.vtx[(size_t)(9 + c) * nc + cell] - P0[c];
+    }
+    const long long first = (long long)s.off[cell] + s.nleft[cell];
+    for (int k = lane; k < ns; k += 32) {
+        const int side = k & 1;
+        const unsigned long long ida = make_id(step, cell, k - side);
+        const dm::U4 r = dm::philox(ida, (unsigned long long)step, TAG_SVEL, 0ULL, p.seed, 0ULL);
+        double sn, cs, X[3];
+        double rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.a)));
+        dm::d_sincos2pi(dm::u01d(r.b), &sn, &cs);
+        X[0] = rad * cs;
+        X[1] = rad * sn;
+        rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.c)));
+        dm::d_sincos2pi(dm::u01d(r.d), &sn, &cs);
+        X[2] = rad * cs;
+        const unsigned long long id = ida + (unsigned long long)side;
+        const dm::U4 rp = dm::philox(id, (unsigned long long)step, TAG_SPOS, 0ULL, p.seed, 0ULL);
+        double a = dm::u01d(rp.a), bb = dm::u01d(rp.b), cc = dm::u01d(rp.c);
+        // cube -> prism -> tet folding of a uniform point (Rocchini & Cignoni 2000)
+        if (a + bb > 1.0) { a = 1.0 - a; bb = 1.0 - bb; }
+        if (bb + cc > 1.0) {
+            const double t = cc;
+            cc = 1.0 - a - bb;
+            bb = 1.0 - t;
+        } else if (a + bb + cc > 1.0) {
+            const double t = cc;
+            cc = a + bb + cc - 1.0;
+            a = 1.0 - bb - t;
+        }
+        const long long j = first + k;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            b.x[c][j] = (Real)(P0[c] + ((a * E1[c] + bb * E2[c]) + cc * E3[c]));
+            b.u[c][j] = (Real)(side == 0 ? U[c] + sig * X[c] : U[c] - sig * X[c]);
+        }
+        b.m[j] = ms;
+        b.cell[j] = cell;
+        b.id[j] = id;
+    }
+    if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_SAMPLED]), (unsigned long long)ns);
+}
+
+// ------------------------------------------------------------------ tracking
+template <class Real> struct Trk;
+template <> struct Trk<float> {
+    __device__ static __forceinline__ void plane(const DevMesh& m, int tet, int k, float& nx, float& ny, float& nz,
+                                                 float& d) {
+        const float4 v = m.trk_f[tet].pl[k];
+        nx = v.x; ny = v.y; nz = v.z; d = v.w;
+    }
+    __device__ static __forceinline__ int nb(const DevMesh& m, int tet, int k) {
+        const int4 v = m.trk_f[tet].nb;
+        return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+    }
+    __device__ static __forceinline__ float tf(double tau, unsigned long long r) {
+        return -((float)tau * dm::f_log(dm::u01f(r)));
+    }
+};
+template <> struct Trk<double> {
+    __device__ static __forceinline__ void plane(const DevMesh& m, int tet, int k, double& nx, double& ny,
+                                                 double& nz, double& d) {
+        const Dbl4 v = m.trk_d[tet].pl[k];
+        nx = v.x; ny = v.y; nz = v.z; d = v.w;
+    }
+    __device__ static __forceinline__ int nb(const DevMesh& m, int tet, int k) {
+        const int4 v = m.trk_d[tet].nb;
+        return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+    }
+    __device__ static __forceinline__ double tf(double tau, unsigned long long r) {
+        return -(tau * dm::d_log(dm::u01d(r)));
+    }
+};
+
+// Fixed-point image of phi = m (1, u, |u|^2/2); false if a value leaves |v| < 2^62.
+template <class Real>
+__device__ __forceinline__ bool phi_q(const Real* u, double mm, const DevParams& p, long long q[5]) {
+    const double u0 = (double)u[0], u1 = (double)u[1], u2 = (double)u[2];
+    const double phi[5] = {mm, mm * u0, mm * u1, mm * u2, 0.5 * (mm * ((u0 * u0 + u1 * u1) + u2 * u2))};
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        double v = phi[k] * p.qinv[k];
+        if (!(fabs(v) < 0x1p62)) { ok = false; v = 0.0; }
+        q[k] = __double2ll_rn(v);
+    }
+    return ok;
+}
+
+template <class Real>
+__global__ void __launch_bounds__(256) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br) {
+    if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
+    const PartView<Real> b = view<Real>(br);
+    const long long n = s.cnt64[CNT_N_B];
+    const long long step = s.cnt64[CNT_STEP];
+    const double dt = s.dt[0];
+    const Real dtR = (Real)dt;
+    const int nc = m.nc;
+    const int lane = threadIdx.x & 31;
+    const long long wstride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += wstride) {
+        const long long i = base + lane;
+        const bool valid = i < n;
+        int status = 0, ncross = 0, nrefl = 0, nwall = 0;
+        int c0 = -1, tet = -1;
+        long long qmass = 0;
+        bool survivor = false;
+        if (valid) {
+            const unsigned long long id = b.id[i];
+            c0 = b.cell[i];
+            Real x0[3], u[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) { x0[c] = b.x[c][i]; u[c] = b.u[c][i]; }
+            const double mm = b.m[i];
+            const Real us[3] = {u[0], u[1], u[2]};
+            Real t_end = dtR;
+            bool coll = false;
+            if ((long long)(id >> 40) != step) {
+                const dm::U4 r = dm::philox(id, (unsigned long long)step, TAG_TF, 0ULL, p.seed, 0ULL);
+                const Real tf = Trk<Real>::tf(s.tau[c0], r.a);
+                if (tf < dtR) { coll = true; t_end = tf; }
+            }
+            // ---- face-by-face walk along x0 + u (t - t0)
+            tet = c0;
+            int last = -1;
+            Real t0 = (Real)0;
+            Real xe[3];
+            for (;;) {
+                int best = -1;
+                Real sbest = (Real)0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (k == last) continue;
+                    Real nx, ny, nz, d;
+                    Trk<Real>::plane(m, tet, k, nx, ny, nz, d);
+                    const Real un = (u[0] * nx + u[1] * ny) + u[2] * nz;
+                    if (un > (Real)0) {
+                        const Real xn = (x0[0] * nx + x0[1] * ny) + x0[2] * nz;
+                        const Real sk = (d - xn) / un;
+                        if (best < 0 || sk < sbest) { best = k; sbest = sk; }
+                    }
+                }
+                const Real rem = t_end - t0;
+                if (best < 0 || sbest >= rem) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) xe[c] = x0[c] + u[c] * rem;
+                    break;
+                }
+                if (sbest < (Real)0) sbest = (Real)0;
+                ++ncross;
+                if (ncross > p.max_crossings) {
+                    status |= 4;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) xe[c] = x0[c];
+                    break;
+                }
+                const int code = Trk<Real>::nb(m, tet, best);
+                if (code >= 0) { tet = code >> 2; last = code & 3; continue; }
+                const int bi = -1 - code;
+                const DevBc& bc = p.bc[m.bf_tag[bi]];
+                if (bc.type == UGKWP_BC_FARFIELD || bc.type == UGKWP_BC_OUTFLOW) { status |= 2; break; }
+                Real xh[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) xh[c] = x0[c] + u[c] * sbest;
+                if (bc.type == UGKWP_BC_SPECULAR) {
+                    Real nx, ny, nz, d;
+                    Trk<Real>::plane(m, tet, best, nx, ny, nz, d);
+                    const Real un = (u[0] * nx + u[1] * ny) + u[2] * nz;
+                    const Real two = un + un;
+                    u[0] = u[0] - two * nx;
+                    u[1] = u[1] - two * ny;
+                    u[2] = u[2] - two * nz;
+                } else {
+                    // diffuse re-emission, full accommodation: |u_n| = sqrt(-2 R T_w ln eta),
+                    // tangential components U_w,t + sqrt(R T_w) N(0,1)
+                    const dm::U4 r = dm::philox(id, (unsigned long long)step, TAG_WALL, (unsigned long long)nwall,
+                                                p.seed, 0ULL);
+                    const double vn = sqrt(-2.0 * p.R * bc.T_w * dm::d_log(dm::u01d(r.a)));
+                    const double rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.b)));
+                    double sn, cs;
+                    dm::d_sincos2pi(dm::u01d(r.c), &sn, &cs);
+                    const double sw = sqrt(p.R * bc.T_w);
+                    const int nbf = m.nbf;
+                    double n3[3], t1[3], t2[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        n3[c] = m.bf_n[(size_t)c * nbf + bi];
+                        t1[c] = m.bf_t1[(size_t)c * nbf + bi];
+                        t2[c] = m.bf_t2[(size_t)c * nbf + bi];
+                    }
+                    const double v1 = ((bc.U_w[0] * t1[0] + bc.U_w[1] * t1[1]) + bc.U_w[2] * t1[2]) + sw * (rad * cs);
+                    const double v2 = ((bc.U_w[0] * t2[0] + bc.U_w[1] * t2[1]) + bc.U_w[2] * t2[2]) + sw * (rad * sn);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) u[c] = (Real)(((-vn) * n3[c] + v1 * t1[c]) + v2 * t2[c]);
+                    ++nwall;
+                }
+                ++nrefl;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) x0[c] = xh[c];
+                t0 = t0 + sbest;
+                last = best;
+            }
+            const bool exited = status & 2;
+            const bool lost = status & 4;
+            survivor = !exited && (!coll || lost);
+            if (coll && !lost && !exited) status |= 1;
+            // ---- particle flux by counting: -phi at the start cell, +phi at the end
+            // cell; a particle that ends in its start cell with its velocity unchanged
+            // contributes nothing and is skipped.
+            long long q0[5], q1[5];
+            bool ok = phi_q(us, mm, p, q0);
+            ok &= phi_q(u, mm, p, q1);
+            if (!ok) set_err(s, ERRB_FIXED_OVERFLOW);
+            if (exited || tet != c0 || nrefl > 0) {
+#pragma unroll
+                for (int q = 0; q < 5; ++q)
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&s.pflux[(size_t)q * nc + c0]),
+                              (unsigned long long)(-q0[q]));
+                if (!exited) {
+#pragma unroll
+                    for (int q = 0; q < 5; ++q)
+                        atomicAdd(reinterpret_cast<unsigned long long*>(&s.pflux[(size_t)q * nc + tet]),
+                                  (unsigned long long)q1[q]);
+                }
+            }
+            qmass = q1[0];
+            // ---- write back
+            if (survivor) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) b.x[c][i] = xe[c];
+                if (nrefl > 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) b.u[c][i] = u[c];
+                }
+                if (tet != c0) b.cell[i] = tet;
+            } else {
+                b.cell[i] = -1;
+            }
+        }
+        // ---- survivors per end cell (count, fixed-point mass): segmented
+        // reduction over lanes with equal keys in a row, one atomic per run
+        const int key = survivor ? tet : -1;
+        long long v = survivor ? qmass : 0;
+        const int prev = __shfl_up_sync(FULL, key, 1);
+        const bool head = lane == 0 || prev != key;
+        const unsigned heads = __ballot_sync(FULL, head);
+        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const long long o = __shfl_up_sync(FULL, v, d);
+            if (lane - d >= start) v += o;
+        }
+        const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+        if (tail && key >= 0) {
+            atomicAdd(&s.nleft_next[key], lane - start + 1);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&s.smass_next[key]), (unsigned long long)v);
+        }
+        // ---- counters
+        const unsigned n_surv = __popc(__ballot_sync(FULL, survivor));
+        const unsigned n_valid = __popc(__ballot_sync(FULL, valid));
+        const unsigned n_coll = __popc(__ballot_sync(FULL, status & 1));
+        const unsigned n_exit = __popc(__ballot_sync(FULL, status & 2));
+        const unsigned n_lost = __popc(__ballot_sync(FULL, status & 4));
+        const unsigned n_x = __reduce_add_sync(FULL, (unsigned)ncross);
+        const unsigned n_w = __reduce_add_sync(FULL, (unsigned)nwall);
+        if (lane == 0) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_ALIVE]), (unsigned long long)n_surv);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_TRACKED]), (unsigned long long)n_valid);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_MOVES]), (unsigned long long)n_valid);
+            if (n_coll) atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_COLLIDED]), (unsigned long long)n_coll);
+            if (n_exit) atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_EXITED]), (unsigned long long)n_exit);
+            if (n_lost) {
+                atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_LOST]), (unsigned long long)n_lost);
+                set_err(s, ERRB_TRACK_LIMIT);
+            }
+            if (n_x) atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_CROSSINGS]), (unsigned long long)n_x);
+            if (n_w) atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_WALL]), (unsigned long long)n_w);
+        }
+    }
+}
+
+}  // namespace
+
+void launch_scatter(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
+                    const PartBufRaw& b, cudaStream_t st) {
+    (void)m;
+    if (p.precision == UGKWP_MIXED) k_scatter<float><<<particle_grid(), 256, 0, st>>>(s, a, b);
+    else k_scatter<double><<<particle_grid(), 256, 0, st>>>(s, a, b);
+}
+
+void launch_sample_write(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b,
+                         cudaStream_t st) {
+    const int blocks = (m.nc + 7) / 8;
+    if (p.precision == UGKWP_MIXED) k_sample_write<float><<<blocks, 256, 0, st>>>(m, s, p, b);
+    else k_sample_write<double><<<blocks, 256, 0, st>>>(m, s, p, b);
+}
+
+void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b, cudaStream_t st) {
+    if (p.precision == UGKWP_MIXED) k_track<float><<<particle_grid(), 256, 0, st>>>(m, s, p, b);
+    else k_track<double><<<particle_grid(), 256, 0, st>>>(m, s, p, b);
+}
+
+}  // namespace ugkwp

@@ -1,0 +1,174 @@
+// Internal types of the ugkwp library: host mesh object, device views passed
+// to the kernels by value, and the launch functions of each kernel family.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ugkwp.h"
+
+namespace ugkwp {
+
+// Error bits of the device error word.
+enum : int32_t {
+    ERRB_CAPACITY = 1,
+    ERRB_TRACK_LIMIT = 2,
+    ERRB_FIXED_OVERFLOW = 4,
+    ERRB_NONFINITE = 8,
+    ERRB_SAMPLE_LIMIT = 16,
+};
+
+// Device counters (int64 slots).
+enum : int {
+    CNT_N_A = 0,        // particles in the current buffer (dead ones included)
+    CNT_N_B = 1,        // particles in the next buffer after the scan
+    CNT_ALIVE = 2,      // survivors of the last step
+    CNT_SAMPLED = 3,
+    CNT_COLLIDED = 4,
+    CNT_EXITED = 5,
+    CNT_LOST = 6,
+    CNT_CROSSINGS = 7,
+    CNT_WALL = 8,
+    CNT_STEP = 9,       // step index of the next step
+    CNT_TRACKED = 10,
+    CNT_DT_BITS = 11,   // min_i |Omega_i| / sum Lambda as ordered bits (positive double)
+    CNT_ERR = 12,       // error bits
+    CNT_MOVES = 13,     // particle moves since init (never reset by a step)
+    CNT_SLOTS = 16,
+};
+
+struct DevBc {
+    int32_t type;
+    int32_t pad;
+    double T_w;
+    double U_w[3];
+    double W_in[5];
+};
+
+struct DevParams {
+    double R, mu_ref, T_ref, omega, CFL, C2;
+    int32_t N_ref, N_min, max_crossings, precision;
+    uint64_t seed;
+    int64_t capacity;
+    int32_t exps[5];
+    int32_t n_bc;
+    double qscale[5];      // 2^e (fixed-point quantum)
+    double qinv[5];        // 2^-e
+    DevBc bc[16];
+};
+
+// Tracking record of one tet: outward face planes (n, d) and neighbour codes
+// (tet << 2 | local face in the neighbour, or -1 - boundary-face index).
+struct __align__(16) TrkF {
+    float4 pl[4];
+    int4 nb;
+};
+struct __align__(16) Dbl4 {
+    double x, y, z, w;
+};
+struct __align__(16) TrkD {
+    Dbl4 pl[4];
+    int4 nb;
+};
+
+struct DevMesh {
+    int32_t nc, nf, nbf;
+    const double* vol;       // [nc]
+    const double* dS;        // [3][nc]
+    const double* vtx;       // [12][nc]: vertex k coordinate c at [(3k+c) nc + i]
+    const int32_t* cf;       // [4][nc] face of local face k
+    const int32_t* cfs;      // [nc] bit k set if the cell owns local face k
+    const TrkF* trk_f;       // [nc]
+    const TrkD* trk_d;       // [nc]
+    const int32_t* f_own;    // [nf]
+    const int32_t* f_nbr;    // [nf] >= 0 tet, else -1 - boundary index
+    const double* f_n;       // [3][nf]
+    const double* f_area;    // [nf]
+    const int32_t* bf_tag;   // [nbf]
+    const double* bf_n;      // [3][nbf] outward unit normal (double)
+    const double* bf_t1;     // [3][nbf]
+    const double* bf_t2;     // [3][nbf]
+};
+
+template <class Real> struct PartView {
+    Real* x[3];
+    Real* u[3];
+    double* m;
+    int32_t* cell;
+    uint64_t* id;
+};
+
+struct PartBufRaw {
+    void* x[3];
+    void* u[3];
+    double* m;
+    int32_t* cell;
+    uint64_t* id;
+};
+
+struct DevState {
+    double* W;            // [5][nc]
+    double* prim;         // [5][nc] rho, Ux, Uy, Uz, T
+    double* tau;          // [nc]
+    double* rhoh;         // [nc]
+    double* rhop;         // [nc]
+    int32_t* nsam;        // [nc]
+    double* msam;         // [nc]
+    int32_t* nleft;       // [nc] survivors at the start of the step
+    int32_t* nleft_next;  // [nc]
+    int64_t* smass;       // [nc] survivors' fixed-point mass
+    int64_t* smass_next;  // [nc]
+    int32_t* cnt;         // [nc] particles per cell after sampling
+    int32_t* off;         // [nc] first slot of the cell in the next buffer
+    int32_t* cursor;      // [nc]
+    int64_t* pflux;       // [5][nc] fixed-point particle flux
+    int64_t* wacc;        // [5][nc] fixed-point scratch for W^p
+    double* mom;          // [5][nc] staging of moments copied to the host
+    double* F;            // [5][nf]
+    int32_t* bsum;        // [n_scan_blocks]
+    double* t;            // [1]
+    double* dt;           // [1]
+    int64_t* cnt64;       // [CNT_SLOTS]
+};
+
+struct MeshHost {
+    int32_t nn = 0, nc = 0, nf = 0, nbf = 0;
+    std::vector<double> xyz;
+    std::vector<int32_t> tet;
+    std::vector<int32_t> cf;       // [4*nc] face of local face k (cell-major)
+    std::vector<int8_t> cf_sign;   // [4*nc]
+    std::vector<int32_t> f_own, f_own_k, f_nbr, f_nbr_k, f_tag;  // f_nbr < 0 for boundary
+    std::vector<double> f_n, f_area, f_d, f_t1, f_t2;            // [3*nf] / [nf]
+    std::vector<double> vol, dS;                                 // [nc], [3*nc]
+    std::vector<int32_t> bf_of_face;                             // [nf] boundary index or -1
+    std::vector<int32_t> face_of_bf;                             // [nbf]
+};
+
+// Kernel launchers (stream-ordered, no synchronisation).
+constexpr int SCAN_BLOCK = 1024;
+inline int scan_blocks(int nc) { return (nc + SCAN_BLOCK - 1) / SCAN_BLOCK; }
+
+void launch_reset(const DevMesh& m, const DevState& s, cudaStream_t st);
+void launch_cell_prep(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
+void launch_sample_count(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
+void launch_scan(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
+void launch_scatter(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
+                    const PartBufRaw& b, cudaStream_t st);
+void launch_sample_write(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b,
+                         cudaStream_t st);
+void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b,
+                  cudaStream_t st);
+void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
+void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
+void launch_rebuild_survivors(const DevMesh& m, const DevState& s, const DevParams& p,
+                              const PartBufRaw& a, cudaStream_t st);
+void launch_wp_moments(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
+                       double* out, cudaStream_t st);
+void launch_prim_moments(const DevMesh& m, const DevState& s, const DevParams& p, int which,
+                         double* out, cudaStream_t st);
+
+int particle_grid();  // fixed grid of particle kernels (multiple of the SM count)
+
+}  // namespace ugkwp

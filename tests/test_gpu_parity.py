@@ -1,0 +1,225 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle.
+
+Protocol (teacher forcing): both sides start one step from the same state
+(the oracle's own state after a few oracle steps, imported into the GPU), then
+  * particles (id, cell, x, u, m) are equal bit for bit,
+  * fixed-point sums (particle flux F^{fr,p}, survivor mass and count) are equal,
+  * dt, tau, rho^h, N_sam, m_sam are equal bit for bit,
+  * the wave flux and W^{n+1} agree within 1e-12 relative L2 (FP64 arithmetic
+    with different exp/erfc implementations and fused multiply-adds).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2007_13091_gb300 import ugkwp, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def _rel_l2(a, b):
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    den = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def _sorted(st):
+    o = np.argsort(st["id"], kind="stable")
+    return {"id": st["id"][o], "cell": st["cell"][o], "x": st["x"][:, o], "u": st["u"][:, o], "m": st["m"][o]}
+
+
+def assert_particles_equal(g, o):
+    a, b = _sorted(g), _sorted(o)
+    assert a["id"].size == b["id"].size, (a["id"].size, b["id"].size)
+    assert np.array_equal(a["id"], b["id"])
+    assert np.array_equal(a["cell"], b["cell"])
+    assert np.array_equal(a["m"], b["m"])
+    assert np.array_equal(a["x"], b["x"])
+    assert np.array_equal(a["u"], b["u"])
+
+
+def compare_step(gsim, osim, check_flux=True):
+    g, o = gsim.state(), osim.state()
+    assert g["step"] == o["step"]
+    assert gsim.last("dt") == osim.last("dt")
+    for k in ("tau", "rho_h", "n_sam", "m_sam"):
+        assert np.array_equal(gsim.last(k), osim.last(k)), k
+    for k in ("pflux", "surv_mass", "surv_count"):
+        assert np.array_equal(gsim.last(k), osim.last(k)), k
+    assert_particles_equal(g, o)
+    if check_flux:
+        Fg, Fo = gsim.last("flux"), osim.last("flux")
+        for q in range(5):
+            scale = max(np.linalg.norm(Fo[q]), np.linalg.norm(Fo[1:4]) * 1e-3)
+            assert np.linalg.norm(Fg[q] - Fo[q]) <= TOL * scale + 1e-300, q
+    for q in range(5):
+        assert _rel_l2(g["W"][q], o["W"][q]) <= TOL, (q, _rel_l2(g["W"][q], o["W"][q]))
+    assert g["t"] == pytest.approx(o["t"], rel=1e-15)
+
+
+def run_teacher_forced(cfg, warm_steps):
+    osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    osim.step(warm_steps)
+    gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    gsim.set_state(osim.state())
+    g0 = gsim.state()
+    assert_particles_equal(g0, osim.state())  # import/export round trip
+    osim.step()
+    gsim.step()
+    gsim.sync()
+    compare_step(gsim, osim)
+    return gsim, osim
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_shock_tube_first_step_from_init(precision):
+    cfg = wl.shock_tube(precision=precision)
+    osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    osim.step()
+    st = gsim.step(1, stats=True)
+    compare_step(gsim, osim)
+    c = osim.last("counters")
+    assert st["n_sampled"] == c["n_sampled"] and st["n_exited"] == c["n_exited"]
+    assert st["n_crossings"] == c["n_crossings"] and st["n_particles"] == osim.sizes()["n_particles"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_shock_tube_teacher_forced(precision):
+    gsim, osim = run_teacher_forced(wl.shock_tube(precision=precision), warm_steps=3)
+    assert osim.last("counters")["n_collided"] > 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cavity_diffuse_walls_teacher_forced(precision):
+    cfg = wl.cavity(n=6, N_ref=40, precision=precision)
+    gsim, osim = run_teacher_forced(cfg, warm_steps=3)
+    assert osim.last("counters")["n_wall_hits"] > 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cube_farfield_jittered_teacher_forced(precision):
+    cfg = wl.cube_flow(h0=0.5, growth=2.0, N_ref=30, precision=precision, Kn=0.1)
+    assert len(cfg["mesh"]["tets"]) > 1024 + 1  # several scan blocks and a ragged tail
+    gsim, osim = run_teacher_forced(cfg, warm_steps=2)
+    c = osim.last("counters")
+    assert c["n_exited"] > 0 and c["n_wall_hits"] > 0
+
+
+def test_specular_box_degenerate_starts():
+    """Particles placed exactly on nodes, edges and faces (teacher-forced import)."""
+    cfg = wl.uniform_box(n=(3, 3, 3), Kn=0.5, N_ref=10, bc_type="specular")
+    osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    osim.step(1)
+    st = osim.state()
+    nodes, tets = cfg["mesh"]["nodes"], cfg["mesh"]["tets"]
+    k = min(400, st["id"].size)
+    P = nodes[tets[st["cell"][:k]]]
+    choice = np.arange(k) % 4
+    st["x"][:, :k] = np.where(choice == 0, P[:, 0], np.where(choice == 1, 0.5 * (P[:, 0] + P[:, 3]),
+                              np.where(choice == 2, (P[:, 1] + P[:, 2] + P[:, 3]) / 3, P.mean(1)))).T
+    osim.set_state(st)
+    gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    gsim.set_state(st)
+    osim.step()
+    gsim.step()
+    compare_step(gsim, osim)
+
+
+def test_free_running_multi_step():
+    """Five steps each side from the same initial state: fields stay within
+    tolerance; particle ids and cells stay identical."""
+    cfg = wl.shock_tube(precision="fp64")
+    osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    for _ in range(5):
+        osim.step()
+        gsim.step()
+        g, o = gsim.state(), osim.state()
+        for q in range(5):
+            assert _rel_l2(g["W"][q], o["W"][q]) <= 1e-11
+        a, b = _sorted(g), _sorted(o)
+        assert np.array_equal(a["id"], b["id"]) and np.array_equal(a["cell"], b["cell"])
+        np.testing.assert_allclose(a["x"], b["x"], rtol=1e-12, atol=1e-14)
+
+
+def test_no_particles_regime():
+    """Near-continuum: e^{-dt/tau} below the sampling floor, no particle at all."""
+    cfg = wl.shock_tube(nx=40, ny=2, nz=2, Kn=1e-9, precision="mixed")
+    osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    for _ in range(3):
+        osim.step()
+        gsim.step()
+    assert gsim.state()["id"].size == 0
+    compare_step(gsim, osim)
+
+
+def test_moments_wp_wh_prim():
+    cfg = wl.cavity(n=5, N_ref=30, precision="mixed")
+    osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    osim.step(2)
+    gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    st = osim.state()
+    gsim.set_state(st)
+    vol = osim.geometry("vol")
+    nc = vol.size
+    phi = np.stack([st["m"], st["m"] * st["u"][0], st["m"] * st["u"][1], st["m"] * st["u"][2],
+                    0.5 * st["m"] * (st["u"] ** 2).sum(0)])
+    WP = np.stack([np.bincount(st["cell"], phi[q], nc) for q in range(5)]) / vol
+    np.testing.assert_allclose(gsim.moments(ugkwp.WP), WP, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(gsim.moments(ugkwp.WH), st["W"] - WP, rtol=1e-11, atol=1e-12)
+    np.testing.assert_array_equal(gsim.moments(ugkwp.W), st["W"])
+    prim = gsim.moments(ugkwp.PRIM)
+    np.testing.assert_allclose(prim[0], st["W"][0], rtol=0)
+    p = (st["W"][4] - 0.5 * (st["W"][1:4] ** 2).sum(0) / st["W"][0]) / 1.5
+    np.testing.assert_allclose(prim[4], p / st["W"][0], rtol=1e-13)
+
+
+def test_capacity_overflow_is_reported():
+    cfg = wl.shock_tube(nx=20, ny=2, nz=2)
+    cfg["params"]["particle_capacity"] = 1000  # far below the 240 x 50 sampled particles
+    gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    gsim.step()
+    with pytest.raises(ugkwp.UgkwpError) as e:
+        gsim.sync()
+    assert e.value.code == ugkwp.E_CAPACITY
+
+
+def test_crossing_limit_is_reported():
+    """A planted fast particle exceeds max_crossings: both sides report it, keep
+    it in place, and otherwise agree."""
+    cfg = wl.shock_tube(nx=40, ny=2, nz=2, Kn=10.0)
+    cfg["params"]["max_crossings"] = 20
+    osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    osim.step()
+    st = osim.state()
+    k = np.argmin(np.abs(st["x"][0] - 0.3))
+    st["u"][:, k] = (500.0, 3.0, 2.0)  # ~0.2 length units in one step: dozens of faces
+    osim.set_state(st)
+    gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    gsim.set_state(st)
+    with pytest.raises(RuntimeError, match="max_crossings"):
+        osim.step()
+    with pytest.raises(ugkwp.UgkwpError) as e:
+        gsim.step(1, stats=True)
+    assert e.value.code == ugkwp.E_TRACK_LIMIT
+    compare_step(gsim, osim)
+
+
+def test_import_rejects_bad_state():
+    cfg = wl.shock_tube(nx=10, ny=2, nz=2, precision="mixed")
+    osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    osim.step()
+    st = osim.state()
+    gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    bad = dict(st, x=st["x"] + 1e-12)  # not representable in binary32
+    with pytest.raises(ugkwp.UgkwpError) as e:
+        gsim.set_state(bad)
+    assert e.value.code == ugkwp.E_STATE
+    bad = dict(st, cell=np.where(np.arange(st["cell"].size) == 0, 10 ** 6, st["cell"]).astype(np.int32))
+    with pytest.raises(ugkwp.UgkwpError):
+        gsim.set_state(bad)
