@@ -118,7 +118,7 @@ def test_specular_box_degenerate_starts():
     nodes, tets = cfg["mesh"]["nodes"], cfg["mesh"]["tets"]
     k = min(400, st["id"].size)
     P = nodes[tets[st["cell"][:k]]]
-    choice = np.arange(k) % 4
+    choice = (np.arange(k) % 4)[:, None]
     st["x"][:, :k] = np.where(choice == 0, P[:, 0], np.where(choice == 1, 0.5 * (P[:, 0] + P[:, 3]),
                               np.where(choice == 2, (P[:, 1] + P[:, 2] + P[:, 3]) / 3, P.mean(1)))).T
     osim.set_state(st)
