@@ -102,6 +102,7 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, D
     S.W = c.take<double>(5 * nc);
     S.prim = c.take<double>(5 * nc);
     S.tau = c.take<double>(nc);
+    S.tauf = c.take<float>(nc);
     S.rhoh = c.take<double>(nc);
     S.rhop = c.take<double>(nc);
     S.nsam = c.take<int32_t>(nc);
@@ -112,12 +113,13 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, D
     S.smass_next = c.take<int64_t>(nc);
     S.cnt = c.take<int32_t>(nc);
     S.off = c.take<int32_t>(nc);
+    S.soff = c.take<int32_t>(nc);
     S.cursor = c.take<int32_t>(nc);
     S.pflux = c.take<int64_t>(5 * nc);
     S.wacc = c.take<int64_t>(5 * nc);
     S.mom = c.take<double>(5 * nc);
     S.F = c.take<double>(5 * nf);
-    S.bsum = c.take<int32_t>((size_t)scan_blocks(mh.nc) + 1);
+    S.bsum = c.take<int2>((size_t)scan_blocks(mh.nc) + 1);
     S.t = c.take<double>(1);
     S.dt = c.take<double>(1);
     S.cnt64 = c.take<int64_t>(CNT_SLOTS);

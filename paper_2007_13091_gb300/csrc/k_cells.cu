@@ -16,27 +16,30 @@ __device__ __forceinline__ void set_err(const DevState& s, int32_t bits) {
     atomicOr(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_ERR]), (unsigned long long)bits);
 }
 
-// Inclusive scan of one int per thread over a block of SCAN_BLOCK threads.
-__device__ __forceinline__ int block_scan_incl(int v, int* sh_warp) {
+// Inclusive scan of two ints per thread (count, N_sam) over one block.
+__device__ __forceinline__ int2 block_scan_incl2(int2 v, int2* sh_warp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const int o = __shfl_up_sync(0xffffffffu, v, d);
-        if (lane >= d) v += o;
+        const int ox = __shfl_up_sync(0xffffffffu, v.x, d);
+        const int oy = __shfl_up_sync(0xffffffffu, v.y, d);
+        if (lane >= d) { v.x += ox; v.y += oy; }
     }
     if (lane == 31) sh_warp[warp] = v;
     __syncthreads();
     if (warp == 0) {
-        int w = (lane < (int)(blockDim.x >> 5)) ? sh_warp[lane] : 0;
+        int2 w = (lane < (int)(blockDim.x >> 5)) ? sh_warp[lane] : make_int2(0, 0);
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const int o = __shfl_up_sync(0xffffffffu, w, d);
-            if (lane >= d) w += o;
+            const int ox = __shfl_up_sync(0xffffffffu, w.x, d);
+            const int oy = __shfl_up_sync(0xffffffffu, w.y, d);
+            if (lane >= d) { w.x += ox; w.y += oy; }
         }
         sh_warp[lane] = w;
     }
     __syncthreads();
-    return v + (warp > 0 ? sh_warp[warp - 1] : 0);
+    if (warp > 0) { v.x += sh_warp[warp - 1].x; v.y += sh_warp[warp - 1].y; }
+    return v;
 }
 
 __global__ void k_reset(DevMesh m, DevState s) {
@@ -91,6 +94,7 @@ __global__ void k_cell_prep(DevMesh m, DevState s, DevParams p) {
         s.prim[3 * nc + i] = Uz;
         s.prim[4 * nc + i] = T;
         s.tau[i] = tau;
+        s.tauf[i] = (float)tau;
         s.rhop[i] = rhop;
         s.rhoh[i] = rho - rhop;
     }
@@ -115,11 +119,11 @@ __global__ void k_cell_prep(DevMesh m, DevState s, DevParams p) {
 // m_sam = rho^hp |Omega| / N_sam (Sec. 2.4 (b)).  Also the per-block sums of
 // the next buffer's per-cell counts.
 __global__ void k_sample_count(DevMesh m, DevState s, DevParams p) {
-    __shared__ int shw[32];
+    __shared__ int2 shw[32];
     const int nc = m.nc;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const double dt = p.CFL * __longlong_as_double(s.cnt64[CNT_DT_BITS]);
-    int count = 0;
+    int count = 0, nsam = 0;
     if (i < nc) {
         const double vol = m.vol[i];
         const double ex = dm::d_exp(-(dt / s.tau[i]));
@@ -142,46 +146,55 @@ __global__ void k_sample_count(DevMesh m, DevState s, DevParams p) {
         }
         s.nsam[i] = (int)ns;
         s.msam[i] = ms;
-        count = s.nleft[i] + (int)ns;
+        nsam = (int)ns;
+        count = s.nleft[i] + nsam;
         s.cnt[i] = count;
     }
-    const int incl = block_scan_incl(count, shw);
+    const int2 incl = block_scan_incl2(make_int2(count, nsam), shw);
     if (threadIdx.x == blockDim.x - 1) s.bsum[blockIdx.x] = incl;
     if (i == 0) s.dt[0] = dt;
 }
 
-// Exclusive scan of the block sums (one block), the total and the capacity check.
+// Exclusive scan of the block sums (one block): totals of the next buffer and
+// of the sampled particles, and the capacity check.
 __global__ void k_scan_bsum(DevState s, DevParams p, int nb) {
-    __shared__ int shw[32];
-    __shared__ long long carry_sh;
-    if (threadIdx.x == 0) carry_sh = 0;
+    __shared__ int2 shw[32];
+    __shared__ long long carry_sh[2];
+    if (threadIdx.x == 0) { carry_sh[0] = 0; carry_sh[1] = 0; }
     __syncthreads();
     for (int base = 0; base < nb; base += blockDim.x) {
         const int j = base + threadIdx.x;
-        const int v = j < nb ? s.bsum[j] : 0;
-        const int incl = block_scan_incl(v, shw);
-        const long long carry = carry_sh;
-        if (j < nb) s.bsum[j] = (int)(carry + incl - v);
+        const int2 v = j < nb ? s.bsum[j] : make_int2(0, 0);
+        const int2 incl = block_scan_incl2(v, shw);
+        const long long c0 = carry_sh[0], c1 = carry_sh[1];
+        if (j < nb) s.bsum[j] = make_int2((int)(c0 + incl.x - v.x), (int)(c1 + incl.y - v.y));
         __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry_sh = carry + incl;
+        if (threadIdx.x == blockDim.x - 1) { carry_sh[0] = c0 + incl.x; carry_sh[1] = c1 + incl.y; }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const long long total = carry_sh;
+        const long long total = carry_sh[0];
         s.cnt64[CNT_N_B] = total;
+        s.cnt64[CNT_NSAM] = carry_sh[1];
+        s.cnt64[CNT_SAMPLED] = carry_sh[1];
         if (total > p.capacity) {
             set_err(s, ERRB_CAPACITY);
             s.cnt64[CNT_N_B] = 0;
+            s.cnt64[CNT_NSAM] = 0;
         }
     }
 }
 
 __global__ void k_scan_apply(DevMesh m, DevState s) {
-    __shared__ int shw[32];
+    __shared__ int2 shw[32];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int v = i < m.nc ? s.cnt[i] : 0;
-    const int incl = block_scan_incl(v, shw);
-    if (i < m.nc) s.off[i] = s.bsum[blockIdx.x] + incl - v;
+    const int2 v = i < m.nc ? make_int2(s.cnt[i], s.nsam[i]) : make_int2(0, 0);
+    const int2 incl = block_scan_incl2(v, shw);
+    if (i < m.nc) {
+        const int2 b = s.bsum[blockIdx.x];
+        s.off[i] = b.x + incl.x - v.x;
+        s.soff[i] = b.y + incl.y - v.y;
+    }
 }
 
 // a10: W^{n+1} = W^n - 1/|Omega| sum_k (+-F_k |S_k|) + F^{fr,p}/|Omega|, faces

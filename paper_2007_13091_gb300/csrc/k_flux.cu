@@ -77,6 +77,9 @@ __device__ __forceinline__ void flux_moments(double Un, const double* Ut, const 
 __device__ __forceinline__ void time_coeffs(double dt, double tau, double& q1, double& q4, double& a4) {
     const double x = dt / tau;
     if (x < 1.0) {
+        // terms x^k/k! with coefficients growing like k: stop once k term falls
+        // below 2^-60 of x^2 (the smallest leading term, of q1 and a4)
+        const double stop = x * x * 0x1p-60;
         double term = 1.0, s1 = 0.0, s4 = 0.0, sa = 0.0;
 #pragma unroll 1
         for (int k = 1; k <= 30; ++k) {
@@ -85,6 +88,7 @@ __device__ __forceinline__ void time_coeffs(double dt, double tau, double& q1, d
             if (k >= 2) s1 += sg * term;
             s4 += -sg * term;
             if (k >= 2) sa += -sg * (double)(1 - k) * term;
+            if (k >= 3 && term * (double)k < stop) break;
         }
         q1 = tau * s1;
         q4 = tau * s4;

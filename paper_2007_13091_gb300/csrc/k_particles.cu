@@ -75,26 +75,22 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
     if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
     const PartView<Real> b = view<Real>(br);
     const int nc = m.nc;
-    const int cell = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (cell >= nc) return;
-    const int ns = s.nsam[cell];
-    if (ns == 0) return;
+    const long long total = s.cnt64[CNT_NSAM];
     const long long step = s.cnt64[CNT_STEP];
-    const double ms = s.msam[cell];
-    const double U[3] = {s.prim[nc + cell], s.prim[2 * nc + cell], s.prim[3 * nc + cell]};
-    const double sig = sqrt(p.R * s.prim[4 * nc + cell]);
-    double P0[3], E1[3], E2[3], E3[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        P0[c] = m.vtx[(size_t)c * nc + cell];
-        E1[c] = m.vtx[(size_t)(3 + c) * nc + cell] - P0[c];
-        E2[c] = m.vtx[(size_t)(6 + c) * nc + cell] - P0[c];
-        E3[c] = m.vtx[(size_t)(9 + c) * nc + cell] - P0[c];
-    }
-    const long long first = (long long)s.off[cell] + s.nleft[cell];
-    for (int k = lane; k < ns; k += 32) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        // owning cell: the last c with soff[c] <= g (cells with N_sam = 0 share
+        // the offset of the next cell and are never the last such c)
+        int lo = 0, hi = nc;  // invariant: soff[lo] <= g < soff[hi] (soff[nc] = +inf)
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s.soff[mid] <= g) lo = mid; else hi = mid;
+        }
+        const int cell = lo;
+        const int k = (int)(g - s.soff[cell]);
         const int side = k & 1;
+        const double U[3] = {s.prim[nc + cell], s.prim[2 * nc + cell], s.prim[3 * nc + cell]};
+        const double sig = sqrt(p.R * s.prim[4 * nc + cell]);
         const unsigned long long ida = make_id(step, cell, k - side);
         const dm::U4 r = dm::philox(ida, (unsigned long long)step, TAG_SVEL, 0ULL, p.seed, 0ULL);
         double sn, cs, X[3];
@@ -119,17 +115,20 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
             cc = a + bb + cc - 1.0;
             a = 1.0 - bb - t;
         }
-        const long long j = first + k;
+        const long long j = (long long)s.off[cell] + s.nleft[cell] + k;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            b.x[c][j] = (Real)(P0[c] + ((a * E1[c] + bb * E2[c]) + cc * E3[c]));
+            const double P0 = m.vtx[(size_t)c * nc + cell];
+            const double E1 = m.vtx[(size_t)(3 + c) * nc + cell] - P0;
+            const double E2 = m.vtx[(size_t)(6 + c) * nc + cell] - P0;
+            const double E3 = m.vtx[(size_t)(9 + c) * nc + cell] - P0;
+            b.x[c][j] = (Real)(P0 + ((a * E1 + bb * E2) + cc * E3));
             b.u[c][j] = (Real)(side == 0 ? U[c] + sig * X[c] : U[c] - sig * X[c]);
         }
-        b.m[j] = ms;
+        b.m[j] = s.msam[cell];
         b.cell[j] = cell;
         b.id[j] = id;
     }
-    if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_SAMPLED]), (unsigned long long)ns);
 }
 
 // ------------------------------------------------------------------ tracking
@@ -144,8 +143,9 @@ template <> struct Trk<float> {
         const int4 v = m.trk_f[tet].nb;
         return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
     }
-    __device__ static __forceinline__ float tf(double tau, unsigned long long r) {
-        return -((float)tau * dm::f_log(dm::u01f(r)));
+    __device__ static __forceinline__ float tau(const DevState& s, int c) { return s.tauf[c]; }
+    __device__ static __forceinline__ float tf(float tau, unsigned long long r) {
+        return -(tau * dm::f_log(dm::u01f(r)));
     }
 };
 template <> struct Trk<double> {
@@ -158,6 +158,7 @@ template <> struct Trk<double> {
         const int4 v = m.trk_d[tet].nb;
         return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
     }
+    __device__ static __forceinline__ double tau(const DevState& s, int c) { return s.tau[c]; }
     __device__ static __forceinline__ double tf(double tau, unsigned long long r) {
         return -(tau * dm::d_log(dm::u01d(r)));
     }
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(256) k_track(DevMesh m, DevState s, DevParams 
             bool coll = false;
             if ((long long)(id >> 40) != step) {
                 const dm::U4 r = dm::philox(id, (unsigned long long)step, TAG_TF, 0ULL, p.seed, 0ULL);
-                const Real tf = Trk<Real>::tf(s.tau[c0], r.a);
+                const Real tf = Trk<Real>::tf(Trk<Real>::tau(s, c0), r.a);
                 if (tf < dtR) { coll = true; t_end = tf; }
             }
             // ---- face-by-face walk along x0 + u (t - t0)
@@ -298,11 +299,11 @@ __global__ void __launch_bounds__(256) k_track(DevMesh m, DevState s, DevParams 
             // ---- particle flux by counting: -phi at the start cell, +phi at the end
             // cell; a particle that ends in its start cell with its velocity unchanged
             // contributes nothing and is skipped.
-            long long q0[5], q1[5];
-            bool ok = phi_q(us, mm, p, q0);
-            ok &= phi_q(u, mm, p, q1);
-            if (!ok) set_err(s, ERRB_FIXED_OVERFLOW);
             if (exited || tet != c0 || nrefl > 0) {
+                long long q0[5], q1[5];
+                bool ok = phi_q(us, mm, p, q0);
+                ok &= phi_q(u, mm, p, q1);
+                if (!ok) set_err(s, ERRB_FIXED_OVERFLOW);
 #pragma unroll
                 for (int q = 0; q < 5; ++q)
                     atomicAdd(reinterpret_cast<unsigned long long*>(&s.pflux[(size_t)q * nc + c0]),
@@ -314,7 +315,11 @@ __global__ void __launch_bounds__(256) k_track(DevMesh m, DevState s, DevParams 
                                   (unsigned long long)q1[q]);
                 }
             }
-            qmass = q1[0];
+            if (survivor) {
+                const double v = mm * p.qinv[0];
+                if (!(fabs(v) < 0x1p62)) set_err(s, ERRB_FIXED_OVERFLOW);
+                qmass = __double2ll_rn(v);
+            }
             // ---- write back
             if (survivor) {
 #pragma unroll
@@ -381,9 +386,9 @@ void launch_scatter(const DevMesh& m, const DevState& s, const DevParams& p, con
 
 void launch_sample_write(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b,
                          cudaStream_t st) {
-    const int blocks = (m.nc + 7) / 8;
-    if (p.precision == UGKWP_MIXED) k_sample_write<float><<<blocks, 256, 0, st>>>(m, s, p, b);
-    else k_sample_write<double><<<blocks, 256, 0, st>>>(m, s, p, b);
+    (void)m;
+    if (p.precision == UGKWP_MIXED) k_sample_write<float><<<particle_grid(), 256, 0, st>>>(m, s, p, b);
+    else k_sample_write<double><<<particle_grid(), 256, 0, st>>>(m, s, p, b);
 }
 
 void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b, cudaStream_t st) {

@@ -36,6 +36,7 @@ enum : int {
     CNT_DT_BITS = 11,   // min_i |Omega_i| / sum Lambda as ordered bits (positive double)
     CNT_ERR = 12,       // error bits
     CNT_MOVES = 13,     // particle moves since init (never reset by a step)
+    CNT_NSAM = 14,      // particles sampled this step (from the scan)
     CNT_SLOTS = 16,
 };
 
@@ -112,6 +113,7 @@ struct DevState {
     double* W;            // [5][nc]
     double* prim;         // [5][nc] rho, Ux, Uy, Uz, T
     double* tau;          // [nc]
+    float* tauf;          // [nc] binary32 rounding of tau (MIXED t_f draw)
     double* rhoh;         // [nc]
     double* rhop;         // [nc]
     int32_t* nsam;        // [nc]
@@ -122,12 +124,13 @@ struct DevState {
     int64_t* smass_next;  // [nc]
     int32_t* cnt;         // [nc] particles per cell after sampling
     int32_t* off;         // [nc] first slot of the cell in the next buffer
+    int32_t* soff;        // [nc] exclusive scan of N_sam (sampled-particle index)
     int32_t* cursor;      // [nc]
     int64_t* pflux;       // [5][nc] fixed-point particle flux
     int64_t* wacc;        // [5][nc] fixed-point scratch for W^p
     double* mom;          // [5][nc] staging of moments copied to the host
     double* F;            // [5][nf]
-    int32_t* bsum;        // [n_scan_blocks]
+    int2* bsum;           // [n_scan_blocks] block sums of (count, N_sam)
     double* t;            // [1]
     double* dt;           // [1]
     int64_t* cnt64;       // [CNT_SLOTS]
