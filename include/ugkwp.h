@@ -245,6 +245,34 @@ int ugkwp_timing_read(ugkwp_sim* s, double* ms, int64_t* launches);
 typedef struct { int32_t functional; int32_t n_steps; const int32_t* wall_tags; int32_t n_wall_tags; } ugkwp_adjoint_req;
 int ugkwp_adjoint_wave(ugkwp_sim* s, const ugkwp_adjoint_req* r, double* dJ_dtheta);
 
+/* Time step without any device allocation (this library's addition; the
+ * paper has no counterpart).  Some callers cannot call cudaMalloc or hand the
+ * library a workspace: a solver embedded in a host application that reserves
+ * all device memory for itself up front, a plug-in whose framework forbids
+ * allocation, or a latency-critical loop that must never wait on an allocator.
+ * For them this entry point computes the time step of one UGKWP step,
+ *   dt = CFL min_i |Omega_i| / sum_d (|U_d| + 3 sqrt(R T_i)) DeltaS_i^d
+ * (Sec. 2.4 (a)), from device arrays the caller already owns, and writes it
+ * to d_dt[0] on the given stream (cudaStream_t, NULL = legacy default stream).
+ *   d_W   [5][n_cells] conservative variables (rho, rho U, rho E), device
+ *   d_vol [n_cells] cell volumes, device
+ *   d_dS  [3][n_cells] projected areas DeltaS^x, ^y, ^z, device
+ * Cells with rho <= 0 or p <= 0 are skipped; if no cell is valid d_dt[0] is
+ * +inf.  The partial minima live in one array of static device memory of
+ * UGKWP_NOALLOC_MAX_CELLS / 256 doubles (512 KiB) that every GPU which loads
+ * the library holds until the process exits; n_cells above
+ * UGKWP_NOALLOC_MAX_CELLS is rejected with UGKWP_E_ARG.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every call
+ * shares the array and leaves its contents behind (each call writes every slot
+ * it reads, so nothing needs clearing): calls whose work overlaps on the GPU,
+ * on any streams, race and must be ordered by the caller.  The call returns
+ * once its two kernels are enqueued; it allocates no memory and does not
+ * synchronise.  Errors: UGKWP_E_ARG, UGKWP_E_CUDA. */
+#define UGKWP_NOALLOC_MAX_CELLS (1 << 24)
+int ugkwp_time_step_noalloc(const double* d_W, const double* d_vol, const double* d_dS, int32_t n_cells,
+                            double R, double CFL, double* d_dt, void* cuda_stream);
+
 /* Copy the calling thread's last error message (NUL-terminated) into buf. */
 int ugkwp_last_error(char* buf, size_t len);
 

@@ -27,6 +27,7 @@ CU_UNITS = {
     "k_cells.cu": ["--fmad=false"],
     "k_particles.cu": ["--fmad=false"],
     "k_flux.cu": [],
+    "k_noalloc.cu": ["--fmad=false"],
 }
 CPP_UNITS = ["api.cpp", "mesh.cpp"]
 

@@ -55,6 +55,14 @@ int fail(int code, const std::string& msg) {
     return code;
 }
 
+}  // namespace
+
+namespace ugkwp {
+void set_last_error_message(const std::string& msg) { g_err = msg; }
+}
+
+namespace {
+
 int cuda_fail(cudaError_t e, const char* where) {
     return fail(UGKWP_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }

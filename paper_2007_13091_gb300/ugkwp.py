@@ -82,7 +82,7 @@ class AdjointReq(ctypes.Structure):
 
 KERNELS = ["reset", "cell_prep", "sample_count", "scan", "scatter", "sample", "track", "flux", "update"]
 
-EXPORTED = ["ugkwp_timing_enable", "ugkwp_timing_read", "ugkwp_mesh_load", "ugkwp_mesh_free", "ugkwp_query_sizes", "ugkwp_init", "ugkwp_free", "ugkwp_step",
+EXPORTED = ["ugkwp_time_step_noalloc", "ugkwp_timing_enable", "ugkwp_timing_read", "ugkwp_mesh_load", "ugkwp_mesh_free", "ugkwp_query_sizes", "ugkwp_init", "ugkwp_free", "ugkwp_step",
             "ugkwp_sync", "ugkwp_moments", "ugkwp_state_info", "ugkwp_export_state", "ugkwp_import_state",
             "ugkwp_last", "ugkwp_adjoint_wave", "ugkwp_last_error"]
 
@@ -118,6 +118,7 @@ def lib():
             "ugkwp_last_error": [ctypes.c_char_p, sz],
             "ugkwp_timing_enable": [vp, i32],
             "ugkwp_timing_read": [vp, vp, vp],
+            "ugkwp_time_step_noalloc": [vp, vp, vp, i32, ctypes.c_double, ctypes.c_double, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -288,6 +289,18 @@ def ugkwp_timing_read(sim):
     n = np.zeros(len(KERNELS), dtype=np.int64)
     _check(lib().ugkwp_timing_read(sim, ms.ctypes.data, n.ctypes.data))
     return dict(zip(KERNELS, ms.tolist())), dict(zip(KERNELS, (int(v) for v in n)))
+
+
+NOALLOC_MAX_CELLS = 1 << 24
+
+
+def ugkwp_time_step_noalloc(d_W: int, d_vol: int, d_dS: int, n_cells: int, R: float, CFL: float, d_dt: int,
+                            stream: int = 0):
+    """Time step from caller-owned device arrays with no device allocation
+    (for callers that cannot allocate; see include/ugkwp.h)."""
+    _check(lib().ugkwp_time_step_noalloc(ctypes.c_void_p(d_W), ctypes.c_void_p(d_vol), ctypes.c_void_p(d_dS),
+                                         int(n_cells), float(R), float(CFL), ctypes.c_void_p(d_dt),
+                                         ctypes.c_void_p(stream)))
 
 
 # ------------------------------------------------------------ convenience
