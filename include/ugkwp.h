@@ -191,8 +191,10 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0,
 int ugkwp_free(ugkwp_sim* s);
 
 /* Advance n_steps time steps (Sec. 2.2 procedure, Eq. update_macro_variables),
- * asynchronously on the bound stream.  If st is non-NULL the call waits for
- * the stream, fills st and returns any device-side error. */
+ * asynchronously on the bound stream.  Within each step the wave flux runs on
+ * a second, library-owned stream forked from and joined back into the bound
+ * stream, so the caller sees one stream-ordered step.  If st is non-NULL the
+ * call waits for the stream, fills st and returns any device-side error. */
 int ugkwp_step(ugkwp_sim* s, int32_t n_steps, ugkwp_stats* st);
 
 /* Wait for the stream and return (then clear) any device-side error. */
@@ -225,7 +227,7 @@ int ugkwp_last(ugkwp_sim* s, int32_t which, void* host_out);
 /* Kernel classes of one step, in launch order (for ugkwp_timing_read). */
 enum {
     UGKWP_K_RESET = 0, UGKWP_K_CELL_PREP, UGKWP_K_SAMPLE_COUNT, UGKWP_K_SCAN, UGKWP_K_SCATTER,
-    UGKWP_K_SAMPLE, UGKWP_K_TRACK, UGKWP_K_FLUX, UGKWP_K_UPDATE, UGKWP_N_KERNELS
+    UGKWP_K_SAMPLE, UGKWP_K_TRACK, UGKWP_K_FLUX, UGKWP_K_UPDATE, UGKWP_K_MOVERS, UGKWP_N_KERNELS
 };
 
 /* Per-kernel timing with CUDA events recorded on the bound stream around each

@@ -40,9 +40,15 @@ struct ugkwp_sim {
     int64_t launches[UGKWP_N_KERNELS] = {};
     std::vector<TimedLaunch> pending;
     std::vector<cudaEvent_t> pool;
+    // the wave flux (binary64-bound) runs beside the particle kernels
+    cudaStream_t wave = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     ~ugkwp_sim() {
         for (auto& t : pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
         for (auto e : pool) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (wave) cudaStreamDestroy(wave);
     }
 };
 
@@ -415,6 +421,9 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     if (ce == cudaSuccess) ce = cudaMemsetAsync(s->S.t, 0, sizeof(double), st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(s->S.dt, 0, sizeof(double), st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s->wave, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming);
     if (ce != cudaSuccess) {
         delete s;
         return cuda_fail(ce, "ugkwp_init upload");
@@ -443,17 +452,17 @@ cudaEvent_t take_event(ugkwp_sim* s) {
     return e;
 }
 
-// Launch one kernel class, bracketed by events when timing is enabled.
-template <class F> void timed(ugkwp_sim* s, int k, int n_kernels, F&& launch) {
+// Launch one kernel class on stream q, bracketed by events when timing is enabled.
+template <class F> void timed(ugkwp_sim* s, int k, int n_kernels, cudaStream_t q, F&& launch) {
     s->launches[k] += n_kernels;
     if (!s->timing) {
         launch();
         return;
     }
     TimedLaunch t{k, take_event(s), take_event(s)};
-    cudaEventRecord(t.a, s->stream);
+    cudaEventRecord(t.a, q);
     launch();
-    cudaEventRecord(t.b, s->stream);
+    cudaEventRecord(t.b, q);
     s->pending.push_back(t);
 }
 }  // namespace
@@ -490,15 +499,22 @@ int ugkwp_step(ugkwp_sim* s, int32_t n_steps, ugkwp_stats* st) {
     cudaStream_t q = s->stream;
     for (int32_t k = 0; k < n_steps; ++k) {
         if (s->step >= ((int64_t)1 << 24) - 1) return fail(UGKWP_E_STATE, "step counter exhausted (2^24 steps)");
-        timed(s, UGKWP_K_RESET, 1, [&] { launch_reset(s->M, s->S, q); });
-        timed(s, UGKWP_K_CELL_PREP, 1, [&] { launch_cell_prep(s->M, s->S, s->P, q); });
-        timed(s, UGKWP_K_SAMPLE_COUNT, 1, [&] { launch_sample_count(s->M, s->S, s->P, q); });
-        timed(s, UGKWP_K_SCAN, 2, [&] { launch_scan(s->M, s->S, s->P, q); });
-        timed(s, UGKWP_K_SCATTER, 1, [&] { launch_scatter(s->M, s->S, s->P, s->A, s->B, q); });
-        timed(s, UGKWP_K_SAMPLE, 1, [&] { launch_sample_write(s->M, s->S, s->P, s->B, q); });
-        timed(s, UGKWP_K_TRACK, 1, [&] { launch_track(s->M, s->S, s->P, s->B, q); });
-        timed(s, UGKWP_K_FLUX, 1, [&] { launch_face_flux(s->M, s->S, s->P, q); });
-        timed(s, UGKWP_K_UPDATE, 1, [&] { launch_cell_update(s->M, s->S, s->P, q); });
+        timed(s, UGKWP_K_RESET, 1, q, [&] { launch_reset(s->M, s->S, q); });
+        timed(s, UGKWP_K_CELL_PREP, 1, q, [&] { launch_cell_prep(s->M, s->S, s->P, q); });
+        timed(s, UGKWP_K_SAMPLE_COUNT, 1, q, [&] { launch_sample_count(s->M, s->S, s->P, q); });
+        // fork: the wave flux needs only W^n, rho^h, tau and dt (ready now) and
+        // writes only F, which no particle kernel touches
+        CU(cudaEventRecord(s->fork, q));
+        CU(cudaStreamWaitEvent(s->wave, s->fork, 0));
+        timed(s, UGKWP_K_FLUX, 1, s->wave, [&] { launch_face_flux(s->M, s->S, s->P, s->wave); });
+        CU(cudaEventRecord(s->join, s->wave));
+        timed(s, UGKWP_K_SCAN, 2, q, [&] { launch_scan(s->M, s->S, s->P, q); });
+        timed(s, UGKWP_K_SCATTER, 1, q, [&] { launch_scatter(s->M, s->S, s->P, s->A, s->B, q); });
+        timed(s, UGKWP_K_SAMPLE, 1, q, [&] { launch_sample_write(s->M, s->S, s->P, s->B, q); });
+        timed(s, UGKWP_K_TRACK, 1, q, [&] { launch_track(s->M, s->S, s->P, s->B, s->A, q); });
+        timed(s, UGKWP_K_MOVERS, 1, q, [&] { launch_movers(s->M, s->S, s->P, s->A, q); });
+        CU(cudaStreamWaitEvent(q, s->join, 0));  // join before the update reads F
+        timed(s, UGKWP_K_UPDATE, 1, q, [&] { launch_cell_update(s->M, s->S, s->P, q); });
         std::swap(s->A, s->B);
         std::swap(s->S.nleft, s->S.nleft_next);
         std::swap(s->S.smass, s->S.smass_next);

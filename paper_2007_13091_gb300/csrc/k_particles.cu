@@ -179,10 +179,43 @@ __device__ __forceinline__ bool phi_q(const Real* u, double mm, const DevParams&
     return ok;
 }
 
+// round-to-nearest-even of m 2^-e for a finite m >= 0, computed on the bits of
+// m with integer operations only (m 2^-e is an exact exponent shift, so this
+// equals rounding the binary64 product); false if the result is >= 2^62.
+__device__ __forceinline__ bool fixed_of_mass(double m, int e, long long& q) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    unsigned long long mant = bits & 0x000fffffffffffffULL;
+    int s;  // value = mant 2^s
+    if (ex == 0) {
+        s = 1 - 1075 - e;
+    } else {
+        mant |= 0x0010000000000000ULL;
+        s = ex - 1075 - e;
+    }
+    if (ex == 0x7ff || (bits >> 63)) { q = 0; return false; }
+    if (s >= 0) {
+        if (mant == 0) { q = 0; return true; }
+        if (s > 9) { q = 0; return false; }  // mant < 2^53: 2^(53+s) > 2^62
+        const unsigned long long v = mant << s;
+        if (v >= (1ULL << 62)) { q = 0; return false; }
+        q = (long long)v;
+        return true;
+    }
+    const int r = -s;
+    if (r > 63) { q = 0; return true; }
+    const unsigned long long hi = mant >> r;
+    const unsigned long long rem = mant & ((1ULL << r) - 1ULL);
+    const unsigned long long half = 1ULL << (r - 1);
+    q = (long long)(hi + ((rem > half || (rem == half && (hi & 1ULL))) ? 1ULL : 0ULL));
+    return true;
+}
+
 template <class Real>
-__global__ void __launch_bounds__(256) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br) {
+__global__ void __launch_bounds__(256) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br, PartBufRaw ar) {
     if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
     const PartView<Real> b = view<Real>(br);
+    const PartView<Real> mv = view<Real>(ar);  // mover list: x = u at start, u = u at end
     const long long n = s.cnt64[CNT_N_B];
     const long long step = s.cnt64[CNT_STEP];
     const double dt = s.dt[0];
@@ -196,15 +229,18 @@ __global__ void __launch_bounds__(256) k_track(DevMesh m, DevState s, DevParams 
         int status = 0, ncross = 0, nrefl = 0, nwall = 0;
         int c0 = -1, tet = -1;
         long long qmass = 0;
-        bool survivor = false;
+        bool survivor = false, mover = false, exited = false;
+        Real us[3] = {(Real)0, (Real)0, (Real)0}, ue[3] = {(Real)0, (Real)0, (Real)0};
+        double mm = 0.0;
         if (valid) {
             const unsigned long long id = b.id[i];
             c0 = b.cell[i];
             Real x0[3], u[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) { x0[c] = b.x[c][i]; u[c] = b.u[c][i]; }
-            const double mm = b.m[i];
-            const Real us[3] = {u[0], u[1], u[2]};
+            mm = b.m[i];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) us[c] = u[c];
             Real t_end = dtR;
             bool coll = false;
             if ((long long)(id >> 40) != step) {
@@ -292,34 +328,17 @@ __global__ void __launch_bounds__(256) k_track(DevMesh m, DevState s, DevParams 
                 t0 = t0 + sbest;
                 last = best;
             }
-            const bool exited = status & 2;
+            exited = status & 2;
             const bool lost = status & 4;
             survivor = !exited && (!coll || lost);
             if (coll && !lost && !exited) status |= 1;
             // ---- particle flux by counting: -phi at the start cell, +phi at the end
             // cell; a particle that ends in its start cell with its velocity unchanged
             // contributes nothing and is skipped.
-            if (exited || tet != c0 || nrefl > 0) {
-                long long q0[5], q1[5];
-                bool ok = phi_q(us, mm, p, q0);
-                ok &= phi_q(u, mm, p, q1);
-                if (!ok) set_err(s, ERRB_FIXED_OVERFLOW);
+            mover = exited || tet != c0 || nrefl > 0;
 #pragma unroll
-                for (int q = 0; q < 5; ++q)
-                    atomicAdd(reinterpret_cast<unsigned long long*>(&s.pflux[(size_t)q * nc + c0]),
-                              (unsigned long long)(-q0[q]));
-                if (!exited) {
-#pragma unroll
-                    for (int q = 0; q < 5; ++q)
-                        atomicAdd(reinterpret_cast<unsigned long long*>(&s.pflux[(size_t)q * nc + tet]),
-                                  (unsigned long long)q1[q]);
-                }
-            }
-            if (survivor) {
-                const double v = mm * p.qinv[0];
-                if (!(fabs(v) < 0x1p62)) set_err(s, ERRB_FIXED_OVERFLOW);
-                qmass = __double2ll_rn(v);
-            }
+            for (int c = 0; c < 3; ++c) ue[c] = u[c];
+            if (survivor && !fixed_of_mass(mm, p.exps[0], qmass)) set_err(s, ERRB_FIXED_OVERFLOW);
             // ---- write back
             if (survivor) {
 #pragma unroll
@@ -351,6 +370,25 @@ __global__ void __launch_bounds__(256) k_track(DevMesh m, DevState s, DevParams 
             atomicAdd(&s.nleft_next[key], lane - start + 1);
             atomicAdd(reinterpret_cast<unsigned long long*>(&s.smass_next[key]), (unsigned long long)v);
         }
+        // ---- movers: compact list (warp-aggregated append) for the flux pass
+        const unsigned mmask = __ballot_sync(FULL, mover);
+        if (mmask) {
+            int base0 = 0;
+            if (lane == 0) base0 = (int)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_MOVERS]),
+                                                  (unsigned long long)__popc(mmask));
+            base0 = __shfl_sync(FULL, base0, 0);
+            if (mover) {
+                const long long j = base0 + __popc(mmask & ((1u << lane) - 1u));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    mv.x[c][j] = us[c];
+                    mv.u[c][j] = ue[c];
+                }
+                mv.m[j] = mm;
+                mv.cell[j] = c0;
+                mv.id[j] = ((unsigned long long)(unsigned)tet << 1) | (exited ? 1ULL : 0ULL);
+            }
+        }
         // ---- counters
         const unsigned n_surv = __popc(__ballot_sync(FULL, survivor));
         const unsigned n_valid = __popc(__ballot_sync(FULL, valid));
@@ -375,6 +413,39 @@ __global__ void __launch_bounds__(256) k_track(DevMesh m, DevState s, DevParams 
     }
 }
 
+// Counting flux of the listed movers: -phi(u_start) at the start cell and, unless
+// the particle left the domain, +phi(u_end) at the end cell (full warps of
+// binary64 work, kept out of the tracking kernel).
+template <class Real>
+__global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams p, PartBufRaw ar) {
+    if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
+    const PartView<Real> mv = view<Real>(ar);
+    const long long n = s.cnt64[CNT_MOVERS];
+    const int nc = m.nc;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const Real us[3] = {mv.x[0][j], mv.x[1][j], mv.x[2][j]};
+        const Real ue[3] = {mv.u[0][j], mv.u[1][j], mv.u[2][j]};
+        const double mm = mv.m[j];
+        const int c0 = mv.cell[j];
+        const unsigned long long code = mv.id[j];
+        const int c1 = (int)(code >> 1);
+        const bool exited = code & 1ULL;
+        long long q0[5], q1[5];
+        bool ok = phi_q(us, mm, p, q0);
+        ok &= phi_q(ue, mm, p, q1);
+        if (!ok) set_err(s, ERRB_FIXED_OVERFLOW);
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&s.pflux[(size_t)q * nc + c0]), (unsigned long long)(-q0[q]));
+        if (!exited) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q)
+                atomicAdd(reinterpret_cast<unsigned long long*>(&s.pflux[(size_t)q * nc + c1]), (unsigned long long)q1[q]);
+        }
+    }
+}
+
 }  // namespace
 
 void launch_scatter(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
@@ -391,9 +462,15 @@ void launch_sample_write(const DevMesh& m, const DevState& s, const DevParams& p
     else k_sample_write<double><<<particle_grid(), 256, 0, st>>>(m, s, p, b);
 }
 
-void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b, cudaStream_t st) {
-    if (p.precision == UGKWP_MIXED) k_track<float><<<particle_grid(), 256, 0, st>>>(m, s, p, b);
-    else k_track<double><<<particle_grid(), 256, 0, st>>>(m, s, p, b);
+void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b, const PartBufRaw& a,
+                  cudaStream_t st) {
+    if (p.precision == UGKWP_MIXED) k_track<float><<<particle_grid(), 256, 0, st>>>(m, s, p, b, a);
+    else k_track<double><<<particle_grid(), 256, 0, st>>>(m, s, p, b, a);
+}
+
+void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a, cudaStream_t st) {
+    if (p.precision == UGKWP_MIXED) k_movers<float><<<particle_grid(), 256, 0, st>>>(m, s, p, a);
+    else k_movers<double><<<particle_grid(), 256, 0, st>>>(m, s, p, a);
 }
 
 }  // namespace ugkwp

@@ -37,6 +37,7 @@ enum : int {
     CNT_ERR = 12,       // error bits
     CNT_MOVES = 13,     // particle moves since init (never reset by a step)
     CNT_NSAM = 14,      // particles sampled this step (from the scan)
+    CNT_MOVERS = 15,    // particles whose flux contribution is non-zero this step
     CNT_SLOTS = 16,
 };
 
@@ -161,8 +162,12 @@ void launch_scatter(const DevMesh& m, const DevState& s, const DevParams& p, con
                     const PartBufRaw& b, cudaStream_t st);
 void launch_sample_write(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b,
                          cudaStream_t st);
+// Tracking of buffer b; particles whose counting flux is non-zero are listed
+// in buffer a (free after the scatter) and their flux added by launch_movers.
 void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b,
-                  cudaStream_t st);
+                  const PartBufRaw& a, cudaStream_t st);
+void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
+                   cudaStream_t st);
 void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_rebuild_survivors(const DevMesh& m, const DevState& s, const DevParams& p,
