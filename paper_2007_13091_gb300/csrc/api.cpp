@@ -105,6 +105,7 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, D
     M.trk_d = nullptr;
     if (rs == 4) M.trk_f = c.take<TrkF>(nc);
     else M.trk_d = c.take<TrkD>(nc);
+    M.face_order = c.take<int32_t>(nf);
     M.f_own = c.take<int32_t>(nf);
     M.f_nbr = c.take<int32_t>(nf);
     M.f_n = c.take<double>(3 * nf);
@@ -359,6 +360,14 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
         for (int d = 0; d < 3; ++d) fn[(size_t)d * nf + f] = mh.f_n[3 * (size_t)f + d];
         fnb[f] = mh.f_nbr[f] >= 0 ? mh.f_nbr[f] : -1 - mh.bf_of_face[f];
     }
+    // flux work order: interior faces, then boundary faces grouped by type
+    std::vector<int32_t> forder;
+    forder.reserve(nf);
+    for (int f = 0; f < nf; ++f)
+        if (mh.f_nbr[f] >= 0) forder.push_back(f);
+    for (int type = 1; type <= 4; ++type)
+        for (int f = 0; f < nf; ++f)
+            if (mh.f_nbr[f] < 0 && p->bc[mh.f_tag[f]].type == type) forder.push_back(f);
     for (int b = 0; b < nbf; ++b) {
         const int f = mh.face_of_bf[b];
         btag[b] = mh.f_tag[f];
@@ -405,6 +414,7 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     UP(s->M.cfs, cfs.data(), cfs.size() * sizeof(int32_t));
     if (s->real_size == 4) { UP(s->M.trk_f, tf.data(), tf.size() * sizeof(TrkF)); }
     else { UP(s->M.trk_d, td.data(), td.size() * sizeof(TrkD)); }
+    UP(s->M.face_order, forder.data(), nf * sizeof(int32_t));
     UP(s->M.f_own, mh.f_own.data(), nf * sizeof(int32_t));
     UP(s->M.f_nbr, fnb.data(), nf * sizeof(int32_t));
     UP(s->M.f_n, fn.data(), fn.size() * sizeof(double));

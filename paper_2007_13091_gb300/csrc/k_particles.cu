@@ -212,7 +212,7 @@ __device__ __forceinline__ bool fixed_of_mass(double m, int e, long long& q) {
 }
 
 template <class Real>
-__global__ void __launch_bounds__(256) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br, PartBufRaw ar) {
+__global__ void __launch_bounds__(256, 3) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br, PartBufRaw ar) {
     if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
     const PartView<Real> b = view<Real>(br);
     const PartView<Real> mv = view<Real>(ar);  // mover list: x = u at start, u = u at end
@@ -220,11 +220,16 @@ __global__ void __launch_bounds__(256) k_track(DevMesh m, DevState s, DevParams 
     const long long step = s.cnt64[CNT_STEP];
     const double dt = s.dt[0];
     const Real dtR = (Real)dt;
-    const int nc = m.nc;
-    const int lane = threadIdx.x & 31;
-    const long long wstride = (long long)gridDim.x * blockDim.x;
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += wstride) {
-        const long long i = base + lane;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ int sh_cnt[8];
+    __shared__ long long sh_base;
+    __shared__ unsigned long long sh_red[8][8];
+    // per-thread counters, reduced once per block at the end
+    unsigned c_surv = 0, c_valid = 0, c_coll = 0, c_exit = 0, c_lost = 0, c_cross = 0, c_wall = 0;
+    const long long bstride = (long long)gridDim.x * blockDim.x;
+    // block-uniform loop: every warp of the block runs the same iterations
+    for (long long bb = (long long)blockIdx.x * blockDim.x; bb < n; bb += bstride) {
+        const long long i = bb + threadIdx.x;
         const bool valid = i < n;
         int status = 0, ncross = 0, nrefl = 0, nwall = 0;
         int c0 = -1, tet = -1;
@@ -332,9 +337,9 @@ __global__ void __launch_bounds__(256) k_track(DevMesh m, DevState s, DevParams 
             const bool lost = status & 4;
             survivor = !exited && (!coll || lost);
             if (coll && !lost && !exited) status |= 1;
-            // ---- particle flux by counting: -phi at the start cell, +phi at the end
-            // cell; a particle that ends in its start cell with its velocity unchanged
-            // contributes nothing and is skipped.
+            // ---- particle flux by counting: a particle that ends in its start
+            // cell with its velocity unchanged contributes nothing; the others
+            // are listed for the binary64 flux pass
             mover = exited || tet != c0 || nrefl > 0;
 #pragma unroll
             for (int c = 0; c < 3; ++c) ue[c] = u[c];
@@ -351,6 +356,13 @@ __global__ void __launch_bounds__(256) k_track(DevMesh m, DevState s, DevParams 
             } else {
                 b.cell[i] = -1;
             }
+            c_valid += 1;
+            c_surv += survivor;
+            c_coll += status & 1;
+            c_exit += (status >> 1) & 1;
+            c_lost += (status >> 2) & 1;
+            c_cross += ncross;
+            c_wall += nwall;
         }
         // ---- survivors per end cell (count, fixed-point mass): segmented
         // reduction over lanes with equal keys in a row, one atomic per run
@@ -370,45 +382,47 @@ __global__ void __launch_bounds__(256) k_track(DevMesh m, DevState s, DevParams 
             atomicAdd(&s.nleft_next[key], lane - start + 1);
             atomicAdd(reinterpret_cast<unsigned long long*>(&s.smass_next[key]), (unsigned long long)v);
         }
-        // ---- movers: compact list (warp-aggregated append) for the flux pass
+        // ---- movers: one slot reservation per block and iteration
         const unsigned mmask = __ballot_sync(FULL, mover);
-        if (mmask) {
-            int base0 = 0;
-            if (lane == 0) base0 = (int)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_MOVERS]),
-                                                  (unsigned long long)__popc(mmask));
-            base0 = __shfl_sync(FULL, base0, 0);
-            if (mover) {
-                const long long j = base0 + __popc(mmask & ((1u << lane) - 1u));
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    mv.x[c][j] = us[c];
-                    mv.u[c][j] = ue[c];
-                }
-                mv.m[j] = mm;
-                mv.cell[j] = c0;
-                mv.id[j] = ((unsigned long long)(unsigned)tet << 1) | (exited ? 1ULL : 0ULL);
-            }
+        if (lane == 0) sh_cnt[warp] = __popc(mmask);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { const int c = sh_cnt[w]; sh_cnt[w] = tot; tot += c; }
+            sh_base = tot ? (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_MOVERS]),
+                                                 (unsigned long long)tot)
+                          : 0LL;
         }
-        // ---- counters
-        const unsigned n_surv = __popc(__ballot_sync(FULL, survivor));
-        const unsigned n_valid = __popc(__ballot_sync(FULL, valid));
-        const unsigned n_coll = __popc(__ballot_sync(FULL, status & 1));
-        const unsigned n_exit = __popc(__ballot_sync(FULL, status & 2));
-        const unsigned n_lost = __popc(__ballot_sync(FULL, status & 4));
-        const unsigned n_x = __reduce_add_sync(FULL, (unsigned)ncross);
-        const unsigned n_w = __reduce_add_sync(FULL, (unsigned)nwall);
-        if (lane == 0) {
-            atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_ALIVE]), (unsigned long long)n_surv);
-            atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_TRACKED]), (unsigned long long)n_valid);
-            atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_MOVES]), (unsigned long long)n_valid);
-            if (n_coll) atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_COLLIDED]), (unsigned long long)n_coll);
-            if (n_exit) atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_EXITED]), (unsigned long long)n_exit);
-            if (n_lost) {
-                atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_LOST]), (unsigned long long)n_lost);
-                set_err(s, ERRB_TRACK_LIMIT);
+        __syncthreads();
+        if (mover) {
+            const long long j = sh_base + sh_cnt[warp] + __popc(mmask & ((1u << lane) - 1u));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                mv.x[c][j] = us[c];
+                mv.u[c][j] = ue[c];
             }
-            if (n_x) atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_CROSSINGS]), (unsigned long long)n_x);
-            if (n_w) atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_WALL]), (unsigned long long)n_w);
+            mv.m[j] = mm;
+            mv.cell[j] = c0;
+            mv.id[j] = ((unsigned long long)(unsigned)tet << 1) | (exited ? 1ULL : 0ULL);
+        }
+        __syncthreads();  // sh_cnt / sh_base are reused next iteration
+    }
+    // ---- counters: one atomic per block and counter
+    unsigned vals[7] = {c_surv, c_valid, c_coll, c_exit, c_lost, c_cross, c_wall};
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const unsigned w = __reduce_add_sync(FULL, vals[k]);
+        if (lane == 0) sh_red[warp][k] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh_red[w][threadIdx.x];
+        const int slot[7] = {CNT_ALIVE, CNT_TRACKED, CNT_COLLIDED, CNT_EXITED, CNT_LOST, CNT_CROSSINGS, CNT_WALL};
+        if (t) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[slot[threadIdx.x]]), t);
+            if (threadIdx.x == 1) atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_MOVES]), t);
+            if (threadIdx.x == 4) set_err(s, ERRB_TRACK_LIMIT);
         }
     }
 }

@@ -84,6 +84,7 @@ struct DevMesh {
     const int32_t* cfs;      // [nc] bit k set if the cell owns local face k
     const TrkF* trk_f;       // [nc]
     const TrkD* trk_d;       // [nc]
+    const int32_t* face_order;  // [nf] interior faces, then boundary faces grouped by type
     const int32_t* f_own;    // [nf]
     const int32_t* f_nbr;    // [nf] >= 0 tet, else -1 - boundary index
     const double* f_n;       // [3][nf]
