@@ -43,7 +43,19 @@ struct ugkwp_sim {
     // the wave flux (binary64-bound) runs beside the particle kernels
     cudaStream_t wave = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    // two-step CUDA graphs, one per ping-pong parity (keyed by buffer A)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    void* graph_key[2] = {nullptr, nullptr};
+    bool graphs_ok = true;
+    void drop_graphs() {
+        for (int k = 0; k < 2; ++k) {
+            if (graph[k]) cudaGraphExecDestroy(graph[k]);
+            graph[k] = nullptr;
+            graph_key[k] = nullptr;
+        }
+    }
     ~ugkwp_sim() {
+        drop_graphs();
         for (auto& t : pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
         for (auto e : pool) cudaEventDestroy(e);
         if (fork) cudaEventDestroy(fork);
@@ -504,11 +516,14 @@ int ugkwp_timing_read(ugkwp_sim* s, double* ms, int64_t* launches) {
     return UGKWP_OK;
 }
 
-int ugkwp_step(ugkwp_sim* s, int32_t n_steps, ugkwp_stats* st) {
-    if (!s || n_steps < 0) return fail(UGKWP_E_ARG, "invalid argument");
+}  // extern "C"
+
+namespace {
+// Enqueue the kernels of one step on the bound stream (the wave flux forked
+// onto the library's second stream) and swap the ping-pong buffers.
+int enqueue_step(ugkwp_sim* s) {
     cudaStream_t q = s->stream;
-    for (int32_t k = 0; k < n_steps; ++k) {
-        if (s->step >= ((int64_t)1 << 24) - 1) return fail(UGKWP_E_STATE, "step counter exhausted (2^24 steps)");
+    {
         timed(s, UGKWP_K_RESET, 1, q, [&] { launch_reset(s->M, s->S, q); });
         timed(s, UGKWP_K_CELL_PREP, 1, q, [&] { launch_cell_prep(s->M, s->S, s->P, q); });
         timed(s, UGKWP_K_SAMPLE_COUNT, 1, q, [&] { launch_sample_count(s->M, s->S, s->P, q); });
@@ -528,7 +543,77 @@ int ugkwp_step(ugkwp_sim* s, int32_t n_steps, ugkwp_stats* st) {
         std::swap(s->A, s->B);
         std::swap(s->S.nleft, s->S.nleft_next);
         std::swap(s->S.smass, s->S.smass_next);
+    }
+    return UGKWP_OK;
+}
+
+// Two steps as one CUDA graph for the current parity (captured on first use).
+int launch_step_pair(ugkwp_sim* s, bool& used) {
+    used = false;
+    if (!s->graphs_ok || s->timing || s->stream == nullptr) return UGKWP_OK;
+    void* key = s->A.x[0];
+    int slot = s->graph_key[0] == key ? 0 : s->graph_key[1] == key ? 1 : -1;
+    if (slot < 0) {
+        slot = s->graph[0] ? 1 : 0;
+        if (s->graph[slot]) { cudaGraphExecDestroy(s->graph[slot]); s->graph[slot] = nullptr; }
+        int64_t saved[UGKWP_N_KERNELS];
+        std::memcpy(saved, s->launches, sizeof(saved));
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            s->graphs_ok = false;
+            return UGKWP_OK;
+        }
+        int rc = enqueue_step(s);
+        if (rc == UGKWP_OK) rc = enqueue_step(s);
+        cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+        std::memcpy(s->launches, saved, sizeof(saved));
+        if (rc != UGKWP_OK || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            s->graphs_ok = false;
+            return UGKWP_OK;
+        }
+        e = cudaGraphInstantiate(&s->graph[slot], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s->graph[slot] = nullptr;
+            s->graphs_ok = false;
+            return UGKWP_OK;
+        }
+        s->graph_key[slot] = key;
+    }
+    CU(cudaGraphLaunch(s->graph[slot], s->stream));
+    // the graph holds two steps of every kernel class
+    int64_t per_step[UGKWP_N_KERNELS] = {1, 1, 1, 2, 1, 1, 1, 1, 1, 1};
+    for (int k = 0; k < UGKWP_N_KERNELS; ++k) s->launches[k] += 2 * per_step[k];
+    used = true;
+    return UGKWP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int ugkwp_step(ugkwp_sim* s, int32_t n_steps, ugkwp_stats* st) {
+    if (!s || n_steps < 0) return fail(UGKWP_E_ARG, "invalid argument");
+    cudaStream_t q = s->stream;
+    for (int32_t k = 0; k < n_steps;) {
+        if (s->step >= ((int64_t)1 << 24) - 2) return fail(UGKWP_E_STATE, "step counter exhausted (2^24 steps)");
+        if (n_steps - k >= 2) {
+            bool used = false;
+            int rc = launch_step_pair(s, used);
+            if (rc) return rc;
+            if (used) {
+                s->step += 2;
+                k += 2;
+                continue;
+            }
+        }
+        int rc = enqueue_step(s);
+        if (rc) return rc;
         s->step += 1;
+        k += 1;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -701,6 +786,7 @@ int ugkwp_import_state(ugkwp_sim* s, const ugkwp_state* st) {
     CU(cudaMemsetAsync(s->S.nleft, 0, nc * sizeof(int32_t), q));
     CU(cudaMemsetAsync(s->S.smass, 0, nc * sizeof(int64_t), q));
     set_exps(s->P, st->exps);
+    s->drop_graphs();  // the graphs carry the parameters by value
     launch_rebuild_survivors(s->M, s->S, s->P, s->A, q);
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(q));
