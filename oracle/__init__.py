@@ -60,6 +60,9 @@ def lib():
         L.orc_set_state.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, d, cp, i32]
         L.orc_last.argtypes = [vp, ctypes.c_int, vp]
         L.orc_track_one.argtypes = [vp, u64, i32, vp, vp, d, d, i64, vp, vp]
+        L.orc_prepare.argtypes = [vp, cp, i32]
+        L.orc_sample_cell.argtypes = [vp, i32, i64, vp, vp, vp, vp]
+        L.orc_sample_cell.restype = i64
         _LIB = L
     return _LIB
 
@@ -250,6 +253,24 @@ class OracleSim:
             keys = ["n_tracked", "n_collided", "n_exited", "n_lost", "n_crossings", "n_wall_hits", "n_sampled"]
             return dict(zip(keys, (int(v) for v in out)))
         return out
+
+    def prepare(self):
+        """Primitives, tau, rho^h, dt and sampling counts of the current state
+        (readable through last()), without stepping."""
+        err = ctypes.create_string_buffer(512)
+        rc = lib().orc_prepare(self._h, err, 512)
+        if rc:
+            raise RuntimeError(f"oracle prepare failed ({rc}): {err.value.decode()}")
+
+    def sample_cell(self, cell):
+        """The particles `cell` samples at the current step (after prepare())."""
+        n = lib().orc_sample_cell(self._h, int(cell), 0, None, None, None, None)
+        pid = np.empty(n, dtype=np.uint64)
+        x = np.empty((n, 3))
+        u = np.empty((n, 3))
+        m = np.empty(n)
+        lib().orc_sample_cell(self._h, int(cell), n, _ptr(pid), _ptr(x), _ptr(u), _ptr(m))
+        return {"id": pid, "x": x.T.copy(), "u": u.T.copy(), "m": m}
 
     def track_one(self, pid, cell, x, u, tau_cell, dt, step):
         io_x = np.ascontiguousarray(x, dtype=np.float64).copy()

@@ -500,6 +500,8 @@ struct SimBase {
     virtual ~SimBase() {}
     virtual int64_t n_particles() const = 0;
     virtual int do_step(std::string& err) = 0;
+    virtual int prepare(std::string& err) = 0;
+    virtual int64_t sample_one_cell(int cell, int64_t cap, uint64_t* id, double* x, double* u, double* m) const = 0;
     virtual void get_particles(uint64_t*, int32_t*, double*, double*, double*) const = 0;
     virtual bool set_particles(int64_t, const uint64_t*, const int32_t*, const double*, const double*,
                                const double*, std::string&) = 0;
@@ -512,20 +514,27 @@ template <class Real> struct Sim : SimBase {
 
     int64_t n_particles() const override { return (int64_t)parts.size(); }
 
-    int do_step(std::string& err) override {
-        const int nc = g.nc, nf = g.nf;
+    // per-cell quantities of the current state (a1, a2, a5 counts)
+    std::vector<Prim> pr;
+    std::vector<double> rho_p;
+    std::vector<int64_t> nleft;
+
+    // a1 + a2 + sampling counts for the current state; no state change.
+    int prepare(std::string& err) override {
+        const int nc = g.nc;
         const orc_params& p = P;
         // ---- a1: primitives and relaxation time; W^h density = W - W^p (Sec. 2.2)
-        std::vector<Prim> pr(nc);
+        pr.assign(nc, Prim());
         tau.assign(nc, 0.0); rhoh.assign(nc, 0.0);
-        std::vector<int64_t> mass_q(nc, 0), nleft(nc, 0);
+        std::vector<int64_t> mass_q(nc, 0);
+        nleft.assign(nc, 0);
         for (const auto& pt : parts) {
             int64_t q[5];
             phi_fixed(pt, e, q);
             mass_q[pt.cell] += q[0];
             nleft[pt.cell] += 1;
         }
-        std::vector<double> rho_p(nc);
+        rho_p.assign(nc, 0.0);
         for (int i = 0; i < nc; ++i) {
             double Wi[5];
             for (int k = 0; k < 5; ++k) Wi[k] = W[(size_t)k * nc + i];
@@ -548,12 +557,8 @@ template <class Real> struct Sim : SimBase {
             if (r < rmin) rmin = r;
         }
         dt = p.CFL * rmin;
-        // ---- a5: sample the collisionless part of the hydrodynamic wave
-        // (Sec. 2.4 (b)): rho^hp = e^{-dt/tau} rho^h, m_ref, N_sam, m_sam; pairs
-        // u = U +/- sqrt(RT) X, X ~ N(0, I); x uniform in the tet.
+        // ---- a5 counts (Sec. 2.4 (b)): rho^hp = e^{-dt/tau} rho^h, m_ref, N_sam, m_sam
         nsam.assign(nc, 0); msam.assign(nc, 0.0);
-        const size_t n_old = parts.size();
-        int64_t n_sampled = 0;
         for (int i = 0; i < nc; ++i) {
             double ex = exp_d(-(dt / tau[i]));
             double rh = rhoh[i] > 0.0 ? rhoh[i] : 0.0;  // reading: clamp noise-negative rho^h
@@ -565,12 +570,22 @@ template <class Real> struct Sim : SimBase {
             int64_t need = (int64_t)p.N_min - nleft[i];
             if (need > ns) ns = need + (need & 1);
             if (ns > 65534) { err = "more than 65534 particles sampled in one cell"; return -6; }
-            double ms = Mhp / (double)ns;
-            nsam[i] = ns; msam[i] = ms;
-            double sig = std::sqrt(p.R * pr[i].T);
-            const double *p0 = &g.xyz[3 * (size_t)g.tet[4 * i]], *p1 = &g.xyz[3 * (size_t)g.tet[4 * i + 1]];
-            const double *p2 = &g.xyz[3 * (size_t)g.tet[4 * i + 2]], *p3 = &g.xyz[3 * (size_t)g.tet[4 * i + 3]];
-            for (int64_t j = 0; j < ns / 2; ++j) {
+            nsam[i] = ns;
+            msam[i] = Mhp / (double)ns;
+        }
+        return 0;
+    }
+
+    // a5: the N_sam particles of cell i, in pairs u = U +/- sqrt(RT) X with
+    // X ~ N(0, I) (Box-Muller), x uniform in the tet (needs prepare()).
+    void sample_cell(int i, std::vector<Part<Real>>& out) const {
+        const orc_params& p = P;
+        const int64_t ns = nsam[i];
+        const double ms = msam[i];
+        double sig = std::sqrt(p.R * pr[i].T);
+        const double *p0 = &g.xyz[3 * (size_t)g.tet[4 * i]], *p1 = &g.xyz[3 * (size_t)g.tet[4 * i + 1]];
+        const double *p2 = &g.xyz[3 * (size_t)g.tet[4 * i + 2]], *p3 = &g.xyz[3 * (size_t)g.tet[4 * i + 3]];
+        for (int64_t j = 0; j < ns / 2; ++j) {
                 uint64_t ida = make_id((uint64_t)step, (uint64_t)i, (uint64_t)(2 * j));
                 Ctr4 r = draw(p.seed, ida, (uint64_t)step, TAG_SVEL, 0);
                 double X[3], sn, cs;
@@ -598,10 +613,23 @@ template <class Real> struct Sim : SimBase {
                         double e1 = p1[c] - p0[c], e2 = p2[c] - p0[c], e3 = p3[c] - p0[c];
                         pt.x[c] = (Real)(p0[c] + ((a * e1 + b * e2) + cc * e3));
                     }
-                    parts.push_back(pt);
+                    out.push_back(pt);
                 }
-            }
-            n_sampled += ns;
+        }
+    }
+
+    int do_step(std::string& err) override {
+        const int nc = g.nc, nf = g.nf;
+        const orc_params& p = P;
+        int prc = prepare(err);
+        if (prc) return prc;
+        // ---- a5: sample the collisionless part of the hydrodynamic wave
+        const size_t n_old = parts.size();
+        int64_t n_sampled = 0;
+        for (int i = 0; i < nc; ++i) {
+            if (!nsam[i]) continue;
+            sample_cell(i, parts);
+            n_sampled += nsam[i];
         }
         // ---- a6..a9: free-transport time (Eq. t_f), streaming, counting flux
         // F^{fr,p}_i = sum_{end in i} phi - sum_{start in i} phi (Sec. 2.3),
@@ -679,6 +707,18 @@ template <class Real> struct Sim : SimBase {
         if (overflow) { err = "fixed-point overflow"; return -8; }
         if (nlost) { err = std::to_string(nlost) + " particles exceeded max_crossings"; return -7; }
         return 0;
+    }
+
+    int64_t sample_one_cell(int cell, int64_t cap, uint64_t* id, double* x, double* u, double* m) const override {
+        std::vector<Part<Real>> v;
+        sample_cell(cell, v);
+        const int64_t n = (int64_t)v.size();
+        for (int64_t k = 0; k < n && k < cap; ++k) {
+            id[k] = v[k].id;
+            m[k] = v[k].m;
+            for (int c = 0; c < 3; ++c) { x[3 * k + c] = (double)v[k].x[c]; u[3 * k + c] = (double)v[k].u[c]; }
+        }
+        return n;
     }
 
     void get_particles(uint64_t* id, int32_t* cell, double* x, double* u, double* m) const override {
@@ -923,6 +963,18 @@ int orc_last(const orc_sim* h, int which, void* out) {
         case 9: std::memcpy(out, s->counters, sizeof(s->counters)); return 0;
         default: return -1;
     }
+}
+
+int orc_prepare(orc_sim* h, char* err, int32_t errlen) {
+    std::string e;
+    int rc = h->s->prepare(e);
+    if (rc) set_err(err, errlen, e);
+    return rc;
+}
+
+int64_t orc_sample_cell(const orc_sim* h, int32_t cell, int64_t cap, uint64_t* id, double* x, double* u, double* m) {
+    if (cell < 0 || cell >= h->s->g.nc) return -1;
+    return h->s->sample_one_cell(cell, cap, id, x, u, m);
 }
 
 int orc_track_one(const orc_sim* h, uint64_t id, int32_t cell, double* io_x, double* io_u,

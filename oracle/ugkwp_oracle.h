@@ -88,6 +88,13 @@ int orc_set_state(orc_sim* s, const double* W, int64_t n, const uint64_t* id,
  *  n_crossings, n_wall_hits, n_sampled] */
 int orc_last(const orc_sim* s, int which, void* out);
 
+/* Cell preparation of the current state without stepping: primitives, tau,
+ * rho^h, dt and the sampling counts (then readable with orc_last 0..4). */
+int orc_prepare(orc_sim* s, char* err, int32_t errlen);
+/* The particles cell `cell` samples at the current step (after orc_prepare):
+ * returns their number n and fills up to cap of them (x, u as [k][3]). */
+int64_t orc_sample_cell(const orc_sim* s, int32_t cell, int64_t cap, uint64_t* id, double* x, double* u, double* m);
+
 /* Track one particle with the simulation's mesh and parameters (sampled checks
  * at sizes where a whole oracle step would be slow).  io_x/io_u are [3];
  * the particle precision follows the simulation.  Returns the status bits

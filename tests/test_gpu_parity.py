@@ -154,7 +154,12 @@ def test_no_particles_regime():
     for _ in range(3):
         osim.step()
         gsim.step()
-    assert gsim.state()["id"].size == 0
+        assert gsim.state()["id"].size == 0
+        for q in range(5):
+            assert _rel_l2(gsim.state()["W"][q], osim.state()["W"][q]) <= TOL
+    gsim.set_state(osim.state())
+    osim.step()
+    gsim.step()
     compare_step(gsim, osim)
 
 
@@ -254,3 +259,20 @@ def test_graph_replay_matches_direct_launches():
     a, b = s_graph.state(), s_direct.state()
     np.testing.assert_array_equal(a["W"], b["W"])
     assert_particles_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["mixed"])
+def test_cavity_full_size_teacher_forced(precision):
+    """The bench workload at full size (24^3 x 6 = 82,944 tets, ~8.4e6 particles)
+    on a side stream as the bench runs it: one step from the oracle's state
+    after its sampling step (graph replay equals direct launches, tested above)."""
+    import torch
+    cfg = wl.cavity(n=24, N_ref=100, precision=precision)
+    osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    osim.step(1)
+    gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], stream=torch.cuda.Stream())
+    gsim.set_state(osim.state())
+    osim.step(1)
+    gsim.step(1)
+    compare_step(gsim, osim)
+    assert osim.sizes()["n_particles"] > 8_000_000
