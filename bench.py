@@ -38,6 +38,10 @@ UNIT = "particle-moves/s"
 TRACK_BYTES_PER_MOVE = {"mixed": 44 + 16, "fp64": 68 + 28}
 # per cell and step: tracking record (planes + neighbours) and tau
 TRACK_BYTES_PER_CELL = {"mixed": 80 + 8, "fp64": 144 + 8}
+# DRAM bytes (read + write) of one k_track launch on this workload, from the ncu
+# capture summarised in profiles/k_track_k_face_flux_cavity24_mixed.md; set to
+# None whenever the kernel changes until it is captured again
+TRACK_DRAM_BYTES = {"mixed": 401.257728e6 + 130.182144e6, "fp64": None}
 
 
 def peaks():
@@ -336,7 +340,9 @@ def main():
            "cell_steps_per_s": cell_steps,
            "roofline": {"kernel": "k_track (a6-a9: t_f draw, tet walk, fixed-point flux, removal)", "bound": "hbm",
                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "peak_kind": f"{peak_kind} HBM copy", "traffic": None,
+                        "peak_kind": f"{peak_kind} HBM copy", "traffic": TRACK_DRAM_BYTES[args.precision],
+                        "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                        "algorithmic_bytes_per_launch": alg,
                         "bytes_per_move": TRACK_BYTES_PER_MOVE[args.precision],
                         "bytes_per_cell": TRACK_BYTES_PER_CELL[args.precision], "ms_per_launch": track_ms,
                         "timing": "CUDA events on the library's stream around each k_track launch over "
