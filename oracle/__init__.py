@@ -27,7 +27,7 @@ class OrcBc(ctypes.Structure):
 class OrcParams(ctypes.Structure):
     _fields_ = [("R", ctypes.c_double), ("mu_ref", ctypes.c_double), ("T_ref", ctypes.c_double),
                 ("omega", ctypes.c_double), ("CFL", ctypes.c_double), ("C2", ctypes.c_double),
-                ("order", ctypes.c_int32), ("N_ref", ctypes.c_int32), ("N_min", ctypes.c_int32),
+                ("venkat_K", ctypes.c_double), ("order", ctypes.c_int32), ("N_ref", ctypes.c_int32), ("N_min", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("max_crossings", ctypes.c_int32),
                 ("n_bc", ctypes.c_int32), ("seed", ctypes.c_uint64), ("bc", OrcBc * 16)]
 
@@ -61,6 +61,10 @@ def lib():
         L.orc_last.argtypes = [vp, ctypes.c_int, vp]
         L.orc_track_one.argtypes = [vp, u64, i32, vp, vp, d, d, i64, vp, vp]
         L.orc_prepare.argtypes = [vp, cp, i32]
+        L.orc_gradients.argtypes = [vp, ctypes.c_int, vp, vp]
+        L.orc_slope_moment.argtypes = [vp, d, ctypes.c_int, vp, ctypes.c_int, vp]
+        L.orc_micro_slope.argtypes = [vp, d, vp, vp]
+        L.orc_face_flux_o2.argtypes = [P(OrcParams), vp, d, vp, vp, vp, vp, d, vp, vp, vp, vp, d, vp]
         L.orc_sample_cell.argtypes = [vp, i32, i64, vp, vp, vp, vp]
         L.orc_sample_cell.restype = i64
         _LIB = L
@@ -86,6 +90,7 @@ def make_params(p: dict) -> OrcParams:
     o = OrcParams()
     for k in ("R", "mu_ref", "T_ref", "omega", "CFL", "C2"):
         setattr(o, k, float(p[k]))
+    o.venkat_K = float(p.get("venkat_K", 5.0))
     o.order = int(p.get("order", 1))
     o.N_ref = int(p["N_ref"])
     o.N_min = int(p.get("N_min", 0))
@@ -153,6 +158,35 @@ def face_flux(params: dict, kind: str, WL, rhohL, WR, rhohR, n, dt, tau_wall=0.0
                              ctypes.byref(bcs) if bcs is not None else None, _ptr(F))
     if rc:
         raise ValueError("orc_face_flux failed")
+    return F
+
+
+def slope_moment(U, lam, half, a, d):
+    """int u_n u_d (a . psi) psi g du for a unit-density Maxwellian in a face
+    frame (components of U and a along n, t1, t2)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    out = np.empty(5)
+    lib().orc_slope_moment(_ptr(U), float(lam), int(half), _ptr(a), int(d), _ptr(out))
+    return out
+
+
+def micro_slope(U, lam, b):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    a = np.empty(5)
+    lib().orc_micro_slope(_ptr(U), float(lam), _ptr(b), _ptr(a))
+    return a
+
+
+def face_flux_o2(params, WL, rhohL, gWL, gHL, dxL, WR, rhohR, gWR, gHR, dxR, n, dt):
+    """Second-order flux of one interior face; gW are [5][3] gradients."""
+    P = make_params(params)
+    arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (WL, gWL, gHL, dxL, WR, gWR, gHR, dxR, n)]
+    F = np.empty(5)
+    lib().orc_face_flux_o2(ctypes.byref(P), _ptr(arrs[0]), float(rhohL), _ptr(arrs[1]), _ptr(arrs[2]),
+                           _ptr(arrs[3]), _ptr(arrs[4]), float(rhohR), _ptr(arrs[5]), _ptr(arrs[6]),
+                           _ptr(arrs[7]), _ptr(arrs[8]), float(dt), _ptr(F))
     return F
 
 
@@ -271,6 +305,17 @@ class OracleSim:
         m = np.empty(n)
         lib().orc_sample_cell(self._h, int(cell), n, _ptr(pid), _ptr(x), _ptr(u), _ptr(m))
         return {"id": pid, "x": x.T.copy(), "u": u.T.copy(), "m": m}
+
+    def gradients(self, limited=True):
+        """Least-squares gradients of W [5, 3, nc] and rho^h [3, nc] of the current
+        state (limited with Venkatakrishnan's limiter if `limited`)."""
+        nc = self.sizes()["n_cells"]
+        gW = np.empty((5, 3, nc))
+        gH = np.empty((3, nc))
+        rc = lib().orc_gradients(self._h, 1 if limited else 0, _ptr(gW), _ptr(gH))
+        if rc:
+            raise RuntimeError("oracle gradients failed")
+        return gW, gH
 
     def track_one(self, pid, cell, x, u, tau_cell, dt, step):
         io_x = np.ascontiguousarray(x, dtype=np.float64).copy()

@@ -363,6 +363,349 @@ static void boundary_flux(const double* WL, double rhohL, double tauL, const orc
     interior_flux(L, Rg, true, n, dt, P, F);
 }
 
+// ------------------------------------------------ second-order reconstruction
+// Least-squares gradients with Venkatakrishnan's limiter (Sec. 2.1).  Readings:
+// inverse-distance-squared weights over the 4 face neighbours; at boundary faces
+// a ghost at the mirror image of the centroid across the face holding the
+// ghost state (specular: mirrored velocity; far field: W_in, all hydro; wall
+// and outflow: the cell's own value); epsilon^2 = (K h)^3, h = |Omega|^(1/3).
+
+// Ghost conservative state and rho^h across boundary face with outward n.
+static void ghost_state(const double* Wi, double rhohi, const orc_bc& bc, const double* n, double* Wg, double* rhohg) {
+    for (int q = 0; q < 5; ++q) Wg[q] = Wi[q];
+    *rhohg = rhohi;
+    if (bc.type == ORC_BC_SPECULAR) {
+        double mn = dot3(&Wi[1], n);
+        for (int d = 0; d < 3; ++d) Wg[1 + d] = Wi[1 + d] - 2.0 * mn * n[d];
+    } else if (bc.type == ORC_BC_INFLOW) {
+        for (int q = 0; q < 5; ++q) Wg[q] = bc.W_in[q];
+        *rhohg = bc.W_in[0];
+    }
+}
+
+// Venkatakrishnan's limiter function for an extrapolated difference d2 and the
+// allowed difference d1 (same sign), with epsilon^2 = eps2.
+static double venkat(double d1, double d2, double eps2) {
+    double num = (d1 * d1 + eps2) * d2 + 2.0 * d2 * d2 * d1;
+    double den = d2 * (d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + eps2);
+    return num / den;
+}
+
+// Limited gradients of W (5 x 3, row-major [q][d]) and rho^h (3) of every cell.
+static void limited_gradients(const Geom& g, const orc_params& P, const std::vector<double>& W,
+                              const std::vector<double>& rhoh, bool limit,
+                              std::vector<double>& gradW, std::vector<double>& gradH) {
+    const int nc = g.nc;
+    gradW.assign(15 * (size_t)nc, 0.0);
+    gradH.assign(3 * (size_t)nc, 0.0);
+    for (int i = 0; i < nc; ++i) {
+        const double* xi = &g.cen[3 * (size_t)i];
+        double Wi[5];
+        for (int q = 0; q < 5; ++q) Wi[q] = W[(size_t)q * nc + i];
+        // neighbour (or ghost) positions and values, 6 quantities: W[5], rho^h
+        double dx[4][3], val[4][6], w[4];
+        for (int k = 0; k < 4; ++k) {
+            int f = g.tet_face[4 * i + k];
+            int j = g.tet_sign[4 * i + k] > 0 ? g.f_nbr[f] : g.f_owner[f];
+            if (j >= 0) {
+                for (int d = 0; d < 3; ++d) dx[k][d] = g.cen[3 * (size_t)j + d] - xi[d];
+                for (int q = 0; q < 5; ++q) val[k][q] = W[(size_t)q * nc + j];
+                val[k][5] = rhoh[j];
+            } else {
+                const double* n = &g.f_n[3 * (size_t)f];
+                const double* xf = &g.f_c[3 * (size_t)f];
+                double h = (xf[0] - xi[0]) * n[0] + (xf[1] - xi[1]) * n[1] + (xf[2] - xi[2]) * n[2];
+                for (int d = 0; d < 3; ++d) dx[k][d] = 2.0 * h * n[d];
+                double Wg[5], hg;
+                ghost_state(Wi, rhoh[i], P.bc[g.f_bc[f]], n, Wg, &hg);
+                for (int q = 0; q < 5; ++q) val[k][q] = Wg[q];
+                val[k][5] = hg;
+            }
+            w[k] = 1.0 / dot3(dx[k], dx[k]);
+        }
+        // normal equations A grad = b, A = sum w dx dx^T (3 x 3), solved by
+        // Gaussian elimination with partial pivoting for each quantity
+        double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int k = 0; k < 4; ++k)
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) A[r][c] += w[k] * dx[k][r] * dx[k][c];
+        const double self[6] = {Wi[0], Wi[1], Wi[2], Wi[3], Wi[4], rhoh[i]};
+        double grad[6][3];
+        for (int q = 0; q < 6; ++q) {
+            double M[3][4];
+            for (int r = 0; r < 3; ++r) {
+                for (int c = 0; c < 3; ++c) M[r][c] = A[r][c];
+                double b = 0.0;
+                for (int k = 0; k < 4; ++k) b += w[k] * dx[k][r] * (val[k][q] - self[q]);
+                M[r][3] = b;
+            }
+            for (int c = 0; c < 3; ++c) {
+                int piv = c;
+                for (int r = c + 1; r < 3; ++r) if (std::fabs(M[r][c]) > std::fabs(M[piv][c])) piv = r;
+                for (int cc = 0; cc < 4; ++cc) std::swap(M[c][cc], M[piv][cc]);
+                for (int r = c + 1; r < 3; ++r) {
+                    double fct = M[r][c] / M[c][c];
+                    for (int cc = c; cc < 4; ++cc) M[r][cc] -= fct * M[c][cc];
+                }
+            }
+            for (int r = 2; r >= 0; --r) {
+                double acc = M[r][3];
+                for (int c = r + 1; c < 3; ++c) acc -= M[r][c] * grad[q][c];
+                grad[q][r] = acc / M[r][r];
+            }
+            double phi = 1.0;
+            if (limit) {
+                double vmax = self[q], vmin = self[q];
+                for (int k = 0; k < 4; ++k) { vmax = std::max(vmax, val[k][q]); vmin = std::min(vmin, val[k][q]); }
+                double h = std::cbrt(g.vol[i]);
+                double eps2 = std::pow(P.venkat_K * h, 3.0);
+                for (int k = 0; k < 4; ++k) {
+                    int f = g.tet_face[4 * i + k];
+                    const double* xf = &g.f_c[3 * (size_t)f];
+                    double d2 = grad[q][0] * (xf[0] - xi[0]) + grad[q][1] * (xf[1] - xi[1]) + grad[q][2] * (xf[2] - xi[2]);
+                    double pk = 1.0;
+                    if (d2 > 0.0) pk = venkat(vmax - self[q], d2, eps2);
+                    else if (d2 < 0.0) pk = venkat(vmin - self[q], d2, eps2);
+                    phi = std::min(phi, pk);
+                }
+            }
+            for (int d = 0; d < 3; ++d) {
+                if (q < 5) gradW[15 * (size_t)i + 3 * q + d] = phi * grad[q][d];
+                else gradH[3 * (size_t)i + d] = phi * grad[q][d];
+            }
+        }
+    }
+}
+
+// ---- velocity moments of a unit-density Maxwellian in the face frame
+// (u along n, v along t1, w along t2), by explicit expansion over monomials.
+struct Term { double c; int a, b, e; };
+typedef std::vector<Term> Poly;
+
+struct FrameMom { double n[8], t1[8], t2[8]; };
+
+// <u^k>, k = 0..7, of the normalised 1D Maxwellian (mean m, lambda), over all u
+// (half = 0) or the half line u > 0 (+1) / u < 0 (-1).
+static void moments1d(double m, double lam, int half, double* M) {
+    if (half == 0) { M[0] = 1.0; M[1] = m; }
+    else {
+        double a = std::sqrt(lam) * m;
+        double edge = 0.5 * std::exp(-lam * m * m) / std::sqrt(PI * lam);
+        if (half > 0) { M[0] = 0.5 * std::erfc(-a); M[1] = m * M[0] + edge; }
+        else          { M[0] = 0.5 * std::erfc(a);  M[1] = m * M[0] - edge; }
+    }
+    for (int k = 0; k < 6; ++k) M[k + 2] = m * M[k + 1] + (double)(k + 1) / (2.0 * lam) * M[k];
+}
+
+static FrameMom frame_moments(const double* Uf, double lam, int half) {
+    FrameMom F;
+    moments1d(Uf[0], lam, half, F.n);
+    moments1d(Uf[1], lam, 0, F.t1);
+    moments1d(Uf[2], lam, 0, F.t2);
+    return F;
+}
+
+static double expect(const FrameMom& M, const Poly& P) {
+    double s = 0.0;
+    for (const Term& t : P) s += t.c * M.n[t.a] * M.t1[t.b] * M.t2[t.e];
+    return s;
+}
+
+static Poly mul(const Poly& A, const Poly& B) {
+    Poly C;
+    for (const Term& x : A) for (const Term& y : B) C.push_back(Term{x.c * y.c, x.a + y.a, x.b + y.b, x.e + y.e});
+    return C;
+}
+
+// psi_k in the face frame: 1, u, v, w, (u^2 + v^2 + w^2)/2
+static Poly psi(int k) {
+    switch (k) {
+        case 0: return Poly{{1.0, 0, 0, 0}};
+        case 1: return Poly{{1.0, 1, 0, 0}};
+        case 2: return Poly{{1.0, 0, 1, 0}};
+        case 3: return Poly{{1.0, 0, 0, 1}};
+        default: return Poly{{0.5, 2, 0, 0}, {0.5, 0, 2, 0}, {0.5, 0, 0, 2}};
+    }
+}
+static Poly lin(const double* a) {  // a . psi
+    return Poly{{a[0], 0, 0, 0}, {a[1], 1, 0, 0}, {a[2], 0, 1, 0}, {a[3], 0, 0, 1},
+                {0.5 * a[4], 2, 0, 0}, {0.5 * a[4], 0, 2, 0}, {0.5 * a[4], 0, 0, 2}};
+}
+static Poly coord(int d) { return Poly{{1.0, d == 0 ? 1 : 0, d == 1 ? 1 : 0, d == 2 ? 1 : 0}}; }
+
+// Micro slope a with <psi psi^T> a = b for the unit Maxwellian (Uf, lam):
+// the moment matrix built from moments, solved by Gaussian elimination.
+static void micro_slope(const double* Uf, double lam, const double* b, double* a) {
+    FrameMom M = frame_moments(Uf, lam, 0);
+    double A[5][6];
+    for (int r = 0; r < 5; ++r) {
+        for (int c = 0; c < 5; ++c) A[r][c] = expect(M, mul(psi(r), psi(c)));
+        A[r][5] = b[r];
+    }
+    for (int c = 0; c < 5; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 5; ++r) if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+        for (int cc = 0; cc < 6; ++cc) std::swap(A[c][cc], A[piv][cc]);
+        for (int r = c + 1; r < 5; ++r) {
+            double f = A[r][c] / A[c][c];
+            for (int cc = c; cc < 6; ++cc) A[r][cc] -= f * A[c][cc];
+        }
+    }
+    for (int r = 4; r >= 0; --r) {
+        double acc = A[r][5];
+        for (int c = r + 1; c < 5; ++c) acc -= A[r][c] * a[c];
+        a[r] = acc / A[r][r];
+    }
+}
+
+// Face frame of a face: rows n, t1, t2.
+struct Frame { double r[3][3]; };
+static void to_frame(const Frame& R, const double* v, double* out) {
+    for (int i = 0; i < 3; ++i) out[i] = dot3(R.r[i], v);
+}
+// W (lab) -> W (frame): rotate the momentum components.
+static void state_to_frame(const Frame& R, const double* W, double* Wf) {
+    Wf[0] = W[0]; to_frame(R, &W[1], &Wf[1]); Wf[4] = W[4];
+}
+// gradient [q][d] (lab) -> slopes along the frame directions, momentum rotated:
+// out[dd][q] = d/d(frame dir dd) of the frame-rotated W_q.
+static void grad_to_frame(const Frame& R, const double* gW, double out[3][5]) {
+    for (int dd = 0; dd < 3; ++dd) {
+        double g[5];
+        for (int q = 0; q < 5; ++q) g[q] = dot3(&gW[3 * q], R.r[dd]);  // directional derivative
+        out[dd][0] = g[0];
+        double m[3] = {g[1], g[2], g[3]};
+        to_frame(R, m, &out[dd][1]);
+        out[dd][4] = g[4];
+    }
+}
+
+static Frame frame_of(const double* n) {
+    Frame R;
+    int a = 0;
+    for (int d = 1; d < 3; ++d) if (std::fabs(n[d]) < std::fabs(n[a])) a = d;
+    double ea[3] = {0.0, 0.0, 0.0}; ea[a] = 1.0;
+    double t1[3], t2[3];
+    cross3(ea, n, t1);
+    double l1 = std::sqrt(dot3(t1, t1));
+    for (int d = 0; d < 3; ++d) t1[d] = t1[d] / l1;
+    cross3(n, t1, t2);
+    for (int d = 0; d < 3; ++d) { R.r[0][d] = n[d]; R.r[1][d] = t1[d]; R.r[2][d] = t2[d]; }
+    return R;
+}
+
+static void frame_to_lab(const Frame& R, const double* Ff, double* F) {
+    F[0] = Ff[0];
+    for (int d = 0; d < 3; ++d) F[1 + d] = (Ff[1] * R.r[0][d] + Ff[2] * R.r[1][d]) + Ff[3] * R.r[2][d];
+    F[4] = Ff[4];
+}
+
+struct SideO2 {
+    double W[5];   // frame state at the face
+    double rhoh;
+    double U[3], lam;
+    double dW[3][5];   // frame slopes of W along n, t1, t2
+    double dWh[3][5];  // frame slopes of W^h = (rho^h/rho) W
+};
+
+static bool side_o2(const Frame& R, const double* Wlab, double rhoh, const double* gW, const double* gH,
+                    const double* dx, SideO2& S) {
+    // reconstruct W and rho^h at the face from the cell values and limited gradients
+    double Wface[5];
+    for (int q = 0; q < 5; ++q) Wface[q] = Wlab[q] + dot3(&gW[3 * q], dx);
+    double rh = rhoh + dot3(gH, dx);
+    Prim pr = prim_of(Wface, 1.0);
+    if (!(Wface[0] > 0.0) || !(pr.p > 0.0)) return false;
+    state_to_frame(R, Wface, S.W);
+    S.rhoh = rh;
+    for (int d = 0; d < 3; ++d) S.U[d] = S.W[1 + d] / S.W[0];
+    S.lam = pr.lam;
+    grad_to_frame(R, gW, S.dW);
+    // grad of (rho^h/rho) W = (rho^h/rho) grad W + W grad(rho^h/rho),
+    // grad(rho^h/rho) = (grad rho^h - (rho^h/rho) grad rho) / rho
+    double ratio = rh / S.W[0];
+    double gr[3];
+    for (int d = 0; d < 3; ++d) gr[d] = (dot3(gH, R.r[d]) - ratio * S.dW[d][0]) / S.W[0];
+    for (int d = 0; d < 3; ++d)
+        for (int q = 0; q < 5; ++q) S.dWh[d][q] = ratio * S.dW[d][q] + S.W[q] * gr[d];
+    return true;
+}
+
+static SideO2 side_o1(const Frame& R, const double* Wlab, double rhoh) {
+    SideO2 S;
+    state_to_frame(R, Wlab, S.W);
+    S.rhoh = rhoh;
+    Prim pr = prim_of(Wlab, 1.0);
+    for (int d = 0; d < 3; ++d) S.U[d] = S.W[1 + d] / S.W[0];
+    S.lam = pr.lam;
+    for (int d = 0; d < 3; ++d) for (int q = 0; q < 5; ++q) { S.dW[d][q] = 0.0; S.dWh[d][q] = 0.0; }
+    return S;
+}
+
+// Second-order flux through an interior face (Sec. 2.1, 2.3), in the face frame:
+//   F^eq       = int u_n [q1 g0 + q2 u.g_x + q3 g_t] psi
+//   F^{fr,wave}= int u_n [a4 g0^h + a5 u.g_x^h] psi  (upwind: L for u_n > 0, R for u_n < 0)
+// with g_x from W_x = (grad W_L + grad W_R)/2 (reading), g_t from
+// W_t = -int u.g_x psi, and all slopes solved from the moment system.
+static void interior_flux_o2(const SideO2& L, const SideO2& Rs, const double* pLR, double dt,
+                             const orc_params& P, double Ff[5]) {
+    FrameMom ML = frame_moments(L.U, L.lam, +1), MR = frame_moments(Rs.U, Rs.lam, -1);
+    double W0[5];
+    for (int k = 0; k < 5; ++k) W0[k] = L.W[0] * expect(ML, psi(k)) + Rs.W[0] * expect(MR, psi(k));
+    Prim s0 = prim_of(W0, P.R);  // frame velocity components in s0.U
+    double tau = P.mu_ref * std::pow(s0.T / P.T_ref, P.omega) / s0.p
+               + P.C2 * std::fabs(pLR[0] - pLR[1]) / std::fabs(pLR[0] + pLR[1]) * dt;
+    double q[7];
+    qcoef(dt, tau, q);
+    FrameMom M0 = frame_moments(s0.U, s0.lam, 0);
+    // equilibrium slopes (with the density factor): a_d = M^-1 W_x,d
+    double a0[3][5];
+    for (int d = 0; d < 3; ++d) {
+        double b[5];
+        for (int k = 0; k < 5; ++k) b[k] = 0.5 * (L.dW[d][k] + Rs.dW[d][k]);
+        micro_slope(s0.U, s0.lam, b, a0[d]);
+    }
+    double Wt[5], At[5];
+    for (int k = 0; k < 5; ++k) {
+        double acc = 0.0;
+        for (int d = 0; d < 3; ++d) acc += expect(M0, mul(mul(coord(d), lin(a0[d])), psi(k)));
+        Wt[k] = -acc;
+    }
+    micro_slope(s0.U, s0.lam, Wt, At);
+    // upwind hydrodynamic slopes a^h_d = M_side^-1 grad_d W^h
+    double aL[3][5], aR[3][5];
+    for (int d = 0; d < 3; ++d) {
+        micro_slope(L.U, L.lam, L.dWh[d], aL[d]);
+        micro_slope(Rs.U, Rs.lam, Rs.dWh[d], aR[d]);
+    }
+    const Poly un = coord(0);
+    for (int k = 0; k < 5; ++k) {
+        Poly unpsi = mul(un, psi(k));
+        double feq = q[0] * s0.rho * expect(M0, unpsi) + q[2] * expect(M0, mul(unpsi, lin(At)));
+        for (int d = 0; d < 3; ++d) feq += q[1] * expect(M0, mul(mul(unpsi, coord(d)), lin(a0[d])));
+        double ffr = q[5] * (L.rhoh * expect(ML, unpsi) + Rs.rhoh * expect(MR, unpsi));
+        for (int d = 0; d < 3; ++d) {
+            Poly ud = mul(unpsi, coord(d));
+            ffr += q[6] * (expect(ML, mul(ud, lin(aL[d]))) + expect(MR, mul(ud, lin(aR[d]))));
+        }
+        Ff[k] = feq + ffr;
+    }
+}
+
+// One interior face at second order: reconstruct both sides (first order on a
+// side whose reconstruction is not positive) and evaluate the O2 flux.
+static void face_flux_o2(const Frame& R, const double* WL, double rhohL, const double* gWL, const double* gHL,
+                         const double* dxL, const double* WR, double rhohR, const double* gWR,
+                         const double* gHR, const double* dxR, double dt, const orc_params& P, double F[5]) {
+    SideO2 L, Rs;
+    if (!side_o2(R, WL, rhohL, gWL, gHL, dxL, L)) L = side_o1(R, WL, rhohL);
+    if (!side_o2(R, WR, rhohR, gWR, gHR, dxR, Rs)) Rs = side_o1(R, WR, rhohR);
+    double pLR[2] = {0.5 * L.W[0] / L.lam, 0.5 * Rs.W[0] / Rs.lam};
+    double Ff[5];
+    interior_flux_o2(L, Rs, pLR, dt, P, Ff);
+    frame_to_lab(R, Ff, F);
+}
+
 // ------------------------------------------------------------ particles
 template <class Real> struct Part { uint64_t id; int32_t cell; Real x[3]; Real u[3]; double m; };
 
@@ -671,14 +1014,28 @@ template <class Real> struct Sim : SimBase {
         counters[0] = (int64_t)parts.size(); counters[1] = ncoll; counters[2] = nexit;
         counters[3] = nlost; counters[4] = ncross; counters[5] = nwall; counters[6] = n_sampled;
         parts.swap(kept);
-        // ---- a4: wave flux per face from W^n and rho^{h,n}
+        // ---- a4: wave flux per face from W^n and rho^{h,n}; a3 (order 2):
+        // limited least-squares gradients of W and rho^h
+        std::vector<double> gW, gH;
+        if (p.order == 2) limited_gradients(g, p, W, rhoh, true, gW, gH);
         F.assign(5 * (size_t)nf, 0.0);
         for (int f = 0; f < nf; ++f) {
             const double* n = &g.f_n[3 * (size_t)f];
             int o = g.f_owner[f], nb = g.f_nbr[f];
             double WL[5], Fv[5];
             for (int k = 0; k < 5; ++k) WL[k] = W[(size_t)k * nc + o];
-            if (nb >= 0) {
+            if (nb >= 0 && p.order == 2) {
+                double WR[5], dxL[3], dxR[3];
+                for (int k = 0; k < 5; ++k) WR[k] = W[(size_t)k * nc + nb];
+                const double* xf = &g.f_c[3 * (size_t)f];
+                for (int d = 0; d < 3; ++d) {
+                    dxL[d] = xf[d] - g.cen[3 * (size_t)o + d];
+                    dxR[d] = xf[d] - g.cen[3 * (size_t)nb + d];
+                }
+                Frame R = frame_of(n);
+                face_flux_o2(R, WL, rhoh[o], &gW[15 * (size_t)o], &gH[3 * (size_t)o], dxL, WR, rhoh[nb],
+                             &gW[15 * (size_t)nb], &gH[3 * (size_t)nb], dxR, dt, p, Fv);
+            } else if (nb >= 0) {
                 double WR[5];
                 for (int k = 0; k < 5; ++k) WR[k] = W[(size_t)k * nc + nb];
                 FaceState L = face_state(WL, rhoh[o], n, p.R), Rs = face_state(WR, rhoh[nb], n, p.R);
@@ -874,7 +1231,7 @@ orc_sim* orc_create(const orc_params* p, int32_t n_nodes, const double* xyz,
                     const int32_t* bfaces, const int32_t* btags, const double* W0,
                     char* err, int32_t errlen) {
     std::string e;
-    if (p->order != 1) { set_err(err, errlen, "only first-order reconstruction is implemented"); return nullptr; }
+    if (p->order != 1 && p->order != 2) { set_err(err, errlen, "order must be 1 or 2"); return nullptr; }
     if (p->n_bc < 0 || p->n_bc > 16) { set_err(err, errlen, "n_bc out of range"); return nullptr; }
     if (n_tets >= (1 << 24)) { set_err(err, errlen, "too many tets for the particle id layout"); return nullptr; }
     SimBase* s = nullptr;
@@ -963,6 +1320,37 @@ int orc_last(const orc_sim* h, int which, void* out) {
         case 9: std::memcpy(out, s->counters, sizeof(s->counters)); return 0;
         default: return -1;
     }
+}
+
+int orc_gradients(orc_sim* h, int limited, double* gradW, double* gradH) {
+    std::string e;
+    SimBase* s = h->s;
+    int rc = s->prepare(e);
+    if (rc) return rc;
+    std::vector<double> gW, gH;
+    limited_gradients(s->g, s->P, s->W, s->rhoh, limited != 0, gW, gH);
+    const int nc = s->g.nc;
+    for (int i = 0; i < nc; ++i) {
+        for (int q = 0; q < 5; ++q)
+            for (int d = 0; d < 3; ++d) gradW[((size_t)q * 3 + d) * nc + i] = gW[15 * (size_t)i + 3 * q + d];
+        for (int d = 0; d < 3; ++d) gradH[(size_t)d * nc + i] = gH[3 * (size_t)i + d];
+    }
+    return 0;
+}
+
+void orc_slope_moment(const double U[3], double lam, int half, const double a[5], int d, double out[5]) {
+    FrameMom M = frame_moments(U, lam, half);
+    for (int k = 0; k < 5; ++k) out[k] = expect(M, mul(mul(mul(coord(0), coord(d)), lin(a)), psi(k)));
+}
+
+void orc_micro_slope(const double U[3], double lam, const double b[5], double a[5]) { micro_slope(U, lam, b, a); }
+
+int orc_face_flux_o2(const orc_params* p, const double WL[5], double rhohL, const double gWL[15], const double gHL[3],
+                     const double dxL[3], const double WR[5], double rhohR, const double gWR[15],
+                     const double gHR[3], const double dxR[3], const double n[3], double dt, double F[5]) {
+    Frame R = frame_of(n);
+    face_flux_o2(R, WL, rhohL, gWL, gHL, dxL, WR, rhohR, gWR, gHR, dxR, dt, *p, F);
+    return 0;
 }
 
 int orc_prepare(orc_sim* h, char* err, int32_t errlen) {

@@ -30,6 +30,7 @@ typedef struct {
 
 typedef struct {
     double R, mu_ref, T_ref, omega, CFL, C2;
+    double venkat_K;   /* Venkatakrishnan constant K: epsilon^2 = (K h)^3 (order 2) */
     int32_t order, N_ref, N_min, precision, max_crossings, n_bc;
     uint64_t seed;
     orc_bc bc[16];
@@ -94,6 +95,19 @@ int orc_prepare(orc_sim* s, char* err, int32_t errlen);
 /* The particles cell `cell` samples at the current step (after orc_prepare):
  * returns their number n and fills up to cap of them (x, u as [k][3]). */
 int64_t orc_sample_cell(const orc_sim* s, int32_t cell, int64_t cap, uint64_t* id, double* x, double* u, double* m);
+
+/* Second-order pieces (order 2).  Gradients of the current state [5][3][nc]
+ * and [3][nc] (limited or not).  Slope moment int u_n u_d (a.psi) psi g du of
+ * a unit-density Maxwellian in a face frame (u along the normal; U given in
+ * that frame; half = +1, -1, 0).  Micro slope a with <psi psi^T> a = b.
+ * Second-order flux of one interior face from cell states, limited gradients
+ * ([q][d] row-major) and centroid-to-face vectors. */
+int orc_gradients(orc_sim* s, int limited, double* gradW, double* gradH);
+void orc_slope_moment(const double U[3], double lam, int half, const double a[5], int d, double out[5]);
+void orc_micro_slope(const double U[3], double lam, const double b[5], double a[5]);
+int orc_face_flux_o2(const orc_params* p, const double WL[5], double rhohL, const double gWL[15], const double gHL[3],
+                     const double dxL[3], const double WR[5], double rhohR, const double gWR[15],
+                     const double gHR[3], const double dxR[3], const double n[3], double dt, double F[5]);
 
 /* Track one particle with the simulation's mesh and parameters (sampled checks
  * at sizes where a whole oracle step would be slow).  io_x/io_u are [3];

@@ -143,7 +143,7 @@ def _params(Kn, omega, CFL, N_ref, precision, seed, bc, C2=0.0, N_min=0, capacit
             n_cells=None, max_crossings=1000):
     cap = capacity if capacity is not None else int(3 * N_ref * n_cells + 4096)
     return {"R": 1.0, "mu_ref": mu_ref_vhs(Kn, omega), "T_ref": 1.0, "omega": omega, "CFL": CFL,
-            "C2": C2, "order": 1, "N_ref": N_ref, "N_min": N_min, "precision": precision,
+            "C2": C2, "order": 1, "venkat_K": 5.0, "N_ref": N_ref, "N_min": N_min, "precision": precision,
             "seed": seed, "max_crossings": max_crossings, "bc": bc, "particle_capacity": cap,
             "Kn": Kn}
 
