@@ -118,8 +118,9 @@ typedef struct {
     double Pr;                   /* reserved (BGK: Pr = 1); must be 0 or 1 */
     double CFL;                  /* Courant number C in (0, 1] */
     double C2;                   /* numerical-dissipation constant (>= 0) */
-    double venkat_K;             /* reserved for second-order reconstruction */
-    int32_t order;               /* reconstruction order: 1 (first order) */
+    double venkat_K;             /* Venkatakrishnan constant K (>= 0): epsilon^2 = (K |Omega|^(1/3))^3 */
+    int32_t order;               /* reconstruction order: 1, or 2 (least-squares gradients with
+                                  * Venkatakrishnan's limiter at interior faces, Sec. 2.1) */
     int32_t N_ref;               /* reference particle number per cell (> 0) */
     int32_t N_min;               /* minimum particles per cell after sampling (>= 0) */
     int32_t precision;           /* UGKWP_FP64 or UGKWP_MIXED */
@@ -221,13 +222,16 @@ int ugkwp_import_state(ugkwp_sim* s, const ugkwp_state* st);
  *  F^eq + F^{fr,wave} per unit area [5][n_faces] (face numbering: by owner
  *  tet then its local face), 6 particle flux F^{fr,p} in fixed point
  *  [5][n_cells] (int64), 7 survivor mass in fixed point [n_cells] (int64),
- *  8 survivor count [n_cells] (int64). */
+ *  8 survivor count [n_cells] (int64); at order 2 only: 9 limited gradients
+ *  of W [5][3][n_cells] (component, direction, cell), 10 limited gradient of
+ *  rho^h [3][n_cells]. */
 int ugkwp_last(ugkwp_sim* s, int32_t which, void* host_out);
 
 /* Kernel classes of one step, in launch order (for ugkwp_timing_read). */
 enum {
     UGKWP_K_RESET = 0, UGKWP_K_CELL_PREP, UGKWP_K_SAMPLE_COUNT, UGKWP_K_SCAN, UGKWP_K_SCATTER,
-    UGKWP_K_SAMPLE, UGKWP_K_TRACK, UGKWP_K_FLUX, UGKWP_K_UPDATE, UGKWP_K_MOVERS, UGKWP_N_KERNELS
+    UGKWP_K_SAMPLE, UGKWP_K_TRACK, UGKWP_K_FLUX, UGKWP_K_UPDATE, UGKWP_K_MOVERS, UGKWP_K_GRADIENTS,
+    UGKWP_N_KERNELS
 };
 
 /* Per-kernel timing with CUDA events recorded on the bound stream around each
@@ -236,7 +240,8 @@ enum {
  * milliseconds (ms[UGKWP_N_KERNELS]) of the launches timed since the last
  * read, and the number of kernels launched since ugkwp_init
  * (launches[UGKWP_N_KERNELS], counted whether or not timing is enabled; the
- * scan class counts its two kernels); either pointer may be NULL.  The timed
+ * scan class counts its two kernels, the flux class its two at order 2);
+ * either pointer may be NULL.  The timed
  * sums are reset by the read. */
 int ugkwp_timing_enable(ugkwp_sim* s, int32_t enable);
 int ugkwp_timing_read(ugkwp_sim* s, double* ms, int64_t* launches);

@@ -107,7 +107,7 @@ struct Carver {
 void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, DevState& S, PartBufRaw& A,
             PartBufRaw& B) {
     const size_t nc = mh.nc, nf = mh.nf, nbf = mh.nbf;
-    M.nc = mh.nc; M.nf = mh.nf; M.nbf = mh.nbf;
+    M.nc = mh.nc; M.nf = mh.nf; M.nbf = mh.nbf; M.nif = mh.nf - mh.nbf;
     M.vol = c.take<double>(nc);
     M.dS = c.take<double>(3 * nc);
     M.vtx = c.take<double>(12 * nc);
@@ -118,6 +118,10 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, D
     if (rs == 4) M.trk_f = c.take<TrkF>(nc);
     else M.trk_d = c.take<TrkD>(nc);
     M.face_order = c.take<int32_t>(nf);
+    M.lsq_c = c.take<double>(12 * nc);
+    M.lsq_dxf = c.take<double>(12 * nc);
+    M.eps2 = c.take<double>(nc);
+    M.f_lk = c.take<int32_t>(nf);
     M.f_own = c.take<int32_t>(nf);
     M.f_nbr = c.take<int32_t>(nf);
     M.f_n = c.take<double>(3 * nf);
@@ -146,6 +150,8 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, D
     S.wacc = c.take<int64_t>(5 * nc);
     S.mom = c.take<double>(5 * nc);
     S.F = c.take<double>(5 * nf);
+    S.gradW = c.take<double>(15 * nc);
+    S.gradH = c.take<double>(3 * nc);
     S.bsum = c.take<int2>((size_t)scan_blocks(mh.nc) + 1);
     S.t = c.take<double>(1);
     S.dt = c.take<double>(1);
@@ -166,7 +172,8 @@ int check_params(const ugkwp_params* p, const MeshHost* mh) {
     if (!(p->CFL > 0.0 && p->CFL <= 1.0)) return fail(UGKWP_E_ARG, "CFL must be in (0, 1]");
     if (!(p->C2 >= 0.0)) return fail(UGKWP_E_ARG, "C2 must be >= 0");
     if (!(p->Pr == 0.0 || p->Pr == 1.0)) return fail(UGKWP_E_UNSUPPORTED, "only the BGK model (Pr = 1) is available");
-    if (p->order != 1) return fail(UGKWP_E_UNSUPPORTED, "only first-order reconstruction (order = 1) is available");
+    if (p->order != 1 && p->order != 2) return fail(UGKWP_E_ARG, "order must be 1 or 2");
+    if (p->order == 2 && !(p->venkat_K >= 0.0)) return fail(UGKWP_E_ARG, "venkat_K must be >= 0");
     if (p->N_ref <= 0 || p->N_min < 0) return fail(UGKWP_E_ARG, "N_ref must be > 0 and N_min >= 0");
     if (p->precision != UGKWP_FP64 && p->precision != UGKWP_MIXED) return fail(UGKWP_E_ARG, "unknown precision");
     if (p->max_crossings <= 0) return fail(UGKWP_E_ARG, "max_crossings must be > 0");
@@ -343,6 +350,7 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     std::memset(&P, 0, sizeof(P));
     P.R = p->R; P.mu_ref = p->mu_ref; P.T_ref = p->T_ref; P.omega = p->omega; P.CFL = p->CFL; P.C2 = p->C2;
     P.N_ref = p->N_ref; P.N_min = p->N_min; P.max_crossings = p->max_crossings; P.precision = p->precision;
+    P.order = p->order;
     P.seed = p->seed; P.capacity = p->particle_capacity; P.n_bc = p->n_bc;
     for (int b = 0; b < p->n_bc; ++b) {
         P.bc[b].type = p->bc[b].type;
@@ -371,6 +379,60 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     for (int f = 0; f < nf; ++f) {
         for (int d = 0; d < 3; ++d) fn[(size_t)d * nf + f] = mh.f_n[3 * (size_t)f + d];
         fnb[f] = mh.f_nbr[f] >= 0 ? mh.f_nbr[f] : -1 - mh.bf_of_face[f];
+    }
+    // least-squares gradient coefficients (Sec. 2.1): weights 1/|dx_k|^2 over
+    // the 4 face neighbours, a boundary face contributing a ghost at the mirror
+    // image of the centroid; grad = sum_k c_k (v_k - v_i) with
+    // c_k = A^-1 w_k dx_k, A = sum_k w_k dx_k dx_k^T.  Also the centroid-to-face
+    // vectors and epsilon^2 = (K |Omega|^(1/3))^3 of Venkatakrishnan's limiter.
+    std::vector<double> lsq_c(12 * (size_t)nc), lsq_dxf(12 * (size_t)nc), eps2(nc);
+    std::vector<int32_t> flk(nf, 0);
+    for (int i = 0; i < nc; ++i) {
+        double xi[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < 4; ++k)
+            for (int d = 0; d < 3; ++d) xi[d] += mh.xyz[3 * (size_t)mh.tet[4 * (size_t)i + k] + d];
+        for (int d = 0; d < 3; ++d) xi[d] *= 0.25;
+        double dx[4][3], w[4], A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int k = 0; k < 4; ++k) {
+            const int f = mh.cf[4 * (size_t)i + k];
+            const bool own = mh.cf_sign[4 * (size_t)i + k] > 0;
+            const double* xf = &mh.f_c[3 * (size_t)f];
+            for (int d = 0; d < 3; ++d) lsq_dxf[(size_t)(3 * k + d) * nc + i] = xf[d] - xi[d];
+            const int j = own ? mh.f_nbr[f] : mh.f_own[f];
+            if (j >= 0) {
+                for (int d = 0; d < 3; ++d) {
+                    double xj = 0.0;
+                    for (int l = 0; l < 4; ++l) xj += mh.xyz[3 * (size_t)mh.tet[4 * (size_t)j + l] + d];
+                    dx[k][d] = 0.25 * xj - xi[d];
+                }
+            } else {
+                const double* n = &mh.f_n[3 * (size_t)f];
+                const double h = (xf[0] - xi[0]) * n[0] + (xf[1] - xi[1]) * n[1] + (xf[2] - xi[2]) * n[2];
+                for (int d = 0; d < 3; ++d) dx[k][d] = 2.0 * h * n[d];
+            }
+            w[k] = 1.0 / (dx[k][0] * dx[k][0] + dx[k][1] * dx[k][1] + dx[k][2] * dx[k][2]);
+            for (int r = 0; r < 3; ++r)
+                for (int cc = 0; cc < 3; ++cc) A[r][cc] += w[k] * dx[k][r] * dx[k][cc];
+            if (own) flk[f] |= k;
+            else flk[f] |= k << 2;
+        }
+        // inverse of the symmetric 3x3 matrix by cofactors
+        double C[3][3];
+        C[0][0] = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+        C[0][1] = A[0][2] * A[2][1] - A[0][1] * A[2][2];
+        C[0][2] = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+        C[1][0] = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+        C[1][1] = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+        C[1][2] = A[0][2] * A[1][0] - A[0][0] * A[1][2];
+        C[2][0] = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+        C[2][1] = A[0][1] * A[2][0] - A[0][0] * A[2][1];
+        C[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+        const double det = A[0][0] * C[0][0] + A[0][1] * C[1][0] + A[0][2] * C[2][0];
+        for (int k = 0; k < 4; ++k)
+            for (int r = 0; r < 3; ++r)
+                lsq_c[(size_t)(3 * k + r) * nc + i] =
+                    w[k] * (C[r][0] * dx[k][0] + C[r][1] * dx[k][1] + C[r][2] * dx[k][2]) / det;
+        eps2[i] = std::pow(p->venkat_K * std::cbrt(mh.vol[i]), 3.0);
     }
     // flux work order: interior faces, then boundary faces grouped by type
     std::vector<int32_t> forder;
@@ -427,6 +489,10 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     if (s->real_size == 4) { UP(s->M.trk_f, tf.data(), tf.size() * sizeof(TrkF)); }
     else { UP(s->M.trk_d, td.data(), td.size() * sizeof(TrkD)); }
     UP(s->M.face_order, forder.data(), nf * sizeof(int32_t));
+    UP(s->M.lsq_c, lsq_c.data(), lsq_c.size() * sizeof(double));
+    UP(s->M.lsq_dxf, lsq_dxf.data(), lsq_dxf.size() * sizeof(double));
+    UP(s->M.eps2, eps2.data(), eps2.size() * sizeof(double));
+    UP(s->M.f_lk, flk.data(), flk.size() * sizeof(int32_t));
     UP(s->M.f_own, mh.f_own.data(), nf * sizeof(int32_t));
     UP(s->M.f_nbr, fnb.data(), nf * sizeof(int32_t));
     UP(s->M.f_n, fn.data(), fn.size() * sizeof(double));
@@ -531,7 +597,10 @@ int enqueue_step(ugkwp_sim* s) {
         // writes only F, which no particle kernel touches
         CU(cudaEventRecord(s->fork, q));
         CU(cudaStreamWaitEvent(s->wave, s->fork, 0));
-        timed(s, UGKWP_K_FLUX, 1, s->wave, [&] { launch_face_flux(s->M, s->S, s->P, s->wave); });
+        if (s->P.order == 2)
+            timed(s, UGKWP_K_GRADIENTS, 1, s->wave, [&] { launch_gradients(s->M, s->S, s->P, s->wave); });
+        const int n_flux = s->P.order == 2 ? (s->M.nif > 0) + (s->M.nf > s->M.nif) : 1;
+        timed(s, UGKWP_K_FLUX, n_flux, s->wave, [&] { launch_face_flux(s->M, s->S, s->P, s->wave); });
         CU(cudaEventRecord(s->join, s->wave));
         timed(s, UGKWP_K_SCAN, 2, q, [&] { launch_scan(s->M, s->S, s->P, q); });
         timed(s, UGKWP_K_SCATTER, 1, q, [&] { launch_scatter(s->M, s->S, s->P, s->A, s->B, q); });
@@ -820,6 +889,12 @@ int ugkwp_last(ugkwp_sim* s, int32_t which, void* host_out) {
             for (size_t i = 0; i < nc; ++i) ((int64_t*)host_out)[i] = v[i];
             break;
         }
+        case 9:
+        case 10:
+            if (s->P.order != 2) return fail(UGKWP_E_ARG, "gradients exist only at order 2");
+            if (which == 9) CU(get(s->S.gradW, 15 * nc * 8));
+            else CU(get(s->S.gradH, 3 * nc * 8));
+            break;
         default: return fail(UGKWP_E_ARG, "unknown diagnostic");
     }
     return UGKWP_OK;

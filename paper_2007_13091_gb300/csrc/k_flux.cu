@@ -141,9 +141,341 @@ __device__ void interior_flux(const Side& L, const Side& R, bool ghost_hydro, co
     for (int k = 0; k < 5; ++k) F[k] = q1 * Feq[k] + a4 * (L.rhoh * GL[k]) + cR * (R.rhoh * GR[k]);
 }
 
-__global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevParams p) {
-    const int nc = m.nc, nf = m.nf;
+// ------------------------------------------------------------- order 2
+// a3: least-squares gradients over the 4 face neighbours (host-precomputed
+// coefficients c_k, ghosts mirrored across boundary faces) limited with
+// Venkatakrishnan's function, per conservative component and for rho^h.
+
+__device__ __forceinline__ double venkat(double d1, double d2, double eps2) {
+    return ((d1 * d1 + eps2) * d2 + 2.0 * d2 * d2 * d1) / (d2 * (d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + eps2));
+}
+
+__global__ void __launch_bounds__(256) k_gradients(DevMesh m, DevState s, DevParams p) {
+    const int nc = m.nc;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    int other[4], bidx[4];
+    const int own = m.cfs[i];
+    for (int k = 0; k < 4; ++k) {
+        const int f = m.cf[k * nc + i];
+        other[k] = ((own >> k) & 1) ? m.f_nbr[f] : m.f_own[f];
+        bidx[k] = other[k] < 0 ? -1 - other[k] : -1;
+    }
+    double Wi[5];
+    for (int q = 0; q < 5; ++q) Wi[q] = s.W[(size_t)q * nc + i];
+    const double eps2 = m.eps2[i];
+    for (int q = 0; q < 6; ++q) {
+        const double self = q < 5 ? Wi[q] : s.rhoh[i];
+        double val[4];
+        for (int k = 0; k < 4; ++k) {
+            if (other[k] >= 0) {
+                val[k] = q < 5 ? s.W[(size_t)q * nc + other[k]] : s.rhoh[other[k]];
+            } else {
+                const DevBc& bc = p.bc[m.bf_tag[bidx[k]]];
+                val[k] = self;
+                if (bc.type == UGKWP_BC_SPECULAR && q >= 1 && q <= 3) {
+                    const int nbf = m.nbf;
+                    double n[3];
+                    for (int d = 0; d < 3; ++d) n[d] = m.bf_n[(size_t)d * nbf + bidx[k]];
+                    const double mn = Wi[1] * n[0] + Wi[2] * n[1] + Wi[3] * n[2];
+                    val[k] = self - 2.0 * mn * n[q - 1];
+                } else if (bc.type == UGKWP_BC_FARFIELD) {
+                    val[k] = q < 5 ? bc.W_in[q] : bc.W_in[0];
+                }
+            }
+        }
+        double g[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < 4; ++k)
+            for (int d = 0; d < 3; ++d) g[d] += m.lsq_c[(size_t)(3 * k + d) * nc + i] * (val[k] - self);
+        double vmax = self, vmin = self;
+        for (int k = 0; k < 4; ++k) { vmax = fmax(vmax, val[k]); vmin = fmin(vmin, val[k]); }
+        double phi = 1.0;
+        for (int k = 0; k < 4; ++k) {
+            const double d2 = g[0] * m.lsq_dxf[(size_t)(3 * k) * nc + i] + g[1] * m.lsq_dxf[(size_t)(3 * k + 1) * nc + i] +
+                              g[2] * m.lsq_dxf[(size_t)(3 * k + 2) * nc + i];
+            double pk = 1.0;
+            if (d2 > 0.0) pk = venkat(vmax - self, d2, eps2);
+            else if (d2 < 0.0) pk = venkat(vmin - self, d2, eps2);
+            phi = fmin(phi, pk);
+        }
+        for (int d = 0; d < 3; ++d) {
+            if (q < 5) s.gradW[(size_t)(3 * q + d) * nc + i] = phi * g[d];
+            else s.gradH[(size_t)d * nc + i] = phi * g[d];
+        }
+    }
+}
+
+// Moment tables of a unit Maxwellian in a face frame: <u^k> (normal, over the
+// half space `half` or all u) and <v^k>, <w^k> (tangential, full), k = 0..6.
+struct Tab { double n[7], v[7], w[7]; };
+
+__device__ __forceinline__ void gauss_mom(double mean, double h, double* M) {  // h = 1/(2 lambda)
+    M[0] = 1.0;
+    M[1] = mean;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) M[k + 2] = mean * M[k + 1] + (double)(k + 1) * h * M[k];
+}
+
+__device__ __forceinline__ void make_tab(const double* U, double lam, double rl, int half, Tab& T) {
+    const double h = 0.5 * rl * rl;
+    if (half == 0) {
+        gauss_mom(U[0], h, T.n);
+    } else {
+        const double a = lam * rl * U[0];
+        const double edge = 0.5 * exp(-a * a) * rl * 0.56418958354775628695;
+        T.n[0] = half > 0 ? 0.5 * erfc(-a) : 0.5 * erfc(a);
+        T.n[1] = U[0] * T.n[0] + (half > 0 ? edge : -edge);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) T.n[k + 2] = U[0] * T.n[k + 1] + (double)(k + 1) * h * T.n[k];
+    }
+    gauss_mom(U[1], h, T.v);
+    gauss_mom(U[2], h, T.w);
+}
+
+// out_k = < u^AL v^BE w^GA (a.psi) psi_k >, psi = (1, u, v, w, |u|^2/2).
+template <int AL, int BE, int GA>
+__device__ __forceinline__ void apsi(const Tab& T, const double* a, double out[5]) {
+#define MM(x, y, z) (T.n[AL + (x)] * T.v[BE + (y)] * T.w[GA + (z)])
+#define PP(x, y, z) (a[0] * MM(x, y, z) + a[1] * MM((x) + 1, y, z) + a[2] * MM(x, (y) + 1, z) + \
+                     a[3] * MM(x, y, (z) + 1) + 0.5 * a[4] * (MM((x) + 2, y, z) + MM(x, (y) + 2, z) + MM(x, y, (z) + 2)))
+    out[0] = PP(0, 0, 0);
+    out[1] = PP(1, 0, 0);
+    out[2] = PP(0, 1, 0);
+    out[3] = PP(0, 0, 1);
+    out[4] = 0.5 * (PP(2, 0, 0) + PP(0, 2, 0) + PP(0, 0, 2));
+#undef PP
+#undef MM
+}
+
+// <u_n u_d (a.psi) psi> for frame direction d (0 normal, 1 t1, 2 t2)
+__device__ __forceinline__ void slope_mom(const Tab& T, int d, const double* a, double out[5]) {
+    if (d == 0) apsi<2, 0, 0>(T, a, out);
+    else if (d == 1) apsi<1, 1, 0>(T, a, out);
+    else apsi<1, 0, 1>(T, a, out);
+}
+
+// Micro slope a with <psi psi^T> a = b for the unit Maxwellian (U, lambda),
+// in closed form: with theta = 1/(2 lambda), R_i = b_i - U_i b_0,
+// R_4 = 2 b_4 - (|U|^2 + 3 theta) b_0:  a_4 = 4 lambda^2/3 (R_4 - 2 U.R),
+// a_i = 2 lambda R_i - U_i a_4,  a_0 = b_0 - U.a - a_4 (|U|^2 + 3 theta)/2.
+__device__ __forceinline__ void micro(const double* U, double lam, const double* b, double* a) {
+    const double th = 0.5 / lam;
+    const double R1 = b[1] - U[0] * b[0], R2 = b[2] - U[1] * b[0], R3 = b[3] - U[2] * b[0];
+    const double U2 = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
+    const double R4 = 2.0 * b[4] - (U2 + 3.0 * th) * b[0];
+    a[4] = (4.0 / 3.0) * lam * lam * (R4 - 2.0 * (U[0] * R1 + U[1] * R2 + U[2] * R3));
+    a[1] = 2.0 * lam * R1 - U[0] * a[4];
+    a[2] = 2.0 * lam * R2 - U[1] * a[4];
+    a[3] = 2.0 * lam * R3 - U[2] * a[4];
+    a[0] = b[0] - (U[0] * a[1] + U[1] * a[2] + U[2] * a[3]) - 0.5 * a[4] * (U2 + 3.0 * th);
+}
+
+// All time coefficients: q1, q2, q3, q4, a4, a5 (power series below x = 1).
+struct QC { double q1, q2, q3, q4, a4, a5; };
+__device__ __forceinline__ QC time_coeffs_all(double dt, double tau) {
+    QC c;
+    const double x = dt / tau;
+    if (x < 1.0) {
+        const double stop = x * x * x * 0x1p-60;  // smallest leading term is O(x^3)
+        double term = 1.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, sa4 = 0.0, sa5 = 0.0;
+#pragma unroll 1
+        for (int k = 1; k <= 30; ++k) {
+            term = term * x * c_inv_k[k];
+            const double sg = (k & 1) ? -1.0 : 1.0;
+            const double dk = (double)k;
+            if (k >= 2) { s1 += sg * term; sa4 += sg * (dk - 1.0) * term; }
+            if (k >= 3) { s2 += sg * (dk - 2.0) * term; s3 -= sg * term; sa5 += sg * 0.5 * (dk - 1.0) * (dk - 2.0) * term; }
+            s4 -= sg * term;
+            if (k >= 4 && term * dk * dk < stop) break;
+        }
+        const double t2 = tau * tau;
+        c.q1 = tau * s1; c.q2 = t2 * s2; c.q3 = t2 * s3; c.q4 = tau * s4; c.a4 = tau * sa4; c.a5 = t2 * sa5;
+    } else {
+        const double e = exp(-x);
+        const double ph = -expm1(-x);
+        c.q1 = dt - tau * ph;
+        c.q2 = 2.0 * tau * tau * ph - tau * dt - tau * dt * e;
+        c.q3 = 0.5 * dt * dt - tau * dt + tau * tau * ph;
+        c.q4 = tau * ph;
+        const double q5 = tau * dt * e - tau * tau * ph;
+        c.a4 = c.q4 - dt * e;
+        c.a5 = q5 + 0.5 * dt * dt * e;
+    }
+    return c;
+}
+
+// Face frame rows n, t1, t2 (t1 = e_a x n / |.| for the axis of smallest |n_a|).
+__device__ __forceinline__ void face_frame(const double* n, double R[3][3]) {
+    int ax = 0;
+    if (fabs(n[1]) < fabs(n[ax])) ax = 1;
+    if (fabs(n[2]) < fabs(n[ax])) ax = 2;
+    double t1[3];
+    t1[0] = ax == 0 ? 0.0 : (ax == 1 ? n[2] : -n[1]);
+    t1[1] = ax == 1 ? 0.0 : (ax == 0 ? -n[2] : n[0]);
+    t1[2] = ax == 2 ? 0.0 : (ax == 0 ? n[1] : -n[0]);
+    const double il = rsqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+    for (int d = 0; d < 3; ++d) t1[d] *= il;
+    R[0][0] = n[0]; R[0][1] = n[1]; R[0][2] = n[2];
+    R[1][0] = t1[0]; R[1][1] = t1[1]; R[1][2] = t1[2];
+    R[2][0] = n[1] * t1[2] - n[2] * t1[1];
+    R[2][1] = n[2] * t1[0] - n[0] * t1[2];
+    R[2][2] = n[0] * t1[1] - n[1] * t1[0];
+}
+
+// Slopes along frame direction dd of the frame-rotated W, from a cell gradient.
+__device__ __forceinline__ void frame_slope(const double* gW, int nc, int c, const double R[3][3], int dd, double out[5]) {
+    double g[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+        g[q] = gW[(size_t)(3 * q) * nc + c] * R[dd][0] + gW[(size_t)(3 * q + 1) * nc + c] * R[dd][1] +
+               gW[(size_t)(3 * q + 2) * nc + c] * R[dd][2];
+    out[0] = g[0];
+    for (int j = 0; j < 3; ++j) out[1 + j] = R[j][0] * g[1] + R[j][1] * g[2] + R[j][2] * g[3];
+    out[4] = g[4];
+}
+
+struct SideF {
+    double W[5];  // frame state at the face
+    double rhoh, U[3], lam, rl;
+    bool o2;      // reconstructed (else first order: zero slopes)
+};
+
+__device__ __forceinline__ SideF make_sideF(const DevMesh& m, const DevState& s, int c, const double* dx,
+                                            const double R[3][3]) {
+    const int nc = m.nc;
+    SideF S;
+    double Wf[5];
+    for (int q = 0; q < 5; ++q)
+        Wf[q] = s.W[(size_t)q * nc + c] + s.gradW[(size_t)(3 * q) * nc + c] * dx[0] +
+                s.gradW[(size_t)(3 * q + 1) * nc + c] * dx[1] + s.gradW[(size_t)(3 * q + 2) * nc + c] * dx[2];
+    double rh = s.rhoh[c] + s.gradH[c] * dx[0] + s.gradH[nc + c] * dx[1] + s.gradH[2 * nc + c] * dx[2];
+    double pr = (Wf[4] - 0.5 * (Wf[1] * Wf[1] + Wf[2] * Wf[2] + Wf[3] * Wf[3]) / Wf[0]) * (2.0 / 3.0);
+    S.o2 = Wf[0] > 0.0 && pr > 0.0;
+    if (!S.o2) {
+        for (int q = 0; q < 5; ++q) Wf[q] = s.W[(size_t)q * nc + c];
+        rh = s.rhoh[c];
+        pr = (Wf[4] - 0.5 * (Wf[1] * Wf[1] + Wf[2] * Wf[2] + Wf[3] * Wf[3]) / Wf[0]) * (2.0 / 3.0);
+    }
+    S.W[0] = Wf[0];
+    for (int j = 0; j < 3; ++j) S.W[1 + j] = R[j][0] * Wf[1] + R[j][1] * Wf[2] + R[j][2] * Wf[3];
+    S.W[4] = Wf[4];
+    S.rhoh = rh;
+    const double ir = 1.0 / S.W[0];
+    for (int j = 0; j < 3; ++j) S.U[j] = S.W[1 + j] * ir;
+    S.lam = 0.5 * S.W[0] / pr;
+    S.rl = rsqrt(S.lam);
+    return S;
+}
+
+// Hydrodynamic slope along dd of side S: grad((rho^h/rho) W) in the frame.
+__device__ __forceinline__ void hydro_slope(const DevMesh& m, const DevState& s, int c, const SideF& S,
+                                            const double R[3][3], int dd, double out[5]) {
+    if (!S.o2) { for (int q = 0; q < 5; ++q) out[q] = 0.0; return; }
+    const int nc = m.nc;
+    double dW[5];
+    frame_slope(s.gradW, nc, c, R, dd, dW);
+    const double gh = s.gradH[c] * R[dd][0] + s.gradH[nc + c] * R[dd][1] + s.gradH[2 * nc + c] * R[dd][2];
+    const double ratio = S.rhoh / S.W[0];
+    const double gr = (gh - ratio * dW[0]) / S.W[0];
+    for (int q = 0; q < 5; ++q) out[q] = ratio * dW[q] + S.W[q] * gr;
+}
+
+__device__ void interior_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p, int f, int o, int nb,
+                                 const double* n, double dt, double inv_Tref, double F[5]) {
+    const int nc = m.nc;
+    double R[3][3];
+    face_frame(n, R);
+    const int lk = m.f_lk[f];
+    double dxL[3], dxR[3];
+    for (int d = 0; d < 3; ++d) {
+        dxL[d] = m.lsq_dxf[(size_t)(3 * (lk & 3) + d) * nc + o];
+        dxR[d] = m.lsq_dxf[(size_t)(3 * ((lk >> 2) & 3) + d) * nc + nb];
+    }
+    const SideF L = make_sideF(m, s, o, dxL, R);
+    const SideF Rs = make_sideF(m, s, nb, dxR, R);
+    const double e0[5] = {1.0, 0.0, 0.0, 0.0, 0.0};
+    Tab T;
+    double HL[5], GL[5], HR[5], GR[5];
+    make_tab(L.U, L.lam, L.rl, +1, T);
+    apsi<0, 0, 0>(T, e0, HL);
+    apsi<1, 0, 0>(T, e0, GL);
+    make_tab(Rs.U, Rs.lam, Rs.rl, -1, T);
+    apsi<0, 0, 0>(T, e0, HR);
+    apsi<1, 0, 0>(T, e0, GR);
+    double W0[5];
+    for (int k = 0; k < 5; ++k) W0[k] = L.W[0] * HL[k] + Rs.W[0] * HR[k];
+    const double rho0 = W0[0], ir0 = 1.0 / rho0;
+    const double U0[3] = {W0[1] * ir0, W0[2] * ir0, W0[3] * ir0};
+    const double p0 = (W0[4] - 0.5 * rho0 * dot3(U0, U0)) * (2.0 / 3.0);
+    const double lam0 = 0.5 * rho0 / p0;
+    const double T0 = p0 * ir0 / p.R;
+    double tau = p.mu_ref * exp(p.omega * log(T0 * inv_Tref)) / p0;
+    if (p.C2 > 0.0) {
+        const double pl = 0.5 * L.W[0] / L.lam, prr = 0.5 * Rs.W[0] / Rs.lam;
+        tau += p.C2 * fabs(pl - prr) / fabs(pl + prr) * dt;
+    }
+    const QC qc = time_coeffs_all(dt, tau);
+    // free transport of the hydrodynamic wave, upwind, with slopes
+    for (int k = 0; k < 5; ++k) F[k] = qc.a4 * (L.rhoh * GL[k] + Rs.rhoh * GR[k]);
+    double sm[5], b[5], a[5];
+    make_tab(L.U, L.lam, L.rl, +1, T);
+    for (int dd = 0; dd < 3; ++dd) {
+        hydro_slope(m, s, o, L, R, dd, b);
+        micro(L.U, L.lam, b, a);
+        slope_mom(T, dd, a, sm);
+        for (int k = 0; k < 5; ++k) F[k] += qc.a5 * sm[k];
+    }
+    make_tab(Rs.U, Rs.lam, Rs.rl, -1, T);
+    for (int dd = 0; dd < 3; ++dd) {
+        hydro_slope(m, s, nb, Rs, R, dd, b);
+        micro(Rs.U, Rs.lam, b, a);
+        slope_mom(T, dd, a, sm);
+        for (int k = 0; k < 5; ++k) F[k] += qc.a5 * sm[k];
+    }
+    // equilibrium part: q1 g0 + q2 u.g_x + q3 g_t
+    make_tab(U0, lam0, rsqrt(lam0), 0, T);
+    double G0[5];
+    apsi<1, 0, 0>(T, e0, G0);
+    for (int k = 0; k < 5; ++k) F[k] += qc.q1 * rho0 * G0[k];
+    double a0[3][5], Wt[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int dd = 0; dd < 3; ++dd) {
+        double sL[5], sR[5];
+        if (L.o2) frame_slope(s.gradW, nc, o, R, dd, sL); else for (int q = 0; q < 5; ++q) sL[q] = 0.0;
+        if (Rs.o2) frame_slope(s.gradW, nc, nb, R, dd, sR); else for (int q = 0; q < 5; ++q) sR[q] = 0.0;
+        for (int q = 0; q < 5; ++q) b[q] = 0.5 * (sL[q] + sR[q]);
+        micro(U0, lam0, b, a0[dd]);
+        slope_mom(T, dd, a0[dd], sm);
+        for (int k = 0; k < 5; ++k) F[k] += qc.q2 * sm[k];
+        if (dd == 0) apsi<1, 0, 0>(T, a0[dd], sm);
+        else if (dd == 1) apsi<0, 1, 0>(T, a0[dd], sm);
+        else apsi<0, 0, 1>(T, a0[dd], sm);
+        for (int k = 0; k < 5; ++k) Wt[k] -= sm[k];
+    }
+    double At[5];
+    micro(U0, lam0, Wt, At);
+    apsi<1, 0, 0>(T, At, sm);
+    for (int k = 0; k < 5; ++k) F[k] += qc.q3 * sm[k];
+    // back to the lab frame
+    const double Fm[3] = {F[1], F[2], F[3]};
+    for (int d = 0; d < 3; ++d) F[1 + d] = Fm[0] * R[0][d] + Fm[1] * R[1][d] + Fm[2] * R[2][d];
+}
+
+// Second-order flux of the interior faces (the first nif entries of face_order).
+__global__ void __launch_bounds__(128) k_face_flux_o2(DevMesh m, DevState s, DevParams p) {
+    const int nf = m.nf;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m.nif) return;
+    const int f = m.face_order[t];
+    const double n[3] = {m.f_n[f], m.f_n[nf + f], m.f_n[2 * nf + f]};
+    double F[5];
+    interior_flux_o2(m, s, p, f, m.f_own[f], m.f_nbr[f], n, s.dt[0], 1.0 / p.T_ref, F);
+    for (int q = 0; q < 5; ++q) s.F[(size_t)q * nf + f] = F[q];
+}
+
+// First-order flux of the faces face_order[first..nf).
+__global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevParams p, int first) {
+    const int nc = m.nc, nf = m.nf;
+    const int t = first + blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nf) return;
     const int f = m.face_order[t];  // interior faces first, then boundary faces by type
     const double dt = s.dt[0];
@@ -195,8 +527,17 @@ __global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevPar
 
 }  // namespace
 
+void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
+    k_gradients<<<(m.nc + 255) / 256, 256, 0, st>>>(m, s, p);
+}
+
 void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
-    k_face_flux<<<(m.nf + 255) / 256, 256, 0, st>>>(m, s, p);
+    int first = 0;
+    if (p.order == 2) {
+        if (m.nif > 0) k_face_flux_o2<<<(m.nif + 127) / 128, 128, 0, st>>>(m, s, p);
+        first = m.nif;
+    }
+    if (m.nf > first) k_face_flux<<<(m.nf - first + 255) / 256, 256, 0, st>>>(m, s, p, first);
 }
 
 }  // namespace ugkwp

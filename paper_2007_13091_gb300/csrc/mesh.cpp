@@ -143,6 +143,7 @@ bool build_mesh(const ugkwp_mesh_desc& d, MeshHost& M, std::string& err) {
     // --- face geometry
     M.f_n.resize(3 * (size_t)nf); M.f_area.resize(nf); M.f_d.resize(nf);
     M.f_t1.assign(3 * (size_t)nf, 0.0); M.f_t2.assign(3 * (size_t)nf, 0.0);
+    M.f_c.resize(3 * (size_t)nf);
     for (int32_t f = 0; f < nf; ++f) {
         const int32_t o = M.f_own[f], k = M.f_own_k[f];
         int32_t v[3], j = 0;
@@ -162,6 +163,7 @@ bool build_mesh(const ugkwp_mesh_desc& d, MeshHost& M, std::string& err) {
         M.f_area[f] = 0.5 * len;
         double cen[3];
         for (int c = 0; c < 3; ++c) cen[c] = ((pa[c] + pb[c]) + pc[c]) / 3.0;
+        for (int c = 0; c < 3; ++c) M.f_c[3 * (size_t)f + c] = cen[c];
         M.f_d[f] = dot(n, cen);
         int ax = 0;
         if (std::fabs(n[1]) < std::fabs(n[ax])) ax = 1;

@@ -52,6 +52,8 @@ struct DevBc {
 struct DevParams {
     double R, mu_ref, T_ref, omega, CFL, C2;
     int32_t N_ref, N_min, max_crossings, precision;
+    int32_t order;
+    int32_t pad_;
     uint64_t seed;
     int64_t capacity;
     int32_t exps[5];
@@ -77,6 +79,7 @@ struct __align__(16) TrkD {
 
 struct DevMesh {
     int32_t nc, nf, nbf;
+    int32_t nif;             // interior faces (they lead face_order)
     const double* vol;       // [nc]
     const double* dS;        // [3][nc]
     const double* vtx;       // [12][nc]: vertex k coordinate c at [(3k+c) nc + i]
@@ -84,6 +87,11 @@ struct DevMesh {
     const int32_t* cfs;      // [nc] bit k set if the cell owns local face k
     const TrkF* trk_f;       // [nc]
     const TrkD* trk_d;       // [nc]
+    // second-order reconstruction (order 2)
+    const double* lsq_c;     // [12][nc]: gradient = sum_k c_k (v_k - v_i), c_k at [(3k+d) nc + i]
+    const double* lsq_dxf;   // [12][nc]: face centroid minus cell centroid for local face k
+    const double* eps2;      // [nc] Venkatakrishnan epsilon^2 = (K h)^3
+    const int32_t* f_lk;     // [nf] owner's local face | neighbour's local face << 2
     const int32_t* face_order;  // [nf] interior faces, then boundary faces grouped by type
     const int32_t* f_own;    // [nf]
     const int32_t* f_nbr;    // [nf] >= 0 tet, else -1 - boundary index
@@ -132,6 +140,8 @@ struct DevState {
     int64_t* wacc;        // [5][nc] fixed-point scratch for W^p
     double* mom;          // [5][nc] staging of moments copied to the host
     double* F;            // [5][nf]
+    double* gradW;        // [15][nc] limited gradients of W, [(3q+d) nc + i] (order 2)
+    double* gradH;        // [3][nc] limited gradient of rho^h (order 2)
     int2* bsum;           // [n_scan_blocks] block sums of (count, N_sam)
     double* t;            // [1]
     double* dt;           // [1]
@@ -145,7 +155,7 @@ struct MeshHost {
     std::vector<int32_t> cf;       // [4*nc] face of local face k (cell-major)
     std::vector<int8_t> cf_sign;   // [4*nc]
     std::vector<int32_t> f_own, f_own_k, f_nbr, f_nbr_k, f_tag;  // f_nbr < 0 for boundary
-    std::vector<double> f_n, f_area, f_d, f_t1, f_t2;            // [3*nf] / [nf]
+    std::vector<double> f_n, f_area, f_d, f_t1, f_t2, f_c;       // [3*nf] / [nf]
     std::vector<double> vol, dS;                                 // [nc], [3*nc]
     std::vector<int32_t> bf_of_face;                             // [nf] boundary index or -1
     std::vector<int32_t> face_of_bf;                             // [nbf]
@@ -170,6 +180,7 @@ void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const
 void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
                    cudaStream_t st);
 void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
+void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_rebuild_survivors(const DevMesh& m, const DevState& s, const DevParams& p,
                               const PartBufRaw& a, cudaStream_t st);

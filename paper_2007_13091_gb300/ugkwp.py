@@ -24,7 +24,7 @@ FP64, MIXED = 0, 1
 PRECISION = {"fp64": FP64, "mixed": MIXED}
 W, WP, WH, PRIM = 0, 1, 2, 3
 LAST = {"dt": 0, "tau": 1, "rho_h": 2, "n_sam": 3, "m_sam": 4, "flux": 5, "pflux": 6, "surv_mass": 7,
-        "surv_count": 8}
+        "surv_count": 8, "grad_W": 9, "grad_rho_h": 10}
 
 
 class UgkwpError(RuntimeError):
@@ -80,7 +80,7 @@ class AdjointReq(ctypes.Structure):
                 ("n_wall_tags", ctypes.c_int32)]
 
 
-KERNELS = ["reset", "cell_prep", "sample_count", "scan", "scatter", "sample", "track", "flux", "update", "movers"]
+KERNELS = ["reset", "cell_prep", "sample_count", "scan", "scatter", "sample", "track", "flux", "update", "movers", "gradients"]
 
 EXPORTED = ["ugkwp_time_step_noalloc", "ugkwp_timing_enable", "ugkwp_timing_read", "ugkwp_mesh_load", "ugkwp_mesh_free", "ugkwp_query_sizes", "ugkwp_init", "ugkwp_free", "ugkwp_step",
             "ugkwp_sync", "ugkwp_moments", "ugkwp_state_info", "ugkwp_export_state", "ugkwp_import_state",
@@ -265,7 +265,8 @@ def ugkwp_last(sim, which: str, n_cells: int, n_faces: int):
     code = LAST[which]
     shape, dt = {0: ((1,), np.float64), 1: ((n_cells,), np.float64), 2: ((n_cells,), np.float64),
                  3: ((n_cells,), np.int64), 4: ((n_cells,), np.float64), 5: ((5, n_faces), np.float64),
-                 6: ((5, n_cells), np.int64), 7: ((n_cells,), np.int64), 8: ((n_cells,), np.int64)}[code]
+                 6: ((5, n_cells), np.int64), 7: ((n_cells,), np.int64), 8: ((n_cells,), np.int64),
+                 9: ((5, 3, n_cells), np.float64), 10: ((3, n_cells), np.float64)}[code]
     out = np.empty(shape, dtype=dt)
     _check(lib().ugkwp_last(sim, code, out.ctypes.data))
     return float(out[0]) if code == 0 else out

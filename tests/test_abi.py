@@ -68,10 +68,12 @@ def test_mesh_validation_errors():
 def test_parameter_validation():
     cfg = wl.uniform_box(n=(2, 2, 2))
     mesh = ugkwp.ugkwp_mesh_load(cfg["mesh"])
-    for key, val, pat in (("CFL", 1.5, "CFL"), ("N_ref", 0, "N_ref"), ("order", 2, "first-order"),
+    for key, val, pat in (("CFL", 1.5, "CFL"), ("N_ref", 0, "N_ref"), ("order", 3, "order must be"),
                           ("particle_capacity", 2 ** 31, "capacity"), ("Pr", 0.7, "BGK")):
         with pytest.raises(ugkwp.UgkwpError, match=pat):
             ugkwp.ugkwp_query_sizes(mesh, dict(cfg["params"], **{key: val}))
+    with pytest.raises(ugkwp.UgkwpError, match="venkat_K"):
+        ugkwp.ugkwp_query_sizes(mesh, dict(cfg["params"], order=2, venkat_K=-1.0))
     with pytest.raises(ugkwp.UgkwpError, match="no entry"):
         ugkwp.ugkwp_query_sizes(mesh, dict(cfg["params"], bc=[]))
 

@@ -120,6 +120,66 @@ def test_cube_farfield_jittered_teacher_forced(precision):
     assert c["n_exited"] > 0 and c["n_wall_hits"] > 0
 
 
+def _order2(cfg, K):
+    cfg["params"]["order"] = 2
+    cfg["params"]["venkat_K"] = K
+    return cfg
+
+
+def _assert_gradients_close(gsim, gW, gH):
+    """Limited gradients of the last step against the oracle's: each component
+    within 1e-11 of the larger of its own norm and 1e-3 of the momentum one."""
+    Gg, Hg = gsim.last("grad_W"), gsim.last("grad_rho_h")
+    mom = np.linalg.norm(gW[1:4])
+    for q in range(5):
+        scale = max(np.linalg.norm(gW[q]), 1e-3 * mom)
+        assert np.linalg.norm(Gg[q] - gW[q]) <= 1e-11 * scale, q
+    assert np.linalg.norm(Hg - gH) <= 1e-11 * np.linalg.norm(gH)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_order2_shock_tube_teacher_forced(precision):
+    """Second-order wave flux (Sec. 2.1): least-squares gradients with
+    Venkatakrishnan's limiter at interior faces, specular and far-field ghosts."""
+    cfg = _order2(wl.shock_tube(precision=precision), K=1.0)
+    osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    osim.step(3)
+    gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    gsim.set_state(osim.state())
+    osim.prepare()
+    gW, gH = osim.gradients(limited=True)
+    osim.step()
+    gsim.step()
+    compare_step(gsim, osim)
+    _assert_gradients_close(gsim, gW, gH)
+
+
+@pytest.mark.parametrize("K", [0.3, 5.0])
+def test_order2_cube_jittered_teacher_forced(K):
+    """Jittered graded tets (several blocks and a ragged tail), far field and a
+    diffuse wall; K = 0.3 keeps the limiter active, K = 5 mostly relaxes it."""
+    cfg = _order2(wl.cube_flow(h0=0.5, growth=2.0, N_ref=30, precision="mixed", Kn=0.1), K=K)
+    osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    osim.step(2)
+    gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    gsim.set_state(osim.state())
+    osim.prepare()
+    gW, gH = osim.gradients(limited=True)
+    ref, _ = osim.gradients(limited=False)
+    osim.step()
+    gsim.step()
+    compare_step(gsim, osim)
+    _assert_gradients_close(gsim, gW, gH)
+    if K < 1.0:  # the limiter acts on a share of the cells
+        assert np.mean(np.abs(gW - ref).max(axis=(0, 1)) > 1e-6 * np.abs(ref).max()) > 0.05
+
+
+def test_order2_cavity_teacher_forced():
+    cfg = _order2(wl.cavity(n=6, N_ref=40, precision="mixed"), K=5.0)
+    gsim, osim = run_teacher_forced(cfg, warm_steps=3)
+    assert osim.last("counters")["n_wall_hits"] > 0
+
+
 def test_specular_box_degenerate_starts():
     """Particles placed exactly on nodes, edges and faces (teacher-forced import)."""
     cfg = wl.uniform_box(n=(3, 3, 3), Kn=0.5, N_ref=10, bc_type="specular")
