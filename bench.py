@@ -53,9 +53,14 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# reconstruction order of the workload (2: least-squares gradients with
+# Venkatakrishnan's limiter, the scheme of the paper's cavity; --order 1 for zero slopes)
+ORDER = 2
+
+
 def workload(precision, seed=None):
     from paper_2007_13091_gb300 import workloads as wl
-    cfg = wl.cavity(n=24, Kn=0.075, N_ref=100, precision=precision)
+    cfg = wl.cavity(n=24, Kn=0.075, N_ref=100, precision=precision, order=ORDER)
     if seed is not None:
         cfg["params"]["seed"] = seed
     return cfg
@@ -251,7 +256,7 @@ def cpu_baseline(steps):
         moves += s.last("counters")["n_tracked"]
     t1 = time.perf_counter()
     return {"value": moves / (t1 - t0), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"cavity 24^3x6 tets, N_ref 100, MIXED: {steps} oracle steps after one sampling step "
+            "sample": f"cavity 24^3x6 tets, N_ref 100, MIXED, order {ORDER}: {steps} oracle steps after one sampling step "
                       f"({moves} particle moves, {t1 - t0:.1f} s)",
             "cell_steps_per_s": len(cfg["mesh"]["tets"]) * steps / (t1 - t0)}
 
@@ -276,6 +281,7 @@ def run_reference(args, ws, rank):
             "warmup": warm, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 cells / f32 particles (oracle)", "data": "synthetic",
             "config": {"workload": "lid-driven cavity 24^3 hexes x 6 = 82944 tets, Kn 0.075, N_ref 100, MIXED",
+                       "order": ORDER,
                        "sample": f"{steps} of the requested {args.steps} steps (CPU oracle, single thread)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{steps} oracle steps after {warm} warm-up step(s), {moves} moves"},
@@ -292,7 +298,10 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip FP64, field error, e2e and CPU baseline")
     ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--order", type=int, default=2, choices=[1, 2], help="reconstruction order of the workload")
     args = ap.parse_args()
+    global ORDER
+    ORDER = args.order
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -334,7 +343,7 @@ def main():
            "data": "synthetic",
            "config": {"workload": "lid-driven cavity 24^3 hexes x 6 = 82944 tets, argon-like VHS gas, Kn 0.075, "
                                   "diffuse walls, lid Mach 0.16, N_ref 100",
-                      "precision": args.precision, "n_cells": nc, "particles_per_step": int(moves_per_step),
+                      "precision": args.precision, "order": ORDER, "n_cells": nc, "particles_per_step": int(moves_per_step),
                       "l2": "inputs larger than L2 (particle SoA %.2f GB per buffer)" % (moves_per_step * 44 / 1e9),
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "cell_steps_per_s": cell_steps,

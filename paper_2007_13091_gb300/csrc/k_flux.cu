@@ -20,8 +20,6 @@ namespace ugkwp {
 
 namespace {
 
-constexpr double PI = 3.14159265358979323846;
-
 struct Side {
     double rho, rhoh, Un, Ut[3], lam, p, rl;  // rl = 1/sqrt(lambda)
 };
@@ -146,8 +144,14 @@ __device__ void interior_flux(const Side& L, const Side& R, bool ghost_hydro, co
 // coefficients c_k, ghosts mirrored across boundary faces) limited with
 // Venkatakrishnan's function, per conservative component and for rho^h.
 
-__device__ __forceinline__ double venkat(double d1, double d2, double eps2) {
-    return ((d1 * d1 + eps2) * d2 + 2.0 * d2 * d2 * d1) / (d2 * (d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + eps2));
+// Venkatakrishnan's function of the allowed difference d1 and the extrapolated
+// difference d2 (same sign, d2 != 0) as the ratio num/den with den > 0:
+// num/den = ((d1^2 + eps^2) d2 + 2 d2^2 d1) / (d2 (d1^2 + 2 d2^2 + d1 d2 + eps^2)).
+// d1^2 + d1 d2 + 2 d2^2 > 0 for d2 != 0, so den has the sign of d2.
+__device__ __forceinline__ void venkat_ratio(double d1, double d2, double eps2, double& num, double& den) {
+    num = (d1 * d1 + eps2) * d2 + 2.0 * d2 * d2 * d1;
+    den = d2 * (d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + eps2);
+    if (den < 0.0) { num = -num; den = -den; }
 }
 
 __global__ void __launch_bounds__(256) k_gradients(DevMesh m, DevState s, DevParams p) {
@@ -189,15 +193,18 @@ __global__ void __launch_bounds__(256) k_gradients(DevMesh m, DevState s, DevPar
             for (int d = 0; d < 3; ++d) g[d] += m.lsq_c[(size_t)(3 * k + d) * nc + i] * (val[k] - self);
         double vmax = self, vmin = self;
         for (int k = 0; k < 4; ++k) { vmax = fmax(vmax, val[k]); vmin = fmin(vmin, val[k]); }
-        double phi = 1.0;
+        // phi = min(1, min_k num_k/den_k), compared by cross products (den > 0)
+        // so that only the chosen ratio is divided
+        double bn = 1.0, bd = 1.0;
         for (int k = 0; k < 4; ++k) {
             const double d2 = g[0] * m.lsq_dxf[(size_t)(3 * k) * nc + i] + g[1] * m.lsq_dxf[(size_t)(3 * k + 1) * nc + i] +
                               g[2] * m.lsq_dxf[(size_t)(3 * k + 2) * nc + i];
-            double pk = 1.0;
-            if (d2 > 0.0) pk = venkat(vmax - self, d2, eps2);
-            else if (d2 < 0.0) pk = venkat(vmin - self, d2, eps2);
-            phi = fmin(phi, pk);
+            if (d2 == 0.0) continue;
+            double num, den;
+            venkat_ratio(d2 > 0.0 ? vmax - self : vmin - self, d2, eps2, num, den);
+            if (num * bd < bn * den) { bn = num; bd = den; }
         }
+        const double phi = bn / bd;
         for (int d = 0; d < 3; ++d) {
             if (q < 5) s.gradW[(size_t)(3 * q + d) * nc + i] = phi * g[d];
             else s.gradH[(size_t)d * nc + i] = phi * g[d];
@@ -233,18 +240,37 @@ __device__ __forceinline__ void make_tab(const double* U, double lam, double rl,
 }
 
 // out_k = < u^AL v^BE w^GA (a.psi) psi_k >, psi = (1, u, v, w, |u|^2/2).
+// With a.psi = A_u(u) + A_v(v) + A_w(w), A_u = a0 + a1 u + a4 u^2/2,
+// A_v = a2 v + a4 v^2/2, A_w = a3 w + a4 w^2/2, every moment factorises into
+// 1D tables: <u^x v^y w^z a.psi> = NA_x v_y w_z + n_x (VA_y w_z + v_y WA_z).
 template <int AL, int BE, int GA>
 __device__ __forceinline__ void apsi(const Tab& T, const double* a, double out[5]) {
-#define MM(x, y, z) (T.n[AL + (x)] * T.v[BE + (y)] * T.w[GA + (z)])
-#define PP(x, y, z) (a[0] * MM(x, y, z) + a[1] * MM((x) + 1, y, z) + a[2] * MM(x, (y) + 1, z) + \
-                     a[3] * MM(x, y, (z) + 1) + 0.5 * a[4] * (MM((x) + 2, y, z) + MM(x, (y) + 2, z) + MM(x, y, (z) + 2)))
-    out[0] = PP(0, 0, 0);
-    out[1] = PP(1, 0, 0);
-    out[2] = PP(0, 1, 0);
-    out[3] = PP(0, 0, 1);
-    out[4] = 0.5 * (PP(2, 0, 0) + PP(0, 2, 0) + PP(0, 0, 2));
-#undef PP
-#undef MM
+    const double h4 = 0.5 * a[4];
+    double NA[3], VA[3], WA[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        NA[i] = a[0] * T.n[AL + i] + a[1] * T.n[AL + i + 1] + h4 * T.n[AL + i + 2];
+        VA[i] = a[2] * T.v[BE + i + 1] + h4 * T.v[BE + i + 2];
+        WA[i] = a[3] * T.w[GA + i + 1] + h4 * T.w[GA + i + 2];
+    }
+#define SS(x, y, z) (NA[x] * T.v[BE + (y)] * T.w[GA + (z)] + \
+                     T.n[AL + (x)] * (VA[y] * T.w[GA + (z)] + T.v[BE + (y)] * WA[z]))
+    out[0] = SS(0, 0, 0);
+    out[1] = SS(1, 0, 0);
+    out[2] = SS(0, 1, 0);
+    out[3] = SS(0, 0, 1);
+    out[4] = 0.5 * (SS(2, 0, 0) + SS(0, 2, 0) + SS(0, 0, 2));
+#undef SS
+}
+
+// out_k = < u^AL psi_k > (a = e_0).
+template <int AL>
+__device__ __forceinline__ void psi_mom(const Tab& T, double out[5]) {
+    out[0] = T.n[AL];
+    out[1] = T.n[AL + 1];
+    out[2] = T.n[AL] * T.v[1];
+    out[3] = T.n[AL] * T.w[1];
+    out[4] = 0.5 * (T.n[AL + 2] + T.n[AL] * (T.v[2] + T.w[2]));
 }
 
 // <u_n u_d (a.psi) psi> for frame direction d (0 normal, 1 t1, 2 t2)
@@ -258,8 +284,7 @@ __device__ __forceinline__ void slope_mom(const Tab& T, int d, const double* a, 
 // in closed form: with theta = 1/(2 lambda), R_i = b_i - U_i b_0,
 // R_4 = 2 b_4 - (|U|^2 + 3 theta) b_0:  a_4 = 4 lambda^2/3 (R_4 - 2 U.R),
 // a_i = 2 lambda R_i - U_i a_4,  a_0 = b_0 - U.a - a_4 (|U|^2 + 3 theta)/2.
-__device__ __forceinline__ void micro(const double* U, double lam, const double* b, double* a) {
-    const double th = 0.5 / lam;
+__device__ __forceinline__ void micro(const double* U, double lam, double th, const double* b, double* a) {
     const double R1 = b[1] - U[0] * b[0], R2 = b[2] - U[1] * b[0], R3 = b[3] - U[2] * b[0];
     const double U2 = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
     const double R4 = 2.0 * b[4] - (U2 + 3.0 * th) * b[0];
@@ -334,50 +359,127 @@ __device__ __forceinline__ void frame_slope(const double* gW, int nc, int c, con
     out[4] = g[4];
 }
 
-struct SideF {
-    double W[5];  // frame state at the face
-    double rhoh, U[3], lam, rl;
-    bool o2;      // reconstructed (else first order: zero slopes)
+// Equilibrium slope terms in closed form.  For the unit-density Maxwellian
+// (U, theta = 1/(2 lambda)) and a micro slope a with <psi psi^T> a = b, the
+// product (a.psi) g is the derivative of g(W) along b, so every slope moment is
+// the derivative of a Maxwellian moment along b, with
+// d rho = b0, dU = b_{1..3} - U b0, d theta = (2 b4 - (|U|^2 + 3 theta) b0 - 2 U.dU)/3:
+//   <u_D (a.psi) psi>     = dF_D(b), F_D the Euler flux along D,
+//   <u_n u_D (a.psi) psi> = dQ_D(b), Q_D = <u_n u_D psi g> with
+//   <u_i u_j> = U_i U_j + theta d_ij,
+//   <u_i u_j u_k> = U_i U_j U_k + theta (U_i d_jk + U_j d_ik + U_k d_ij),
+//   <u_i u_j |u|^2/2> = (U_i U_j (|U|^2 + 7 theta) + d_ij theta (|U|^2 + 5 theta))/2.
+// The face frame has the normal as direction 0.
+struct DPrim { double dr, dU[3], dth, UdU; };
+
+__device__ __forceinline__ DPrim dprim(const double* U, double th, double U2, const double* b) {
+    DPrim q;
+    q.dr = b[0];
+    for (int j = 0; j < 3; ++j) q.dU[j] = b[1 + j] - U[j] * b[0];
+    q.UdU = U[0] * q.dU[0] + U[1] * q.dU[1] + U[2] * q.dU[2];
+    q.dth = ((2.0 * b[4] - (U2 + 3.0 * th) * b[0]) - 2.0 * q.UdU) * (1.0 / 3.0);
+    return q;
+}
+
+// dF_D(b) (Euler flux Jacobian along frame direction D applied to b)
+template <int D>
+__device__ __forceinline__ void euler_jac(const double* U, double th, double U2, const double* b, const DPrim& q,
+                                          double out[5]) {
+    out[0] = b[1 + D];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        double v = q.dr * (U[D] * U[j]) + q.dU[D] * U[j] + U[D] * q.dU[j];
+        if (j == D) v += q.dr * th + q.dth;
+        out[1 + j] = v;
+    }
+    out[4] = b[1 + D] * (0.5 * U2 + 2.5 * th) + U[D] * (q.UdU + 2.5 * q.dth);
+}
+
+// dQ_D(b) = <u_n u_D (a.psi) psi>
+template <int D>
+__device__ __forceinline__ void q_jac(const double* U, double th, double U2, const DPrim& q, double out[5]) {
+    const double un_ud = U[0] * U[D];
+    const double d_un_ud = q.dU[0] * U[D] + U[0] * q.dU[D];
+    out[0] = q.dr * un_ud + d_un_ud;
+    if (D == 0) out[0] += q.dr * th + q.dth;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        // Q = U_n U_D U_j + theta (U_n d_Dj + U_D d_nj + U_j d_nD)
+        double s = 0.0, ds = 0.0;  // sum of the delta-selected velocities and its derivative
+        if (D == j) { s += U[0]; ds += q.dU[0]; }
+        if (j == 0) { s += U[D]; ds += q.dU[D]; }
+        if (D == 0) { s += U[j]; ds += q.dU[j]; }
+        out[1 + j] = q.dr * (un_ud * U[j] + th * s) + d_un_ud * U[j] + un_ud * q.dU[j] + q.dth * s + th * ds;
+    }
+    const double A = U2 + 7.0 * th;
+    double v = q.dr * (0.5 * un_ud * A) + 0.5 * (d_un_ud * A + un_ud * (2.0 * q.UdU + 7.0 * q.dth));
+    if (D == 0) {
+        const double Bq = U2 + 5.0 * th;
+        v += q.dr * (0.5 * th * Bq) + 0.5 * (q.dth * Bq + th * (2.0 * q.UdU + 5.0 * q.dth));
+    }
+    out[4] = v;
+}
+
+// One side of an interior face at second order, in the face frame: the
+// reconstructed state (first order if not positive), its half-space moments
+// H = <psi>, G = <u_n psi>, the slope part S = sum_d <u_n u_d (a^h_d.psi) psi>
+// of its hydrodynamic wave (a^h_d solved from grad_d W^h, W^h = (rho^h/rho) W),
+// and half of its frame slopes of W (the equilibrium slope averages both sides).
+struct SideOut {
+    double rho, rhoh, p;
+    double H[5], G[5], S[5];
 };
 
-__device__ __forceinline__ SideF make_sideF(const DevMesh& m, const DevState& s, int c, const double* dx,
-                                            const double R[3][3]) {
+__device__ __forceinline__ SideOut side_o2(const DevMesh& m, const DevState& s, int c, const double* dx,
+                                           const double R[3][3], int half, double B[3][5], bool first) {
     const int nc = m.nc;
-    SideF S;
     double Wf[5];
     for (int q = 0; q < 5; ++q)
         Wf[q] = s.W[(size_t)q * nc + c] + s.gradW[(size_t)(3 * q) * nc + c] * dx[0] +
                 s.gradW[(size_t)(3 * q + 1) * nc + c] * dx[1] + s.gradW[(size_t)(3 * q + 2) * nc + c] * dx[2];
     double rh = s.rhoh[c] + s.gradH[c] * dx[0] + s.gradH[nc + c] * dx[1] + s.gradH[2 * nc + c] * dx[2];
     double pr = (Wf[4] - 0.5 * (Wf[1] * Wf[1] + Wf[2] * Wf[2] + Wf[3] * Wf[3]) / Wf[0]) * (2.0 / 3.0);
-    S.o2 = Wf[0] > 0.0 && pr > 0.0;
-    if (!S.o2) {
+    const bool o2 = Wf[0] > 0.0 && pr > 0.0;
+    if (!o2) {
         for (int q = 0; q < 5; ++q) Wf[q] = s.W[(size_t)q * nc + c];
         rh = s.rhoh[c];
         pr = (Wf[4] - 0.5 * (Wf[1] * Wf[1] + Wf[2] * Wf[2] + Wf[3] * Wf[3]) / Wf[0]) * (2.0 / 3.0);
     }
-    S.W[0] = Wf[0];
-    for (int j = 0; j < 3; ++j) S.W[1 + j] = R[j][0] * Wf[1] + R[j][1] * Wf[2] + R[j][2] * Wf[3];
-    S.W[4] = Wf[4];
-    S.rhoh = rh;
-    const double ir = 1.0 / S.W[0];
-    for (int j = 0; j < 3; ++j) S.U[j] = S.W[1 + j] * ir;
-    S.lam = 0.5 * S.W[0] / pr;
-    S.rl = rsqrt(S.lam);
-    return S;
-}
-
-// Hydrodynamic slope along dd of side S: grad((rho^h/rho) W) in the frame.
-__device__ __forceinline__ void hydro_slope(const DevMesh& m, const DevState& s, int c, const SideF& S,
-                                            const double R[3][3], int dd, double out[5]) {
-    if (!S.o2) { for (int q = 0; q < 5; ++q) out[q] = 0.0; return; }
-    const int nc = m.nc;
-    double dW[5];
-    frame_slope(s.gradW, nc, c, R, dd, dW);
-    const double gh = s.gradH[c] * R[dd][0] + s.gradH[nc + c] * R[dd][1] + s.gradH[2 * nc + c] * R[dd][2];
-    const double ratio = S.rhoh / S.W[0];
-    const double gr = (gh - ratio * dW[0]) / S.W[0];
-    for (int q = 0; q < 5; ++q) out[q] = ratio * dW[q] + S.W[q] * gr;
+    SideOut o;
+    double W[5];
+    W[0] = Wf[0];
+    for (int j = 0; j < 3; ++j) W[1 + j] = R[j][0] * Wf[1] + R[j][1] * Wf[2] + R[j][2] * Wf[3];
+    W[4] = Wf[4];
+    o.rho = W[0];
+    o.rhoh = rh;
+    o.p = pr;
+    const double ir = 1.0 / W[0];
+    const double U[3] = {W[1] * ir, W[2] * ir, W[3] * ir};
+    const double lam = 0.5 * W[0] / pr;
+    const double rl = rsqrt(lam);
+    const double th = 0.5 * rl * rl;
+    Tab T;
+    make_tab(U, lam, rl, half, T);
+    psi_mom<0>(T, o.H);
+    psi_mom<1>(T, o.G);
+    for (int k = 0; k < 5; ++k) o.S[k] = 0.0;
+    if (!o2) {
+        if (first) for (int dd = 0; dd < 3; ++dd) for (int q = 0; q < 5; ++q) B[dd][q] = 0.0;
+        return o;
+    }
+    const double ratio = rh * ir;
+    for (int dd = 0; dd < 3; ++dd) {
+        double dW[5], b[5], a[5], sm[5];
+        frame_slope(s.gradW, nc, c, R, dd, dW);
+        for (int q = 0; q < 5; ++q) B[dd][q] = first ? 0.5 * dW[q] : B[dd][q] + 0.5 * dW[q];
+        const double gh = s.gradH[c] * R[dd][0] + s.gradH[nc + c] * R[dd][1] + s.gradH[2 * nc + c] * R[dd][2];
+        const double gr = (gh - ratio * dW[0]) * ir;
+        for (int q = 0; q < 5; ++q) b[q] = ratio * dW[q] + W[q] * gr;
+        micro(U, lam, th, b, a);
+        slope_mom(T, dd, a, sm);
+        for (int k = 0; k < 5; ++k) o.S[k] += sm[k];
+    }
+    return o;
 }
 
 __device__ void interior_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p, int f, int o, int nb,
@@ -391,70 +493,54 @@ __device__ void interior_flux_o2(const DevMesh& m, const DevState& s, const DevP
         dxL[d] = m.lsq_dxf[(size_t)(3 * (lk & 3) + d) * nc + o];
         dxR[d] = m.lsq_dxf[(size_t)(3 * ((lk >> 2) & 3) + d) * nc + nb];
     }
-    const SideF L = make_sideF(m, s, o, dxL, R);
-    const SideF Rs = make_sideF(m, s, nb, dxR, R);
-    const double e0[5] = {1.0, 0.0, 0.0, 0.0, 0.0};
-    Tab T;
-    double HL[5], GL[5], HR[5], GR[5];
-    make_tab(L.U, L.lam, L.rl, +1, T);
-    apsi<0, 0, 0>(T, e0, HL);
-    apsi<1, 0, 0>(T, e0, GL);
-    make_tab(Rs.U, Rs.lam, Rs.rl, -1, T);
-    apsi<0, 0, 0>(T, e0, HR);
-    apsi<1, 0, 0>(T, e0, GR);
+    double B[3][5];
+    const SideOut L = side_o2(m, s, o, dxL, R, +1, B, true);
+    const SideOut Rs = side_o2(m, s, nb, dxR, R, -1, B, false);
     double W0[5];
-    for (int k = 0; k < 5; ++k) W0[k] = L.W[0] * HL[k] + Rs.W[0] * HR[k];
+    for (int k = 0; k < 5; ++k) W0[k] = L.rho * L.H[k] + Rs.rho * Rs.H[k];
     const double rho0 = W0[0], ir0 = 1.0 / rho0;
     const double U0[3] = {W0[1] * ir0, W0[2] * ir0, W0[3] * ir0};
     const double p0 = (W0[4] - 0.5 * rho0 * dot3(U0, U0)) * (2.0 / 3.0);
-    const double lam0 = 0.5 * rho0 / p0;
     const double T0 = p0 * ir0 / p.R;
     double tau = p.mu_ref * exp(p.omega * log(T0 * inv_Tref)) / p0;
-    if (p.C2 > 0.0) {
-        const double pl = 0.5 * L.W[0] / L.lam, prr = 0.5 * Rs.W[0] / Rs.lam;
-        tau += p.C2 * fabs(pl - prr) / fabs(pl + prr) * dt;
-    }
+    if (p.C2 > 0.0) tau += p.C2 * fabs(L.p - Rs.p) / fabs(L.p + Rs.p) * dt;
     const QC qc = time_coeffs_all(dt, tau);
     // free transport of the hydrodynamic wave, upwind, with slopes
-    for (int k = 0; k < 5; ++k) F[k] = qc.a4 * (L.rhoh * GL[k] + Rs.rhoh * GR[k]);
-    double sm[5], b[5], a[5];
-    make_tab(L.U, L.lam, L.rl, +1, T);
-    for (int dd = 0; dd < 3; ++dd) {
-        hydro_slope(m, s, o, L, R, dd, b);
-        micro(L.U, L.lam, b, a);
-        slope_mom(T, dd, a, sm);
-        for (int k = 0; k < 5; ++k) F[k] += qc.a5 * sm[k];
+    for (int k = 0; k < 5; ++k)
+        F[k] = qc.a4 * (L.rhoh * L.G[k] + Rs.rhoh * Rs.G[k]) + qc.a5 * (L.S[k] + Rs.S[k]);
+    // equilibrium part: q1 g0 + q2 u.g_x + q3 g_t, in closed form
+    const double th0 = p0 * ir0;
+    const double U20 = dot3(U0, U0);
+    F[0] += qc.q1 * W0[1];
+    for (int j = 0; j < 3; ++j) F[1 + j] += qc.q1 * (W0[1] * U0[j] + (j == 0 ? p0 : 0.0));
+    F[4] += qc.q1 * U0[0] * (W0[4] + p0);
+    double Wt[5], t5[5];
+    {
+        const DPrim q = dprim(U0, th0, U20, B[0]);
+        q_jac<0>(U0, th0, U20, q, t5);
+        for (int k = 0; k < 5; ++k) F[k] += qc.q2 * t5[k];
+        euler_jac<0>(U0, th0, U20, B[0], q, t5);
+        for (int k = 0; k < 5; ++k) Wt[k] = -t5[k];
     }
-    make_tab(Rs.U, Rs.lam, Rs.rl, -1, T);
-    for (int dd = 0; dd < 3; ++dd) {
-        hydro_slope(m, s, nb, Rs, R, dd, b);
-        micro(Rs.U, Rs.lam, b, a);
-        slope_mom(T, dd, a, sm);
-        for (int k = 0; k < 5; ++k) F[k] += qc.a5 * sm[k];
+    {
+        const DPrim q = dprim(U0, th0, U20, B[1]);
+        q_jac<1>(U0, th0, U20, q, t5);
+        for (int k = 0; k < 5; ++k) F[k] += qc.q2 * t5[k];
+        euler_jac<1>(U0, th0, U20, B[1], q, t5);
+        for (int k = 0; k < 5; ++k) Wt[k] -= t5[k];
     }
-    // equilibrium part: q1 g0 + q2 u.g_x + q3 g_t
-    make_tab(U0, lam0, rsqrt(lam0), 0, T);
-    double G0[5];
-    apsi<1, 0, 0>(T, e0, G0);
-    for (int k = 0; k < 5; ++k) F[k] += qc.q1 * rho0 * G0[k];
-    double a0[3][5], Wt[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int dd = 0; dd < 3; ++dd) {
-        double sL[5], sR[5];
-        if (L.o2) frame_slope(s.gradW, nc, o, R, dd, sL); else for (int q = 0; q < 5; ++q) sL[q] = 0.0;
-        if (Rs.o2) frame_slope(s.gradW, nc, nb, R, dd, sR); else for (int q = 0; q < 5; ++q) sR[q] = 0.0;
-        for (int q = 0; q < 5; ++q) b[q] = 0.5 * (sL[q] + sR[q]);
-        micro(U0, lam0, b, a0[dd]);
-        slope_mom(T, dd, a0[dd], sm);
-        for (int k = 0; k < 5; ++k) F[k] += qc.q2 * sm[k];
-        if (dd == 0) apsi<1, 0, 0>(T, a0[dd], sm);
-        else if (dd == 1) apsi<0, 1, 0>(T, a0[dd], sm);
-        else apsi<0, 0, 1>(T, a0[dd], sm);
-        for (int k = 0; k < 5; ++k) Wt[k] -= sm[k];
+    {
+        const DPrim q = dprim(U0, th0, U20, B[2]);
+        q_jac<2>(U0, th0, U20, q, t5);
+        for (int k = 0; k < 5; ++k) F[k] += qc.q2 * t5[k];
+        euler_jac<2>(U0, th0, U20, B[2], q, t5);
+        for (int k = 0; k < 5; ++k) Wt[k] -= t5[k];
     }
-    double At[5];
-    micro(U0, lam0, Wt, At);
-    apsi<1, 0, 0>(T, At, sm);
-    for (int k = 0; k < 5; ++k) F[k] += qc.q3 * sm[k];
+    {
+        const DPrim q = dprim(U0, th0, U20, Wt);
+        euler_jac<0>(U0, th0, U20, Wt, q, t5);
+        for (int k = 0; k < 5; ++k) F[k] += qc.q3 * t5[k];
+    }
     // back to the lab frame
     const double Fm[3] = {F[1], F[2], F[3]};
     for (int d = 0; d < 3; ++d) F[1 + d] = Fm[0] * R[0][d] + Fm[1] * R[1][d] + Fm[2] * R[2][d];

@@ -11,7 +11,8 @@ Conventions
   "bfaces": [nb,3] i32, "btags": [nb] i32 (index into params["bc"])}
 * W0 = [5, nc] f64 conservative state (rho, rho U, rho E) with
   rho E = 1/2 rho |U|^2 + 3/2 p (monatomic, K = 0), R = 1.
-* params = dict with R, mu_ref, T_ref, omega, CFL, C2, order, N_ref, N_min,
+* params = dict with R, mu_ref, T_ref, omega, CFL, C2, order (1, or 2 for the
+  least-squares reconstruction with Venkatakrishnan's limiter, venkat_K = 5), N_ref, N_min,
   precision ('fp64' | 'mixed'), seed, max_crossings, bc (list of dicts with
   type 'wall' | 'specular' | 'farfield' (alias 'inflow') | 'outflow', T_w,
   U_w, W_in) and
@@ -140,16 +141,16 @@ def centroids(nodes, tets):
 
 
 def _params(Kn, omega, CFL, N_ref, precision, seed, bc, C2=0.0, N_min=0, capacity=None,
-            n_cells=None, max_crossings=1000):
+            n_cells=None, max_crossings=1000, order=1):
     cap = capacity if capacity is not None else int(3 * N_ref * n_cells + 4096)
     return {"R": 1.0, "mu_ref": mu_ref_vhs(Kn, omega), "T_ref": 1.0, "omega": omega, "CFL": CFL,
-            "C2": C2, "order": 1, "venkat_K": 5.0, "N_ref": N_ref, "N_min": N_min, "precision": precision,
+            "C2": C2, "order": order, "venkat_K": 5.0, "N_ref": N_ref, "N_min": N_min, "precision": precision,
             "seed": seed, "max_crossings": max_crossings, "bc": bc, "particle_capacity": cap,
             "Kn": Kn}
 
 
 def shock_tube(nx=100, ny=4, nz=4, Kn=1e-2, N_ref=50, precision="fp64", CFL=0.5, seed=1,
-               omega=0.81, C2=0.0, length=1.0, width=0.04):
+               omega=0.81, C2=0.0, length=1.0, width=0.04, order=1):
     """3D Sod tube [0,1] x [0,0.04]^2: left rho=1, p=1; right rho=0.125, p=0.1;
     far-field (outflow) ends, specular side walls."""
     xs = np.linspace(0.0, length, nx + 1)
@@ -167,12 +168,12 @@ def shock_tube(nx=100, ny=4, nz=4, Kn=1e-2, N_ref=50, precision="fp64", CFL=0.5,
     WR = conservative(np.array(0.125), np.zeros(3), np.array(0.1))
     bc = [{"type": "farfield", "W_in": tuple(float(v) for v in WL)},
           {"type": "farfield", "W_in": tuple(float(v) for v in WR)}, {"type": "specular"}]
-    params = _params(Kn, omega, CFL, N_ref, precision, seed, bc, C2=C2, n_cells=len(tets))
+    params = _params(Kn, omega, CFL, N_ref, precision, seed, bc, C2=C2, n_cells=len(tets), order=order)
     return {"name": f"shock_tube_{nx}x{ny}x{nz}", "mesh": {"nodes": nodes, "tets": tets, "bfaces": bf,
             "btags": btags}, "W0": W0, "params": params}
 
 
-def cavity(n=24, Kn=0.075, N_ref=100, precision="mixed", CFL=0.5, seed=2, omega=0.81, lid_mach=0.16):
+def cavity(n=24, Kn=0.075, N_ref=100, precision="mixed", CFL=0.5, seed=2, omega=0.81, lid_mach=0.16, order=1):
     """Lid-driven cubic cavity: unit cube, all walls diffuse at T0 = 1, the z = 1
     lid moving at U = (lid_mach sqrt(gamma R T0), 0, 0); gas at rest, rho = 1."""
     xs = np.linspace(0.0, 1.0, n + 1)
@@ -182,7 +183,7 @@ def cavity(n=24, Kn=0.075, N_ref=100, precision="mixed", CFL=0.5, seed=2, omega=
     Ulid = lid_mach * math.sqrt(GAMMA)
     bc = [{"type": "wall", "T_w": 1.0, "U_w": (0.0, 0.0, 0.0)},
           {"type": "wall", "T_w": 1.0, "U_w": (Ulid, 0.0, 0.0)}]
-    params = _params(Kn, omega, CFL, N_ref, precision, seed, bc, n_cells=len(tets))
+    params = _params(Kn, omega, CFL, N_ref, precision, seed, bc, n_cells=len(tets), order=order)
     return {"name": f"cavity_{n}^3", "mesh": {"nodes": nodes, "tets": tets, "bfaces": bf, "btags": btags},
             "W0": W0, "params": params}
 
@@ -210,7 +211,7 @@ def graded_axis(lo, hi, c_lo, c_hi, h0, growth, h_max=None):
 
 
 def cube_flow(h0=1.0 / 42, growth=1.5, Kn=0.1, mach=4.0, N_ref=200, precision="mixed", CFL=0.5, seed=3,
-              omega=0.81, jitter_amount=0.1, h_max=None):
+              omega=0.81, jitter_amount=0.1, h_max=None, order=1):
     """Hypersonic flow past a unit cube [-0.5,0.5]^3 in the box [-6,10] x [-6,6]^2:
     graded hexes (spacing h0 on the cube, growing by `growth` away from it;
     the default gives 192,152 hexes, 1,152,912 tets), Kuhn tets, jittered
@@ -241,7 +242,7 @@ def cube_flow(h0=1.0 / 42, growth=1.5, Kn=0.1, mach=4.0, N_ref=200, precision="m
     bc = [{"type": "farfield", "W_in": tuple(float(v) for v in W_in)},
           {"type": "farfield", "W_in": tuple(float(v) for v in W_in)},
           {"type": "wall", "T_w": 1.0, "U_w": (0.0, 0.0, 0.0)}]
-    params = _params(Kn, omega, CFL, N_ref, precision, seed, bc, n_cells=len(tets))
+    params = _params(Kn, omega, CFL, N_ref, precision, seed, bc, n_cells=len(tets), order=order)
     return {"name": f"cube_ma{mach:g}_{len(tets)}tets", "mesh": {"nodes": nodes, "tets": tets, "bfaces": bf,
             "btags": btags}, "W0": W0, "params": params}
 

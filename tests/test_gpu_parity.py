@@ -332,11 +332,11 @@ def test_graph_replay_matches_direct_launches():
 
 @pytest.mark.parametrize("precision", ["mixed"])
 def test_cavity_full_size_teacher_forced(precision):
-    """The bench workload at full size (24^3 x 6 = 82,944 tets, ~8.4e6 particles)
-    on a side stream as the bench runs it: one step from the oracle's state
+    """The bench workload at full size (24^3 x 6 = 82,944 tets, ~8.4e6 particles,
+    second-order reconstruction) on a side stream as the bench runs it: one step from the oracle's state
     after its sampling step (graph replay equals direct launches, tested above)."""
     import torch
-    cfg = wl.cavity(n=24, N_ref=100, precision=precision)
+    cfg = wl.cavity(n=24, N_ref=100, precision=precision, order=2)
     osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
     osim.step(1)
     gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], stream=torch.cuda.Stream())
