@@ -46,6 +46,7 @@ def lib():
         vp, cp = ctypes.c_void_p, ctypes.c_char_p
         L.orc_math_d.argtypes = [ctypes.c_int, vp, vp, i64]
         L.orc_math_logf.argtypes = [vp, vp, i64]
+        L.orc_math_sincos2pi_f.argtypes = [vp, vp, vp, i64]
         L.orc_philox.argtypes = [vp, vp, vp]
         L.orc_qcoef.argtypes = [d, d, vp]
         L.orc_maxwell_moments.argtypes = [vp, d, vp, ctypes.c_int, vp, vp]
@@ -117,6 +118,15 @@ def logf(x):
     y = np.empty_like(x)
     lib().orc_math_logf(_ptr(x), _ptr(y), x.size)
     return y
+
+
+def sincos2pi_f(x):
+    """(sin 2 pi x, cos 2 pi x) in binary32, as the mixed-mode particles use them."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    sn = np.empty_like(x)
+    cs = np.empty_like(x)
+    lib().orc_math_sincos2pi_f(_ptr(x), _ptr(sn), _ptr(cs), x.size)
+    return sn, cs
 
 
 def philox(ctr, key):

@@ -16,7 +16,8 @@
 //             log m = 2 atanh f = 2 (f + f^3/3 + ... + f^23/23), |f| < 0.172.
 //   log_f     the same identity in binary32 (series up to f^11/11).
 //   sincos2pi sin/cos of 2*pi*u: exact reduction by quarter turns (4u - j),
-//             then Taylor series of sin and cos on [-pi/4, pi/4].
+//             then Taylor series of sin and cos on [-pi/4, pi/4]; sincos2pi_f
+//             the same in binary32 (sin to th^11/11!, cos to th^12/12!).
 //   philox    Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
 //             numbers: as easy as 1, 2, 3", SC'11): 10 rounds of two 64x64->128
 //             multiplies with the published multipliers and Weyl key bumps.
@@ -160,6 +161,36 @@ inline void sincos2pi_d(double u, double* s_out, double* c_out) {
     pc = pc * t2 + 0x1.5555555555555p-5;           // +1/4!
     pc = pc * t2 - 0x1.0000000000000p-1;           // -1/2!
     double cs = 1.0 + t2 * pc;
+    int quadrant = ((int)j) & 3;
+    switch (quadrant) {
+        case 0: *s_out = sn;  *c_out = cs;  break;
+        case 1: *s_out = cs;  *c_out = -sn; break;
+        case 2: *s_out = -sn; *c_out = -cs; break;
+        default: *s_out = -cs; *c_out = sn; break;
+    }
+}
+
+// Binary32 variant for particles of the mixed-precision mode.  4u and q - j
+// are exact for u on the 2^-24 grid of u01_f; |th| <= pi/4 in binary32 with
+// truncation errors th^13/13! and th^14/14! below 1e-11.
+inline void sincos2pi_f(float u, float* s_out, float* c_out) {
+    float q = 4.0f * u;
+    float j = std::floor(q + 0.5f);
+    float th = (q - j) * 0x1.921fb6p+0f;           // pi/2 in binary32
+    float t2 = th * th;
+    float ps = -0x1.ae6456p-26f;                   // -1/11!
+    ps = ps * t2 + 0x1.71de3ap-19f;                // +1/9!
+    ps = ps * t2 - 0x1.a01a02p-13f;                // -1/7!
+    ps = ps * t2 + 0x1.111112p-7f;                 // +1/5!
+    ps = ps * t2 - 0x1.555556p-3f;                 // -1/3!
+    float sn = th + (th * t2) * ps;
+    float pc = 0x1.1eed8ep-29f;                    // +1/12!
+    pc = pc * t2 - 0x1.27e4fcp-22f;                // -1/10!
+    pc = pc * t2 + 0x1.a01a02p-16f;                // +1/8!
+    pc = pc * t2 - 0x1.6c16c2p-10f;                // -1/6!
+    pc = pc * t2 + 0x1.555556p-5f;                 // +1/4!
+    pc = pc * t2 - 0x1p-1f;                        // -1/2!
+    float cs = 1.0f + t2 * pc;
     int quadrant = ((int)j) & 3;
     switch (quadrant) {
         case 0: *s_out = sn;  *c_out = cs;  break;

@@ -30,6 +30,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 namespace orc {
@@ -789,17 +790,34 @@ static TrackOut track(const Geom& g, const Planes<Real>& pl, const orc_params& P
             // Diffuse re-emission with full accommodation (reading): flux-weighted
             // normal speed sqrt(-2 R T_w ln eta), Gaussian tangential components.
             Ctr4 r = draw(P.seed, pt.id, step, TAG_WALL, (uint64_t)o.nwall);
-            double vn = std::sqrt(-2.0 * P.R * bc.T_w * log_d(u01_d(r.v[0])));
-            double rad = std::sqrt(-2.0 * log_d(u01_d(r.v[1])));
-            double sn, cs;
-            sincos2pi_d(u01_d(r.v[2]), &sn, &cs);
-            double sw = std::sqrt(P.R * bc.T_w);
-            const double* n = &g.f_n[3 * (size_t)f];
-            const double* t1 = &g.f_t1[3 * (size_t)f];
-            const double* t2 = &g.f_t2[3 * (size_t)f];
-            double v1 = dot3(bc.U_w, t1) + sw * (rad * cs);
-            double v2 = dot3(bc.U_w, t2) + sw * (rad * sn);
-            for (int c = 0; c < 3; ++c) u[c] = (Real)(((-vn) * n[c] + v1 * t1[c]) + v2 * t2[c]);
+            if constexpr (std::is_same<Real, float>::value) {
+                // mixed precision: binary32 arithmetic from the wall constants,
+                // the face frame and U_w.t rounded to binary32
+                const float c2 = (float)(-2.0 * P.R * bc.T_w);
+                const float sw = (float)std::sqrt(P.R * bc.T_w);
+                float vn = std::sqrt(c2 * log_f(u01_f(r.v[0])));
+                float rad = std::sqrt(-2.0f * log_f(u01_f(r.v[1])));
+                float sn, cs;
+                sincos2pi_f(u01_f(r.v[2]), &sn, &cs);
+                const double* n = &g.f_n[3 * (size_t)f];
+                const double* t1 = &g.f_t1[3 * (size_t)f];
+                const double* t2 = &g.f_t2[3 * (size_t)f];
+                float v1 = (float)dot3(bc.U_w, t1) + sw * (rad * cs);
+                float v2 = (float)dot3(bc.U_w, t2) + sw * (rad * sn);
+                for (int c = 0; c < 3; ++c) u[c] = ((-vn) * (float)n[c] + v1 * (float)t1[c]) + v2 * (float)t2[c];
+            } else {
+                double vn = std::sqrt(-2.0 * P.R * bc.T_w * log_d(u01_d(r.v[0])));
+                double rad = std::sqrt(-2.0 * log_d(u01_d(r.v[1])));
+                double sn, cs;
+                sincos2pi_d(u01_d(r.v[2]), &sn, &cs);
+                double sw = std::sqrt(P.R * bc.T_w);
+                const double* n = &g.f_n[3 * (size_t)f];
+                const double* t1 = &g.f_t1[3 * (size_t)f];
+                const double* t2 = &g.f_t2[3 * (size_t)f];
+                double v1 = dot3(bc.U_w, t1) + sw * (rad * cs);
+                double v2 = dot3(bc.U_w, t2) + sw * (rad * sn);
+                for (int c = 0; c < 3; ++c) u[c] = (Real)(((-vn) * n[c] + v1 * t1[c]) + v2 * t2[c]);
+            }
             o.nwall++;
         }
         for (int c = 0; c < 3; ++c) x0[c] = xh[c];
@@ -928,6 +946,46 @@ template <class Real> struct Sim : SimBase {
         double sig = std::sqrt(p.R * pr[i].T);
         const double *p0 = &g.xyz[3 * (size_t)g.tet[4 * i]], *p1 = &g.xyz[3 * (size_t)g.tet[4 * i + 1]];
         const double *p2 = &g.xyz[3 * (size_t)g.tet[4 * i + 2]], *p3 = &g.xyz[3 * (size_t)g.tet[4 * i + 3]];
+        if constexpr (std::is_same<Real, float>::value) {
+            // Mixed precision (reading): the particle arithmetic is binary32,
+            // from U and sqrt(RT) of the cell and the tet's first vertex and
+            // edge vectors rounded to binary32.
+            const float Uf[3] = {(float)pr[i].U[0], (float)pr[i].U[1], (float)pr[i].U[2]};
+            const float sigf = (float)sig;
+            float P0[3], E[3][3];
+            for (int c = 0; c < 3; ++c) {
+                P0[c] = (float)p0[c];
+                E[0][c] = (float)(p1[c] - p0[c]);
+                E[1][c] = (float)(p2[c] - p0[c]);
+                E[2][c] = (float)(p3[c] - p0[c]);
+            }
+            for (int64_t j = 0; j < ns / 2; ++j) {
+                uint64_t ida = make_id((uint64_t)step, (uint64_t)i, (uint64_t)(2 * j));
+                Ctr4 r = draw(p.seed, ida, (uint64_t)step, TAG_SVEL, 0);
+                float X[3], sn, cs;
+                float rad = std::sqrt(-2.0f * log_f(u01_f(r.v[0])));
+                sincos2pi_f(u01_f(r.v[1]), &sn, &cs);
+                X[0] = rad * cs; X[1] = rad * sn;
+                rad = std::sqrt(-2.0f * log_f(u01_f(r.v[2])));
+                sincos2pi_f(u01_f(r.v[3]), &sn, &cs);
+                X[2] = rad * cs;
+                for (int side = 0; side < 2; ++side) {
+                    Part<Real> pt;
+                    pt.id = ida + (uint64_t)side;
+                    pt.cell = i;
+                    pt.m = ms;
+                    for (int c = 0; c < 3; ++c) pt.u[c] = side == 0 ? Uf[c] + sigf * X[c] : Uf[c] - sigf * X[c];
+                    Ctr4 rp = draw(p.seed, pt.id, (uint64_t)step, TAG_SPOS, 0);
+                    float a = u01_f(rp.v[0]), b = u01_f(rp.v[1]), cc = u01_f(rp.v[2]);
+                    if (a + b > 1.0f) { a = 1.0f - a; b = 1.0f - b; }
+                    if (b + cc > 1.0f) { float tmp = cc; cc = 1.0f - a - b; b = 1.0f - tmp; }
+                    else if (a + b + cc > 1.0f) { float tmp = cc; cc = a + b + cc - 1.0f; a = 1.0f - b - tmp; }
+                    for (int c = 0; c < 3; ++c) pt.x[c] = P0[c] + ((a * E[0][c] + b * E[1][c]) + cc * E[2][c]);
+                    out.push_back(pt);
+                }
+            }
+            return;
+        }
         for (int64_t j = 0; j < ns / 2; ++j) {
                 uint64_t ida = make_id((uint64_t)step, (uint64_t)i, (uint64_t)(2 * j));
                 Ctr4 r = draw(p.seed, ida, (uint64_t)step, TAG_SVEL, 0);
@@ -1195,6 +1253,10 @@ void orc_math_d(int which, const double* x, double* y, int64_t n) {
 
 void orc_math_logf(const float* x, float* y, int64_t n) {
     for (int64_t k = 0; k < n; ++k) y[k] = log_f(x[k]);
+}
+
+void orc_math_sincos2pi_f(const float* x, float* s, float* c, int64_t n) {
+    for (int64_t k = 0; k < n; ++k) sincos2pi_f(x[k], &s[k], &c[k]);
 }
 
 void orc_philox(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {

@@ -101,3 +101,25 @@ def test_sincos2pi_within_2ulp():
         err_abs = np.abs(got[big] - ref[big]) <= 4e-16
         assert np.all((err <= 2.0) | err_abs)
     assert np.allclose(s * s + c * c, 1.0, rtol=0, atol=4e-16)
+
+
+def test_sincos2pi_f_against_libm_and_symmetry():
+    """Binary32 sin/cos(2 pi u) of the mixed-mode particles: within 3 binary32
+    ulps of the double-precision libm value (absolute 6e-8 near a zero), the
+    exact quarter-turn values, and the exact symmetry u -> 1 - u that a wrong
+    quadrant rotation or sign would break."""
+    k = np.arange(0, 2**23, 37, dtype=np.int64)
+    u = ((k + 0.5) * 2.0 ** -23).astype(np.float32)
+    s, c = oracle.sincos2pi_f(u)
+    ang = 2.0 * np.pi * u.astype(np.float64)
+    for got, ref in ((s, np.sin(ang)), (c, np.cos(ang))):
+        ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+        err = np.abs(got.astype(np.float64) - ref)
+        assert np.all((err <= 3.0 * ulp) | (err <= 6e-8))
+    assert np.abs(s.astype(np.float64) ** 2 + c.astype(np.float64) ** 2 - 1.0).max() < 3e-7
+    q = np.array([0.0, 0.25, 0.5, 0.75], dtype=np.float32)
+    sq, cq = oracle.sincos2pi_f(q)
+    assert np.array_equal(np.abs(sq), [0.0, 1.0, 0.0, 1.0]) and np.array_equal(np.abs(cq), [1.0, 0.0, 1.0, 0.0])
+    assert sq[1] == 1.0 and sq[3] == -1.0 and cq[0] == 1.0 and cq[2] == -1.0
+    s2, c2 = oracle.sincos2pi_f((1.0 - u.astype(np.float64)).astype(np.float32))
+    assert np.array_equal(s2, -s) and np.array_equal(c2, c)

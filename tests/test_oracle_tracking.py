@@ -116,3 +116,32 @@ def test_free_transport_time_draw():
         coll += out["status"] & 1
     p = 1 - np.exp(-dt / tau)
     assert abs(coll - n * p) < 5 * np.sqrt(n * p * (1 - p))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_diffuse_wall_reemission_law(precision):
+    """Diffuse re-emission with full accommodation (Sec. 2.4 (e)): a particle
+    that hits the x = 0 wall leaves with a flux-weighted half-Maxwellian of the
+    wall temperature, u_x^2 / (2 R T_w) ~ Exp(1), and Gaussian tangential
+    components N(0, R T_w); one draw per particle id."""
+    from scipy import stats
+    T_w = 2.0
+    cfg = wl.uniform_box(n=(2, 2, 2), bc_type="wall", T_w=T_w, precision=precision, Kn=1e6)
+    nodes, tets = cfg["mesh"]["nodes"], cfg["mesh"]["tets"]
+    s = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    cen = nodes[tets].mean(1)
+    c = int(np.argmin(cen[:, 0] + 10 * np.abs(cen[:, 1] - 0.25) + 10 * np.abs(cen[:, 2] - 0.25)))
+    x = cen[c].astype(np.float32).astype(np.float64)
+    speed = 16.0
+    dt = float(np.float32(x[0] / speed * (1 + 1e-4)))
+    out_u = []
+    for k in range(3000):
+        pid = (5 << 40) | (1 << 16) | k
+        out = s.track_one(pid=pid, cell=c, x=x, u=[-speed, 0.0, 0.0], tau_cell=1.0, dt=dt, step=5)
+        assert out["status"] == 0
+        out_u.append(out["u"])
+    U = np.array(out_u)
+    assert np.all(U[:, 0] > 0)
+    assert stats.kstest(U[:, 0] ** 2 / (2 * T_w), "expon").pvalue > 1e-4
+    for comp in (1, 2):
+        assert stats.kstest(U[:, comp] / np.sqrt(T_w), "norm").pvalue > 1e-4
