@@ -41,7 +41,7 @@ TRACK_BYTES_PER_CELL = {"mixed": 80 + 8, "fp64": 144 + 8}
 # DRAM bytes (read + write) of one k_track launch on this workload, from the ncu
 # capture summarised in profiles/k_track_k_face_flux_cavity24_mixed.md; set to
 # None whenever the kernel changes until it is captured again
-TRACK_DRAM_BYTES = {"mixed": 401.257728e6 + 130.182144e6, "fp64": None}
+TRACK_DRAM_BYTES = {"mixed": None, "fp64": None}
 
 
 def peaks():

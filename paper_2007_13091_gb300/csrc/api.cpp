@@ -118,6 +118,8 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, D
     if (rs == 4) M.trk_f = c.take<TrkF>(nc);
     else M.trk_d = c.take<TrkD>(nc);
     M.face_order = c.take<int32_t>(nf);
+    M.vtx_f = c.take<float>(12 * nc);
+    M.bf_f = c.take<float>(11 * (nbf ? nbf : 1));
     M.lsq_c = c.take<double>(12 * nc);
     M.lsq_dxf = c.take<double>(12 * nc);
     M.eps2 = c.take<double>(nc);
@@ -134,6 +136,7 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, D
     S.prim = c.take<double>(5 * nc);
     S.tau = c.take<double>(nc);
     S.tauf = c.take<float>(nc);
+    S.usig = c.take<float4>(nc);
     S.rhoh = c.take<double>(nc);
     S.rhop = c.take<double>(nc);
     S.nsam = c.take<int32_t>(nc);
@@ -357,6 +360,8 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
         P.bc[b].T_w = p->bc[b].T_w;
         for (int k = 0; k < 3; ++k) P.bc[b].U_w[k] = p->bc[b].U_w[k];
         for (int k = 0; k < 5; ++k) P.bc[b].W_in[k] = p->bc[b].W_in[k];
+        P.bc[b].c2rt_f = (float)(-2.0 * p->R * p->bc[b].T_w);
+        P.bc[b].sw_f = (float)std::sqrt(p->R * p->bc[b].T_w);
     }
     int32_t e[5];
     fixed_point_exponents(mh, *p, W0, e);
@@ -442,6 +447,30 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     for (int type = 1; type <= 4; ++type)
         for (int f = 0; f < nf; ++f)
             if (mh.f_nbr[f] < 0 && p->bc[mh.f_tag[f]].type == type) forder.push_back(f);
+    // binary32 images for the mixed mode: tet vertex 0 and edges (double
+    // differences rounded once), boundary-face frames and U_w.t (Sec. 2.4 (b), (e))
+    std::vector<float> vtxf(12 * (size_t)nc), bff(11 * (size_t)std::max(nbf, 1), 0.0f);
+    for (int i = 0; i < nc; ++i) {
+        const double* p0 = &mh.xyz[3 * (size_t)mh.tet[4 * (size_t)i]];
+        for (int d = 0; d < 3; ++d) vtxf[(size_t)d * nc + i] = (float)p0[d];
+        for (int k = 1; k < 4; ++k) {
+            const double* pk = &mh.xyz[3 * (size_t)mh.tet[4 * (size_t)i + k]];
+            for (int d = 0; d < 3; ++d) vtxf[(size_t)(3 * k + d) * nc + i] = (float)(pk[d] - p0[d]);
+        }
+    }
+    for (int b = 0; b < nbf; ++b) {
+        const int f = mh.face_of_bf[b];
+        const double* t1 = &mh.f_t1[3 * (size_t)f];
+        const double* t2 = &mh.f_t2[3 * (size_t)f];
+        for (int d = 0; d < 3; ++d) {
+            bff[(size_t)d * nbf + b] = (float)mh.f_n[3 * (size_t)f + d];
+            bff[(size_t)(3 + d) * nbf + b] = (float)t1[d];
+            bff[(size_t)(6 + d) * nbf + b] = (float)t2[d];
+        }
+        const double* Uw = p->bc[mh.f_tag[f]].U_w;
+        bff[(size_t)9 * nbf + b] = (float)((Uw[0] * t1[0] + Uw[1] * t1[1]) + Uw[2] * t1[2]);
+        bff[(size_t)10 * nbf + b] = (float)((Uw[0] * t2[0] + Uw[1] * t2[1]) + Uw[2] * t2[2]);
+    }
     for (int b = 0; b < nbf; ++b) {
         const int f = mh.face_of_bf[b];
         btag[b] = mh.f_tag[f];
@@ -489,6 +518,8 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     if (s->real_size == 4) { UP(s->M.trk_f, tf.data(), tf.size() * sizeof(TrkF)); }
     else { UP(s->M.trk_d, td.data(), td.size() * sizeof(TrkD)); }
     UP(s->M.face_order, forder.data(), nf * sizeof(int32_t));
+    UP(s->M.vtx_f, vtxf.data(), vtxf.size() * sizeof(float));
+    UP(s->M.bf_f, bff.data(), bff.size() * sizeof(float));
     UP(s->M.lsq_c, lsq_c.data(), lsq_c.size() * sizeof(double));
     UP(s->M.lsq_dxf, lsq_dxf.data(), lsq_dxf.size() * sizeof(double));
     UP(s->M.eps2, eps2.data(), eps2.size() * sizeof(double));

@@ -11,7 +11,8 @@
 //               log m = 2f (1 + s/3 + ... + s^11/23), s = f^2.
 //   f_log       the same identity in binary32, series to s^5/11.
 //   d_sincos2pi sin/cos of 2 pi u by exact quarter-turn reduction and the
-//               Taylor series of sin and cos on [-pi/4, pi/4].
+//               Taylor series of sin and cos on [-pi/4, pi/4]; f_sincos2pi the
+//               same in binary32 (sin to th^11/11!, cos to th^12/12!).
 //   philox      Philox4x64-10 of Salmon et al. (SC'11).
 #pragma once
 #include <cstdint>
@@ -156,6 +157,33 @@ __device__ __forceinline__ void d_sincos2pi(double u, double* sn_out, double* cs
     pc = pc * t2 + inv_fact(4);
     pc = pc * t2 - inv_fact(2);
     const double cs = 1.0 + t2 * pc;
+    const int quadrant = ((int)j) & 3;
+    if (quadrant == 0) { *sn_out = sn; *cs_out = cs; }
+    else if (quadrant == 1) { *sn_out = cs; *cs_out = -sn; }
+    else if (quadrant == 2) { *sn_out = -sn; *cs_out = -cs; }
+    else { *sn_out = -cs; *cs_out = sn; }
+}
+
+// Binary32 variant (mixed-mode particles): 4u and q - j are exact for u on
+// the 2^-24 grid of u01f.
+__device__ __forceinline__ void f_sincos2pi(float u, float* sn_out, float* cs_out) {
+    const float q = 4.0f * u;
+    const float j = floorf(q + 0.5f);
+    const float th = (q - j) * 0x1.921fb6p+0f;
+    const float t2 = th * th;
+    float ps = -0x1.ae6456p-26f;   // -1/11!
+    ps = ps * t2 + 0x1.71de3ap-19f;  // +1/9!
+    ps = ps * t2 - 0x1.a01a02p-13f;  // -1/7!
+    ps = ps * t2 + 0x1.111112p-7f;   // +1/5!
+    ps = ps * t2 - 0x1.555556p-3f;   // -1/3!
+    const float sn = th + (th * t2) * ps;
+    float pc = 0x1.1eed8ep-29f;    // +1/12!
+    pc = pc * t2 - 0x1.27e4fcp-22f;  // -1/10!
+    pc = pc * t2 + 0x1.a01a02p-16f;  // +1/8!
+    pc = pc * t2 - 0x1.6c16c2p-10f;  // -1/6!
+    pc = pc * t2 + 0x1.555556p-5f;   // +1/4!
+    pc = pc * t2 - 0x1p-1f;          // -1/2!
+    const float cs = 1.0f + t2 * pc;
     const int quadrant = ((int)j) & 3;
     if (quadrant == 0) { *sn_out = sn; *cs_out = cs; }
     else if (quadrant == 1) { *sn_out = cs; *cs_out = -sn; }

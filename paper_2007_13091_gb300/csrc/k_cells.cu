@@ -96,6 +96,8 @@ __global__ void k_cell_prep(DevMesh m, DevState s, DevParams p) {
         s.prim[4 * nc + i] = T;
         s.tau[i] = tau;
         s.tauf[i] = (float)tau;
+        if (p.precision == UGKWP_MIXED)
+            s.usig[i] = make_float4((float)Ux, (float)Uy, (float)Uz, (float)sqrt(p.R * T));
         s.rhop[i] = rhop;
         s.rhoh[i] = rho - rhop;
     }
@@ -298,16 +300,18 @@ inline int cdiv(long long a, int b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
 
-int particle_grid() {
+int sm_count() {
     static int g = 0;
     if (!g) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
-        g = sms * 8;
+        g = sms;
     }
     return g;
 }
+
+int particle_grid() { return sm_count() * 8; }
 
 void launch_reset(const DevMesh& m, const DevState& s, cudaStream_t st) {
     k_reset<<<cdiv(5LL * m.nc, 256) < 4096 ? cdiv(5LL * m.nc, 256) : 4096, 256, 0, st>>>(m, s);

@@ -16,6 +16,17 @@
 // Maxwellian moments use the recurrence <u^{k+2}> = U <u^{k+1}> + (k+1)/(2 lambda) <u^k>.
 #include "ugkwp_internal.hpp"
 
+// The second-order wave kernels are bound by the FP64 pipe, which a few warps
+// per SM saturate; they run as persistent grids of WAVE_BLOCKS_PER_SM blocks
+// per SM so that the particle kernels running beside them keep most of each
+// SM's registers and warp slots.
+#ifndef UGKWP_WAVE_BLOCKS_PER_SM
+#define UGKWP_WAVE_BLOCKS_PER_SM 1
+#endif
+#ifndef UGKWP_WAVE_THREADS
+#define UGKWP_WAVE_THREADS 128
+#endif
+
 namespace ugkwp {
 
 namespace {
@@ -154,10 +165,8 @@ __device__ __forceinline__ void venkat_ratio(double d1, double d2, double eps2, 
     if (den < 0.0) { num = -num; den = -den; }
 }
 
-__global__ void __launch_bounds__(256) k_gradients(DevMesh m, DevState s, DevParams p) {
+__device__ __forceinline__ void gradients_of_cell(const DevMesh& m, const DevState& s, const DevParams& p, int i) {
     const int nc = m.nc;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nc) return;
     int other[4], bidx[4];
     const int own = m.cfs[i];
     for (int k = 0; k < 4; ++k) {
@@ -210,6 +219,12 @@ __global__ void __launch_bounds__(256) k_gradients(DevMesh m, DevState s, DevPar
             else s.gradH[(size_t)d * nc + i] = phi * g[d];
         }
     }
+}
+
+__global__ void __launch_bounds__(UGKWP_WAVE_THREADS) k_gradients(DevMesh m, DevState s, DevParams p) {
+    const int nc = m.nc;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+        gradients_of_cell(m, s, p, i);
 }
 
 // Moment tables of a unit Maxwellian in a face frame: <u^k> (normal, over the
@@ -295,37 +310,22 @@ __device__ __forceinline__ void micro(const double* U, double lam, double th, co
     a[0] = b[0] - (U[0] * a[1] + U[1] * a[2] + U[2] * a[3]) - 0.5 * a[4] * (U2 + 3.0 * th);
 }
 
-// All time coefficients: q1, q2, q3, q4, a4, a5 (power series below x = 1).
+// All time coefficients: q1, q2, q3, q4, a4, a5 in closed form from one
+// expm1.  Where x = dt/tau is small the differences cancel, but their absolute
+// errors stay at rounding level of dt (q1, q4, a4) and dt^2 (q2, q3, a5), the
+// scales at which they enter the flux.
 struct QC { double q1, q2, q3, q4, a4, a5; };
 __device__ __forceinline__ QC time_coeffs_all(double dt, double tau) {
     QC c;
-    const double x = dt / tau;
-    if (x < 1.0) {
-        const double stop = x * x * x * 0x1p-60;  // smallest leading term is O(x^3)
-        double term = 1.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, sa4 = 0.0, sa5 = 0.0;
-#pragma unroll 1
-        for (int k = 1; k <= 30; ++k) {
-            term = term * x * c_inv_k[k];
-            const double sg = (k & 1) ? -1.0 : 1.0;
-            const double dk = (double)k;
-            if (k >= 2) { s1 += sg * term; sa4 += sg * (dk - 1.0) * term; }
-            if (k >= 3) { s2 += sg * (dk - 2.0) * term; s3 -= sg * term; sa5 += sg * 0.5 * (dk - 1.0) * (dk - 2.0) * term; }
-            s4 -= sg * term;
-            if (k >= 4 && term * dk * dk < stop) break;
-        }
-        const double t2 = tau * tau;
-        c.q1 = tau * s1; c.q2 = t2 * s2; c.q3 = t2 * s3; c.q4 = tau * s4; c.a4 = tau * sa4; c.a5 = t2 * sa5;
-    } else {
-        const double e = exp(-x);
-        const double ph = -expm1(-x);
-        c.q1 = dt - tau * ph;
-        c.q2 = 2.0 * tau * tau * ph - tau * dt - tau * dt * e;
-        c.q3 = 0.5 * dt * dt - tau * dt + tau * tau * ph;
-        c.q4 = tau * ph;
-        const double q5 = tau * dt * e - tau * tau * ph;
-        c.a4 = c.q4 - dt * e;
-        c.a5 = q5 + 0.5 * dt * dt * e;
-    }
+    const double em1 = expm1(-dt / tau);  // e^{-dt/tau} - 1
+    const double e = 1.0 + em1;
+    const double tdt = tau * dt;
+    c.q4 = -tau * em1;
+    c.q1 = dt - c.q4;
+    c.a4 = c.q4 - dt * e;
+    c.q2 = 2.0 * tau * c.q4 - tdt - tdt * e;
+    c.q3 = 0.5 * dt * dt - tdt + tau * c.q4;
+    c.a5 = (tdt * e - tau * c.q4) + 0.5 * dt * dt * e;
     return c;
 }
 
@@ -547,15 +547,17 @@ __device__ void interior_flux_o2(const DevMesh& m, const DevState& s, const DevP
 }
 
 // Second-order flux of the interior faces (the first nif entries of face_order).
-__global__ void __launch_bounds__(128) k_face_flux_o2(DevMesh m, DevState s, DevParams p) {
+__global__ void __launch_bounds__(UGKWP_WAVE_THREADS) k_face_flux_o2(DevMesh m, DevState s, DevParams p) {
     const int nf = m.nf;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= m.nif) return;
-    const int f = m.face_order[t];
-    const double n[3] = {m.f_n[f], m.f_n[nf + f], m.f_n[2 * nf + f]};
-    double F[5];
-    interior_flux_o2(m, s, p, f, m.f_own[f], m.f_nbr[f], n, s.dt[0], 1.0 / p.T_ref, F);
-    for (int q = 0; q < 5; ++q) s.F[(size_t)q * nf + f] = F[q];
+    const double dt = s.dt[0];
+    const double inv_Tref = 1.0 / p.T_ref;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.nif; t += gridDim.x * blockDim.x) {
+        const int f = m.face_order[t];
+        const double n[3] = {m.f_n[f], m.f_n[nf + f], m.f_n[2 * nf + f]};
+        double F[5];
+        interior_flux_o2(m, s, p, f, m.f_own[f], m.f_nbr[f], n, dt, inv_Tref, F);
+        for (int q = 0; q < 5; ++q) s.F[(size_t)q * nf + f] = F[q];
+    }
 }
 
 // First-order flux of the faces face_order[first..nf).
@@ -613,14 +615,20 @@ __global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevPar
 
 }  // namespace
 
+static int wave_grid(int n) {
+    const int cap = sm_count() * UGKWP_WAVE_BLOCKS_PER_SM;
+    const int need = (n + UGKWP_WAVE_THREADS - 1) / UGKWP_WAVE_THREADS;
+    return need < cap ? need : cap;
+}
+
 void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
-    k_gradients<<<(m.nc + 255) / 256, 256, 0, st>>>(m, s, p);
+    k_gradients<<<wave_grid(m.nc), UGKWP_WAVE_THREADS, 0, st>>>(m, s, p);
 }
 
 void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
     int first = 0;
     if (p.order == 2) {
-        if (m.nif > 0) k_face_flux_o2<<<(m.nif + 127) / 128, 128, 0, st>>>(m, s, p);
+        if (m.nif > 0) k_face_flux_o2<<<wave_grid(m.nif), UGKWP_WAVE_THREADS, 0, st>>>(m, s, p);
         first = m.nif;
     }
     if (m.nf > first) k_face_flux<<<(m.nf - first + 255) / 256, 256, 0, st>>>(m, s, p, first);

@@ -89,6 +89,49 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
         const int cell = lo;
         const int k = (int)(g - s.soff[cell]);
         const int side = k & 1;
+        const long long j = (long long)s.off[cell] + s.nleft[cell] + k;
+        if constexpr (sizeof(Real) == 4) {
+            // mixed mode: binary32 arithmetic from U, sqrt(RT) and the tet's
+            // vertex and edges rounded to binary32
+            const float4 us = s.usig[cell];
+            const unsigned long long ida = make_id(step, cell, k - side);
+            const dm::U4 r = dm::philox(ida, (unsigned long long)step, TAG_SVEL, 0ULL, p.seed, 0ULL);
+            float sn, cs, X[3];
+            float rad = sqrtf(-2.0f * dm::f_log(dm::u01f(r.a)));
+            dm::f_sincos2pi(dm::u01f(r.b), &sn, &cs);
+            X[0] = rad * cs;
+            X[1] = rad * sn;
+            rad = sqrtf(-2.0f * dm::f_log(dm::u01f(r.c)));
+            dm::f_sincos2pi(dm::u01f(r.d), &sn, &cs);
+            X[2] = rad * cs;
+            const unsigned long long id = ida + (unsigned long long)side;
+            const dm::U4 rp = dm::philox(id, (unsigned long long)step, TAG_SPOS, 0ULL, p.seed, 0ULL);
+            float a = dm::u01f(rp.a), bb = dm::u01f(rp.b), cc = dm::u01f(rp.c);
+            if (a + bb > 1.0f) { a = 1.0f - a; bb = 1.0f - bb; }
+            if (bb + cc > 1.0f) {
+                const float t = cc;
+                cc = 1.0f - a - bb;
+                bb = 1.0f - t;
+            } else if (a + bb + cc > 1.0f) {
+                const float t = cc;
+                cc = a + bb + cc - 1.0f;
+                a = 1.0f - bb - t;
+            }
+            const float U[3] = {us.x, us.y, us.z};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float P0 = m.vtx_f[(size_t)c * nc + cell];
+                const float E1 = m.vtx_f[(size_t)(3 + c) * nc + cell];
+                const float E2 = m.vtx_f[(size_t)(6 + c) * nc + cell];
+                const float E3 = m.vtx_f[(size_t)(9 + c) * nc + cell];
+                b.x[c][j] = P0 + ((a * E1 + bb * E2) + cc * E3);
+                b.u[c][j] = side == 0 ? U[c] + us.w * X[c] : U[c] - us.w * X[c];
+            }
+            b.m[j] = s.msam[cell];
+            b.cell[j] = cell;
+            b.id[j] = id;
+            continue;
+        }
         const double U[3] = {s.prim[nc + cell], s.prim[2 * nc + cell], s.prim[3 * nc + cell]};
         const double sig = sqrt(p.R * s.prim[4 * nc + cell]);
         const unsigned long long ida = make_id(step, cell, k - side);
@@ -115,7 +158,6 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
             cc = a + bb + cc - 1.0;
             a = 1.0 - bb - t;
         }
-        const long long j = (long long)s.off[cell] + s.nleft[cell] + k;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const double P0 = m.vtx[(size_t)c * nc + cell];
@@ -308,23 +350,39 @@ __global__ void __launch_bounds__(256, 3) k_track(DevMesh m, DevState s, DevPara
                     // tangential components U_w,t + sqrt(R T_w) N(0,1)
                     const dm::U4 r = dm::philox(id, (unsigned long long)step, TAG_WALL, (unsigned long long)nwall,
                                                 p.seed, 0ULL);
-                    const double vn = sqrt(-2.0 * p.R * bc.T_w * dm::d_log(dm::u01d(r.a)));
-                    const double rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.b)));
-                    double sn, cs;
-                    dm::d_sincos2pi(dm::u01d(r.c), &sn, &cs);
-                    const double sw = sqrt(p.R * bc.T_w);
-                    const int nbf = m.nbf;
-                    double n3[3], t1[3], t2[3];
+                    if constexpr (sizeof(Real) == 4) {
+                        // mixed mode: binary32 from the wall constants and the
+                        // face frame rounded to binary32
+                        const float vn = sqrtf(bc.c2rt_f * dm::f_log(dm::u01f(r.a)));
+                        const float rad = sqrtf(-2.0f * dm::f_log(dm::u01f(r.b)));
+                        float sn, cs;
+                        dm::f_sincos2pi(dm::u01f(r.c), &sn, &cs);
+                        const int nbf = m.nbf;
+                        const float v1 = m.bf_f[(size_t)9 * nbf + bi] + bc.sw_f * (rad * cs);
+                        const float v2 = m.bf_f[(size_t)10 * nbf + bi] + bc.sw_f * (rad * sn);
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        n3[c] = m.bf_n[(size_t)c * nbf + bi];
-                        t1[c] = m.bf_t1[(size_t)c * nbf + bi];
-                        t2[c] = m.bf_t2[(size_t)c * nbf + bi];
+                        for (int c = 0; c < 3; ++c)
+                            u[c] = ((-vn) * m.bf_f[(size_t)c * nbf + bi] + v1 * m.bf_f[(size_t)(3 + c) * nbf + bi]) +
+                                   v2 * m.bf_f[(size_t)(6 + c) * nbf + bi];
+                    } else {
+                        const double vn = sqrt(-2.0 * p.R * bc.T_w * dm::d_log(dm::u01d(r.a)));
+                        const double rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.b)));
+                        double sn, cs;
+                        dm::d_sincos2pi(dm::u01d(r.c), &sn, &cs);
+                        const double sw = sqrt(p.R * bc.T_w);
+                        const int nbf = m.nbf;
+                        double n3[3], t1[3], t2[3];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            n3[c] = m.bf_n[(size_t)c * nbf + bi];
+                            t1[c] = m.bf_t1[(size_t)c * nbf + bi];
+                            t2[c] = m.bf_t2[(size_t)c * nbf + bi];
+                        }
+                        const double v1 = ((bc.U_w[0] * t1[0] + bc.U_w[1] * t1[1]) + bc.U_w[2] * t1[2]) + sw * (rad * cs);
+                        const double v2 = ((bc.U_w[0] * t2[0] + bc.U_w[1] * t2[1]) + bc.U_w[2] * t2[2]) + sw * (rad * sn);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) u[c] = (Real)(((-vn) * n3[c] + v1 * t1[c]) + v2 * t2[c]);
                     }
-                    const double v1 = ((bc.U_w[0] * t1[0] + bc.U_w[1] * t1[1]) + bc.U_w[2] * t1[2]) + sw * (rad * cs);
-                    const double v2 = ((bc.U_w[0] * t2[0] + bc.U_w[1] * t2[1]) + bc.U_w[2] * t2[2]) + sw * (rad * sn);
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) u[c] = (Real)(((-vn) * n3[c] + v1 * t1[c]) + v2 * t2[c]);
                     ++nwall;
                 }
                 ++nrefl;

@@ -47,6 +47,8 @@ struct DevBc {
     double T_w;
     double U_w[3];
     double W_in[5];
+    float c2rt_f;  // binary32 rounding of -2 R T_w (mixed-mode wall emission)
+    float sw_f;    // binary32 rounding of sqrt(R T_w)
 };
 
 struct DevParams {
@@ -87,6 +89,8 @@ struct DevMesh {
     const int32_t* cfs;      // [nc] bit k set if the cell owns local face k
     const TrkF* trk_f;       // [nc]
     const TrkD* trk_d;       // [nc]
+    const float* vtx_f;      // [12][nc] mixed mode: vertex 0, then edges p_k - p_0 (k = 1..3), binary32
+    const float* bf_f;       // [11][nbf] mixed mode: n, t1, t2, U_w.t1, U_w.t2 of each boundary face, binary32
     // second-order reconstruction (order 2)
     const double* lsq_c;     // [12][nc]: gradient = sum_k c_k (v_k - v_i), c_k at [(3k+d) nc + i]
     const double* lsq_dxf;   // [12][nc]: face centroid minus cell centroid for local face k
@@ -124,6 +128,7 @@ struct DevState {
     double* prim;         // [5][nc] rho, Ux, Uy, Uz, T
     double* tau;          // [nc]
     float* tauf;          // [nc] binary32 rounding of tau (MIXED t_f draw)
+    float4* usig;         // [nc] binary32 roundings of U and sqrt(RT) (MIXED sampling)
     double* rhoh;         // [nc]
     double* rhop;         // [nc]
     int32_t* nsam;        // [nc]
@@ -189,6 +194,7 @@ void launch_wp_moments(const DevMesh& m, const DevState& s, const DevParams& p, 
 void launch_prim_moments(const DevMesh& m, const DevState& s, const DevParams& p, int which,
                          double* out, cudaStream_t st);
 
+int sm_count();       // multiprocessors of the current device
 int particle_grid();  // fixed grid of particle kernels (multiple of the SM count)
 
 }  // namespace ugkwp
