@@ -26,6 +26,9 @@
 #ifndef UGKWP_WAVE_THREADS
 #define UGKWP_WAVE_THREADS 128
 #endif
+#ifndef UGKWP_WAVE_MIN_BLOCKS
+#define UGKWP_WAVE_MIN_BLOCKS 1
+#endif
 
 namespace ugkwp {
 
@@ -547,7 +550,7 @@ __device__ void interior_flux_o2(const DevMesh& m, const DevState& s, const DevP
 }
 
 // Second-order flux of the interior faces (the first nif entries of face_order).
-__global__ void __launch_bounds__(UGKWP_WAVE_THREADS) k_face_flux_o2(DevMesh m, DevState s, DevParams p) {
+__global__ void __launch_bounds__(UGKWP_WAVE_THREADS, UGKWP_WAVE_MIN_BLOCKS) k_face_flux_o2(DevMesh m, DevState s, DevParams p) {
     const int nf = m.nf;
     const double dt = s.dt[0];
     const double inv_Tref = 1.0 / p.T_ref;

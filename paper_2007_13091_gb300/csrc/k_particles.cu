@@ -16,6 +16,11 @@ namespace ugkwp {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+
+// Resident blocks of k_track per SM that its register budget is sized for.
+#ifndef UGKWP_TRACK_MIN_BLOCKS
+#define UGKWP_TRACK_MIN_BLOCKS 4
+#endif
 enum : unsigned long long { TAG_TF = 1, TAG_SVEL = 2, TAG_SPOS = 3, TAG_WALL = 4 };
 
 __device__ __forceinline__ void set_err(const DevState& s, int32_t bits) {
@@ -206,18 +211,69 @@ template <> struct Trk<double> {
     }
 };
 
+// Round-to-nearest-even of v 2^-e for a binary64 v, from the bits of v with
+// integer operations only (v 2^-e is an exact exponent shift, so this equals
+// rounding the scaled binary64 value); false (q = 0) if v is not finite or
+// |v 2^-e| >= 2^62.  Keeps the conversions off the FP64 pipe.
+__device__ __forceinline__ bool fixed_of(double v, int e, long long& q) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    unsigned long long mant = bits & 0x000fffffffffffffULL;
+    q = 0;
+    if (ex == 0x7ff) return false;
+    int sh;  // |v| 2^-e = mant 2^sh
+    if (ex == 0) {
+        sh = 1 - 1075 - e;
+    } else {
+        mant |= 0x0010000000000000ULL;
+        sh = ex - 1075 - e;
+    }
+    unsigned long long mag;
+    if (sh >= 0) {
+        if (mant == 0) return true;
+        if (sh > 9) return false;  // mant >= 2^52 when nonzero and normal: 2^(52+10) = 2^62
+        mag = mant << sh;
+        if (mag >= (1ULL << 62)) return false;
+    } else {
+        const int r = -sh;
+        if (r > 63) return true;
+        const unsigned long long hi = mant >> r;
+        const unsigned long long rem = mant & ((1ULL << r) - 1ULL);
+        const unsigned long long half = 1ULL << (r - 1);
+        mag = hi + ((rem > half || (rem == half && (hi & 1ULL))) ? 1ULL : 0ULL);
+    }
+    q = (bits >> 63) ? -(long long)mag : (long long)mag;
+    return true;
+}
+
+// Exact binary32 -> binary64 widening on the bits (integer pipes only).
+__device__ __forceinline__ double widen(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    int ex = (int)((b >> 23) & 0xff);
+    unsigned mant = b & 0x7fffffu;
+    if (ex == 0xff) return __longlong_as_double((long long)(sign | (0x7ffULL << 52) | ((unsigned long long)mant << 29)));
+    if (ex == 0) {
+        if (mant == 0) return __longlong_as_double((long long)sign);
+        const int k = __clz(mant) - 8;  // shift that brings the leading one to bit 23
+        mant = (mant << k) & 0x7fffffu;
+        ex = 1 - k;
+    }
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)(ex - 127 + 1023) << 52) | ((unsigned long long)mant << 29)));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 // Fixed-point image of phi = m (1, u, |u|^2/2); false if a value leaves |v| < 2^62.
+// The factor 1/2 of the energy is applied as an exponent shift.
 template <class Real>
 __device__ __forceinline__ bool phi_q(const Real* u, double mm, const DevParams& p, long long q[5]) {
-    const double u0 = (double)u[0], u1 = (double)u[1], u2 = (double)u[2];
-    const double phi[5] = {mm, mm * u0, mm * u1, mm * u2, 0.5 * (mm * ((u0 * u0 + u1 * u1) + u2 * u2))};
-    bool ok = true;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        double v = phi[k] * p.qinv[k];
-        if (!(fabs(v) < 0x1p62)) { ok = false; v = 0.0; }
-        q[k] = __double2ll_rn(v);
-    }
+    const double u0 = widen(u[0]), u1 = widen(u[1]), u2 = widen(u[2]);
+    bool ok = fixed_of(mm, p.exps[0], q[0]);
+    ok &= fixed_of(mm * u0, p.exps[1], q[1]);
+    ok &= fixed_of(mm * u1, p.exps[2], q[2]);
+    ok &= fixed_of(mm * u2, p.exps[3], q[3]);
+    ok &= fixed_of(mm * ((u0 * u0 + u1 * u1) + u2 * u2), p.exps[4] + 1, q[4]);
     return ok;
 }
 
@@ -254,7 +310,7 @@ __device__ __forceinline__ bool fixed_of_mass(double m, int e, long long& q) {
 }
 
 template <class Real>
-__global__ void __launch_bounds__(256, 3) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br, PartBufRaw ar) {
+__global__ void __launch_bounds__(256, UGKWP_TRACK_MIN_BLOCKS) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br, PartBufRaw ar) {
     if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
     const PartView<Real> b = view<Real>(br);
     const PartView<Real> mv = view<Real>(ar);  // mover list: x = u at start, u = u at end
