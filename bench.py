@@ -41,7 +41,20 @@ TRACK_BYTES_PER_CELL = {"mixed": 80 + 8, "fp64": 144 + 8}
 # DRAM bytes (read + write) of one k_track launch on this workload, from the ncu
 # capture summarised in profiles/k_track_k_face_flux_cavity24_mixed.md; set to
 # None whenever the kernel changes until it is captured again
-TRACK_DRAM_BYTES = {"mixed": None, "fp64": None}
+TRACK_DRAM_BYTES = {"mixed": 399780352 + 128354304, "fp64": None}
+# Binary64 flops per interior face of k_face_flux_o2 (the second-order wave flux):
+# ncu's executed dadd + dmul + 2 dfma per launch divided by the interior faces, on
+# this workload (profiles/); None until captured for the current kernel.
+FLUX_O2_FLOPS_PER_FACE = (27613440 + 75894656 + 2 * 144012032) / 162432
+FLUX_O2_DRAM_BYTES = 30774016 + 768
+# FP64 peak: 2 FP64 FMA lanes per clock per SM (the nominal 1.25 TFLOP/s of this
+# part at 152 SMs and 2.07 GHz), 2 flops per FMA
+FP64_FMA_LANES_PER_SM = 2
+
+
+def flux_ms_dominant(kms):
+    """The O2 wave flux is the dominant kernel when its device time exceeds k_track's."""
+    return kms.get("flux_o2", 0.0) > kms.get("track", 0.0)
 
 
 def peaks():
@@ -337,6 +350,40 @@ def main():
     kmoves = kms.pop("_moves") / args.steps
     alg = TRACK_BYTES_PER_MOVE[args.precision] * kmoves + TRACK_BYTES_PER_CELL[args.precision] * nc
     achieved = alg / (track_ms * 1e-3) / 1e9
+    roof_track = {"kernel": "k_track (a6-a9: t_f draw, tet walk, fixed-point flux, removal)", "bound": "hbm",
+                  "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                  "peak_kind": f"{peak_kind} HBM copy", "traffic": TRACK_DRAM_BYTES[args.precision],
+                  "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                  "algorithmic_bytes_per_launch": alg,
+                  "bytes_per_move": TRACK_BYTES_PER_MOVE[args.precision],
+                  "bytes_per_cell": TRACK_BYTES_PER_CELL[args.precision], "ms_per_launch": track_ms,
+                  "timing": "CUDA events on the library's stream around each k_track launch over "
+                            f"{args.steps} further steps of the same run (direct launches, wave flux "
+                            "overlapping on the second stream)"}
+    roof_flux = None
+    if ORDER == 2 and kms.get("flux_o2", 0.0) > 0.0:
+        props = torch.cuda.get_device_properties(local)
+        sm_mhz = 2070.0
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                sm_mhz = float(json.load(f).get("sm_max_mhz", sm_mhz))
+        except OSError:
+            pass
+        fp64_peak = props.multi_processor_count * FP64_FMA_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        flux_ms = kms["flux_o2"] / args.steps
+        n_if = sim.n_faces - sim.n_bfaces
+        flops = FLUX_O2_FLOPS_PER_FACE * n_if if FLUX_O2_FLOPS_PER_FACE else None
+        ach = flops / (flux_ms * 1e-3) / 1e12 if flops else None
+        roof_flux = {"kernel": "k_face_flux_o2 (a3-a4: second-order wave flux of the interior faces)",
+                     "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": ach / fp64_peak if ach else None,
+                     "peak_kind": f"FP64 nominal: {props.multi_processor_count} SMs x {FP64_FMA_LANES_PER_SM} "
+                                  f"FMA lanes/clk x 2 flop x {sm_mhz:.0f} MHz",
+                     "traffic": FLUX_O2_DRAM_BYTES, "traffic_unit": "bytes per launch (ncu)",
+                     "flops_per_face": FLUX_O2_FLOPS_PER_FACE, "faces_per_launch": n_if,
+                     "ms_per_launch": flux_ms,
+                     "timing": "CUDA events on the library's wave stream around each launch, overlapping the "
+                               "particle kernels"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 particles / f64 cells / int64 flux" if args.precision == "mixed" else "f64",
@@ -347,16 +394,8 @@ def main():
                       "l2": "inputs larger than L2 (particle SoA %.2f GB per buffer)" % (moves_per_step * 44 / 1e9),
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "cell_steps_per_s": cell_steps,
-           "roofline": {"kernel": "k_track (a6-a9: t_f draw, tet walk, fixed-point flux, removal)", "bound": "hbm",
-                        "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "peak_kind": f"{peak_kind} HBM copy", "traffic": TRACK_DRAM_BYTES[args.precision],
-                        "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                        "algorithmic_bytes_per_launch": alg,
-                        "bytes_per_move": TRACK_BYTES_PER_MOVE[args.precision],
-                        "bytes_per_cell": TRACK_BYTES_PER_CELL[args.precision], "ms_per_launch": track_ms,
-                        "timing": "CUDA events on the library's stream around each k_track launch over "
-                                  f"{args.steps} further steps of the same run (direct launches, wave flux "
-                                  "overlapping on the second stream)"},
+           "roofline": roof_flux if roof_flux and roof_flux["achieved"] and flux_ms_dominant(kms) else roof_track,
+           "roofline_track": roof_track, "roofline_flux_o2": roof_flux,
            "kernels_ms_per_step": {k: v / args.steps for k, v in kms.items()},
            "step_launch": "two-step CUDA graphs replayed on the caller's stream",
            "gpu_launches": int(launches), "clocks": clocks}

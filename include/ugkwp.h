@@ -231,7 +231,7 @@ int ugkwp_last(ugkwp_sim* s, int32_t which, void* host_out);
 enum {
     UGKWP_K_RESET = 0, UGKWP_K_CELL_PREP, UGKWP_K_SAMPLE_COUNT, UGKWP_K_SCAN, UGKWP_K_SCATTER,
     UGKWP_K_SAMPLE, UGKWP_K_TRACK, UGKWP_K_FLUX, UGKWP_K_UPDATE, UGKWP_K_MOVERS, UGKWP_K_GRADIENTS,
-    UGKWP_N_KERNELS
+    UGKWP_K_FLUX_O2, UGKWP_N_KERNELS
 };
 
 /* Per-kernel timing with CUDA events recorded on the bound stream around each
@@ -240,8 +240,9 @@ enum {
  * milliseconds (ms[UGKWP_N_KERNELS]) of the launches timed since the last
  * read, and the number of kernels launched since ugkwp_init
  * (launches[UGKWP_N_KERNELS], counted whether or not timing is enabled; the
- * scan class counts its two kernels, the flux class its two at order 2);
- * either pointer may be NULL.  The timed
+ * scan class counts its two kernels); at order 2 the flux class times the
+ * boundary faces and UGKWP_K_FLUX_O2 the interior faces; either pointer may
+ * be NULL.  The timed
  * sums are reset by the read. */
 int ugkwp_timing_enable(ugkwp_sim* s, int32_t enable);
 int ugkwp_timing_read(ugkwp_sim* s, double* ms, int64_t* launches);

@@ -630,8 +630,11 @@ int enqueue_step(ugkwp_sim* s) {
         CU(cudaStreamWaitEvent(s->wave, s->fork, 0));
         if (s->P.order == 2)
             timed(s, UGKWP_K_GRADIENTS, 1, s->wave, [&] { launch_gradients(s->M, s->S, s->P, s->wave); });
-        const int n_flux = s->P.order == 2 ? (s->M.nif > 0) + (s->M.nf > s->M.nif) : 1;
-        timed(s, UGKWP_K_FLUX, n_flux, s->wave, [&] { launch_face_flux(s->M, s->S, s->P, s->wave); });
+        if (s->P.order == 2 && s->M.nif > 0)
+            timed(s, UGKWP_K_FLUX_O2, 1, s->wave, [&] { launch_face_flux_o2(s->M, s->S, s->P, s->wave); });
+        const int first = s->P.order == 2 ? s->M.nif : 0;
+        if (s->M.nf > first)
+            timed(s, UGKWP_K_FLUX, 1, s->wave, [&] { launch_face_flux(s->M, s->S, s->P, first, s->wave); });
         CU(cudaEventRecord(s->join, s->wave));
         timed(s, UGKWP_K_SCAN, 2, q, [&] { launch_scan(s->M, s->S, s->P, q); });
         timed(s, UGKWP_K_SCATTER, 1, q, [&] { launch_scatter(s->M, s->S, s->P, s->A, s->B, q); });

@@ -628,13 +628,12 @@ void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, c
     k_gradients<<<wave_grid(m.nc), UGKWP_WAVE_THREADS, 0, st>>>(m, s, p);
 }
 
-void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
-    int first = 0;
-    if (p.order == 2) {
-        if (m.nif > 0) k_face_flux_o2<<<wave_grid(m.nif), UGKWP_WAVE_THREADS, 0, st>>>(m, s, p);
-        first = m.nif;
-    }
-    if (m.nf > first) k_face_flux<<<(m.nf - first + 255) / 256, 256, 0, st>>>(m, s, p, first);
+void launch_face_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
+    k_face_flux_o2<<<wave_grid(m.nif), UGKWP_WAVE_THREADS, 0, st>>>(m, s, p);
+}
+
+void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, int first, cudaStream_t st) {
+    k_face_flux<<<(m.nf - first + 255) / 256, 256, 0, st>>>(m, s, p, first);
 }
 
 }  // namespace ugkwp

@@ -184,7 +184,9 @@ void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const
                   const PartBufRaw& a, cudaStream_t st);
 void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
                    cudaStream_t st);
-void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
+// First-order flux of face_order[first..nf); second-order flux of the nif interior faces.
+void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, int first, cudaStream_t st);
+void launch_face_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_rebuild_survivors(const DevMesh& m, const DevState& s, const DevParams& p,

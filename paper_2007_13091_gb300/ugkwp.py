@@ -80,7 +80,7 @@ class AdjointReq(ctypes.Structure):
                 ("n_wall_tags", ctypes.c_int32)]
 
 
-KERNELS = ["reset", "cell_prep", "sample_count", "scan", "scatter", "sample", "track", "flux", "update", "movers", "gradients"]
+KERNELS = ["reset", "cell_prep", "sample_count", "scan", "scatter", "sample", "track", "flux", "update", "movers", "gradients", "flux_o2"]
 
 EXPORTED = ["ugkwp_time_step_noalloc", "ugkwp_timing_enable", "ugkwp_timing_read", "ugkwp_mesh_load", "ugkwp_mesh_free", "ugkwp_query_sizes", "ugkwp_init", "ugkwp_free", "ugkwp_step",
             "ugkwp_sync", "ugkwp_moments", "ugkwp_state_info", "ugkwp_export_state", "ugkwp_import_state",
@@ -315,6 +315,7 @@ class Simulation:
         self.mesh = ugkwp_mesh_load(mesh)
         sizes = ugkwp_query_sizes(self.mesh, params)
         self.n_cells, self.n_faces = int(sizes.n_cells), int(sizes.n_faces)
+        self.n_bfaces = int(sizes.n_bfaces)
         self.workspace_bytes = int(sizes.workspace_bytes)
         self._ws = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=device)
         base = self._ws.data_ptr()
