@@ -201,32 +201,39 @@ def time_steps(sim, steps, warmup, ws, timing=True):
     return ms, moves, launches, kms, st1
 
 
-def field_error(steps, device):
-    """Per-field relative L2 of MIXED vs FP64 after `steps` steps from the same
-    initial state and seed, and the FP64 seed-to-seed noise floor."""
+def field_error(horizons, device):
+    """Per-field relative L2 of MIXED vs FP64 after each of `horizons` steps from
+    the same initial state and seed, and the FP64 seed-to-seed noise floor."""
     from paper_2007_13091_gb300 import ugkwp
 
-    def prim(precision, seed):
+    def prims(precision, seed):
         cfg = workload(precision, seed)
         sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device)
-        sim.step(steps)
-        P = sim.moments(ugkwp.PRIM)
+        out, done = {}, 0
+        for h in horizons:
+            sim.step(h - done)
+            done = h
+            P = sim.moments(ugkwp.PRIM)
+            rho, U, T = P[0], P[1:4], P[4]
+            out[h] = {"rho": rho, "U": U, "T": T, "p": rho * T}
         sim.close()
-        rho, U, T = P[0], P[1:4], P[4]
-        return {"rho": rho, "U": U, "T": T, "p": rho * T}
+        return out
 
-    a, b, c = prim("mixed", 2), prim("fp64", 2), prim("fp64", 1002)
+    a, b, c = prims("mixed", 2), prims("fp64", 2), prims("fp64", 1002)
 
     def rel(x, y):
         return float(np.linalg.norm(x - y) / np.linalg.norm(y))
     # velocity error relative to the lid speed scale (the cavity starts at rest)
     ulid = 0.16 * math.sqrt(5.0 / 3.0)
     uerr = lambda x, y: float(np.linalg.norm(x - y) / (ulid * math.sqrt(y.shape[1])))
-    err = {k: rel(a[k], b[k]) for k in ("rho", "T", "p")}
-    err["U"] = uerr(a["U"], b["U"])
-    floor = {k: rel(c[k], b[k]) for k in ("rho", "T", "p")}
-    floor["U"] = uerr(c["U"], b["U"])
-    return {"steps": steps, "mixed_vs_fp64": err, "noise_floor_fp64_seed": floor}
+    res = {}
+    for h in horizons:
+        err = {k: rel(a[h][k], b[h][k]) for k in ("rho", "T", "p")}
+        err["U"] = uerr(a[h]["U"], b[h]["U"])
+        floor = {k: rel(c[h][k], b[h][k]) for k in ("rho", "T", "p")}
+        floor["U"] = uerr(c[h]["U"], b[h]["U"])
+        res[str(h)] = {"mixed_vs_fp64": err, "noise_floor_fp64_seed": floor}
+    return {"horizons": list(horizons), "by_horizon": res}
 
 
 def e2e(cfg, steps, device):
@@ -253,6 +260,40 @@ def e2e(cfg, steps, device):
     sim.close()
     return {"value": moves / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "steps": steps, "particles": int(n)}
+
+
+def batched(precision, steps, warmup, device):
+    """The batched form: 64 independent shock tubes and cavities of 2k-60k tets,
+    Kn log-uniform in [1e-4, 1], Mach in [0.1, 3], stepped as one CUDA graph per
+    step pair after the batch autotuner picked the grid sizes."""
+    import torch
+    from paper_2007_13091_gb300 import ugkwp
+    from paper_2007_13091_gb300 import workloads as wl
+    cases = wl.batch_instances(precision=precision, order=ORDER)
+    sims = [ugkwp.Simulation(c["mesh"], c["W0"], c["params"], device=device, stream=torch.cuda.Stream(device=device))
+            for c in cases]
+    b = ugkwp.Batch(sims)
+    best = b.autotune(2)
+    b.step(warmup)
+    b.sync()
+    m0 = sum(s.step(0, stats=True)["n_moves_total"] for s in sims)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.step(steps)
+    e1.record(b.stream)
+    b.sync()
+    ms = e0.elapsed_time(e1)
+    m1 = sum(s.step(0, stats=True)["n_moves_total"] for s in sims)
+    n_cells = sum(s.n_cells for s in sims)
+    b.close()
+    for s in sims:
+        s.close()
+    return {"value": (m1 - m0) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "instances": len(cases),
+            "n_cells": n_cells, "particles_per_step": (m1 - m0) / steps,
+            "cell_steps_per_s": n_cells * steps / (ms * 1e-3), "launch_cfg": best,
+            "workload": "64 instances (even: shock tubes moving at Mach M, N_ref 50; odd: cavities with lid "
+                        "Mach M, N_ref 100), 2k-60k tets each, Kn log-uniform [1e-4, 1], M uniform [0.1, 3], "
+                        f"seed 4, order {ORDER}, {precision}"}
 
 
 def cpu_baseline(steps):
@@ -410,8 +451,11 @@ def main():
                        "cell_steps_per_s": nc * args.steps / (ms64 * 1e-3),
                        "kernels_ms_per_step": {k: v / args.steps for k, v in k64.items()}}
         out["mixed_over_fp64"] = out["value"] / out["fp64"]["value"]
-        out["field_error"] = field_error(10, device)
+        out["field_error"] = field_error((1, 10, 20), device)
         out["e2e"] = e2e(cfg, 3, device)
+        out["batched"] = {"mixed": batched("mixed", args.steps, args.warmup, device)}
+        out["batched"]["fp64"] = batched("fp64", args.steps, args.warmup, device)
+        out["batched"]["mixed_over_fp64"] = out["batched"]["mixed"]["value"] / out["batched"]["fp64"]["value"]
         out["cpu_baseline"] = cpu_baseline(args.cpu_steps)
     elif rank == 0:
         out["e2e"] = None

@@ -72,6 +72,7 @@ enum {
  * mass, fluxes (fixed point), relaxation times and all cell/face arithmetic
  * stay binary64. */
 enum { UGKWP_FP64 = 0, UGKWP_MIXED = 1 };
+enum { UGKWP_SAMPLE_MAXWELL = 0, UGKWP_SAMPLE_ENERGY_MATCHED = 1 };
 
 /* Which quantity ugkwp_moments returns (all [5][n_cells] unless stated). */
 enum {
@@ -126,6 +127,11 @@ typedef struct {
     int32_t precision;           /* UGKWP_FP64 or UGKWP_MIXED */
     int32_t max_crossings;       /* cap on face crossings per particle and step (> 0) */
     int32_t n_bc;                /* number of used entries of bc (<= 16) */
+    int32_t sampling;            /* UGKWP_SAMPLE_MAXWELL: pairs U +/- sqrt(RT) X (Sec. 2.4 (b));
+                                  * UGKWP_SAMPLE_ENERGY_MATCHED: the same pairs with X scaled per
+                                  * cell so that their thermal energy is exactly
+                                  * rho^hp |Omega| (3/2) R T (a variance reduction) */
+    int32_t reserved_;           /* must be 0 */
     uint64_t seed;               /* Philox4x64-10 key word 0 */
     int64_t particle_capacity;   /* particles the device buffers hold (< 2^31) */
     ugkwp_bc bc[16];
@@ -233,6 +239,47 @@ enum {
     UGKWP_K_SAMPLE, UGKWP_K_TRACK, UGKWP_K_FLUX, UGKWP_K_UPDATE, UGKWP_K_MOVERS, UGKWP_K_GRADIENTS,
     UGKWP_K_FLUX_O2, UGKWP_N_KERNELS
 };
+
+/* ---- launch configuration and autotuning -------------------------------
+ * Grid sizes of the step kernels that loop over their work.  Results do not
+ * depend on them (every particle draws from its own counter-based stream and
+ * every sum over particles is fixed point), only the speed does. */
+typedef struct {
+    int32_t particle_blocks;     /* blocks of 256 threads for scatter, sampling, tracking, movers (> 0) */
+    int32_t wave_blocks;         /* blocks of the persistent second-order wave kernels (> 0) */
+} ugkwp_launch_cfg;
+
+int ugkwp_get_launch_cfg(const ugkwp_sim* s, ugkwp_launch_cfg* out);
+/* Takes effect at the next step (the step graphs are recaptured). */
+int ugkwp_set_launch_cfg(ugkwp_sim* s, const ugkwp_launch_cfg* cfg);
+/* Autotuner: for each candidate grid pair (particle blocks 1, 2, 4, 8 or 16 per
+ * SM; wave blocks 1 or 2 per SM at order 2) runs 2 warm-up steps and
+ * steps_per_trial timed steps (even, >= 2) on the bound stream, keeps the
+ * fastest pair and returns it in *best (may be NULL).  The trial steps advance
+ * the simulation like any other steps.  E_STATE while per-kernel timing is on. */
+int ugkwp_autotune(ugkwp_sim* s, int32_t steps_per_trial, ugkwp_launch_cfg* best);
+
+/* ---- batches of independent simulations --------------------------------
+ * A batch steps n simulations of any sizes and parameters together: every
+ * step pair of all members is captured into one CUDA graph in which the
+ * members run concurrently on the batch's own streams, and the graph is
+ * launched on cuda_stream (NULL: the legacy default stream).  Each member
+ * keeps its own state, random streams and results, bit for bit the same as
+ * when stepped alone.  Members must be distinct; while stepped through a batch
+ * a member is read or stepped on its own only after ugkwp_batch_sync.  The
+ * batch does not own its members (free it before them). */
+typedef struct ugkwp_batch ugkwp_batch;
+
+int ugkwp_batch_create(ugkwp_sim* const* sims, int32_t n_sims, void* cuda_stream, ugkwp_batch** out);
+/* Enqueue n_steps steps of every member (asynchronous on cuda_stream). */
+int ugkwp_batch_step(ugkwp_batch* b, int32_t n_steps);
+/* Wait for the batch's stream; returns the first member's device-side error
+ * (the message names the member index). */
+int ugkwp_batch_sync(ugkwp_batch* b);
+/* The autotuner over the whole batch: one grid pair for all members, chosen by
+ * the time of batch step pairs (trial steps advance every member). */
+int ugkwp_batch_autotune(ugkwp_batch* b, int32_t steps_per_trial, ugkwp_launch_cfg* best);
+int ugkwp_batch_free(ugkwp_batch* b);
 
 /* Per-kernel timing with CUDA events recorded on the bound stream around each
  * kernel launch of ugkwp_step while enabled (enable != 0).  ugkwp_timing_read

@@ -29,7 +29,8 @@ class OrcParams(ctypes.Structure):
                 ("omega", ctypes.c_double), ("CFL", ctypes.c_double), ("C2", ctypes.c_double),
                 ("venkat_K", ctypes.c_double), ("order", ctypes.c_int32), ("N_ref", ctypes.c_int32), ("N_min", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("max_crossings", ctypes.c_int32),
-                ("n_bc", ctypes.c_int32), ("seed", ctypes.c_uint64), ("bc", OrcBc * 16)]
+                ("n_bc", ctypes.c_int32), ("sampling", ctypes.c_int32), ("pad2_", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("bc", OrcBc * 16)]
 
 
 _LIB = None
@@ -87,6 +88,9 @@ def make_bc(b: dict) -> OrcBc:
     return c
 
 
+SAMPLING = {"maxwell": 0, "energy_matched": 1}
+
+
 def make_params(p: dict) -> OrcParams:
     o = OrcParams()
     for k in ("R", "mu_ref", "T_ref", "omega", "CFL", "C2"):
@@ -97,6 +101,7 @@ def make_params(p: dict) -> OrcParams:
     o.N_min = int(p.get("N_min", 0))
     o.precision = PRECISION[p.get("precision", "fp64")]
     o.max_crossings = int(p.get("max_crossings", 1000))
+    o.sampling = SAMPLING[p.get("sampling", "maxwell")]
     o.seed = int(p["seed"])
     o.n_bc = len(p["bc"])
     for k, b in enumerate(p["bc"]):

@@ -937,6 +937,29 @@ template <class Real> struct Sim : SimBase {
         return 0;
     }
 
+    // The three normals X of the pair whose first member has id `ida`, by
+    // Box-Muller in the particle precision (binary32 in the mixed mode), widened.
+    static void normals_of_pair(uint64_t seed, uint64_t step, uint64_t ida, double X[3]) {
+        Ctr4 r = draw(seed, ida, step, TAG_SVEL, 0);
+        if constexpr (std::is_same<Real, float>::value) {
+            float sn, cs;
+            float rad = std::sqrt(-2.0f * log_f(u01_f(r.v[0])));
+            sincos2pi_f(u01_f(r.v[1]), &sn, &cs);
+            X[0] = (double)(rad * cs); X[1] = (double)(rad * sn);
+            rad = std::sqrt(-2.0f * log_f(u01_f(r.v[2])));
+            sincos2pi_f(u01_f(r.v[3]), &sn, &cs);
+            X[2] = (double)(rad * cs);
+        } else {
+            double sn, cs;
+            double rad = std::sqrt(-2.0 * log_d(u01_d(r.v[0])));
+            sincos2pi_d(u01_d(r.v[1]), &sn, &cs);
+            X[0] = rad * cs; X[1] = rad * sn;
+            rad = std::sqrt(-2.0 * log_d(u01_d(r.v[2])));
+            sincos2pi_d(u01_d(r.v[3]), &sn, &cs);
+            X[2] = rad * cs;
+        }
+    }
+
     // a5: the N_sam particles of cell i, in pairs u = U +/- sqrt(RT) X with
     // X ~ N(0, I) (Box-Muller), x uniform in the tet (needs prepare()).
     void sample_cell(int i, std::vector<Part<Real>>& out) const {
@@ -946,6 +969,18 @@ template <class Real> struct Sim : SimBase {
         double sig = std::sqrt(p.R * pr[i].T);
         const double *p0 = &g.xyz[3 * (size_t)g.tet[4 * i]], *p1 = &g.xyz[3 * (size_t)g.tet[4 * i + 1]];
         const double *p2 = &g.xyz[3 * (size_t)g.tet[4 * i + 2]], *p3 = &g.xyz[3 * (size_t)g.tet[4 * i + 3]];
+        // Energy-matched sampling (option): one factor s for all pairs of the
+        // cell so that the sampled thermal energy sum_j m (s sqrt(RT))^2 |X_j|^2
+        // equals N_sam m (3/2) R T exactly, i.e. s^2 sum_j |X_j|^2 = 3 N_sam / 2.
+        if (p.sampling == 1 && ns >= 2) {
+            double S = 0.0;
+            for (int64_t j = 0; j < ns / 2; ++j) {
+                double X[3];
+                normals_of_pair(p.seed, (uint64_t)step, make_id((uint64_t)step, (uint64_t)i, (uint64_t)(2 * j)), X);
+                S = S + ((X[0] * X[0] + X[1] * X[1]) + X[2] * X[2]);
+            }
+            if (S > 0.0) sig = sig * std::sqrt((double)(3 * (ns / 2)) / S);
+        }
         if constexpr (std::is_same<Real, float>::value) {
             // Mixed precision (reading): the particle arithmetic is binary32,
             // from U and sqrt(RT) of the cell and the tet's first vertex and

@@ -32,6 +32,10 @@ typedef struct {
     double R, mu_ref, T_ref, omega, CFL, C2;
     double venkat_K;   /* Venkatakrishnan constant K: epsilon^2 = (K h)^3 (order 2) */
     int32_t order, N_ref, N_min, precision, max_crossings, n_bc;
+    int32_t sampling;  /* 0: pairs U +/- sqrt(RT) X as printed; 1: the same pairs with X
+                        * scaled per cell so that their thermal energy is exactly
+                        * rho^hp |Omega| (3/2) R T (energy-matched sampling) */
+    int32_t pad2_;
     uint64_t seed;
     orc_bc bc[16];
 } orc_params;

@@ -43,9 +43,13 @@ struct ugkwp_sim {
     // the wave flux (binary64-bound) runs beside the particle kernels
     cudaStream_t wave = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
-    // two-step CUDA graphs, one per ping-pong parity (keyed by buffer A)
+    // grid sizes of the looping step kernels
+    LaunchCfg lc{0, 0};
+    // two-step CUDA graphs, one per ping-pong parity (keyed by buffer A), with
+    // the kernels each one launches per class
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     void* graph_key[2] = {nullptr, nullptr};
+    int64_t graph_launches[2][UGKWP_N_KERNELS] = {};
     bool graphs_ok = true;
     void drop_graphs() {
         for (int k = 0; k < 2; ++k) {
@@ -137,6 +141,7 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, D
     S.tau = c.take<double>(nc);
     S.tauf = c.take<float>(nc);
     S.usig = c.take<float4>(nc);
+    S.sig = c.take<double>(nc);
     S.rhoh = c.take<double>(nc);
     S.rhop = c.take<double>(nc);
     S.nsam = c.take<int32_t>(nc);
@@ -180,6 +185,8 @@ int check_params(const ugkwp_params* p, const MeshHost* mh) {
     if (p->N_ref <= 0 || p->N_min < 0) return fail(UGKWP_E_ARG, "N_ref must be > 0 and N_min >= 0");
     if (p->precision != UGKWP_FP64 && p->precision != UGKWP_MIXED) return fail(UGKWP_E_ARG, "unknown precision");
     if (p->max_crossings <= 0) return fail(UGKWP_E_ARG, "max_crossings must be > 0");
+    if (p->sampling != UGKWP_SAMPLE_MAXWELL && p->sampling != UGKWP_SAMPLE_ENERGY_MATCHED)
+        return fail(UGKWP_E_ARG, "unknown sampling mode");
     if (p->particle_capacity < 0 || p->particle_capacity >= ((int64_t)1 << 31))
         return fail(UGKWP_E_ARG, "particle_capacity must be in [0, 2^31)");
     if (p->n_bc < 0 || p->n_bc > 16) return fail(UGKWP_E_ARG, "n_bc must be in [0, 16]");
@@ -354,6 +361,7 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     P.R = p->R; P.mu_ref = p->mu_ref; P.T_ref = p->T_ref; P.omega = p->omega; P.CFL = p->CFL; P.C2 = p->C2;
     P.N_ref = p->N_ref; P.N_min = p->N_min; P.max_crossings = p->max_crossings; P.precision = p->precision;
     P.order = p->order;
+    P.sampling = p->sampling;
     P.seed = p->seed; P.capacity = p->particle_capacity; P.n_bc = p->n_bc;
     for (int b = 0; b < p->n_bc; ++b) {
         P.bc[b].type = p->bc[b].type;
@@ -547,6 +555,8 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
         delete s;
         return cuda_fail(ce, "ugkwp_init upload");
     }
+    s->lc.particle_blocks = particle_grid();
+    s->lc.wave_blocks = sm_count();
     *out = s;
     return UGKWP_OK;
 }
@@ -629,18 +639,22 @@ int enqueue_step(ugkwp_sim* s) {
         CU(cudaEventRecord(s->fork, q));
         CU(cudaStreamWaitEvent(s->wave, s->fork, 0));
         if (s->P.order == 2)
-            timed(s, UGKWP_K_GRADIENTS, 1, s->wave, [&] { launch_gradients(s->M, s->S, s->P, s->wave); });
+            timed(s, UGKWP_K_GRADIENTS, 1, s->wave, [&] { launch_gradients(s->M, s->S, s->P, s->lc.wave_blocks, s->wave); });
         if (s->P.order == 2 && s->M.nif > 0)
-            timed(s, UGKWP_K_FLUX_O2, 1, s->wave, [&] { launch_face_flux_o2(s->M, s->S, s->P, s->wave); });
+            timed(s, UGKWP_K_FLUX_O2, 1, s->wave, [&] { launch_face_flux_o2(s->M, s->S, s->P, s->lc.wave_blocks, s->wave); });
         const int first = s->P.order == 2 ? s->M.nif : 0;
         if (s->M.nf > first)
             timed(s, UGKWP_K_FLUX, 1, s->wave, [&] { launch_face_flux(s->M, s->S, s->P, first, s->wave); });
         CU(cudaEventRecord(s->join, s->wave));
         timed(s, UGKWP_K_SCAN, 2, q, [&] { launch_scan(s->M, s->S, s->P, q); });
-        timed(s, UGKWP_K_SCATTER, 1, q, [&] { launch_scatter(s->M, s->S, s->P, s->A, s->B, q); });
-        timed(s, UGKWP_K_SAMPLE, 1, q, [&] { launch_sample_write(s->M, s->S, s->P, s->B, q); });
-        timed(s, UGKWP_K_TRACK, 1, q, [&] { launch_track(s->M, s->S, s->P, s->B, s->A, q); });
-        timed(s, UGKWP_K_MOVERS, 1, q, [&] { launch_movers(s->M, s->S, s->P, s->A, q); });
+        timed(s, UGKWP_K_SCATTER, 1, q, [&] { launch_scatter(s->M, s->S, s->P, s->A, s->B, s->lc.particle_blocks, q); });
+        const bool matched = s->P.sampling == UGKWP_SAMPLE_ENERGY_MATCHED;
+        timed(s, UGKWP_K_SAMPLE, matched ? 2 : 1, q, [&] {
+            if (matched) launch_sample_scale(s->M, s->S, s->P, q);
+            launch_sample_write(s->M, s->S, s->P, s->B, s->lc.particle_blocks, q);
+        });
+        timed(s, UGKWP_K_TRACK, 1, q, [&] { launch_track(s->M, s->S, s->P, s->B, s->A, s->lc.particle_blocks, q); });
+        timed(s, UGKWP_K_MOVERS, 1, q, [&] { launch_movers(s->M, s->S, s->P, s->A, s->lc.particle_blocks, q); });
         CU(cudaStreamWaitEvent(q, s->join, 0));  // join before the update reads F
         timed(s, UGKWP_K_UPDATE, 1, q, [&] { launch_cell_update(s->M, s->S, s->P, q); });
         std::swap(s->A, s->B);
@@ -670,6 +684,7 @@ int launch_step_pair(ugkwp_sim* s, bool& used) {
         int rc = enqueue_step(s);
         if (rc == UGKWP_OK) rc = enqueue_step(s);
         cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+        for (int k = 0; k < UGKWP_N_KERNELS; ++k) s->graph_launches[slot][k] = s->launches[k] - saved[k];
         std::memcpy(s->launches, saved, sizeof(saved));
         if (rc != UGKWP_OK || e != cudaSuccess || !g) {
             if (g) cudaGraphDestroy(g);
@@ -688,9 +703,7 @@ int launch_step_pair(ugkwp_sim* s, bool& used) {
         s->graph_key[slot] = key;
     }
     CU(cudaGraphLaunch(s->graph[slot], s->stream));
-    // the graph holds two steps of every kernel class
-    int64_t per_step[UGKWP_N_KERNELS] = {1, 1, 1, 2, 1, 1, 1, 1, 1, 1};
-    for (int k = 0; k < UGKWP_N_KERNELS; ++k) s->launches[k] += 2 * per_step[k];
+    for (int k = 0; k < UGKWP_N_KERNELS; ++k) s->launches[k] += s->graph_launches[slot][k];
     used = true;
     return UGKWP_OK;
 }
@@ -937,6 +950,320 @@ int ugkwp_last(ugkwp_sim* s, int32_t which, void* host_out) {
 int ugkwp_adjoint_wave(ugkwp_sim* s, const ugkwp_adjoint_req* r, double* dJ_dtheta) {
     (void)s; (void)r; (void)dJ_dtheta;
     return fail(UGKWP_E_UNSUPPORTED, "the adjoint of the wave flux is not available in this build");
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------ launch configuration
+extern "C" {
+
+int ugkwp_get_launch_cfg(const ugkwp_sim* s, ugkwp_launch_cfg* out) {
+    if (!s || !out) return fail(UGKWP_E_ARG, "NULL argument");
+    out->particle_blocks = s->lc.particle_blocks;
+    out->wave_blocks = s->lc.wave_blocks;
+    return UGKWP_OK;
+}
+
+int ugkwp_set_launch_cfg(ugkwp_sim* s, const ugkwp_launch_cfg* cfg) {
+    if (!s || !cfg) return fail(UGKWP_E_ARG, "NULL argument");
+    if (cfg->particle_blocks <= 0 || cfg->wave_blocks <= 0 || cfg->particle_blocks > (1 << 20) ||
+        cfg->wave_blocks > (1 << 20))
+        return fail(UGKWP_E_ARG, "grid sizes must be in [1, 2^20]");
+    if (cfg->particle_blocks != s->lc.particle_blocks || cfg->wave_blocks != s->lc.wave_blocks) {
+        s->lc.particle_blocks = cfg->particle_blocks;
+        s->lc.wave_blocks = cfg->wave_blocks;
+        s->drop_graphs();
+    }
+    return UGKWP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Candidate grid pairs of the autotuner for a simulation of this order.
+std::vector<LaunchCfg> tune_candidates(int order) {
+    std::vector<LaunchCfg> c;
+    const int sms = sm_count();
+    for (int pb : {1, 2, 4, 8, 16})
+        for (int wb : {1, 2}) {
+            if (order != 2 && wb != 1) continue;
+            c.push_back(LaunchCfg{pb * sms, wb * sms});
+        }
+    return c;
+}
+
+// Device time of `steps` steps enqueued by `run` on stream q.
+template <class F> int time_steps(cudaStream_t q, F&& run, float& ms) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    CU(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return fail(UGKWP_E_CUDA, "cudaEventCreate");
+    }
+    int rc = UGKWP_OK;
+    if (cudaEventRecord(a, q) != cudaSuccess) rc = fail(UGKWP_E_CUDA, "cudaEventRecord");
+    if (rc == UGKWP_OK) rc = run();
+    if (rc == UGKWP_OK && cudaEventRecord(b, q) != cudaSuccess) rc = fail(UGKWP_E_CUDA, "cudaEventRecord");
+    if (rc == UGKWP_OK && cudaEventSynchronize(b) != cudaSuccess) rc = fail(UGKWP_E_CUDA, "cudaEventSynchronize");
+    if (rc == UGKWP_OK && cudaEventElapsedTime(&ms, a, b) != cudaSuccess) rc = fail(UGKWP_E_CUDA, "cudaEventElapsedTime");
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ugkwp_autotune(ugkwp_sim* s, int32_t steps_per_trial, ugkwp_launch_cfg* best) {
+    if (!s) return fail(UGKWP_E_ARG, "NULL simulation");
+    if (steps_per_trial < 2 || (steps_per_trial & 1)) return fail(UGKWP_E_ARG, "steps_per_trial must be even and >= 2");
+    if (s->timing) return fail(UGKWP_E_STATE, "per-kernel timing is enabled");
+    float best_ms = 0.0f;
+    LaunchCfg best_lc = s->lc;
+    bool have = false;
+    for (const LaunchCfg& c : tune_candidates(s->P.order)) {
+        ugkwp_launch_cfg u{c.particle_blocks, c.wave_blocks};
+        int rc = ugkwp_set_launch_cfg(s, &u);
+        if (rc) return rc;
+        rc = ugkwp_step(s, 2, nullptr);
+        if (rc) return rc;
+        float ms = 0.0f;
+        rc = time_steps(s->stream, [&] { return ugkwp_step(s, steps_per_trial, nullptr); }, ms);
+        if (rc) return rc;
+        rc = read_error(s);
+        if (rc) return rc;
+        if (!have || ms < best_ms) { best_ms = ms; best_lc = c; have = true; }
+    }
+    ugkwp_launch_cfg u{best_lc.particle_blocks, best_lc.wave_blocks};
+    int rc = ugkwp_set_launch_cfg(s, &u);
+    if (rc) return rc;
+    if (best) *best = u;
+    return UGKWP_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+struct ugkwp_batch {
+    std::vector<ugkwp_sim*> sims;
+    cudaStream_t stream = nullptr;
+    std::vector<cudaStream_t> lanes;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    // two-step graphs keyed by every member's buffer A (ping-pong parities)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::vector<void*> key[2];
+    std::vector<std::vector<int64_t>> launches[2];  // per member, per kernel class
+    void drop_graphs() {
+        for (int k = 0; k < 2; ++k) {
+            if (graph[k]) cudaGraphExecDestroy(graph[k]);
+            graph[k] = nullptr;
+            key[k].clear();
+            launches[k].clear();
+        }
+    }
+    ~ugkwp_batch() {
+        if (stream) cudaStreamSynchronize(stream);
+        drop_graphs();
+        for (auto e : join) if (e) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+        for (auto l : lanes) if (l) cudaStreamDestroy(l);
+    }
+};
+
+namespace {
+
+std::vector<void*> batch_key(const ugkwp_batch* b) {
+    std::vector<void*> k;
+    k.reserve(b->sims.size());
+    for (auto* s : b->sims) k.push_back(s->A.x[0]);
+    return k;
+}
+
+bool batch_graphs_allowed(const ugkwp_batch* b) {
+    for (auto* s : b->sims)
+        if (s->timing || !s->graphs_ok) return false;
+    return true;
+}
+
+// Enqueue `n` (1 or 2) steps of every member on the batch's lanes, forked from
+// and joined back into the batch stream.
+int batch_enqueue(ugkwp_batch* b, int n) {
+    CU(cudaEventRecord(b->fork, b->stream));
+    const size_t L = b->lanes.size();
+    for (size_t i = 0; i < b->sims.size(); ++i) {
+        ugkwp_sim* s = b->sims[i];
+        cudaStream_t lane = b->lanes[i % L];
+        CU(cudaStreamWaitEvent(lane, b->fork, 0));
+        cudaStream_t own = s->stream;
+        s->stream = lane;
+        int rc = UGKWP_OK;
+        for (int k = 0; k < n && rc == UGKWP_OK; ++k) rc = enqueue_step(s);
+        s->stream = own;
+        if (rc) return rc;
+        CU(cudaEventRecord(b->join[i], lane));
+        CU(cudaStreamWaitEvent(b->stream, b->join[i], 0));
+    }
+    return UGKWP_OK;
+}
+
+int batch_step_pair(ugkwp_batch* b, bool& used) {
+    used = false;
+    if (!batch_graphs_allowed(b)) return UGKWP_OK;
+    const std::vector<void*> k = batch_key(b);
+    int slot = b->key[0] == k ? 0 : b->key[1] == k ? 1 : -1;
+    if (slot < 0) {
+        slot = b->graph[0] ? 1 : 0;
+        if (b->graph[slot]) { cudaGraphExecDestroy(b->graph[slot]); b->graph[slot] = nullptr; }
+        std::vector<std::vector<int64_t>> saved(b->sims.size());
+        for (size_t i = 0; i < b->sims.size(); ++i)
+            saved[i].assign(b->sims[i]->launches, b->sims[i]->launches + UGKWP_N_KERNELS);
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return UGKWP_OK;
+        }
+        int rc = batch_enqueue(b, 2);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        b->launches[slot].assign(b->sims.size(), std::vector<int64_t>(UGKWP_N_KERNELS, 0));
+        for (size_t i = 0; i < b->sims.size(); ++i)
+            for (int c = 0; c < UGKWP_N_KERNELS; ++c) {
+                b->launches[slot][i][c] = b->sims[i]->launches[c] - saved[i][c];
+                b->sims[i]->launches[c] = saved[i][c];
+            }
+        if (rc != UGKWP_OK || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return rc;
+        }
+        e = cudaGraphInstantiate(&b->graph[slot], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b->graph[slot] = nullptr;
+            return UGKWP_OK;
+        }
+        b->key[slot] = k;
+    }
+    CU(cudaGraphLaunch(b->graph[slot], b->stream));
+    for (size_t i = 0; i < b->sims.size(); ++i)
+        for (int c = 0; c < UGKWP_N_KERNELS; ++c) b->sims[i]->launches[c] += b->launches[slot][i][c];
+    used = true;
+    return UGKWP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ugkwp_batch_create(ugkwp_sim* const* sims, int32_t n_sims, void* cuda_stream, ugkwp_batch** out) {
+    if (!out) return fail(UGKWP_E_ARG, "NULL argument");
+    *out = nullptr;
+    if (!sims || n_sims <= 0) return fail(UGKWP_E_ARG, "a batch needs at least one simulation");
+    std::vector<ugkwp_sim*> v(sims, sims + n_sims);
+    for (auto* s : v)
+        if (!s) return fail(UGKWP_E_ARG, "NULL simulation in the batch");
+    std::vector<ugkwp_sim*> sorted = v;
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+        return fail(UGKWP_E_ARG, "a simulation appears twice in the batch");
+    ugkwp_batch* b = new ugkwp_batch;
+    b->sims = v;
+    b->stream = (cudaStream_t)cuda_stream;
+    const int n_lanes = std::min(n_sims, 32);
+    cudaError_t ce = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int i = 0; i < n_lanes && ce == cudaSuccess; ++i) {
+        cudaStream_t l = nullptr;
+        ce = cudaStreamCreateWithFlags(&l, cudaStreamNonBlocking);
+        b->lanes.push_back(l);
+    }
+    b->join.assign(v.size(), nullptr);
+    for (size_t i = 0; i < v.size() && ce == cudaSuccess; ++i) ce = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    if (ce != cudaSuccess) {
+        delete b;
+        return cuda_fail(ce, "ugkwp_batch_create");
+    }
+    *out = b;
+    return UGKWP_OK;
+}
+
+int ugkwp_batch_step(ugkwp_batch* b, int32_t n_steps) {
+    if (!b || n_steps < 0) return fail(UGKWP_E_ARG, "invalid argument");
+    for (auto* s : b->sims)
+        if (s->step + n_steps >= ((int64_t)1 << 24) - 2) return fail(UGKWP_E_STATE, "step counter exhausted (2^24 steps)");
+    for (int32_t k = 0; k < n_steps;) {
+        if (n_steps - k >= 2) {
+            bool used = false;
+            int rc = batch_step_pair(b, used);
+            if (rc) return rc;
+            if (used) {
+                for (auto* s : b->sims) s->step += 2;
+                k += 2;
+                continue;
+            }
+        }
+        int rc = batch_enqueue(b, 1);
+        if (rc) return rc;
+        for (auto* s : b->sims) s->step += 1;
+        k += 1;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    return UGKWP_OK;
+}
+
+int ugkwp_batch_sync(ugkwp_batch* b) {
+    if (!b) return fail(UGKWP_E_ARG, "NULL batch");
+    CU(cudaStreamSynchronize(b->stream));
+    for (size_t i = 0; i < b->sims.size(); ++i) {
+        int rc = read_error(b->sims[i]);
+        if (rc) return fail(rc, "batch member " + std::to_string(i) + ": " + g_err);
+    }
+    return UGKWP_OK;
+}
+
+int ugkwp_batch_autotune(ugkwp_batch* b, int32_t steps_per_trial, ugkwp_launch_cfg* best) {
+    if (!b) return fail(UGKWP_E_ARG, "NULL batch");
+    if (steps_per_trial < 2 || (steps_per_trial & 1)) return fail(UGKWP_E_ARG, "steps_per_trial must be even and >= 2");
+    int order = 1;
+    for (auto* s : b->sims) {
+        if (s->timing) return fail(UGKWP_E_STATE, "per-kernel timing is enabled on a member");
+        order = std::max(order, (int)s->P.order);
+    }
+    float best_ms = 0.0f;
+    LaunchCfg best_lc{0, 0};
+    bool have = false;
+    for (const LaunchCfg& c : tune_candidates(order)) {
+        ugkwp_launch_cfg u{c.particle_blocks, c.wave_blocks};
+        for (auto* s : b->sims) {
+            int rc = ugkwp_set_launch_cfg(s, &u);
+            if (rc) return rc;
+        }
+        b->drop_graphs();
+        int rc = ugkwp_batch_step(b, 2);
+        if (rc) return rc;
+        float ms = 0.0f;
+        rc = time_steps(b->stream, [&] { return ugkwp_batch_step(b, steps_per_trial); }, ms);
+        if (rc) return rc;
+        rc = ugkwp_batch_sync(b);
+        if (rc) return rc;
+        if (!have || ms < best_ms) { best_ms = ms; best_lc = c; have = true; }
+    }
+    ugkwp_launch_cfg u{best_lc.particle_blocks, best_lc.wave_blocks};
+    for (auto* s : b->sims) {
+        int rc = ugkwp_set_launch_cfg(s, &u);
+        if (rc) return rc;
+    }
+    b->drop_graphs();
+    if (best) *best = u;
+    return UGKWP_OK;
+}
+
+int ugkwp_batch_free(ugkwp_batch* b) {
+    delete b;
+    return UGKWP_OK;
 }
 
 }  // extern "C"

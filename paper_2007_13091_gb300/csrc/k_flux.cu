@@ -17,12 +17,9 @@
 #include "ugkwp_internal.hpp"
 
 // The second-order wave kernels are bound by the FP64 pipe, which a few warps
-// per SM saturate; they run as persistent grids of WAVE_BLOCKS_PER_SM blocks
-// per SM so that the particle kernels running beside them keep most of each
-// SM's registers and warp slots.
-#ifndef UGKWP_WAVE_BLOCKS_PER_SM
-#define UGKWP_WAVE_BLOCKS_PER_SM 1
-#endif
+// per SM saturate; they run as persistent grids (by default one block per SM,
+// see LaunchCfg) so that the particle kernels running beside them keep most of
+// each SM's registers and warp slots.
 #ifndef UGKWP_WAVE_THREADS
 #define UGKWP_WAVE_THREADS 128
 #endif
@@ -618,19 +615,20 @@ __global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevPar
 
 }  // namespace
 
-static int wave_grid(int n) {
-    const int cap = sm_count() * UGKWP_WAVE_BLOCKS_PER_SM;
+static int wave_grid(int n, int blocks) {
     const int need = (n + UGKWP_WAVE_THREADS - 1) / UGKWP_WAVE_THREADS;
-    return need < cap ? need : cap;
+    return need < blocks ? need : blocks;
 }
 
-void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
-    k_gradients<<<wave_grid(m.nc), UGKWP_WAVE_THREADS, 0, st>>>(m, s, p);
+void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, int blocks, cudaStream_t st) {
+    k_gradients<<<wave_grid(m.nc, blocks), UGKWP_WAVE_THREADS, 0, st>>>(m, s, p);
 }
 
-void launch_face_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
-    k_face_flux_o2<<<wave_grid(m.nif), UGKWP_WAVE_THREADS, 0, st>>>(m, s, p);
+void launch_face_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p, int blocks, cudaStream_t st) {
+    k_face_flux_o2<<<wave_grid(m.nif, blocks), UGKWP_WAVE_THREADS, 0, st>>>(m, s, p);
 }
+
+int wave_threads() { return UGKWP_WAVE_THREADS; }
 
 void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, int first, cudaStream_t st) {
     k_face_flux<<<(m.nf - first + 255) / 256, 256, 0, st>>>(m, s, p, first);

@@ -75,6 +75,57 @@ __global__ void __launch_bounds__(256) k_scatter(DevState s, PartBufRaw ar, Part
 }
 
 // ------------------------------------------------------------------ sampling
+// The three normals X of the pair whose first member has id `ida`: Box-Muller
+// in the particle precision (binary32 in the mixed mode).
+template <class Real>
+__device__ __forceinline__ void pair_normals(unsigned long long ida, long long step, unsigned long long seed, Real X[3]) {
+    const dm::U4 r = dm::philox(ida, (unsigned long long)step, TAG_SVEL, 0ULL, seed, 0ULL);
+    if constexpr (sizeof(Real) == 4) {
+        float sn, cs;
+        float rad = sqrtf(-2.0f * dm::f_log(dm::u01f(r.a)));
+        dm::f_sincos2pi(dm::u01f(r.b), &sn, &cs);
+        X[0] = rad * cs;
+        X[1] = rad * sn;
+        rad = sqrtf(-2.0f * dm::f_log(dm::u01f(r.c)));
+        dm::f_sincos2pi(dm::u01f(r.d), &sn, &cs);
+        X[2] = rad * cs;
+    } else {
+        double sn, cs;
+        double rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.a)));
+        dm::d_sincos2pi(dm::u01d(r.b), &sn, &cs);
+        X[0] = rad * cs;
+        X[1] = rad * sn;
+        rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.c)));
+        dm::d_sincos2pi(dm::u01d(r.d), &sn, &cs);
+        X[2] = rad * cs;
+    }
+}
+
+// Energy-matched sampling: one factor per cell, s^2 sum_j |X_j|^2 = 3 N_sam / 2,
+// so the pairs' thermal energy is exactly rho^hp |Omega| (3/2) R T.  The sum
+// runs over the cell's pairs in order in binary64; spread = s sqrt(RT).
+template <class Real>
+__global__ void __launch_bounds__(256) k_sample_scale(DevMesh m, DevState s, DevParams p) {
+    const int nc = m.nc;
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= nc) return;
+    const long long step = s.cnt64[CNT_STEP];
+    const int ns = s.nsam[cell];
+    double sig = sqrt(p.R * s.prim[4 * nc + cell]);
+    if (ns >= 2) {
+        double S = 0.0;
+        for (int j = 0; j < ns / 2; ++j) {
+            Real X[3];
+            pair_normals<Real>(make_id(step, cell, 2 * j), step, p.seed, X);
+            const double x0 = (double)X[0], x1 = (double)X[1], x2 = (double)X[2];
+            S = S + ((x0 * x0 + x1 * x1) + x2 * x2);
+        }
+        if (S > 0.0) sig = sig * sqrt((double)(3 * (ns / 2)) / S);
+    }
+    s.sig[cell] = sig;
+    if constexpr (sizeof(Real) == 4) s.usig[cell].w = (float)sig;
+}
+
 template <class Real>
 __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, DevParams p, PartBufRaw br) {
     if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
@@ -100,15 +151,8 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
             // vertex and edges rounded to binary32
             const float4 us = s.usig[cell];
             const unsigned long long ida = make_id(step, cell, k - side);
-            const dm::U4 r = dm::philox(ida, (unsigned long long)step, TAG_SVEL, 0ULL, p.seed, 0ULL);
-            float sn, cs, X[3];
-            float rad = sqrtf(-2.0f * dm::f_log(dm::u01f(r.a)));
-            dm::f_sincos2pi(dm::u01f(r.b), &sn, &cs);
-            X[0] = rad * cs;
-            X[1] = rad * sn;
-            rad = sqrtf(-2.0f * dm::f_log(dm::u01f(r.c)));
-            dm::f_sincos2pi(dm::u01f(r.d), &sn, &cs);
-            X[2] = rad * cs;
+            float X[3];
+            pair_normals<float>(ida, step, p.seed, X);
             const unsigned long long id = ida + (unsigned long long)side;
             const dm::U4 rp = dm::philox(id, (unsigned long long)step, TAG_SPOS, 0ULL, p.seed, 0ULL);
             float a = dm::u01f(rp.a), bb = dm::u01f(rp.b), cc = dm::u01f(rp.c);
@@ -138,17 +182,10 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
             continue;
         }
         const double U[3] = {s.prim[nc + cell], s.prim[2 * nc + cell], s.prim[3 * nc + cell]};
-        const double sig = sqrt(p.R * s.prim[4 * nc + cell]);
+        const double sig = p.sampling == UGKWP_SAMPLE_ENERGY_MATCHED ? s.sig[cell] : sqrt(p.R * s.prim[4 * nc + cell]);
         const unsigned long long ida = make_id(step, cell, k - side);
-        const dm::U4 r = dm::philox(ida, (unsigned long long)step, TAG_SVEL, 0ULL, p.seed, 0ULL);
-        double sn, cs, X[3];
-        double rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.a)));
-        dm::d_sincos2pi(dm::u01d(r.b), &sn, &cs);
-        X[0] = rad * cs;
-        X[1] = rad * sn;
-        rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.c)));
-        dm::d_sincos2pi(dm::u01d(r.d), &sn, &cs);
-        X[2] = rad * cs;
+        double X[3];
+        pair_normals<double>(ida, step, p.seed, X);
         const unsigned long long id = ida + (unsigned long long)side;
         const dm::U4 rp = dm::philox(id, (unsigned long long)step, TAG_SPOS, 0ULL, p.seed, 0ULL);
         double a = dm::u01d(rp.a), bb = dm::u01d(rp.b), cc = dm::u01d(rp.c);
@@ -577,28 +614,33 @@ __global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams
 }  // namespace
 
 void launch_scatter(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
-                    const PartBufRaw& b, cudaStream_t st) {
+                    const PartBufRaw& b, int blocks, cudaStream_t st) {
     (void)m;
-    if (p.precision == UGKWP_MIXED) k_scatter<float><<<particle_grid(), 256, 0, st>>>(s, a, b);
-    else k_scatter<double><<<particle_grid(), 256, 0, st>>>(s, a, b);
+    if (p.precision == UGKWP_MIXED) k_scatter<float><<<blocks, 256, 0, st>>>(s, a, b);
+    else k_scatter<double><<<blocks, 256, 0, st>>>(s, a, b);
 }
 
 void launch_sample_write(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b,
-                         cudaStream_t st) {
+                         int blocks, cudaStream_t st) {
     (void)m;
-    if (p.precision == UGKWP_MIXED) k_sample_write<float><<<particle_grid(), 256, 0, st>>>(m, s, p, b);
-    else k_sample_write<double><<<particle_grid(), 256, 0, st>>>(m, s, p, b);
+    if (p.precision == UGKWP_MIXED) k_sample_write<float><<<blocks, 256, 0, st>>>(m, s, p, b);
+    else k_sample_write<double><<<blocks, 256, 0, st>>>(m, s, p, b);
+}
+
+void launch_sample_scale(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
+    if (p.precision == UGKWP_MIXED) k_sample_scale<float><<<(m.nc + 255) / 256, 256, 0, st>>>(m, s, p);
+    else k_sample_scale<double><<<(m.nc + 255) / 256, 256, 0, st>>>(m, s, p);
 }
 
 void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b, const PartBufRaw& a,
-                  cudaStream_t st) {
-    if (p.precision == UGKWP_MIXED) k_track<float><<<particle_grid(), 256, 0, st>>>(m, s, p, b, a);
-    else k_track<double><<<particle_grid(), 256, 0, st>>>(m, s, p, b, a);
+                  int blocks, cudaStream_t st) {
+    if (p.precision == UGKWP_MIXED) k_track<float><<<blocks, 256, 0, st>>>(m, s, p, b, a);
+    else k_track<double><<<blocks, 256, 0, st>>>(m, s, p, b, a);
 }
 
-void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a, cudaStream_t st) {
-    if (p.precision == UGKWP_MIXED) k_movers<float><<<particle_grid(), 256, 0, st>>>(m, s, p, a);
-    else k_movers<double><<<particle_grid(), 256, 0, st>>>(m, s, p, a);
+void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a, int blocks, cudaStream_t st) {
+    if (p.precision == UGKWP_MIXED) k_movers<float><<<blocks, 256, 0, st>>>(m, s, p, a);
+    else k_movers<double><<<blocks, 256, 0, st>>>(m, s, p, a);
 }
 
 }  // namespace ugkwp

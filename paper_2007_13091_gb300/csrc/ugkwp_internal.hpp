@@ -55,7 +55,7 @@ struct DevParams {
     double R, mu_ref, T_ref, omega, CFL, C2;
     int32_t N_ref, N_min, max_crossings, precision;
     int32_t order;
-    int32_t pad_;
+    int32_t sampling;      // UGKWP_SAMPLE_*
     uint64_t seed;
     int64_t capacity;
     int32_t exps[5];
@@ -128,7 +128,8 @@ struct DevState {
     double* prim;         // [5][nc] rho, Ux, Uy, Uz, T
     double* tau;          // [nc]
     float* tauf;          // [nc] binary32 rounding of tau (MIXED t_f draw)
-    float4* usig;         // [nc] binary32 roundings of U and sqrt(RT) (MIXED sampling)
+    float4* usig;         // [nc] binary32 roundings of U and the sampling spread (MIXED sampling)
+    double* sig;          // [nc] sampling spread s sqrt(RT) of energy-matched sampling
     double* rhoh;         // [nc]
     double* rhop;         // [nc]
     int32_t* nsam;        // [nc]
@@ -174,20 +175,29 @@ void launch_reset(const DevMesh& m, const DevState& s, cudaStream_t st);
 void launch_cell_prep(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_sample_count(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_scan(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
+// Grid sizes of the step kernels that loop over their work (any positive
+// value gives the same results; chosen for speed, e.g. by the autotuner).
+struct LaunchCfg {
+    int particle_blocks;  // blocks of 256 threads for scatter, sampling, tracking, movers
+    int wave_blocks;      // blocks of the persistent second-order wave kernels
+};
+
 void launch_scatter(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
-                    const PartBufRaw& b, cudaStream_t st);
+                    const PartBufRaw& b, int blocks, cudaStream_t st);
 void launch_sample_write(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b,
-                         cudaStream_t st);
+                         int blocks, cudaStream_t st);
+// Energy-matched sampling: the per-cell spread s sqrt(RT) (sig, usig.w).
+void launch_sample_scale(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 // Tracking of buffer b; particles whose counting flux is non-zero are listed
 // in buffer a (free after the scatter) and their flux added by launch_movers.
 void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b,
-                  const PartBufRaw& a, cudaStream_t st);
+                  const PartBufRaw& a, int blocks, cudaStream_t st);
 void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
-                   cudaStream_t st);
+                   int blocks, cudaStream_t st);
 // First-order flux of face_order[first..nf); second-order flux of the nif interior faces.
 void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, int first, cudaStream_t st);
-void launch_face_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
-void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
+void launch_face_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p, int blocks, cudaStream_t st);
+void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, int blocks, cudaStream_t st);
 void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_rebuild_survivors(const DevMesh& m, const DevState& s, const DevParams& p,
                               const PartBufRaw& a, cudaStream_t st);
@@ -197,6 +207,7 @@ void launch_prim_moments(const DevMesh& m, const DevState& s, const DevParams& p
                          double* out, cudaStream_t st);
 
 int sm_count();       // multiprocessors of the current device
-int particle_grid();  // fixed grid of particle kernels (multiple of the SM count)
+int particle_grid();  // default grid of particle kernels (8 blocks per SM)
+int wave_threads();   // threads per block of the persistent wave kernels
 
 }  // namespace ugkwp

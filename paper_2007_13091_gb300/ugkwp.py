@@ -49,13 +49,21 @@ class Params(ctypes.Structure):
                 ("omega", ctypes.c_double), ("Pr", ctypes.c_double), ("CFL", ctypes.c_double),
                 ("C2", ctypes.c_double), ("venkat_K", ctypes.c_double), ("order", ctypes.c_int32),
                 ("N_ref", ctypes.c_int32), ("N_min", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("max_crossings", ctypes.c_int32), ("n_bc", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("max_crossings", ctypes.c_int32), ("n_bc", ctypes.c_int32), ("sampling", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("particle_capacity", ctypes.c_int64), ("bc", Bc * 16)]
 
 
 class Sizes(ctypes.Structure):
     _fields_ = [("workspace_bytes", ctypes.c_size_t), ("n_cells", ctypes.c_int64), ("n_faces", ctypes.c_int64),
                 ("n_bfaces", ctypes.c_int64)]
+
+
+SAMPLING = {"maxwell": 0, "energy_matched": 1}
+
+
+class LaunchCfg(ctypes.Structure):
+    _fields_ = [("particle_blocks", ctypes.c_int32), ("wave_blocks", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -82,7 +90,9 @@ class AdjointReq(ctypes.Structure):
 
 KERNELS = ["reset", "cell_prep", "sample_count", "scan", "scatter", "sample", "track", "flux", "update", "movers", "gradients", "flux_o2"]
 
-EXPORTED = ["ugkwp_time_step_noalloc", "ugkwp_timing_enable", "ugkwp_timing_read", "ugkwp_mesh_load", "ugkwp_mesh_free", "ugkwp_query_sizes", "ugkwp_init", "ugkwp_free", "ugkwp_step",
+EXPORTED = ["ugkwp_get_launch_cfg", "ugkwp_set_launch_cfg", "ugkwp_autotune", "ugkwp_batch_create",
+            "ugkwp_batch_step", "ugkwp_batch_sync", "ugkwp_batch_autotune", "ugkwp_batch_free",
+            "ugkwp_time_step_noalloc", "ugkwp_timing_enable", "ugkwp_timing_read", "ugkwp_mesh_load", "ugkwp_mesh_free", "ugkwp_query_sizes", "ugkwp_init", "ugkwp_free", "ugkwp_step",
             "ugkwp_sync", "ugkwp_moments", "ugkwp_state_info", "ugkwp_export_state", "ugkwp_import_state",
             "ugkwp_last", "ugkwp_adjoint_wave", "ugkwp_last_error"]
 
@@ -119,6 +129,14 @@ def lib():
             "ugkwp_timing_enable": [vp, i32],
             "ugkwp_timing_read": [vp, vp, vp],
             "ugkwp_time_step_noalloc": [vp, vp, vp, i32, ctypes.c_double, ctypes.c_double, vp, vp],
+            "ugkwp_get_launch_cfg": [vp, P(LaunchCfg)],
+            "ugkwp_set_launch_cfg": [vp, P(LaunchCfg)],
+            "ugkwp_autotune": [vp, i32, P(LaunchCfg)],
+            "ugkwp_batch_create": [vp, i32, vp, P(vp)],
+            "ugkwp_batch_step": [vp, i32],
+            "ugkwp_batch_sync": [vp],
+            "ugkwp_batch_autotune": [vp, i32, P(LaunchCfg)],
+            "ugkwp_batch_free": [vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -153,6 +171,7 @@ def make_params(p: dict) -> Params:
     o.seed = int(p["seed"])
     o.particle_capacity = int(p["particle_capacity"])
     o.n_bc = len(p["bc"])
+    o.sampling = SAMPLING[p.get("sampling", "maxwell")]
     for k, b in enumerate(p["bc"]):
         c = o.bc[k]
         c.type = BC_TYPES[b["type"]]
@@ -304,6 +323,48 @@ def ugkwp_time_step_noalloc(d_W: int, d_vol: int, d_dS: int, n_cells: int, R: fl
                                          ctypes.c_void_p(stream)))
 
 
+def ugkwp_get_launch_cfg(sim) -> dict:
+    c = LaunchCfg()
+    _check(lib().ugkwp_get_launch_cfg(sim, ctypes.byref(c)))
+    return {"particle_blocks": c.particle_blocks, "wave_blocks": c.wave_blocks}
+
+
+def ugkwp_set_launch_cfg(sim, particle_blocks: int, wave_blocks: int):
+    c = LaunchCfg(int(particle_blocks), int(wave_blocks))
+    _check(lib().ugkwp_set_launch_cfg(sim, ctypes.byref(c)))
+
+
+def ugkwp_autotune(sim, steps_per_trial: int = 2) -> dict:
+    c = LaunchCfg()
+    _check(lib().ugkwp_autotune(sim, int(steps_per_trial), ctypes.byref(c)))
+    return {"particle_blocks": c.particle_blocks, "wave_blocks": c.wave_blocks}
+
+
+def ugkwp_batch_create(handles, stream: int):
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    out = ctypes.c_void_p()
+    _check(lib().ugkwp_batch_create(arr, len(handles), ctypes.c_void_p(stream), ctypes.byref(out)))
+    return out
+
+
+def ugkwp_batch_step(batch, n: int):
+    _check(lib().ugkwp_batch_step(batch, int(n)))
+
+
+def ugkwp_batch_sync(batch):
+    _check(lib().ugkwp_batch_sync(batch))
+
+
+def ugkwp_batch_autotune(batch, steps_per_trial: int = 2) -> dict:
+    c = LaunchCfg()
+    _check(lib().ugkwp_batch_autotune(batch, int(steps_per_trial), ctypes.byref(c)))
+    return {"particle_blocks": c.particle_blocks, "wave_blocks": c.wave_blocks}
+
+
+def ugkwp_batch_free(batch):
+    _check(lib().ugkwp_batch_free(batch))
+
+
 # ------------------------------------------------------------ convenience
 class Simulation:
     """A UGKWP simulation on one GPU: workspace from the PyTorch allocator,
@@ -360,3 +421,36 @@ class Simulation:
 
     def last(self, which: str):
         return ugkwp_last(self.handle, which, self.n_cells, self.n_faces)
+
+
+class Batch:
+    """Independent simulations stepped together, one CUDA graph per step pair
+    launched on `stream` (a new PyTorch stream by default).  Members keep their
+    own results; read them after sync()."""
+
+    def __init__(self, sims, stream=None):
+        import torch
+        self.sims = list(sims)
+        dev = self.sims[0].device
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        self.handle = ugkwp_batch_create([s.handle for s in self.sims], self.stream.cuda_stream)
+
+    def step(self, n: int = 1):
+        ugkwp_batch_step(self.handle, n)
+
+    def sync(self):
+        ugkwp_batch_sync(self.handle)
+
+    def autotune(self, steps_per_trial: int = 2) -> dict:
+        return ugkwp_batch_autotune(self.handle, steps_per_trial)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ugkwp_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

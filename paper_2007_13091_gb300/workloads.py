@@ -150,9 +150,10 @@ def _params(Kn, omega, CFL, N_ref, precision, seed, bc, C2=0.0, N_min=0, capacit
 
 
 def shock_tube(nx=100, ny=4, nz=4, Kn=1e-2, N_ref=50, precision="fp64", CFL=0.5, seed=1,
-               omega=0.81, C2=0.0, length=1.0, width=0.04, order=1):
+               omega=0.81, C2=0.0, length=1.0, width=0.04, order=1, U=0.0):
     """3D Sod tube [0,1] x [0,0.04]^2: left rho=1, p=1; right rho=0.125, p=0.1;
-    far-field (outflow) ends, specular side walls."""
+    both moving at U along x (0 for the Sod problem); far-field ends holding
+    the undisturbed states, specular side walls."""
     xs = np.linspace(0.0, length, nx + 1)
     ys = np.linspace(0.0, width, ny + 1)
     zs = np.linspace(0.0, width, nz + 1)
@@ -162,10 +163,11 @@ def shock_tube(nx=100, ny=4, nz=4, Kn=1e-2, N_ref=50, precision="fp64", CFL=0.5,
     left = c[:, 0] < 0.5 * length
     rho = np.where(left, 1.0, 0.125)
     p = np.where(left, 1.0, 0.1)
-    W0 = conservative(rho, np.zeros(3), p)
+    Uv = np.array([U, 0.0, 0.0])
+    W0 = conservative(rho, Uv, p)
     # far-field ends hold the undisturbed left and right states
-    WL = conservative(np.array(1.0), np.zeros(3), np.array(1.0))
-    WR = conservative(np.array(0.125), np.zeros(3), np.array(0.1))
+    WL = conservative(np.array(1.0), Uv, np.array(1.0))
+    WR = conservative(np.array(0.125), Uv, np.array(0.1))
     bc = [{"type": "farfield", "W_in": tuple(float(v) for v in WL)},
           {"type": "farfield", "W_in": tuple(float(v) for v in WR)}, {"type": "specular"}]
     params = _params(Kn, omega, CFL, N_ref, precision, seed, bc, C2=C2, n_cells=len(tets), order=order)
@@ -266,3 +268,36 @@ def uniform_box(n=(3, 3, 3), size=(1.0, 1.0, 1.0), rho=1.0, U=(0.0, 0.0, 0.0), p
     params = _params(Kn, omega, CFL, N_ref, precision, seed, [b], n_cells=len(tets))
     return {"name": "uniform_box", "mesh": {"nodes": nodes, "tets": tets, "bfaces": bf, "btags": btags},
             "W0": W0, "params": params}
+
+
+def batch_instances(n=64, seed=4, tets_lo=2000, tets_hi=60000, precision="mixed", order=1, cap_factor=2.0,
+                    moving_tubes=True):
+    """Independent instances of uneven size and Knudsen number for batched
+    stepping: sizes uniform in [tets_lo, tets_hi] tets, Kn log-uniform in
+    [1e-4, 1], Mach uniform in [0.1, 3]; even instances are shock tubes (aspect
+    25:1:1, both states moving at Mach times the left sound speed, N_ref 50),
+    odd ones cavities (lid at that Mach, N_ref 100); instance k has seed
+    1000 seed + k.  Particle capacity cap_factor N_ref per cell (+4096)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        target = rng.uniform(tets_lo, tets_hi)
+        Kn = 10.0 ** rng.uniform(-4.0, 0.0)
+        mach = rng.uniform(0.1, 3.0)
+        s_k = 1000 * seed + k
+        if k % 2 == 0:
+            ny = max(2, int(round((target / (6.0 * 25.0)) ** (1.0 / 3.0))))
+            nx = max(4, int(round(target / (6.0 * ny * ny))))
+            cfg = shock_tube(nx=nx, ny=ny, nz=ny, Kn=Kn, N_ref=50, precision=precision, seed=s_k, order=order,
+                             width=ny / nx, U=mach * math.sqrt(GAMMA) if moving_tubes else 0.0)
+            N_ref = 50
+        else:
+            m = max(3, int(round((target / 6.0) ** (1.0 / 3.0))))
+            cfg = cavity(n=m, Kn=Kn, N_ref=100, precision=precision, seed=s_k, lid_mach=mach, order=order)
+            N_ref = 100
+        nc = len(cfg["mesh"]["tets"])
+        cfg["params"]["particle_capacity"] = int(cap_factor * N_ref * nc + 4096)
+        cfg["name"] = f"instance{k}_" + cfg["name"]
+        cfg["Kn"], cfg["mach"] = Kn, mach
+        out.append(cfg)
+    return out

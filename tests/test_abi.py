@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header():
     # sizes follow from the header's field order with natural alignment
     assert ctypes.sizeof(ugkwp.Bc) == 80
-    assert ctypes.sizeof(ugkwp.Params) == 8 * 8 + 6 * 4 + 8 + 8 + 16 * 80
+    assert ctypes.sizeof(ugkwp.Params) == 8 * 8 + 8 * 4 + 8 + 8 + 16 * 80
     assert ctypes.sizeof(ugkwp.MeshDesc) == 16 + 4 * 8
     assert ctypes.sizeof(ugkwp.State) == 8 + 8 + 8 + 20 + 4 + 6 * 8
 
@@ -65,6 +65,14 @@ def test_mesh_validation_errors():
         ugkwp.ugkwp_mesh_load({**m, "tets": oob})
 
 
+def _raise_sampling(mesh, params):
+    """query_sizes with an unknown sampling mode (bypassing the binding's names)."""
+    p = ugkwp.make_params(params)
+    p.sampling = 7
+    s = ugkwp.Sizes()
+    ugkwp._check(ugkwp.lib().ugkwp_query_sizes(mesh.handle, ctypes.byref(p), ctypes.byref(s)))
+
+
 def test_parameter_validation():
     cfg = wl.uniform_box(n=(2, 2, 2))
     mesh = ugkwp.ugkwp_mesh_load(cfg["mesh"])
@@ -72,6 +80,8 @@ def test_parameter_validation():
                           ("particle_capacity", 2 ** 31, "capacity"), ("Pr", 0.7, "BGK")):
         with pytest.raises(ugkwp.UgkwpError, match=pat):
             ugkwp.ugkwp_query_sizes(mesh, dict(cfg["params"], **{key: val}))
+    with pytest.raises(ugkwp.UgkwpError, match="sampling"):
+        _raise_sampling(mesh, cfg["params"])
     with pytest.raises(ugkwp.UgkwpError, match="venkat_K"):
         ugkwp.ugkwp_query_sizes(mesh, dict(cfg["params"], order=2, venkat_K=-1.0))
     with pytest.raises(ugkwp.UgkwpError, match="no entry"):
@@ -82,3 +92,18 @@ def test_adjoint_reports_unsupported_without_gpu_work():
     with pytest.raises(ugkwp.UgkwpError) as e:
         ugkwp.ugkwp_adjoint_wave(None)
     assert e.value.code == ugkwp.E_UNSUPPORTED
+
+
+def test_batch_and_launch_cfg_reject_bad_arguments_without_gpu_work():
+    """Argument checks that run before any CUDA call."""
+    import ctypes
+    L = ugkwp.lib()
+    out = ctypes.c_void_p()
+    assert L.ugkwp_batch_create(None, 0, None, ctypes.byref(out)) == ugkwp.E_ARG
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert L.ugkwp_batch_create(arr, 2, None, ctypes.byref(out)) == ugkwp.E_ARG
+    assert L.ugkwp_batch_step(None, 1) == ugkwp.E_ARG
+    assert L.ugkwp_batch_sync(None) == ugkwp.E_ARG
+    assert L.ugkwp_set_launch_cfg(None, None) == ugkwp.E_ARG
+    assert L.ugkwp_autotune(None, 2, None) == ugkwp.E_ARG
+    assert L.ugkwp_batch_autotune(None, 2, None) == ugkwp.E_ARG

@@ -1,0 +1,124 @@
+"""Batched stepping, launch configurations and the autotuner on the GPU.
+
+A batch captures every member's step pair into one CUDA graph; the members
+must end bit for bit where they end when stepped alone (their kernels, random
+streams and fixed-point sums are their own), and each member's batched step
+must match the oracle's step teacher-forced from the same state.  Grid sizes
+chosen by hand or by the autotuner change only the speed.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2007_13091_gb300 import ugkwp, workloads as wl
+from tests.test_gpu_parity import assert_particles_equal, compare_step
+
+pytestmark = pytest.mark.gpu
+
+
+def _members():
+    return [
+        wl.shock_tube(nx=40, ny=2, nz=2, precision="mixed", U=0.8),
+        wl.cavity(n=6, N_ref=60, precision="mixed", order=2),
+        wl.uniform_box(n=(3, 3, 3), Kn=0.5, N_ref=30, bc_type="specular", precision="fp64"),
+        wl.cube_flow(h0=0.5, growth=2.0, N_ref=40, precision="mixed", Kn=0.1, order=2),
+    ]
+
+
+def _sim(cfg, stream=None):
+    return ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], stream=stream)
+
+
+def _assert_same(a, b):
+    sa, sb = a.state(), b.state()
+    assert sa["step"] == sb["step"]
+    np.testing.assert_array_equal(sa["W"], sb["W"])
+    assert_particles_equal(sa, sb)
+
+
+def test_batch_equals_members_stepped_alone():
+    import torch
+    cfgs = _members()
+    batched = [_sim(c, torch.cuda.Stream()) for c in cfgs]
+    alone = [_sim(c, torch.cuda.Stream()) for c in cfgs]
+    b = ugkwp.Batch(batched)
+    b.step(5)  # two graph-replayed pairs and one directly enqueued step
+    b.sync()
+    for s in alone:
+        s.step(5)
+    for x, y in zip(batched, alone):
+        _assert_same(x, y)
+    # a member stepped on its own after a sync continues consistently
+    batched[1].step(2)
+    alone[1].step(2)
+    _assert_same(batched[1], alone[1])
+    b.close()
+
+
+def test_batched_step_matches_oracle():
+    """One batched step of each member from the oracle's state, against the
+    oracle's own step (teacher forcing, the single-simulation protocol)."""
+    import torch
+    cfgs = [wl.shock_tube(precision="fp64"), wl.cavity(n=6, N_ref=40, precision="mixed", order=2)]
+    osims = [oracle.OracleSim(c["mesh"], c["W0"], c["params"]) for c in cfgs]
+    gsims = [_sim(c, torch.cuda.Stream()) for c in cfgs]
+    for o, g in zip(osims, gsims):
+        o.step(3)
+        g.set_state(o.state())
+    b = ugkwp.Batch(gsims)
+    b.step(1)
+    b.sync()
+    for o, g in zip(osims, gsims):
+        o.step()
+        compare_step(g, o)
+    b.close()
+
+
+def test_launch_cfg_changes_only_speed():
+    import torch
+    cfg = wl.cavity(n=6, N_ref=60, precision="mixed", order=2)
+    a, c = _sim(cfg, torch.cuda.Stream()), _sim(cfg, torch.cuda.Stream())
+    d = ugkwp.ugkwp_get_launch_cfg(a.handle)
+    assert d["particle_blocks"] > 0 and d["wave_blocks"] > 0
+    ugkwp.ugkwp_set_launch_cfg(a.handle, 7, 3)   # odd grids on purpose
+    assert ugkwp.ugkwp_get_launch_cfg(a.handle) == {"particle_blocks": 7, "wave_blocks": 3}
+    a.step(4)
+    c.step(4)
+    _assert_same(a, c)
+    with pytest.raises(ugkwp.UgkwpError):
+        ugkwp.ugkwp_set_launch_cfg(a.handle, 0, 1)
+
+
+def test_autotuner_picks_a_candidate_and_keeps_results():
+    import torch
+    cfg = wl.cavity(n=6, N_ref=60, precision="mixed", order=2)
+    a, c = _sim(cfg, torch.cuda.Stream()), _sim(cfg, torch.cuda.Stream())
+    best = ugkwp.ugkwp_autotune(a.handle, 2)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert best["particle_blocks"] % sms == 0 and best["wave_blocks"] % sms == 0
+    assert ugkwp.ugkwp_get_launch_cfg(a.handle) == best
+    n = a.step(0, stats=True)["step"]
+    assert n == 10 * 4  # 10 candidates at order 2, 2 warm-up + 2 timed steps each
+    c.step(n)
+    _assert_same(a, c)
+
+
+def test_batch_autotune_and_member_errors():
+    import torch
+    cfgs = _members()[:2]
+    sims = [_sim(c, torch.cuda.Stream()) for c in cfgs]
+    b = ugkwp.Batch(sims)
+    best = b.autotune(2)
+    assert best["particle_blocks"] > 0
+    b.step(2)
+    b.sync()
+    b.close()
+    # a member that overflows its particle capacity is reported by index
+    bad = wl.shock_tube(nx=20, ny=2, nz=2)
+    bad["params"]["particle_capacity"] = 1000
+    sims2 = [_sim(cfgs[0], torch.cuda.Stream()), _sim(bad, torch.cuda.Stream())]
+    b2 = ugkwp.Batch(sims2)
+    b2.step(1)
+    with pytest.raises(ugkwp.UgkwpError, match="batch member 1"):
+        b2.sync()
+    b2.close()

@@ -180,6 +180,22 @@ def test_order2_cavity_teacher_forced():
     assert osim.last("counters")["n_wall_hits"] > 0
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_energy_matched_sampling_teacher_forced(precision):
+    """Energy-matched sampling: the per-cell spread (a sequential binary64 sum over
+    the cell's pairs) and every sampled particle bit for bit."""
+    cfg = wl.shock_tube(precision=precision)
+    cfg["params"]["sampling"] = "energy_matched"
+    gsim, osim = run_teacher_forced(cfg, warm_steps=3)
+    assert osim.last("counters")["n_sampled"] > 0
+
+
+def test_energy_matched_sampling_cavity_order2():
+    cfg = wl.cavity(n=6, N_ref=40, precision="mixed", order=2)
+    cfg["params"]["sampling"] = "energy_matched"
+    run_teacher_forced(cfg, warm_steps=3)
+
+
 def test_specular_box_degenerate_starts():
     """Particles placed exactly on nodes, edges and faces (teacher-forced import)."""
     cfg = wl.uniform_box(n=(3, 3, 3), Kn=0.5, N_ref=10, bc_type="specular")
