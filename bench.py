@@ -269,7 +269,10 @@ def batched(precision, steps, warmup, device):
     import torch
     from paper_2007_13091_gb300 import ugkwp
     from paper_2007_13091_gb300 import workloads as wl
-    cases = wl.batch_instances(precision=precision, order=ORDER)
+    # capacity 4 N_ref per cell: in rarefied cells the printed pair count adds at
+    # least one pair per cell and step, so the population grows by ~2 per cell
+    # and step until collisions balance it
+    cases = wl.batch_instances(precision=precision, order=ORDER, cap_factor=4.0)
     sims = [ugkwp.Simulation(c["mesh"], c["W0"], c["params"], device=device, stream=torch.cuda.Stream(device=device))
             for c in cases]
     b = ugkwp.Batch(sims)
