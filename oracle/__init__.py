@@ -67,6 +67,8 @@ def lib():
         L.orc_slope_moment.argtypes = [vp, d, ctypes.c_int, vp, ctypes.c_int, vp]
         L.orc_micro_slope.argtypes = [vp, d, vp, vp]
         L.orc_face_flux_o2.argtypes = [P(OrcParams), vp, d, vp, vp, vp, vp, d, vp, vp, vp, vp, d, vp]
+        L.orc_frozen_objective.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, vp, i32, vp]
+        L.orc_frozen_value.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, vp, i32, vp]
         L.orc_sample_cell.argtypes = [vp, i32, i64, vp, vp, vp, vp]
         L.orc_sample_cell.restype = i64
         _LIB = L
@@ -302,6 +304,37 @@ class OracleSim:
             keys = ["n_tracked", "n_collided", "n_exited", "n_lost", "n_crossings", "n_wall_hits", "n_sampled"]
             return dict(zip(keys, (int(v) for v in out)))
         return out
+
+    def record_frozen(self, K):
+        """Take K steps, recording what the frozen-particle wave map needs:
+        (W0, dt[K], rho_p[K][nc], pflux[K][5][nc] scaled to conservative units)."""
+        st = self.state()
+        W0 = st["W"].copy()
+        e = st["exps"]
+        nc = W0.shape[1]
+        vol = self.geometry("vol")
+        dt, rho_p, pf = [], [], []
+        for _ in range(K):
+            W = self.state()["W"]
+            self.step()
+            dt.append(self.last("dt"))
+            rho_p.append(W[0] - self.last("rho_h"))
+            q = self.last("pflux").astype(np.float64)
+            pf.append(np.stack([np.ldexp(q[c], int(e[c])) for c in range(5)]))
+        return W0, np.array(dt), np.array(rho_p).reshape(K, nc), np.array(pf).reshape(K, 5, nc)
+
+    def frozen_objective(self, frozen, theta, functional=0, tags=(), grad=True):
+        """J (and dJ/dtheta by dual numbers) of the frozen-particle wave map."""
+        W0, dt, rho_p, pf = (np.ascontiguousarray(a, dtype=np.float64) for a in frozen)
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        tg = np.ascontiguousarray(tags, dtype=np.int32)
+        out = np.zeros(4)
+        fn = lib().orc_frozen_objective if grad else lib().orc_frozen_value
+        rc = fn(self._h, len(dt), _ptr(W0), _ptr(dt), _ptr(rho_p), _ptr(pf), _ptr(th), int(functional),
+                _ptr(tg) if tg.size else None, tg.size, _ptr(out))
+        if rc:
+            raise RuntimeError("oracle frozen objective failed")
+        return out if grad else float(out[0])
 
     def prepare(self):
         """Primitives, tau, rho^h, dt and sampling counts of the current state

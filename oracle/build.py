@@ -17,7 +17,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = SOURCES + ["omath.hpp", "ugkwp_oracle.h"]
+    deps = SOURCES + ["omath.hpp", "dual.hpp", "ugkwp_oracle.h"]
     return any(os.path.getmtime(os.path.join(HERE, f)) > t for f in deps)
 
 

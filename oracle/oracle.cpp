@@ -22,6 +22,7 @@
 // notes; each is marked "reading:" below.
 #include "ugkwp_oracle.h"
 #include "omath.hpp"
+#include "dual.hpp"
 
 #include <algorithm>
 #include <array>
@@ -1266,6 +1267,240 @@ static void scale_exponents(const Geom& g, const orc_params& P, const std::vecto
 
 using namespace orc;
 
+// --------------------------------------------- frozen-particle wave map
+// The wave part of the step with the particle part frozen (first order): from
+// W^0, for n = 0..K-1,
+//   W^{n+1}_i = W^n_i - sum_f (+/-) F_f(W^n) |S_f| / |Omega_i| + pf^n_i / |Omega_i|
+// with the recorded time steps dt^n, particle densities rho^p_n (so that
+// rho^h = rho - rho^p) and particle fluxes pf^n (Sec. 2.3 update with
+// F^{fr,p} a constant).  The face fluxes are those of the step (Sec. 2.1, 2.3,
+// 2.4 (d), (e)), written once more here generic in the scalar type so that
+// the same code gives the value (double) and forward-mode derivatives (Dual).
+// Parameters theta = (rho_inf, U_inf, T_w): every far-field condition whose
+// state equals the first far-field state becomes the Maxwellian of density
+// rho_inf and speed U_inf along that state's velocity direction (x if it is
+// at rest) at its own temperature; every diffuse wall whose tag is listed
+// gets the temperature T_w.  J = sum_n sum_{faces with a listed tag}
+// F_f[c] |S_f|, c = 1 (x momentum delivered to the walls: drag) or 4 (energy:
+// wall heat flux), wave part only.
+namespace frozen {
+
+template <class S> struct PrimS { S rho, U[3], p, T, lam; };
+
+template <class S> PrimS<S> prim_s(const S* W, double R) {
+    PrimS<S> s;
+    s.rho = W[0];
+    for (int d = 0; d < 3; ++d) s.U[d] = W[1 + d] / s.rho;
+    S U2 = (s.U[0] * s.U[0] + s.U[1] * s.U[1]) + s.U[2] * s.U[2];
+    s.p = (W[4] - 0.5 * (s.rho * U2)) / 1.5;
+    s.T = s.p / (s.rho * R);
+    s.lam = s.rho / (2.0 * s.p);
+    return s;
+}
+
+template <class S> S tau_cell_s(const PrimS<S>& s, const orc_params& P) {
+    return (P.mu_ref / s.p) * exp_d(P.omega * log_d(s.T / P.T_ref));
+}
+
+// q1, q4, a4 = q4 - dt e^{-dt/tau}: series below x = dt/tau = 1, closed forms above
+template <class S> void qcoef_s(double dt, const S& tau, S& q1, S& q4, S& a4) {
+    S x = dt / tau;
+    if (x < 1.0) {
+        S s1 = 0.0, s4 = 0.0, sa = 0.0, term = 1.0;
+        for (int k = 1; k <= 30; ++k) {
+            term = term * x / (double)k;
+            double sg = (k % 2 == 0) ? 1.0 : -1.0;
+            if (k >= 2) s1 = s1 + sg * term;
+            s4 = s4 + (-sg) * term;
+            if (k >= 2) sa = sa + (-sg * (double)(1 - k)) * term;
+        }
+        q1 = tau * s1; q4 = tau * s4; a4 = tau * sa;
+    } else {
+        S e = exp(-x);
+        S ph = -expm1(-x);
+        q1 = dt - tau * ph;
+        q4 = tau * ph;
+        a4 = q4 - dt * e;
+    }
+}
+
+template <class S> void un_moments_s(const S& Un, const S& lam, int half, S M[5]) {
+    if (half == 0) {
+        M[0] = 1.0; M[1] = Un;
+    } else {
+        S a = sqrt(lam) * Un;
+        S edge = 0.5 * exp(-lam * Un * Un) / sqrt(PI * lam);
+        if (half > 0) { M[0] = 0.5 * erfc(-a); M[1] = Un * M[0] + edge; }
+        else          { M[0] = 0.5 * erfc(a);  M[1] = Un * M[0] - edge; }
+    }
+    for (int k = 0; k < 3; ++k) M[k + 2] = Un * M[k + 1] + (double)(k + 1) / (2.0 * lam) * M[k];
+}
+
+template <class S> void half_moments_s(const S& Un, const S* Ut, const double* n, const S& lam, int half,
+                                      S H[5], S G[5]) {
+    S M[5];
+    un_moments_s(Un, lam, half, M);
+    S Ut2 = (Ut[0] * Ut[0] + Ut[1] * Ut[1]) + Ut[2] * Ut[2];
+    S tv = Ut2 + 1.0 / lam;
+    H[0] = M[0];
+    G[0] = M[1];
+    for (int d = 0; d < 3; ++d) {
+        H[1 + d] = M[1] * n[d] + M[0] * Ut[d];
+        G[1 + d] = M[2] * n[d] + M[1] * Ut[d];
+    }
+    H[4] = 0.5 * (M[2] + M[0] * tv);
+    G[4] = 0.5 * (M[3] + M[1] * tv);
+}
+
+template <class S> struct FaceS { S rho, rhoh, Un, Ut[3], lam, p, T; };
+
+template <class S> FaceS<S> face_state_s(const S* W, const S& rhoh, const double* n, double R) {
+    PrimS<S> s = prim_s(W, R);
+    FaceS<S> f;
+    f.rho = s.rho; f.rhoh = rhoh; f.lam = s.lam; f.p = s.p; f.T = s.T;
+    f.Un = (s.U[0] * n[0] + s.U[1] * n[1]) + s.U[2] * n[2];
+    for (int d = 0; d < 3; ++d) f.Ut[d] = s.U[d] - f.Un * n[d];
+    return f;
+}
+
+template <class S> void interior_flux_s(const FaceS<S>& L, const FaceS<S>& Rs, bool ghost_hydro, const double* n,
+                                       double dt, const orc_params& P, S F[5]) {
+    S HL[5], GL[5], HR[5], GR[5];
+    half_moments_s(L.Un, L.Ut, n, L.lam, +1, HL, GL);
+    half_moments_s(Rs.Un, Rs.Ut, n, Rs.lam, -1, HR, GR);
+    S W0[5];
+    for (int q = 0; q < 5; ++q) W0[q] = L.rho * HL[q] + Rs.rho * HR[q];
+    PrimS<S> s0 = prim_s(W0, P.R);
+    S tau = P.mu_ref * pow(s0.T / P.T_ref, P.omega) / s0.p;
+    if (P.C2 > 0.0) tau = tau + P.C2 * fabs(L.p - Rs.p) / fabs(L.p + Rs.p) * dt;
+    S q1, q4, a4;
+    qcoef_s(dt, tau, q1, q4, a4);
+    S Un0 = (s0.U[0] * n[0] + s0.U[1] * n[1]) + s0.U[2] * n[2], Ut0[3];
+    for (int d = 0; d < 3; ++d) Ut0[d] = s0.U[d] - Un0 * n[d];
+    S H0[5], G0[5];
+    half_moments_s(Un0, Ut0, n, s0.lam, 0, H0, G0);
+    S cR = ghost_hydro ? q4 : a4;
+    for (int k = 0; k < 5; ++k) F[k] = q1 * (s0.rho * G0[k]) + a4 * (L.rhoh * GL[k]) + cR * (Rs.rhoh * GR[k]);
+}
+
+template <class S> struct BcS { int type; S T_w; double U_w[3]; S W_in[5]; };
+
+template <class S> void boundary_flux_s(const S* WL, const S& rhohL, const S& tauL, const BcS<S>& bc, const double* n,
+                                       double dt, const orc_params& P, S F[5]) {
+    FaceS<S> L = face_state_s(WL, rhohL, n, P.R);
+    if (bc.type == ORC_BC_DIFFUSE_WALL) {
+        S q1, q4, a4;
+        qcoef_s(dt, tauL, q1, q4, a4);
+        S HL[5], GL[5];
+        half_moments_s(L.Un, L.Ut, n, L.lam, +1, HL, GL);
+        S Gin[5];
+        for (int k = 0; k < 5; ++k) Gin[k] = q1 * (L.rho * GL[k]) + a4 * (L.rhoh * GL[k]);
+        S lamw = 1.0 / (2.0 * P.R * bc.T_w);
+        double Uwn = (bc.U_w[0] * n[0] + bc.U_w[1] * n[1]) + bc.U_w[2] * n[2];
+        S Uwt[3];
+        for (int d = 0; d < 3; ++d) Uwt[d] = bc.U_w[d] - Uwn * n[d];
+        S Hw[5], Gw[5];
+        half_moments_s(S(Uwn), Uwt, n, lamw, -1, Hw, Gw);
+        S rhow = -Gin[0] / (dt * Gw[0]);
+        for (int k = 0; k < 5; ++k) F[k] = Gin[k] + dt * rhow * Gw[k];
+        return;
+    }
+    if (bc.type == ORC_BC_SPECULAR) {
+        FaceS<S> Rg = L;
+        Rg.Un = -L.Un;
+        S Ff[5];
+        interior_flux_s(L, Rg, false, n, dt, P, Ff);
+        S fn = (Ff[1] * n[0] + Ff[2] * n[1]) + Ff[3] * n[2];
+        F[0] = 0.0; F[4] = 0.0;
+        for (int d = 0; d < 3; ++d) F[1 + d] = fn * n[d];
+        return;
+    }
+    FaceS<S> Rg = (bc.type == ORC_BC_INFLOW) ? face_state_s(bc.W_in, bc.W_in[0], n, P.R) : L;
+    Rg.rhoh = Rg.rho;
+    interior_flux_s(L, Rg, true, n, dt, P, F);
+}
+
+// The parameterised boundary conditions for theta (see the header comment).
+template <class S> std::vector<BcS<S>> bcs_of(const orc_params& P, const S theta[3], const std::vector<char>& listed) {
+    std::vector<BcS<S>> out(P.n_bc);
+    int ff = -1;
+    for (int b = 0; b < P.n_bc; ++b)
+        if (P.bc[b].type == ORC_BC_INFLOW) { ff = b; break; }
+    for (int b = 0; b < P.n_bc; ++b) {
+        const orc_bc& c = P.bc[b];
+        BcS<S>& o = out[b];
+        o.type = c.type;
+        o.T_w = c.T_w;
+        for (int d = 0; d < 3; ++d) o.U_w[d] = c.U_w[d];
+        for (int q = 0; q < 5; ++q) o.W_in[q] = c.W_in[q];
+        if (c.type == ORC_BC_DIFFUSE_WALL && listed[b]) o.T_w = theta[2];
+        if (c.type == ORC_BC_INFLOW && ff >= 0 && std::memcmp(c.W_in, P.bc[ff].W_in, sizeof(c.W_in)) == 0) {
+            const double r0 = c.W_in[0];
+            const double U0[3] = {c.W_in[1] / r0, c.W_in[2] / r0, c.W_in[3] / r0};
+            const double s0 = std::sqrt((U0[0] * U0[0] + U0[1] * U0[1]) + U0[2] * U0[2]);
+            const double e[3] = {s0 > 0.0 ? U0[0] / s0 : 1.0, s0 > 0.0 ? U0[1] / s0 : 0.0, s0 > 0.0 ? U0[2] / s0 : 0.0};
+            const double p0 = (c.W_in[4] - 0.5 * r0 * s0 * s0) / 1.5;
+            const double RT = p0 / r0;
+            o.W_in[0] = theta[0];
+            for (int d = 0; d < 3; ++d) o.W_in[1 + d] = theta[0] * theta[1] * e[d];
+            o.W_in[4] = theta[0] * (0.5 * theta[1] * theta[1] + 1.5 * RT);
+        }
+    }
+    return out;
+}
+
+template <class S> S objective(const SimBase& sim, int K, const double* W0, const double* dtv, const double* rho_p,
+                               const double* pflux, const S theta[3], int functional, const std::vector<char>& listed) {
+    const Geom& g = sim.g;
+    const orc_params& P = sim.P;
+    const int nc = g.nc, nf = g.nf;
+    const int comp = functional == 0 ? 1 : 4;
+    std::vector<BcS<S>> bcs = bcs_of(P, theta, listed);
+    std::vector<S> W(5 * (size_t)nc), F(5 * (size_t)nf), rhoh(nc), tau(nc);
+    for (size_t k = 0; k < W.size(); ++k) W[k] = W0[k];
+    S J = 0.0;
+    for (int n = 0; n < K; ++n) {
+        const double dt = dtv[n];
+        for (int i = 0; i < nc; ++i) {
+            S Wi[5];
+            for (int q = 0; q < 5; ++q) Wi[q] = W[(size_t)q * nc + i];
+            PrimS<S> pr = prim_s(Wi, P.R);
+            tau[i] = tau_cell_s(pr, P);
+            rhoh[i] = pr.rho - rho_p[(size_t)n * nc + i];
+        }
+        for (int f = 0; f < nf; ++f) {
+            const double* nn = &g.f_n[3 * (size_t)f];
+            const int o = g.f_owner[f], nb = g.f_nbr[f];
+            S WL[5], Fv[5];
+            for (int q = 0; q < 5; ++q) WL[q] = W[(size_t)q * nc + o];
+            if (nb >= 0) {
+                S WR[5];
+                for (int q = 0; q < 5; ++q) WR[q] = W[(size_t)q * nc + nb];
+                FaceS<S> L = face_state_s(WL, rhoh[o], nn, P.R), Rs = face_state_s(WR, rhoh[nb], nn, P.R);
+                interior_flux_s(L, Rs, false, nn, dt, P, Fv);
+            } else {
+                boundary_flux_s(WL, rhoh[o], tau[o], bcs[g.f_bc[f]], nn, dt, P, Fv);
+                if (listed[g.f_bc[f]]) J = J + Fv[comp] * g.f_area[f];
+            }
+            for (int q = 0; q < 5; ++q) F[(size_t)q * nf + f] = Fv[q];
+        }
+        for (int i = 0; i < nc; ++i)
+            for (int q = 0; q < 5; ++q) {
+                S acc = 0.0;
+                for (int k = 0; k < 4; ++k) {
+                    const int f = g.tet_face[4 * i + k];
+                    S v = F[(size_t)q * nf + f] * g.f_area[f];
+                    acc = acc + (g.tet_sign[4 * i + k] > 0 ? v : -v);
+                }
+                S& Wq = W[(size_t)q * nc + i];
+                Wq = (Wq - acc / g.vol[i]) + pflux[((size_t)n * 5 + q) * nc + i] / g.vol[i];
+            }
+    }
+    return J;
+}
+
+}  // namespace frozen
+
 struct orc_sim { SimBase* s; };
 
 static void set_err(char* err, int32_t len, const std::string& msg) {
@@ -1465,6 +1700,34 @@ int64_t orc_sample_cell(const orc_sim* h, int32_t cell, int64_t cap, uint64_t* i
 int orc_track_one(const orc_sim* h, uint64_t id, int32_t cell, double* io_x, double* io_u,
                   double tau_cell_v, double dt, int64_t step, int32_t* cell_out, int32_t* ncross) {
     return h->s->track_one(id, cell, io_x, io_u, tau_cell_v, dt, step, cell_out, ncross);
+}
+
+int orc_frozen_objective(const orc_sim* h, int32_t K, const double* W0, const double* dt, const double* rho_p,
+                         const double* pflux, const double theta[3], int32_t functional, const int32_t* tags,
+                         int32_t n_tags, double out[4]) {
+    const SimBase& sim = *h->s;
+    if (sim.P.order != 1 || K < 1 || (functional != 0 && functional != 1)) return -1;
+    std::vector<char> listed(16, 0);
+    for (int k = 0; k < n_tags; ++k)
+        if (tags[k] >= 0 && tags[k] < 16) listed[tags[k]] = 1;
+    orc::Dual<3> th[3];
+    for (int k = 0; k < 3; ++k) { th[k] = orc::Dual<3>(theta[k]); th[k].d[k] = 1.0; }
+    orc::Dual<3> J = frozen::objective(sim, K, W0, dt, rho_p, pflux, th, functional, listed);
+    out[0] = J.v;
+    for (int k = 0; k < 3; ++k) out[1 + k] = J.d[k];
+    return 0;
+}
+
+int orc_frozen_value(const orc_sim* h, int32_t K, const double* W0, const double* dt, const double* rho_p,
+                     const double* pflux, const double theta[3], int32_t functional, const int32_t* tags,
+                     int32_t n_tags, double* J) {
+    const SimBase& sim = *h->s;
+    if (sim.P.order != 1 || K < 1 || (functional != 0 && functional != 1)) return -1;
+    std::vector<char> listed(16, 0);
+    for (int k = 0; k < n_tags; ++k)
+        if (tags[k] >= 0 && tags[k] < 16) listed[tags[k]] = 1;
+    *J = frozen::objective(sim, K, W0, dt, rho_p, pflux, theta, functional, listed);
+    return 0;
 }
 
 }  // extern "C"

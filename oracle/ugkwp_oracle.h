@@ -115,6 +115,24 @@ int orc_face_flux_o2(const orc_params* p, const double WL[5], double rhohL, cons
                      const double dxL[3], const double WR[5], double rhohR, const double gWR[15],
                      const double gHR[3], const double dxR[3], const double n[3], double dt, double F[5]);
 
+/* Frozen-particle wave map (first order only): K steps of
+ *   W^{n+1} = W^n - sum_f (+/-) F_f(W^n; theta) |S_f| / |Omega| + pf^n / |Omega|
+ * from W0 [5][nc] with the recorded dt[K], particle densities rho_p[K][nc]
+ * (rho^h = rho - rho^p) and particle fluxes pflux[K][5][nc] (scaled, per cell).
+ * theta = (rho_inf, U_inf, T_w) sets every far-field state equal to the first
+ * one (density, speed along its direction, same temperature) and the
+ * temperature of the diffuse walls with a listed tag.  J = sum over steps and
+ * listed boundary faces of F[c] |S|, c = 1 (functional 0, drag) or 4
+ * (functional 1, wall heat flux).  orc_frozen_objective: out = [J, dJ/dtheta]
+ * by forward-mode dual numbers; orc_frozen_value: J alone in binary64.
+ * Return 0, or -1 (order != 1, K < 1, unknown functional). */
+int orc_frozen_objective(const orc_sim* s, int32_t K, const double* W0, const double* dt, const double* rho_p,
+                         const double* pflux, const double theta[3], int32_t functional, const int32_t* tags,
+                         int32_t n_tags, double out[4]);
+int orc_frozen_value(const orc_sim* s, int32_t K, const double* W0, const double* dt, const double* rho_p,
+                     const double* pflux, const double theta[3], int32_t functional, const int32_t* tags,
+                     int32_t n_tags, double* J);
+
 /* Track one particle with the simulation's mesh and parameters (sampled checks
  * at sizes where a whole oracle step would be slow).  io_x/io_u are [3];
  * the particle precision follows the simulation.  Returns the status bits

@@ -305,3 +305,21 @@ def batch_instances(n=64, seed=4, tets_lo=2000, tets_hi=60000, precision="mixed"
         cfg["Kn"], cfg["mach"] = Kn, mach
         out.append(cfg)
     return out
+
+
+def wall_channel(n=(6, 3, 3), size=(1.0, 0.5, 0.5), mach=0.5, Kn=0.05, N_ref=30, precision="fp64", order=1,
+                 T_w=1.0, seed=6, CFL=0.5, omega=0.81):
+    """A box channel: far-field ends at x = 0 and x = L holding the free stream
+    (rho = 1, p = 1, Mach `mach` along x; tag 0), diffuse walls at T_w on the
+    four sides (tag 1); the gas starts as the free stream."""
+    xs, ys, zs = (np.linspace(0.0, s_, k + 1) for k, s_ in zip(n, size))
+    nodes, tets, bf, where = structured_tet_mesh(xs, ys, zs)
+    btags = np.where(where <= 1, 0, 1).astype(np.int32)
+    U = np.array([mach * math.sqrt(GAMMA), 0.0, 0.0])
+    W0 = conservative(np.ones(len(tets)), U, np.ones(len(tets)))
+    W_in = conservative(np.array(1.0), U, np.array(1.0))
+    bc = [{"type": "farfield", "W_in": tuple(float(v) for v in W_in)},
+          {"type": "wall", "T_w": T_w, "U_w": (0.0, 0.0, 0.0)}]
+    params = _params(Kn, omega, CFL, N_ref, precision, seed, bc, n_cells=len(tets), order=order)
+    return {"name": f"channel_{n[0]}x{n[1]}x{n[2]}", "mesh": {"nodes": nodes, "tets": tets, "bfaces": bf,
+            "btags": btags}, "W0": W0, "params": params}
