@@ -294,11 +294,38 @@ int ugkwp_batch_free(ugkwp_batch* b);
 int ugkwp_timing_enable(ugkwp_sim* s, int32_t enable);
 int ugkwp_timing_read(ugkwp_sim* s, double* ms, int64_t* launches);
 
-/* Gradient of a wall functional with respect to far-field / wall parameters
- * with the particle sample frozen (hand-written adjoint of the wave flux and
- * update).  Not available in this build: returns UGKWP_E_UNSUPPORTED. */
-typedef struct { int32_t functional; int32_t n_steps; const int32_t* wall_tags; int32_t n_wall_tags; } ugkwp_adjoint_req;
-int ugkwp_adjoint_wave(ugkwp_sim* s, const ugkwp_adjoint_req* r, double* dJ_dtheta);
+/* ---- adjoint of the wave update with the particle sample frozen ---------
+ * The call takes n_steps = K real steps of the simulation (advancing it like
+ * ugkwp_step), recording each step's time step, particle density rho^p and
+ * particle flux F^{fr,p}.  With those frozen, the wave part of the K steps
+ * from the state at the call is a smooth map
+ *   W^{n+1} = W^n - sum_f (+/-) F_f(W^n; theta) |S_f| / |Omega| + F^{fr,p,n} / |Omega|
+ * (first-order flux of Sec. 2.1, 2.3, 2.4 (d), (e)), and
+ *   J = sum_n sum_{boundary faces with a tag in wall_tags} F_f[c] |S_f|
+ * with c = 1 for functional 0 (x momentum delivered to the walls: drag) and
+ * c = 4 for functional 1 (energy: wall heat flux), wave part only.
+ * theta = (rho_inf, U_inf, T_w): every far-field condition whose state equals
+ * that of the first far-field condition becomes the Maxwellian of density
+ * rho_inf moving at speed U_inf along that state's velocity direction (x if it
+ * is at rest) at that state's temperature; every diffuse wall whose tag is in
+ * wall_tags gets temperature T_w.  theta == NULL evaluates at the simulation's
+ * own values.  out[0] = J at theta, out[1..3] = dJ/dtheta by the hand-written
+ * reverse sweep (face states recomputed from per-step checkpoints of W).
+ * The recorded particle data never depend on theta.  Order 1 only
+ * (E_UNSUPPORTED at order 2); the scratch memory is the caller's device
+ * workspace of at least ugkwp_adjoint_query bytes (256-byte aligned). */
+typedef struct {
+    int32_t functional;          /* 0 drag, 1 wall heat flux */
+    int32_t n_steps;             /* K >= 1 */
+    const int32_t* wall_tags;    /* host array of boundary tags */
+    int32_t n_wall_tags;
+    int32_t reserved_;
+    const double* theta;         /* host [3] or NULL */
+    void* d_workspace;
+    size_t workspace_bytes;
+} ugkwp_adjoint_req;
+int ugkwp_adjoint_query(const ugkwp_sim* s, int32_t n_steps, size_t* bytes);
+int ugkwp_adjoint_wave(ugkwp_sim* s, const ugkwp_adjoint_req* r, double* out);
 
 /* Time step without any device allocation (this library's addition; the
  * paper has no counterpart).  Some callers cannot call cudaMalloc or hand the

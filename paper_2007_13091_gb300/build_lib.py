@@ -28,6 +28,7 @@ CU_UNITS = {
     "k_particles.cu": ["--fmad=false"],
     "k_flux.cu": [],
     "k_noalloc.cu": ["--fmad=false"],
+    "k_adjoint.cu": [],
 }
 CPP_UNITS = ["api.cpp", "mesh.cpp"]
 

@@ -947,9 +947,124 @@ int ugkwp_last(ugkwp_sim* s, int32_t which, void* host_out) {
     return UGKWP_OK;
 }
 
-int ugkwp_adjoint_wave(ugkwp_sim* s, const ugkwp_adjoint_req* r, double* dJ_dtheta) {
-    (void)s; (void)r; (void)dJ_dtheta;
-    return fail(UGKWP_E_UNSUPPORTED, "the adjoint of the wave flux is not available in this build");
+// Device scratch of the adjoint for K steps: checkpoints of W (K + 1), the
+// recorded rho^p (K) and particle fluxes (5 K), time steps, fluxes, face
+// terms, two adjoint states, face products and per-step sums.
+static void adjoint_layout(const ugkwp_sim* s, int K, Carver& c, double** ck, double** rp, double** pf, double** dt,
+                           double** F, double** jf, double** lam0, double** lam1, double** wbar, double** thbar,
+                           double** sums, double** theta) {
+    const size_t nc = s->M.nc, nf = s->M.nf;
+    *ck = c.take<double>((size_t)(K + 1) * 5 * nc);
+    *rp = c.take<double>((size_t)K * nc);
+    *pf = c.take<double>((size_t)K * 5 * nc);
+    *dt = c.take<double>((size_t)K);
+    *F = c.take<double>(5 * nf);
+    *jf = c.take<double>(nf);
+    *lam0 = c.take<double>(5 * nc);
+    *lam1 = c.take<double>(5 * nc);
+    *wbar = c.take<double>(10 * nf);
+    *thbar = c.take<double>(3 * nf);
+    *sums = c.take<double>((size_t)4 * K);
+    *theta = c.take<double>(3);
+}
+
+int ugkwp_adjoint_query(const ugkwp_sim* s, int32_t n_steps, size_t* bytes) {
+    if (!s || !bytes || n_steps < 1) return fail(UGKWP_E_ARG, "invalid argument");
+    Carver c(nullptr);
+    double* p[12];
+    adjoint_layout(s, n_steps, c, &p[0], &p[1], &p[2], &p[3], &p[4], &p[5], &p[6], &p[7], &p[8], &p[9], &p[10], &p[11]);
+    *bytes = (c.off + 255) & ~(size_t)255;
+    return UGKWP_OK;
+}
+
+int ugkwp_adjoint_wave(ugkwp_sim* s, const ugkwp_adjoint_req* r, double* out) {
+    if (!s || !r || !out) return fail(UGKWP_E_ARG, "NULL argument");
+    if (s->P.order != 1) return fail(UGKWP_E_UNSUPPORTED, "the adjoint covers the first-order wave flux only");
+    if (r->n_steps < 1 || (r->functional != 0 && r->functional != 1) || r->n_wall_tags < 0 ||
+        (r->n_wall_tags > 0 && !r->wall_tags))
+        return fail(UGKWP_E_ARG, "invalid adjoint request");
+    const int K = r->n_steps;
+    size_t need = 0;
+    int rc = ugkwp_adjoint_query(s, K, &need);
+    if (rc) return rc;
+    if (!r->d_workspace || r->workspace_bytes < need || ((uintptr_t)r->d_workspace & 255))
+        return fail(UGKWP_E_WORKSPACE, "adjoint workspace missing, misaligned or smaller than ugkwp_adjoint_query");
+    // parameterisation of the boundary conditions
+    AdjParams ap;
+    std::memset(&ap, 0, sizeof(ap));
+    ap.comp = r->functional == 0 ? 1 : 4;
+    for (int k = 0; k < r->n_wall_tags; ++k)
+        if (r->wall_tags[k] >= 0 && r->wall_tags[k] < 16) ap.b[r->wall_tags[k]].listed = 1;
+    int ff = -1, wall = -1;
+    for (int b = 0; b < s->P.n_bc; ++b) {
+        if (s->P.bc[b].type == UGKWP_BC_FARFIELD && ff < 0) ff = b;
+        if (s->P.bc[b].type == UGKWP_BC_DIFFUSE_WALL && ap.b[b].listed && wall < 0) wall = b;
+    }
+    double theta0[3] = {0.0, 0.0, wall >= 0 ? s->P.bc[wall].T_w : 0.0};
+    if (ff >= 0) {
+        const double* Wi = s->P.bc[ff].W_in;
+        const double r0 = Wi[0];
+        const double U0[3] = {Wi[1] / r0, Wi[2] / r0, Wi[3] / r0};
+        const double sp = std::sqrt((U0[0] * U0[0] + U0[1] * U0[1]) + U0[2] * U0[2]);
+        const double e[3] = {sp > 0.0 ? U0[0] / sp : 1.0, sp > 0.0 ? U0[1] / sp : 0.0, sp > 0.0 ? U0[2] / sp : 0.0};
+        const double RT = ((Wi[4] - 0.5 * r0 * sp * sp) / 1.5) / r0;
+        theta0[0] = r0;
+        theta0[1] = sp;
+        for (int b = 0; b < s->P.n_bc; ++b) {
+            if (s->P.bc[b].type != UGKWP_BC_FARFIELD || std::memcmp(s->P.bc[b].W_in, Wi, 5 * sizeof(double)) != 0)
+                continue;
+            ap.b[b].param_ff = 1;
+            for (int d = 0; d < 3; ++d) ap.b[b].e[d] = e[d];
+            ap.b[b].RT = RT;
+        }
+    }
+    for (int b = 0; b < s->P.n_bc; ++b)
+        if (s->P.bc[b].type == UGKWP_BC_DIFFUSE_WALL && ap.b[b].listed) ap.b[b].param_wall = 1;
+    const double th_h[3] = {r->theta ? r->theta[0] : theta0[0], r->theta ? r->theta[1] : theta0[1],
+                            r->theta ? r->theta[2] : theta0[2]};
+    Carver c(r->d_workspace);
+    double *ck, *rp, *pf, *dtv, *F, *jf, *lam0, *lam1, *wbar, *thbar, *sums, *theta;
+    adjoint_layout(s, K, c, &ck, &rp, &pf, &dtv, &F, &jf, &lam0, &lam1, &wbar, &thbar, &sums, &theta);
+    cudaStream_t q = s->stream;
+    const size_t nc = s->M.nc;
+    CU(cudaMemcpyAsync(theta, th_h, sizeof(th_h), cudaMemcpyHostToDevice, q));
+    // 1. record K real steps
+    CU(cudaMemcpyAsync(ck, s->S.W, 5 * nc * sizeof(double), cudaMemcpyDeviceToDevice, q));
+    for (int n = 0; n < K; ++n) {
+        rc = ugkwp_step(s, 1, nullptr);
+        if (rc) return rc;
+        CU(cudaMemcpyAsync(dtv + n, s->S.dt, sizeof(double), cudaMemcpyDeviceToDevice, q));
+        launch_adj_record(s->M, s->S, s->P, rp + (size_t)n * nc, pf + (size_t)n * 5 * nc, q);
+    }
+    rc = read_error(s);
+    if (rc) return rc;
+    std::vector<double> dth(K);
+    CU(cudaMemcpyAsync(dth.data(), dtv, K * sizeof(double), cudaMemcpyDeviceToHost, q));
+    CU(cudaStreamSynchronize(q));
+    // 2. frozen forward at theta: checkpoints and the functional
+    for (int n = 0; n < K; ++n)
+        launch_adj_forward(s->M, s->P, ap, ck + (size_t)n * 5 * nc, rp + (size_t)n * nc, pf + (size_t)n * 5 * nc, dth[n],
+                           theta, F, jf, sums + n, ck + (size_t)(n + 1) * 5 * nc, q);
+    // 3. reverse sweep
+    CU(cudaMemsetAsync(lam1, 0, 5 * nc * sizeof(double), q));
+    double* next = lam1;
+    double* cur = lam0;
+    for (int n = K - 1; n >= 0; --n) {
+        launch_adj_reverse(s->M, s->P, ap, ck + (size_t)n * 5 * nc, rp + (size_t)n * nc, dth[n], theta, next, cur, wbar,
+                           thbar, sums + K + 3 * (size_t)n, q);
+        std::swap(next, cur);
+    }
+    CU(cudaGetLastError());
+    std::vector<double> h(4 * (size_t)K);
+    CU(cudaMemcpyAsync(h.data(), sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost, q));
+    CU(cudaStreamSynchronize(q));
+    out[0] = 0.0;
+    out[1] = out[2] = out[3] = 0.0;
+    for (int n = 0; n < K; ++n) {
+        out[0] += h[n];
+        for (int k = 0; k < 3; ++k) out[1 + k] += h[K + 3 * (size_t)n + k];
+    }
+    return UGKWP_OK;
 }
 
 }  // extern "C"

@@ -206,6 +206,31 @@ void launch_wp_moments(const DevMesh& m, const DevState& s, const DevParams& p, 
 void launch_prim_moments(const DevMesh& m, const DevState& s, const DevParams& p, int which,
                          double* out, cudaStream_t st);
 
+// ---- adjoint of the frozen-particle wave map (first order)
+struct AdjBc {
+    int32_t param_ff;    // far-field state replaced by theta (rho_inf, U_inf)
+    int32_t param_wall;  // diffuse-wall temperature replaced by theta[2]
+    int32_t listed;      // boundary faces with this tag enter the functional
+    int32_t pad;
+    double e[3];         // direction of the parameterised far-field velocity
+    double RT;           // its R T (kept)
+};
+struct AdjParams {
+    AdjBc b[16];
+    int32_t comp;        // 1: x momentum (drag), 4: energy (wall heat flux)
+    int32_t pad;
+};
+void launch_adj_record(const DevMesh& m, const DevState& s, const DevParams& p, double* rho_p, double* pf,
+                       cudaStream_t st);
+// Fluxes at theta, the step's functional term Jn[0] and the next state Wn.
+void launch_adj_forward(const DevMesh& m, const DevParams& p, const AdjParams& ap, const double* W, const double* rho_p,
+                        const double* pf, double dt, const double* theta, double* F, double* jf, double* Jn,
+                        double* Wn, cudaStream_t st);
+// lambda^n from lambda^{n+1} and this step's dJ/dtheta terms th_out[3].
+void launch_adj_reverse(const DevMesh& m, const DevParams& p, const AdjParams& ap, const double* W,
+                        const double* rho_p, double dt, const double* theta, const double* lam_next, double* lam,
+                        double* wbar, double* thbar, double* th_out, cudaStream_t st);
+
 int sm_count();       // multiprocessors of the current device
 int particle_grid();  // default grid of particle kernels (8 blocks per SM)
 int wave_threads();   // threads per block of the persistent wave kernels

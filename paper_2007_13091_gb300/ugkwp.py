@@ -85,12 +85,13 @@ class State(ctypes.Structure):
 
 class AdjointReq(ctypes.Structure):
     _fields_ = [("functional", ctypes.c_int32), ("n_steps", ctypes.c_int32), ("wall_tags", ctypes.c_void_p),
-                ("n_wall_tags", ctypes.c_int32)]
+                ("n_wall_tags", ctypes.c_int32), ("reserved_", ctypes.c_int32), ("theta", ctypes.c_void_p),
+                ("d_workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
 
 
 KERNELS = ["reset", "cell_prep", "sample_count", "scan", "scatter", "sample", "track", "flux", "update", "movers", "gradients", "flux_o2"]
 
-EXPORTED = ["ugkwp_get_launch_cfg", "ugkwp_set_launch_cfg", "ugkwp_autotune", "ugkwp_batch_create",
+EXPORTED = ["ugkwp_adjoint_query", "ugkwp_get_launch_cfg", "ugkwp_set_launch_cfg", "ugkwp_autotune", "ugkwp_batch_create",
             "ugkwp_batch_step", "ugkwp_batch_sync", "ugkwp_batch_autotune", "ugkwp_batch_free",
             "ugkwp_time_step_noalloc", "ugkwp_timing_enable", "ugkwp_timing_read", "ugkwp_mesh_load", "ugkwp_mesh_free", "ugkwp_query_sizes", "ugkwp_init", "ugkwp_free", "ugkwp_step",
             "ugkwp_sync", "ugkwp_moments", "ugkwp_state_info", "ugkwp_export_state", "ugkwp_import_state",
@@ -125,6 +126,7 @@ def lib():
             "ugkwp_import_state": [vp, P(State)],
             "ugkwp_last": [vp, i32, vp],
             "ugkwp_adjoint_wave": [vp, P(AdjointReq), vp],
+            "ugkwp_adjoint_query": [vp, i32, P(sz)],
             "ugkwp_last_error": [ctypes.c_char_p, sz],
             "ugkwp_timing_enable": [vp, i32],
             "ugkwp_timing_read": [vp, vp, vp],
@@ -291,10 +293,21 @@ def ugkwp_last(sim, which: str, n_cells: int, n_faces: int):
     return float(out[0]) if code == 0 else out
 
 
-def ugkwp_adjoint_wave(sim, functional: int = 0, n_steps: int = 1, wall_tags=(), out=None):
+def ugkwp_adjoint_query(sim, n_steps: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().ugkwp_adjoint_query(sim, int(n_steps), ctypes.byref(b)))
+    return int(b.value)
+
+
+def ugkwp_adjoint_wave(sim, functional: int = 0, n_steps: int = 1, wall_tags=(), theta=None, d_workspace: int = 0,
+                       workspace_bytes: int = 0):
+    """[J, dJ/drho_inf, dJ/dU_inf, dJ/dT_w] of the frozen-particle wave map over
+    the next n_steps steps (which the call takes); see include/ugkwp.h."""
     tags = np.ascontiguousarray(wall_tags, dtype=np.int32)
-    req = AdjointReq(functional, n_steps, tags.ctypes.data if tags.size else None, tags.size)
-    out = np.zeros(8) if out is None else out
+    th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float64)
+    req = AdjointReq(int(functional), int(n_steps), tags.ctypes.data if tags.size else None, tags.size, 0,
+                     th.ctypes.data if th is not None else None, d_workspace or None, int(workspace_bytes))
+    out = np.zeros(4)
     _check(lib().ugkwp_adjoint_wave(sim, ctypes.byref(req), out.ctypes.data))
     return out
 
@@ -422,6 +435,17 @@ class Simulation:
     def last(self, which: str):
         return ugkwp_last(self.handle, which, self.n_cells, self.n_faces)
 
+    def adjoint(self, functional: int, n_steps: int, wall_tags, theta=None):
+        """[J, dJ/dtheta] of the frozen-particle wave map over the next n_steps
+        steps (taken by the call); the scratch comes from the PyTorch allocator."""
+        import torch
+        nb = ugkwp_adjoint_query(self.handle, n_steps)
+        ws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+        base = (ws.data_ptr() + 255) // 256 * 256
+        out = ugkwp_adjoint_wave(self.handle, functional, n_steps, wall_tags, theta, base, nb)
+        del ws
+        return out
+
 
 class Batch:
     """Independent simulations stepped together, one CUDA graph per step pair
@@ -454,3 +478,24 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def wall_functional(theta, sim: Simulation, functional: int, n_steps: int, wall_tags):
+    """J(theta) as a differentiable PyTorch scalar: the forward runs the
+    adjoint call (taking n_steps steps of `sim`), the backward returns its
+    hand-written reverse-sweep gradient."""
+    import torch
+
+    class _WallFunctional(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, th):
+            out = sim.adjoint(functional, n_steps, wall_tags, th.detach().double().cpu().numpy())
+            ctx.save_for_backward(torch.tensor(out[1:], dtype=th.dtype, device=th.device))
+            return torch.tensor(out[0], dtype=th.dtype, device=th.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            (g,) = ctx.saved_tensors
+            return gJ * g
+
+    return _WallFunctional.apply(theta)

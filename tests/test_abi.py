@@ -88,10 +88,13 @@ def test_parameter_validation():
         ugkwp.ugkwp_query_sizes(mesh, dict(cfg["params"], bc=[]))
 
 
-def test_adjoint_reports_unsupported_without_gpu_work():
+def test_adjoint_rejects_bad_arguments_without_gpu_work():
     with pytest.raises(ugkwp.UgkwpError) as e:
         ugkwp.ugkwp_adjoint_wave(None)
-    assert e.value.code == ugkwp.E_UNSUPPORTED
+    assert e.value.code == ugkwp.E_ARG
+    with pytest.raises(ugkwp.UgkwpError) as e:
+        ugkwp.ugkwp_adjoint_query(None, 3)
+    assert e.value.code == ugkwp.E_ARG
 
 
 def test_batch_and_launch_cfg_reject_bad_arguments_without_gpu_work():
