@@ -751,18 +751,23 @@ static TrackOut track(const Geom& g, const Planes<Real>& pl, const orc_params& P
     Real u[3] = {pt.u[0], pt.u[1], pt.u[2]};
     Real t0 = 0;
     for (;;) {
+        // exit face: the smallest crossing time (d_k - n_k.x0)/(u.n_k) over the
+        // faces with u.n_k > 0, compared as (d_k - n_k.x0)(u.n_j) <
+        // (d_j - n_j.x0)(u.n_k) (both denominators positive); ties keep the
+        // lower local face; the chosen time is one division
         int best = -1;
-        Real sbest = 0;
+        Real nbest = 0, dbest = 1;
         for (int k = 0; k < 4; ++k) {
             if (k == last) continue;
             const Real* nk = &pl.n[12 * (size_t)tet + 3 * k];
             Real un = (u[0] * nk[0] + u[1] * nk[1]) + u[2] * nk[2];
             if (un > (Real)0) {
                 Real xn = (x0[0] * nk[0] + x0[1] * nk[1]) + x0[2] * nk[2];
-                Real s = (pl.d[4 * (size_t)tet + k] - xn) / un;
-                if (best < 0 || s < sbest) { best = k; sbest = s; }
+                Real num = pl.d[4 * (size_t)tet + k] - xn;
+                if (best < 0 || num * dbest < nbest * un) { best = k; nbest = num; dbest = un; }
             }
         }
+        Real sbest = best >= 0 ? nbest / dbest : (Real)0;
         Real rem = t_end - t0;
         if (best < 0 || sbest >= rem) {
             for (int c = 0; c < 3; ++c) pt.x[c] = x0[c] + u[c] * rem;

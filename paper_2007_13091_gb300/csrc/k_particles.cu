@@ -394,8 +394,10 @@ __global__ void __launch_bounds__(256, UGKWP_TRACK_MIN_BLOCKS) k_track(DevMesh m
             Real t0 = (Real)0;
             Real xe[3];
             for (;;) {
+                // smallest crossing time (d - n.x0)/(u.n) over u.n > 0, compared
+                // by cross products (positive denominators), one division
                 int best = -1;
-                Real sbest = (Real)0;
+                Real nbest = (Real)0, dbest = (Real)1;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     if (k == last) continue;
@@ -404,10 +406,11 @@ __global__ void __launch_bounds__(256, UGKWP_TRACK_MIN_BLOCKS) k_track(DevMesh m
                     const Real un = (u[0] * nx + u[1] * ny) + u[2] * nz;
                     if (un > (Real)0) {
                         const Real xn = (x0[0] * nx + x0[1] * ny) + x0[2] * nz;
-                        const Real sk = (d - xn) / un;
-                        if (best < 0 || sk < sbest) { best = k; sbest = sk; }
+                        const Real num = d - xn;
+                        if (best < 0 || num * dbest < nbest * un) { best = k; nbest = num; dbest = un; }
                     }
                 }
+                Real sbest = best >= 0 ? nbest / dbest : (Real)0;
                 const Real rem = t_end - t0;
                 if (best < 0 || sbest >= rem) {
 #pragma unroll
