@@ -41,7 +41,7 @@ TRACK_BYTES_PER_CELL = {"mixed": 80 + 8, "fp64": 144 + 8}
 # DRAM bytes (read + write) of one k_track launch on this workload, from the ncu
 # capture summarised in profiles/k_track_k_face_flux_cavity24_mixed.md; set to
 # None whenever the kernel changes until it is captured again
-TRACK_DRAM_BYTES = {"mixed": 399780352 + 128354304, "fp64": None}
+TRACK_DRAM_BYTES = {"mixed": 399483648 + 128100864, "fp64": None}
 # Binary64 flops per interior face of k_face_flux_o2 (the second-order wave flux):
 # ncu's executed dadd + dmul + 2 dfma per launch divided by the interior faces, on
 # this workload (profiles/); None until captured for the current kernel.

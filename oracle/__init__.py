@@ -47,6 +47,7 @@ def lib():
         vp, cp = ctypes.c_void_p, ctypes.c_char_p
         L.orc_math_d.argtypes = [ctypes.c_int, vp, vp, i64]
         L.orc_math_logf.argtypes = [vp, vp, i64]
+        L.orc_philox32.argtypes = [vp, vp, vp]
         L.orc_math_sincos2pi_f.argtypes = [vp, vp, vp, i64]
         L.orc_philox.argtypes = [vp, vp, vp]
         L.orc_qcoef.argtypes = [d, d, vp]
@@ -134,6 +135,15 @@ def sincos2pi_f(x):
     cs = np.empty_like(x)
     lib().orc_math_sincos2pi_f(_ptr(x), _ptr(sn), _ptr(cs), x.size)
     return sn, cs
+
+
+def philox32(ctr, key):
+    """Philox4x32-10 of one counter (4 x uint32) and key (2 x uint32)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.empty(4, dtype=np.uint32)
+    lib().orc_philox32(_ptr(c), _ptr(k), _ptr(out))
+    return out
 
 
 def philox(ctr, key):

@@ -18,9 +18,10 @@
 //   sincos2pi sin/cos of 2*pi*u: exact reduction by quarter turns (4u - j),
 //             then Taylor series of sin and cos on [-pi/4, pi/4]; sincos2pi_f
 //             the same in binary32 (sin to th^11/11!, cos to th^12/12!).
-//   philox    Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
-//             numbers: as easy as 1, 2, 3", SC'11): 10 rounds of two 64x64->128
-//             multiplies with the published multipliers and Weyl key bumps.
+//   philox    Philox4x64-10 and Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
+//             "Parallel random numbers: as easy as 1, 2, 3", SC'11): 10 rounds of
+//             two multiplies (64x64->128, resp. 32x32->64) with the published
+//             multipliers and Weyl key bumps.
 //
 // Constants are hexadecimal literals of the exact rationals they stand for
 // (1/k!, 1/(2k+1), ln2 split into a 32-bit head and a tail, pi/2).
@@ -216,6 +217,29 @@ inline Ctr4 philox4x64_10(Ctr4 c, uint64_t k0, uint64_t k1) {
         n.v[1] = lo1;
         n.v[2] = hi0 ^ c.v[3] ^ k1;
         n.v[3] = lo0;
+        c = n;
+        k0 += W0; k1 += W1;
+    }
+    return c;
+}
+
+// Philox4x32-10 (same paper): 10 rounds of two 32x32->64 multiplies with the
+// published multipliers 0xD2511F53, 0xCD9E8D57 and Weyl key bumps 0x9E3779B9,
+// 0xBB67AE85.  Used for the free-transport-time draw, the one draw per particle
+// and step on the tracking path.
+struct Ctr4x32 { uint32_t v[4]; };
+
+inline Ctr4x32 philox4x32_10(Ctr4x32 c, uint32_t k0, uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)M0 * c.v[0];
+        uint64_t p1 = (uint64_t)M1 * c.v[2];
+        Ctr4x32 n;
+        n.v[0] = (uint32_t)(p1 >> 32) ^ c.v[1] ^ k0;
+        n.v[1] = (uint32_t)p1;
+        n.v[2] = (uint32_t)(p0 >> 32) ^ c.v[3] ^ k1;
+        n.v[3] = (uint32_t)p0;
         c = n;
         k0 += W0; k1 += W1;
     }

@@ -52,6 +52,16 @@ static inline Ctr4 draw(uint64_t seed, uint64_t a, uint64_t b, uint64_t tag, uin
     return philox4x64_10(c, seed, 0);
 }
 
+// The free-transport-time draw of particle `id` at `step`: Philox4x32-10 with
+// counter (id low, id high, step, TAG_TF) and key (seed low, seed high); the
+// first two output words form the 64 random bits (word 0 high).
+static inline uint64_t draw_tf(uint64_t seed, uint64_t id, uint64_t step) {
+    Ctr4x32 c;
+    c.v[0] = (uint32_t)id; c.v[1] = (uint32_t)(id >> 32); c.v[2] = (uint32_t)step; c.v[3] = 1u;
+    Ctr4x32 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return ((uint64_t)r.v[0] << 32) | r.v[1];
+}
+
 // ------------------------------------------------------------- small vectors
 static inline double dot3(const double* a, const double* b) { return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]; }
 static inline void cross3(const double* a, const double* b, double* c) {
@@ -1091,10 +1101,10 @@ template <class Real> struct Sim : SimBase {
             Real t_end = dtR;
             bool coll = false;
             if (k < n_old) {
-                Ctr4 r = draw(p.seed, pt.id, (uint64_t)step, TAG_TF, 0);
+                const uint64_t r = draw_tf(p.seed, pt.id, (uint64_t)step);
                 Real tf;
-                if (sizeof(Real) == 8) tf = (Real)(-((double)tau[c0] * log_d(u01_d(r.v[0]))));
-                else tf = (Real)(-((float)tau[c0] * log_f(u01_f(r.v[0]))));
+                if (sizeof(Real) == 8) tf = (Real)(-((double)tau[c0] * log_d(u01_d(r))));
+                else tf = (Real)(-((float)tau[c0] * log_f(u01_f(r))));
                 if (tf < dtR) { coll = true; t_end = tf; }
             }
             TrackOut o = track<Real>(g, pl, p, pt, t_end, (uint64_t)step);
@@ -1218,10 +1228,10 @@ template <class Real> struct Sim : SimBase {
         Real t_end = dtR;
         int st = 0;
         if (id_step(id) != (uint64_t)stp) {
-            Ctr4 r = draw(P.seed, id, (uint64_t)stp, TAG_TF, 0);
+            const uint64_t r = draw_tf(P.seed, id, (uint64_t)stp);
             Real tf;
-            if (sizeof(Real) == 8) tf = (Real)(-(tau_c * log_d(u01_d(r.v[0]))));
-            else tf = (Real)(-((float)tau_c * log_f(u01_f(r.v[0]))));
+            if (sizeof(Real) == 8) tf = (Real)(-(tau_c * log_d(u01_d(r))));
+            else tf = (Real)(-((float)tau_c * log_f(u01_f(r))));
             if (tf < dtR) { st |= ST_COLL; t_end = tf; }
         }
         TrackOut o = track<Real>(g, pl, P, pt, t_end, (uint64_t)stp);
@@ -1532,6 +1542,13 @@ void orc_math_logf(const float* x, float* y, int64_t n) {
 
 void orc_math_sincos2pi_f(const float* x, float* s, float* c, int64_t n) {
     for (int64_t k = 0; k < n; ++k) sincos2pi_f(x[k], &s[k], &c[k]);
+}
+
+void orc_philox32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    Ctr4x32 c;
+    for (int k = 0; k < 4; ++k) c.v[k] = ctr[k];
+    Ctr4x32 r = philox4x32_10(c, key[0], key[1]);
+    for (int k = 0; k < 4; ++k) out[k] = r.v[k];
 }
 
 void orc_philox(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {

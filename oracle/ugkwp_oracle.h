@@ -49,6 +49,7 @@ void orc_math_logf(const float* x, float* y, int64_t n);
 /* sin(2 pi x), cos(2 pi x) in binary32 (the particle arithmetic of the mixed mode) */
 void orc_math_sincos2pi_f(const float* x, float* s, float* c, int64_t n);
 void orc_philox(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+void orc_philox32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* q1..q5, then the two free-transport coefficients of the collisional wave:
  * a4 = q4 - dt e^{-dt/tau}, a5 = q5 + dt^2/2 e^{-dt/tau}. */
 void orc_qcoef(double dt, double tau, double q[7]);

@@ -13,7 +13,7 @@
 //   d_sincos2pi sin/cos of 2 pi u by exact quarter-turn reduction and the
 //               Taylor series of sin and cos on [-pi/4, pi/4]; f_sincos2pi the
 //               same in binary32 (sin to th^11/11!, cos to th^12/12!).
-//   philox      Philox4x64-10 of Salmon et al. (SC'11).
+//   philox      Philox4x64-10 and (philox32_2) Philox4x32-10 of Salmon et al. (SC'11).
 #pragma once
 #include <cstdint>
 
@@ -208,6 +208,22 @@ __device__ __forceinline__ U4 philox(unsigned long long c0, unsigned long long c
         k1 += 0xBB67AE8584CAA73BULL;
     }
     return U4{c0, c1, c2, c3};
+}
+
+// Philox4x32-10 (same paper, 32x32->64 multiplies); returns output words 0
+// and 1 as one 64-bit value (word 0 high).
+__device__ __forceinline__ unsigned long long philox32_2(unsigned c0, unsigned c1, unsigned c2, unsigned c3,
+                                                         unsigned k0, unsigned k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const unsigned n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return ((unsigned long long)c0 << 32) | c1;
 }
 
 __device__ __forceinline__ double u01d(unsigned long long r) { return ((double)(r >> 11) + 0.5) * 0x1p-53; }

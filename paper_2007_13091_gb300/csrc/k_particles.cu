@@ -384,8 +384,11 @@ __global__ void __launch_bounds__(256, UGKWP_TRACK_MIN_BLOCKS) k_track(DevMesh m
             Real t_end = dtR;
             bool coll = false;
             if ((long long)(id >> 40) != step) {
-                const dm::U4 r = dm::philox(id, (unsigned long long)step, TAG_TF, 0ULL, p.seed, 0ULL);
-                const Real tf = Trk<Real>::tf(Trk<Real>::tau(s, c0), r.a);
+                // Philox4x32-10, counter (id low, id high, step, TAG_TF), key (seed low, seed high)
+                const unsigned long long r = dm::philox32_2((unsigned)id, (unsigned)(id >> 32), (unsigned)step,
+                                                            (unsigned)TAG_TF, (unsigned)p.seed,
+                                                            (unsigned)(p.seed >> 32));
+                const Real tf = Trk<Real>::tf(Trk<Real>::tau(s, c0), r);
                 if (tf < dtR) { coll = true; t_end = tf; }
             }
             // ---- face-by-face walk along x0 + u (t - t0)
