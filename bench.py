@@ -34,14 +34,14 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-moves/s & cell-steps/s on 1 GB300: mixed vs FP64 at fixed error"
 UNIT = "particle-moves/s"
 # minimum bytes the tracking kernel moves (MIXED / FP64): read the particle
-# record (x, u, m, cell, id) and write back position and cell
-TRACK_BYTES_PER_MOVE = {"mixed": 44 + 16, "fp64": 68 + 28}
+# record (x, u, m, cell, id) and write it (compacted) for the next step
+TRACK_BYTES_PER_MOVE = {"mixed": 44 + 44, "fp64": 68 + 68}
 # per cell and step: tracking record (planes + neighbours) and tau
 TRACK_BYTES_PER_CELL = {"mixed": 80 + 8, "fp64": 144 + 8}
 # DRAM bytes (read + write) of one k_track launch on this workload, from the ncu
 # capture summarised in profiles/k_track_k_face_flux_cavity24_mixed.md; set to
 # None whenever the kernel changes until it is captured again
-TRACK_DRAM_BYTES = {"mixed": 959102208 + 352500480, "fp64": None}
+TRACK_DRAM_BYTES = {"mixed": 962823424 + 978838528, "fp64": None}
 # Binary64 flops per interior face of k_face_flux_o2 (the second-order wave flux):
 # ncu's executed dadd + dmul + 2 dfma per launch divided by the interior faces, on
 # this workload (profiles/); None until captured for the current kernel.
@@ -415,10 +415,10 @@ def main():
     cfg = workload(args.precision)
     nc = len(cfg["mesh"]["tets"])
     sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=stream)
-    # grid sizes from the library's autotuner (its trial steps are part of the
-    # spin-up to the settled particle population)
-    launch_cfg = ugkwp.ugkwp_autotune(sim.handle, 2)
-    sim.step(max(0, SPIN_UP - sim.step(0, stats=True)["step"]))
+    # spin-up to the settled particle population, then the library's autotuner
+    # picks the grid sizes on that state (its trial steps are untimed)
+    sim.step(SPIN_UP)
+    launch_cfg = ugkwp.ugkwp_autotune(sim.handle, 4)
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
@@ -437,7 +437,7 @@ def main():
     kmoves = kms.pop("_moves") / args.steps
     alg = TRACK_BYTES_PER_MOVE[args.precision] * kmoves + TRACK_BYTES_PER_CELL[args.precision] * nc
     achieved = alg / (track_ms * 1e-3) / 1e9
-    roof_track = {"kernel": "k_track (a6-a9: t_f draw, tet walk, fixed-point flux, removal)", "bound": "hbm",
+    roof_track = {"kernel": "k_track (a6-a9, a11: t_f draw, tet walk, fixed-point flux, removal, compaction)", "bound": "hbm",
                   "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                   "peak_kind": f"{peak_kind} HBM copy", "traffic": TRACK_DRAM_BYTES[args.precision],
                   "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
@@ -492,8 +492,8 @@ def main():
     if not args.no_extras and rank == 0:
         c64 = workload("fp64")
         s64 = ugkwp.Simulation(c64["mesh"], c64["W0"], c64["params"], device=device, stream=stream)
-        cfg64 = ugkwp.ugkwp_autotune(s64.handle, 2)
-        s64.step(max(0, SPIN_UP - s64.step(0, stats=True)["step"]))
+        s64.step(SPIN_UP)
+        cfg64 = ugkwp.ugkwp_autotune(s64.handle, 4)
         ms64, mv64, _, k64, _ = time_steps(s64, args.steps, args.warmup, 1)
         s64.close()
         k64.pop("_moves", None)

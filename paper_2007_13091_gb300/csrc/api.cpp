@@ -30,7 +30,8 @@ struct ugkwp_sim {
     DevParams P;
     DevMesh M;
     DevState S;
-    PartBufRaw A, B;
+    PartBufRaw A, B;   // A: the current particles (between steps: the survivors); B: the next survivors
+    PartBufRaw Mv;     // the step's movers (particles whose counting flux is non-zero)
     cudaStream_t stream = nullptr;
     int64_t step = 0;
     int32_t n_bc = 0;
@@ -109,7 +110,7 @@ struct Carver {
 };
 
 void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, DevState& S, PartBufRaw& A,
-            PartBufRaw& B) {
+            PartBufRaw& B, PartBufRaw& Mv) {
     const size_t nc = mh.nc, nf = mh.nf, nbf = mh.nbf;
     M.nc = mh.nc; M.nf = mh.nf; M.nbf = mh.nbf; M.nif = mh.nf - mh.nbf;
     M.vol = c.take<double>(nc);
@@ -151,9 +152,7 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, D
     S.smass = c.take<int64_t>(nc);
     S.smass_next = c.take<int64_t>(nc);
     S.cnt = c.take<int32_t>(nc);
-    S.off = c.take<int32_t>(nc);
     S.soff = c.take<int32_t>(nc);
-    S.cursor = c.take<int32_t>(nc);
     S.pflux = c.take<int64_t>(5 * nc);
     S.wacc = c.take<int64_t>(5 * nc);
     S.mom = c.take<double>(5 * nc);
@@ -164,7 +163,7 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, D
     S.t = c.take<double>(1);
     S.dt = c.take<double>(1);
     S.cnt64 = c.take<int64_t>(CNT_SLOTS);
-    for (PartBufRaw* pb : {&A, &B}) {
+    for (PartBufRaw* pb : {&A, &B, &Mv}) {
         for (int d = 0; d < 3; ++d) pb->x[d] = c.take<char>(rs * (size_t)cap);
         for (int d = 0; d < 3; ++d) pb->u[d] = c.take<char>(rs * (size_t)cap);
         pb->m = c.take<double>((size_t)cap);
@@ -317,7 +316,8 @@ int ugkwp_query_sizes(const ugkwp_mesh* m, const ugkwp_params* p, ugkwp_sizes* o
     DevState S{};
     PartBufRaw A{}, B{};
     Carver c(nullptr);
-    layout(m->h, p->particle_capacity, p->precision == UGKWP_MIXED ? 4 : 8, c, M, S, A, B);
+    PartBufRaw Mv{};
+    layout(m->h, p->particle_capacity, p->precision == UGKWP_MIXED ? 4 : 8, c, M, S, A, B, Mv);
     out->workspace_bytes = (c.off + 255) & ~(size_t)255;
     out->n_cells = m->h.nc;
     out->n_faces = m->h.nf;
@@ -354,7 +354,7 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     s->capacity = p->particle_capacity;
     s->n_bc = p->n_bc;
     Carver c(d_workspace);
-    layout(mh, p->particle_capacity, s->real_size, c, s->M, s->S, s->A, s->B);
+    layout(mh, p->particle_capacity, s->real_size, c, s->M, s->S, s->A, s->B, s->Mv);
     // parameters
     DevParams& P = s->P;
     std::memset(&P, 0, sizeof(P));
@@ -647,14 +647,14 @@ int enqueue_step(ugkwp_sim* s) {
             timed(s, UGKWP_K_FLUX, 1, s->wave, [&] { launch_face_flux(s->M, s->S, s->P, first, s->wave); });
         CU(cudaEventRecord(s->join, s->wave));
         timed(s, UGKWP_K_SCAN, 2, q, [&] { launch_scan(s->M, s->S, s->P, q); });
-        timed(s, UGKWP_K_SCATTER, 1, q, [&] { launch_scatter(s->M, s->S, s->P, s->A, s->B, s->lc.particle_blocks, q); });
         const bool matched = s->P.sampling == UGKWP_SAMPLE_ENERGY_MATCHED;
         timed(s, UGKWP_K_SAMPLE, matched ? 2 : 1, q, [&] {
             if (matched) launch_sample_scale(s->M, s->S, s->P, q);
-            launch_sample_write(s->M, s->S, s->P, s->B, s->lc.particle_blocks, q);
+            launch_sample_write(s->M, s->S, s->P, s->A, s->lc.particle_blocks, q);
         });
-        timed(s, UGKWP_K_TRACK, 1, q, [&] { launch_track(s->M, s->S, s->P, s->B, s->A, s->lc.particle_blocks, q); });
-        timed(s, UGKWP_K_MOVERS, 1, q, [&] { launch_movers(s->M, s->S, s->P, s->A, s->lc.particle_blocks, q); });
+        timed(s, UGKWP_K_TRACK, 1, q,
+              [&] { launch_track(s->M, s->S, s->P, s->A, s->B, s->Mv, s->lc.particle_blocks, q); });
+        timed(s, UGKWP_K_MOVERS, 1, q, [&] { launch_movers(s->M, s->S, s->P, s->Mv, s->lc.particle_blocks, q); });
         CU(cudaStreamWaitEvent(q, s->join, 0));  // join before the update reads F
         timed(s, UGKWP_K_UPDATE, 1, q, [&] { launch_cell_update(s->M, s->S, s->P, q); });
         std::swap(s->A, s->B);
@@ -783,15 +783,8 @@ int ugkwp_state_info(ugkwp_sim* s, ugkwp_state* st) {
     CU(cudaMemcpyAsync(h, s->S.cnt64, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
     CU(cudaMemcpyAsync(&t, s->S.t, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CU(cudaStreamSynchronize(s->stream));
-    // alive particles = non-negative cells among the N_A entries of the current buffer
-    std::vector<int32_t> cell((size_t)h[CNT_N_A]);
-    if (h[CNT_N_A] > 0) {
-        CU(cudaMemcpyAsync(cell.data(), s->A.cell, cell.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
-        CU(cudaStreamSynchronize(s->stream));
-    }
-    int64_t alive = 0;
-    for (int32_t c : cell) alive += c >= 0;
-    st->n_particles = alive;
+    // the current buffer holds exactly the N_A live particles
+    st->n_particles = h[CNT_N_A];
     st->step = s->step;
     st->t = t;
     for (int q = 0; q < 5; ++q) st->exps[q] = s->P.exps[q];

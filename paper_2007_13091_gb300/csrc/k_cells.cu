@@ -1,7 +1,7 @@
 // Per-cell kernels of the UGKWP step: primitives, relaxation time and the
 // time-step reduction (a1, a2), hydro-particle counts (a5), the exclusive scan
-// that lays out the next particle buffer (a11), and the conservative update
-// (a10).  Compiled with --fmad=false: tau, dt, N_sam and m_sam decide integer
+// that places each cell's samples after the survivors (a11), and the
+// conservative update (a10).  Compiled with --fmad=false: tau, dt, N_sam and m_sam decide integer
 // outcomes of the particle path and must be reproducible bit for bit.
 #include <cfloat>
 
@@ -50,7 +50,6 @@ __global__ void k_reset(DevMesh m, DevState s) {
         if (i < nc) {
             s.nleft_next[i] = 0;
             s.smass_next[i] = 0;
-            s.cursor[i] = 0;
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -120,7 +119,7 @@ __global__ void k_cell_prep(DevMesh m, DevState s, DevParams p) {
 // a5 counts: rho^hp = e^{-dt/tau} rho^h, m_ref = (rho^p + rho^hp)|Omega|/N_ref,
 // N_sam = 2 ceil(rho^hp |Omega| / (2 m_ref)), N_sam >= N_min - N_left,
 // m_sam = rho^hp |Omega| / N_sam (Sec. 2.4 (b)).  Also the per-block sums of
-// the next buffer's per-cell counts.
+// the per-cell particle counts (survivors + samples) and of N_sam.
 __global__ void k_sample_count(DevMesh m, DevState s, DevParams p) {
     __shared__ int2 shw[32];
     const int nc = m.nc;
@@ -193,11 +192,7 @@ __global__ void k_scan_apply(DevMesh m, DevState s) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int2 v = i < m.nc ? make_int2(s.cnt[i], s.nsam[i]) : make_int2(0, 0);
     const int2 incl = block_scan_incl2(v, shw);
-    if (i < m.nc) {
-        const int2 b = s.bsum[blockIdx.x];
-        s.off[i] = b.x + incl.x - v.x;
-        s.soff[i] = b.y + incl.y - v.y;
-    }
+    if (i < m.nc) s.soff[i] = s.bsum[blockIdx.x].y + incl.y - v.y;
 }
 
 // a10: W^{n+1} = W^n - 1/|Omega| sum_k (+-F_k |S_k|) + F^{fr,p}/|Omega|, faces
@@ -208,7 +203,7 @@ __global__ void k_cell_update(DevMesh m, DevState s, DevParams p) {
     if (i == 0) {
         s.t[0] = s.t[0] + s.dt[0];
         s.cnt64[CNT_STEP] += 1;
-        s.cnt64[CNT_N_A] = s.cnt64[CNT_N_B];  // the tracked buffer becomes the current one
+        s.cnt64[CNT_N_A] = s.cnt64[CNT_ALIVE];  // the compacted survivors become the current particles
     }
     if (i >= nc) return;
     int f[4];

@@ -2,12 +2,13 @@
 // (double: FP64 mode; float: MIXED mode).  Compiled with --fmad=false so that
 // every particle trajectory and fixed-point flux is reproducible bit for bit.
 //
-//   k_scatter       a11: survivors of the last step -> cell-sorted slots of the
-//                   next buffer (warp-aggregated slot reservation per cell).
 //   k_sample_write  a5: N_sam hydro particles per cell, in pairs U +/- sqrt(RT) X
 //                   with X ~ N(0, I) (Box-Muller), uniform in the tet.
-//   k_track         a6-a9: t_f = min(-tau ln eta, dt), face-by-face streaming,
-//                   boundary interaction, fixed-point particle flux, removal.
+//   k_track         a6-a9, a11: t_f = min(-tau ln eta, dt), face-by-face
+//                   streaming, boundary interaction, particle flux (movers
+//                   listed for k_movers), removal; the survivors are written
+//                   compacted into the other buffer (block-level slot
+//                   reservation), where the next step's samples follow them.
 #include "dmath.cuh"
 #include "ugkwp_internal.hpp"
 
@@ -41,37 +42,6 @@ template <class Real> __device__ __forceinline__ PartView<Real> view(const PartB
     v.cell = r.cell;
     v.id = r.id;
     return v;
-}
-
-// ------------------------------------------------------------------ scatter
-template <class Real>
-__global__ void __launch_bounds__(256) k_scatter(DevState s, PartBufRaw ar, PartBufRaw br) {
-    if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
-    const PartView<Real> a = view<Real>(ar), b = view<Real>(br);
-    const long long n = s.cnt64[CNT_N_A];
-    const int lane = threadIdx.x & 31;
-    const long long wstride = (long long)gridDim.x * blockDim.x;
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += wstride) {
-        const long long i = base + lane;
-        const int c = i < n ? a.cell[i] : -1;
-        const unsigned grp = __match_any_sync(FULL, c);
-        if (c >= 0) {
-            const int leader = __ffs(grp) - 1;
-            const int rank = __popc(grp & ((1u << lane) - 1u));
-            int slot0 = 0;
-            if (lane == leader) slot0 = atomicAdd(&s.cursor[c], __popc(grp));
-            slot0 = __shfl_sync(grp, slot0, leader);
-            const long long j = (long long)s.off[c] + slot0 + rank;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                b.x[d][j] = a.x[d][i];
-                b.u[d][j] = a.u[d][i];
-            }
-            b.m[j] = a.m[i];
-            b.cell[j] = c;
-            b.id[j] = a.id[i];
-        }
-    }
 }
 
 // ------------------------------------------------------------------ sampling
@@ -145,7 +115,8 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
         const int cell = lo;
         const int k = (int)(g - s.soff[cell]);
         const int side = k & 1;
-        const long long j = (long long)s.off[cell] + s.nleft[cell] + k;
+        // the samples follow the survivors of the last step in cell order
+        const long long j = s.cnt64[CNT_N_A] + g;
         if constexpr (sizeof(Real) == 4) {
             // mixed mode: binary32 arithmetic from U, sqrt(RT) and the tet's
             // vertex and edges rounded to binary32
@@ -347,20 +318,22 @@ __device__ __forceinline__ bool fixed_of_mass(double m, int e, long long& q) {
 }
 
 template <class Real>
-__global__ void __launch_bounds__(256, UGKWP_TRACK_MIN_BLOCKS) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br, PartBufRaw ar) {
+__global__ void __launch_bounds__(256, UGKWP_TRACK_MIN_BLOCKS) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br,
+                                                                     PartBufRaw nr, PartBufRaw ar) {
     if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
-    const PartView<Real> b = view<Real>(br);
+    const PartView<Real> b = view<Real>(br);   // this step's particles: survivors, then samples
+    const PartView<Real> nxt = view<Real>(nr);  // the next step's survivors, compacted
     const PartView<Real> mv = view<Real>(ar);  // mover list: x = u at start, u = u at end
     const long long n = s.cnt64[CNT_N_B];
     const long long step = s.cnt64[CNT_STEP];
     const double dt = s.dt[0];
     const Real dtR = (Real)dt;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ int sh_cnt[8];
-    __shared__ long long sh_base;
+    __shared__ int sh_cnt[8], sh_scnt[8];
+    __shared__ long long sh_base, sh_sbase;
     __shared__ unsigned long long sh_red[8][8];
     // per-thread counters, reduced once per block at the end
-    unsigned c_surv = 0, c_valid = 0, c_coll = 0, c_exit = 0, c_lost = 0, c_cross = 0, c_wall = 0;
+    unsigned c_valid = 0, c_coll = 0, c_exit = 0, c_lost = 0, c_cross = 0, c_wall = 0;
     const long long bstride = (long long)gridDim.x * blockDim.x;
     // block-uniform loop: every warp of the block runs the same iterations
     for (long long bb = (long long)blockIdx.x * blockDim.x; bb < n; bb += bstride) {
@@ -371,9 +344,11 @@ __global__ void __launch_bounds__(256, UGKWP_TRACK_MIN_BLOCKS) k_track(DevMesh m
         long long qmass = 0;
         bool survivor = false, mover = false, exited = false;
         Real us[3] = {(Real)0, (Real)0, (Real)0}, ue[3] = {(Real)0, (Real)0, (Real)0};
+        Real xe[3] = {(Real)0, (Real)0, (Real)0};
         double mm = 0.0;
+        unsigned long long id = 0;
         if (valid) {
-            const unsigned long long id = b.id[i];
+            id = b.id[i];
             c0 = b.cell[i];
             Real x0[3], u[3];
 #pragma unroll
@@ -395,7 +370,6 @@ __global__ void __launch_bounds__(256, UGKWP_TRACK_MIN_BLOCKS) k_track(DevMesh m
             tet = c0;
             int last = -1;
             Real t0 = (Real)0;
-            Real xe[3];
             for (;;) {
                 // smallest crossing time (d - n.x0)/(u.n) over u.n > 0, compared
                 // by cross products (positive denominators), one division
@@ -501,20 +475,7 @@ __global__ void __launch_bounds__(256, UGKWP_TRACK_MIN_BLOCKS) k_track(DevMesh m
 #pragma unroll
             for (int c = 0; c < 3; ++c) ue[c] = u[c];
             if (survivor && !fixed_of_mass(mm, p.exps[0], qmass)) set_err(s, ERRB_FIXED_OVERFLOW);
-            // ---- write back
-            if (survivor) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) b.x[c][i] = xe[c];
-                if (nrefl > 0) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) b.u[c][i] = u[c];
-                }
-                if (tet != c0) b.cell[i] = tet;
-            } else {
-                b.cell[i] = -1;
-            }
             c_valid += 1;
-            c_surv += survivor;
             c_coll += status & 1;
             c_exit += (status >> 1) & 1;
             c_lost += (status >> 2) & 1;
@@ -539,18 +500,43 @@ __global__ void __launch_bounds__(256, UGKWP_TRACK_MIN_BLOCKS) k_track(DevMesh m
             atomicAdd(&s.nleft_next[key], lane - start + 1);
             atomicAdd(reinterpret_cast<unsigned long long*>(&s.smass_next[key]), (unsigned long long)v);
         }
-        // ---- movers: one slot reservation per block and iteration
+        // ---- survivors (compacted into the next buffer) and movers: one slot
+        // reservation of each per block and iteration
         const unsigned mmask = __ballot_sync(FULL, mover);
-        if (lane == 0) sh_cnt[warp] = __popc(mmask);
+        const unsigned smask = __ballot_sync(FULL, survivor);
+        if (lane == 0) {
+            sh_cnt[warp] = __popc(mmask);
+            sh_scnt[warp] = __popc(smask);
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            int tot = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { const int c = sh_cnt[w]; sh_cnt[w] = tot; tot += c; }
+            int tot = 0, stot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                const int c = sh_cnt[w], sc = sh_scnt[w];
+                sh_cnt[w] = tot;
+                sh_scnt[w] = stot;
+                tot += c;
+                stot += sc;
+            }
             sh_base = tot ? (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_MOVERS]),
                                                  (unsigned long long)tot)
                           : 0LL;
+            sh_sbase = stot ? (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_ALIVE]),
+                                                   (unsigned long long)stot)
+                            : 0LL;
         }
         __syncthreads();
+        if (survivor) {
+            const long long j = sh_sbase + sh_scnt[warp] + __popc(smask & ((1u << lane) - 1u));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                nxt.x[c][j] = xe[c];
+                nxt.u[c][j] = ue[c];
+            }
+            nxt.m[j] = mm;
+            nxt.cell[j] = tet;
+            nxt.id[j] = id;
+        }
         if (mover) {
             const long long j = sh_base + sh_cnt[warp] + __popc(mmask & ((1u << lane) - 1u));
 #pragma unroll
@@ -564,22 +550,23 @@ __global__ void __launch_bounds__(256, UGKWP_TRACK_MIN_BLOCKS) k_track(DevMesh m
         }
         __syncthreads();  // sh_cnt / sh_base are reused next iteration
     }
-    // ---- counters: one atomic per block and counter
-    unsigned vals[7] = {c_surv, c_valid, c_coll, c_exit, c_lost, c_cross, c_wall};
+    // ---- counters: one atomic per block and counter (survivors were counted
+    // by their slot reservations)
+    unsigned vals[6] = {c_valid, c_coll, c_exit, c_lost, c_cross, c_wall};
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
+    for (int k = 0; k < 6; ++k) {
         const unsigned w = __reduce_add_sync(FULL, vals[k]);
         if (lane == 0) sh_red[warp][k] = w;
     }
     __syncthreads();
-    if (threadIdx.x < 7) {
+    if (threadIdx.x < 6) {
         unsigned long long t = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh_red[w][threadIdx.x];
-        const int slot[7] = {CNT_ALIVE, CNT_TRACKED, CNT_COLLIDED, CNT_EXITED, CNT_LOST, CNT_CROSSINGS, CNT_WALL};
+        const int slot[6] = {CNT_TRACKED, CNT_COLLIDED, CNT_EXITED, CNT_LOST, CNT_CROSSINGS, CNT_WALL};
         if (t) {
             atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[slot[threadIdx.x]]), t);
-            if (threadIdx.x == 1) atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_MOVES]), t);
-            if (threadIdx.x == 4) set_err(s, ERRB_TRACK_LIMIT);
+            if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_MOVES]), t);
+            if (threadIdx.x == 3) set_err(s, ERRB_TRACK_LIMIT);
         }
     }
 }
@@ -619,13 +606,6 @@ __global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams
 
 }  // namespace
 
-void launch_scatter(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
-                    const PartBufRaw& b, int blocks, cudaStream_t st) {
-    (void)m;
-    if (p.precision == UGKWP_MIXED) k_scatter<float><<<blocks, 256, 0, st>>>(s, a, b);
-    else k_scatter<double><<<blocks, 256, 0, st>>>(s, a, b);
-}
-
 void launch_sample_write(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b,
                          int blocks, cudaStream_t st) {
     (void)m;
@@ -638,10 +618,10 @@ void launch_sample_scale(const DevMesh& m, const DevState& s, const DevParams& p
     else k_sample_scale<double><<<(m.nc + 255) / 256, 256, 0, st>>>(m, s, p);
 }
 
-void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b, const PartBufRaw& a,
-                  int blocks, cudaStream_t st) {
-    if (p.precision == UGKWP_MIXED) k_track<float><<<blocks, 256, 0, st>>>(m, s, p, b, a);
-    else k_track<double><<<blocks, 256, 0, st>>>(m, s, p, b, a);
+void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b, const PartBufRaw& nxt,
+                  const PartBufRaw& movers, int blocks, cudaStream_t st) {
+    if (p.precision == UGKWP_MIXED) k_track<float><<<blocks, 256, 0, st>>>(m, s, p, b, nxt, movers);
+    else k_track<double><<<blocks, 256, 0, st>>>(m, s, p, b, nxt, movers);
 }
 
 void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a, int blocks, cudaStream_t st) {

@@ -22,9 +22,9 @@ enum : int32_t {
 
 // Device counters (int64 slots).
 enum : int {
-    CNT_N_A = 0,        // particles in the current buffer (dead ones included)
-    CNT_N_B = 1,        // particles in the next buffer after the scan
-    CNT_ALIVE = 2,      // survivors of the last step
+    CNT_N_A = 0,        // particles in the current buffer: the survivors of the last step
+    CNT_N_B = 1,        // particles tracked this step (survivors + samples), from the scan
+    CNT_ALIVE = 2,      // survivors of this step (the slot counter of the compacted next buffer)
     CNT_SAMPLED = 3,
     CNT_COLLIDED = 4,
     CNT_EXITED = 5,
@@ -139,9 +139,7 @@ struct DevState {
     int64_t* smass;       // [nc] survivors' fixed-point mass
     int64_t* smass_next;  // [nc]
     int32_t* cnt;         // [nc] particles per cell after sampling
-    int32_t* off;         // [nc] first slot of the cell in the next buffer
     int32_t* soff;        // [nc] exclusive scan of N_sam (sampled-particle index)
-    int32_t* cursor;      // [nc]
     int64_t* pflux;       // [5][nc] fixed-point particle flux
     int64_t* wacc;        // [5][nc] fixed-point scratch for W^p
     double* mom;          // [5][nc] staging of moments copied to the host
@@ -178,20 +176,19 @@ void launch_scan(const DevMesh& m, const DevState& s, const DevParams& p, cudaSt
 // Grid sizes of the step kernels that loop over their work (any positive
 // value gives the same results; chosen for speed, e.g. by the autotuner).
 struct LaunchCfg {
-    int particle_blocks;  // blocks of 256 threads for scatter, sampling, tracking, movers
+    int particle_blocks;  // blocks of 256 threads for sampling, tracking, movers
     int wave_blocks;      // blocks of the persistent second-order wave kernels
 };
 
-void launch_scatter(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
-                    const PartBufRaw& b, int blocks, cudaStream_t st);
 void launch_sample_write(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b,
                          int blocks, cudaStream_t st);
 // Energy-matched sampling: the per-cell spread s sqrt(RT) (sig, usig.w).
 void launch_sample_scale(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
-// Tracking of buffer b; particles whose counting flux is non-zero are listed
-// in buffer a (free after the scatter) and their flux added by launch_movers.
+// Tracking of buffer b (survivors, then this step's samples); the survivors go
+// compacted to nxt, the particles whose counting flux is non-zero are listed in
+// movers and their flux added by launch_movers.
 void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b,
-                  const PartBufRaw& a, int blocks, cudaStream_t st);
+                  const PartBufRaw& nxt, const PartBufRaw& movers, int blocks, cudaStream_t st);
 void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
                    int blocks, cudaStream_t st);
 // First-order flux of face_order[first..nf); second-order flux of the nif interior faces.

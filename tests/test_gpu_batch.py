@@ -106,6 +106,8 @@ def test_autotuner_picks_a_candidate_and_keeps_results():
 def test_batch_autotune_and_member_errors():
     import torch
     cfgs = _members()[:2]
+    for c in cfgs:  # 42 steps: keep the low-N_ref tube physical (energy-matched sampling)
+        c["params"]["sampling"] = "energy_matched"
     sims = [_sim(c, torch.cuda.Stream()) for c in cfgs]
     b = ugkwp.Batch(sims)
     best = b.autotune(2)
