@@ -61,11 +61,6 @@ def guarded(fn):
         return {"error": f"{type(e).__name__}: {e}"[:300]}
 
 
-def flux_ms_dominant(kms):
-    """The O2 wave flux is the dominant kernel when its device time exceeds k_track's."""
-    return kms.get("flux_o2", 0.0) > kms.get("track", 0.0)
-
-
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -482,7 +477,7 @@ def main():
                       "l2": "inputs larger than L2 (particle SoA %.2f GB per buffer)" % (moves_per_step * 44 / 1e9),
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "cell_steps_per_s": cell_steps,
-           "roofline": roof_flux if roof_flux and roof_flux["achieved"] and flux_ms_dominant(kms) else roof_track,
+           "roofline": roof_track,
            "roofline_track": roof_track, "roofline_flux_o2": roof_flux,
            "kernels_ms_per_step": {k: v / args.steps for k, v in kms.items()},
            "step_launch": "two-step CUDA graphs replayed on the caller's stream",

@@ -18,9 +18,13 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-// Resident blocks of k_track per SM that its register budget is sized for.
+// Threads per block of k_track and the resident blocks per SM its register
+// budget is sized for.
+#ifndef UGKWP_TRACK_THREADS
+#define UGKWP_TRACK_THREADS 128
+#endif
 #ifndef UGKWP_TRACK_MIN_BLOCKS
-#define UGKWP_TRACK_MIN_BLOCKS 4
+#define UGKWP_TRACK_MIN_BLOCKS (1024 / UGKWP_TRACK_THREADS)
 #endif
 enum : unsigned long long { TAG_TF = 1, TAG_SVEL = 2, TAG_SPOS = 3, TAG_WALL = 4 };
 
@@ -318,7 +322,7 @@ __device__ __forceinline__ bool fixed_of_mass(double m, int e, long long& q) {
 }
 
 template <class Real>
-__global__ void __launch_bounds__(256, UGKWP_TRACK_MIN_BLOCKS) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br,
+__global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br,
                                                                      PartBufRaw nr, PartBufRaw ar) {
     if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
     const PartView<Real> b = view<Real>(br);   // this step's particles: survivors, then samples
@@ -620,8 +624,8 @@ void launch_sample_scale(const DevMesh& m, const DevState& s, const DevParams& p
 
 void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b, const PartBufRaw& nxt,
                   const PartBufRaw& movers, int blocks, cudaStream_t st) {
-    if (p.precision == UGKWP_MIXED) k_track<float><<<blocks, 256, 0, st>>>(m, s, p, b, nxt, movers);
-    else k_track<double><<<blocks, 256, 0, st>>>(m, s, p, b, nxt, movers);
+    if (p.precision == UGKWP_MIXED) k_track<float><<<blocks, UGKWP_TRACK_THREADS, 0, st>>>(m, s, p, b, nxt, movers);
+    else k_track<double><<<blocks, UGKWP_TRACK_THREADS, 0, st>>>(m, s, p, b, nxt, movers);
 }
 
 void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a, int blocks, cudaStream_t st) {
