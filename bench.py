@@ -41,12 +41,12 @@ TRACK_BYTES_PER_CELL = {"mixed": 80 + 8, "fp64": 144 + 8}
 # DRAM bytes (read + write) of one k_track launch on this workload, from the ncu
 # capture summarised in profiles/k_track_k_face_flux_cavity24_mixed.md; set to
 # None whenever the kernel changes until it is captured again
-TRACK_DRAM_BYTES = {"mixed": 962823424 + 978838528, "fp64": None}
+TRACK_DRAM_BYTES = {"mixed": 962181632 + 979341824, "fp64": None}
 # Binary64 flops per interior face of k_face_flux_o2 (the second-order wave flux):
 # ncu's executed dadd + dmul + 2 dfma per launch divided by the interior faces, on
 # this workload (profiles/); None until captured for the current kernel.
-FLUX_O2_FLOPS_PER_FACE = (27613440 + 75894656 + 2 * 144012032) / 162432
-FLUX_O2_DRAM_BYTES = 30774016 + 768
+FLUX_O2_FLOPS_PER_FACE = (27613440 + 75933568 + 2 * 144109312) / 162432
+FLUX_O2_DRAM_BYTES = 30773760 + 1792
 # FP64 peak: 2 FP64 FMA lanes per clock per SM (the nominal 1.25 TFLOP/s of this
 # part at 152 SMs and 2.07 GHz), 2 flops per FMA
 FP64_FMA_LANES_PER_SM = 2
