@@ -235,7 +235,8 @@ int ugkwp_last(ugkwp_sim* s, int32_t which, void* host_out);
 
 /* Kernel classes of one step, in launch order (for ugkwp_timing_read). */
 enum {
-    UGKWP_K_RESET = 0, UGKWP_K_CELL_PREP, UGKWP_K_SAMPLE_COUNT, UGKWP_K_SCAN, UGKWP_K_SCATTER,
+    UGKWP_K_RESET = 0, UGKWP_K_CELL_PREP, UGKWP_K_SAMPLE_COUNT, UGKWP_K_SCAN,
+    UGKWP_K_SCATTER, /* no kernel launches in this class: the tracking kernel compacts the survivors */
     UGKWP_K_SAMPLE, UGKWP_K_TRACK, UGKWP_K_FLUX, UGKWP_K_UPDATE, UGKWP_K_MOVERS, UGKWP_K_GRADIENTS,
     UGKWP_K_FLUX_O2, UGKWP_N_KERNELS
 };
@@ -245,7 +246,7 @@ enum {
  * depend on them (every particle draws from its own counter-based stream and
  * every sum over particles is fixed point), only the speed does. */
 typedef struct {
-    int32_t particle_blocks;     /* blocks of 256 threads for scatter, sampling, tracking, movers (> 0) */
+    int32_t particle_blocks;     /* blocks of the sampling, tracking and movers kernels (> 0) */
     int32_t wave_blocks;         /* blocks of the persistent second-order wave kernels (> 0) */
 } ugkwp_launch_cfg;
 
