@@ -151,24 +151,34 @@ def dist_setup():
     return ws, rank, local
 
 
-def reduce_max(x, ws):
+def _reduce(x, ws, op):
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def reduce_max(x, ws):
+    """Maximum over the ranks (the slowest replica sets the job's time)."""
+    import torch.distributed as dist
+    return _reduce(x, ws, dist.ReduceOp.MAX) if ws > 1 else x
 
 
 def reduce_sum(x, ws):
-    if ws == 1:
-        return x
-    import torch
+    """Sum over the ranks (work of all replicas)."""
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, ws, dist.ReduceOp.SUM) if ws > 1 else x
+
+
+def job_rates(ms, moves, cells, steps, ws):
+    """Whole-job rates of independent replicas: every rank's moves and
+    cell-steps over the slowest rank's time."""
+    ms_max = reduce_max(ms, ws)
+    return ms_max, reduce_sum(moves, ws) / (ms_max * 1e-3), reduce_sum(cells * steps, ws) / (ms_max * 1e-3)
 
 
 def barrier(ws):
@@ -422,10 +432,7 @@ def main():
     with ClockSampler(uuid) as clk:
         ms, moves, launches, kms, st = time_steps(sim, args.steps, args.warmup, ws)
     clocks = clk.summary()
-    ms_max = reduce_max(ms, ws)
-    moves_all = reduce_sum(moves, ws)
-    value = moves_all / (ms_max * 1e-3)
-    cell_steps = reduce_sum(nc * args.steps, ws) / (ms_max * 1e-3)
+    ms_max, value, cell_steps = job_rates(ms, moves, nc, args.steps, ws)
     peak, peak_kind = peaks()
     track_ms = kms["track"] / args.steps
     moves_per_step = moves / args.steps
