@@ -79,7 +79,8 @@ enum {
     UGKWP_W = 0,     /* conservative W = (rho, rho U, rho E) of the whole gas */
     UGKWP_WP = 1,    /* W^p: conservative variables carried by the particles (Eq. W^p) */
     UGKWP_WH = 2,    /* W^h = W - W^p, the hydrodynamic wave */
-    UGKWP_PRIM = 3   /* primitives (rho, U_x, U_y, U_z, T) of W */
+    UGKWP_PRIM = 3,  /* primitives (rho, U_x, U_y, U_z, T) of W */
+    UGKWP_WBAR = 4   /* time average W-bar = sum dt^n W^n / sum dt^n (Sec. 2.4 (c)), see ugkwp_average */
 };
 
 /* ------------------------------------------------------------------ types */
@@ -207,7 +208,23 @@ int ugkwp_step(ugkwp_sim* s, int32_t n_steps, ugkwp_stats* st);
 /* Wait for the stream and return (then clear) any device-side error. */
 int ugkwp_sync(ugkwp_sim* s);
 
-/* Copy a per-cell quantity (UGKWP_W, _WP, _WH, _PRIM) to out: a device
+/* Time averaging for steady states (Sec. 2.4 (c)).  start != 0 resets the
+ * sums and, from the next step on, adds dt^n W^n (the state after step n) to
+ * them; start == 0 stops adding (the sums stay readable).  UGKWP_WBAR then
+ * returns sum dt^n W^n / sum dt^n; *t_avg (may be NULL) receives sum dt^n.
+ * E_STATE for UGKWP_WBAR before any averaged step. */
+int ugkwp_average(ugkwp_sim* s, int32_t start);
+int ugkwp_average_time(ugkwp_sim* s, double* t_avg);
+
+/* Gradient-length local Knudsen number Kn_GLL = l |grad rho| / rho per cell
+ * (the diagnostic the paper plots), with the unlimited least-squares gradient
+ * of rho over the 4 face neighbours (boundary ghosts as in the reconstruction)
+ * and the VHS mean free path l = 2 (5 - 2 omega)(7 - 2 omega) / 15
+ * mu / (rho sqrt(2 pi R T)), mu = mu_ref (T / T_ref)^omega.  out: host
+ * [n_cells] (synchronising). */
+int ugkwp_kn_gll(ugkwp_sim* s, double* out);
+
+/* Copy a per-cell quantity (UGKWP_W, _WP, _WH, _PRIM, _WBAR) to out: a device
  * pointer (out_on_device = 1, enqueued on the stream) or host memory
  * (out_on_device = 0, synchronising).  [5][n_cells] doubles. */
 int ugkwp_moments(ugkwp_sim* s, int32_t which, double* out, int32_t out_on_device);

@@ -143,6 +143,8 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, D
     S.tauf = c.take<float>(nc);
     S.usig = c.take<float4>(nc);
     S.sig = c.take<double>(nc);
+    S.wsum = c.take<double>(5 * nc);
+    S.tsum = c.take<double>(1);
     S.rhoh = c.take<double>(nc);
     S.rhop = c.take<double>(nc);
     S.nsam = c.take<int32_t>(nc);
@@ -547,6 +549,7 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     if (ce == cudaSuccess) ce = cudaMemsetAsync(s->S.cnt64, 0, CNT_SLOTS * sizeof(int64_t), st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(s->S.t, 0, sizeof(double), st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(s->S.dt, 0, sizeof(double), st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(s->S.tsum, 0, sizeof(double), st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s->wave, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming);
@@ -750,6 +753,37 @@ int ugkwp_step(ugkwp_sim* s, int32_t n_steps, ugkwp_stats* st) {
     return UGKWP_OK;
 }
 
+int ugkwp_average(ugkwp_sim* s, int32_t start) {
+    if (!s) return fail(UGKWP_E_ARG, "NULL simulation");
+    if (start) {
+        CU(cudaMemsetAsync(s->S.wsum, 0, 5 * (size_t)s->M.nc * sizeof(double), s->stream));
+        CU(cudaMemsetAsync(s->S.tsum, 0, sizeof(double), s->stream));
+    }
+    const int32_t on = start ? 1 : 0;
+    if (s->P.averaging != on) {
+        s->P.averaging = on;
+        s->drop_graphs();  // the graphs carry the parameters by value
+    }
+    return UGKWP_OK;
+}
+
+int ugkwp_average_time(ugkwp_sim* s, double* t_avg) {
+    if (!s || !t_avg) return fail(UGKWP_E_ARG, "NULL argument");
+    CU(cudaMemcpyAsync(t_avg, s->S.tsum, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    return UGKWP_OK;
+}
+
+int ugkwp_kn_gll(ugkwp_sim* s, double* out) {
+    if (!s || !out) return fail(UGKWP_E_ARG, "NULL argument");
+    cudaStream_t q = s->stream;
+    launch_kn_gll(s->M, s->S, s->P, s->S.mom, q);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(out, s->S.mom, (size_t)s->M.nc * sizeof(double), cudaMemcpyDeviceToHost, q));
+    CU(cudaStreamSynchronize(q));
+    return read_error(s);
+}
+
 int ugkwp_sync(ugkwp_sim* s) {
     if (!s) return fail(UGKWP_E_ARG, "NULL simulation");
     return read_error(s);
@@ -757,9 +791,24 @@ int ugkwp_sync(ugkwp_sim* s) {
 
 int ugkwp_moments(ugkwp_sim* s, int32_t which, double* out, int32_t out_on_device) {
     if (!s || !out) return fail(UGKWP_E_ARG, "NULL argument");
-    if (which < UGKWP_W || which > UGKWP_PRIM) return fail(UGKWP_E_ARG, "unknown moment");
+    if (which < UGKWP_W || which > UGKWP_WBAR) return fail(UGKWP_E_ARG, "unknown moment");
     const size_t bytes = 5 * (size_t)s->M.nc * sizeof(double);
     cudaStream_t q = s->stream;
+    if (which == UGKWP_WBAR) {
+        double T = 0.0;
+        CU(cudaMemcpyAsync(&T, s->S.tsum, sizeof(double), cudaMemcpyDeviceToHost, q));
+        CU(cudaStreamSynchronize(q));
+        if (!(T > 0.0)) return fail(UGKWP_E_STATE, "no averaged step yet (ugkwp_average)");
+        double* dst = out_on_device ? out : s->S.mom;
+        launch_wbar(s->M, s->S, dst, q);
+        CU(cudaGetLastError());
+        if (!out_on_device) {
+            CU(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, q));
+            CU(cudaStreamSynchronize(q));
+            return read_error(s);
+        }
+        return UGKWP_OK;
+    }
     if (which == UGKWP_W) {
         CU(cudaMemcpyAsync(out, s->S.W, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, q));
     } else {

@@ -202,6 +202,7 @@ __global__ void k_cell_update(DevMesh m, DevState s, DevParams p) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         s.t[0] = s.t[0] + s.dt[0];
+        if (p.averaging) s.tsum[0] += s.dt[0];
         s.cnt64[CNT_STEP] += 1;
         s.cnt64[CNT_N_A] = s.cnt64[CNT_ALIVE];  // the compacted survivors become the current particles
     }
@@ -222,7 +223,42 @@ __global__ void k_cell_update(DevMesh m, DevState s, DevParams p) {
         const double fp = (double)s.pflux[(size_t)q * nc + i] * p.qscale[q];
         double& w = s.W[(size_t)q * nc + i];
         w = (w - acc / vol) + fp / vol;
+        if (p.averaging) s.wsum[(size_t)q * nc + i] += s.dt[0] * w;
     }
+}
+
+// Time average W-bar = sum dt^n W^n / sum dt^n (Sec. 2.4 (c)).
+__global__ void k_wbar(DevMesh m, DevState s, double* out) {
+    const long long n = 5LL * m.nc;
+    const double T = s.tsum[0];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = s.wsum[i] / T;
+}
+
+// Kn_GLL = l |grad rho| / rho with the unlimited least-squares gradient of rho
+// and the VHS mean free path l = 2(5-2w)(7-2w)/15 mu / (rho sqrt(2 pi R T)).
+__global__ void k_kn_gll(DevMesh m, DevState s, DevParams p, double* out) {
+    const int nc = m.nc;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const double rho = s.W[i];
+    const int own = m.cfs[i];
+    double g[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 4; ++k) {
+        const int f = m.cf[k * nc + i];
+        const int o = ((own >> k) & 1) ? m.f_nbr[f] : m.f_own[f];
+        double v = rho;
+        if (o >= 0) v = s.W[o];
+        else if (p.bc[m.bf_tag[-1 - o]].type == UGKWP_BC_FARFIELD) v = p.bc[m.bf_tag[-1 - o]].W_in[0];
+        for (int d = 0; d < 3; ++d) g[d] += m.lsq_c[(size_t)(3 * k + d) * nc + i] * (v - rho);
+    }
+    const double Ux = s.W[nc + i] / rho, Uy = s.W[2 * nc + i] / rho, Uz = s.W[3 * nc + i] / rho;
+    const double pr = (s.W[4 * nc + i] - 0.5 * (rho * ((Ux * Ux + Uy * Uy) + Uz * Uz))) / 1.5;
+    const double T = pr / (rho * p.R);
+    const double mu = p.mu_ref * dm::d_exp(p.omega * dm::d_log(T / p.T_ref));
+    const double w = p.omega;
+    const double l = (2.0 * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / 15.0) * mu / (rho * sqrt(2.0 * 3.141592653589793 * p.R * T));
+    out[i] = l * sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) / rho;
 }
 
 template <class Real>
@@ -335,6 +371,12 @@ void launch_wp_moments(const DevMesh& m, const DevState& s, const DevParams& p, 
     if (p.precision == UGKWP_MIXED) k_wp_acc<float><<<particle_grid(), 256, 0, st>>>(m, s, p, a);
     else k_wp_acc<double><<<particle_grid(), 256, 0, st>>>(m, s, p, a);
     (void)out;
+}
+void launch_wbar(const DevMesh& m, const DevState& s, double* out, cudaStream_t st) {
+    k_wbar<<<cdiv(5LL * m.nc, 256) < 4096 ? cdiv(5LL * m.nc, 256) : 4096, 256, 0, st>>>(m, s, out);
+}
+void launch_kn_gll(const DevMesh& m, const DevState& s, const DevParams& p, double* out, cudaStream_t st) {
+    k_kn_gll<<<cdiv(m.nc, 256), 256, 0, st>>>(m, s, p, out);
 }
 void launch_prim_moments(const DevMesh& m, const DevState& s, const DevParams& p, int which, double* out,
                          cudaStream_t st) {

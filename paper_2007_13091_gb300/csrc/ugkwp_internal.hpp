@@ -56,6 +56,8 @@ struct DevParams {
     int32_t N_ref, N_min, max_crossings, precision;
     int32_t order;
     int32_t sampling;      // UGKWP_SAMPLE_*
+    int32_t averaging;     // add dt W^{n+1} to the time-average sums
+    int32_t pad2_;
     uint64_t seed;
     int64_t capacity;
     int32_t exps[5];
@@ -130,6 +132,8 @@ struct DevState {
     float* tauf;          // [nc] binary32 rounding of tau (MIXED t_f draw)
     float4* usig;         // [nc] binary32 roundings of U and the sampling spread (MIXED sampling)
     double* sig;          // [nc] sampling spread s sqrt(RT) of energy-matched sampling
+    double* wsum;         // [5][nc] time-average sums of dt^n W^n
+    double* tsum;         // [1] sum of dt^n
     double* rhoh;         // [nc]
     double* rhop;         // [nc]
     int32_t* nsam;        // [nc]
@@ -202,6 +206,8 @@ void launch_wp_moments(const DevMesh& m, const DevState& s, const DevParams& p, 
                        double* out, cudaStream_t st);
 void launch_prim_moments(const DevMesh& m, const DevState& s, const DevParams& p, int which,
                          double* out, cudaStream_t st);
+void launch_wbar(const DevMesh& m, const DevState& s, double* out, cudaStream_t st);
+void launch_kn_gll(const DevMesh& m, const DevState& s, const DevParams& p, double* out, cudaStream_t st);
 
 // ---- adjoint of the frozen-particle wave map (first order)
 struct AdjBc {

@@ -22,7 +22,7 @@ BC_TYPES = {"wall": BC_DIFFUSE_WALL, "specular": BC_SPECULAR, "farfield": BC_FAR
             "outflow": BC_OUTFLOW}
 FP64, MIXED = 0, 1
 PRECISION = {"fp64": FP64, "mixed": MIXED}
-W, WP, WH, PRIM = 0, 1, 2, 3
+W, WP, WH, PRIM, WBAR = 0, 1, 2, 3, 4
 LAST = {"dt": 0, "tau": 1, "rho_h": 2, "n_sam": 3, "m_sam": 4, "flux": 5, "pflux": 6, "surv_mass": 7,
         "surv_count": 8, "grad_W": 9, "grad_rho_h": 10}
 
@@ -91,7 +91,7 @@ class AdjointReq(ctypes.Structure):
 
 KERNELS = ["reset", "cell_prep", "sample_count", "scan", "scatter", "sample", "track", "flux", "update", "movers", "gradients", "flux_o2"]
 
-EXPORTED = ["ugkwp_adjoint_query", "ugkwp_get_launch_cfg", "ugkwp_set_launch_cfg", "ugkwp_autotune", "ugkwp_batch_create",
+EXPORTED = ["ugkwp_average", "ugkwp_average_time", "ugkwp_kn_gll", "ugkwp_adjoint_query", "ugkwp_get_launch_cfg", "ugkwp_set_launch_cfg", "ugkwp_autotune", "ugkwp_batch_create",
             "ugkwp_batch_step", "ugkwp_batch_sync", "ugkwp_batch_autotune", "ugkwp_batch_free",
             "ugkwp_time_step_noalloc", "ugkwp_timing_enable", "ugkwp_timing_read", "ugkwp_mesh_load", "ugkwp_mesh_free", "ugkwp_query_sizes", "ugkwp_init", "ugkwp_free", "ugkwp_step",
             "ugkwp_sync", "ugkwp_moments", "ugkwp_state_info", "ugkwp_export_state", "ugkwp_import_state",
@@ -132,6 +132,9 @@ def lib():
             "ugkwp_timing_read": [vp, vp, vp],
             "ugkwp_time_step_noalloc": [vp, vp, vp, i32, ctypes.c_double, ctypes.c_double, vp, vp],
             "ugkwp_get_launch_cfg": [vp, P(LaunchCfg)],
+            "ugkwp_average": [vp, i32],
+            "ugkwp_average_time": [vp, P(ctypes.c_double)],
+            "ugkwp_kn_gll": [vp, vp],
             "ugkwp_set_launch_cfg": [vp, P(LaunchCfg)],
             "ugkwp_autotune": [vp, i32, P(LaunchCfg)],
             "ugkwp_batch_create": [vp, i32, vp, P(vp)],
@@ -334,6 +337,22 @@ def ugkwp_time_step_noalloc(d_W: int, d_vol: int, d_dS: int, n_cells: int, R: fl
     _check(lib().ugkwp_time_step_noalloc(ctypes.c_void_p(d_W), ctypes.c_void_p(d_vol), ctypes.c_void_p(d_dS),
                                          int(n_cells), float(R), float(CFL), ctypes.c_void_p(d_dt),
                                          ctypes.c_void_p(stream)))
+
+
+def ugkwp_average(sim, start: bool = True):
+    _check(lib().ugkwp_average(sim, 1 if start else 0))
+
+
+def ugkwp_average_time(sim) -> float:
+    t = ctypes.c_double()
+    _check(lib().ugkwp_average_time(sim, ctypes.byref(t)))
+    return t.value
+
+
+def ugkwp_kn_gll(sim, n_cells: int) -> np.ndarray:
+    out = np.empty(n_cells)
+    _check(lib().ugkwp_kn_gll(sim, out.ctypes.data))
+    return out
 
 
 def ugkwp_get_launch_cfg(sim) -> dict:
