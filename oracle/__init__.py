@@ -27,7 +27,7 @@ class OrcBc(ctypes.Structure):
 class OrcParams(ctypes.Structure):
     _fields_ = [("R", ctypes.c_double), ("mu_ref", ctypes.c_double), ("T_ref", ctypes.c_double),
                 ("omega", ctypes.c_double), ("CFL", ctypes.c_double), ("C2", ctypes.c_double),
-                ("venkat_K", ctypes.c_double), ("order", ctypes.c_int32), ("N_ref", ctypes.c_int32), ("N_min", ctypes.c_int32),
+                ("venkat_K", ctypes.c_double), ("Pr", ctypes.c_double), ("order", ctypes.c_int32), ("N_ref", ctypes.c_int32), ("N_min", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("max_crossings", ctypes.c_int32),
                 ("n_bc", ctypes.c_int32), ("sampling", ctypes.c_int32), ("pad2_", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("bc", OrcBc * 16)]
@@ -52,11 +52,12 @@ def lib():
         L.orc_philox.argtypes = [vp, vp, vp]
         L.orc_qcoef.argtypes = [d, d, vp]
         L.orc_maxwell_moments.argtypes = [vp, d, vp, ctypes.c_int, vp, vp]
-        L.orc_face_flux.argtypes = [P(OrcParams), ctypes.c_int, vp, d, vp, d, vp, d, d, P(OrcBc), vp]
+        L.orc_face_flux.argtypes = [P(OrcParams), ctypes.c_int, vp, d, vp, d, vp, d, d, P(OrcBc), i32, vp]
         L.orc_create.argtypes = [P(OrcParams), i32, vp, i32, vp, i32, vp, vp, vp, cp, i32]
         L.orc_create.restype = vp
         L.orc_free.argtypes = [vp]
         L.orc_step.argtypes = [vp, cp, i32]
+        L.orc_gks_step.argtypes = [vp, i32, cp, i32]
         L.orc_sizes.argtypes = [vp, vp]
         L.orc_geometry.argtypes = [vp, ctypes.c_int, vp]
         L.orc_get_state.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -67,7 +68,7 @@ def lib():
         L.orc_gradients.argtypes = [vp, ctypes.c_int, vp, vp]
         L.orc_slope_moment.argtypes = [vp, d, ctypes.c_int, vp, ctypes.c_int, vp]
         L.orc_micro_slope.argtypes = [vp, d, vp, vp]
-        L.orc_face_flux_o2.argtypes = [P(OrcParams), vp, d, vp, vp, vp, vp, d, vp, vp, vp, vp, d, vp]
+        L.orc_face_flux_o2.argtypes = [P(OrcParams), vp, d, vp, vp, vp, vp, d, vp, vp, vp, vp, d, i32, vp]
         L.orc_frozen_objective.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, vp, i32, vp]
         L.orc_frozen_value.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, vp, i32, vp]
         L.orc_sample_cell.argtypes = [vp, i32, i64, vp, vp, vp, vp]
@@ -99,6 +100,7 @@ def make_params(p: dict) -> OrcParams:
     for k in ("R", "mu_ref", "T_ref", "omega", "CFL", "C2"):
         setattr(o, k, float(p[k]))
     o.venkat_K = float(p.get("venkat_K", 5.0))
+    o.Pr = float(p.get("Pr", 0.0))
     o.order = int(p.get("order", 1))
     o.N_ref = int(p["N_ref"])
     o.N_min = int(p.get("N_min", 0))
@@ -169,8 +171,9 @@ def maxwell_moments(U, lam, n, half):
     return H, G
 
 
-def face_flux(params: dict, kind: str, WL, rhohL, WR, rhohR, n, dt, tau_wall=0.0, bc=None):
-    """kind: 'interior' or a boundary type name; WR is ignored for boundaries."""
+def face_flux(params: dict, kind: str, WL, rhohL, WR, rhohR, n, dt, tau_wall=0.0, bc=None, gks=False):
+    """kind: 'interior' or a boundary type name; WR is ignored for boundaries.
+    gks: the flux of a step without particles (whole free transport in the wave)."""
     P = make_params(params)
     WL = np.ascontiguousarray(WL, dtype=np.float64)
     WR = np.ascontiguousarray(WR if WR is not None else WL, dtype=np.float64)
@@ -182,7 +185,7 @@ def face_flux(params: dict, kind: str, WL, rhohL, WR, rhohR, n, dt, tau_wall=0.0
     bcs = make_bc(bc) if bc is not None else None
     rc = lib().orc_face_flux(ctypes.byref(P), kcode, _ptr(WL), float(rhohL), _ptr(WR), float(rhohR),
                              _ptr(n), float(dt), float(tau_wall),
-                             ctypes.byref(bcs) if bcs is not None else None, _ptr(F))
+                             ctypes.byref(bcs) if bcs is not None else None, int(bool(gks)), _ptr(F))
     if rc:
         raise ValueError("orc_face_flux failed")
     return F
@@ -206,14 +209,14 @@ def micro_slope(U, lam, b):
     return a
 
 
-def face_flux_o2(params, WL, rhohL, gWL, gHL, dxL, WR, rhohR, gWR, gHR, dxR, n, dt):
+def face_flux_o2(params, WL, rhohL, gWL, gHL, dxL, WR, rhohR, gWR, gHR, dxR, n, dt, gks=False):
     """Second-order flux of one interior face; gW are [5][3] gradients."""
     P = make_params(params)
     arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (WL, gWL, gHL, dxL, WR, gWR, gHR, dxR, n)]
     F = np.empty(5)
     lib().orc_face_flux_o2(ctypes.byref(P), _ptr(arrs[0]), float(rhohL), _ptr(arrs[1]), _ptr(arrs[2]),
                            _ptr(arrs[3]), _ptr(arrs[4]), float(rhohR), _ptr(arrs[5]), _ptr(arrs[6]),
-                           _ptr(arrs[7]), _ptr(arrs[8]), float(dt), _ptr(F))
+                           _ptr(arrs[7]), _ptr(arrs[8]), float(dt), int(bool(gks)), _ptr(F))
     return F
 
 
@@ -257,6 +260,15 @@ class OracleSim:
             rc = lib().orc_step(self._h, err, 512)
             if rc:
                 raise RuntimeError(f"oracle step failed ({rc}): {err.value.decode()}")
+
+    def gks_step(self, n: int = 1, local: bool = False):
+        """n steps of the gas-kinetic scheme (no particles), with the global or
+        local time steps."""
+        err = ctypes.create_string_buffer(512)
+        for _ in range(n):
+            rc = lib().orc_gks_step(self._h, int(bool(local)), err, 512)
+            if rc:
+                raise RuntimeError(f"oracle GKS step failed ({rc}): {err.value.decode()}")
 
     def geometry(self, which: str):
         s = self.sizes()

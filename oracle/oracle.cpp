@@ -311,7 +311,9 @@ static FaceState face_state(const double* W, double rhoh, const double* n, doubl
 // Face relaxation time (Sec. 2.4 (d)): tau = mu(T0)/p0 + C2 |pL-pR|/|pL+pR| dt.
 // ghost_hydro: the R side is a far-field ghost that emits no particles, so its
 // incoming half carries the full UGKS free-transport coefficient q4.
-static void interior_flux(const FaceState& L, const FaceState& Rs, bool ghost_hydro,
+// gks: a step without particles (the gas-kinetic scheme the method reduces to
+// when no particle is sampled, Sec. 4): both halves carry q4.
+static void interior_flux(const FaceState& L, const FaceState& Rs, bool ghost_hydro, bool gks,
                           const double* n, double dt, const orc_params& P, double F[5]) {
     double HL[5], GL[5], HR[5], GR[5];
     half_moments(L.Un, L.Ut, n, L.lam, +1, HL, GL);
@@ -327,9 +329,10 @@ static void interior_flux(const FaceState& L, const FaceState& Rs, bool ghost_hy
     for (int d = 0; d < 3; ++d) Ut0[d] = s0.U[d] - Un0 * n[d];
     double H0[5], G0[5];
     half_moments(Un0, Ut0, n, s0.lam, 0, H0, G0);
-    double cR = ghost_hydro ? q[3] : q[5];
+    double cL = gks ? q[3] : q[5];
+    double cR = (ghost_hydro || gks) ? q[3] : q[5];
     for (int k = 0; k < 5; ++k)
-        F[k] = q[0] * (s0.rho * G0[k]) + q[5] * (L.rhoh * GL[k]) + cR * (Rs.rhoh * GR[k]);
+        F[k] = q[0] * (s0.rho * G0[k]) + cL * (L.rhoh * GL[k]) + cR * (Rs.rhoh * GR[k]);
 }
 
 // Diffuse isothermal wall (Sec. 2.4 (e)), n pointing from the gas into the wall.
@@ -337,13 +340,14 @@ static void interior_flux(const FaceState& L, const FaceState& Rs, bool ghost_hy
 // half: the wall Maxwellian g_w(T_w, U_w) over the whole step with rho_w from
 // zero net mass flux of the wave (reading: particles reflect individually).
 static void wall_flux(const FaceState& L, double tau, const orc_bc& bc, const double* n,
-                      double dt, const orc_params& P, double F[5]) {
+                      double dt, bool gks, const orc_params& P, double F[5]) {
     double q[7];
     qcoef(dt, tau, q);
     double HL[5], GL[5];
     half_moments(L.Un, L.Ut, n, L.lam, +1, HL, GL);
     double Gin[5];
-    for (int k = 0; k < 5; ++k) Gin[k] = q[0] * (L.rho * GL[k]) + q[5] * (L.rhoh * GL[k]);
+    const double c4 = gks ? q[3] : q[5];
+    for (int k = 0; k < 5; ++k) Gin[k] = q[0] * (L.rho * GL[k]) + c4 * (L.rhoh * GL[k]);
     double lamw = 1.0 / (2.0 * P.R * bc.T_w);
     double Uwn = dot3(bc.U_w, n), Uwt[3];
     for (int d = 0; d < 3; ++d) Uwt[d] = bc.U_w[d] - Uwn * n[d];
@@ -354,15 +358,15 @@ static void wall_flux(const FaceState& L, double tau, const orc_bc& bc, const do
 }
 
 static void boundary_flux(const double* WL, double rhohL, double tauL, const orc_bc& bc,
-                          const double* n, double dt, const orc_params& P, double F[5]) {
+                          const double* n, double dt, bool gks, const orc_params& P, double F[5]) {
     FaceState L = face_state(WL, rhohL, n, P.R);
-    if (bc.type == ORC_BC_DIFFUSE_WALL) { wall_flux(L, tauL, bc, n, dt, P, F); return; }
+    if (bc.type == ORC_BC_DIFFUSE_WALL) { wall_flux(L, tauL, bc, n, dt, gks, P, F); return; }
     if (bc.type == ORC_BC_SPECULAR) {
         // Mirror ghost: same state with the normal velocity reversed.  Only the
         // normal momentum flux survives; mass, energy and shear are zero.
         FaceState Rg = L; Rg.Un = -L.Un;
         double Ff[5];
-        interior_flux(L, Rg, false, n, dt, P, Ff);
+        interior_flux(L, Rg, false, gks, n, dt, P, Ff);
         double fn = dot3(&Ff[1], n);
         F[0] = 0.0; F[4] = 0.0;
         for (int d = 0; d < 3; ++d) F[1 + d] = fn * n[d];
@@ -372,7 +376,7 @@ static void boundary_flux(const double* WL, double rhohL, double tauL, const orc
     // both all-hydrodynamic and emitting no particles (reading).
     FaceState Rg = (bc.type == ORC_BC_INFLOW) ? face_state(bc.W_in, bc.W_in[0], n, P.R) : L;
     Rg.rhoh = Rg.rho;
-    interior_flux(L, Rg, true, n, dt, P, F);
+    interior_flux(L, Rg, true, gks, n, dt, P, F);
 }
 
 // ------------------------------------------------ second-order reconstruction
@@ -659,7 +663,7 @@ static SideO2 side_o1(const Frame& R, const double* Wlab, double rhoh) {
 //   F^{fr,wave}= int u_n [a4 g0^h + a5 u.g_x^h] psi  (upwind: L for u_n > 0, R for u_n < 0)
 // with g_x from W_x = (grad W_L + grad W_R)/2 (reading), g_t from
 // W_t = -int u.g_x psi, and all slopes solved from the moment system.
-static void interior_flux_o2(const SideO2& L, const SideO2& Rs, const double* pLR, double dt,
+static void interior_flux_o2(const SideO2& L, const SideO2& Rs, const double* pLR, double dt, bool gks,
                              const orc_params& P, double Ff[5]) {
     FrameMom ML = frame_moments(L.U, L.lam, +1), MR = frame_moments(Rs.U, Rs.lam, -1);
     double W0[5];
@@ -695,12 +699,32 @@ static void interior_flux_o2(const SideO2& L, const SideO2& Rs, const double* pL
         Poly unpsi = mul(un, psi(k));
         double feq = q[0] * s0.rho * expect(M0, unpsi) + q[2] * expect(M0, mul(unpsi, lin(At)));
         for (int d = 0; d < 3; ++d) feq += q[1] * expect(M0, mul(mul(unpsi, coord(d)), lin(a0[d])));
-        double ffr = q[5] * (L.rhoh * expect(ML, unpsi) + Rs.rhoh * expect(MR, unpsi));
+        // without particles (gks) the whole free transport q4, q5 is the wave's
+        const double c4 = gks ? q[3] : q[5], c5 = gks ? q[4] : q[6];
+        double ffr = c4 * (L.rhoh * expect(ML, unpsi) + Rs.rhoh * expect(MR, unpsi));
         for (int d = 0; d < 3; ++d) {
             Poly ud = mul(unpsi, coord(d));
-            ffr += q[6] * (expect(ML, mul(ud, lin(aL[d]))) + expect(MR, mul(ud, lin(aR[d]))));
+            ffr += c5 * (expect(ML, mul(ud, lin(aL[d]))) + expect(MR, mul(ud, lin(aR[d]))));
         }
         Ff[k] = feq + ffr;
+    }
+    // Prandtl-number fix of the equilibrium part (reading, after the GKS
+    // correction of Xu 2001): the energy flux gains (1/Pr - 1) q_n, q_n the
+    // heat flux int (u_n - U0_n) |u - U0|^2/2 f_eq of the time-integrated
+    // equilibrium part f_eq = q1 g0 + q2 u.g_x + q3 g_t, relative to U0.
+    if (P.Pr > 0.0 && P.Pr != 1.0) {
+        Poly sq;
+        for (int d = 0; d < 3; ++d) {
+            Poly rd = coord(d);
+            rd.push_back(Term{-s0.U[d], 0, 0, 0});
+            for (const Term& t : mul(rd, rd)) sq.push_back(Term{0.5 * t.c, t.a, t.b, t.e});
+        }
+        Poly rn = coord(0);
+        rn.push_back(Term{-s0.U[0], 0, 0, 0});
+        const Poly h = mul(rn, sq);
+        double qn = q[0] * s0.rho * expect(M0, h) + q[2] * expect(M0, mul(h, lin(At)));
+        for (int d = 0; d < 3; ++d) qn += q[1] * expect(M0, mul(mul(h, coord(d)), lin(a0[d])));
+        Ff[4] += (1.0 / P.Pr - 1.0) * qn;
     }
 }
 
@@ -708,13 +732,14 @@ static void interior_flux_o2(const SideO2& L, const SideO2& Rs, const double* pL
 // side whose reconstruction is not positive) and evaluate the O2 flux.
 static void face_flux_o2(const Frame& R, const double* WL, double rhohL, const double* gWL, const double* gHL,
                          const double* dxL, const double* WR, double rhohR, const double* gWR,
-                         const double* gHR, const double* dxR, double dt, const orc_params& P, double F[5]) {
+                         const double* gHR, const double* dxR, double dt, bool gks, const orc_params& P,
+                         double F[5]) {
     SideO2 L, Rs;
     if (!side_o2(R, WL, rhohL, gWL, gHL, dxL, L)) L = side_o1(R, WL, rhohL);
     if (!side_o2(R, WR, rhohR, gWR, gHR, dxR, Rs)) Rs = side_o1(R, WR, rhohR);
     double pLR[2] = {0.5 * L.W[0] / L.lam, 0.5 * Rs.W[0] / Rs.lam};
     double Ff[5];
-    interior_flux_o2(L, Rs, pLR, dt, P, Ff);
+    interior_flux_o2(L, Rs, pLR, dt, gks, P, Ff);
     frame_to_lab(R, Ff, F);
 }
 
@@ -883,6 +908,101 @@ struct SimBase {
     virtual bool set_particles(int64_t, const uint64_t*, const int32_t*, const double*, const double*,
                                const double*, std::string&) = 0;
     virtual int track_one(uint64_t, int32_t, double*, double*, double, double, int64_t, int32_t*, int32_t*) const = 0;
+    // a3 (order 2): limited least-squares gradients of W and rho^h; a4: the
+    // time-integrated wave flux F of every face from W and rho^h, over dt or,
+    // when dtf is given, over dtf[f].  gks: no particles (both halves of the
+    // free transport carry q4, q5).
+    void face_fluxes(bool gks, const std::vector<double>* dtf) {
+        const int nc = g.nc, nf = g.nf;
+        const orc_params& p = P;
+        std::vector<double> gW, gH;
+        if (p.order == 2) limited_gradients(g, p, W, rhoh, true, gW, gH);
+        F.assign(5 * (size_t)nf, 0.0);
+        for (int f = 0; f < nf; ++f) {
+            const double* n = &g.f_n[3 * (size_t)f];
+            const double dtv = dtf ? (*dtf)[f] : dt;
+            int o = g.f_owner[f], nb = g.f_nbr[f];
+            double WL[5], Fv[5];
+            for (int k = 0; k < 5; ++k) WL[k] = W[(size_t)k * nc + o];
+            if (nb >= 0 && p.order == 2) {
+                double WR[5], dxL[3], dxR[3];
+                for (int k = 0; k < 5; ++k) WR[k] = W[(size_t)k * nc + nb];
+                const double* xf = &g.f_c[3 * (size_t)f];
+                for (int d = 0; d < 3; ++d) {
+                    dxL[d] = xf[d] - g.cen[3 * (size_t)o + d];
+                    dxR[d] = xf[d] - g.cen[3 * (size_t)nb + d];
+                }
+                Frame R = frame_of(n);
+                face_flux_o2(R, WL, rhoh[o], &gW[15 * (size_t)o], &gH[3 * (size_t)o], dxL, WR, rhoh[nb],
+                             &gW[15 * (size_t)nb], &gH[3 * (size_t)nb], dxR, dtv, gks, p, Fv);
+            } else if (nb >= 0) {
+                double WR[5];
+                for (int k = 0; k < 5; ++k) WR[k] = W[(size_t)k * nc + nb];
+                FaceState L = face_state(WL, rhoh[o], n, p.R), Rs = face_state(WR, rhoh[nb], n, p.R);
+                interior_flux(L, Rs, false, gks, n, dtv, p, Fv);
+            } else {
+                boundary_flux(WL, rhoh[o], tau[o], p.bc[g.f_bc[f]], n, dtv, gks, p, Fv);
+            }
+            for (int k = 0; k < 5; ++k) F[(size_t)k * nf + f] = Fv[k];
+        }
+    }
+
+    // One step of the gas-kinetic scheme (GKS) that the method reduces to
+    // without particles (Sec. 4), for the start-up fields of the steady cases
+    // (Sec. 5): W^h = W, nothing sampled, the whole free transport in the wave
+    // flux.  local: local time stepping (reading) with dt_i = CFL |Omega_i| /
+    // sum_d Lambda_i^d per cell, each face integrated over dt_f = the smaller
+    // dt of its cells (the interior cell's at a boundary), and cell i advanced
+    // by dt_i times the mean flux rate F_f / dt_f; t is then left unchanged.
+    int gks_step(bool local, std::string& err) {
+        if (n_particles() != 0) { err = "a GKS step needs a state without particles"; return -10; }
+        const int nc = g.nc, nf = g.nf;
+        const orc_params& p = P;
+        tau.assign(nc, 0.0); rhoh.assign(nc, 0.0);
+        std::vector<double> dtc(nc, 0.0);
+        double rmin = HUGE_VAL;
+        for (int i = 0; i < nc; ++i) {
+            double Wi[5];
+            for (int k = 0; k < 5; ++k) Wi[k] = W[(size_t)k * nc + i];
+            Prim s = prim_of(Wi, p.R);
+            if (!(s.rho > 0.0) || !(s.p > 0.0) || !std::isfinite(s.p)) {
+                err = "non-positive density or pressure in cell " + std::to_string(i);
+                return -9;
+            }
+            tau[i] = tau_cell(s, p);
+            rhoh[i] = s.rho;
+            double c = 3.0 * std::sqrt(p.R * s.T);
+            double lam = ((std::fabs(s.U[0]) + c) * g.dS[3 * i] + (std::fabs(s.U[1]) + c) * g.dS[3 * i + 1])
+                       + (std::fabs(s.U[2]) + c) * g.dS[3 * i + 2];
+            double r = g.vol[i] / lam;
+            dtc[i] = p.CFL * r;
+            if (r < rmin) rmin = r;
+        }
+        dt = p.CFL * rmin;
+        std::vector<double> dtf;
+        if (local) {
+            dtf.assign(nf, 0.0);
+            for (int f = 0; f < nf; ++f) {
+                const int o = g.f_owner[f], nb = g.f_nbr[f];
+                dtf[f] = nb >= 0 ? std::fmin(dtc[o], dtc[nb]) : dtc[o];
+            }
+        }
+        face_fluxes(true, local ? &dtf : nullptr);
+        for (int i = 0; i < nc; ++i) {
+            for (int q = 0; q < 5; ++q) {
+                double s = 0.0;
+                for (int k = 0; k < 4; ++k) {
+                    int f = g.tet_face[4 * i + k];
+                    double v = local ? (F[(size_t)q * nf + f] / dtf[f]) * g.f_area[f] : F[(size_t)q * nf + f] * g.f_area[f];
+                    s = s + (g.tet_sign[4 * i + k] > 0 ? v : -v);
+                }
+                double& Wq = W[(size_t)q * nc + i];
+                Wq = local ? Wq - (dtc[i] * s) / g.vol[i] : Wq - s / g.vol[i];
+            }
+        }
+        if (!local) t += dt;
+        return 0;
+    }
 };
 
 template <class Real> struct Sim : SimBase {
@@ -1123,37 +1243,8 @@ template <class Real> struct Sim : SimBase {
         counters[0] = (int64_t)parts.size(); counters[1] = ncoll; counters[2] = nexit;
         counters[3] = nlost; counters[4] = ncross; counters[5] = nwall; counters[6] = n_sampled;
         parts.swap(kept);
-        // ---- a4: wave flux per face from W^n and rho^{h,n}; a3 (order 2):
-        // limited least-squares gradients of W and rho^h
-        std::vector<double> gW, gH;
-        if (p.order == 2) limited_gradients(g, p, W, rhoh, true, gW, gH);
-        F.assign(5 * (size_t)nf, 0.0);
-        for (int f = 0; f < nf; ++f) {
-            const double* n = &g.f_n[3 * (size_t)f];
-            int o = g.f_owner[f], nb = g.f_nbr[f];
-            double WL[5], Fv[5];
-            for (int k = 0; k < 5; ++k) WL[k] = W[(size_t)k * nc + o];
-            if (nb >= 0 && p.order == 2) {
-                double WR[5], dxL[3], dxR[3];
-                for (int k = 0; k < 5; ++k) WR[k] = W[(size_t)k * nc + nb];
-                const double* xf = &g.f_c[3 * (size_t)f];
-                for (int d = 0; d < 3; ++d) {
-                    dxL[d] = xf[d] - g.cen[3 * (size_t)o + d];
-                    dxR[d] = xf[d] - g.cen[3 * (size_t)nb + d];
-                }
-                Frame R = frame_of(n);
-                face_flux_o2(R, WL, rhoh[o], &gW[15 * (size_t)o], &gH[3 * (size_t)o], dxL, WR, rhoh[nb],
-                             &gW[15 * (size_t)nb], &gH[3 * (size_t)nb], dxR, dt, p, Fv);
-            } else if (nb >= 0) {
-                double WR[5];
-                for (int k = 0; k < 5; ++k) WR[k] = W[(size_t)k * nc + nb];
-                FaceState L = face_state(WL, rhoh[o], n, p.R), Rs = face_state(WR, rhoh[nb], n, p.R);
-                interior_flux(L, Rs, false, n, dt, p, Fv);
-            } else {
-                boundary_flux(WL, rhoh[o], tau[o], p.bc[g.f_bc[f]], n, dt, p, Fv);
-            }
-            for (int k = 0; k < 5; ++k) F[(size_t)k * nf + f] = Fv[k];
-        }
+        // ---- a3 (order 2) + a4: wave flux per face from W^n and rho^{h,n}
+        face_fluxes(false, nullptr);
         // ---- a10: W^{n+1} = W^n - 1/|Omega| sum_j (F^eq + F^{fr,wave}) |S| + F^{fr,p}/|Omega|
         for (int i = 0; i < nc; ++i) {
             for (int q = 0; q < 5; ++q) {
@@ -1569,14 +1660,14 @@ void orc_maxwell_moments(const double U[3], double lam, const double n[3], int h
 
 int orc_face_flux(const orc_params* p, int kind, const double WL[5], double rhohL,
                   const double WR[5], double rhohR, const double n[3], double dt,
-                  double tau_wall, const orc_bc* bc, double F[5]) {
+                  double tau_wall, const orc_bc* bc, int32_t gks, double F[5]) {
     if (kind == 0) {
         FaceState L = face_state(WL, rhohL, n, p->R), R = face_state(WR, rhohR, n, p->R);
-        interior_flux(L, R, false, n, dt, *p, F);
+        interior_flux(L, R, false, gks != 0, n, dt, *p, F);
         return 0;
     }
     if (!bc) return -1;
-    boundary_flux(WL, rhohL, tau_wall, *bc, n, dt, *p, F);
+    boundary_flux(WL, rhohL, tau_wall, *bc, n, dt, gks != 0, *p, F);
     return 0;
 }
 
@@ -1612,6 +1703,13 @@ void orc_free(orc_sim* h) {
 int orc_step(orc_sim* h, char* err, int32_t errlen) {
     std::string e;
     int rc = h->s->do_step(e);
+    if (rc) set_err(err, errlen, e);
+    return rc;
+}
+
+int orc_gks_step(orc_sim* h, int32_t local, char* err, int32_t errlen) {
+    std::string e;
+    int rc = h->s->gks_step(local != 0, e);
     if (rc) set_err(err, errlen, e);
     return rc;
 }
@@ -1701,9 +1799,10 @@ void orc_micro_slope(const double U[3], double lam, const double b[5], double a[
 
 int orc_face_flux_o2(const orc_params* p, const double WL[5], double rhohL, const double gWL[15], const double gHL[3],
                      const double dxL[3], const double WR[5], double rhohR, const double gWR[15],
-                     const double gHR[3], const double dxR[3], const double n[3], double dt, double F[5]) {
+                     const double gHR[3], const double dxR[3], const double n[3], double dt, int32_t gks,
+                     double F[5]) {
     Frame R = frame_of(n);
-    face_flux_o2(R, WL, rhohL, gWL, gHL, dxL, WR, rhohR, gWR, gHR, dxR, dt, *p, F);
+    face_flux_o2(R, WL, rhohL, gWL, gHL, dxL, WR, rhohR, gWR, gHR, dxR, dt, gks != 0, *p, F);
     return 0;
 }
 

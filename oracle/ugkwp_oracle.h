@@ -31,6 +31,9 @@ typedef struct {
 typedef struct {
     double R, mu_ref, T_ref, omega, CFL, C2;
     double venkat_K;   /* Venkatakrishnan constant K: epsilon^2 = (K h)^3 (order 2) */
+    double Pr;         /* Prandtl number of the wave's equilibrium heat flux (order 2):
+                        * 0 or 1 = BGK as printed; otherwise the energy flux of the
+                        * equilibrium part gains (1/Pr - 1) times its heat flux */
     int32_t order, N_ref, N_min, precision, max_crossings, n_bc;
     int32_t sampling;  /* 0: pairs U +/- sqrt(RT) X as printed; 1: the same pairs with X
                         * scaled per cell so that their thermal energy is exactly
@@ -60,10 +63,11 @@ void orc_maxwell_moments(const double U[3], double lam, const double n[3], int h
                          double H[5], double G[5]);
 /* Time-integrated wave flux of one face (F^eq + F^{fr,wave}, per unit area,
  * normal from L to R).  kind: 0 interior, or an ORC_BC_* type with the ghost
- * built from WL (and bc).  rhoh = hydrodynamic density rho^h of each side. */
+ * built from WL (and bc).  rhoh = hydrodynamic density rho^h of each side.
+ * gks != 0: the flux of a step without particles (free transport q4). */
 int orc_face_flux(const orc_params* p, int kind, const double WL[5], double rhohL,
                   const double WR[5], double rhohR, const double n[3], double dt,
-                  double tau_wall, const orc_bc* bc, double F[5]);
+                  double tau_wall, const orc_bc* bc, int32_t gks, double F[5]);
 
 /* ---- simulation --------------------------------------------------------- */
 orc_sim* orc_create(const orc_params* p, int32_t n_nodes, const double* xyz,
@@ -72,6 +76,9 @@ orc_sim* orc_create(const orc_params* p, int32_t n_nodes, const double* xyz,
                     char* err, int32_t errlen);
 void orc_free(orc_sim* s);
 int orc_step(orc_sim* s, char* err, int32_t errlen);
+/* One step of the gas-kinetic scheme (no particles; the state must hold none):
+ * global time step (local = 0) or local time steps (local = 1). */
+int orc_gks_step(orc_sim* s, int32_t local, char* err, int32_t errlen);
 
 /* sizes: [n_cells, n_faces, n_boundary_faces, n_particles, step] */
 void orc_sizes(const orc_sim* s, int64_t out[5]);
@@ -114,7 +121,8 @@ void orc_slope_moment(const double U[3], double lam, int half, const double a[5]
 void orc_micro_slope(const double U[3], double lam, const double b[5], double a[5]);
 int orc_face_flux_o2(const orc_params* p, const double WL[5], double rhohL, const double gWL[15], const double gHL[3],
                      const double dxL[3], const double WR[5], double rhohR, const double gWR[15],
-                     const double gHR[3], const double dxR[3], const double n[3], double dt, double F[5]);
+                     const double gHR[3], const double dxR[3], const double n[3], double dt, int32_t gks,
+                     double F[5]);
 
 /* Frozen-particle wave map (first order only): K steps of
  *   W^{n+1} = W^n - sum_f (+/-) F_f(W^n; theta) |S_f| / |Omega| + pf^n / |Omega|

@@ -8,7 +8,11 @@
 * the Chapman-Enskog limit (tau << dt): shear stress -mu dw/dx dt and heat
   flux -5/2 R mu dT/dx dt with mu = tau p (BGK, Pr = 1);
 * zero gradients give the first-order flux; at equal resolution the
-  second-order scheme is closer to the exact Sod solution.
+  second-order scheme is closer to the exact Sod solution;
+* Prandtl-number fix: for any uniform velocity and pressure with a
+  temperature gradient, the energy flux of the equilibrium part is exactly
+  q2 (5/2) p R dT/dn / Pr (the Chapman-Enskog heat flux of the BGK model with
+  the conductivity scaled by 1/Pr), and shear alone is left untouched.
 """
 import math
 
@@ -158,6 +162,62 @@ def test_navier_stokes_heat_flux_limit():
     F = oracle.face_flux_o2(params, W, rho, gW, gW[0], z, W, rho, gW, gW[0], z, [1.0, 0.0, 0.0], dt)
     mu = tau * p
     assert F[4] == pytest.approx(-2.5 * 1.0 * mu * gam * dt, rel=3e-3)
+
+
+@pytest.mark.parametrize("tau", [1e-4, 1e-2, 1.0])
+def test_prandtl_fix_heat_flux_closed_form(tau):
+    """rho^h = 0 leaves the equilibrium part alone.  With p and U uniform and T
+    varying, g_t = -(U.grad) g, and the heat flux relative to U0 of
+    q2 u.g_x + q3 g_t is q2 (5/2) p R dT/dn whatever U (the odd moments drop);
+    the fix multiplies it by 1/Pr and changes nothing else."""
+    rng = np.random.default_rng(int(1e4 * tau) + 3)
+    Rg, rho, T = 1.0, 1.3, 0.9
+    p = rho * Rg * T
+    dt = 0.01
+    n = rng.normal(size=3); n /= np.linalg.norm(n)
+    U = rng.normal(size=3) * 0.4
+    gT = rng.normal(size=3) * 0.05
+    grho = -rho * gT / T  # uniform pressure
+    gW = np.zeros((5, 3))
+    gW[0] = grho
+    for c in range(3):
+        gW[1 + c] = U[c] * grho
+    gW[4] = 0.5 * U.dot(U) * grho
+    W = _W(rho, U, p)
+    z = np.zeros(3)
+    params = dict(PARAMS, R=Rg, mu_ref=tau * p / T ** PARAMS["omega"])
+    q2 = oracle.qcoef(dt, tau)[1]
+    ref = None
+    for Pr in (1.0, 2.0 / 3.0, 0.72):
+        F = oracle.face_flux_o2(dict(params, Pr=Pr), W, 0.0, gW, z, z, W, 0.0, gW, z, z, n, dt)
+        if ref is None:
+            ref = F
+            continue
+        np.testing.assert_array_equal(F[:4], ref[:4])
+        assert F[4] - ref[4] == pytest.approx((1.0 / Pr - 1.0) * q2 * 2.5 * p * Rg * gT.dot(n), rel=1e-9)
+    # at rest the whole energy flux is the heat flux
+    W0 = _W(rho, (0.0, 0.0, 0.0), p)
+    g0 = np.zeros((5, 3)); g0[0] = grho
+    for Pr in (1.0, 2.0 / 3.0):
+        F = oracle.face_flux_o2(dict(params, Pr=Pr), W0, 0.0, g0, z, z, W0, 0.0, g0, z, z, n, dt)
+        assert F[4] == pytest.approx(q2 * 2.5 * p * Rg * gT.dot(n) / Pr, rel=1e-11)
+
+
+def test_prandtl_fix_leaves_shear_and_uniform_states():
+    rho, p, gam, dt = 1.0, 1.0, 0.05, 0.01
+    W = _W(rho, (0.0, 0.0, 0.0), p)
+    gW = np.zeros((5, 3)); gW[3, 0] = rho * gam  # d(rho w)/dx: shear, no heat flux
+    z = np.zeros(3)
+    n = [1.0, 0.0, 0.0]
+    a = oracle.face_flux_o2(dict(PARAMS, Pr=1.0), W, rho, gW, gW[0], z, W, rho, gW, gW[0], z, n, dt)
+    b = oracle.face_flux_o2(dict(PARAMS, Pr=2.0 / 3.0), W, rho, gW, gW[0], z, W, rho, gW, gW[0], z, n, dt)
+    np.testing.assert_allclose(b, a, rtol=0, atol=1e-18)
+    WL = _W(1.0, (0.3, -0.1, 0.2), 0.9)
+    WR = _W(0.4, (0.1, 0.2, -0.1), 0.5)
+    z5 = np.zeros((5, 3))
+    a = oracle.face_flux_o2(dict(PARAMS, Pr=1.0), WL, 0.6, z5, z, z, WR, 0.3, z5, z, z, n, dt)
+    b = oracle.face_flux_o2(dict(PARAMS, Pr=0.5), WL, 0.6, z5, z, z, WR, 0.3, z5, z, z, n, dt)
+    np.testing.assert_allclose(b, a, rtol=1e-13, atol=1e-18)
 
 
 def test_zero_gradients_reduce_to_first_order():
