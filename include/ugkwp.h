@@ -117,7 +117,11 @@ typedef struct {
 typedef struct {
     double R;                    /* specific gas constant */
     double mu_ref, T_ref, omega; /* viscosity law */
-    double Pr;                   /* reserved (BGK: Pr = 1); must be 0 or 1 */
+    double Pr;                   /* Prandtl number (0 or 1: BGK).  Otherwise, at order 2, the
+                                  * energy flux of the wave's equilibrium part gains (1/Pr - 1)
+                                  * times its heat flux relative to the face velocity (the
+                                  * GKS Prandtl fix; particles stay BGK).  E_ARG if < 0 or
+                                  * not finite */
     double CFL;                  /* Courant number C in (0, 1] */
     double C2;                   /* numerical-dissipation constant (>= 0) */
     double venkat_K;             /* Venkatakrishnan constant K (>= 0): epsilon^2 = (K |Omega|^(1/3))^3 */
@@ -208,6 +212,21 @@ int ugkwp_step(ugkwp_sim* s, int32_t n_steps, ugkwp_stats* st);
 /* Wait for the stream and return (then clear) any device-side error. */
 int ugkwp_sync(ugkwp_sim* s);
 
+/* Start-up steps of the gas-kinetic scheme (GKS), the method without
+ * particles (Sec. 3.2), for the initial field of a steady case (Sec. 4.3, 4.4: GKS
+ * start-up, with local time stepping): per step, no particle is sampled
+ * (W^h = W) and the wave flux carries the whole free transport (q4, q5 in
+ * place of a4, a5).  local_dt = 0: the global time step; t advances.
+ * local_dt = 1: local time steps dt_i = CFL |Omega_i| / sum_d Lambda_i^d, each
+ * face integrated over the smaller dt of its cells (the interior cell's at a
+ * boundary) and cell i advanced by dt_i times the mean flux rates (a pseudo
+ * time: t stays).  Neither advances the step counter or the time averages.
+ * Asynchronous like ugkwp_step (st, if non-NULL, gets t and dt and syncs);
+ * the call itself reads the particle count first (synchronising).
+ * Errors: E_ARG, E_STATE (the state holds particles: GKS steps come before
+ * the first ugkwp_step), E_NONFINITE at the next synchronising call. */
+int ugkwp_gks_steps(ugkwp_sim* s, int32_t n_steps, int32_t local_dt, ugkwp_stats* st);
+
 /* Time averaging for steady states (Sec. 2.4 (c)).  start != 0 resets the
  * sums and, from the next step on, adds dt^n W^n (the state after step n) to
  * them; start == 0 stops adding (the sums stay readable).  UGKWP_WBAR then
@@ -243,7 +262,8 @@ int ugkwp_import_state(ugkwp_sim* s, const ugkwp_state* st);
  *  0 dt (1 double), 1 tau [n_cells], 2 rho^h before sampling [n_cells],
  *  3 N_sam [n_cells] (int64), 4 m_sam [n_cells], 5 wave flux
  *  F^eq + F^{fr,wave} per unit area [5][n_faces] (face numbering: by owner
- *  tet then its local face), 6 particle flux F^{fr,p} in fixed point
+ *  tet then its local face; after a GKS step with local time steps the mean
+ *  rate F / dt_f), 6 particle flux F^{fr,p} in fixed point
  *  [5][n_cells] (int64), 7 survivor mass in fixed point [n_cells] (int64),
  *  8 survivor count [n_cells] (int64); at order 2 only: 9 limited gradients
  *  of W [5][3][n_cells] (component, direction, cell), 10 limited gradient of

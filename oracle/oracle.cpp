@@ -312,7 +312,7 @@ static FaceState face_state(const double* W, double rhoh, const double* n, doubl
 // ghost_hydro: the R side is a far-field ghost that emits no particles, so its
 // incoming half carries the full UGKS free-transport coefficient q4.
 // gks: a step without particles (the gas-kinetic scheme the method reduces to
-// when no particle is sampled, Sec. 4): both halves carry q4.
+// when no particle is sampled, Sec. 3.2): both halves carry q4.
 static void interior_flux(const FaceState& L, const FaceState& Rs, bool ghost_hydro, bool gks,
                           const double* n, double dt, const orc_params& P, double F[5]) {
     double HL[5], GL[5], HR[5], GR[5];
@@ -948,12 +948,13 @@ struct SimBase {
     }
 
     // One step of the gas-kinetic scheme (GKS) that the method reduces to
-    // without particles (Sec. 4), for the start-up fields of the steady cases
-    // (Sec. 5): W^h = W, nothing sampled, the whole free transport in the wave
+    // without particles (Sec. 3.2), for the start-up fields of the steady cases
+    // (Sec. 4.3, 4.4): W^h = W, nothing sampled, the whole free transport in the wave
     // flux.  local: local time stepping (reading) with dt_i = CFL |Omega_i| /
     // sum_d Lambda_i^d per cell, each face integrated over dt_f = the smaller
     // dt of its cells (the interior cell's at a boundary), and cell i advanced
-    // by dt_i times the mean flux rate F_f / dt_f; t is then left unchanged.
+    // by dt_i times the mean flux rate F_f / dt_f (which F then holds); t is
+    // then left unchanged.
     int gks_step(bool local, std::string& err) {
         if (n_particles() != 0) { err = "a GKS step needs a state without particles"; return -10; }
         const int nc = g.nc, nf = g.nf;
@@ -988,12 +989,15 @@ struct SimBase {
             }
         }
         face_fluxes(true, local ? &dtf : nullptr);
+        if (local)  // F becomes the mean flux rate F_f / dt_f
+            for (int q = 0; q < 5; ++q)
+                for (int f = 0; f < nf; ++f) F[(size_t)q * nf + f] = F[(size_t)q * nf + f] / dtf[f];
         for (int i = 0; i < nc; ++i) {
             for (int q = 0; q < 5; ++q) {
                 double s = 0.0;
                 for (int k = 0; k < 4; ++k) {
                     int f = g.tet_face[4 * i + k];
-                    double v = local ? (F[(size_t)q * nf + f] / dtf[f]) * g.f_area[f] : F[(size_t)q * nf + f] * g.f_area[f];
+                    double v = F[(size_t)q * nf + f] * g.f_area[f];
                     s = s + (g.tet_sign[4 * i + k] > 0 ? v : -v);
                 }
                 double& Wq = W[(size_t)q * nc + i];

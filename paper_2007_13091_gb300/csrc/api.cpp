@@ -143,6 +143,7 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, D
     S.tauf = c.take<float>(nc);
     S.usig = c.take<float4>(nc);
     S.sig = c.take<double>(nc);
+    S.dtc = c.take<double>(nc);
     S.wsum = c.take<double>(5 * nc);
     S.tsum = c.take<double>(1);
     S.rhoh = c.take<double>(nc);
@@ -180,7 +181,7 @@ int check_params(const ugkwp_params* p, const MeshHost* mh) {
         return fail(UGKWP_E_ARG, "R, mu_ref and T_ref must be positive and omega finite");
     if (!(p->CFL > 0.0 && p->CFL <= 1.0)) return fail(UGKWP_E_ARG, "CFL must be in (0, 1]");
     if (!(p->C2 >= 0.0)) return fail(UGKWP_E_ARG, "C2 must be >= 0");
-    if (!(p->Pr == 0.0 || p->Pr == 1.0)) return fail(UGKWP_E_UNSUPPORTED, "only the BGK model (Pr = 1) is available");
+    if (!(p->Pr >= 0.0) || !std::isfinite(p->Pr)) return fail(UGKWP_E_ARG, "Pr must be finite and >= 0 (0: BGK)");
     if (p->order != 1 && p->order != 2) return fail(UGKWP_E_ARG, "order must be 1 or 2");
     if (p->order == 2 && !(p->venkat_K >= 0.0)) return fail(UGKWP_E_ARG, "venkat_K must be >= 0");
     if (p->N_ref <= 0 || p->N_min < 0) return fail(UGKWP_E_ARG, "N_ref must be > 0 and N_min >= 0");
@@ -361,6 +362,7 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     DevParams& P = s->P;
     std::memset(&P, 0, sizeof(P));
     P.R = p->R; P.mu_ref = p->mu_ref; P.T_ref = p->T_ref; P.omega = p->omega; P.CFL = p->CFL; P.C2 = p->C2;
+    P.pr_fix = (p->Pr > 0.0 && p->Pr != 1.0) ? 1.0 / p->Pr - 1.0 : 0.0;
     P.N_ref = p->N_ref; P.N_min = p->N_min; P.max_crossings = p->max_crossings; P.precision = p->precision;
     P.order = p->order;
     P.sampling = p->sampling;
@@ -667,6 +669,27 @@ int enqueue_step(ugkwp_sim* s) {
     return UGKWP_OK;
 }
 
+// One step of the gas-kinetic scheme (no particles; mode 1: global time step,
+// 2: local time steps) on the bound stream, as direct launches with a copy of
+// the parameters that carries the mode.
+int enqueue_gks_step(ugkwp_sim* s, int32_t mode) {
+    cudaStream_t q = s->stream;
+    DevParams P = s->P;
+    P.gks = mode;
+    P.averaging = 0;
+    timed(s, UGKWP_K_RESET, 1, q, [&] { launch_reset(s->M, s->S, q); });
+    timed(s, UGKWP_K_CELL_PREP, 1, q, [&] { launch_cell_prep(s->M, s->S, P, q); });
+    timed(s, UGKWP_K_SAMPLE_COUNT, 1, q, [&] { launch_sample_count(s->M, s->S, P, q); });
+    if (P.order == 2)
+        timed(s, UGKWP_K_GRADIENTS, 1, q, [&] { launch_gradients(s->M, s->S, P, s->lc.wave_blocks, q); });
+    if (P.order == 2 && s->M.nif > 0)
+        timed(s, UGKWP_K_FLUX_O2, 1, q, [&] { launch_face_flux_o2(s->M, s->S, P, s->lc.wave_blocks, q); });
+    const int first = P.order == 2 ? s->M.nif : 0;
+    if (s->M.nf > first) timed(s, UGKWP_K_FLUX, 1, q, [&] { launch_face_flux(s->M, s->S, P, first, q); });
+    timed(s, UGKWP_K_UPDATE, 1, q, [&] { launch_cell_update(s->M, s->S, P, q); });
+    return UGKWP_OK;
+}
+
 // Two steps as one CUDA graph for the current parity (captured on first use).
 int launch_step_pair(ugkwp_sim* s, bool& used) {
     used = false;
@@ -748,6 +771,32 @@ int ugkwp_step(ugkwp_sim* s, int32_t n_steps, ugkwp_stats* st) {
         st->n_sampled = h[CNT_SAMPLED]; st->n_collided = h[CNT_COLLIDED]; st->n_exited = h[CNT_EXITED];
         st->n_lost = h[CNT_LOST]; st->n_crossings = h[CNT_CROSSINGS]; st->n_wall_hits = h[CNT_WALL];
         st->n_moves_total = h[CNT_MOVES];
+        return read_error(s);
+    }
+    return UGKWP_OK;
+}
+
+int ugkwp_gks_steps(ugkwp_sim* s, int32_t n_steps, int32_t local_dt, ugkwp_stats* st) {
+    if (!s || n_steps < 0) return fail(UGKWP_E_ARG, "invalid argument");
+    if (local_dt != 0 && local_dt != 1) return fail(UGKWP_E_ARG, "local_dt must be 0 or 1");
+    cudaStream_t q = s->stream;
+    int64_t na = 0;
+    CU(cudaMemcpyAsync(&na, s->S.cnt64 + CNT_N_A, sizeof(na), cudaMemcpyDeviceToHost, q));
+    CU(cudaStreamSynchronize(q));
+    if (na != 0) return fail(UGKWP_E_STATE, "a GKS step needs a state without particles");
+    for (int32_t k = 0; k < n_steps; ++k) {
+        int rc = enqueue_gks_step(s, local_dt ? 2 : 1);
+        if (rc) return rc;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if (st) {
+        double t = 0, dt = 0;
+        CU(cudaMemcpyAsync(&t, s->S.t, sizeof(double), cudaMemcpyDeviceToHost, q));
+        CU(cudaMemcpyAsync(&dt, s->S.dt, sizeof(double), cudaMemcpyDeviceToHost, q));
+        CU(cudaStreamSynchronize(q));
+        std::memset(st, 0, sizeof(*st));
+        st->t = t; st->dt = dt; st->step = s->step;
         return read_error(s);
     }
     return UGKWP_OK;

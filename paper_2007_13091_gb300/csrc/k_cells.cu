@@ -87,6 +87,7 @@ __global__ void k_cell_prep(DevMesh m, DevState s, DevParams p) {
             const double lam = ((fabs(Ux) + c) * m.dS[i] + (fabs(Uy) + c) * m.dS[nc + i]) + (fabs(Uz) + c) * m.dS[2 * nc + i];
             r = m.vol[i] / lam;
         }
+        if (p.gks == 2) s.dtc[i] = p.CFL * r;
         const double rhop = ((double)s.smass[i] * p.qscale[0]) / m.vol[i];
         s.prim[i] = rho;
         s.prim[nc + i] = Ux;
@@ -125,6 +126,10 @@ __global__ void k_sample_count(DevMesh m, DevState s, DevParams p) {
     const int nc = m.nc;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const double dt = p.CFL * __longlong_as_double(s.cnt64[CNT_DT_BITS]);
+    if (p.gks) {  // GKS step: the time step only, nothing is sampled
+        if (i == 0) s.dt[0] = dt;
+        return;
+    }
     int count = 0, nsam = 0;
     if (i < nc) {
         const double vol = m.vol[i];
@@ -200,6 +205,25 @@ __global__ void k_scan_apply(DevMesh m, DevState s) {
 __global__ void k_cell_update(DevMesh m, DevState s, DevParams p) {
     const int nc = m.nc, nf = m.nf;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p.gks) {
+        // GKS step (no particles): W -= sum_k (+-F_k |S_k|) / |Omega|; with local
+        // steps F_k holds the flux rate and the cell advances by its own dt
+        if (i == 0 && p.gks == 1) s.t[0] = s.t[0] + s.dt[0];
+        if (i >= nc) return;
+        const int own = m.cfs[i];
+        const double vol = m.vol[i];
+        for (int q = 0; q < 5; ++q) {
+            double acc = 0.0;
+            for (int k = 0; k < 4; ++k) {
+                const int f = m.cf[k * nc + i];
+                const double v = s.F[(size_t)q * nf + f] * m.f_area[f];
+                acc = acc + (((own >> k) & 1) ? v : -v);
+            }
+            double& w = s.W[(size_t)q * nc + i];
+            w = p.gks == 2 ? w - (s.dtc[i] * acc) / vol : w - acc / vol;
+        }
+        return;
+    }
     if (i == 0) {
         s.t[0] = s.t[0] + s.dt[0];
         if (p.averaging) s.tsum[0] += s.dt[0];

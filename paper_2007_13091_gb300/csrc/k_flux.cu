@@ -122,6 +122,8 @@ __device__ __forceinline__ void time_coeffs(double dt, double tau, double& q1, d
 
 __device__ void interior_flux(const Side& L, const Side& R, bool ghost_hydro, const double* n, double dt,
                               const DevParams& p, double inv_Tref, double F[5]) {
+    // ghost_hydro: R is a far-field ghost emitting no particles; p.gks: no
+    // particles at all (both halves of the free transport carry q4)
     double GL[5], HL[5], GR[5], HR[5];
     flux_moments(L.Un, L.Ut, n, L.lam, L.rl, +1, GL, HL);
     flux_moments(R.Un, R.Ut, n, R.lam, R.rl, -1, GR, HR);
@@ -146,8 +148,9 @@ __device__ void interior_flux(const Side& L, const Side& R, bool ghost_hydro, co
     for (int c = 0; c < 3; ++c) Feq[1 + c] = rho0 * Un0 * U0[c] + p0 * n[c];
     Feq[4] = Un0 * (E0 + p0);
     (void)lam0;
-    const double cR = ghost_hydro ? q4 : a4;
-    for (int k = 0; k < 5; ++k) F[k] = q1 * Feq[k] + a4 * (L.rhoh * GL[k]) + cR * (R.rhoh * GR[k]);
+    const double cL = p.gks ? q4 : a4;
+    const double cR = (ghost_hydro || p.gks) ? q4 : a4;
+    for (int k = 0; k < 5; ++k) F[k] = q1 * Feq[k] + cL * (L.rhoh * GL[k]) + cR * (R.rhoh * GR[k]);
 }
 
 // ------------------------------------------------------------- order 2
@@ -314,7 +317,7 @@ __device__ __forceinline__ void micro(const double* U, double lam, double th, co
 // expm1.  Where x = dt/tau is small the differences cancel, but their absolute
 // errors stay at rounding level of dt (q1, q4, a4) and dt^2 (q2, q3, a5), the
 // scales at which they enter the flux.
-struct QC { double q1, q2, q3, q4, a4, a5; };
+struct QC { double q1, q2, q3, q4, q5, a4, a5; };
 __device__ __forceinline__ QC time_coeffs_all(double dt, double tau) {
     QC c;
     const double em1 = expm1(-dt / tau);  // e^{-dt/tau} - 1
@@ -325,7 +328,8 @@ __device__ __forceinline__ QC time_coeffs_all(double dt, double tau) {
     c.a4 = c.q4 - dt * e;
     c.q2 = 2.0 * tau * c.q4 - tdt - tdt * e;
     c.q3 = 0.5 * dt * dt - tdt + tau * c.q4;
-    c.a5 = (tdt * e - tau * c.q4) + 0.5 * dt * dt * e;
+    c.q5 = tdt * e - tau * c.q4;
+    c.a5 = c.q5 + 0.5 * dt * dt * e;
     return c;
 }
 
@@ -505,57 +509,78 @@ __device__ void interior_flux_o2(const DevMesh& m, const DevState& s, const DevP
     double tau = p.mu_ref * exp(p.omega * log(T0 * inv_Tref)) / p0;
     if (p.C2 > 0.0) tau += p.C2 * fabs(L.p - Rs.p) / fabs(L.p + Rs.p) * dt;
     const QC qc = time_coeffs_all(dt, tau);
-    // free transport of the hydrodynamic wave, upwind, with slopes
+    // free transport of the hydrodynamic wave, upwind, with slopes; without
+    // particles (GKS step) the whole free transport, q4 and q5, is the wave's
+    const double c4 = p.gks ? qc.q4 : qc.a4, c5 = p.gks ? qc.q5 : qc.a5;
     for (int k = 0; k < 5; ++k)
-        F[k] = qc.a4 * (L.rhoh * L.G[k] + Rs.rhoh * Rs.G[k]) + qc.a5 * (L.S[k] + Rs.S[k]);
-    // equilibrium part: q1 g0 + q2 u.g_x + q3 g_t, in closed form
+        F[k] = c4 * (L.rhoh * L.G[k] + Rs.rhoh * Rs.G[k]) + c5 * (L.S[k] + Rs.S[k]);
+    // equilibrium part Fe: q1 g0 + q2 u.g_x + q3 g_t, in closed form
     const double th0 = p0 * ir0;
     const double U20 = dot3(U0, U0);
-    F[0] += qc.q1 * W0[1];
-    for (int j = 0; j < 3; ++j) F[1 + j] += qc.q1 * (W0[1] * U0[j] + (j == 0 ? p0 : 0.0));
-    F[4] += qc.q1 * U0[0] * (W0[4] + p0);
+    double Fe[5];
+    Fe[0] = qc.q1 * W0[1];
+    for (int j = 0; j < 3; ++j) Fe[1 + j] = qc.q1 * (W0[1] * U0[j] + (j == 0 ? p0 : 0.0));
+    Fe[4] = qc.q1 * U0[0] * (W0[4] + p0);
     double Wt[5], t5[5];
     {
         const DPrim q = dprim(U0, th0, U20, B[0]);
         q_jac<0>(U0, th0, U20, q, t5);
-        for (int k = 0; k < 5; ++k) F[k] += qc.q2 * t5[k];
+        for (int k = 0; k < 5; ++k) Fe[k] += qc.q2 * t5[k];
         euler_jac<0>(U0, th0, U20, B[0], q, t5);
         for (int k = 0; k < 5; ++k) Wt[k] = -t5[k];
     }
     {
         const DPrim q = dprim(U0, th0, U20, B[1]);
         q_jac<1>(U0, th0, U20, q, t5);
-        for (int k = 0; k < 5; ++k) F[k] += qc.q2 * t5[k];
+        for (int k = 0; k < 5; ++k) Fe[k] += qc.q2 * t5[k];
         euler_jac<1>(U0, th0, U20, B[1], q, t5);
         for (int k = 0; k < 5; ++k) Wt[k] -= t5[k];
     }
     {
         const DPrim q = dprim(U0, th0, U20, B[2]);
         q_jac<2>(U0, th0, U20, q, t5);
-        for (int k = 0; k < 5; ++k) F[k] += qc.q2 * t5[k];
+        for (int k = 0; k < 5; ++k) Fe[k] += qc.q2 * t5[k];
         euler_jac<2>(U0, th0, U20, B[2], q, t5);
         for (int k = 0; k < 5; ++k) Wt[k] -= t5[k];
     }
     {
         const DPrim q = dprim(U0, th0, U20, Wt);
         euler_jac<0>(U0, th0, U20, Wt, q, t5);
-        for (int k = 0; k < 5; ++k) F[k] += qc.q3 * t5[k];
+        for (int k = 0; k < 5; ++k) Fe[k] += qc.q3 * t5[k];
     }
+    if (p.pr_fix != 0.0) {
+        // Prandtl-number fix: + (1/Pr - 1) q_n, q_n the heat flux of Fe relative
+        // to U0, from its flux moments and its full moments q1 W0 + (q3 - q2) W_t
+        // (int psi u.g_x = -W_t, int psi g_t = W_t):
+        // q_n = Fe_E - U0.Fe_m + |U0|^2/2 Fe_rho - U0_n (E' - U0.M' + |U0|^2/2 rho')
+        double mo[5];
+        for (int k = 0; k < 5; ++k) mo[k] = qc.q1 * W0[k] + (qc.q3 - qc.q2) * Wt[k];
+        const double qf = (Fe[4] - ((U0[0] * Fe[1] + U0[1] * Fe[2]) + U0[2] * Fe[3])) + 0.5 * U20 * Fe[0];
+        const double qm = (mo[4] - ((U0[0] * mo[1] + U0[1] * mo[2]) + U0[2] * mo[3])) + 0.5 * U20 * mo[0];
+        Fe[4] += p.pr_fix * (qf - U0[0] * qm);
+    }
+    for (int k = 0; k < 5; ++k) F[k] += Fe[k];
     // back to the lab frame
     const double Fm[3] = {F[1], F[2], F[3]};
     for (int d = 0; d < 3; ++d) F[1 + d] = Fm[0] * R[0][d] + Fm[1] * R[1][d] + Fm[2] * R[2][d];
 }
 
 // Second-order flux of the interior faces (the first nif entries of face_order).
+// With local time steps (GKS step) each face is integrated over the smaller
+// step of its cells and stores the mean flux rate F / dt_f.
 __global__ void __launch_bounds__(UGKWP_WAVE_THREADS, UGKWP_WAVE_MIN_BLOCKS) k_face_flux_o2(DevMesh m, DevState s, DevParams p) {
     const int nf = m.nf;
     const double dt = s.dt[0];
     const double inv_Tref = 1.0 / p.T_ref;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.nif; t += gridDim.x * blockDim.x) {
         const int f = m.face_order[t];
+        const int o = m.f_own[f], nb = m.f_nbr[f];
         const double n[3] = {m.f_n[f], m.f_n[nf + f], m.f_n[2 * nf + f]};
+        const double dtf = p.gks == 2 ? fmin(s.dtc[o], s.dtc[nb]) : dt;
         double F[5];
-        interior_flux_o2(m, s, p, f, m.f_own[f], m.f_nbr[f], n, dt, inv_Tref, F);
+        interior_flux_o2(m, s, p, f, o, nb, n, dtf, inv_Tref, F);
+        if (p.gks == 2)
+            for (int q = 0; q < 5; ++q) F[q] = F[q] / dtf;
         for (int q = 0; q < 5; ++q) s.F[(size_t)q * nf + f] = F[q];
     }
 }
@@ -566,10 +591,11 @@ __global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevPar
     const int t = first + blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nf) return;
     const int f = m.face_order[t];  // interior faces first, then boundary faces by type
-    const double dt = s.dt[0];
     const double inv_Tref = 1.0 / p.T_ref;
     const double n[3] = {m.f_n[f], m.f_n[nf + f], m.f_n[2 * nf + f]};
     const int o = m.f_own[f], nb = m.f_nbr[f];
+    // local time steps (GKS step): the smaller step of the face's cells
+    const double dt = p.gks == 2 ? (nb >= 0 ? fmin(s.dtc[o], s.dtc[nb]) : s.dtc[o]) : s.dt[0];
     double WL[5];
     for (int q = 0; q < 5; ++q) WL[q] = s.W[(size_t)q * nc + o];
     const Side L = make_side(WL, s.rhoh[o], n);
@@ -586,7 +612,8 @@ __global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevPar
             time_coeffs(dt, s.tau[o], q1, q4, a4);
             double GL[5], HL[5], Gin[5];
             flux_moments(L.Un, L.Ut, n, L.lam, L.rl, +1, GL, HL);
-            for (int k = 0; k < 5; ++k) Gin[k] = q1 * (L.rho * GL[k]) + a4 * (L.rhoh * GL[k]);
+            const double c4 = p.gks ? q4 : a4;
+            for (int k = 0; k < 5; ++k) Gin[k] = q1 * (L.rho * GL[k]) + c4 * (L.rhoh * GL[k]);
             const double lamw = 1.0 / (2.0 * p.R * bc.T_w);
             const double Uwn = dot3(bc.U_w, n);
             double Uwt[3];
@@ -610,6 +637,8 @@ __global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevPar
             interior_flux(L, R, true, n, dt, p, inv_Tref, F);
         }
     }
+    if (p.gks == 2)
+        for (int q = 0; q < 5; ++q) F[q] = F[q] / dt;
     for (int q = 0; q < 5; ++q) s.F[(size_t)q * nf + f] = F[q];
 }
 

@@ -53,11 +53,12 @@ struct DevBc {
 
 struct DevParams {
     double R, mu_ref, T_ref, omega, CFL, C2;
+    double pr_fix;         // 1/Pr - 1: factor of the equilibrium heat flux added to the energy flux (0: BGK)
     int32_t N_ref, N_min, max_crossings, precision;
     int32_t order;
     int32_t sampling;      // UGKWP_SAMPLE_*
     int32_t averaging;     // add dt W^{n+1} to the time-average sums
-    int32_t pad2_;
+    int32_t gks;           // 0: UGKWP step; 1: GKS step (no particles); 2: GKS step, local time steps
     uint64_t seed;
     int64_t capacity;
     int32_t exps[5];
@@ -132,6 +133,7 @@ struct DevState {
     float* tauf;          // [nc] binary32 rounding of tau (MIXED t_f draw)
     float4* usig;         // [nc] binary32 roundings of U and the sampling spread (MIXED sampling)
     double* sig;          // [nc] sampling spread s sqrt(RT) of energy-matched sampling
+    double* dtc;          // [nc] local time step CFL |Omega| / sum_d Lambda^d (GKS step, local steps)
     double* wsum;         // [5][nc] time-average sums of dt^n W^n
     double* tsum;         // [1] sum of dt^n
     double* rhoh;         // [nc]

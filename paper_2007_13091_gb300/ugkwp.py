@@ -91,7 +91,7 @@ class AdjointReq(ctypes.Structure):
 
 KERNELS = ["reset", "cell_prep", "sample_count", "scan", "scatter", "sample", "track", "flux", "update", "movers", "gradients", "flux_o2"]
 
-EXPORTED = ["ugkwp_average", "ugkwp_average_time", "ugkwp_kn_gll", "ugkwp_adjoint_query", "ugkwp_get_launch_cfg", "ugkwp_set_launch_cfg", "ugkwp_autotune", "ugkwp_batch_create",
+EXPORTED = ["ugkwp_gks_steps", "ugkwp_average", "ugkwp_average_time", "ugkwp_kn_gll", "ugkwp_adjoint_query", "ugkwp_get_launch_cfg", "ugkwp_set_launch_cfg", "ugkwp_autotune", "ugkwp_batch_create",
             "ugkwp_batch_step", "ugkwp_batch_sync", "ugkwp_batch_autotune", "ugkwp_batch_free",
             "ugkwp_time_step_noalloc", "ugkwp_timing_enable", "ugkwp_timing_read", "ugkwp_mesh_load", "ugkwp_mesh_free", "ugkwp_query_sizes", "ugkwp_init", "ugkwp_free", "ugkwp_step",
             "ugkwp_sync", "ugkwp_moments", "ugkwp_state_info", "ugkwp_export_state", "ugkwp_import_state",
@@ -132,6 +132,7 @@ def lib():
             "ugkwp_timing_read": [vp, vp, vp],
             "ugkwp_time_step_noalloc": [vp, vp, vp, i32, ctypes.c_double, ctypes.c_double, vp, vp],
             "ugkwp_get_launch_cfg": [vp, P(LaunchCfg)],
+            "ugkwp_gks_steps": [vp, i32, i32, P(Stats)],
             "ugkwp_average": [vp, i32],
             "ugkwp_average_time": [vp, P(ctypes.c_double)],
             "ugkwp_kn_gll": [vp, vp],
@@ -236,6 +237,13 @@ def ugkwp_free(sim):
 def ugkwp_step(sim, n_steps: int = 1, stats: bool = False):
     st = Stats() if stats else None
     _check(lib().ugkwp_step(sim, int(n_steps), ctypes.byref(st) if st is not None else None))
+    return st.as_dict() if st is not None else None
+
+
+def ugkwp_gks_steps(sim, n_steps: int = 1, local_dt: bool = False, stats: bool = False):
+    st = Stats() if stats else None
+    _check(lib().ugkwp_gks_steps(sim, int(n_steps), 1 if local_dt else 0,
+                                 ctypes.byref(st) if st is not None else None))
     return st.as_dict() if st is not None else None
 
 
@@ -431,6 +439,10 @@ class Simulation:
 
     def step(self, n: int = 1, stats: bool = False):
         return ugkwp_step(self.handle, n, stats)
+
+    def gks_steps(self, n: int = 1, local_dt: bool = False, stats: bool = False):
+        """n start-up steps of the gas-kinetic scheme (no particles)."""
+        return ugkwp_gks_steps(self.handle, n, local_dt, stats)
 
     def sync(self):
         ugkwp_sync(self.handle)

@@ -77,7 +77,8 @@ def test_parameter_validation():
     cfg = wl.uniform_box(n=(2, 2, 2))
     mesh = ugkwp.ugkwp_mesh_load(cfg["mesh"])
     for key, val, pat in (("CFL", 1.5, "CFL"), ("N_ref", 0, "N_ref"), ("order", 3, "order must be"),
-                          ("particle_capacity", 2 ** 31, "capacity"), ("Pr", 0.7, "BGK")):
+                          ("particle_capacity", 2 ** 31, "capacity"), ("Pr", -0.5, "Pr must be"),
+                          ("Pr", float("nan"), "Pr must be")):
         with pytest.raises(ugkwp.UgkwpError, match=pat):
             ugkwp.ugkwp_query_sizes(mesh, dict(cfg["params"], **{key: val}))
     with pytest.raises(ugkwp.UgkwpError, match="sampling"):

@@ -1,5 +1,5 @@
 """Pins of the oracle's gas-kinetic (GKS) start-up step: the method without
-particles (Sec. 4), used for the initial fields of the steady cases (Sec. 5),
+particles (Sec. 3.2), used for the initial fields of the steady cases (Sec. 4.3, 4.4),
 with the global time step or local time steps.
 
 * free-molecular limit (tau -> infinity): the GKS flux is dt times the upwind
