@@ -41,7 +41,7 @@ TRACK_BYTES_PER_CELL = {"mixed": 80 + 8, "fp64": 144 + 8}
 # DRAM bytes (read + write) of one k_track launch on this workload, from the ncu
 # capture summarised in profiles/k_track_k_face_flux_cavity24_mixed.md; set to
 # None whenever the kernel changes until it is captured again
-TRACK_DRAM_BYTES = {"mixed": 962181632 + 979341824, "fp64": None}
+TRACK_DRAM_BYTES = {"mixed": None, "fp64": None}
 # Binary64 flops per interior face of k_face_flux_o2 (the second-order wave flux):
 # ncu's executed dadd + dmul + 2 dfma per launch divided by the interior faces, on
 # this workload (profiles/); None until captured for the current kernel.
@@ -446,7 +446,8 @@ def main():
                   "algorithmic_bytes_per_launch": alg,
                   "bytes_per_move": TRACK_BYTES_PER_MOVE[args.precision],
                   "bytes_per_cell": TRACK_BYTES_PER_CELL[args.precision], "ms_per_launch": track_ms,
-                  "timing": "CUDA events on the library's stream around each k_track launch over "
+                  "timing": "CUDA events on the library's stream around the tracking phase of each step (its "
+                            "two k_track launches: the second starts when the wave flux is done) over "
                             f"{args.steps} further steps of the same run (direct launches, wave flux "
                             "overlapping on the second stream)"}
     roof_flux = None

@@ -41,9 +41,10 @@ struct ugkwp_sim {
     int64_t launches[UGKWP_N_KERNELS] = {};
     std::vector<TimedLaunch> pending;
     std::vector<cudaEvent_t> pool;
-    // the wave flux (binary64-bound) runs beside the particle kernels
-    cudaStream_t wave = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    // the wave flux (binary64-bound) runs beside the particle kernels; the
+    // second half of the tracking grid joins from `aux` once the wave is done
+    cudaStream_t wave = nullptr, aux = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, sampled = nullptr, tracked = nullptr;
     // grid sizes of the looping step kernels
     LaunchCfg lc{0, 0};
     // two-step CUDA graphs, one per ping-pong parity (keyed by buffer A), with
@@ -65,7 +66,10 @@ struct ugkwp_sim {
         for (auto e : pool) cudaEventDestroy(e);
         if (fork) cudaEventDestroy(fork);
         if (join) cudaEventDestroy(join);
+        if (sampled) cudaEventDestroy(sampled);
+        if (tracked) cudaEventDestroy(tracked);
         if (wave) cudaStreamDestroy(wave);
+        if (aux) cudaStreamDestroy(aux);
     }
 };
 
@@ -556,6 +560,9 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s->wave, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s->sampled, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s->tracked, cudaEventDisableTiming);
     if (ce != cudaSuccess) {
         delete s;
         return cuda_fail(ce, "ugkwp_init upload");
@@ -657,10 +664,25 @@ int enqueue_step(ugkwp_sim* s) {
             if (matched) launch_sample_scale(s->M, s->S, s->P, q);
             launch_sample_write(s->M, s->S, s->P, s->A, s->lc.particle_blocks, q);
         });
-        timed(s, UGKWP_K_TRACK, 1, q,
-              [&] { launch_track(s->M, s->S, s->P, s->A, s->B, s->Mv, s->lc.particle_blocks, q); });
+        // tracking in two launches that take tiles from one counter: the first
+        // half of the grid starts now and leaves room on each SM for a block
+        // of the wave flux; the second half starts once the wave flux is done
+        // and takes the tiles that are left
+        cudaError_t ce = cudaSuccess;
+        const int first_half = (s->lc.particle_blocks + 1) / 2;
+        timed(s, UGKWP_K_TRACK, s->lc.particle_blocks > first_half ? 2 : 1, q, [&] {
+            ce = cudaEventRecord(s->sampled, q);
+            launch_track(s->M, s->S, s->P, s->A, s->B, s->Mv, first_half, q);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s->aux, s->sampled, 0);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s->aux, s->join, 0);
+            if (s->lc.particle_blocks > first_half)
+                launch_track(s->M, s->S, s->P, s->A, s->B, s->Mv, s->lc.particle_blocks - first_half, s->aux);
+            if (ce == cudaSuccess) ce = cudaEventRecord(s->tracked, s->aux);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(q, s->tracked, 0);
+        });
+        if (ce != cudaSuccess) return cuda_fail(ce, "tracking launch order");
         timed(s, UGKWP_K_MOVERS, 1, q, [&] { launch_movers(s->M, s->S, s->P, s->Mv, s->lc.particle_blocks, q); });
-        CU(cudaStreamWaitEvent(q, s->join, 0));  // join before the update reads F
+        CU(cudaStreamWaitEvent(q, s->join, 0));  // join before the update reads F (already joined via aux)
         timed(s, UGKWP_K_UPDATE, 1, q, [&] { launch_cell_update(s->M, s->S, s->P, q); });
         std::swap(s->A, s->B);
         std::swap(s->S.nleft, s->S.nleft_next);

@@ -63,6 +63,7 @@ __global__ void k_reset(DevMesh m, DevState s) {
         s.cnt64[CNT_TRACKED] = 0;
         s.cnt64[CNT_DT_BITS] = 0x7ff0000000000000LL;  // +inf
         s.cnt64[CNT_MOVERS] = 0;
+        s.cnt64[CNT_TILE] = 0;
     }
 }
 

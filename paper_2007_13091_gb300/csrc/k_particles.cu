@@ -9,6 +9,7 @@
 //                   listed for k_movers), removal; the survivors are written
 //                   compacted into the other buffer (block-level slot
 //                   reservation), where the next step's samples follow them.
+//                   Blocks take 128-particle tiles from a global counter.
 #include "dmath.cuh"
 #include "ugkwp_internal.hpp"
 
@@ -334,13 +335,18 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
     const Real dtR = (Real)dt;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ int sh_cnt[8], sh_scnt[8];
-    __shared__ long long sh_base, sh_sbase;
+    __shared__ long long sh_base, sh_sbase, sh_tile;
     __shared__ unsigned long long sh_red[8][8];
     // per-thread counters, reduced once per block at the end
     unsigned c_valid = 0, c_coll = 0, c_exit = 0, c_lost = 0, c_cross = 0, c_wall = 0;
-    const long long bstride = (long long)gridDim.x * blockDim.x;
-    // block-uniform loop: every warp of the block runs the same iterations
-    for (long long bb = (long long)blockIdx.x * blockDim.x; bb < n; bb += bstride) {
+    // tiles of blockDim.x particles are taken from a global counter, so that
+    // blocks that start late (or walk short paths) take fewer tiles
+    if (threadIdx.x == 0)
+        sh_tile = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_TILE]), 1ULL) * blockDim.x;
+    __syncthreads();
+    for (;;) {
+        const long long bb = sh_tile;  // block-uniform
+        if (bb >= n) break;
         const long long i = bb + threadIdx.x;
         const bool valid = i < n;
         int status = 0, ncross = 0, nrefl = 0, nwall = 0;
@@ -528,6 +534,8 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
             sh_sbase = stot ? (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_ALIVE]),
                                                    (unsigned long long)stot)
                             : 0LL;
+            // the next tile (every thread has read sh_tile before the barrier above)
+            sh_tile = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_TILE]), 1ULL) * blockDim.x;
         }
         __syncthreads();
         if (survivor) {
@@ -552,7 +560,7 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
             mv.cell[j] = c0;
             mv.id[j] = ((unsigned long long)(unsigned)tet << 1) | (exited ? 1ULL : 0ULL);
         }
-        __syncthreads();  // sh_cnt / sh_base are reused next iteration
+        __syncthreads();  // sh_cnt / sh_base / sh_tile are reused next iteration
     }
     // ---- counters: one atomic per block and counter (survivors were counted
     // by their slot reservations)

@@ -38,7 +38,8 @@ enum : int {
     CNT_MOVES = 13,     // particle moves since init (never reset by a step)
     CNT_NSAM = 14,      // particles sampled this step (from the scan)
     CNT_MOVERS = 15,    // particles whose flux contribution is non-zero this step
-    CNT_SLOTS = 16,
+    CNT_TILE = 16,      // next 128-particle tile of the tracking kernel
+    CNT_SLOTS = 17,
 };
 
 struct DevBc {
