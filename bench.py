@@ -38,15 +38,16 @@ UNIT = "particle-moves/s"
 TRACK_BYTES_PER_MOVE = {"mixed": 44 + 44, "fp64": 68 + 68}
 # per cell and step: tracking record (planes + neighbours) and tau
 TRACK_BYTES_PER_CELL = {"mixed": 80 + 8, "fp64": 144 + 8}
-# DRAM bytes (read + write) of one k_track launch on this workload, from the ncu
-# capture summarised in profiles/k_track_k_face_flux_cavity24_mixed.md; set to
-# None whenever the kernel changes until it is captured again
-TRACK_DRAM_BYTES = {"mixed": None, "fp64": None}
+# DRAM bytes (read + write) of the tracking phase of one step (both k_track
+# launches) on this workload, from the ncu capture summarised in
+# profiles/k_track_k_face_flux_o2_cavity24_mixed.md; set to None whenever the
+# kernel changes until it is captured again
+TRACK_DRAM_BYTES = {"mixed": 963521024 + 980432896 + 28160, "fp64": None}
 # Binary64 flops per interior face of k_face_flux_o2 (the second-order wave flux):
 # ncu's executed dadd + dmul + 2 dfma per launch divided by the interior faces, on
 # this workload (profiles/); None until captured for the current kernel.
-FLUX_O2_FLOPS_PER_FACE = (27613440 + 75933568 + 2 * 144109312) / 162432
-FLUX_O2_DRAM_BYTES = 30773760 + 1792
+FLUX_O2_FLOPS_PER_FACE = (28425600 + 76992768 + 2 * 143199872) / 162432
+FLUX_O2_DRAM_BYTES = 30776832 + 0
 # FP64 peak: 2 FP64 FMA lanes per clock per SM (the nominal 1.25 TFLOP/s of this
 # part at 152 SMs and 2.07 GHz), 2 flops per FMA
 FP64_FMA_LANES_PER_SM = 2
@@ -442,7 +443,7 @@ def main():
     roof_track = {"kernel": "k_track (a6-a9, a11: t_f draw, tet walk, fixed-point flux, removal, compaction)", "bound": "hbm",
                   "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                   "peak_kind": f"{peak_kind} HBM copy", "traffic": TRACK_DRAM_BYTES[args.precision],
-                  "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                  "traffic_unit": "bytes per step, both k_track launches (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                   "algorithmic_bytes_per_launch": alg,
                   "bytes_per_move": TRACK_BYTES_PER_MOVE[args.precision],
                   "bytes_per_cell": TRACK_BYTES_PER_CELL[args.precision], "ms_per_launch": track_ms,
