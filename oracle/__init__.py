@@ -73,6 +73,8 @@ def lib():
         L.orc_frozen_value.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, vp, i32, vp]
         L.orc_sample_cell.argtypes = [vp, i32, i64, vp, vp, vp, vp]
         L.orc_sample_cell.restype = i64
+        L.orc_gp_coefficients.argtypes = [vp, i32, vp]
+        L.orc_gp_draw.argtypes = [i32, u64, u64, vp, u64, i64, vp]
         _LIB = L
     return _LIB
 
@@ -92,7 +94,7 @@ def make_bc(b: dict) -> OrcBc:
     return c
 
 
-SAMPLING = {"maxwell": 0, "energy_matched": 1}
+SAMPLING = {"maxwell": 0, "energy_matched": 1, "gp1": 2}
 
 
 def make_params(p: dict) -> OrcParams:
@@ -218,6 +220,14 @@ def face_flux_o2(params, WL, rhohL, gWL, gHL, dxL, WR, rhohR, gWR, gHR, dxR, n, 
                            _ptr(arrs[3]), _ptr(arrs[4]), float(rhohR), _ptr(arrs[5]), _ptr(arrs[6]),
                            _ptr(arrs[7]), _ptr(arrs[8]), float(dt), int(bool(gks)), _ptr(F))
     return F
+
+
+def gp_draw(coef, n, id0=0, step=1, seed=1, precision="fp64"):
+    """n first-order g_p draws X [3, n] for the acceptance polynomial `coef`."""
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    X = np.empty((n, 3))
+    lib().orc_gp_draw(PRECISION[precision], int(seed), int(step), _ptr(c), int(id0), int(n), _ptr(X))
+    return X.T.copy()
 
 
 # ------------------------------------------------------------- simulation
@@ -375,6 +385,14 @@ class OracleSim:
         m = np.empty(n)
         lib().orc_sample_cell(self._h, int(cell), n, _ptr(pid), _ptr(x), _ptr(u), _ptr(m))
         return {"id": pid, "x": x.T.copy(), "u": u.T.copy(), "m": m}
+
+    def gp_coefficients(self, cell):
+        """First-order g_p sampling: the cell's acceptance polynomial and bound
+        [a0, L(3), Qxx, Qyy, Qzz, Qxy, Qxz, Qyz, C(3), M] (after prepare())."""
+        out = np.empty(14)
+        if lib().orc_gp_coefficients(self._h, int(cell), _ptr(out)):
+            raise ValueError("no first-order g_p coefficients (sampling 'gp1' and prepare() needed)")
+        return out
 
     def gradients(self, limited=True):
         """Least-squares gradients of W [5, 3, nc] and rho^h [3, nc] of the current

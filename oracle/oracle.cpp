@@ -45,7 +45,7 @@ static inline uint64_t make_id(uint64_t step, uint64_t cell, uint64_t k) {
 }
 static inline uint64_t id_step(uint64_t id) { return id >> 40; }
 // Random-number purposes (third counter word).
-enum { TAG_TF = 1, TAG_SVEL = 2, TAG_SPOS = 3, TAG_WALL = 4 };
+enum { TAG_TF = 1, TAG_SVEL = 2, TAG_SPOS = 3, TAG_WALL = 4, TAG_GP = 5 };
 
 static inline Ctr4 draw(uint64_t seed, uint64_t a, uint64_t b, uint64_t tag, uint64_t idx) {
     Ctr4 c; c.v[0] = a; c.v[1] = b; c.v[2] = tag; c.v[3] = idx;
@@ -743,6 +743,135 @@ static void face_flux_o2(const Frame& R, const double* WL, double rhohL, const d
     frame_to_lab(R, Ff, F);
 }
 
+// ------------------------------------------------ first-order g_p sampling
+// Option (sampling = 2): the hydrodynamic particles are drawn from the
+// first-order g_p of Sec. 2.2 instead of the Maxwellian.  Reading: at the
+// start of a step the collisional part represents the end of an interval of
+// length dt, whose equilibrium, expanded about the cell's current state and
+// averaged with the weights e^{-(t-t')/tau}/tau, is
+//   g_p = g - c (u.grad g + g_t),  c = tau - dt e^{-dt/tau} / (1 - e^{-dt/tau})
+// (the printed g_p with g0 moved to the end of the interval; c -> tau as
+// tau/dt -> 0, the Chapman-Enskog distribution, and c -> dt/2 as tau/dt -> oo).
+// grad g from the cell's limited least-squares gradient, g_t from
+// W_t = -int u.grad g psi; both as (slope . psi) g.  With u = U + sqrt(RT) X,
+// g_p / rho = N(X) (1 + phi(X)), phi = a0 + L.X + X^T Q X + (C.X)|X|^2, which
+// is drawn by acceptance-rejection with the bound M = 1 + Phi,
+// Phi = |a0| + 5|L| + 25|Q|_F + 125|C| (phi over |X| <= 5); where Phi > 1 the
+// correction is scaled down to Phi = 1 (a limiter on the non-equilibrium part).
+// Coefficients: [a0, L(3), Qxx, Qyy, Qzz, Qxy, Qxz, Qyz, C(3), M].
+static const int GP_NC = 14;
+static const int GP_ATTEMPTS = 64;
+
+static void gp_coefficients(const Prim& s, const double* gW, double tau, double dt, double R, double* out) {
+    const double* U = s.U;
+    const double sig = std::sqrt(R * s.T);
+    // unit-density slopes: <psi psi^T> b_d = (d W / d x_d) / rho
+    double b[3][5];
+    for (int d = 0; d < 3; ++d) {
+        double rhs[5];
+        for (int q = 0; q < 5; ++q) rhs[q] = gW[3 * q + d] / s.rho;
+        micro_slope(U, s.lam, rhs, b[d]);
+    }
+    // W_t / rho = -sum_d <u_d psi (b_d . psi)>, <psi psi^T> B = W_t / rho
+    FrameMom M0 = frame_moments(U, s.lam, 0);
+    double Wt[5], B[5];
+    for (int k = 0; k < 5; ++k) {
+        double acc = 0.0;
+        for (int d = 0; d < 3; ++d) acc += expect(M0, mul(mul(coord(d), lin(b[d])), psi(k)));
+        Wt[k] = -acc;
+    }
+    micro_slope(U, s.lam, Wt, B);
+    // P(u) = sum_d u_d (b_d . psi) + B . psi
+    //      = B0 + v.u + u^T K u + (h/2)|u|^2 + (|u|^2/2)(beta.u)
+    double v[3], K[3][3], beta[3];
+    const double h = B[4];
+    for (int j = 0; j < 3; ++j) {
+        v[j] = B[1 + j] + b[j][0];
+        beta[j] = b[j][4];
+        for (int d = 0; d < 3; ++d) K[d][j] = b[d][1 + j];
+    }
+    const double UU = dot3(U, U), bU = dot3(beta, U);
+    double KU[3];  // (K + K^T) U
+    for (int d = 0; d < 3; ++d) {
+        KU[d] = 0.0;
+        for (int j = 0; j < 3; ++j) KU[d] += (K[d][j] + K[j][d]) * U[j];
+    }
+    double UKU = 0.0;
+    for (int d = 0; d < 3; ++d)
+        for (int j = 0; j < 3; ++j) UKU += U[d] * K[d][j] * U[j];
+    double a0 = B[0] + dot3(v, U) + UKU + 0.5 * h * UU + 0.5 * UU * bU;
+    double L[3], Q[3][3], C[3];
+    for (int d = 0; d < 3; ++d) {
+        L[d] = sig * (v[d] + KU[d] + h * U[d] + 0.5 * UU * beta[d] + bU * U[d]);
+        C[d] = 0.5 * sig * sig * sig * beta[d];
+        for (int j = 0; j < 3; ++j)
+            Q[d][j] = sig * sig * (0.5 * (K[d][j] + K[j][d]) + 0.5 * (U[d] * beta[j] + U[j] * beta[d])
+                                   + (d == j ? 0.5 * h + 0.5 * bU : 0.0));
+    }
+    const double e = exp_d(-(dt / tau));
+    const double c = tau - dt * e / (1.0 - e);
+    double co[13] = {a0, L[0], L[1], L[2], Q[0][0], Q[1][1], Q[2][2], Q[0][1], Q[0][2], Q[1][2], C[0], C[1], C[2]};
+    for (int k = 0; k < 13; ++k) co[k] = -c * co[k];
+    const double nL = std::sqrt(co[1] * co[1] + co[2] * co[2] + co[3] * co[3]);
+    const double nQ = std::sqrt(co[4] * co[4] + co[5] * co[5] + co[6] * co[6]
+                                + 2.0 * (co[7] * co[7] + co[8] * co[8] + co[9] * co[9]));
+    const double nC = std::sqrt(co[10] * co[10] + co[11] * co[11] + co[12] * co[12]);
+    double Phi = std::fabs(co[0]) + 5.0 * nL + 25.0 * nQ + 125.0 * nC;
+    if (Phi > 1.0) {
+        for (int k = 0; k < 13; ++k) co[k] = co[k] / Phi;
+        Phi = 1.0;
+    }
+    for (int k = 0; k < 13; ++k) out[k] = co[k];
+    out[13] = 1.0 + Phi;
+}
+
+// One acceptance-rejection draw of X ~ (1 + phi(X)) N(0, I) / (normalised)
+// for particle `id` of a cell with coefficients c (first-order g_p), in the
+// particle precision: attempt k draws three normals by Box-Muller from
+// Philox counter (id, step, TAG_GP, 2k) and eta from (id, step, TAG_GP,
+// 2k + 1), and accepts if eta M <= 1 + phi(X); after GP_ATTEMPTS attempts the
+// last draw is kept.
+template <class Real>
+static void gp_draw(uint64_t seed, uint64_t step, const double* c, uint64_t id, double Xout[3]) {
+    typedef Real R;
+    const R a0 = (R)c[0], L0 = (R)c[1], L1 = (R)c[2], L2 = (R)c[3];
+    const R Q0 = (R)c[4], Q1 = (R)c[5], Q2 = (R)c[6], Q3 = (R)c[7], Q4 = (R)c[8], Q5 = (R)c[9];
+    const R C0 = (R)c[10], C1 = (R)c[11], C2 = (R)c[12], Mb = (R)c[13];
+    R X[3] = {(R)0, (R)0, (R)0};
+    for (int k = 0; k < GP_ATTEMPTS; ++k) {
+        Ctr4 r = draw(seed, id, step, TAG_GP, (uint64_t)(2 * k));
+        Ctr4 r2 = draw(seed, id, step, TAG_GP, (uint64_t)(2 * k + 1));
+        R eta;
+        if constexpr (std::is_same<Real, float>::value) {
+            float sn, cs;
+            float rad = std::sqrt(-2.0f * log_f(u01_f(r.v[0])));
+            sincos2pi_f(u01_f(r.v[1]), &sn, &cs);
+            X[0] = rad * cs; X[1] = rad * sn;
+            rad = std::sqrt(-2.0f * log_f(u01_f(r.v[2])));
+            sincos2pi_f(u01_f(r.v[3]), &sn, &cs);
+            X[2] = rad * cs;
+            eta = u01_f(r2.v[0]);
+        } else {
+            double sn, cs;
+            double rad = std::sqrt(-2.0 * log_d(u01_d(r.v[0])));
+            sincos2pi_d(u01_d(r.v[1]), &sn, &cs);
+            X[0] = rad * cs; X[1] = rad * sn;
+            rad = std::sqrt(-2.0 * log_d(u01_d(r.v[2])));
+            sincos2pi_d(u01_d(r.v[3]), &sn, &cs);
+            X[2] = rad * cs;
+            eta = u01_d(r2.v[0]);
+        }
+        // phi = a0 + L.X + X^T Q X + (C.X) |X|^2, in this order
+        const R lin = (L0 * X[0] + L1 * X[1]) + L2 * X[2];
+        const R qd = ((Q0 * X[0]) * X[0] + (Q1 * X[1]) * X[1]) + (Q2 * X[2]) * X[2];
+        const R qo = ((Q3 * X[0]) * X[1] + (Q4 * X[0]) * X[2]) + (Q5 * X[1]) * X[2];
+        const R cub = ((C0 * X[0] + C1 * X[1]) + C2 * X[2]) * ((X[0] * X[0] + X[1] * X[1]) + X[2] * X[2]);
+        const R phi = ((a0 + lin) + (qd + (qo + qo))) + cub;
+        if (eta * Mb <= (R)1 + phi) break;
+    }
+    for (int d = 0; d < 3; ++d) Xout[d] = (double)X[d];
+}
+
 // ------------------------------------------------------------ particles
 template <class Real> struct Part { uint64_t id; int32_t cell; Real x[3]; Real u[3]; double m; };
 
@@ -904,6 +1033,7 @@ struct SimBase {
     virtual int do_step(std::string& err) = 0;
     virtual int prepare(std::string& err) = 0;
     virtual int64_t sample_one_cell(int cell, int64_t cap, uint64_t* id, double* x, double* u, double* m) const = 0;
+    virtual bool gp_coef(int cell, double* out) const = 0;
     virtual void get_particles(uint64_t*, int32_t*, double*, double*, double*) const = 0;
     virtual bool set_particles(int64_t, const uint64_t*, const int32_t*, const double*, const double*,
                                const double*, std::string&) = 0;
@@ -1019,6 +1149,9 @@ template <class Real> struct Sim : SimBase {
     std::vector<Prim> pr;
     std::vector<double> rho_p;
     std::vector<int64_t> nleft;
+    // first-order g_p sampling: per cell the polynomial phi(X) of the
+    // acceptance weight 1 + phi and its bound (GP_NC values, see gp_coefficients)
+    std::vector<double> gpc;
 
     // a1 + a2 + sampling counts for the current state; no state change.
     int prepare(std::string& err) override {
@@ -1074,7 +1207,17 @@ template <class Real> struct Sim : SimBase {
             nsam[i] = ns;
             msam[i] = Mhp / (double)ns;
         }
+        if (p.sampling == 2) {
+            std::vector<double> gW, gH;
+            limited_gradients(g, p, W, rhoh, true, gW, gH);
+            gpc.assign(GP_NC * (size_t)nc, 0.0);
+            for (int i = 0; i < nc; ++i) gp_coefficients(pr[i], &gW[15 * (size_t)i], tau[i], dt, P.R, &gpc[GP_NC * (size_t)i]);
+        }
         return 0;
+    }
+
+    void gp_normals(const double* c, uint64_t id, double Xout[3]) const {
+        gp_draw<Real>(P.seed, (uint64_t)step, c, id, Xout);
     }
 
     // The three normals X of the pair whose first member has id `ida`, by
@@ -1149,7 +1292,14 @@ template <class Real> struct Sim : SimBase {
                     pt.id = ida + (uint64_t)side;
                     pt.cell = i;
                     pt.m = ms;
-                    for (int c = 0; c < 3; ++c) pt.u[c] = side == 0 ? Uf[c] + sigf * X[c] : Uf[c] - sigf * X[c];
+                    if (p.sampling == 2) {
+                        // first-order g_p: every particle drawn on its own
+                        double Xg[3];
+                        gp_normals(&gpc[GP_NC * (size_t)i], pt.id, Xg);
+                        for (int c = 0; c < 3; ++c) pt.u[c] = Uf[c] + sigf * (float)Xg[c];
+                    } else {
+                        for (int c = 0; c < 3; ++c) pt.u[c] = side == 0 ? Uf[c] + sigf * X[c] : Uf[c] - sigf * X[c];
+                    }
                     Ctr4 rp = draw(p.seed, pt.id, (uint64_t)step, TAG_SPOS, 0);
                     float a = u01_f(rp.v[0]), b = u01_f(rp.v[1]), cc = u01_f(rp.v[2]);
                     if (a + b > 1.0f) { a = 1.0f - a; b = 1.0f - b; }
@@ -1176,8 +1326,14 @@ template <class Real> struct Sim : SimBase {
                     pt.id = ida + (uint64_t)side;
                     pt.cell = i;
                     pt.m = ms;
-                    for (int c = 0; c < 3; ++c)
-                        pt.u[c] = (Real)(side == 0 ? pr[i].U[c] + sig * X[c] : pr[i].U[c] - sig * X[c]);
+                    if (p.sampling == 2) {
+                        double Xg[3];
+                        gp_normals(&gpc[GP_NC * (size_t)i], pt.id, Xg);
+                        for (int c = 0; c < 3; ++c) pt.u[c] = (Real)(pr[i].U[c] + sig * Xg[c]);
+                    } else {
+                        for (int c = 0; c < 3; ++c)
+                            pt.u[c] = (Real)(side == 0 ? pr[i].U[c] + sig * X[c] : pr[i].U[c] - sig * X[c]);
+                    }
                     // Uniform point in the tet: cube -> prism -> tet folding
                     // (Rocchini and Cignoni, J. Graphics Tools 5(4), 2000).
                     Ctr4 rp = draw(p.seed, pt.id, (uint64_t)step, TAG_SPOS, 0);
@@ -1268,6 +1424,12 @@ template <class Real> struct Sim : SimBase {
         if (overflow) { err = "fixed-point overflow"; return -8; }
         if (nlost) { err = std::to_string(nlost) + " particles exceeded max_crossings"; return -7; }
         return 0;
+    }
+
+    bool gp_coef(int cell, double* out) const override {
+        if (gpc.size() != GP_NC * (size_t)g.nc) return false;
+        for (int k = 0; k < GP_NC; ++k) out[k] = gpc[GP_NC * (size_t)cell + k];
+        return true;
     }
 
     int64_t sample_one_cell(int cell, int64_t cap, uint64_t* id, double* x, double* u, double* m) const override {
@@ -1682,6 +1844,11 @@ orc_sim* orc_create(const orc_params* p, int32_t n_nodes, const double* xyz,
     std::string e;
     if (p->order != 1 && p->order != 2) { set_err(err, errlen, "order must be 1 or 2"); return nullptr; }
     if (p->n_bc < 0 || p->n_bc > 16) { set_err(err, errlen, "n_bc out of range"); return nullptr; }
+    if (p->sampling < 0 || p->sampling > 2) { set_err(err, errlen, "unknown sampling mode"); return nullptr; }
+    if (p->sampling == 2 && p->order != 2) {
+        set_err(err, errlen, "first-order g_p sampling needs order 2 (the cell slopes)");
+        return nullptr;
+    }
     if (n_tets >= (1 << 24)) { set_err(err, errlen, "too many tets for the particle id layout"); return nullptr; }
     SimBase* s = nullptr;
     if (p->precision == ORC_MIXED) s = new Sim<float>(); else s = new Sim<double>();
@@ -1820,6 +1987,19 @@ int orc_prepare(orc_sim* h, char* err, int32_t errlen) {
 int64_t orc_sample_cell(const orc_sim* h, int32_t cell, int64_t cap, uint64_t* id, double* x, double* u, double* m) {
     if (cell < 0 || cell >= h->s->g.nc) return -1;
     return h->s->sample_one_cell(cell, cap, id, x, u, m);
+}
+
+void orc_gp_draw(int32_t precision, uint64_t seed, uint64_t step, const double coef[14], uint64_t id0, int64_t n,
+                 double* X) {
+    for (int64_t k = 0; k < n; ++k) {
+        if (precision == ORC_MIXED) gp_draw<float>(seed, step, coef, id0 + (uint64_t)k, &X[3 * k]);
+        else gp_draw<double>(seed, step, coef, id0 + (uint64_t)k, &X[3 * k]);
+    }
+}
+
+int orc_gp_coefficients(const orc_sim* h, int32_t cell, double out[14]) {
+    if (cell < 0 || cell >= h->s->g.nc) return -1;
+    return h->s->gp_coef(cell, out) ? 0 : -1;
 }
 
 int orc_track_one(const orc_sim* h, uint64_t id, int32_t cell, double* io_x, double* io_u,

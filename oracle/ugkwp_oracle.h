@@ -37,7 +37,9 @@ typedef struct {
     int32_t order, N_ref, N_min, precision, max_crossings, n_bc;
     int32_t sampling;  /* 0: pairs U +/- sqrt(RT) X as printed; 1: the same pairs with X
                         * scaled per cell so that their thermal energy is exactly
-                        * rho^hp |Omega| (3/2) R T (energy-matched sampling) */
+                        * rho^hp |Omega| (3/2) R T (energy-matched sampling); 2: every
+                        * particle drawn on its own from the first-order g_p
+                        * (acceptance-rejection; order 2 only) */
     int32_t pad2_;
     uint64_t seed;
     orc_bc bc[16];
@@ -109,6 +111,16 @@ int orc_prepare(orc_sim* s, char* err, int32_t errlen);
 /* The particles cell `cell` samples at the current step (after orc_prepare):
  * returns their number n and fills up to cap of them (x, u as [k][3]). */
 int64_t orc_sample_cell(const orc_sim* s, int32_t cell, int64_t cap, uint64_t* id, double* x, double* u, double* m);
+/* First-order g_p sampling (sampling = 2), after orc_prepare: the cell's
+ * acceptance polynomial phi(X) = a0 + L.X + X^T Q X + (C.X)|X|^2 of X = (u - U)
+ * / sqrt(RT) and its bound: [a0, L(3), Qxx, Qyy, Qzz, Qxy, Qxz, Qyz, C(3), M].
+ * -1 if the state has none. */
+int orc_gp_coefficients(const orc_sim* s, int32_t cell, double out[14]);
+/* n acceptance-rejection draws X[n][3] of first-order g_p for the given
+ * coefficients, particle ids id0 .. id0 + n - 1 at `step`, in the particle
+ * precision (ORC_FP64 / ORC_MIXED). */
+void orc_gp_draw(int32_t precision, uint64_t seed, uint64_t step, const double coef[14], uint64_t id0, int64_t n,
+                 double* X);
 
 /* Second-order pieces (order 2).  Gradients of the current state [5][3][nc]
  * and [3][nc] (limited or not).  Slope moment int u_n u_d (a.psi) psi g du of
