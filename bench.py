@@ -11,6 +11,9 @@ int64 fixed-point particle flux).  A step is one full UGKWP time step.
   field_error MIXED vs FP64 after a fixed number of steps, with the Monte-Carlo
              noise floor (two FP64 runs with different seeds)
   e2e        per step: state import from host buffers, step, W back to host
+  batched    64 independent instances in one graph, MIXED and FP64
+  adjoint    the frozen-particle wave adjoint on a channel
+  gks_start_up the particle-free start-up steps, global and local time steps
   cpu_baseline the CPU oracle (single thread) on a bounded sample
 
 Multi-GPU: replicas only (each rank runs its own simulation; value = all
@@ -344,6 +347,36 @@ def adjoint(device, K=10):
             "cell_steps_per_s": n * K / (t1 - t0)}
 
 
+def gks_start_up(device, steps=20, warmup=3):
+    """Start-up steps of the gas-kinetic scheme (the method without particles,
+    Sec. 3.2; the initial fields of the steady cases, Sec. 4.3, 4.4) on the
+    cavity 24^3 at second order with the Prandtl fix at Pr = 2/3: cell-steps/s
+    with the global time step and with local time steps, CUDA events on the
+    simulation's stream around `steps` direct-launch steps."""
+    import torch
+    from paper_2007_13091_gb300 import ugkwp
+    from paper_2007_13091_gb300 import workloads as wl
+    cfg = wl.cavity(n=24, Kn=0.075, N_ref=100, precision="mixed", order=2)
+    cfg["params"]["Pr"] = 2.0 / 3.0
+    stream = torch.cuda.Stream(device=device)
+    sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=stream)
+    n = sim.n_cells
+    out = {"workload": "cavity 24^3 hexes x 6 = 82,944 tets, Kn 0.075, order 2, Pr 2/3, no particles", "n_cells": n}
+    for local in (False, True):
+        sim.gks_steps(warmup, local_dt=local)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.gks_steps(steps, local_dt=local)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        out["local_dt" if local else "global_dt"] = {"ms_per_step": ms / steps,
+                                                      "cell_steps_per_s": n * steps / (ms * 1e-3)}
+    sim.sync()
+    sim.close()
+    return out
+
+
 def cpu_baseline(steps):
     """The CPU oracle (single thread) on the same workload: one untimed step
     samples the particle population, then `steps` timed steps."""
@@ -515,6 +548,7 @@ def main():
             return r
         out["batched"] = guarded(both)
         out["adjoint"] = guarded(lambda: adjoint(device))
+        out["gks_start_up"] = guarded(lambda: gks_start_up(device))
         out["cpu_baseline"] = cpu_baseline(args.cpu_steps)
     elif rank == 0:
         out["e2e"] = None

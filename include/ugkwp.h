@@ -72,7 +72,7 @@ enum {
  * mass, fluxes (fixed point), relaxation times and all cell/face arithmetic
  * stay binary64. */
 enum { UGKWP_FP64 = 0, UGKWP_MIXED = 1 };
-enum { UGKWP_SAMPLE_MAXWELL = 0, UGKWP_SAMPLE_ENERGY_MATCHED = 1 };
+enum { UGKWP_SAMPLE_MAXWELL = 0, UGKWP_SAMPLE_ENERGY_MATCHED = 1, UGKWP_SAMPLE_GP1 = 2 };
 
 /* Which quantity ugkwp_moments returns (all [5][n_cells] unless stated). */
 enum {
@@ -135,7 +135,11 @@ typedef struct {
     int32_t sampling;            /* UGKWP_SAMPLE_MAXWELL: pairs U +/- sqrt(RT) X (Sec. 2.4 (b));
                                   * UGKWP_SAMPLE_ENERGY_MATCHED: the same pairs with X scaled per
                                   * cell so that their thermal energy is exactly
-                                  * rho^hp |Omega| (3/2) R T (a variance reduction) */
+                                  * rho^hp |Omega| (3/2) R T (a variance reduction);
+                                  * UGKWP_SAMPLE_GP1: every particle drawn on its own from the
+                                  * first-order g_p of Sec. 2.2, g - c (u.grad g + g_t) with
+                                  * c = tau - dt e^{-dt/tau}/(1 - e^{-dt/tau}), by
+                                  * acceptance-rejection (order 2 only: the cell slopes) */
     int32_t reserved_;           /* must be 0 */
     uint64_t seed;               /* Philox4x64-10 key word 0 */
     int64_t particle_capacity;   /* particles the device buffers hold (< 2^31) */

@@ -44,7 +44,7 @@ struct ugkwp_sim {
     // the wave flux (binary64-bound) runs beside the particle kernels; the
     // second half of the tracking grid joins from `aux` once the wave is done
     cudaStream_t wave = nullptr, aux = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr, sampled = nullptr, tracked = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, sampled = nullptr, tracked = nullptr, gp_ready = nullptr;
     // grid sizes of the looping step kernels
     LaunchCfg lc{0, 0};
     // two-step CUDA graphs, one per ping-pong parity (keyed by buffer A), with
@@ -68,6 +68,7 @@ struct ugkwp_sim {
         if (join) cudaEventDestroy(join);
         if (sampled) cudaEventDestroy(sampled);
         if (tracked) cudaEventDestroy(tracked);
+        if (gp_ready) cudaEventDestroy(gp_ready);
         if (wave) cudaStreamDestroy(wave);
         if (aux) cudaStreamDestroy(aux);
     }
@@ -148,6 +149,7 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, D
     S.usig = c.take<float4>(nc);
     S.sig = c.take<double>(nc);
     S.dtc = c.take<double>(nc);
+    S.gpc = c.take<double>((size_t)GP_NC * nc);
     S.wsum = c.take<double>(5 * nc);
     S.tsum = c.take<double>(1);
     S.rhoh = c.take<double>(nc);
@@ -191,8 +193,11 @@ int check_params(const ugkwp_params* p, const MeshHost* mh) {
     if (p->N_ref <= 0 || p->N_min < 0) return fail(UGKWP_E_ARG, "N_ref must be > 0 and N_min >= 0");
     if (p->precision != UGKWP_FP64 && p->precision != UGKWP_MIXED) return fail(UGKWP_E_ARG, "unknown precision");
     if (p->max_crossings <= 0) return fail(UGKWP_E_ARG, "max_crossings must be > 0");
-    if (p->sampling != UGKWP_SAMPLE_MAXWELL && p->sampling != UGKWP_SAMPLE_ENERGY_MATCHED)
+    if (p->sampling != UGKWP_SAMPLE_MAXWELL && p->sampling != UGKWP_SAMPLE_ENERGY_MATCHED &&
+        p->sampling != UGKWP_SAMPLE_GP1)
         return fail(UGKWP_E_ARG, "unknown sampling mode");
+    if (p->sampling == UGKWP_SAMPLE_GP1 && p->order != 2)
+        return fail(UGKWP_E_ARG, "first-order g_p sampling needs order 2 (the cell slopes)");
     if (p->particle_capacity < 0 || p->particle_capacity >= ((int64_t)1 << 31))
         return fail(UGKWP_E_ARG, "particle_capacity must be in [0, 2^31)");
     if (p->n_bc < 0 || p->n_bc > 16) return fail(UGKWP_E_ARG, "n_bc must be in [0, 16]");
@@ -563,6 +568,7 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s->sampled, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s->tracked, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s->gp_ready, cudaEventDisableTiming);
     if (ce != cudaSuccess) {
         delete s;
         return cuda_fail(ce, "ugkwp_init upload");
@@ -650,8 +656,14 @@ int enqueue_step(ugkwp_sim* s) {
         // writes only F, which no particle kernel touches
         CU(cudaEventRecord(s->fork, q));
         CU(cudaStreamWaitEvent(s->wave, s->fork, 0));
+        const bool gp = s->P.sampling == UGKWP_SAMPLE_GP1;
         if (s->P.order == 2)
-            timed(s, UGKWP_K_GRADIENTS, 1, s->wave, [&] { launch_gradients(s->M, s->S, s->P, s->lc.wave_blocks, s->wave); });
+            timed(s, UGKWP_K_GRADIENTS, gp ? 2 : 1, s->wave, [&] {
+                launch_gradients(s->M, s->S, s->P, s->lc.wave_blocks, s->wave);
+                // first-order g_p sampling needs the cell slopes
+                if (gp) launch_gp_coef(s->M, s->S, s->P, s->wave);
+            });
+        if (gp) CU(cudaEventRecord(s->gp_ready, s->wave));
         if (s->P.order == 2 && s->M.nif > 0)
             timed(s, UGKWP_K_FLUX_O2, 1, s->wave, [&] { launch_face_flux_o2(s->M, s->S, s->P, s->lc.wave_blocks, s->wave); });
         const int first = s->P.order == 2 ? s->M.nif : 0;
@@ -659,6 +671,7 @@ int enqueue_step(ugkwp_sim* s) {
             timed(s, UGKWP_K_FLUX, 1, s->wave, [&] { launch_face_flux(s->M, s->S, s->P, first, s->wave); });
         CU(cudaEventRecord(s->join, s->wave));
         timed(s, UGKWP_K_SCAN, 2, q, [&] { launch_scan(s->M, s->S, s->P, q); });
+        if (gp) CU(cudaStreamWaitEvent(q, s->gp_ready, 0));  // the sampler reads the g_p coefficients
         const bool matched = s->P.sampling == UGKWP_SAMPLE_ENERGY_MATCHED;
         timed(s, UGKWP_K_SAMPLE, matched ? 2 : 1, q, [&] {
             if (matched) launch_sample_scale(s->M, s->S, s->P, q);

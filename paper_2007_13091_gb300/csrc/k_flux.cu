@@ -565,6 +565,87 @@ __device__ void interior_flux_o2(const DevMesh& m, const DevState& s, const DevP
     for (int d = 0; d < 3; ++d) F[1 + d] = Fm[0] * R[0][d] + Fm[1] * R[1][d] + Fm[2] * R[2][d];
 }
 
+// First-order g_p sampling (Sec. 2.2), per cell: g_p = g - c (u.grad g + g_t),
+// c = tau - dt e^{-dt/tau}/(1 - e^{-dt/tau}), with grad g from the limited
+// gradient and g_t from W_t = -sum_d dF_d/dx_d; as a polynomial phi of
+// X = (u - U)/sqrt(RT) in g_p = rho N(X)(1 + phi), bounded over |X| <= 5 and
+// scaled down where that bound Phi exceeds 1; stores GP_NC values per cell.
+__global__ void __launch_bounds__(128) k_gp_coef(DevMesh m, DevState s, DevParams p) {
+    const int nc = m.nc;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const double rho = s.prim[i];
+    const double U[3] = {s.prim[nc + i], s.prim[2 * nc + i], s.prim[3 * nc + i]};
+    const double th = p.R * s.prim[4 * nc + i];
+    const double lam = 0.5 / th;
+    const double sig = sqrt(th);
+    const double U2 = dot3(U, U);
+    const double ir = 1.0 / rho;
+    double bd[3][5], a[3][5], Wt[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, t5[5];
+    for (int d = 0; d < 3; ++d)
+        for (int q = 0; q < 5; ++q) bd[d][q] = s.gradW[(size_t)(3 * q + d) * nc + i] * ir;
+    {
+        const DPrim q = dprim(U, th, U2, bd[0]);
+        euler_jac<0>(U, th, U2, bd[0], q, t5);
+        for (int k = 0; k < 5; ++k) Wt[k] -= t5[k];
+    }
+    {
+        const DPrim q = dprim(U, th, U2, bd[1]);
+        euler_jac<1>(U, th, U2, bd[1], q, t5);
+        for (int k = 0; k < 5; ++k) Wt[k] -= t5[k];
+    }
+    {
+        const DPrim q = dprim(U, th, U2, bd[2]);
+        euler_jac<2>(U, th, U2, bd[2], q, t5);
+        for (int k = 0; k < 5; ++k) Wt[k] -= t5[k];
+    }
+    double B[5];
+    for (int d = 0; d < 3; ++d) micro(U, lam, th, bd[d], a[d]);
+    micro(U, lam, th, Wt, B);
+    // P(u) = B0 + v.u + u^T K u + (h/2)|u|^2 + (|u|^2/2)(beta.u), K[d][j] = a_d,1+j
+    double v[3], beta[3];
+    const double h = B[4];
+    for (int j = 0; j < 3; ++j) {
+        v[j] = B[1 + j] + a[j][0];
+        beta[j] = a[j][4];
+    }
+    const double bU = dot3(beta, U);
+    double KU[3], UKU = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        KU[d] = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            KU[d] += (a[d][1 + j] + a[j][1 + d]) * U[j];
+            UKU += U[d] * a[d][1 + j] * U[j];
+        }
+    }
+    double co[13];
+    co[0] = B[0] + dot3(v, U) + UKU + 0.5 * h * U2 + 0.5 * U2 * bU;
+    for (int d = 0; d < 3; ++d) {
+        co[1 + d] = sig * (v[d] + KU[d] + h * U[d] + 0.5 * U2 * beta[d] + bU * U[d]);
+        co[10 + d] = 0.5 * sig * sig * sig * beta[d];
+    }
+    const int qi[6] = {0, 1, 2, 0, 0, 1}, qj[6] = {0, 1, 2, 1, 2, 2};
+    for (int k = 0; k < 6; ++k) {
+        const int d = qi[k], j = qj[k];
+        co[4 + k] = sig * sig * (0.5 * (a[d][1 + j] + a[j][1 + d]) + 0.5 * (U[d] * beta[j] + U[j] * beta[d]) +
+                                 (d == j ? 0.5 * h + 0.5 * bU : 0.0));
+    }
+    const double dt = s.dt[0];
+    const double e = exp(-(dt / s.tau[i]));
+    const double c = s.tau[i] - dt * e / (1.0 - e);
+    for (int k = 0; k < 13; ++k) co[k] = -c * co[k];
+    const double nL = sqrt(co[1] * co[1] + co[2] * co[2] + co[3] * co[3]);
+    const double nQ = sqrt(co[4] * co[4] + co[5] * co[5] + co[6] * co[6] + 2.0 * (co[7] * co[7] + co[8] * co[8] + co[9] * co[9]));
+    const double nC = sqrt(co[10] * co[10] + co[11] * co[11] + co[12] * co[12]);
+    double Phi = fabs(co[0]) + 5.0 * nL + 25.0 * nQ + 125.0 * nC;
+    if (Phi > 1.0) {
+        for (int k = 0; k < 13; ++k) co[k] = co[k] / Phi;
+        Phi = 1.0;
+    }
+    for (int k = 0; k < 13; ++k) s.gpc[(size_t)k * nc + i] = co[k];
+    s.gpc[(size_t)13 * nc + i] = 1.0 + Phi;
+}
+
 // Second-order flux of the interior faces (the first nif entries of face_order).
 // With local time steps (GKS step) each face is integrated over the smaller
 // step of its cells and stores the mean flux rate F / dt_f.
@@ -651,6 +732,10 @@ static int wave_grid(int n, int blocks) {
 
 void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, int blocks, cudaStream_t st) {
     k_gradients<<<wave_grid(m.nc, blocks), UGKWP_WAVE_THREADS, 0, st>>>(m, s, p);
+}
+
+void launch_gp_coef(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
+    k_gp_coef<<<(m.nc + 127) / 128, 128, 0, st>>>(m, s, p);
 }
 
 void launch_face_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p, int blocks, cudaStream_t st) {

@@ -27,7 +27,7 @@ constexpr unsigned FULL = 0xffffffffu;
 #ifndef UGKWP_TRACK_MIN_BLOCKS
 #define UGKWP_TRACK_MIN_BLOCKS (1024 / UGKWP_TRACK_THREADS)
 #endif
-enum : unsigned long long { TAG_TF = 1, TAG_SVEL = 2, TAG_SPOS = 3, TAG_WALL = 4 };
+enum : unsigned long long { TAG_TF = 1, TAG_SVEL = 2, TAG_SPOS = 3, TAG_WALL = 4, TAG_GP = 5 };
 
 __device__ __forceinline__ void set_err(const DevState& s, int32_t bits) {
     atomicOr(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_ERR]), (unsigned long long)bits);
@@ -73,6 +73,53 @@ __device__ __forceinline__ void pair_normals(unsigned long long ida, long long s
         rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.c)));
         dm::d_sincos2pi(dm::u01d(r.d), &sn, &cs);
         X[2] = rad * cs;
+    }
+}
+
+// First-order g_p sampling: X ~ N(0, I) (1 + phi(X)) for particle `id` by
+// acceptance-rejection in the particle precision: attempt k draws three normals
+// by Box-Muller from Philox counter (id, step, TAG_GP, 2k) and eta from
+// (id, step, TAG_GP, 2k + 1); accepted if eta M <= 1 + phi(X), the last draw
+// kept after GP_ATTEMPTS attempts.  Coefficients: the cell's GP_NC values.
+template <class Real>
+__device__ __forceinline__ void gp_normals(const double* gpc, int nc, int cell, unsigned long long id, long long step,
+                                           unsigned long long seed, Real X[3]) {
+    Real c[GP_NC];
+#pragma unroll
+    for (int k = 0; k < GP_NC; ++k) c[k] = (Real)gpc[(size_t)k * nc + cell];
+    X[0] = X[1] = X[2] = (Real)0;
+    for (int k = 0; k < GP_ATTEMPTS; ++k) {
+        const dm::U4 r = dm::philox(id, (unsigned long long)step, TAG_GP, (unsigned long long)(2 * k), seed, 0ULL);
+        const dm::U4 r2 = dm::philox(id, (unsigned long long)step, TAG_GP, (unsigned long long)(2 * k + 1), seed, 0ULL);
+        Real eta;
+        if constexpr (sizeof(Real) == 4) {
+            float sn, cs;
+            float rad = sqrtf(-2.0f * dm::f_log(dm::u01f(r.a)));
+            dm::f_sincos2pi(dm::u01f(r.b), &sn, &cs);
+            X[0] = rad * cs;
+            X[1] = rad * sn;
+            rad = sqrtf(-2.0f * dm::f_log(dm::u01f(r.c)));
+            dm::f_sincos2pi(dm::u01f(r.d), &sn, &cs);
+            X[2] = rad * cs;
+            eta = dm::u01f(r2.a);
+        } else {
+            double sn, cs;
+            double rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.a)));
+            dm::d_sincos2pi(dm::u01d(r.b), &sn, &cs);
+            X[0] = rad * cs;
+            X[1] = rad * sn;
+            rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.c)));
+            dm::d_sincos2pi(dm::u01d(r.d), &sn, &cs);
+            X[2] = rad * cs;
+            eta = dm::u01d(r2.a);
+        }
+        // phi = a0 + L.X + X^T Q X + (C.X) |X|^2, in this order
+        const Real lin = (c[1] * X[0] + c[2] * X[1]) + c[3] * X[2];
+        const Real qd = ((c[4] * X[0]) * X[0] + (c[5] * X[1]) * X[1]) + (c[6] * X[2]) * X[2];
+        const Real qo = ((c[7] * X[0]) * X[1] + (c[8] * X[0]) * X[2]) + (c[9] * X[1]) * X[2];
+        const Real cub = ((c[10] * X[0] + c[11] * X[1]) + c[12] * X[2]) * ((X[0] * X[0] + X[1] * X[1]) + X[2] * X[2]);
+        const Real phi = ((c[0] + lin) + (qd + (qo + qo))) + cub;
+        if (eta * c[13] <= (Real)1 + phi) break;
     }
 }
 
@@ -127,9 +174,11 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
             // vertex and edges rounded to binary32
             const float4 us = s.usig[cell];
             const unsigned long long ida = make_id(step, cell, k - side);
-            float X[3];
-            pair_normals<float>(ida, step, p.seed, X);
             const unsigned long long id = ida + (unsigned long long)side;
+            const bool gp = p.sampling == UGKWP_SAMPLE_GP1;
+            float X[3];
+            if (gp) gp_normals<float>(s.gpc, nc, cell, id, step, p.seed, X);  // every particle on its own
+            else pair_normals<float>(ida, step, p.seed, X);
             const dm::U4 rp = dm::philox(id, (unsigned long long)step, TAG_SPOS, 0ULL, p.seed, 0ULL);
             float a = dm::u01f(rp.a), bb = dm::u01f(rp.b), cc = dm::u01f(rp.c);
             if (a + bb > 1.0f) { a = 1.0f - a; bb = 1.0f - bb; }
@@ -150,7 +199,7 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
                 const float E2 = m.vtx_f[(size_t)(6 + c) * nc + cell];
                 const float E3 = m.vtx_f[(size_t)(9 + c) * nc + cell];
                 b.x[c][j] = P0 + ((a * E1 + bb * E2) + cc * E3);
-                b.u[c][j] = side == 0 ? U[c] + us.w * X[c] : U[c] - us.w * X[c];
+                b.u[c][j] = (gp || side == 0) ? U[c] + us.w * X[c] : U[c] - us.w * X[c];
             }
             b.m[j] = s.msam[cell];
             b.cell[j] = cell;
@@ -160,9 +209,11 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
         const double U[3] = {s.prim[nc + cell], s.prim[2 * nc + cell], s.prim[3 * nc + cell]};
         const double sig = p.sampling == UGKWP_SAMPLE_ENERGY_MATCHED ? s.sig[cell] : sqrt(p.R * s.prim[4 * nc + cell]);
         const unsigned long long ida = make_id(step, cell, k - side);
-        double X[3];
-        pair_normals<double>(ida, step, p.seed, X);
         const unsigned long long id = ida + (unsigned long long)side;
+        const bool gp = p.sampling == UGKWP_SAMPLE_GP1;
+        double X[3];
+        if (gp) gp_normals<double>(s.gpc, nc, cell, id, step, p.seed, X);
+        else pair_normals<double>(ida, step, p.seed, X);
         const dm::U4 rp = dm::philox(id, (unsigned long long)step, TAG_SPOS, 0ULL, p.seed, 0ULL);
         double a = dm::u01d(rp.a), bb = dm::u01d(rp.b), cc = dm::u01d(rp.c);
         // cube -> prism -> tet folding of a uniform point (Rocchini & Cignoni 2000)
@@ -183,7 +234,7 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
             const double E2 = m.vtx[(size_t)(6 + c) * nc + cell] - P0;
             const double E3 = m.vtx[(size_t)(9 + c) * nc + cell] - P0;
             b.x[c][j] = (Real)(P0 + ((a * E1 + bb * E2) + cc * E3));
-            b.u[c][j] = (Real)(side == 0 ? U[c] + sig * X[c] : U[c] - sig * X[c]);
+            b.u[c][j] = (Real)((gp || side == 0) ? U[c] + sig * X[c] : U[c] - sig * X[c]);
         }
         b.m[j] = s.msam[cell];
         b.cell[j] = cell;

@@ -135,6 +135,7 @@ struct DevState {
     float4* usig;         // [nc] binary32 roundings of U and the sampling spread (MIXED sampling)
     double* sig;          // [nc] sampling spread s sqrt(RT) of energy-matched sampling
     double* dtc;          // [nc] local time step CFL |Omega| / sum_d Lambda^d (GKS step, local steps)
+    double* gpc;          // [GP_NC][nc] first-order g_p: acceptance polynomial and bound per cell
     double* wsum;         // [5][nc] time-average sums of dt^n W^n
     double* tsum;         // [1] sum of dt^n
     double* rhoh;         // [nc]
@@ -172,6 +173,12 @@ struct MeshHost {
     std::vector<int32_t> face_of_bf;                             // [nbf]
 };
 
+// First-order g_p sampling: per cell phi(X) = a0 + L.X + X^T Q X + (C.X)|X|^2
+// of X = (u - U)/sqrt(RT) and the acceptance bound M:
+// [a0, L(3), Qxx, Qyy, Qzz, Qxy, Qxz, Qyz, C(3), M].
+constexpr int GP_NC = 14;
+constexpr int GP_ATTEMPTS = 64;
+
 // Kernel launchers (stream-ordered, no synchronisation).
 constexpr int SCAN_BLOCK = 1024;
 inline int scan_blocks(int nc) { return (nc + SCAN_BLOCK - 1) / SCAN_BLOCK; }
@@ -202,6 +209,7 @@ void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, cons
 void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, int first, cudaStream_t st);
 void launch_face_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p, int blocks, cudaStream_t st);
 void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, int blocks, cudaStream_t st);
+void launch_gp_coef(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_rebuild_survivors(const DevMesh& m, const DevState& s, const DevParams& p,
                               const PartBufRaw& a, cudaStream_t st);

@@ -59,7 +59,7 @@ class Sizes(ctypes.Structure):
                 ("n_bfaces", ctypes.c_int64)]
 
 
-SAMPLING = {"maxwell": 0, "energy_matched": 1}
+SAMPLING = {"maxwell": 0, "energy_matched": 1, "gp1": 2}
 
 
 class LaunchCfg(ctypes.Structure):

@@ -83,6 +83,8 @@ def test_parameter_validation():
             ugkwp.ugkwp_query_sizes(mesh, dict(cfg["params"], **{key: val}))
     with pytest.raises(ugkwp.UgkwpError, match="sampling"):
         _raise_sampling(mesh, cfg["params"])
+    with pytest.raises(ugkwp.UgkwpError, match="order 2"):
+        ugkwp.ugkwp_query_sizes(mesh, dict(cfg["params"], order=1, sampling="gp1"))
     with pytest.raises(ugkwp.UgkwpError, match="venkat_K"):
         ugkwp.ugkwp_query_sizes(mesh, dict(cfg["params"], order=2, venkat_K=-1.0))
     with pytest.raises(ugkwp.UgkwpError, match="no entry"):
