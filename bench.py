@@ -14,6 +14,7 @@ int64 fixed-point particle flux).  A step is one full UGKWP time step.
   batched    64 independent instances in one graph, MIXED and FP64
   adjoint    the frozen-particle wave adjoint on a channel
   gks_start_up the particle-free start-up steps, global and local time steps
+  gp1_sampling the workload with first-order g_p sampling
   cpu_baseline the CPU oracle (single thread) on a bounded sample
 
 Multi-GPU: replicas only (each rank runs its own simulation; value = all
@@ -347,6 +348,25 @@ def adjoint(device, K=10):
             "cell_steps_per_s": n * K / (t1 - t0)}
 
 
+def gp1_sampling(device, steps, warmup, launch_cfg):
+    """The bench workload with first-order g_p sampling (every hydrodynamic
+    particle drawn by acceptance-rejection from its cell's g_p) after 200
+    spin-up steps, timed like the main line with the main line's grid sizes."""
+    import torch
+    from paper_2007_13091_gb300 import ugkwp
+    cfg = workload("mixed")
+    cfg["params"]["sampling"] = "gp1"
+    sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=torch.cuda.Stream(device=device))
+    ugkwp.ugkwp_set_launch_cfg(sim.handle, launch_cfg["particle_blocks"], launch_cfg["wave_blocks"])
+    sim.step(200)
+    ms, moves, _, kms, _ = time_steps(sim, steps, warmup, 1)
+    sim.close()
+    kms.pop("_moves", None)
+    return {"value": moves / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+            "kernels_ms_per_step": {k: v / steps for k, v in kms.items()},
+            "workload": "cavity 24^3, MIXED, order 2, sampling gp1, 200 spin-up steps"}
+
+
 def gks_start_up(device, steps=20, warmup=3):
     """Start-up steps of the gas-kinetic scheme (the method without particles,
     Sec. 3.2; the initial fields of the steady cases, Sec. 4.3, 4.4) on the
@@ -549,6 +569,7 @@ def main():
         out["batched"] = guarded(both)
         out["adjoint"] = guarded(lambda: adjoint(device))
         out["gks_start_up"] = guarded(lambda: gks_start_up(device))
+        out["gp1_sampling"] = guarded(lambda: gp1_sampling(device, args.steps, args.warmup, launch_cfg))
         out["cpu_baseline"] = cpu_baseline(args.cpu_steps)
     elif rank == 0:
         out["e2e"] = None
