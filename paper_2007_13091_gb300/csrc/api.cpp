@@ -659,7 +659,7 @@ int enqueue_step(ugkwp_sim* s) {
         const bool gp = s->P.sampling == UGKWP_SAMPLE_GP1;
         if (s->P.order == 2)
             timed(s, UGKWP_K_GRADIENTS, gp ? 2 : 1, s->wave, [&] {
-                launch_gradients(s->M, s->S, s->P, s->lc.wave_blocks, s->wave);
+                launch_gradients(s->M, s->S, s->P, s->wave);
                 // first-order g_p sampling needs the cell slopes
                 if (gp) launch_gp_coef(s->M, s->S, s->P, s->wave);
             });
@@ -716,7 +716,7 @@ int enqueue_gks_step(ugkwp_sim* s, int32_t mode) {
     timed(s, UGKWP_K_CELL_PREP, 1, q, [&] { launch_cell_prep(s->M, s->S, P, q); });
     timed(s, UGKWP_K_SAMPLE_COUNT, 1, q, [&] { launch_sample_count(s->M, s->S, P, q); });
     if (P.order == 2)
-        timed(s, UGKWP_K_GRADIENTS, 1, q, [&] { launch_gradients(s->M, s->S, P, s->lc.wave_blocks, q); });
+        timed(s, UGKWP_K_GRADIENTS, 1, q, [&] { launch_gradients(s->M, s->S, P, q); });
     if (P.order == 2 && s->M.nif > 0)
         timed(s, UGKWP_K_FLUX_O2, 1, q, [&] { launch_face_flux_o2(s->M, s->S, P, s->lc.wave_blocks, q); });
     const int first = P.order == 2 ? s->M.nif : 0;

@@ -168,66 +168,69 @@ __device__ __forceinline__ void venkat_ratio(double d1, double d2, double eps2, 
     if (den < 0.0) { num = -num; den = -den; }
 }
 
-__device__ __forceinline__ void gradients_of_cell(const DevMesh& m, const DevState& s, const DevParams& p, int i) {
+// Limited gradient of quantity q (0..4: W, 5: rho^h) of cell i.
+__device__ __forceinline__ void gradient_of(const DevMesh& m, const DevState& s, const DevParams& p, int i, int q) {
     const int nc = m.nc;
-    int other[4], bidx[4];
     const int own = m.cfs[i];
+    const double self = q < 5 ? s.W[(size_t)q * nc + i] : s.rhoh[i];
+    double val[4];
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int f = m.cf[k * nc + i];
-        other[k] = ((own >> k) & 1) ? m.f_nbr[f] : m.f_own[f];
-        bidx[k] = other[k] < 0 ? -1 - other[k] : -1;
-    }
-    double Wi[5];
-    for (int q = 0; q < 5; ++q) Wi[q] = s.W[(size_t)q * nc + i];
-    const double eps2 = m.eps2[i];
-    for (int q = 0; q < 6; ++q) {
-        const double self = q < 5 ? Wi[q] : s.rhoh[i];
-        double val[4];
-        for (int k = 0; k < 4; ++k) {
-            if (other[k] >= 0) {
-                val[k] = q < 5 ? s.W[(size_t)q * nc + other[k]] : s.rhoh[other[k]];
-            } else {
-                const DevBc& bc = p.bc[m.bf_tag[bidx[k]]];
-                val[k] = self;
-                if (bc.type == UGKWP_BC_SPECULAR && q >= 1 && q <= 3) {
-                    const int nbf = m.nbf;
-                    double n[3];
-                    for (int d = 0; d < 3; ++d) n[d] = m.bf_n[(size_t)d * nbf + bidx[k]];
-                    const double mn = Wi[1] * n[0] + Wi[2] * n[1] + Wi[3] * n[2];
-                    val[k] = self - 2.0 * mn * n[q - 1];
-                } else if (bc.type == UGKWP_BC_FARFIELD) {
-                    val[k] = q < 5 ? bc.W_in[q] : bc.W_in[0];
-                }
+        const int other = ((own >> k) & 1) ? m.f_nbr[f] : m.f_own[f];
+        if (other >= 0) {
+            val[k] = q < 5 ? s.W[(size_t)q * nc + other] : s.rhoh[other];
+        } else {
+            const int b = -1 - other;
+            const DevBc& bc = p.bc[m.bf_tag[b]];
+            val[k] = self;
+            if (bc.type == UGKWP_BC_SPECULAR && q >= 1 && q <= 3) {
+                const int nbf = m.nbf;
+                double n[3];
+                for (int d = 0; d < 3; ++d) n[d] = m.bf_n[(size_t)d * nbf + b];
+                const double mn = s.W[(size_t)nc + i] * n[0] + s.W[(size_t)2 * nc + i] * n[1] + s.W[(size_t)3 * nc + i] * n[2];
+                val[k] = self - 2.0 * mn * n[q - 1];
+            } else if (bc.type == UGKWP_BC_FARFIELD) {
+                val[k] = q < 5 ? bc.W_in[q] : bc.W_in[0];
             }
         }
-        double g[3] = {0.0, 0.0, 0.0};
-        for (int k = 0; k < 4; ++k)
-            for (int d = 0; d < 3; ++d) g[d] += m.lsq_c[(size_t)(3 * k + d) * nc + i] * (val[k] - self);
-        double vmax = self, vmin = self;
-        for (int k = 0; k < 4; ++k) { vmax = fmax(vmax, val[k]); vmin = fmin(vmin, val[k]); }
-        // phi = min(1, min_k num_k/den_k), compared by cross products (den > 0)
-        // so that only the chosen ratio is divided
-        double bn = 1.0, bd = 1.0;
-        for (int k = 0; k < 4; ++k) {
-            const double d2 = g[0] * m.lsq_dxf[(size_t)(3 * k) * nc + i] + g[1] * m.lsq_dxf[(size_t)(3 * k + 1) * nc + i] +
-                              g[2] * m.lsq_dxf[(size_t)(3 * k + 2) * nc + i];
-            if (d2 == 0.0) continue;
-            double num, den;
-            venkat_ratio(d2 > 0.0 ? vmax - self : vmin - self, d2, eps2, num, den);
-            if (num * bd < bn * den) { bn = num; bd = den; }
-        }
-        const double phi = bn / bd;
-        for (int d = 0; d < 3; ++d) {
-            if (q < 5) s.gradW[(size_t)(3 * q + d) * nc + i] = phi * g[d];
-            else s.gradH[(size_t)d * nc + i] = phi * g[d];
-        }
+    }
+    const double eps2 = m.eps2[i];
+    double g[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        for (int d = 0; d < 3; ++d) g[d] += m.lsq_c[(size_t)(3 * k + d) * nc + i] * (val[k] - self);
+    double vmax = self, vmin = self;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { vmax = fmax(vmax, val[k]); vmin = fmin(vmin, val[k]); }
+    // phi = min(1, min_k num_k/den_k), compared by cross products (den > 0)
+    // so that only the chosen ratio is divided
+    double bn = 1.0, bd = 1.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double d2 = g[0] * m.lsq_dxf[(size_t)(3 * k) * nc + i] + g[1] * m.lsq_dxf[(size_t)(3 * k + 1) * nc + i] +
+                          g[2] * m.lsq_dxf[(size_t)(3 * k + 2) * nc + i];
+        if (d2 == 0.0) continue;
+        double num, den;
+        venkat_ratio(d2 > 0.0 ? vmax - self : vmin - self, d2, eps2, num, den);
+        if (num * bd < bn * den) { bn = num; bd = den; }
+    }
+    const double phi = bn / bd;
+    for (int d = 0; d < 3; ++d) {
+        if (q < 5) s.gradW[(size_t)(3 * q + d) * nc + i] = phi * g[d];
+        else s.gradH[(size_t)d * nc + i] = phi * g[d];
     }
 }
 
-__global__ void __launch_bounds__(UGKWP_WAVE_THREADS) k_gradients(DevMesh m, DevState s, DevParams p) {
+// One thread per (quantity, cell), quantity-major so that neighbouring threads
+// read neighbouring cells of one array.
+__global__ void __launch_bounds__(128) k_gradients(DevMesh m, DevState s, DevParams p) {
     const int nc = m.nc;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
-        gradients_of_cell(m, s, p, i);
+    const long long n = 6LL * nc;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(t / nc);
+        gradient_of(m, s, p, (int)(t - (long long)q * nc), q);
+    }
 }
 
 // Moment tables of a unit Maxwellian in a face frame: <u^k> (normal, over the
@@ -730,8 +733,13 @@ static int wave_grid(int n, int blocks) {
     return need < blocks ? need : blocks;
 }
 
-void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, int blocks, cudaStream_t st) {
-    k_gradients<<<wave_grid(m.nc, blocks), UGKWP_WAVE_THREADS, 0, st>>>(m, s, p);
+// A persistent grid of 4 blocks per SM (56 registers at 128 threads): enough
+// warps for this latency-bound kernel, and room beside it for the first half
+// of the tracking grid.
+void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
+    const long long need = (6LL * m.nc + 127) / 128;
+    const long long cap = 4LL * sm_count();
+    k_gradients<<<(int)(need < cap ? need : cap), 128, 0, st>>>(m, s, p);
 }
 
 void launch_gp_coef(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {

@@ -208,7 +208,7 @@ void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, cons
 // First-order flux of face_order[first..nf); second-order flux of the nif interior faces.
 void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, int first, cudaStream_t st);
 void launch_face_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p, int blocks, cudaStream_t st);
-void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, int blocks, cudaStream_t st);
+void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_gp_coef(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_rebuild_survivors(const DevMesh& m, const DevState& s, const DevParams& p,
