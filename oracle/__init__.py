@@ -29,7 +29,7 @@ class OrcParams(ctypes.Structure):
                 ("omega", ctypes.c_double), ("CFL", ctypes.c_double), ("C2", ctypes.c_double),
                 ("venkat_K", ctypes.c_double), ("Pr", ctypes.c_double), ("order", ctypes.c_int32), ("N_ref", ctypes.c_int32), ("N_min", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("max_crossings", ctypes.c_int32),
-                ("n_bc", ctypes.c_int32), ("sampling", ctypes.c_int32), ("pad2_", ctypes.c_int32),
+                ("n_bc", ctypes.c_int32), ("sampling", ctypes.c_int32), ("K", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("bc", OrcBc * 16)]
 
 
@@ -51,7 +51,7 @@ def lib():
         L.orc_math_sincos2pi_f.argtypes = [vp, vp, vp, i64]
         L.orc_philox.argtypes = [vp, vp, vp]
         L.orc_qcoef.argtypes = [d, d, vp]
-        L.orc_maxwell_moments.argtypes = [vp, d, vp, ctypes.c_int, vp, vp]
+        L.orc_maxwell_moments.argtypes = [vp, d, vp, ctypes.c_int, i32, vp, vp]
         L.orc_face_flux.argtypes = [P(OrcParams), ctypes.c_int, vp, d, vp, d, vp, d, d, P(OrcBc), i32, vp]
         L.orc_create.argtypes = [P(OrcParams), i32, vp, i32, vp, i32, vp, vp, vp, cp, i32]
         L.orc_create.restype = vp
@@ -60,18 +60,18 @@ def lib():
         L.orc_gks_step.argtypes = [vp, i32, cp, i32]
         L.orc_sizes.argtypes = [vp, vp]
         L.orc_geometry.argtypes = [vp, ctypes.c_int, vp]
-        L.orc_get_state.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
-        L.orc_set_state.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, d, cp, i32]
+        L.orc_get_state.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_set_state.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, d, vp, cp, i32]
         L.orc_last.argtypes = [vp, ctypes.c_int, vp]
-        L.orc_track_one.argtypes = [vp, u64, i32, vp, vp, d, d, i64, vp, vp]
+        L.orc_track_one.argtypes = [vp, u64, i32, vp, vp, vp, d, d, i64, vp, vp]
         L.orc_prepare.argtypes = [vp, cp, i32]
         L.orc_gradients.argtypes = [vp, ctypes.c_int, vp, vp]
-        L.orc_slope_moment.argtypes = [vp, d, ctypes.c_int, vp, ctypes.c_int, vp]
-        L.orc_micro_slope.argtypes = [vp, d, vp, vp]
+        L.orc_slope_moment.argtypes = [vp, d, ctypes.c_int, i32, vp, ctypes.c_int, vp]
+        L.orc_micro_slope.argtypes = [vp, d, i32, vp, vp]
         L.orc_face_flux_o2.argtypes = [P(OrcParams), vp, d, vp, vp, vp, vp, d, vp, vp, vp, vp, d, i32, vp]
         L.orc_frozen_objective.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, vp, i32, vp]
         L.orc_frozen_value.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, vp, i32, vp]
-        L.orc_sample_cell.argtypes = [vp, i32, i64, vp, vp, vp, vp]
+        L.orc_sample_cell.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp]
         L.orc_sample_cell.restype = i64
         L.orc_gp_coefficients.argtypes = [vp, i32, vp]
         L.orc_gp_draw.argtypes = [i32, u64, u64, vp, u64, i64, vp]
@@ -109,6 +109,7 @@ def make_params(p: dict) -> OrcParams:
     o.precision = PRECISION[p.get("precision", "fp64")]
     o.max_crossings = int(p.get("max_crossings", 1000))
     o.sampling = SAMPLING[p.get("sampling", "maxwell")]
+    o.K = int(p.get("K", 0))
     o.seed = int(p["seed"])
     o.n_bc = len(p["bc"])
     for k, b in enumerate(p["bc"]):
@@ -164,12 +165,12 @@ def qcoef(dt: float, tau: float):
     return q
 
 
-def maxwell_moments(U, lam, n, half):
+def maxwell_moments(U, lam, n, half, K=0):
     U = np.ascontiguousarray(U, dtype=np.float64)
     n = np.ascontiguousarray(n, dtype=np.float64)
     H = np.empty(5)
     G = np.empty(5)
-    lib().orc_maxwell_moments(_ptr(U), float(lam), _ptr(n), int(half), _ptr(H), _ptr(G))
+    lib().orc_maxwell_moments(_ptr(U), float(lam), _ptr(n), int(half), int(K), _ptr(H), _ptr(G))
     return H, G
 
 
@@ -193,21 +194,21 @@ def face_flux(params: dict, kind: str, WL, rhohL, WR, rhohR, n, dt, tau_wall=0.0
     return F
 
 
-def slope_moment(U, lam, half, a, d):
+def slope_moment(U, lam, half, a, d, K=0):
     """int u_n u_d (a . psi) psi g du for a unit-density Maxwellian in a face
     frame (components of U and a along n, t1, t2)."""
     U = np.ascontiguousarray(U, dtype=np.float64)
     a = np.ascontiguousarray(a, dtype=np.float64)
     out = np.empty(5)
-    lib().orc_slope_moment(_ptr(U), float(lam), int(half), _ptr(a), int(d), _ptr(out))
+    lib().orc_slope_moment(_ptr(U), float(lam), int(half), int(K), _ptr(a), int(d), _ptr(out))
     return out
 
 
-def micro_slope(U, lam, b):
+def micro_slope(U, lam, b, K=0):
     U = np.ascontiguousarray(U, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
     a = np.empty(5)
-    lib().orc_micro_slope(_ptr(U), float(lam), _ptr(b), _ptr(a))
+    lib().orc_micro_slope(_ptr(U), float(lam), int(K), _ptr(b), _ptr(a))
     return a
 
 
@@ -299,11 +300,12 @@ class OracleSim:
         x = np.empty((3, n))
         u = np.empty((3, n))
         m = np.empty(n)
+        e = np.empty(n)
         scal = np.empty(6, dtype=np.int64)
         t = ctypes.c_double()
         lib().orc_get_state(self._h, _ptr(W), _ptr(pid), _ptr(cell), _ptr(x), _ptr(u), _ptr(m),
-                            _ptr(scal), ctypes.byref(t))
-        return {"W": W, "id": pid, "cell": cell, "x": x, "u": u, "m": m,
+                            _ptr(scal), ctypes.byref(t), _ptr(e))
+        return {"W": W, "id": pid, "cell": cell, "x": x, "u": u, "m": m, "e": e,
                 "step": int(scal[0]), "exps": scal[1:].copy(), "t": t.value}
 
     def set_state(self, st: dict):
@@ -314,9 +316,11 @@ class OracleSim:
         u = np.ascontiguousarray(st["u"], dtype=np.float64)
         m = np.ascontiguousarray(st["m"], dtype=np.float64)
         scal = np.ascontiguousarray([st["step"], *st["exps"]], dtype=np.int64)
+        e = st.get("e")
+        e = None if e is None else np.ascontiguousarray(e, dtype=np.float64)
         err = ctypes.create_string_buffer(512)
         rc = lib().orc_set_state(self._h, _ptr(W), pid.size, _ptr(pid), _ptr(cell), _ptr(x), _ptr(u),
-                                 _ptr(m), _ptr(scal), float(st["t"]), err, 512)
+                                 _ptr(m), _ptr(scal), float(st["t"]), _ptr(e) if e is not None else None, err, 512)
         if rc:
             raise ValueError("oracle set_state: " + err.value.decode())
 
@@ -378,13 +382,14 @@ class OracleSim:
 
     def sample_cell(self, cell):
         """The particles `cell` samples at the current step (after prepare())."""
-        n = lib().orc_sample_cell(self._h, int(cell), 0, None, None, None, None)
+        n = lib().orc_sample_cell(self._h, int(cell), 0, None, None, None, None, None)
         pid = np.empty(n, dtype=np.uint64)
         x = np.empty((n, 3))
         u = np.empty((n, 3))
         m = np.empty(n)
-        lib().orc_sample_cell(self._h, int(cell), n, _ptr(pid), _ptr(x), _ptr(u), _ptr(m))
-        return {"id": pid, "x": x.T.copy(), "u": u.T.copy(), "m": m}
+        e = np.empty(n)
+        lib().orc_sample_cell(self._h, int(cell), n, _ptr(pid), _ptr(x), _ptr(u), _ptr(m), _ptr(e))
+        return {"id": pid, "x": x.T.copy(), "u": u.T.copy(), "m": m, "e": e}
 
     def gp_coefficients(self, cell):
         """First-order g_p sampling: the cell's acceptance polynomial and bound
@@ -405,11 +410,13 @@ class OracleSim:
             raise RuntimeError("oracle gradients failed")
         return gW, gH
 
-    def track_one(self, pid, cell, x, u, tau_cell, dt, step):
+    def track_one(self, pid, cell, x, u, tau_cell, dt, step, e=0.0):
         io_x = np.ascontiguousarray(x, dtype=np.float64).copy()
         io_u = np.ascontiguousarray(u, dtype=np.float64).copy()
+        io_e = ctypes.c_double(float(e))
         c_out = ctypes.c_int32()
         nc = ctypes.c_int32()
-        st = lib().orc_track_one(self._h, int(pid), int(cell), _ptr(io_x), _ptr(io_u), float(tau_cell),
-                                 float(dt), int(step), ctypes.byref(c_out), ctypes.byref(nc))
-        return {"status": int(st), "cell": int(c_out.value), "x": io_x, "u": io_u, "ncross": int(nc.value)}
+        st = lib().orc_track_one(self._h, int(pid), int(cell), _ptr(io_x), _ptr(io_u), ctypes.byref(io_e),
+                                 float(tau_cell), float(dt), int(step), ctypes.byref(c_out), ctypes.byref(nc))
+        return {"status": int(st), "cell": int(c_out.value), "x": io_x, "u": io_u, "e": io_e.value,
+                "ncross": int(nc.value)}

@@ -45,7 +45,7 @@ static inline uint64_t make_id(uint64_t step, uint64_t cell, uint64_t k) {
 }
 static inline uint64_t id_step(uint64_t id) { return id >> 40; }
 // Random-number purposes (third counter word).
-enum { TAG_TF = 1, TAG_SVEL = 2, TAG_SPOS = 3, TAG_WALL = 4, TAG_GP = 5 };
+enum { TAG_TF = 1, TAG_SVEL = 2, TAG_SPOS = 3, TAG_WALL = 4, TAG_GP = 5, TAG_SINT = 6, TAG_WINT = 7 };
 
 static inline Ctr4 draw(uint64_t seed, uint64_t a, uint64_t b, uint64_t tag, uint64_t idx) {
     Ctr4 c; c.v[0] = a; c.v[1] = b; c.v[2] = tag; c.v[3] = idx;
@@ -198,15 +198,15 @@ static bool build_geometry(Geom& g, int nn, const double* xyz, int nc, const int
 }
 
 // ------------------------------------------------------------- primitives
-// Sec. 2: W = (rho, rho U, rho E), rho E = 1/2 rho |U|^2 + (3+K)/2 p with K = 0,
-// p = rho R T, lambda = 1/(2RT).
+// Sec. 2: W = (rho, rho U, rho E), rho E = 1/2 rho |U|^2 + (3+K)/2 p with K
+// internal degrees of freedom, p = rho R T, lambda = 1/(2RT).
 struct Prim { double rho, U[3], p, T, lam; };
-static inline Prim prim_of(const double* W, double R) {
+static inline Prim prim_of(const double* W, double R, int K) {
     Prim s;
     s.rho = W[0];
     for (int d = 0; d < 3; ++d) s.U[d] = W[1 + d] / s.rho;
     double U2 = (s.U[0] * s.U[0] + s.U[1] * s.U[1]) + s.U[2] * s.U[2];
-    s.p = (W[4] - 0.5 * (s.rho * U2)) / 1.5;
+    s.p = (W[4] - 0.5 * (s.rho * U2)) / (1.5 + 0.5 * (double)K);
     s.T = s.p / (s.rho * R);
     s.lam = s.rho / (2.0 * s.p);
     return s;
@@ -271,14 +271,16 @@ static void un_moments(double Un, double lam, int half, double M[5]) {
     for (int k = 0; k < 3; ++k) M[k + 2] = Un * M[k + 1] + (double)(k + 1) / (2.0 * lam) * M[k];
 }
 
-// H = int g psi du and G = int u_n g psi du over the half space, for a unit-density
-// Maxwellian with velocity U = Un n + Ut and lambda; psi = (1, u, |u|^2/2), K = 0.
-static void half_moments(double Un, const double* Ut, const double* n, double lam, int half,
+// H = int g psi du dxi and G = int u_n g psi du dxi over the half space, for a
+// unit-density Maxwellian with velocity U = Un n + Ut and lambda;
+// psi = (1, u, (|u|^2 + |xi|^2)/2) with K internal degrees of freedom xi.
+static void half_moments(double Un, const double* Ut, const double* n, double lam, int half, int K,
                          double H[5], double G[5]) {
     double M[5];
     un_moments(Un, lam, half, M);
     double Ut2 = (Ut[0] * Ut[0] + Ut[1] * Ut[1]) + Ut[2] * Ut[2];
-    double tv = Ut2 + 1.0 / lam;  // <|u_t|^2> of the two tangential directions
+    // <|u_t|^2> of the two tangential directions, then + <|xi|^2> = K/(2 lambda)
+    double tv = (Ut2 + 1.0 / lam) + (double)K * (0.5 / lam);
     H[0] = M[0];
     G[0] = M[1];
     for (int d = 0; d < 3; ++d) {
@@ -290,8 +292,8 @@ static void half_moments(double Un, const double* Ut, const double* n, double la
 }
 
 struct FaceState { double rho, rhoh, Un, Ut[3], lam, p, T; };
-static FaceState face_state(const double* W, double rhoh, const double* n, double R) {
-    Prim s = prim_of(W, R);
+static FaceState face_state(const double* W, double rhoh, const double* n, double R, int K) {
+    Prim s = prim_of(W, R, K);
     FaceState f;
     f.rho = s.rho; f.rhoh = rhoh; f.lam = s.lam; f.p = s.p; f.T = s.T;
     f.Un = dot3(s.U, n);
@@ -316,11 +318,11 @@ static FaceState face_state(const double* W, double rhoh, const double* n, doubl
 static void interior_flux(const FaceState& L, const FaceState& Rs, bool ghost_hydro, bool gks,
                           const double* n, double dt, const orc_params& P, double F[5]) {
     double HL[5], GL[5], HR[5], GR[5];
-    half_moments(L.Un, L.Ut, n, L.lam, +1, HL, GL);
-    half_moments(Rs.Un, Rs.Ut, n, Rs.lam, -1, HR, GR);
+    half_moments(L.Un, L.Ut, n, L.lam, +1, P.K, HL, GL);
+    half_moments(Rs.Un, Rs.Ut, n, Rs.lam, -1, P.K, HR, GR);
     double W0[5];
     for (int q = 0; q < 5; ++q) W0[q] = L.rho * HL[q] + Rs.rho * HR[q];
-    Prim s0 = prim_of(W0, P.R);
+    Prim s0 = prim_of(W0, P.R, P.K);
     double tau = P.mu_ref * std::pow(s0.T / P.T_ref, P.omega) / s0.p
                + P.C2 * std::fabs(L.p - Rs.p) / std::fabs(L.p + Rs.p) * dt;
     double q[7];
@@ -328,7 +330,7 @@ static void interior_flux(const FaceState& L, const FaceState& Rs, bool ghost_hy
     double Un0 = dot3(s0.U, n), Ut0[3];
     for (int d = 0; d < 3; ++d) Ut0[d] = s0.U[d] - Un0 * n[d];
     double H0[5], G0[5];
-    half_moments(Un0, Ut0, n, s0.lam, 0, H0, G0);
+    half_moments(Un0, Ut0, n, s0.lam, 0, P.K, H0, G0);
     double cL = gks ? q[3] : q[5];
     double cR = (ghost_hydro || gks) ? q[3] : q[5];
     for (int k = 0; k < 5; ++k)
@@ -344,7 +346,7 @@ static void wall_flux(const FaceState& L, double tau, const orc_bc& bc, const do
     double q[7];
     qcoef(dt, tau, q);
     double HL[5], GL[5];
-    half_moments(L.Un, L.Ut, n, L.lam, +1, HL, GL);
+    half_moments(L.Un, L.Ut, n, L.lam, +1, P.K, HL, GL);
     double Gin[5];
     const double c4 = gks ? q[3] : q[5];
     for (int k = 0; k < 5; ++k) Gin[k] = q[0] * (L.rho * GL[k]) + c4 * (L.rhoh * GL[k]);
@@ -352,14 +354,14 @@ static void wall_flux(const FaceState& L, double tau, const orc_bc& bc, const do
     double Uwn = dot3(bc.U_w, n), Uwt[3];
     for (int d = 0; d < 3; ++d) Uwt[d] = bc.U_w[d] - Uwn * n[d];
     double Hw[5], Gw[5];
-    half_moments(Uwn, Uwt, n, lamw, -1, Hw, Gw);
+    half_moments(Uwn, Uwt, n, lamw, -1, P.K, Hw, Gw);
     double rhow = -Gin[0] / (dt * Gw[0]);
     for (int k = 0; k < 5; ++k) F[k] = Gin[k] + dt * rhow * Gw[k];
 }
 
 static void boundary_flux(const double* WL, double rhohL, double tauL, const orc_bc& bc,
                           const double* n, double dt, bool gks, const orc_params& P, double F[5]) {
-    FaceState L = face_state(WL, rhohL, n, P.R);
+    FaceState L = face_state(WL, rhohL, n, P.R, P.K);
     if (bc.type == ORC_BC_DIFFUSE_WALL) { wall_flux(L, tauL, bc, n, dt, gks, P, F); return; }
     if (bc.type == ORC_BC_SPECULAR) {
         // Mirror ghost: same state with the normal velocity reversed.  Only the
@@ -374,7 +376,7 @@ static void boundary_flux(const double* WL, double rhohL, double tauL, const orc
     }
     // Far field: inflow ghost = prescribed state, outflow ghost = interior state;
     // both all-hydrodynamic and emitting no particles (reading).
-    FaceState Rg = (bc.type == ORC_BC_INFLOW) ? face_state(bc.W_in, bc.W_in[0], n, P.R) : L;
+    FaceState Rg = (bc.type == ORC_BC_INFLOW) ? face_state(bc.W_in, bc.W_in[0], n, P.R, P.K) : L;
     Rg.rhoh = Rg.rho;
     interior_flux(L, Rg, true, gks, n, dt, P, F);
 }
@@ -495,10 +497,12 @@ static void limited_gradients(const Geom& g, const orc_params& P, const std::vec
 
 // ---- velocity moments of a unit-density Maxwellian in the face frame
 // (u along n, v along t1, w along t2), by explicit expansion over monomials.
-struct Term { double c; int a, b, e; };
+// a monomial c u^a v^b w^e |xi|^(2x) (xi: the K internal degrees of freedom)
+struct Term { double c; int a, b, e, x; };
 typedef std::vector<Term> Poly;
 
-struct FrameMom { double n[8], t1[8], t2[8]; };
+// 1D moments of the frame directions and <|xi|^(2j)>, j = 0..3
+struct FrameMom { double n[8], t1[8], t2[8], xi[4]; };
 
 // <u^k>, k = 0..7, of the normalised 1D Maxwellian (mean m, lambda), over all u
 // (half = 0) or the half line u > 0 (+1) / u < 0 (-1).
@@ -513,46 +517,52 @@ static void moments1d(double m, double lam, int half, double* M) {
     for (int k = 0; k < 6; ++k) M[k + 2] = m * M[k + 1] + (double)(k + 1) / (2.0 * lam) * M[k];
 }
 
-static FrameMom frame_moments(const double* Uf, double lam, int half) {
+static FrameMom frame_moments(const double* Uf, double lam, int half, int K) {
     FrameMom F;
     moments1d(Uf[0], lam, half, F.n);
     moments1d(Uf[1], lam, 0, F.t1);
     moments1d(Uf[2], lam, 0, F.t2);
+    // |xi|^2 is a sum of K squared normals of variance 1/(2 lambda):
+    // <|xi|^(2j)> = K (K+2) ... (K+2j-2) / (2 lambda)^j
+    F.xi[0] = 1.0;
+    for (int j = 1; j < 4; ++j) F.xi[j] = F.xi[j - 1] * (double)(K + 2 * (j - 1)) / (2.0 * lam);
     return F;
 }
 
 static double expect(const FrameMom& M, const Poly& P) {
     double s = 0.0;
-    for (const Term& t : P) s += t.c * M.n[t.a] * M.t1[t.b] * M.t2[t.e];
+    for (const Term& t : P) s += t.c * M.n[t.a] * M.t1[t.b] * M.t2[t.e] * M.xi[t.x];
     return s;
 }
 
 static Poly mul(const Poly& A, const Poly& B) {
     Poly C;
-    for (const Term& x : A) for (const Term& y : B) C.push_back(Term{x.c * y.c, x.a + y.a, x.b + y.b, x.e + y.e});
+    for (const Term& x : A)
+        for (const Term& y : B) C.push_back(Term{x.c * y.c, x.a + y.a, x.b + y.b, x.e + y.e, x.x + y.x});
     return C;
 }
 
-// psi_k in the face frame: 1, u, v, w, (u^2 + v^2 + w^2)/2
+// psi_k in the face frame: 1, u, v, w, (u^2 + v^2 + w^2 + |xi|^2)/2
 static Poly psi(int k) {
     switch (k) {
-        case 0: return Poly{{1.0, 0, 0, 0}};
-        case 1: return Poly{{1.0, 1, 0, 0}};
-        case 2: return Poly{{1.0, 0, 1, 0}};
-        case 3: return Poly{{1.0, 0, 0, 1}};
-        default: return Poly{{0.5, 2, 0, 0}, {0.5, 0, 2, 0}, {0.5, 0, 0, 2}};
+        case 0: return Poly{{1.0, 0, 0, 0, 0}};
+        case 1: return Poly{{1.0, 1, 0, 0, 0}};
+        case 2: return Poly{{1.0, 0, 1, 0, 0}};
+        case 3: return Poly{{1.0, 0, 0, 1, 0}};
+        default: return Poly{{0.5, 2, 0, 0, 0}, {0.5, 0, 2, 0, 0}, {0.5, 0, 0, 2, 0}, {0.5, 0, 0, 0, 1}};
     }
 }
 static Poly lin(const double* a) {  // a . psi
-    return Poly{{a[0], 0, 0, 0}, {a[1], 1, 0, 0}, {a[2], 0, 1, 0}, {a[3], 0, 0, 1},
-                {0.5 * a[4], 2, 0, 0}, {0.5 * a[4], 0, 2, 0}, {0.5 * a[4], 0, 0, 2}};
+    return Poly{{a[0], 0, 0, 0, 0}, {a[1], 1, 0, 0, 0}, {a[2], 0, 1, 0, 0}, {a[3], 0, 0, 1, 0},
+                {0.5 * a[4], 2, 0, 0, 0}, {0.5 * a[4], 0, 2, 0, 0}, {0.5 * a[4], 0, 0, 2, 0},
+                {0.5 * a[4], 0, 0, 0, 1}};
 }
-static Poly coord(int d) { return Poly{{1.0, d == 0 ? 1 : 0, d == 1 ? 1 : 0, d == 2 ? 1 : 0}}; }
+static Poly coord(int d) { return Poly{{1.0, d == 0 ? 1 : 0, d == 1 ? 1 : 0, d == 2 ? 1 : 0, 0}}; }
 
 // Micro slope a with <psi psi^T> a = b for the unit Maxwellian (Uf, lam):
 // the moment matrix built from moments, solved by Gaussian elimination.
-static void micro_slope(const double* Uf, double lam, const double* b, double* a) {
-    FrameMom M = frame_moments(Uf, lam, 0);
+static void micro_slope(const double* Uf, double lam, int K, const double* b, double* a) {
+    FrameMom M = frame_moments(Uf, lam, 0, K);
     double A[5][6];
     for (int r = 0; r < 5; ++r) {
         for (int c = 0; c < 5; ++c) A[r][c] = expect(M, mul(psi(r), psi(c)));
@@ -625,12 +635,12 @@ struct SideO2 {
 };
 
 static bool side_o2(const Frame& R, const double* Wlab, double rhoh, const double* gW, const double* gH,
-                    const double* dx, SideO2& S) {
+                    const double* dx, int K, SideO2& S) {
     // reconstruct W and rho^h at the face from the cell values and limited gradients
     double Wface[5];
     for (int q = 0; q < 5; ++q) Wface[q] = Wlab[q] + dot3(&gW[3 * q], dx);
     double rh = rhoh + dot3(gH, dx);
-    Prim pr = prim_of(Wface, 1.0);
+    Prim pr = prim_of(Wface, 1.0, K);
     if (!(Wface[0] > 0.0) || !(pr.p > 0.0)) return false;
     state_to_frame(R, Wface, S.W);
     S.rhoh = rh;
@@ -647,11 +657,11 @@ static bool side_o2(const Frame& R, const double* Wlab, double rhoh, const doubl
     return true;
 }
 
-static SideO2 side_o1(const Frame& R, const double* Wlab, double rhoh) {
+static SideO2 side_o1(const Frame& R, const double* Wlab, double rhoh, int K) {
     SideO2 S;
     state_to_frame(R, Wlab, S.W);
     S.rhoh = rhoh;
-    Prim pr = prim_of(Wlab, 1.0);
+    Prim pr = prim_of(Wlab, 1.0, K);
     for (int d = 0; d < 3; ++d) S.U[d] = S.W[1 + d] / S.W[0];
     S.lam = pr.lam;
     for (int d = 0; d < 3; ++d) for (int q = 0; q < 5; ++q) { S.dW[d][q] = 0.0; S.dWh[d][q] = 0.0; }
@@ -665,21 +675,21 @@ static SideO2 side_o1(const Frame& R, const double* Wlab, double rhoh) {
 // W_t = -int u.g_x psi, and all slopes solved from the moment system.
 static void interior_flux_o2(const SideO2& L, const SideO2& Rs, const double* pLR, double dt, bool gks,
                              const orc_params& P, double Ff[5]) {
-    FrameMom ML = frame_moments(L.U, L.lam, +1), MR = frame_moments(Rs.U, Rs.lam, -1);
+    FrameMom ML = frame_moments(L.U, L.lam, +1, P.K), MR = frame_moments(Rs.U, Rs.lam, -1, P.K);
     double W0[5];
     for (int k = 0; k < 5; ++k) W0[k] = L.W[0] * expect(ML, psi(k)) + Rs.W[0] * expect(MR, psi(k));
-    Prim s0 = prim_of(W0, P.R);  // frame velocity components in s0.U
+    Prim s0 = prim_of(W0, P.R, P.K);  // frame velocity components in s0.U
     double tau = P.mu_ref * std::pow(s0.T / P.T_ref, P.omega) / s0.p
                + P.C2 * std::fabs(pLR[0] - pLR[1]) / std::fabs(pLR[0] + pLR[1]) * dt;
     double q[7];
     qcoef(dt, tau, q);
-    FrameMom M0 = frame_moments(s0.U, s0.lam, 0);
+    FrameMom M0 = frame_moments(s0.U, s0.lam, 0, P.K);
     // equilibrium slopes (with the density factor): a_d = M^-1 W_x,d
     double a0[3][5];
     for (int d = 0; d < 3; ++d) {
         double b[5];
         for (int k = 0; k < 5; ++k) b[k] = 0.5 * (L.dW[d][k] + Rs.dW[d][k]);
-        micro_slope(s0.U, s0.lam, b, a0[d]);
+        micro_slope(s0.U, s0.lam, P.K, b, a0[d]);
     }
     double Wt[5], At[5];
     for (int k = 0; k < 5; ++k) {
@@ -687,12 +697,12 @@ static void interior_flux_o2(const SideO2& L, const SideO2& Rs, const double* pL
         for (int d = 0; d < 3; ++d) acc += expect(M0, mul(mul(coord(d), lin(a0[d])), psi(k)));
         Wt[k] = -acc;
     }
-    micro_slope(s0.U, s0.lam, Wt, At);
+    micro_slope(s0.U, s0.lam, P.K, Wt, At);
     // upwind hydrodynamic slopes a^h_d = M_side^-1 grad_d W^h
     double aL[3][5], aR[3][5];
     for (int d = 0; d < 3; ++d) {
-        micro_slope(L.U, L.lam, L.dWh[d], aL[d]);
-        micro_slope(Rs.U, Rs.lam, Rs.dWh[d], aR[d]);
+        micro_slope(L.U, L.lam, P.K, L.dWh[d], aL[d]);
+        micro_slope(Rs.U, Rs.lam, P.K, Rs.dWh[d], aR[d]);
     }
     const Poly un = coord(0);
     for (int k = 0; k < 5; ++k) {
@@ -721,6 +731,7 @@ static void interior_flux_o2(const SideO2& L, const SideO2& Rs, const double* pL
         }
         Poly rn = coord(0);
         rn.push_back(Term{-s0.U[0], 0, 0, 0});
+        sq.push_back(Term{0.5, 0, 0, 0, 1});  // + |xi|^2 / 2
         const Poly h = mul(rn, sq);
         double qn = q[0] * s0.rho * expect(M0, h) + q[2] * expect(M0, mul(h, lin(At)));
         for (int d = 0; d < 3; ++d) qn += q[1] * expect(M0, mul(mul(h, coord(d)), lin(a0[d])));
@@ -735,8 +746,8 @@ static void face_flux_o2(const Frame& R, const double* WL, double rhohL, const d
                          const double* gHR, const double* dxR, double dt, bool gks, const orc_params& P,
                          double F[5]) {
     SideO2 L, Rs;
-    if (!side_o2(R, WL, rhohL, gWL, gHL, dxL, L)) L = side_o1(R, WL, rhohL);
-    if (!side_o2(R, WR, rhohR, gWR, gHR, dxR, Rs)) Rs = side_o1(R, WR, rhohR);
+    if (!side_o2(R, WL, rhohL, gWL, gHL, dxL, P.K, L)) L = side_o1(R, WL, rhohL, P.K);
+    if (!side_o2(R, WR, rhohR, gWR, gHR, dxR, P.K, Rs)) Rs = side_o1(R, WR, rhohR, P.K);
     double pLR[2] = {0.5 * L.W[0] / L.lam, 0.5 * Rs.W[0] / Rs.lam};
     double Ff[5];
     interior_flux_o2(L, Rs, pLR, dt, gks, P, Ff);
@@ -770,17 +781,17 @@ static void gp_coefficients(const Prim& s, const double* gW, double tau, double 
     for (int d = 0; d < 3; ++d) {
         double rhs[5];
         for (int q = 0; q < 5; ++q) rhs[q] = gW[3 * q + d] / s.rho;
-        micro_slope(U, s.lam, rhs, b[d]);
+        micro_slope(U, s.lam, 0, rhs, b[d]);
     }
     // W_t / rho = -sum_d <u_d psi (b_d . psi)>, <psi psi^T> B = W_t / rho
-    FrameMom M0 = frame_moments(U, s.lam, 0);
+    FrameMom M0 = frame_moments(U, s.lam, 0, 0);
     double Wt[5], B[5];
     for (int k = 0; k < 5; ++k) {
         double acc = 0.0;
         for (int d = 0; d < 3; ++d) acc += expect(M0, mul(mul(coord(d), lin(b[d])), psi(k)));
         Wt[k] = -acc;
     }
-    micro_slope(U, s.lam, Wt, B);
+    micro_slope(U, s.lam, 0, Wt, B);
     // P(u) = sum_d u_d (b_d . psi) + B . psi
     //      = B0 + v.u + u^T K u + (h/2)|u|^2 + (|u|^2/2)(beta.u)
     double v[3], K[3][3], beta[3];
@@ -873,7 +884,43 @@ static void gp_draw(uint64_t seed, uint64_t step, const double* c, uint64_t id, 
 }
 
 // ------------------------------------------------------------ particles
-template <class Real> struct Part { uint64_t id; int32_t cell; Real x[3]; Real u[3]; double m; };
+// e: internal energy per unit mass (|xi|^2, zero when K = 0), phi = m (1, u, (|u|^2 + e)/2)
+template <class Real> struct Part { uint64_t id; int32_t cell; Real x[3]; Real u[3]; double m; Real e = (Real)0; };
+
+// Internal energy of a particle with K internal degrees of freedom at spread
+// sig = sqrt(RT): e = sum_{i<K} (sig N_i)^2, the normals N by Box-Muller from
+// Philox counters (id, step, tag, idx0 + j), four per counter, summed in order
+// in the particle precision.
+template <class Real>
+static Real internal_energy(uint64_t seed, uint64_t id, uint64_t step, uint64_t tag, uint64_t idx0, int K, Real sig) {
+    Real e = (Real)0;
+    for (int j = 0; 4 * j < K; ++j) {
+        Ctr4 r = draw(seed, id, step, tag, idx0 + (uint64_t)j);
+        Real N[4];
+        if constexpr (std::is_same<Real, float>::value) {
+            float sn, cs;
+            float rad = std::sqrt(-2.0f * log_f(u01_f(r.v[0])));
+            sincos2pi_f(u01_f(r.v[1]), &sn, &cs);
+            N[0] = rad * cs; N[1] = rad * sn;
+            rad = std::sqrt(-2.0f * log_f(u01_f(r.v[2])));
+            sincos2pi_f(u01_f(r.v[3]), &sn, &cs);
+            N[2] = rad * cs; N[3] = rad * sn;
+        } else {
+            double sn, cs;
+            double rad = std::sqrt(-2.0 * log_d(u01_d(r.v[0])));
+            sincos2pi_d(u01_d(r.v[1]), &sn, &cs);
+            N[0] = rad * cs; N[1] = rad * sn;
+            rad = std::sqrt(-2.0 * log_d(u01_d(r.v[2])));
+            sincos2pi_d(u01_d(r.v[3]), &sn, &cs);
+            N[2] = rad * cs; N[3] = rad * sn;
+        }
+        for (int i = 0; i < 4 && 4 * j + i < K; ++i) {
+            const Real si = sig * N[i];
+            e = e + si * si;
+        }
+    }
+    return e;
+}
 
 template <class Real> struct Planes {
     std::vector<Real> n;  // [4*nc][3]
@@ -975,6 +1022,7 @@ static TrackOut track(const Geom& g, const Planes<Real>& pl, const orc_params& P
                 float v1 = (float)dot3(bc.U_w, t1) + sw * (rad * cs);
                 float v2 = (float)dot3(bc.U_w, t2) + sw * (rad * sn);
                 for (int c = 0; c < 3; ++c) u[c] = ((-vn) * (float)n[c] + v1 * (float)t1[c]) + v2 * (float)t2[c];
+                if (P.K > 0) pt.e = internal_energy<float>(P.seed, pt.id, step, TAG_WINT, 2 * (uint64_t)o.nwall, P.K, sw);
             } else {
                 double vn = std::sqrt(-2.0 * P.R * bc.T_w * log_d(u01_d(r.v[0])));
                 double rad = std::sqrt(-2.0 * log_d(u01_d(r.v[1])));
@@ -987,6 +1035,8 @@ static TrackOut track(const Geom& g, const Planes<Real>& pl, const orc_params& P
                 double v1 = dot3(bc.U_w, t1) + sw * (rad * cs);
                 double v2 = dot3(bc.U_w, t2) + sw * (rad * sn);
                 for (int c = 0; c < 3; ++c) u[c] = (Real)(((-vn) * n[c] + v1 * t1[c]) + v2 * t2[c]);
+                if (P.K > 0)
+                    pt.e = (Real)internal_energy<double>(P.seed, pt.id, step, TAG_WINT, 2 * (uint64_t)o.nwall, P.K, sw);
             }
             o.nwall++;
         }
@@ -1005,7 +1055,7 @@ template <class Real>
 static bool phi_fixed(const Part<Real>& pt, const int* e, int64_t q[5]) {
     double u0 = (double)pt.u[0], u1 = (double)pt.u[1], u2 = (double)pt.u[2];
     double m = pt.m;
-    double phi[5] = {m, m * u0, m * u1, m * u2, 0.5 * (m * ((u0 * u0 + u1 * u1) + u2 * u2))};
+    double phi[5] = {m, m * u0, m * u1, m * u2, 0.5 * (m * (((u0 * u0 + u1 * u1) + u2 * u2) + (double)pt.e))};
     bool ok = true;
     for (int k = 0; k < 5; ++k) {
         double v = std::ldexp(phi[k], -e[k]);
@@ -1032,12 +1082,13 @@ struct SimBase {
     virtual int64_t n_particles() const = 0;
     virtual int do_step(std::string& err) = 0;
     virtual int prepare(std::string& err) = 0;
-    virtual int64_t sample_one_cell(int cell, int64_t cap, uint64_t* id, double* x, double* u, double* m) const = 0;
+    virtual int64_t sample_one_cell(int cell, int64_t cap, uint64_t* id, double* x, double* u, double* m,
+                                    double* e) const = 0;
     virtual bool gp_coef(int cell, double* out) const = 0;
-    virtual void get_particles(uint64_t*, int32_t*, double*, double*, double*) const = 0;
+    virtual void get_particles(uint64_t*, int32_t*, double*, double*, double*, double*) const = 0;
     virtual bool set_particles(int64_t, const uint64_t*, const int32_t*, const double*, const double*,
-                               const double*, std::string&) = 0;
-    virtual int track_one(uint64_t, int32_t, double*, double*, double, double, int64_t, int32_t*, int32_t*) const = 0;
+                               const double*, const double*, std::string&) = 0;
+    virtual int track_one(uint64_t, int32_t, double*, double*, double*, double, double, int64_t, int32_t*, int32_t*) const = 0;
     // a3 (order 2): limited least-squares gradients of W and rho^h; a4: the
     // time-integrated wave flux F of every face from W and rho^h, over dt or,
     // when dtf is given, over dtf[f].  gks: no particles (both halves of the
@@ -1068,7 +1119,7 @@ struct SimBase {
             } else if (nb >= 0) {
                 double WR[5];
                 for (int k = 0; k < 5; ++k) WR[k] = W[(size_t)k * nc + nb];
-                FaceState L = face_state(WL, rhoh[o], n, p.R), Rs = face_state(WR, rhoh[nb], n, p.R);
+                FaceState L = face_state(WL, rhoh[o], n, p.R, p.K), Rs = face_state(WR, rhoh[nb], n, p.R, p.K);
                 interior_flux(L, Rs, false, gks, n, dtv, p, Fv);
             } else {
                 boundary_flux(WL, rhoh[o], tau[o], p.bc[g.f_bc[f]], n, dtv, gks, p, Fv);
@@ -1095,7 +1146,7 @@ struct SimBase {
         for (int i = 0; i < nc; ++i) {
             double Wi[5];
             for (int k = 0; k < 5; ++k) Wi[k] = W[(size_t)k * nc + i];
-            Prim s = prim_of(Wi, p.R);
+            Prim s = prim_of(Wi, p.R, p.K);
             if (!(s.rho > 0.0) || !(s.p > 0.0) || !std::isfinite(s.p)) {
                 err = "non-positive density or pressure in cell " + std::to_string(i);
                 return -9;
@@ -1172,7 +1223,7 @@ template <class Real> struct Sim : SimBase {
         for (int i = 0; i < nc; ++i) {
             double Wi[5];
             for (int k = 0; k < 5; ++k) Wi[k] = W[(size_t)k * nc + i];
-            pr[i] = prim_of(Wi, p.R);
+            pr[i] = prim_of(Wi, p.R, p.K);
             if (!(pr[i].rho > 0.0) || !(pr[i].p > 0.0) || !std::isfinite(pr[i].p)) {
                 err = "non-positive density or pressure in cell " + std::to_string(i);
                 return -9;
@@ -1300,6 +1351,7 @@ template <class Real> struct Sim : SimBase {
                     } else {
                         for (int c = 0; c < 3; ++c) pt.u[c] = side == 0 ? Uf[c] + sigf * X[c] : Uf[c] - sigf * X[c];
                     }
+                    if (p.K > 0) pt.e = internal_energy<float>(p.seed, pt.id, (uint64_t)step, TAG_SINT, 0, p.K, sigf);
                     Ctr4 rp = draw(p.seed, pt.id, (uint64_t)step, TAG_SPOS, 0);
                     float a = u01_f(rp.v[0]), b = u01_f(rp.v[1]), cc = u01_f(rp.v[2]);
                     if (a + b > 1.0f) { a = 1.0f - a; b = 1.0f - b; }
@@ -1334,6 +1386,7 @@ template <class Real> struct Sim : SimBase {
                         for (int c = 0; c < 3; ++c)
                             pt.u[c] = (Real)(side == 0 ? pr[i].U[c] + sig * X[c] : pr[i].U[c] - sig * X[c]);
                     }
+                    if (p.K > 0) pt.e = (Real)internal_energy<double>(p.seed, pt.id, (uint64_t)step, TAG_SINT, 0, p.K, sig);
                     // Uniform point in the tet: cube -> prism -> tet folding
                     // (Rocchini and Cignoni, J. Graphics Tools 5(4), 2000).
                     Ctr4 rp = draw(p.seed, pt.id, (uint64_t)step, TAG_SPOS, 0);
@@ -1432,19 +1485,21 @@ template <class Real> struct Sim : SimBase {
         return true;
     }
 
-    int64_t sample_one_cell(int cell, int64_t cap, uint64_t* id, double* x, double* u, double* m) const override {
+    int64_t sample_one_cell(int cell, int64_t cap, uint64_t* id, double* x, double* u, double* m,
+                            double* e) const override {
         std::vector<Part<Real>> v;
         sample_cell(cell, v);
         const int64_t n = (int64_t)v.size();
         for (int64_t k = 0; k < n && k < cap; ++k) {
             id[k] = v[k].id;
             m[k] = v[k].m;
+            if (e) e[k] = (double)v[k].e;
             for (int c = 0; c < 3; ++c) { x[3 * k + c] = (double)v[k].x[c]; u[3 * k + c] = (double)v[k].u[c]; }
         }
         return n;
     }
 
-    void get_particles(uint64_t* id, int32_t* cell, double* x, double* u, double* m) const override {
+    void get_particles(uint64_t* id, int32_t* cell, double* x, double* u, double* m, double* e) const override {
         size_t n = parts.size();
         for (size_t k = 0; k < n; ++k) {
             const auto& pt = parts[k];
@@ -1455,11 +1510,12 @@ template <class Real> struct Sim : SimBase {
                 if (u) u[c * n + k] = (double)pt.u[c];
             }
             if (m) m[k] = pt.m;
+            if (e) e[k] = (double)pt.e;
         }
     }
 
     bool set_particles(int64_t n, const uint64_t* id, const int32_t* cell, const double* x,
-                       const double* u, const double* m, std::string& err) override {
+                       const double* u, const double* m, const double* e, std::string& err) override {
         parts.resize((size_t)n);
         for (int64_t k = 0; k < n; ++k) {
             Part<Real>& pt = parts[(size_t)k];
@@ -1472,15 +1528,23 @@ template <class Real> struct Sim : SimBase {
                     err = "particle state not representable in the particle precision"; return false;
                 }
             }
+            pt.e = (Real)0;
+            if (e && P.K > 0) {
+                pt.e = (Real)e[k];
+                if ((double)pt.e != e[k] || !(e[k] >= 0.0)) {
+                    err = "internal energy negative or not representable in the particle precision"; return false;
+                }
+            }
         }
         return true;
     }
 
-    int track_one(uint64_t id, int32_t cell, double* io_x, double* io_u, double tau_c, double dtv,
+    int track_one(uint64_t id, int32_t cell, double* io_x, double* io_u, double* io_e, double tau_c, double dtv,
                   int64_t stp, int32_t* cell_out, int32_t* nc_out) const override {
         Part<Real> pt;
         pt.id = id; pt.cell = cell; pt.m = 1.0;
         for (int c = 0; c < 3; ++c) { pt.x[c] = (Real)io_x[c]; pt.u[c] = (Real)io_u[c]; }
+        if (io_e) pt.e = (Real)*io_e;
         const Real dtR = (Real)dtv;
         Real t_end = dtR;
         int st = 0;
@@ -1493,6 +1557,7 @@ template <class Real> struct Sim : SimBase {
         }
         TrackOut o = track<Real>(g, pl, P, pt, t_end, (uint64_t)stp);
         for (int c = 0; c < 3; ++c) { io_x[c] = (double)pt.x[c]; io_u[c] = (double)pt.u[c]; }
+        if (io_e) *io_e = (double)pt.e;
         *cell_out = o.cell;
         *nc_out = o.ncross;
         return st | o.status;
@@ -1513,7 +1578,7 @@ static void scale_exponents(const Geom& g, const orc_params& P, const std::vecto
     for (int i = 0; i < nc; ++i) {
         double Wi[5];
         for (int k = 0; k < 5; ++k) Wi[k] = W[(size_t)k * nc + i];
-        Prim s = prim_of(Wi, P.R);
+        Prim s = prim_of(Wi, P.R, P.K);
         double mass = s.rho * g.vol[i];
         if (mass > bm) bm = mass;
         double c = std::sqrt(dot3(s.U, s.U)) + 5.0 * std::sqrt(P.R * s.T);
@@ -1525,7 +1590,7 @@ static void scale_exponents(const Geom& g, const orc_params& P, const std::vecto
             double c = std::sqrt(dot3(bc.U_w, bc.U_w)) + 5.0 * std::sqrt(P.R * bc.T_w);
             if (c > cmax) cmax = c;
         } else if (bc.type == ORC_BC_INFLOW) {
-            Prim s = prim_of(bc.W_in, P.R);
+            Prim s = prim_of(bc.W_in, P.R, P.K);
             double c = std::sqrt(dot3(s.U, s.U)) + 5.0 * std::sqrt(P.R * s.T);
             if (c > cmax) cmax = c;
         }
@@ -1817,18 +1882,18 @@ void orc_philox(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
 
 void orc_qcoef(double dt, double tau, double q[7]) { qcoef(dt, tau, q); }
 
-void orc_maxwell_moments(const double U[3], double lam, const double n[3], int half,
+void orc_maxwell_moments(const double U[3], double lam, const double n[3], int half, int32_t K,
                          double H[5], double G[5]) {
     double Un = dot3(U, n), Ut[3];
     for (int d = 0; d < 3; ++d) Ut[d] = U[d] - Un * n[d];
-    half_moments(Un, Ut, n, lam, half, H, G);
+    half_moments(Un, Ut, n, lam, half, K, H, G);
 }
 
 int orc_face_flux(const orc_params* p, int kind, const double WL[5], double rhohL,
                   const double WR[5], double rhohR, const double n[3], double dt,
                   double tau_wall, const orc_bc* bc, int32_t gks, double F[5]) {
     if (kind == 0) {
-        FaceState L = face_state(WL, rhohL, n, p->R), R = face_state(WR, rhohR, n, p->R);
+        FaceState L = face_state(WL, rhohL, n, p->R, p->K), R = face_state(WR, rhohR, n, p->R, p->K);
         interior_flux(L, R, false, gks != 0, n, dt, *p, F);
         return 0;
     }
@@ -1845,6 +1910,11 @@ orc_sim* orc_create(const orc_params* p, int32_t n_nodes, const double* xyz,
     if (p->order != 1 && p->order != 2) { set_err(err, errlen, "order must be 1 or 2"); return nullptr; }
     if (p->n_bc < 0 || p->n_bc > 16) { set_err(err, errlen, "n_bc out of range"); return nullptr; }
     if (p->sampling < 0 || p->sampling > 2) { set_err(err, errlen, "unknown sampling mode"); return nullptr; }
+    if (p->K < 0 || p->K > 8) { set_err(err, errlen, "K must be in [0, 8]"); return nullptr; }
+    if (p->K > 0 && p->sampling != 0) {
+        set_err(err, errlen, "internal degrees of freedom (K > 0) need the printed sampling");
+        return nullptr;
+    }
     if (p->sampling == 2 && p->order != 2) {
         set_err(err, errlen, "first-order g_p sampling needs order 2 (the cell slopes)");
         return nullptr;
@@ -1907,20 +1977,20 @@ int orc_geometry(const orc_sim* h, int which, double* out) {
 }
 
 void orc_get_state(const orc_sim* h, double* W, uint64_t* id, int32_t* cell,
-                   double* x, double* u, double* m, int64_t* scal, double* t) {
+                   double* x, double* u, double* m, int64_t* scal, double* t, double* e) {
     const SimBase* s = h->s;
     if (W) std::memcpy(W, s->W.data(), s->W.size() * sizeof(double));
-    s->get_particles(id, cell, x, u, m);
+    s->get_particles(id, cell, x, u, m, e);
     if (scal) { scal[0] = s->step; for (int k = 0; k < 5; ++k) scal[1 + k] = s->e[k]; }
     if (t) *t = s->t;
 }
 
 int orc_set_state(orc_sim* h, const double* W, int64_t n, const uint64_t* id,
                   const int32_t* cell, const double* x, const double* u, const double* m,
-                  const int64_t* scal, double t, char* err, int32_t errlen) {
+                  const int64_t* scal, double t, const double* ei, char* err, int32_t errlen) {
     SimBase* s = h->s;
     std::string e;
-    if (!s->set_particles(n, id, cell, x, u, m, e)) { set_err(err, errlen, e); return -1; }
+    if (!s->set_particles(n, id, cell, x, u, m, ei, e)) { set_err(err, errlen, e); return -1; }
     std::memcpy(s->W.data(), W, s->W.size() * sizeof(double));
     s->step = scal[0];
     for (int k = 0; k < 5; ++k) s->e[k] = (int)scal[1 + k];
@@ -1961,12 +2031,14 @@ int orc_gradients(orc_sim* h, int limited, double* gradW, double* gradH) {
     return 0;
 }
 
-void orc_slope_moment(const double U[3], double lam, int half, const double a[5], int d, double out[5]) {
-    FrameMom M = frame_moments(U, lam, half);
+void orc_slope_moment(const double U[3], double lam, int half, int32_t K, const double a[5], int d, double out[5]) {
+    FrameMom M = frame_moments(U, lam, half, K);
     for (int k = 0; k < 5; ++k) out[k] = expect(M, mul(mul(mul(coord(0), coord(d)), lin(a)), psi(k)));
 }
 
-void orc_micro_slope(const double U[3], double lam, const double b[5], double a[5]) { micro_slope(U, lam, b, a); }
+void orc_micro_slope(const double U[3], double lam, int32_t K, const double b[5], double a[5]) {
+    micro_slope(U, lam, K, b, a);
+}
 
 int orc_face_flux_o2(const orc_params* p, const double WL[5], double rhohL, const double gWL[15], const double gHL[3],
                      const double dxL[3], const double WR[5], double rhohR, const double gWR[15],
@@ -1984,9 +2056,10 @@ int orc_prepare(orc_sim* h, char* err, int32_t errlen) {
     return rc;
 }
 
-int64_t orc_sample_cell(const orc_sim* h, int32_t cell, int64_t cap, uint64_t* id, double* x, double* u, double* m) {
+int64_t orc_sample_cell(const orc_sim* h, int32_t cell, int64_t cap, uint64_t* id, double* x, double* u, double* m,
+                        double* e) {
     if (cell < 0 || cell >= h->s->g.nc) return -1;
-    return h->s->sample_one_cell(cell, cap, id, x, u, m);
+    return h->s->sample_one_cell(cell, cap, id, x, u, m, e);
 }
 
 void orc_gp_draw(int32_t precision, uint64_t seed, uint64_t step, const double coef[14], uint64_t id0, int64_t n,
@@ -2002,16 +2075,16 @@ int orc_gp_coefficients(const orc_sim* h, int32_t cell, double out[14]) {
     return h->s->gp_coef(cell, out) ? 0 : -1;
 }
 
-int orc_track_one(const orc_sim* h, uint64_t id, int32_t cell, double* io_x, double* io_u,
+int orc_track_one(const orc_sim* h, uint64_t id, int32_t cell, double* io_x, double* io_u, double* io_e,
                   double tau_cell_v, double dt, int64_t step, int32_t* cell_out, int32_t* ncross) {
-    return h->s->track_one(id, cell, io_x, io_u, tau_cell_v, dt, step, cell_out, ncross);
+    return h->s->track_one(id, cell, io_x, io_u, io_e, tau_cell_v, dt, step, cell_out, ncross);
 }
 
 int orc_frozen_objective(const orc_sim* h, int32_t K, const double* W0, const double* dt, const double* rho_p,
                          const double* pflux, const double theta[3], int32_t functional, const int32_t* tags,
                          int32_t n_tags, double out[4]) {
     const SimBase& sim = *h->s;
-    if (sim.P.order != 1 || K < 1 || (functional != 0 && functional != 1)) return -1;
+    if (sim.P.order != 1 || sim.P.K != 0 || K < 1 || (functional != 0 && functional != 1)) return -1;
     std::vector<char> listed(16, 0);
     for (int k = 0; k < n_tags; ++k)
         if (tags[k] >= 0 && tags[k] < 16) listed[tags[k]] = 1;
@@ -2027,7 +2100,7 @@ int orc_frozen_value(const orc_sim* h, int32_t K, const double* W0, const double
                      const double* pflux, const double theta[3], int32_t functional, const int32_t* tags,
                      int32_t n_tags, double* J) {
     const SimBase& sim = *h->s;
-    if (sim.P.order != 1 || K < 1 || (functional != 0 && functional != 1)) return -1;
+    if (sim.P.order != 1 || sim.P.K != 0 || K < 1 || (functional != 0 && functional != 1)) return -1;
     std::vector<char> listed(16, 0);
     for (int k = 0; k < n_tags; ++k)
         if (tags[k] >= 0 && tags[k] < 16) listed[tags[k]] = 1;

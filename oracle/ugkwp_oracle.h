@@ -40,7 +40,9 @@ typedef struct {
                         * rho^hp |Omega| (3/2) R T (energy-matched sampling); 2: every
                         * particle drawn on its own from the first-order g_p
                         * (acceptance-rejection; order 2 only) */
-    int32_t pad2_;
+    int32_t K;         /* internal degrees of freedom: rho E = rho |U|^2/2 + (3+K)/2 p; particles
+                        * carry an internal energy e ~ R T chi^2_K (0 <= K <= 8; K > 0 with
+                        * sampling 0 only) */
     uint64_t seed;
     orc_bc bc[16];
 } orc_params;
@@ -61,7 +63,7 @@ void orc_qcoef(double dt, double tau, double q[7]);
 /* Moments of a unit-density Maxwellian (U, lambda) with K = 0, normal n:
  * H[5] = int_{half} g psi du, G[5] = int_{half} u.n g psi du,
  * half = +1 (u.n > 0), -1 (u.n < 0) or 0 (all u). */
-void orc_maxwell_moments(const double U[3], double lam, const double n[3], int half,
+void orc_maxwell_moments(const double U[3], double lam, const double n[3], int half, int32_t K,
                          double H[5], double G[5]);
 /* Time-integrated wave flux of one face (F^eq + F^{fr,wave}, per unit area,
  * normal from L to R).  kind: 0 interior, or an ORC_BC_* type with the ghost
@@ -89,14 +91,15 @@ void orc_sizes(const orc_sim* s, int64_t out[5]);
  * 6 dS[3][nc], 7 face plane offset d[nf] */
 int orc_geometry(const orc_sim* s, int which, double* out);
 /* State export.  Any pointer may be NULL.  scal = [step, e_0..e_4] (int64),
- * t = simulation time. */
+ * t = simulation time, e = the particles' internal energies (0 when K = 0). */
 void orc_get_state(const orc_sim* s, double* W, uint64_t* id, int32_t* cell,
-                   double* x, double* u, double* m, int64_t* scal, double* t);
-/* State import (teacher forcing).  Positions/velocities must be exactly
- * representable in the particle precision. */
+                   double* x, double* u, double* m, int64_t* scal, double* t, double* e);
+/* State import (teacher forcing).  Positions/velocities (and internal
+ * energies, read when K > 0; e may be NULL) must be exactly representable in
+ * the particle precision. */
 int orc_set_state(orc_sim* s, const double* W, int64_t n, const uint64_t* id,
                   const int32_t* cell, const double* x, const double* u, const double* m,
-                  const int64_t* scal, double t, char* err, int32_t errlen);
+                  const int64_t* scal, double t, const double* e, char* err, int32_t errlen);
 /* Diagnostics of the last step (which):
  *  0 dt (1 value), 1 tau[nc], 2 rho_h[nc] (before sampling), 3 n_sam[nc],
  *  4 m_sam[nc], 5 wave flux F[5][nf], 6 particle flux F^{fr,p}[5][nc] (fixed point,
@@ -110,7 +113,8 @@ int orc_last(const orc_sim* s, int which, void* out);
 int orc_prepare(orc_sim* s, char* err, int32_t errlen);
 /* The particles cell `cell` samples at the current step (after orc_prepare):
  * returns their number n and fills up to cap of them (x, u as [k][3]). */
-int64_t orc_sample_cell(const orc_sim* s, int32_t cell, int64_t cap, uint64_t* id, double* x, double* u, double* m);
+int64_t orc_sample_cell(const orc_sim* s, int32_t cell, int64_t cap, uint64_t* id, double* x, double* u, double* m,
+                        double* e);
 /* First-order g_p sampling (sampling = 2), after orc_prepare: the cell's
  * acceptance polynomial phi(X) = a0 + L.X + X^T Q X + (C.X)|X|^2 of X = (u - U)
  * / sqrt(RT) and its bound: [a0, L(3), Qxx, Qyy, Qzz, Qxy, Qxz, Qyz, C(3), M].
@@ -129,8 +133,8 @@ void orc_gp_draw(int32_t precision, uint64_t seed, uint64_t step, const double c
  * Second-order flux of one interior face from cell states, limited gradients
  * ([q][d] row-major) and centroid-to-face vectors. */
 int orc_gradients(orc_sim* s, int limited, double* gradW, double* gradH);
-void orc_slope_moment(const double U[3], double lam, int half, const double a[5], int d, double out[5]);
-void orc_micro_slope(const double U[3], double lam, const double b[5], double a[5]);
+void orc_slope_moment(const double U[3], double lam, int half, int32_t K, const double a[5], int d, double out[5]);
+void orc_micro_slope(const double U[3], double lam, int32_t K, const double b[5], double a[5]);
 int orc_face_flux_o2(const orc_params* p, const double WL[5], double rhohL, const double gWL[15], const double gHL[3],
                      const double dxL[3], const double WR[5], double rhohR, const double gWR[15],
                      const double gHR[3], const double dxR[3], const double n[3], double dt, int32_t gks,
@@ -158,7 +162,7 @@ int orc_frozen_value(const orc_sim* s, int32_t K, const double* W0, const double
  * at sizes where a whole oracle step would be slow).  io_x/io_u are [3];
  * the particle precision follows the simulation.  Returns the status bits
  * 1 collided, 2 exited, 4 lost; *cell_out the end tet; *ncross the crossings. */
-int orc_track_one(const orc_sim* s, uint64_t id, int32_t cell, double* io_x, double* io_u,
+int orc_track_one(const orc_sim* s, uint64_t id, int32_t cell, double* io_x, double* io_u, double* io_e,
                   double tau_cell, double dt, int64_t step, int32_t* cell_out, int32_t* ncross);
 
 #ifdef __cplusplus

@@ -117,7 +117,8 @@ def jitter(nodes, tets, bfaces, amount, spacing, seed, min_ratio=0.2):
     return nodes
 
 
-def conservative(rho, U, p):
+def conservative(rho, U, p, K=0):
+    """(rho, rho U, rho E) with rho E = rho |U|^2 / 2 + (3 + K)/2 p."""
     rho = np.asarray(rho, dtype=np.float64)
     U = np.asarray(U, dtype=np.float64)
     p = np.asarray(p, dtype=np.float64)
@@ -125,7 +126,7 @@ def conservative(rho, U, p):
     W = np.empty((5,) + rho.shape)
     W[0] = rho
     W[1:4] = np.moveaxis(rho[..., None] * U, -1, 0)
-    W[4] = 0.5 * rho * np.sum(U * U, axis=-1) + 1.5 * p
+    W[4] = 0.5 * rho * np.sum(U * U, axis=-1) + (1.5 + 0.5 * K) * p
     return W
 
 
@@ -150,7 +151,7 @@ def _params(Kn, omega, CFL, N_ref, precision, seed, bc, C2=0.0, N_min=0, capacit
 
 
 def shock_tube(nx=100, ny=4, nz=4, Kn=1e-2, N_ref=50, precision="fp64", CFL=0.5, seed=1,
-               omega=0.81, C2=0.0, length=1.0, width=0.04, order=1, U=0.0):
+               omega=0.81, C2=0.0, length=1.0, width=0.04, order=1, U=0.0, K=0):
     """3D Sod tube [0,1] x [0,0.04]^2: left rho=1, p=1; right rho=0.125, p=0.1;
     both moving at U along x (0 for the Sod problem); far-field ends holding
     the undisturbed states, specular side walls."""
@@ -164,28 +165,30 @@ def shock_tube(nx=100, ny=4, nz=4, Kn=1e-2, N_ref=50, precision="fp64", CFL=0.5,
     rho = np.where(left, 1.0, 0.125)
     p = np.where(left, 1.0, 0.1)
     Uv = np.array([U, 0.0, 0.0])
-    W0 = conservative(rho, Uv, p)
+    W0 = conservative(rho, Uv, p, K)
     # far-field ends hold the undisturbed left and right states
-    WL = conservative(np.array(1.0), Uv, np.array(1.0))
-    WR = conservative(np.array(0.125), Uv, np.array(0.1))
+    WL = conservative(np.array(1.0), Uv, np.array(1.0), K)
+    WR = conservative(np.array(0.125), Uv, np.array(0.1), K)
     bc = [{"type": "farfield", "W_in": tuple(float(v) for v in WL)},
           {"type": "farfield", "W_in": tuple(float(v) for v in WR)}, {"type": "specular"}]
     params = _params(Kn, omega, CFL, N_ref, precision, seed, bc, C2=C2, n_cells=len(tets), order=order)
+    params["K"] = K
     return {"name": f"shock_tube_{nx}x{ny}x{nz}", "mesh": {"nodes": nodes, "tets": tets, "bfaces": bf,
             "btags": btags}, "W0": W0, "params": params}
 
 
-def cavity(n=24, Kn=0.075, N_ref=100, precision="mixed", CFL=0.5, seed=2, omega=0.81, lid_mach=0.16, order=1):
+def cavity(n=24, Kn=0.075, N_ref=100, precision="mixed", CFL=0.5, seed=2, omega=0.81, lid_mach=0.16, order=1, K=0):
     """Lid-driven cubic cavity: unit cube, all walls diffuse at T0 = 1, the z = 1
     lid moving at U = (lid_mach sqrt(gamma R T0), 0, 0); gas at rest, rho = 1."""
     xs = np.linspace(0.0, 1.0, n + 1)
     nodes, tets, bf, where = structured_tet_mesh(xs, xs, xs)
     btags = (where == 5).astype(np.int32)
-    W0 = conservative(np.ones(len(tets)), np.zeros(3), np.ones(len(tets)))
-    Ulid = lid_mach * math.sqrt(GAMMA)
+    W0 = conservative(np.ones(len(tets)), np.zeros(3), np.ones(len(tets)), K)
+    Ulid = lid_mach * math.sqrt((K + 5.0) / (K + 3.0))
     bc = [{"type": "wall", "T_w": 1.0, "U_w": (0.0, 0.0, 0.0)},
           {"type": "wall", "T_w": 1.0, "U_w": (Ulid, 0.0, 0.0)}]
     params = _params(Kn, omega, CFL, N_ref, precision, seed, bc, n_cells=len(tets), order=order)
+    params["K"] = K
     return {"name": f"cavity_{n}^3", "mesh": {"nodes": nodes, "tets": tets, "bfaces": bf, "btags": btags},
             "W0": W0, "params": params}
 
@@ -251,7 +254,7 @@ def cube_flow(h0=1.0 / 42, growth=1.5, Kn=0.1, mach=4.0, N_ref=200, precision="m
 
 def uniform_box(n=(3, 3, 3), size=(1.0, 1.0, 1.0), rho=1.0, U=(0.0, 0.0, 0.0), p=1.0, Kn=0.1, N_ref=20,
                 precision="fp64", CFL=0.5, seed=7, bc_type="specular", T_w=1.0, omega=0.81,
-                jitter_amount=0.0):
+                jitter_amount=0.0, K=0):
     """Box of n hexes (x 6 tets), one boundary condition on all sides, uniform gas."""
     xs, ys, zs = (np.linspace(0.0, s, k + 1) for k, s in zip(n, size))
     nodes, tets, bf, where = structured_tet_mesh(xs, ys, zs)
@@ -259,13 +262,14 @@ def uniform_box(n=(3, 3, 3), size=(1.0, 1.0, 1.0), rho=1.0, U=(0.0, 0.0, 0.0), p
         h = min(s / k for k, s in zip(n, size))
         nodes = jitter(nodes, tets, bf, jitter_amount, h, seed)
     btags = np.zeros(len(bf), dtype=np.int32)
-    W0 = conservative(np.full(len(tets), rho), np.asarray(U, dtype=np.float64), np.full(len(tets), p))
+    W0 = conservative(np.full(len(tets), rho), np.asarray(U, dtype=np.float64), np.full(len(tets), p), K)
     b = {"type": bc_type}
     if bc_type == "wall":
         b.update(T_w=T_w, U_w=(0.0, 0.0, 0.0))
     if bc_type in ("inflow", "farfield"):
-        b.update(W_in=tuple(float(v) for v in conservative(np.array(rho), np.asarray(U, float), np.array(p))))
+        b.update(W_in=tuple(float(v) for v in conservative(np.array(rho), np.asarray(U, float), np.array(p), K)))
     params = _params(Kn, omega, CFL, N_ref, precision, seed, [b], n_cells=len(tets))
+    params["K"] = K
     return {"name": "uniform_box", "mesh": {"nodes": nodes, "tets": tets, "bfaces": bf, "btags": btags},
             "W0": W0, "params": params}
 
