@@ -140,7 +140,11 @@ typedef struct {
                                   * first-order g_p of Sec. 2.2, g - c (u.grad g + g_t) with
                                   * c = tau - dt e^{-dt/tau}/(1 - e^{-dt/tau}), by
                                   * acceptance-rejection (order 2 only: the cell slopes) */
-    int32_t reserved_;           /* must be 0 */
+    int32_t K;                   /* internal degrees of freedom (Sec. 2.2): rho E = rho |U|^2/2 +
+                                  * (3+K)/2 p, and each particle carries an internal energy e
+                                  * (phi = m (1, u, (|u|^2 + e)/2)) sampled as R T chi^2_K and
+                                  * re-drawn at diffuse walls from T_w.  0 <= K <= 8; K > 0 needs
+                                  * UGKWP_SAMPLE_MAXWELL; the adjoint needs K = 0 */
     uint64_t seed;               /* Philox4x64-10 key word 0 */
     int64_t particle_capacity;   /* particles the device buffers hold (< 2^31) */
     ugkwp_bc bc[16];
@@ -163,8 +167,9 @@ typedef struct {
 
 /* Host-side image of the simulation state for checkpoint/restart and for
  * teacher-forced comparison.  All pointers are caller-owned host buffers:
- * W [5][n_cells]; id, cell, m [n]; x, u [3][n] (binary64; in MIXED mode the
- * values are binary32 numbers widened exactly).  exps are the base-2
+ * W [5][n_cells]; id, cell, m, e [n]; x, u [3][n] (binary64; in MIXED mode
+ * the values are binary32 numbers widened exactly).  e: the internal energies
+ * (read and written when K > 0; may be NULL when K = 0).  exps are the base-2
  * exponents of the fixed-point quanta of (mass, 3 x momentum, energy). */
 typedef struct {
     int64_t n_particles;
@@ -178,6 +183,7 @@ typedef struct {
     double* x;
     double* u;
     double* m;
+    double* e;
 } ugkwp_state;
 
 /* ---------------------------------------------------------------- mesh */
@@ -378,7 +384,8 @@ int ugkwp_adjoint_wave(ugkwp_sim* s, const ugkwp_adjoint_req* r, double* out);
  *   dt = CFL min_i |Omega_i| / sum_d (|U_d| + 3 sqrt(R T_i)) DeltaS_i^d
  * (Sec. 2.4 (a)), from device arrays the caller already owns, and writes it
  * to d_dt[0] on the given stream (cudaStream_t, NULL = legacy default stream).
- *   d_W   [5][n_cells] conservative variables (rho, rho U, rho E), device
+ *   d_W   [5][n_cells] conservative variables (rho, rho U, rho E) of a
+ *         monatomic gas (K = 0: p = (rho E - rho |U|^2/2) / 1.5), device
  *   d_vol [n_cells] cell volumes, device
  *   d_dS  [3][n_cells] projected areas DeltaS^x, ^y, ^z, device
  * Cells with rho <= 0 or p <= 0 are skipped; if no cell is valid d_dt[0] is

@@ -114,8 +114,8 @@ struct Carver {
     }
 };
 
-void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, DevState& S, PartBufRaw& A,
-            PartBufRaw& B, PartBufRaw& Mv) {
+void layout(const MeshHost& mh, int64_t cap, size_t rs, bool with_e, Carver& c, DevMesh& M, DevState& S,
+            PartBufRaw& A, PartBufRaw& B, PartBufRaw& Mv) {
     const size_t nc = mh.nc, nf = mh.nf, nbf = mh.nbf;
     M.nc = mh.nc; M.nf = mh.nf; M.nbf = mh.nbf; M.nif = mh.nf - mh.nbf;
     M.vol = c.take<double>(nc);
@@ -178,6 +178,8 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, Carver& c, DevMesh& M, D
         pb->m = c.take<double>((size_t)cap);
         pb->cell = c.take<int32_t>((size_t)cap);
         pb->id = c.take<uint64_t>((size_t)cap);
+        pb->e = with_e ? (void*)c.take<char>(rs * (size_t)cap) : nullptr;
+        pb->e2 = (with_e && pb == &Mv) ? (void*)c.take<char>(rs * (size_t)cap) : nullptr;
     }
 }
 
@@ -196,6 +198,9 @@ int check_params(const ugkwp_params* p, const MeshHost* mh) {
     if (p->sampling != UGKWP_SAMPLE_MAXWELL && p->sampling != UGKWP_SAMPLE_ENERGY_MATCHED &&
         p->sampling != UGKWP_SAMPLE_GP1)
         return fail(UGKWP_E_ARG, "unknown sampling mode");
+    if (p->K < 0 || p->K > 8) return fail(UGKWP_E_ARG, "K must be in [0, 8]");
+    if (p->K > 0 && p->sampling != UGKWP_SAMPLE_MAXWELL)
+        return fail(UGKWP_E_ARG, "internal degrees of freedom (K > 0) need UGKWP_SAMPLE_MAXWELL");
     if (p->sampling == UGKWP_SAMPLE_GP1 && p->order != 2)
         return fail(UGKWP_E_ARG, "first-order g_p sampling needs order 2 (the cell slopes)");
     if (p->particle_capacity < 0 || p->particle_capacity >= ((int64_t)1 << 31))
@@ -329,7 +334,7 @@ int ugkwp_query_sizes(const ugkwp_mesh* m, const ugkwp_params* p, ugkwp_sizes* o
     PartBufRaw A{}, B{};
     Carver c(nullptr);
     PartBufRaw Mv{};
-    layout(m->h, p->particle_capacity, p->precision == UGKWP_MIXED ? 4 : 8, c, M, S, A, B, Mv);
+    layout(m->h, p->particle_capacity, p->precision == UGKWP_MIXED ? 4 : 8, p->K > 0, c, M, S, A, B, Mv);
     out->workspace_bytes = (c.off + 255) & ~(size_t)255;
     out->n_cells = m->h.nc;
     out->n_faces = m->h.nf;
@@ -366,7 +371,7 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     s->capacity = p->particle_capacity;
     s->n_bc = p->n_bc;
     Carver c(d_workspace);
-    layout(mh, p->particle_capacity, s->real_size, c, s->M, s->S, s->A, s->B, s->Mv);
+    layout(mh, p->particle_capacity, s->real_size, p->K > 0, c, s->M, s->S, s->A, s->B, s->Mv);
     // parameters
     DevParams& P = s->P;
     std::memset(&P, 0, sizeof(P));
@@ -375,6 +380,7 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     P.N_ref = p->N_ref; P.N_min = p->N_min; P.max_crossings = p->max_crossings; P.precision = p->precision;
     P.order = p->order;
     P.sampling = p->sampling;
+    P.K = p->K;
     P.seed = p->seed; P.capacity = p->particle_capacity; P.n_bc = p->n_bc;
     for (int b = 0; b < p->n_bc; ++b) {
         P.bc[b].type = p->bc[b].type;
@@ -941,6 +947,8 @@ int ugkwp_export_state(ugkwp_sim* s, ugkwp_state* st) {
     std::vector<double> m(n);
     std::vector<int32_t> cell(n);
     std::vector<uint64_t> id(n);
+    std::vector<char> es(s->A.e ? n * rs : 0);
+    if (s->A.e && n) CU(cudaMemcpyAsync(es.data(), s->A.e, n * rs, cudaMemcpyDeviceToHost, q));
     for (int d = 0; d < 3; ++d) {
         xs[d].resize(n * rs);
         us[d].resize(n * rs);
@@ -962,6 +970,7 @@ int ugkwp_export_state(ugkwp_sim* s, ugkwp_state* st) {
         if (st->id) st->id[k] = id[i];
         if (st->cell) st->cell[k] = cell[i];
         if (st->m) st->m[k] = m[i];
+        if (st->e) st->e[k] = !s->A.e ? 0.0 : rs == 4 ? (double)((const float*)es.data())[i] : ((const double*)es.data())[i];
         for (int d = 0; d < 3; ++d) {
             double xv, uv;
             if (rs == 4) { xv = ((const float*)xs[d].data())[i]; uv = ((const float*)us[d].data())[i]; }
@@ -982,13 +991,26 @@ int ugkwp_import_state(ugkwp_sim* s, const ugkwp_state* st) {
     if (st->step < 0 || st->step >= ((int64_t)1 << 24) - 1) return fail(UGKWP_E_STATE, "step out of range");
     const int nc = s->M.nc;
     const size_t rs = s->real_size;
+    if (s->A.e && n > 0 && !st->e) return fail(UGKWP_E_ARG, "internal energies (e) needed when K > 0");
     std::vector<char> xs[3], us[3];
+    std::vector<char> es(s->A.e ? (size_t)n * rs : 0);
     for (int d = 0; d < 3; ++d) {
         xs[d].resize((size_t)n * rs);
         us[d].resize((size_t)n * rs);
     }
     for (int64_t i = 0; i < n; ++i) {
         if (st->cell[i] < 0 || st->cell[i] >= nc) return fail(UGKWP_E_STATE, "particle cell out of range");
+        if (s->A.e) {
+            const double ev = st->e[i];
+            if (!(ev >= 0.0)) return fail(UGKWP_E_STATE, "negative internal energy");
+            if (rs == 4) {
+                const float ef = (float)ev;
+                if ((double)ef != ev) return fail(UGKWP_E_STATE, "internal energy not representable in binary32");
+                ((float*)es.data())[i] = ef;
+            } else {
+                ((double*)es.data())[i] = ev;
+            }
+        }
         for (int d = 0; d < 3; ++d) {
             const double xv = st->x[d * n + i], uv = st->u[d * n + i];
             if (rs == 4) {
@@ -1009,6 +1031,7 @@ int ugkwp_import_state(ugkwp_sim* s, const ugkwp_state* st) {
             CU(cudaMemcpyAsync(s->A.x[d], xs[d].data(), (size_t)n * rs, cudaMemcpyHostToDevice, q));
             CU(cudaMemcpyAsync(s->A.u[d], us[d].data(), (size_t)n * rs, cudaMemcpyHostToDevice, q));
         }
+    if (n && s->A.e) CU(cudaMemcpyAsync(s->A.e, es.data(), (size_t)n * rs, cudaMemcpyHostToDevice, q));
     if (n) {
         CU(cudaMemcpyAsync(s->A.m, st->m, (size_t)n * 8, cudaMemcpyHostToDevice, q));
         CU(cudaMemcpyAsync(s->A.cell, st->cell, (size_t)n * 4, cudaMemcpyHostToDevice, q));
@@ -1106,6 +1129,7 @@ int ugkwp_adjoint_query(const ugkwp_sim* s, int32_t n_steps, size_t* bytes) {
 int ugkwp_adjoint_wave(ugkwp_sim* s, const ugkwp_adjoint_req* r, double* out) {
     if (!s || !r || !out) return fail(UGKWP_E_ARG, "NULL argument");
     if (s->P.order != 1) return fail(UGKWP_E_UNSUPPORTED, "the adjoint covers the first-order wave flux only");
+    if (s->P.K != 0) return fail(UGKWP_E_UNSUPPORTED, "the adjoint covers K = 0 only");
     if (r->n_steps < 1 || (r->functional != 0 && r->functional != 1) || r->n_wall_tags < 0 ||
         (r->n_wall_tags > 0 && !r->wall_tags))
         return fail(UGKWP_E_ARG, "invalid adjoint request");

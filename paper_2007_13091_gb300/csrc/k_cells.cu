@@ -77,7 +77,7 @@ __global__ void k_cell_prep(DevMesh m, DevState s, DevParams p) {
         const double rho = s.W[i];
         const double Ux = s.W[nc + i] / rho, Uy = s.W[2 * nc + i] / rho, Uz = s.W[3 * nc + i] / rho;
         const double U2 = (Ux * Ux + Uy * Uy) + Uz * Uz;
-        const double pr = (s.W[4 * nc + i] - 0.5 * (rho * U2)) / 1.5;
+        const double pr = (s.W[4 * nc + i] - 0.5 * (rho * U2)) / (1.5 + 0.5 * (double)p.K);
         const double T = pr / (rho * p.R);
         double tau = 1.0;
         if (!(rho > 0.0) || !(pr > 0.0) || !isfinite(pr)) {
@@ -278,7 +278,7 @@ __global__ void k_kn_gll(DevMesh m, DevState s, DevParams p, double* out) {
         for (int d = 0; d < 3; ++d) g[d] += m.lsq_c[(size_t)(3 * k + d) * nc + i] * (v - rho);
     }
     const double Ux = s.W[nc + i] / rho, Uy = s.W[2 * nc + i] / rho, Uz = s.W[3 * nc + i] / rho;
-    const double pr = (s.W[4 * nc + i] - 0.5 * (rho * ((Ux * Ux + Uy * Uy) + Uz * Uz))) / 1.5;
+    const double pr = (s.W[4 * nc + i] - 0.5 * (rho * ((Ux * Ux + Uy * Uy) + Uz * Uz))) / (1.5 + 0.5 * (double)p.K);
     const double T = pr / (rho * p.R);
     const double mu = p.mu_ref * dm::d_exp(p.omega * dm::d_log(T / p.T_ref));
     const double w = p.omega;
@@ -308,11 +308,13 @@ __global__ void k_wp_acc(DevMesh m, DevState s, DevParams p, PartBufRaw a) {
     const Real* ux = (const Real*)a.u[0];
     const Real* uy = (const Real*)a.u[1];
     const Real* uz = (const Real*)a.u[2];
+    const Real* ei = (const Real*)a.e;  // internal energy (K > 0)
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int c = a.cell[i];
         if (c < 0) continue;
         const double u0 = (double)ux[i], u1 = (double)uy[i], u2 = (double)uz[i], mm = a.m[i];
-        const double phi[5] = {mm, mm * u0, mm * u1, mm * u2, 0.5 * (mm * ((u0 * u0 + u1 * u1) + u2 * u2))};
+        const double e = ei ? (double)ei[i] : 0.0;
+        const double phi[5] = {mm, mm * u0, mm * u1, mm * u2, 0.5 * (mm * (((u0 * u0 + u1 * u1) + u2 * u2) + e))};
 #pragma unroll
         for (int q = 0; q < 5; ++q)
             atomicAdd(reinterpret_cast<unsigned long long*>(&s.wacc[(size_t)q * nc + c]),
@@ -344,7 +346,7 @@ __global__ void k_prim_out(DevMesh m, DevState s, DevParams p, double* out) {
     const double rho = s.W[i];
     const double Ux = s.W[nc + i] / rho, Uy = s.W[2 * nc + i] / rho, Uz = s.W[3 * nc + i] / rho;
     const double U2 = (Ux * Ux + Uy * Uy) + Uz * Uz;
-    const double pr = (s.W[4 * nc + i] - 0.5 * (rho * U2)) / 1.5;
+    const double pr = (s.W[4 * nc + i] - 0.5 * (rho * U2)) / (1.5 + 0.5 * (double)p.K);
     out[i] = rho;
     out[nc + i] = Ux;
     out[2 * nc + i] = Uy;

@@ -35,15 +35,34 @@ struct Side {
     double rho, rhoh, Un, Ut[3], lam, p, rl;  // rl = 1/sqrt(lambda)
 };
 
+// Constants of K internal degrees of freedom (rho E = rho |U|^2/2 + (3+K)/2 p,
+// <|xi|^2> = K theta, <|xi|^4> = K (K+2) theta^2, theta = 1/(2 lambda)); for
+// K = 0 each is the monatomic literal (2/3, 4/3, 1/3, 3, 5/2, 5, 7) exactly.
+struct KC {
+    double K, c23, c43, c13, e3, e5h, e5, e7;
+};
+__device__ __forceinline__ KC kconst(int K) {
+    KC k;
+    k.K = (double)K;
+    k.c23 = 2.0 / (3.0 + k.K);
+    k.c43 = 4.0 / (3.0 + k.K);
+    k.c13 = 1.0 / (3.0 + k.K);
+    k.e3 = 3.0 + k.K;
+    k.e5h = 0.5 * (5.0 + k.K);
+    k.e5 = 5.0 + k.K;
+    k.e7 = 7.0 + k.K;
+    return k;
+}
+
 __device__ __forceinline__ double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
 // Primitive state in the face frame; two divisions (1/rho, rho/p).
-__device__ __forceinline__ Side make_side(const double* W, double rhoh, const double* n) {
+__device__ __forceinline__ Side make_side(const double* W, double rhoh, const double* n, const KC& kc) {
     Side s;
     s.rho = W[0];
     const double ir = 1.0 / s.rho;
     const double U[3] = {W[1] * ir, W[2] * ir, W[3] * ir};
-    s.p = (W[4] - 0.5 * s.rho * dot3(U, U)) * (2.0 / 3.0);
+    s.p = (W[4] - 0.5 * s.rho * dot3(U, U)) * kc.c23;
     s.lam = 0.5 * s.rho / s.p;
     s.rl = rsqrt(s.lam);
     s.rhoh = rhoh;
@@ -72,10 +91,10 @@ __device__ __forceinline__ void moments(double Un, double lam, double rl, int ha
 // G = int_{half} u.n g psi du and H = int_{half} g psi du for a unit-density
 // Maxwellian (Un n + Ut, lambda).
 __device__ __forceinline__ void flux_moments(double Un, const double* Ut, const double* n, double lam, double rl,
-                                             int half, double G[5], double H[5]) {
+                                             int half, const KC& kc, double G[5], double H[5]) {
     double M[4];
     moments(Un, lam, rl, half, M);
-    const double tv = dot3(Ut, Ut) + rl * rl;  // |Ut|^2 + 1/lambda
+    const double tv = (dot3(Ut, Ut) + rl * rl) + kc.K * (0.5 * rl * rl);  // |Ut|^2 + 1/lambda + <|xi|^2>
     G[0] = M[1];
     H[0] = M[0];
     for (int c = 0; c < 3; ++c) {
@@ -125,14 +144,15 @@ __device__ void interior_flux(const Side& L, const Side& R, bool ghost_hydro, co
     // ghost_hydro: R is a far-field ghost emitting no particles; p.gks: no
     // particles at all (both halves of the free transport carry q4)
     double GL[5], HL[5], GR[5], HR[5];
-    flux_moments(L.Un, L.Ut, n, L.lam, L.rl, +1, GL, HL);
-    flux_moments(R.Un, R.Ut, n, R.lam, R.rl, -1, GR, HR);
+    const KC kc = kconst(p.K);
+    flux_moments(L.Un, L.Ut, n, L.lam, L.rl, +1, kc, GL, HL);
+    flux_moments(R.Un, R.Ut, n, R.lam, R.rl, -1, kc, GR, HR);
     double W0[5];
     for (int q = 0; q < 5; ++q) W0[q] = L.rho * HL[q] + R.rho * HR[q];
     const double rho0 = W0[0];
     const double ir0 = 1.0 / rho0;
     const double U0[3] = {W0[1] * ir0, W0[2] * ir0, W0[3] * ir0};
-    const double p0 = (W0[4] - 0.5 * rho0 * dot3(U0, U0)) * (2.0 / 3.0);
+    const double p0 = (W0[4] - 0.5 * rho0 * dot3(U0, U0)) * kc.c23;
     const double ip0 = 1.0 / p0;
     const double lam0 = 0.5 * rho0 * ip0;
     const double T0 = p0 * ir0 / p.R;
@@ -235,7 +255,8 @@ __global__ void __launch_bounds__(128) k_gradients(DevMesh m, DevState s, DevPar
 
 // Moment tables of a unit Maxwellian in a face frame: <u^k> (normal, over the
 // half space `half` or all u) and <v^k>, <w^k> (tangential, full), k = 0..6.
-struct Tab { double n[7], v[7], w[7]; };
+// x1 = <|xi|^2>, x2 = <|xi|^4> - <|xi|^2>^2 = 2 K theta^2 (internal degrees of freedom)
+struct Tab { double n[7], v[7], w[7], x1, x2; };
 
 __device__ __forceinline__ void gauss_mom(double mean, double h, double* M) {  // h = 1/(2 lambda)
     M[0] = 1.0;
@@ -244,8 +265,10 @@ __device__ __forceinline__ void gauss_mom(double mean, double h, double* M) {  /
     for (int k = 0; k < 5; ++k) M[k + 2] = mean * M[k + 1] + (double)(k + 1) * h * M[k];
 }
 
-__device__ __forceinline__ void make_tab(const double* U, double lam, double rl, int half, Tab& T) {
+__device__ __forceinline__ void make_tab(const double* U, double lam, double rl, int half, const KC& kc, Tab& T) {
     const double h = 0.5 * rl * rl;
+    T.x1 = kc.K * h;
+    T.x2 = 2.0 * kc.K * h * h;
     if (half == 0) {
         gauss_mom(U[0], h, T.n);
     } else {
@@ -260,17 +283,20 @@ __device__ __forceinline__ void make_tab(const double* U, double lam, double rl,
     gauss_mom(U[2], h, T.w);
 }
 
-// out_k = < u^AL v^BE w^GA (a.psi) psi_k >, psi = (1, u, v, w, |u|^2/2).
-// With a.psi = A_u(u) + A_v(v) + A_w(w), A_u = a0 + a1 u + a4 u^2/2,
+// out_k = < u^AL v^BE w^GA (a.psi) psi_k >, psi = (1, u, v, w, (|u|^2 + |xi|^2)/2).
+// With a.psi = A_u(u) + A_v(v) + A_w(w) + a4 |xi|^2/2, A_u = a0 + a1 u + a4 u^2/2,
 // A_v = a2 v + a4 v^2/2, A_w = a3 w + a4 w^2/2, every moment factorises into
-// 1D tables: <u^x v^y w^z a.psi> = NA_x v_y w_z + n_x (VA_y w_z + v_y WA_z).
+// 1D tables: <u^x v^y w^z a.psi> = NA_x v_y w_z + n_x (VA_y w_z + v_y WA_z),
+// the xi part averaged into a0 (a0 + a4 <|xi|^2>/2) and, for psi_4, the
+// moment <|xi|^2 a.psi>/2 = (x1 SS_000 + a4/2 x2 n v w)/2.
 template <int AL, int BE, int GA>
 __device__ __forceinline__ void apsi(const Tab& T, const double* a, double out[5]) {
     const double h4 = 0.5 * a[4];
+    const double a0 = a[0] + h4 * T.x1;
     double NA[3], VA[3], WA[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        NA[i] = a[0] * T.n[AL + i] + a[1] * T.n[AL + i + 1] + h4 * T.n[AL + i + 2];
+        NA[i] = a0 * T.n[AL + i] + a[1] * T.n[AL + i + 1] + h4 * T.n[AL + i + 2];
         VA[i] = a[2] * T.v[BE + i + 1] + h4 * T.v[BE + i + 2];
         WA[i] = a[3] * T.w[GA + i + 1] + h4 * T.w[GA + i + 2];
     }
@@ -280,7 +306,8 @@ __device__ __forceinline__ void apsi(const Tab& T, const double* a, double out[5
     out[1] = SS(1, 0, 0);
     out[2] = SS(0, 1, 0);
     out[3] = SS(0, 0, 1);
-    out[4] = 0.5 * (SS(2, 0, 0) + SS(0, 2, 0) + SS(0, 0, 2));
+    out[4] = 0.5 * ((SS(2, 0, 0) + SS(0, 2, 0) + SS(0, 0, 2)) +
+                    (T.x1 * out[0] + h4 * T.x2 * (T.n[AL] * T.v[BE] * T.w[GA])));
 #undef SS
 }
 
@@ -291,7 +318,7 @@ __device__ __forceinline__ void psi_mom(const Tab& T, double out[5]) {
     out[1] = T.n[AL + 1];
     out[2] = T.n[AL] * T.v[1];
     out[3] = T.n[AL] * T.w[1];
-    out[4] = 0.5 * (T.n[AL + 2] + T.n[AL] * (T.v[2] + T.w[2]));
+    out[4] = 0.5 * (T.n[AL + 2] + T.n[AL] * ((T.v[2] + T.w[2]) + T.x1));
 }
 
 // <u_n u_d (a.psi) psi> for frame direction d (0 normal, 1 t1, 2 t2)
@@ -305,15 +332,16 @@ __device__ __forceinline__ void slope_mom(const Tab& T, int d, const double* a, 
 // in closed form: with theta = 1/(2 lambda), R_i = b_i - U_i b_0,
 // R_4 = 2 b_4 - (|U|^2 + 3 theta) b_0:  a_4 = 4 lambda^2/3 (R_4 - 2 U.R),
 // a_i = 2 lambda R_i - U_i a_4,  a_0 = b_0 - U.a - a_4 (|U|^2 + 3 theta)/2.
-__device__ __forceinline__ void micro(const double* U, double lam, double th, const double* b, double* a) {
+__device__ __forceinline__ void micro(const double* U, double lam, double th, const double* b, double* a,
+                                      const KC& kc) {
     const double R1 = b[1] - U[0] * b[0], R2 = b[2] - U[1] * b[0], R3 = b[3] - U[2] * b[0];
     const double U2 = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
-    const double R4 = 2.0 * b[4] - (U2 + 3.0 * th) * b[0];
-    a[4] = (4.0 / 3.0) * lam * lam * (R4 - 2.0 * (U[0] * R1 + U[1] * R2 + U[2] * R3));
+    const double R4 = 2.0 * b[4] - (U2 + kc.e3 * th) * b[0];
+    a[4] = kc.c43 * lam * lam * (R4 - 2.0 * (U[0] * R1 + U[1] * R2 + U[2] * R3));
     a[1] = 2.0 * lam * R1 - U[0] * a[4];
     a[2] = 2.0 * lam * R2 - U[1] * a[4];
     a[3] = 2.0 * lam * R3 - U[2] * a[4];
-    a[0] = b[0] - (U[0] * a[1] + U[1] * a[2] + U[2] * a[3]) - 0.5 * a[4] * (U2 + 3.0 * th);
+    a[0] = b[0] - (U[0] * a[1] + U[1] * a[2] + U[2] * a[3]) - 0.5 * a[4] * (U2 + kc.e3 * th);
 }
 
 // All time coefficients: q1, q2, q3, q4, a4, a5 in closed form from one
@@ -379,19 +407,19 @@ __device__ __forceinline__ void frame_slope(const double* gW, int nc, int c, con
 // The face frame has the normal as direction 0.
 struct DPrim { double dr, dU[3], dth, UdU; };
 
-__device__ __forceinline__ DPrim dprim(const double* U, double th, double U2, const double* b) {
+__device__ __forceinline__ DPrim dprim(const double* U, double th, double U2, const double* b, const KC& kc) {
     DPrim q;
     q.dr = b[0];
     for (int j = 0; j < 3; ++j) q.dU[j] = b[1 + j] - U[j] * b[0];
     q.UdU = U[0] * q.dU[0] + U[1] * q.dU[1] + U[2] * q.dU[2];
-    q.dth = ((2.0 * b[4] - (U2 + 3.0 * th) * b[0]) - 2.0 * q.UdU) * (1.0 / 3.0);
+    q.dth = ((2.0 * b[4] - (U2 + kc.e3 * th) * b[0]) - 2.0 * q.UdU) * kc.c13;
     return q;
 }
 
 // dF_D(b) (Euler flux Jacobian along frame direction D applied to b)
 template <int D>
 __device__ __forceinline__ void euler_jac(const double* U, double th, double U2, const double* b, const DPrim& q,
-                                          double out[5]) {
+                                          const KC& kc, double out[5]) {
     out[0] = b[1 + D];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -399,12 +427,13 @@ __device__ __forceinline__ void euler_jac(const double* U, double th, double U2,
         if (j == D) v += q.dr * th + q.dth;
         out[1 + j] = v;
     }
-    out[4] = b[1 + D] * (0.5 * U2 + 2.5 * th) + U[D] * (q.UdU + 2.5 * q.dth);
+    out[4] = b[1 + D] * (0.5 * U2 + kc.e5h * th) + U[D] * (q.UdU + kc.e5h * q.dth);
 }
 
 // dQ_D(b) = <u_n u_D (a.psi) psi>
 template <int D>
-__device__ __forceinline__ void q_jac(const double* U, double th, double U2, const DPrim& q, double out[5]) {
+__device__ __forceinline__ void q_jac(const double* U, double th, double U2, const DPrim& q, const KC& kc,
+                                      double out[5]) {
     const double un_ud = U[0] * U[D];
     const double d_un_ud = q.dU[0] * U[D] + U[0] * q.dU[D];
     out[0] = q.dr * un_ud + d_un_ud;
@@ -418,11 +447,12 @@ __device__ __forceinline__ void q_jac(const double* U, double th, double U2, con
         if (D == 0) { s += U[j]; ds += q.dU[j]; }
         out[1 + j] = q.dr * (un_ud * U[j] + th * s) + d_un_ud * U[j] + un_ud * q.dU[j] + q.dth * s + th * ds;
     }
-    const double A = U2 + 7.0 * th;
-    double v = q.dr * (0.5 * un_ud * A) + 0.5 * (d_un_ud * A + un_ud * (2.0 * q.UdU + 7.0 * q.dth));
+    // <u_i u_j (|u|^2 + |xi|^2)> = U_i U_j (|U|^2 + (7+K) theta) + d_ij theta (|U|^2 + (5+K) theta)
+    const double A = U2 + kc.e7 * th;
+    double v = q.dr * (0.5 * un_ud * A) + 0.5 * (d_un_ud * A + un_ud * (2.0 * q.UdU + kc.e7 * q.dth));
     if (D == 0) {
-        const double Bq = U2 + 5.0 * th;
-        v += q.dr * (0.5 * th * Bq) + 0.5 * (q.dth * Bq + th * (2.0 * q.UdU + 5.0 * q.dth));
+        const double Bq = U2 + kc.e5 * th;
+        v += q.dr * (0.5 * th * Bq) + 0.5 * (q.dth * Bq + th * (2.0 * q.UdU + kc.e5 * q.dth));
     }
     out[4] = v;
 }
@@ -438,19 +468,20 @@ struct SideOut {
 };
 
 __device__ __forceinline__ SideOut side_o2(const DevMesh& m, const DevState& s, int c, const double* dx,
-                                           const double R[3][3], int half, double B[3][5], bool first) {
+                                           const double R[3][3], int half, double B[3][5], bool first,
+                                           const KC& kc) {
     const int nc = m.nc;
     double Wf[5];
     for (int q = 0; q < 5; ++q)
         Wf[q] = s.W[(size_t)q * nc + c] + s.gradW[(size_t)(3 * q) * nc + c] * dx[0] +
                 s.gradW[(size_t)(3 * q + 1) * nc + c] * dx[1] + s.gradW[(size_t)(3 * q + 2) * nc + c] * dx[2];
     double rh = s.rhoh[c] + s.gradH[c] * dx[0] + s.gradH[nc + c] * dx[1] + s.gradH[2 * nc + c] * dx[2];
-    double pr = (Wf[4] - 0.5 * (Wf[1] * Wf[1] + Wf[2] * Wf[2] + Wf[3] * Wf[3]) / Wf[0]) * (2.0 / 3.0);
+    double pr = (Wf[4] - 0.5 * (Wf[1] * Wf[1] + Wf[2] * Wf[2] + Wf[3] * Wf[3]) / Wf[0]) * kc.c23;
     const bool o2 = Wf[0] > 0.0 && pr > 0.0;
     if (!o2) {
         for (int q = 0; q < 5; ++q) Wf[q] = s.W[(size_t)q * nc + c];
         rh = s.rhoh[c];
-        pr = (Wf[4] - 0.5 * (Wf[1] * Wf[1] + Wf[2] * Wf[2] + Wf[3] * Wf[3]) / Wf[0]) * (2.0 / 3.0);
+        pr = (Wf[4] - 0.5 * (Wf[1] * Wf[1] + Wf[2] * Wf[2] + Wf[3] * Wf[3]) / Wf[0]) * kc.c23;
     }
     SideOut o;
     double W[5];
@@ -466,7 +497,7 @@ __device__ __forceinline__ SideOut side_o2(const DevMesh& m, const DevState& s, 
     const double rl = rsqrt(lam);
     const double th = 0.5 * rl * rl;
     Tab T;
-    make_tab(U, lam, rl, half, T);
+    make_tab(U, lam, rl, half, kc, T);
     psi_mom<0>(T, o.H);
     psi_mom<1>(T, o.G);
     for (int k = 0; k < 5; ++k) o.S[k] = 0.0;
@@ -482,7 +513,7 @@ __device__ __forceinline__ SideOut side_o2(const DevMesh& m, const DevState& s, 
         const double gh = s.gradH[c] * R[dd][0] + s.gradH[nc + c] * R[dd][1] + s.gradH[2 * nc + c] * R[dd][2];
         const double gr = (gh - ratio * dW[0]) * ir;
         for (int q = 0; q < 5; ++q) b[q] = ratio * dW[q] + W[q] * gr;
-        micro(U, lam, th, b, a);
+        micro(U, lam, th, b, a, kc);
         slope_mom(T, dd, a, sm);
         for (int k = 0; k < 5; ++k) o.S[k] += sm[k];
     }
@@ -501,13 +532,14 @@ __device__ void interior_flux_o2(const DevMesh& m, const DevState& s, const DevP
         dxR[d] = m.lsq_dxf[(size_t)(3 * ((lk >> 2) & 3) + d) * nc + nb];
     }
     double B[3][5];
-    const SideOut L = side_o2(m, s, o, dxL, R, +1, B, true);
-    const SideOut Rs = side_o2(m, s, nb, dxR, R, -1, B, false);
+    const KC kc = kconst(p.K);
+    const SideOut L = side_o2(m, s, o, dxL, R, +1, B, true, kc);
+    const SideOut Rs = side_o2(m, s, nb, dxR, R, -1, B, false, kc);
     double W0[5];
     for (int k = 0; k < 5; ++k) W0[k] = L.rho * L.H[k] + Rs.rho * Rs.H[k];
     const double rho0 = W0[0], ir0 = 1.0 / rho0;
     const double U0[3] = {W0[1] * ir0, W0[2] * ir0, W0[3] * ir0};
-    const double p0 = (W0[4] - 0.5 * rho0 * dot3(U0, U0)) * (2.0 / 3.0);
+    const double p0 = (W0[4] - 0.5 * rho0 * dot3(U0, U0)) * kc.c23;
     const double T0 = p0 * ir0 / p.R;
     double tau = p.mu_ref * exp(p.omega * log(T0 * inv_Tref)) / p0;
     if (p.C2 > 0.0) tau += p.C2 * fabs(L.p - Rs.p) / fabs(L.p + Rs.p) * dt;
@@ -526,29 +558,29 @@ __device__ void interior_flux_o2(const DevMesh& m, const DevState& s, const DevP
     Fe[4] = qc.q1 * U0[0] * (W0[4] + p0);
     double Wt[5], t5[5];
     {
-        const DPrim q = dprim(U0, th0, U20, B[0]);
-        q_jac<0>(U0, th0, U20, q, t5);
+        const DPrim q = dprim(U0, th0, U20, B[0], kc);
+        q_jac<0>(U0, th0, U20, q, kc, t5);
         for (int k = 0; k < 5; ++k) Fe[k] += qc.q2 * t5[k];
-        euler_jac<0>(U0, th0, U20, B[0], q, t5);
+        euler_jac<0>(U0, th0, U20, B[0], q, kc, t5);
         for (int k = 0; k < 5; ++k) Wt[k] = -t5[k];
     }
     {
-        const DPrim q = dprim(U0, th0, U20, B[1]);
-        q_jac<1>(U0, th0, U20, q, t5);
+        const DPrim q = dprim(U0, th0, U20, B[1], kc);
+        q_jac<1>(U0, th0, U20, q, kc, t5);
         for (int k = 0; k < 5; ++k) Fe[k] += qc.q2 * t5[k];
-        euler_jac<1>(U0, th0, U20, B[1], q, t5);
+        euler_jac<1>(U0, th0, U20, B[1], q, kc, t5);
         for (int k = 0; k < 5; ++k) Wt[k] -= t5[k];
     }
     {
-        const DPrim q = dprim(U0, th0, U20, B[2]);
-        q_jac<2>(U0, th0, U20, q, t5);
+        const DPrim q = dprim(U0, th0, U20, B[2], kc);
+        q_jac<2>(U0, th0, U20, q, kc, t5);
         for (int k = 0; k < 5; ++k) Fe[k] += qc.q2 * t5[k];
-        euler_jac<2>(U0, th0, U20, B[2], q, t5);
+        euler_jac<2>(U0, th0, U20, B[2], q, kc, t5);
         for (int k = 0; k < 5; ++k) Wt[k] -= t5[k];
     }
     {
-        const DPrim q = dprim(U0, th0, U20, Wt);
-        euler_jac<0>(U0, th0, U20, Wt, q, t5);
+        const DPrim q = dprim(U0, th0, U20, Wt, kc);
+        euler_jac<0>(U0, th0, U20, Wt, q, kc, t5);
         for (int k = 0; k < 5; ++k) Fe[k] += qc.q3 * t5[k];
     }
     if (p.pr_fix != 0.0) {
@@ -584,27 +616,28 @@ __global__ void __launch_bounds__(128) k_gp_coef(DevMesh m, DevState s, DevParam
     const double sig = sqrt(th);
     const double U2 = dot3(U, U);
     const double ir = 1.0 / rho;
+    const KC kc = kconst(p.K);
     double bd[3][5], a[3][5], Wt[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, t5[5];
     for (int d = 0; d < 3; ++d)
         for (int q = 0; q < 5; ++q) bd[d][q] = s.gradW[(size_t)(3 * q + d) * nc + i] * ir;
     {
-        const DPrim q = dprim(U, th, U2, bd[0]);
-        euler_jac<0>(U, th, U2, bd[0], q, t5);
+        const DPrim q = dprim(U, th, U2, bd[0], kc);
+        euler_jac<0>(U, th, U2, bd[0], q, kc, t5);
         for (int k = 0; k < 5; ++k) Wt[k] -= t5[k];
     }
     {
-        const DPrim q = dprim(U, th, U2, bd[1]);
-        euler_jac<1>(U, th, U2, bd[1], q, t5);
+        const DPrim q = dprim(U, th, U2, bd[1], kc);
+        euler_jac<1>(U, th, U2, bd[1], q, kc, t5);
         for (int k = 0; k < 5; ++k) Wt[k] -= t5[k];
     }
     {
-        const DPrim q = dprim(U, th, U2, bd[2]);
-        euler_jac<2>(U, th, U2, bd[2], q, t5);
+        const DPrim q = dprim(U, th, U2, bd[2], kc);
+        euler_jac<2>(U, th, U2, bd[2], q, kc, t5);
         for (int k = 0; k < 5; ++k) Wt[k] -= t5[k];
     }
     double B[5];
-    for (int d = 0; d < 3; ++d) micro(U, lam, th, bd[d], a[d]);
-    micro(U, lam, th, Wt, B);
+    for (int d = 0; d < 3; ++d) micro(U, lam, th, bd[d], a[d], kc);
+    micro(U, lam, th, Wt, B, kc);
     // P(u) = B0 + v.u + u^T K u + (h/2)|u|^2 + (|u|^2/2)(beta.u), K[d][j] = a_d,1+j
     double v[3], beta[3];
     const double h = B[4];
@@ -682,12 +715,13 @@ __global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevPar
     const double dt = p.gks == 2 ? (nb >= 0 ? fmin(s.dtc[o], s.dtc[nb]) : s.dtc[o]) : s.dt[0];
     double WL[5];
     for (int q = 0; q < 5; ++q) WL[q] = s.W[(size_t)q * nc + o];
-    const Side L = make_side(WL, s.rhoh[o], n);
+    const KC kc = kconst(p.K);
+    const Side L = make_side(WL, s.rhoh[o], n, kc);
     double F[5];
     if (nb >= 0) {
         double WR[5];
         for (int q = 0; q < 5; ++q) WR[q] = s.W[(size_t)q * nc + nb];
-        const Side R = make_side(WR, s.rhoh[nb], n);
+        const Side R = make_side(WR, s.rhoh[nb], n, kc);
         interior_flux(L, R, false, n, dt, p, inv_Tref, F);
     } else {
         const DevBc& bc = p.bc[m.bf_tag[-1 - nb]];
@@ -695,7 +729,7 @@ __global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevPar
             double q1, q4, a4;
             time_coeffs(dt, s.tau[o], q1, q4, a4);
             double GL[5], HL[5], Gin[5];
-            flux_moments(L.Un, L.Ut, n, L.lam, L.rl, +1, GL, HL);
+            flux_moments(L.Un, L.Ut, n, L.lam, L.rl, +1, kc, GL, HL);
             const double c4 = p.gks ? q4 : a4;
             for (int k = 0; k < 5; ++k) Gin[k] = q1 * (L.rho * GL[k]) + c4 * (L.rhoh * GL[k]);
             const double lamw = 1.0 / (2.0 * p.R * bc.T_w);
@@ -703,7 +737,7 @@ __global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevPar
             double Uwt[3];
             for (int c = 0; c < 3; ++c) Uwt[c] = bc.U_w[c] - Uwn * n[c];
             double Gw[5], Hw[5];
-            flux_moments(Uwn, Uwt, n, lamw, rsqrt(lamw), -1, Gw, Hw);
+            flux_moments(Uwn, Uwt, n, lamw, rsqrt(lamw), -1, kc, Gw, Hw);
             const double rhow = -Gin[0] / (dt * Gw[0]);
             for (int k = 0; k < 5; ++k) F[k] = Gin[k] + dt * rhow * Gw[k];
         } else if (bc.type == UGKWP_BC_SPECULAR) {
@@ -716,7 +750,7 @@ __global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevPar
             F[4] = 0.0;
             for (int c = 0; c < 3; ++c) F[1 + c] = fn * n[c];
         } else {
-            Side R = (bc.type == UGKWP_BC_FARFIELD) ? make_side(bc.W_in, bc.W_in[0], n) : L;
+            Side R = (bc.type == UGKWP_BC_FARFIELD) ? make_side(bc.W_in, bc.W_in[0], n, kc) : L;
             R.rhoh = R.rho;
             interior_flux(L, R, true, n, dt, p, inv_Tref, F);
         }

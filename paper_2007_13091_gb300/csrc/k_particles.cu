@@ -27,7 +27,7 @@ constexpr unsigned FULL = 0xffffffffu;
 #ifndef UGKWP_TRACK_MIN_BLOCKS
 #define UGKWP_TRACK_MIN_BLOCKS (1024 / UGKWP_TRACK_THREADS)
 #endif
-enum : unsigned long long { TAG_TF = 1, TAG_SVEL = 2, TAG_SPOS = 3, TAG_WALL = 4, TAG_GP = 5 };
+enum : unsigned long long { TAG_TF = 1, TAG_SVEL = 2, TAG_SPOS = 3, TAG_WALL = 4, TAG_GP = 5, TAG_SINT = 6, TAG_WINT = 7 };
 
 __device__ __forceinline__ void set_err(const DevState& s, int32_t bits) {
     atomicOr(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_ERR]), (unsigned long long)bits);
@@ -46,6 +46,8 @@ template <class Real> __device__ __forceinline__ PartView<Real> view(const PartB
     v.m = r.m;
     v.cell = r.cell;
     v.id = r.id;
+    v.e = (Real*)r.e;
+    v.e2 = (Real*)r.e2;
     return v;
 }
 
@@ -74,6 +76,46 @@ __device__ __forceinline__ void pair_normals(unsigned long long ida, long long s
         dm::d_sincos2pi(dm::u01d(r.d), &sn, &cs);
         X[2] = rad * cs;
     }
+}
+
+// Internal energy of a particle with K internal degrees of freedom at spread
+// sig = sqrt(RT): e = sum_{i<K} (sig N_i)^2, the normals by Box-Muller from
+// Philox counters (id, step, tag, idx0 + j), four per counter, summed in
+// order in the particle precision.
+template <class Real>
+__device__ __forceinline__ Real internal_energy(unsigned long long id, long long step, unsigned long long tag,
+                                                unsigned long long idx0, int K, Real sig, unsigned long long seed) {
+    Real e = (Real)0;
+    for (int j = 0; 4 * j < K; ++j) {
+        const dm::U4 r = dm::philox(id, (unsigned long long)step, tag, idx0 + (unsigned long long)j, seed, 0ULL);
+        Real N[4];
+        if constexpr (sizeof(Real) == 4) {
+            float sn, cs;
+            float rad = sqrtf(-2.0f * dm::f_log(dm::u01f(r.a)));
+            dm::f_sincos2pi(dm::u01f(r.b), &sn, &cs);
+            N[0] = rad * cs;
+            N[1] = rad * sn;
+            rad = sqrtf(-2.0f * dm::f_log(dm::u01f(r.c)));
+            dm::f_sincos2pi(dm::u01f(r.d), &sn, &cs);
+            N[2] = rad * cs;
+            N[3] = rad * sn;
+        } else {
+            double sn, cs;
+            double rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.a)));
+            dm::d_sincos2pi(dm::u01d(r.b), &sn, &cs);
+            N[0] = rad * cs;
+            N[1] = rad * sn;
+            rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.c)));
+            dm::d_sincos2pi(dm::u01d(r.d), &sn, &cs);
+            N[2] = rad * cs;
+            N[3] = rad * sn;
+        }
+        for (int i = 0; i < 4 && 4 * j + i < K; ++i) {
+            const Real si = sig * N[i];
+            e = e + si * si;
+        }
+    }
+    return e;
 }
 
 // First-order g_p sampling: X ~ N(0, I) (1 + phi(X)) for particle `id` by
@@ -204,6 +246,7 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
             b.m[j] = s.msam[cell];
             b.cell[j] = cell;
             b.id[j] = id;
+            if (p.K > 0) b.e[j] = internal_energy<float>(id, step, TAG_SINT, 0ULL, p.K, us.w, p.seed);
             continue;
         }
         const double U[3] = {s.prim[nc + cell], s.prim[2 * nc + cell], s.prim[3 * nc + cell]};
@@ -239,6 +282,7 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
         b.m[j] = s.msam[cell];
         b.cell[j] = cell;
         b.id[j] = id;
+        if (p.K > 0) b.e[j] = (Real)internal_energy<double>(id, step, TAG_SINT, 0ULL, p.K, sig, p.seed);
     }
 }
 
@@ -331,13 +375,13 @@ __device__ __forceinline__ double widen(double d) { return d; }
 // Fixed-point image of phi = m (1, u, |u|^2/2); false if a value leaves |v| < 2^62.
 // The factor 1/2 of the energy is applied as an exponent shift.
 template <class Real>
-__device__ __forceinline__ bool phi_q(const Real* u, double mm, const DevParams& p, long long q[5]) {
+__device__ __forceinline__ bool phi_q(const Real* u, Real e, double mm, const DevParams& p, long long q[5]) {
     const double u0 = widen(u[0]), u1 = widen(u[1]), u2 = widen(u[2]);
     bool ok = fixed_of(mm, p.exps[0], q[0]);
     ok &= fixed_of(mm * u0, p.exps[1], q[1]);
     ok &= fixed_of(mm * u1, p.exps[2], q[2]);
     ok &= fixed_of(mm * u2, p.exps[3], q[3]);
-    ok &= fixed_of(mm * ((u0 * u0 + u1 * u1) + u2 * u2), p.exps[4] + 1, q[4]);
+    ok &= fixed_of(mm * (((u0 * u0 + u1 * u1) + u2 * u2) + widen(e)), p.exps[4] + 1, q[4]);
     return ok;
 }
 
@@ -373,7 +417,8 @@ __device__ __forceinline__ bool fixed_of_mass(double m, int e, long long& q) {
     return true;
 }
 
-template <class Real>
+// KE: the particles carry an internal energy (K > 0)
+template <class Real, bool KE>
 __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br,
                                                                      PartBufRaw nr, PartBufRaw ar) {
     if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
@@ -406,6 +451,7 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
         bool survivor = false, mover = false, exited = false;
         Real us[3] = {(Real)0, (Real)0, (Real)0}, ue[3] = {(Real)0, (Real)0, (Real)0};
         Real xe[3] = {(Real)0, (Real)0, (Real)0};
+        Real es = (Real)0, ee = (Real)0;  // internal energy at start and end (KE)
         double mm = 0.0;
         unsigned long long id = 0;
         if (valid) {
@@ -415,6 +461,10 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
 #pragma unroll
             for (int c = 0; c < 3; ++c) { x0[c] = b.x[c][i]; u[c] = b.u[c][i]; }
             mm = b.m[i];
+            if constexpr (KE) {
+                es = b.e[i];
+                ee = es;
+            }
 #pragma unroll
             for (int c = 0; c < 3; ++c) us[c] = u[c];
             Real t_end = dtR;
@@ -498,6 +548,9 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
                         for (int c = 0; c < 3; ++c)
                             u[c] = ((-vn) * m.bf_f[(size_t)c * nbf + bi] + v1 * m.bf_f[(size_t)(3 + c) * nbf + bi]) +
                                    v2 * m.bf_f[(size_t)(6 + c) * nbf + bi];
+                        if constexpr (KE)
+                            ee = internal_energy<float>(id, step, TAG_WINT, 2ULL * (unsigned long long)nwall, p.K, bc.sw_f,
+                                                        p.seed);
                     } else {
                         const double vn = sqrt(-2.0 * p.R * bc.T_w * dm::d_log(dm::u01d(r.a)));
                         const double rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.b)));
@@ -516,6 +569,9 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
                         const double v2 = ((bc.U_w[0] * t2[0] + bc.U_w[1] * t2[1]) + bc.U_w[2] * t2[2]) + sw * (rad * sn);
 #pragma unroll
                         for (int c = 0; c < 3; ++c) u[c] = (Real)(((-vn) * n3[c] + v1 * t1[c]) + v2 * t2[c]);
+                        if constexpr (KE)
+                            ee = (Real)internal_energy<double>(id, step, TAG_WINT, 2ULL * (unsigned long long)nwall, p.K,
+                                                               sw, p.seed);
                     }
                     ++nwall;
                 }
@@ -599,6 +655,7 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
             nxt.m[j] = mm;
             nxt.cell[j] = tet;
             nxt.id[j] = id;
+            if constexpr (KE) nxt.e[j] = ee;
         }
         if (mover) {
             const long long j = sh_base + sh_cnt[warp] + __popc(mmask & ((1u << lane) - 1u));
@@ -610,6 +667,10 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
             mv.m[j] = mm;
             mv.cell[j] = c0;
             mv.id[j] = ((unsigned long long)(unsigned)tet << 1) | (exited ? 1ULL : 0ULL);
+            if constexpr (KE) {
+                mv.e[j] = es;
+                mv.e2[j] = ee;
+            }
         }
         __syncthreads();  // sh_cnt / sh_base / sh_tile are reused next iteration
     }
@@ -653,8 +714,9 @@ __global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams
         const int c1 = (int)(code >> 1);
         const bool exited = code & 1ULL;
         long long q0[5], q1[5];
-        bool ok = phi_q(us, mm, p, q0);
-        ok &= phi_q(ue, mm, p, q1);
+        const Real es = mv.e ? mv.e[j] : (Real)0, ee = mv.e2 ? mv.e2[j] : (Real)0;
+        bool ok = phi_q(us, es, mm, p, q0);
+        ok &= phi_q(ue, ee, mm, p, q1);
         if (!ok) set_err(s, ERRB_FIXED_OVERFLOW);
 #pragma unroll
         for (int q = 0; q < 5; ++q)
@@ -683,8 +745,13 @@ void launch_sample_scale(const DevMesh& m, const DevState& s, const DevParams& p
 
 void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b, const PartBufRaw& nxt,
                   const PartBufRaw& movers, int blocks, cudaStream_t st) {
-    if (p.precision == UGKWP_MIXED) k_track<float><<<blocks, UGKWP_TRACK_THREADS, 0, st>>>(m, s, p, b, nxt, movers);
-    else k_track<double><<<blocks, UGKWP_TRACK_THREADS, 0, st>>>(m, s, p, b, nxt, movers);
+    if (p.precision == UGKWP_MIXED) {
+        if (p.K > 0) k_track<float, true><<<blocks, UGKWP_TRACK_THREADS, 0, st>>>(m, s, p, b, nxt, movers);
+        else k_track<float, false><<<blocks, UGKWP_TRACK_THREADS, 0, st>>>(m, s, p, b, nxt, movers);
+    } else {
+        if (p.K > 0) k_track<double, true><<<blocks, UGKWP_TRACK_THREADS, 0, st>>>(m, s, p, b, nxt, movers);
+        else k_track<double, false><<<blocks, UGKWP_TRACK_THREADS, 0, st>>>(m, s, p, b, nxt, movers);
+    }
 }
 
 void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a, int blocks, cudaStream_t st) {

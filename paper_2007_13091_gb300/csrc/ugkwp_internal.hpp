@@ -60,6 +60,8 @@ struct DevParams {
     int32_t sampling;      // UGKWP_SAMPLE_*
     int32_t averaging;     // add dt W^{n+1} to the time-average sums
     int32_t gks;           // 0: UGKWP step; 1: GKS step (no particles); 2: GKS step, local time steps
+    int32_t K;             // internal degrees of freedom
+    int32_t kpad_;
     uint64_t seed;
     int64_t capacity;
     int32_t exps[5];
@@ -117,6 +119,8 @@ template <class Real> struct PartView {
     double* m;
     int32_t* cell;
     uint64_t* id;
+    Real* e;   // internal energy (K > 0; NULL otherwise)
+    Real* e2;  // mover list only: internal energy at the end
 };
 
 struct PartBufRaw {
@@ -125,6 +129,8 @@ struct PartBufRaw {
     double* m;
     int32_t* cell;
     uint64_t* id;
+    void* e;
+    void* e2;
 };
 
 struct DevState {

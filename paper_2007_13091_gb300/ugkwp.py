@@ -50,7 +50,7 @@ class Params(ctypes.Structure):
                 ("C2", ctypes.c_double), ("venkat_K", ctypes.c_double), ("order", ctypes.c_int32),
                 ("N_ref", ctypes.c_int32), ("N_min", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("max_crossings", ctypes.c_int32), ("n_bc", ctypes.c_int32), ("sampling", ctypes.c_int32),
-                ("reserved_", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("K", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("particle_capacity", ctypes.c_int64), ("bc", Bc * 16)]
 
 
@@ -80,7 +80,7 @@ class State(ctypes.Structure):
     _fields_ = [("n_particles", ctypes.c_int64), ("step", ctypes.c_int64), ("t", ctypes.c_double),
                 ("exps", ctypes.c_int32 * 5), ("reserved", ctypes.c_int32), ("W", ctypes.c_void_p),
                 ("id", ctypes.c_void_p), ("cell", ctypes.c_void_p), ("x", ctypes.c_void_p),
-                ("u", ctypes.c_void_p), ("m", ctypes.c_void_p)]
+                ("u", ctypes.c_void_p), ("m", ctypes.c_void_p), ("e", ctypes.c_void_p)]
 
 
 class AdjointReq(ctypes.Structure):
@@ -178,6 +178,7 @@ def make_params(p: dict) -> Params:
     o.particle_capacity = int(p["particle_capacity"])
     o.n_bc = len(p["bc"])
     o.sampling = SAMPLING[p.get("sampling", "maxwell")]
+    o.K = int(p.get("K", 0))
     for k, b in enumerate(p["bc"]):
         c = o.bc[k]
         c.type = BC_TYPES[b["type"]]
@@ -265,10 +266,10 @@ def ugkwp_export_state(sim, n_cells: int) -> dict:
     info = ugkwp_state_info(sim)
     n = info.n_particles
     out = {"W": np.empty((5, n_cells)), "id": np.empty(n, dtype=np.uint64), "cell": np.empty(n, dtype=np.int32),
-           "x": np.empty((3, n)), "u": np.empty((3, n)), "m": np.empty(n)}
+           "x": np.empty((3, n)), "u": np.empty((3, n)), "m": np.empty(n), "e": np.empty(n)}
     st = State()
     st.n_particles = n
-    for k in ("W", "id", "cell", "x", "u", "m"):
+    for k in ("W", "id", "cell", "x", "u", "m", "e"):
         setattr(st, k, out[k].ctypes.data)
     _check(lib().ugkwp_export_state(sim, ctypes.byref(st)))
     out.update(step=int(st.step), t=float(st.t), exps=np.array(list(st.exps), dtype=np.int64))
@@ -282,6 +283,8 @@ def ugkwp_import_state(sim, state: dict):
             "x": np.ascontiguousarray(state["x"], dtype=np.float64),
             "u": np.ascontiguousarray(state["u"], dtype=np.float64),
             "m": np.ascontiguousarray(state["m"], dtype=np.float64)}
+    if state.get("e") is not None:
+        arrs["e"] = np.ascontiguousarray(state["e"], dtype=np.float64)
     st = State()
     st.n_particles = arrs["id"].size
     st.step = int(state["step"])

@@ -40,7 +40,9 @@ def assert_fields_close(Wg, Wo, tol):
 
 def _sorted(st):
     o = np.argsort(st["id"], kind="stable")
-    return {"id": st["id"][o], "cell": st["cell"][o], "x": st["x"][:, o], "u": st["u"][:, o], "m": st["m"][o]}
+    e = st.get("e")
+    return {"id": st["id"][o], "cell": st["cell"][o], "x": st["x"][:, o], "u": st["u"][:, o], "m": st["m"][o],
+            "e": None if e is None else np.asarray(e)[o]}
 
 
 def assert_particles_equal(g, o):
@@ -51,6 +53,8 @@ def assert_particles_equal(g, o):
     assert np.array_equal(a["m"], b["m"])
     assert np.array_equal(a["x"], b["x"])
     assert np.array_equal(a["u"], b["u"])
+    if a["e"] is not None and b["e"] is not None:
+        assert np.array_equal(a["e"], b["e"])
 
 
 def compare_step(gsim, osim, check_flux=True):
@@ -228,6 +232,25 @@ def test_gp1_sampling_limited_wave():
     # particles and sums bit for bit; the wave flux of this steep unlimited
     # profile is checked through the fields only
     compare_step(gsim, o, check_flux=False)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("order", [1, 2])
+def test_internal_degrees_of_freedom_teacher_forced(precision, order):
+    """K = 2 (diatomic): wave moments with |xi|^2, particles carrying internal
+    energies (sampled, kept, re-drawn at the diffuse walls), the energy flux
+    in fixed point; particles and their internal energies bit for bit."""
+    cfg = wl.cavity(n=6, N_ref=40, precision=precision, order=order, K=2)
+    gsim, osim = run_teacher_forced(cfg, warm_steps=3)
+    c = osim.last("counters")
+    assert c["n_wall_hits"] > 0 and c["n_sampled"] > 0
+    assert np.all(osim.state()["e"] > 0.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_internal_degrees_of_freedom_shock_tube(precision):
+    cfg = _order2(wl.shock_tube(precision=precision, K=5), K=1.0)
+    run_teacher_forced(cfg, warm_steps=3)
 
 
 def test_specular_box_degenerate_starts():
