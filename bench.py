@@ -15,6 +15,7 @@ int64 fixed-point particle flux).  A step is one full UGKWP time step.
   adjoint    the frozen-particle wave adjoint on a channel
   gks_start_up the particle-free start-up steps, global and local time steps
   gp1_sampling the workload with first-order g_p sampling
+  diatomic   the workload with K = 2 internal degrees of freedom
   cpu_baseline the CPU oracle (single thread) on a bounded sample
 
 Multi-GPU: replicas only (each rank runs its own simulation; value = all
@@ -367,6 +368,25 @@ def gp1_sampling(device, steps, warmup, launch_cfg):
             "workload": "cavity 24^3, MIXED, order 2, sampling gp1, 200 spin-up steps"}
 
 
+def diatomic(device, steps, warmup, launch_cfg):
+    """The bench workload for a diatomic gas (K = 2 internal degrees of freedom:
+    particles carry an internal energy, 4 more bytes per particle record in
+    MIXED) after 200 spin-up steps, timed like the main line with its grid sizes."""
+    import torch
+    from paper_2007_13091_gb300 import ugkwp
+    from paper_2007_13091_gb300 import workloads as wl
+    cfg = wl.cavity(n=24, Kn=0.075, N_ref=100, precision="mixed", order=ORDER, K=2)
+    sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=torch.cuda.Stream(device=device))
+    ugkwp.ugkwp_set_launch_cfg(sim.handle, launch_cfg["particle_blocks"], launch_cfg["wave_blocks"])
+    sim.step(200)
+    ms, moves, _, kms, _ = time_steps(sim, steps, warmup, 1)
+    sim.close()
+    kms.pop("_moves", None)
+    return {"value": moves / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+            "kernels_ms_per_step": {k: v / steps for k, v in kms.items()},
+            "workload": "cavity 24^3, MIXED, order 2, K = 2 (diatomic), 200 spin-up steps"}
+
+
 def gks_start_up(device, steps=20, warmup=3):
     """Start-up steps of the gas-kinetic scheme (the method without particles,
     Sec. 3.2; the initial fields of the steady cases, Sec. 4.3, 4.4) on the
@@ -570,6 +590,7 @@ def main():
         out["adjoint"] = guarded(lambda: adjoint(device))
         out["gks_start_up"] = guarded(lambda: gks_start_up(device))
         out["gp1_sampling"] = guarded(lambda: gp1_sampling(device, args.steps, args.warmup, launch_cfg))
+        out["diatomic"] = guarded(lambda: diatomic(device, args.steps, args.warmup, launch_cfg))
         out["cpu_baseline"] = cpu_baseline(args.cpu_steps)
     elif rank == 0:
         out["e2e"] = None
