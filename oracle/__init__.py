@@ -71,6 +71,7 @@ def lib():
         L.orc_face_flux_o2.argtypes = [P(OrcParams), vp, d, vp, vp, vp, vp, d, vp, vp, vp, vp, d, i32, vp]
         L.orc_frozen_objective.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, vp, i32, vp]
         L.orc_frozen_value.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, vp, i32, vp]
+        L.orc_frozen_o2_value.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, vp, i32, vp, i32, vp]
         L.orc_sample_cell.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp]
         L.orc_sample_cell.restype = i64
         L.orc_gp_coefficients.argtypes = [vp, i32, vp]
@@ -371,6 +372,39 @@ class OracleSim:
         if rc:
             raise RuntimeError("oracle frozen objective failed")
         return out if grad else float(out[0])
+
+    def frozen_o2(self, frozen, theta, functional=0, tags=(), phi=None):
+        """J of the second-order frozen-particle wave map and the limiter values
+        phi [K][6][nc]: computed at theta (and returned) when phi is None, else
+        taken as given (the limiter frozen)."""
+        W0, dt, rho_p, pf = (np.ascontiguousarray(a, dtype=np.float64) for a in frozen)
+        nc = W0.shape[1]
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        tg = np.ascontiguousarray(tags, dtype=np.int32)
+        record = phi is None
+        ph = np.zeros((len(dt), 6, nc)) if record else np.ascontiguousarray(phi, dtype=np.float64).copy()
+        out = np.zeros(1)
+        rc = lib().orc_frozen_o2_value(self._h, len(dt), _ptr(W0), _ptr(dt), _ptr(rho_p), _ptr(pf), _ptr(th),
+                                       int(functional), _ptr(tg) if tg.size else None, tg.size, _ptr(ph),
+                                       int(record), _ptr(out))
+        if rc:
+            raise RuntimeError("oracle second-order frozen map failed")
+        return float(out[0]), ph
+
+    def frozen_o2_gradient(self, frozen, theta, functional=0, tags=(), rel_step=1e-5):
+        """[J, dJ/dtheta] of the second-order frozen map: the limiter frozen at
+        theta, derivatives by central differences with steps rel_step * theta."""
+        th = np.asarray(theta, dtype=np.float64)
+        J, phi = self.frozen_o2(frozen, th, functional, tags)
+        out = [J]
+        for k in range(3):
+            h = rel_step * th[k]
+            tp, tm = th.copy(), th.copy()
+            tp[k] += h
+            tm[k] -= h
+            out.append((self.frozen_o2(frozen, tp, functional, tags, phi)[0] -
+                        self.frozen_o2(frozen, tm, functional, tags, phi)[0]) / (2.0 * h))
+        return np.array(out)
 
     def prepare(self):
         """Primitives, tau, rho^h, dt and sampling counts of the current state

@@ -410,9 +410,13 @@ static double venkat(double d1, double d2, double eps2) {
 }
 
 // Limited gradients of W (5 x 3, row-major [q][d]) and rho^h (3) of every cell.
+// phi_io (optional, [6][nc]): with phi_given the limiter values are taken from
+// it instead of computed (a frozen limiter); otherwise the computed ones are
+// stored there.
 static void limited_gradients(const Geom& g, const orc_params& P, const std::vector<double>& W,
                               const std::vector<double>& rhoh, bool limit,
-                              std::vector<double>& gradW, std::vector<double>& gradH) {
+                              std::vector<double>& gradW, std::vector<double>& gradH,
+                              double* phi_io = nullptr, bool phi_given = false) {
     const int nc = g.nc;
     gradW.assign(15 * (size_t)nc, 0.0);
     gradH.assign(3 * (size_t)nc, 0.0);
@@ -472,7 +476,9 @@ static void limited_gradients(const Geom& g, const orc_params& P, const std::vec
                 grad[q][r] = acc / M[r][r];
             }
             double phi = 1.0;
-            if (limit) {
+            if (phi_given) {
+                phi = phi_io[(size_t)q * nc + i];
+            } else if (limit) {
                 double vmax = self[q], vmin = self[q];
                 for (int k = 0; k < 4; ++k) { vmax = std::max(vmax, val[k][q]); vmin = std::min(vmin, val[k][q]); }
                 double h = std::cbrt(g.vol[i]);
@@ -487,6 +493,7 @@ static void limited_gradients(const Geom& g, const orc_params& P, const std::vec
                     phi = std::min(phi, pk);
                 }
             }
+            if (phi_io && !phi_given) phi_io[(size_t)q * nc + i] = phi;
             for (int d = 0; d < 3; ++d) {
                 if (q < 5) gradW[15 * (size_t)i + 3 * q + d] = phi * grad[q][d];
                 else gradH[3 * (size_t)i + d] = phi * grad[q][d];
@@ -1836,6 +1843,73 @@ template <class S> S objective(const SimBase& sim, int K, const double* W0, cons
     return J;
 }
 
+// Second order: the same map with the limited least-squares reconstruction
+// (Sec. 2.1) at the interior faces and first-order boundary faces, as in the
+// step, in binary64 only.  The far-field ghosts of the reconstruction hold the
+// far-field state at theta.  phi [K][6][nc] holds the limiter values: computed
+// and stored with record, taken as given otherwise, so that with phi frozen at
+// theta_0 the map is a smooth function of theta whose derivative central
+// differences approximate (reading: the limiter is frozen in the derivative).
+double objective_o2(const SimBase& sim, int K, const double* W0, const double* dtv, const double* rho_p,
+                    const double* pflux, const double theta[3], int functional, const std::vector<char>& listed,
+                    double* phi, bool record) {
+    const Geom& g = sim.g;
+    const int nc = g.nc, nf = g.nf;
+    const int comp = functional == 0 ? 1 : 4;
+    orc_params Pt = sim.P;
+    std::vector<BcS<double>> bcs = bcs_of(sim.P, theta, listed);
+    for (int b = 0; b < Pt.n_bc; ++b) {
+        Pt.bc[b].T_w = bcs[b].T_w;
+        for (int q = 0; q < 5; ++q) Pt.bc[b].W_in[q] = bcs[b].W_in[q];
+    }
+    std::vector<double> W(W0, W0 + 5 * (size_t)nc), F(5 * (size_t)nf), rhoh(nc), tau(nc), gW, gH;
+    double J = 0.0;
+    for (int n = 0; n < K; ++n) {
+        const double dt = dtv[n];
+        for (int i = 0; i < nc; ++i) {
+            double Wi[5];
+            for (int q = 0; q < 5; ++q) Wi[q] = W[(size_t)q * nc + i];
+            Prim pr = prim_of(Wi, Pt.R, 0);
+            tau[i] = tau_cell(pr, Pt);
+            rhoh[i] = pr.rho - rho_p[(size_t)n * nc + i];
+        }
+        limited_gradients(g, Pt, W, rhoh, true, gW, gH, phi + (size_t)n * 6 * nc, !record);
+        for (int f = 0; f < nf; ++f) {
+            const double* nn = &g.f_n[3 * (size_t)f];
+            const int o = g.f_owner[f], nb = g.f_nbr[f];
+            double WL[5], Fv[5];
+            for (int q = 0; q < 5; ++q) WL[q] = W[(size_t)q * nc + o];
+            if (nb >= 0) {
+                double WR[5], dxL[3], dxR[3];
+                for (int q = 0; q < 5; ++q) WR[q] = W[(size_t)q * nc + nb];
+                const double* xf = &g.f_c[3 * (size_t)f];
+                for (int d = 0; d < 3; ++d) {
+                    dxL[d] = xf[d] - g.cen[3 * (size_t)o + d];
+                    dxR[d] = xf[d] - g.cen[3 * (size_t)nb + d];
+                }
+                face_flux_o2(frame_of(nn), WL, rhoh[o], &gW[15 * (size_t)o], &gH[3 * (size_t)o], dxL, WR, rhoh[nb],
+                             &gW[15 * (size_t)nb], &gH[3 * (size_t)nb], dxR, dt, false, Pt, Fv);
+            } else {
+                boundary_flux(WL, rhoh[o], tau[o], Pt.bc[g.f_bc[f]], nn, dt, false, Pt, Fv);
+                if (listed[g.f_bc[f]]) J += Fv[comp] * g.f_area[f];
+            }
+            for (int q = 0; q < 5; ++q) F[(size_t)q * nf + f] = Fv[q];
+        }
+        for (int i = 0; i < nc; ++i)
+            for (int q = 0; q < 5; ++q) {
+                double acc = 0.0;
+                for (int k = 0; k < 4; ++k) {
+                    const int f = g.tet_face[4 * i + k];
+                    double v = F[(size_t)q * nf + f] * g.f_area[f];
+                    acc += g.tet_sign[4 * i + k] > 0 ? v : -v;
+                }
+                double& Wq = W[(size_t)q * nc + i];
+                Wq = (Wq - acc / g.vol[i]) + pflux[((size_t)n * 5 + q) * nc + i] / g.vol[i];
+            }
+    }
+    return J;
+}
+
 }  // namespace frozen
 
 struct orc_sim { SimBase* s; };
@@ -2105,6 +2179,18 @@ int orc_frozen_value(const orc_sim* h, int32_t K, const double* W0, const double
     for (int k = 0; k < n_tags; ++k)
         if (tags[k] >= 0 && tags[k] < 16) listed[tags[k]] = 1;
     *J = frozen::objective(sim, K, W0, dt, rho_p, pflux, theta, functional, listed);
+    return 0;
+}
+
+int orc_frozen_o2_value(const orc_sim* h, int32_t K, const double* W0, const double* dt, const double* rho_p,
+                        const double* pflux, const double theta[3], int32_t functional, const int32_t* tags,
+                        int32_t n_tags, double* phi, int32_t record, double* J) {
+    const SimBase& sim = *h->s;
+    if (sim.P.order != 2 || sim.P.K != 0 || K < 1 || (functional != 0 && functional != 1)) return -1;
+    std::vector<char> listed(16, 0);
+    for (int k = 0; k < n_tags; ++k)
+        if (tags[k] >= 0 && tags[k] < 16) listed[tags[k]] = 1;
+    *J = frozen::objective_o2(sim, K, W0, dt, rho_p, pflux, theta, functional, listed, phi, record != 0);
     return 0;
 }
 

@@ -158,6 +158,16 @@ int orc_frozen_value(const orc_sim* s, int32_t K, const double* W0, const double
                      const double* pflux, const double theta[3], int32_t functional, const int32_t* tags,
                      int32_t n_tags, double* J);
 
+/* The same map at second order (the simulation's order must be 2): limited
+ * least-squares reconstruction at interior faces, first-order boundary faces,
+ * far-field ghosts at theta, binary64 only.  phi [K][6][nc] holds the limiter
+ * values of W (5) and rho^h: computed and written with record != 0, read
+ * otherwise (the limiter frozen).  Return 0, or -1 (order != 2, K != 0 internal
+ * degrees of freedom, K < 1, unknown functional). */
+int orc_frozen_o2_value(const orc_sim* s, int32_t K, const double* W0, const double* dt, const double* rho_p,
+                        const double* pflux, const double theta[3], int32_t functional, const int32_t* tags,
+                        int32_t n_tags, double* phi, int32_t record, double* J);
+
 /* Track one particle with the simulation's mesh and parameters (sampled checks
  * at sizes where a whole oracle step would be slow).  io_x/io_u are [3];
  * the particle precision follows the simulation.  Returns the status bits
