@@ -348,7 +348,9 @@ int ugkwp_timing_read(ugkwp_sim* s, double* ms, int64_t* launches);
  * particle flux F^{fr,p}.  With those frozen, the wave part of the K steps
  * from the state at the call is a smooth map
  *   W^{n+1} = W^n - sum_f (+/-) F_f(W^n; theta) |S_f| / |Omega| + F^{fr,p,n} / |Omega|
- * (first-order flux of Sec. 2.1, 2.3, 2.4 (d), (e)), and
+ * (the step's flux of Sec. 2.1, 2.3, 2.4 (d), (e): first order, or at order 2
+ * the limited least-squares reconstruction at interior faces, boundary faces
+ * first order), and
  *   J = sum_n sum_{boundary faces with a tag in wall_tags} F_f[c] |S_f|
  * with c = 1 for functional 0 (x momentum delivered to the walls: drag) and
  * c = 4 for functional 1 (energy: wall heat flux), wave part only.
@@ -359,9 +361,13 @@ int ugkwp_timing_read(ugkwp_sim* s, double* ms, int64_t* launches);
  * wall_tags gets temperature T_w.  theta == NULL evaluates at the simulation's
  * own values.  out[0] = J at theta, out[1..3] = dJ/dtheta by the hand-written
  * reverse sweep (face states recomputed from per-step checkpoints of W).
- * The recorded particle data never depend on theta.  Order 1 only
- * (E_UNSUPPORTED at order 2); the scratch memory is the caller's device
- * workspace of at least ugkwp_adjoint_query bytes (256-byte aligned). */
+ * The recorded particle data never depend on theta.  At order 2 the
+ * limiter values of each step are those of the frozen forward at theta and are
+ * held fixed in the derivative (a frozen limiter); the far-field ghosts of the
+ * reconstruction hold the far-field state at theta.  K = 0 internal degrees
+ * of freedom only (E_UNSUPPORTED otherwise); the scratch memory is the
+ * caller's device workspace of at least ugkwp_adjoint_query bytes (256-byte
+ * aligned). */
 typedef struct {
     int32_t functional;          /* 0 drag, 1 wall heat flux */
     int32_t n_steps;             /* K >= 1 */

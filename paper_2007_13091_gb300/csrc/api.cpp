@@ -1101,8 +1101,17 @@ int ugkwp_last(ugkwp_sim* s, int32_t which, void* host_out) {
 // terms, two adjoint states, face products and per-step sums.
 static void adjoint_layout(const ugkwp_sim* s, int K, Carver& c, double** ck, double** rp, double** pf, double** dt,
                            double** F, double** jf, double** lam0, double** lam1, double** wbar, double** thbar,
-                           double** sums, double** theta) {
+                           double** sums, double** theta, AdjO2* o2) {
     const size_t nc = s->M.nc, nf = s->M.nf;
+    std::memset(o2, 0, sizeof(*o2));
+    if (s->P.order == 2) {  // limiter values of every step, and scratch
+        o2->phi = c.take<double>((size_t)K * 6 * nc);
+        o2->gW = c.take<double>(15 * nc);
+        o2->gH = c.take<double>(3 * nc);
+        o2->gbar = c.take<double>(36 * nf);
+        o2->gg = c.take<double>(18 * nc);
+        o2->thc = c.take<double>(3 * nc);
+    }
     *ck = c.take<double>((size_t)(K + 1) * 5 * nc);
     *rp = c.take<double>((size_t)K * nc);
     *pf = c.take<double>((size_t)K * 5 * nc);
@@ -1121,14 +1130,14 @@ int ugkwp_adjoint_query(const ugkwp_sim* s, int32_t n_steps, size_t* bytes) {
     if (!s || !bytes || n_steps < 1) return fail(UGKWP_E_ARG, "invalid argument");
     Carver c(nullptr);
     double* p[12];
-    adjoint_layout(s, n_steps, c, &p[0], &p[1], &p[2], &p[3], &p[4], &p[5], &p[6], &p[7], &p[8], &p[9], &p[10], &p[11]);
+    AdjO2 o2;
+    adjoint_layout(s, n_steps, c, &p[0], &p[1], &p[2], &p[3], &p[4], &p[5], &p[6], &p[7], &p[8], &p[9], &p[10], &p[11], &o2);
     *bytes = (c.off + 255) & ~(size_t)255;
     return UGKWP_OK;
 }
 
 int ugkwp_adjoint_wave(ugkwp_sim* s, const ugkwp_adjoint_req* r, double* out) {
     if (!s || !r || !out) return fail(UGKWP_E_ARG, "NULL argument");
-    if (s->P.order != 1) return fail(UGKWP_E_UNSUPPORTED, "the adjoint covers the first-order wave flux only");
     if (s->P.K != 0) return fail(UGKWP_E_UNSUPPORTED, "the adjoint covers K = 0 only");
     if (r->n_steps < 1 || (r->functional != 0 && r->functional != 1) || r->n_wall_tags < 0 ||
         (r->n_wall_tags > 0 && !r->wall_tags))
@@ -1174,7 +1183,13 @@ int ugkwp_adjoint_wave(ugkwp_sim* s, const ugkwp_adjoint_req* r, double* out) {
                             r->theta ? r->theta[2] : theta0[2]};
     Carver c(r->d_workspace);
     double *ck, *rp, *pf, *dtv, *F, *jf, *lam0, *lam1, *wbar, *thbar, *sums, *theta;
-    adjoint_layout(s, K, c, &ck, &rp, &pf, &dtv, &F, &jf, &lam0, &lam1, &wbar, &thbar, &sums, &theta);
+    AdjO2 o2;
+    adjoint_layout(s, K, c, &ck, &rp, &pf, &dtv, &F, &jf, &lam0, &lam1, &wbar, &thbar, &sums, &theta, &o2);
+    auto step_o2 = [&](int n) {
+        AdjO2 t = o2;
+        if (t.phi) t.phi += (size_t)n * 6 * (size_t)s->M.nc;
+        return t;
+    };
     cudaStream_t q = s->stream;
     const size_t nc = s->M.nc;
     CU(cudaMemcpyAsync(theta, th_h, sizeof(th_h), cudaMemcpyHostToDevice, q));
@@ -1194,14 +1209,14 @@ int ugkwp_adjoint_wave(ugkwp_sim* s, const ugkwp_adjoint_req* r, double* out) {
     // 2. frozen forward at theta: checkpoints and the functional
     for (int n = 0; n < K; ++n)
         launch_adj_forward(s->M, s->P, ap, ck + (size_t)n * 5 * nc, rp + (size_t)n * nc, pf + (size_t)n * 5 * nc, dth[n],
-                           theta, F, jf, sums + n, ck + (size_t)(n + 1) * 5 * nc, q);
+                           theta, step_o2(n), F, jf, sums + n, ck + (size_t)(n + 1) * 5 * nc, q);
     // 3. reverse sweep
     CU(cudaMemsetAsync(lam1, 0, 5 * nc * sizeof(double), q));
     double* next = lam1;
     double* cur = lam0;
     for (int n = K - 1; n >= 0; --n) {
-        launch_adj_reverse(s->M, s->P, ap, ck + (size_t)n * 5 * nc, rp + (size_t)n * nc, dth[n], theta, next, cur, wbar,
-                           thbar, sums + K + 3 * (size_t)n, q);
+        launch_adj_reverse(s->M, s->P, ap, ck + (size_t)n * 5 * nc, rp + (size_t)n * nc, dth[n], theta, step_o2(n), next,
+                           cur, wbar, thbar, sums + K + 3 * (size_t)n, q);
         std::swap(next, cur);
     }
     CU(cudaGetLastError());

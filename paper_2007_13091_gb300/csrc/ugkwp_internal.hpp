@@ -242,14 +242,26 @@ struct AdjParams {
 };
 void launch_adj_record(const DevMesh& m, const DevState& s, const DevParams& p, double* rho_p, double* pf,
                        cudaStream_t st);
+// Second order: the step's limiter values phi [6][nc] (recorded by the forward
+// pass, used by the reverse one) and scratch: limited gradients gW [15][nc],
+// gH [3][nc], the faces' products with both cells' gradients gbar [36][nf],
+// phi times their per-cell sums gg [18][nc], far-field ghost products thc [3][nc].
+struct AdjO2 {
+    double* phi;
+    double* gW;
+    double* gH;
+    double* gbar;
+    double* gg;
+    double* thc;
+};
 // Fluxes at theta, the step's functional term Jn[0] and the next state Wn.
 void launch_adj_forward(const DevMesh& m, const DevParams& p, const AdjParams& ap, const double* W, const double* rho_p,
-                        const double* pf, double dt, const double* theta, double* F, double* jf, double* Jn,
-                        double* Wn, cudaStream_t st);
+                        const double* pf, double dt, const double* theta, const AdjO2& o2, double* F, double* jf,
+                        double* Jn, double* Wn, cudaStream_t st);
 // lambda^n from lambda^{n+1} and this step's dJ/dtheta terms th_out[3].
 void launch_adj_reverse(const DevMesh& m, const DevParams& p, const AdjParams& ap, const double* W,
-                        const double* rho_p, double dt, const double* theta, const double* lam_next, double* lam,
-                        double* wbar, double* thbar, double* th_out, cudaStream_t st);
+                        const double* rho_p, double dt, const double* theta, const AdjO2& o2, const double* lam_next,
+                        double* lam, double* wbar, double* thbar, double* th_out, cudaStream_t st);
 
 int sm_count();       // multiprocessors of the current device
 int particle_grid();  // default grid of particle kernels (8 blocks per SM)

@@ -4,7 +4,10 @@ From a common state, the GPU call (K real steps recorded, frozen forward,
 reverse sweep) is compared with the oracle's reference (its own K steps
 recorded, the same map evaluated on forward-mode dual numbers), with central
 finite differences of the GPU's own frozen map, and through the PyTorch
-autograd wrapper.
+autograd wrapper.  At second order the limiter values are those of the call's
+theta (frozen in the derivative) and the oracle's reference gradient is the
+central difference of its own second-order map with the same frozen limiter.
+The adjoint refuses K > 0 internal degrees of freedom.
 """
 import numpy as np
 import pytest
@@ -21,9 +24,9 @@ def _theta0():
     return np.array([1.0, 0.5 * np.sqrt(5.0 / 3.0), 1.0])
 
 
-def _setup(precision):
+def _setup(precision, order=1):
     import torch
-    cfg = wl.wall_channel(precision=precision)
+    cfg = wl.wall_channel(precision=precision, order=order)
     g = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], stream=torch.cuda.Stream())
     g.step(2)
     return cfg, g, g.state()
@@ -60,7 +63,29 @@ def test_adjoint_matches_gpu_finite_differences():
         assert abs(out[1 + k] - fd) <= 1e-6 * max(abs(out[1 + k]), 1e-3 * np.abs(out[1:]).max()), (k, out, fd)
 
 
-def test_autograd_wrapper_and_order2_refusal():
+@pytest.mark.parametrize("precision,theta", [("fp64", None), ("mixed", None), ("mixed", (1.1, 0.7, 1.3))])
+@pytest.mark.parametrize("functional", [0, 1])
+def test_adjoint_o2_matches_oracle_reference(precision, theta, functional):
+    """Second order: the limiter frozen at the call's theta on both sides; the
+    oracle's gradient by central differences of its own second-order map."""
+    cfg, g, st = _setup(precision, order=2)
+    th = _theta0() if theta is None else np.array(theta)
+    out = g.adjoint(functional, K, [1], th)
+    o = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    o.set_state(st)
+    fr = o.record_frozen(K)
+    ref = o.frozen_o2_gradient(fr, th, functional=functional, tags=[1])
+    assert out[0] == pytest.approx(ref[0], rel=1e-10)
+    scale = np.abs(ref[1:]).max()
+    for k in range(3):
+        assert abs(out[1 + k] - ref[1 + k]) <= 1e-6 * max(abs(ref[1 + k]), 1e-3 * scale), (k, out, ref)
+    # the reconstruction matters: the first-order map's gradient is another
+    o1 = oracle.OracleSim(cfg["mesh"], cfg["W0"], dict(cfg["params"], order=1))
+    r1 = o1.frozen_objective(fr, th, functional=functional, tags=[1])
+    assert (np.abs(r1[1:] - ref[1:]) / np.abs(ref[1:])).max() > 1e-3
+
+
+def test_autograd_wrapper_and_internal_degrees_refusal():
     import torch
     cfg, g, st = _setup("mixed")
     theta = torch.tensor(_theta0(), dtype=torch.float64, requires_grad=True)
@@ -70,8 +95,8 @@ def test_autograd_wrapper_and_order2_refusal():
     out = g.adjoint(1, K, [1], _theta0())
     assert float(J.detach()) == pytest.approx(out[0], rel=1e-12)
     np.testing.assert_allclose(theta.grad.numpy(), out[1:], rtol=1e-12)
-    o2 = wl.wall_channel(precision="mixed", order=2)
-    g2 = ugkwp.Simulation(o2["mesh"], o2["W0"], o2["params"])
+    dia = wl.uniform_box(n=(2, 2, 2), K=2)
+    g2 = ugkwp.Simulation(dia["mesh"], dia["W0"], dia["params"])
     with pytest.raises(ugkwp.UgkwpError) as e:
         g2.adjoint(0, 1, [1])
     assert e.value.code == ugkwp.E_UNSUPPORTED
