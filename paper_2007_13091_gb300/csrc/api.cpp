@@ -674,7 +674,7 @@ int enqueue_step(ugkwp_sim* s) {
             timed(s, UGKWP_K_FLUX_O2, 1, s->wave, [&] { launch_face_flux_o2(s->M, s->S, s->P, s->lc.wave_blocks, s->wave); });
         const int first = s->P.order == 2 ? s->M.nif : 0;
         if (s->M.nf > first)
-            timed(s, UGKWP_K_FLUX, 1, s->wave, [&] { launch_face_flux(s->M, s->S, s->P, first, s->wave); });
+            timed(s, UGKWP_K_FLUX, 1, s->wave, [&] { launch_face_flux(s->M, s->S, s->P, first, s->lc.wave_blocks, s->wave); });
         CU(cudaEventRecord(s->join, s->wave));
         timed(s, UGKWP_K_SCAN, 2, q, [&] { launch_scan(s->M, s->S, s->P, q); });
         if (gp) CU(cudaStreamWaitEvent(q, s->gp_ready, 0));  // the sampler reads the g_p coefficients
@@ -726,7 +726,7 @@ int enqueue_gks_step(ugkwp_sim* s, int32_t mode) {
     if (P.order == 2 && s->M.nif > 0)
         timed(s, UGKWP_K_FLUX_O2, 1, q, [&] { launch_face_flux_o2(s->M, s->S, P, s->lc.wave_blocks, q); });
     const int first = P.order == 2 ? s->M.nif : 0;
-    if (s->M.nf > first) timed(s, UGKWP_K_FLUX, 1, q, [&] { launch_face_flux(s->M, s->S, P, first, q); });
+    if (s->M.nf > first) timed(s, UGKWP_K_FLUX, 1, q, [&] { launch_face_flux(s->M, s->S, P, first, 0, q); });
     timed(s, UGKWP_K_UPDATE, 1, q, [&] { launch_cell_update(s->M, s->S, P, q); });
     return UGKWP_OK;
 }

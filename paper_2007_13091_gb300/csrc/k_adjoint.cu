@@ -584,6 +584,7 @@ __device__ __forceinline__ void face_dx(const DevMesh& m, int f, int o, int nb, 
 }
 
 // ---- forward: fluxes and the functional's face terms at theta
+template <bool O2>
 __global__ void __launch_bounds__(128) k_adj_fwd_flux(DevMesh m, DevParams P, AdjParams ap, const double* W,
                                                       const double* rho_p, double dt, const double* theta,
                                                       const double* gW, const double* gH, double* F, double* jf) {
@@ -597,7 +598,7 @@ __global__ void __launch_bounds__(128) k_adj_fwd_flux(DevMesh m, DevParams P, Ad
             WR[q] = nb >= 0 ? W[(size_t)q * nc + nb] : 0.0;
         }
         double Fv[5];
-        if (P.order == 2 && nb >= 0) {
+        if (O2 && nb >= 0) {
             double gwl[15], ghl[3], gwr[15], ghr[3], dxL[3], dxR[3];
             load_grad(gW, gH, nc, o, gwl, ghl);
             load_grad(gW, gH, nc, nb, gwr, ghr);
@@ -646,6 +647,7 @@ __global__ void k_adj_sum(const double* x, int n, int ncomp, double* out, int ac
 }
 
 // ---- reverse: per face, g_f and its products with the local Jacobians
+template <bool O2>
 __global__ void __launch_bounds__(128) k_adj_face(DevMesh m, DevParams P, AdjParams ap, const double* W,
                                                   const double* rho_p, double dt, const double* theta,
                                                   const double* gW, const double* gH, const double* lam_next,
@@ -661,7 +663,7 @@ __global__ void __launch_bounds__(128) k_adj_face(DevMesh m, DevParams P, AdjPar
         }
         if (listed_face(m, ap, f)) g[ap.comp] += area;
         const double rpL = rho_p[o], rpR = nb >= 0 ? rho_p[nb] : 0.0;
-        if (P.order == 2 && nb >= 0) {
+        if (O2 && nb >= 0) {
             // second order: products with the face's Jacobians with respect to
             // both cells' W and limited gradients, five directions at a time
             double gw[2][15], gh[2][3], dxL[3], dxR[3], Wc[2][5];
@@ -712,7 +714,7 @@ __global__ void __launch_bounds__(128) k_adj_face(DevMesh m, DevParams P, AdjPar
             for (int k = 0; k < 3; ++k) thbar[(size_t)k * nf + f] = 0.0;
             continue;
         }
-        if (P.order == 2)  // a boundary face at second order: first order, no gradient products
+        if (O2)  // a boundary face at second order: first order, no gradient products
             for (int j = 0; j < 36; ++j) gbar[(size_t)j * nf + f] = 0.0;
         // owner's W
         {
@@ -882,7 +884,8 @@ void launch_adj_forward(const DevMesh& m, const DevParams& p, const AdjParams& a
                         double* Jn, double* Wn, cudaStream_t st) {
     const int g = (m.nf + 127) / 128;
     if (p.order == 2) k_adj_grad<<<grad_grid(m), 128, 0, st>>>(m, p, ap, W, rho_p, theta, o2.phi, 1, o2.gW, o2.gH);
-    k_adj_fwd_flux<<<g, 128, 0, st>>>(m, p, ap, W, rho_p, dt, theta, o2.gW, o2.gH, F, jf);
+    if (p.order == 2) k_adj_fwd_flux<true><<<g, 128, 0, st>>>(m, p, ap, W, rho_p, dt, theta, o2.gW, o2.gH, F, jf);
+    else k_adj_fwd_flux<false><<<g, 128, 0, st>>>(m, p, ap, W, rho_p, dt, theta, o2.gW, o2.gH, F, jf);
     k_adj_sum<<<1, 256, 0, st>>>(jf, m.nf, 1, Jn, 0);
     k_adj_update<<<(m.nc + 255) / 256, 256, 0, st>>>(m, W, F, pf, Wn);
 }
@@ -892,7 +895,10 @@ void launch_adj_reverse(const DevMesh& m, const DevParams& p, const AdjParams& a
                         double* lam, double* wbar, double* thbar, double* th_out, cudaStream_t st) {
     const int g = (m.nf + 127) / 128;
     if (p.order == 2) k_adj_grad<<<grad_grid(m), 128, 0, st>>>(m, p, ap, W, rho_p, theta, o2.phi, 0, o2.gW, o2.gH);
-    k_adj_face<<<g, 128, 0, st>>>(m, p, ap, W, rho_p, dt, theta, o2.gW, o2.gH, lam_next, wbar, o2.gbar, thbar);
+    if (p.order == 2)
+        k_adj_face<true><<<g, 128, 0, st>>>(m, p, ap, W, rho_p, dt, theta, o2.gW, o2.gH, lam_next, wbar, o2.gbar, thbar);
+    else
+        k_adj_face<false><<<g, 128, 0, st>>>(m, p, ap, W, rho_p, dt, theta, o2.gW, o2.gH, lam_next, wbar, o2.gbar, thbar);
     if (p.order == 2) k_adj_gg<<<(m.nc + 255) / 256, 256, 0, st>>>(m, o2.phi, o2.gbar, o2.gg);
     k_adj_cell<<<(m.nc + 255) / 256, 256, 0, st>>>(m, p, ap, W, theta, lam_next, wbar, o2.gg, lam, o2.thc);
     k_adj_sum<<<1, 256, 0, st>>>(thbar, m.nf, 3, th_out, 0);

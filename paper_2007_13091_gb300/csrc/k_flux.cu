@@ -702,11 +702,9 @@ __global__ void __launch_bounds__(UGKWP_WAVE_THREADS, UGKWP_WAVE_MIN_BLOCKS) k_f
     }
 }
 
-// First-order flux of the faces face_order[first..nf).
-__global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevParams p, int first) {
+// First-order flux of face face_order[t].
+__device__ __forceinline__ void face_flux_o1(const DevMesh& m, const DevState& s, const DevParams& p, int t) {
     const int nc = m.nc, nf = m.nf;
-    const int t = first + blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nf) return;
     const int f = m.face_order[t];  // interior faces first, then boundary faces by type
     const double inv_Tref = 1.0 / p.T_ref;
     const double n[3] = {m.f_n[f], m.f_n[nf + f], m.f_n[2 * nf + f]};
@@ -760,6 +758,12 @@ __global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevPar
     for (int q = 0; q < 5; ++q) s.F[(size_t)q * nf + f] = F[q];
 }
 
+// First-order flux of the faces face_order[first..nf), grid-stride.
+__global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevParams p, int first) {
+    for (int t = first + blockIdx.x * blockDim.x + threadIdx.x; t < m.nf; t += gridDim.x * blockDim.x)
+        face_flux_o1(m, s, p, t);
+}
+
 }  // namespace
 
 static int wave_grid(int n, int blocks) {
@@ -786,8 +790,12 @@ void launch_face_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p
 
 int wave_threads() { return UGKWP_WAVE_THREADS; }
 
-void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, int first, cudaStream_t st) {
-    k_face_flux<<<(m.nf - first + 255) / 256, 256, 0, st>>>(m, s, p, first);
+// blocks > 0 bounds the grid (a step of the method: the flux shares the GPU
+// with the particle kernels launched beside it); 0: one thread per face.
+void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, int first, int blocks,
+                      cudaStream_t st) {
+    const int need = (m.nf - first + 255) / 256;
+    k_face_flux<<<blocks > 0 && blocks < need ? blocks : need, 256, 0, st>>>(m, s, p, first);
 }
 
 }  // namespace ugkwp

@@ -212,7 +212,8 @@ void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const
 void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
                    int blocks, cudaStream_t st);
 // First-order flux of face_order[first..nf); second-order flux of the nif interior faces.
-void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, int first, cudaStream_t st);
+void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, int first, int blocks,
+                      cudaStream_t st);
 void launch_face_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p, int blocks, cudaStream_t st);
 void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_gp_coef(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);

@@ -85,6 +85,59 @@ def test_adjoint_o2_matches_oracle_reference(precision, theta, functional):
     assert (np.abs(r1[1:] - ref[1:]) / np.abs(ref[1:])).max() > 1e-3
 
 
+def _teacher_forced_record(g, st, o, n_steps):
+    """The frozen data of n_steps steps of the GPU simulation from state st,
+    each step taken by the oracle from the GPU's state before it (so the
+    particle data are those the GPU records, bit for bit, over any number of
+    steps)."""
+    g.set_state(st)
+    W0 = st["W"].copy()
+    nc = W0.shape[1]
+    dt, rho_p, pf = [], [], []
+    for _ in range(n_steps):
+        cur = g.state()
+        o.set_state(cur)
+        o.step()
+        e = cur["exps"]
+        dt.append(o.last("dt"))
+        rho_p.append(cur["W"][0] - o.last("rho_h"))
+        q = o.last("pflux").astype(np.float64)
+        pf.append(np.stack([np.ldexp(q[c], int(e[c])) for c in range(5)]))
+        g.step(1)
+    return W0, np.array(dt), np.array(rho_p).reshape(n_steps, nc), np.array(pf).reshape(n_steps, 5, nc)
+
+
+def test_blunt_vehicle_adjoint_matches_oracle_reference():
+    """The adjoint configuration on a coarse mesh (16,776 tets): Ma 8 past the
+    sphere-capped cone, T_w = 3 T_inf, Kn 1e-3, mixed precision, from a
+    gas-kinetic start-up field; drag and wall heat flux of the body over 14
+    steps against the oracle's dual-number reference on the same recorded
+    particle data.  The far field is 11 tets from the body: theta reaches a
+    body cell's state after 12 steps, and J sums the fluxes of the states
+    before each step, so 13 steps are the fewest with dJ/d(rho_inf, U_inf)
+    non-zero."""
+    import torch
+    cfg = wl.blunt_vehicle(h0=0.1, growth=1.5)
+    o = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    o.gks_step(150, local=True)
+    g = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], stream=torch.cuda.Stream())
+    g.set_state(o.state())
+    g.step(2)
+    st = g.state()
+    assert st["id"].size > 1_000_000
+    n_steps = 14
+    fr = _teacher_forced_record(g, st, o, n_steps)
+    th = np.array([1.0, 8.0 * np.sqrt(5.0 / 3.0), 3.0])
+    for functional in (0, 1):
+        g.set_state(st)
+        out = g.adjoint(functional, n_steps, [2])  # theta = the simulation's own values
+        ref = o.frozen_objective(fr, th, functional=functional, tags=[2])
+        assert out[0] == pytest.approx(ref[0], rel=1e-10)
+        assert np.all(np.abs(ref[1:]) > 0)  # the far field reaches the body within the steps
+        for k in range(3):
+            assert abs(out[1 + k] - ref[1 + k]) <= 1e-6 * abs(ref[1 + k]), (k, out, ref)
+
+
 def test_autograd_wrapper_and_internal_degrees_refusal():
     import torch
     cfg, g, st = _setup("mixed")

@@ -96,3 +96,34 @@ def test_mesh_errors():
         oracle.OracleSim({**m, "tets": bad}, cfg["W0"], cfg["params"])
     with pytest.raises(ValueError, match="boundary tag"):
         oracle.OracleSim({**m, "bfaces": m["bfaces"][1:], "btags": m["btags"][1:]}, cfg["W0"], cfg["params"])
+
+
+def test_blunt_vehicle_mesh_and_start_up():
+    """The generated blunt vehicle: positive volumes, the body carved out (no
+    tet inside it), body faces on or near the sphere-cone surface (every
+    node moved there where the volumes allow it), box sides and body tagged;
+    gas-kinetic start-up steps with local time steps from the impulsive start
+    keep density and pressure positive and fill the base region."""
+    cfg = wl.blunt_vehicle(h0=0.1, growth=1.5)
+    m, body = cfg["mesh"], cfg["body"]
+    nodes, tets, bf, tags = m["nodes"], m["tets"], m["bfaces"], m["btags"]
+    assert wl._volumes(nodes, tets).min() > 0.0
+    # carved out: no tet lies inside the body; the staircase leaves a few
+    # centroids within the surface's curvature
+    assert not body.inside(nodes[tets]).all(1).any()
+    assert body.inside(nodes[tets].mean(1)).mean() < 0.01
+    on = np.unique(bf[tags == 2])
+    d = np.linalg.norm(body.closest(nodes[on]) - nodes[on], axis=1)
+    assert d.max() < 0.1 and (d < 1e-12).mean() > 0.3
+    assert set(np.unique(tags).tolist()) == {0, 1, 2}
+    x0 = nodes[bf[tags == 0]][:, :, 0]
+    assert np.all(x0 == -1.0)
+    s = oracle.OracleSim(m, cfg["W0"], cfg["params"])
+    s.gks_step(150, local=True)
+    W = s.state()["W"]
+    U = W[1:4] / W[0]
+    p = (W[4] - 0.5 * W[0] * (U * U).sum(0)) / 1.5
+    assert W[0].min() > 0.0 and p.min() > 0.01
+    cen = nodes[tets].mean(1)
+    base = (cen[:, 0] > 1.0) & (cen[:, 0] < 1.1) & (np.hypot(cen[:, 1], cen[:, 2]) < 0.2)
+    assert base.any() and W[0][base].max() < 0.5  # the wake behind the base
