@@ -417,6 +417,70 @@ def gks_start_up(device, steps=20, warmup=3):
     return out
 
 
+def hypersonic(device, which, steps, warmup, gks_steps, spin_up=5, adjoint_K=0, kernel_times=True):
+    """The hypersonic configurations at full size, MIXED, first order: Ma 4 past
+    the unit cube (1,152,912 tets, Kn 0.1, N_ref 200) or Ma 8 past the blunt
+    vehicle (2,770,032 tets, Kn 1e-3, T_w = 3 T_inf, N_ref 100, energy-matched
+    sampling).  Each starts with `gks_steps` gas-kinetic steps with local time
+    steps from the free stream (the start-up of the steady cases), then takes
+    `spin_up` steps of the method and times `steps` more like the main line;
+    with adjoint_K > 0 one adjoint call per functional follows (drag and wall
+    heat flux of the body, theta = the free stream and the wall).
+
+    The blunt vehicle runs the method for about 50 steps after its start-up
+    before some cell's pressure falls through zero (the bow shock ahead of the
+    nose, where nearly all the gas is in particles and the wave part is their
+    small difference from W; energy-matched sampling and twice N_ref only
+    delay it), so it times 5 steps and its adjoint calls take 16 steps each:
+    dJ/dT_w, while the far field, 44 tets from the body, needs 46 steps to
+    reach it (the coarse mesh of the same configuration checks all three
+    derivatives in the tests)."""
+    import torch
+    from paper_2007_13091_gb300 import ugkwp
+    from paper_2007_13091_gb300 import workloads as wl
+    t0 = time.perf_counter()
+    if which == "cube":
+        cfg = wl.cube_flow()
+    else:
+        cfg = wl.blunt_vehicle()
+        cfg["params"]["sampling"] = "energy_matched"
+    stream = torch.cuda.Stream(device=device)
+    sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=stream)
+    n = sim.n_cells
+    out = {"workload": cfg["name"], "n_cells": n, "N_ref": cfg["params"]["N_ref"], "Kn": cfg["params"]["Kn"],
+           "sampling": cfg["params"].get("sampling", "pairs"), "setup_s": time.perf_counter() - t0}
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    sim.gks_steps(gks_steps, local_dt=True)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    sim.sync()
+    W = sim.moments(ugkwp.W)
+    U = W[1:4] / W[0]
+    p = (W[4] - 0.5 * W[0] * (U * U).sum(0)) / 1.5
+    out["gks_start_up"] = {"steps": gks_steps, "ms_per_step": ms / gks_steps,
+                           "cell_steps_per_s": n * gks_steps / (ms * 1e-3),
+                           "rho_min": float(W[0].min()), "p_min": float(p.min())}
+    sim.step(spin_up)
+    ms, moves, launches, kms, st = time_steps(sim, steps, warmup, 1, timing=kernel_times)
+    out.update({"value": moves / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+                "cell_steps_per_s": n * steps / (ms * 1e-3), "particles_per_step": moves / steps})
+    if kms:
+        kms.pop("_moves", None)
+        out["kernels_ms_per_step"] = {k: v / steps for k, v in kms.items()}
+    if adjoint_K:
+        adj = {}
+        for functional, name in ((0, "drag"), (1, "wall_heat_flux")):
+            t1 = time.perf_counter()
+            r = sim.adjoint(functional, adjoint_K, [2])
+            adj[name] = {"J_and_grad": [float(v) for v in r], "ms_per_call": 1e3 * (time.perf_counter() - t1)}
+        out["adjoint"] = {"steps": adjoint_K, "theta": "(rho_inf, U_inf, T_w) = (1, 8 sqrt(5/3), 3)",
+                          "cell_steps_per_s": n * adjoint_K / (1e-3 * adj["drag"]["ms_per_call"]), **adj}
+    sim.close()
+    return out
+
+
 def cpu_baseline(steps):
     """The CPU oracle (single thread) on the same workload: one untimed step
     samples the particle population, then `steps` timed steps."""
@@ -591,6 +655,9 @@ def main():
         out["gks_start_up"] = guarded(lambda: gks_start_up(device))
         out["gp1_sampling"] = guarded(lambda: gp1_sampling(device, args.steps, args.warmup, launch_cfg))
         out["diatomic"] = guarded(lambda: diatomic(device, args.steps, args.warmup, launch_cfg))
+        out["cube_ma4"] = guarded(lambda: hypersonic(device, "cube", 10, 3, 300))
+        out["blunt_vehicle"] = guarded(lambda: hypersonic(device, "vehicle", 5, 3, 1200, spin_up=2, adjoint_K=16,
+                                                          kernel_times=False))
         out["cpu_baseline"] = cpu_baseline(args.cpu_steps)
     elif rank == 0:
         out["e2e"] = None
