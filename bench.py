@@ -262,6 +262,37 @@ def field_error(horizons, device):
     return {"horizons": list(horizons), "by_horizon": res}
 
 
+def field_error_averaged(device, spin=300, avg=600):
+    """The steady cavity's time-averaged fields (the paper's averaging of
+    Sec. 2.4 (c), over `avg` steps after `spin` steps): per-field relative L2
+    of MIXED vs FP64 at the same seed, and the FP64 seed-to-seed floor of the
+    same averages."""
+    from paper_2007_13091_gb300 import ugkwp
+
+    def averaged(precision, seed):
+        cfg = workload(precision, seed)
+        sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device)
+        sim.step(spin)
+        ugkwp.ugkwp_average(sim.handle, True)
+        sim.step(avg)
+        Wb = sim.moments(ugkwp.WBAR)
+        sim.close()
+        rho = Wb[0]
+        U = Wb[1:4] / rho
+        p = (Wb[4] - 0.5 * rho * (U * U).sum(0)) / 1.5
+        return {"rho": rho, "U": U, "T": p / rho, "p": p}
+
+    a, b, c = averaged("mixed", 2), averaged("fp64", 2), averaged("fp64", 1002)
+    ulid = 0.16 * math.sqrt(5.0 / 3.0)
+
+    def err(x, y):
+        e = {k: float(np.linalg.norm(x[k] - y[k]) / np.linalg.norm(y[k])) for k in ("rho", "T", "p")}
+        e["U"] = float(np.linalg.norm(x["U"] - y["U"]) / (ulid * math.sqrt(y["U"].shape[1])))
+        return e
+    return {"spin_up_steps": spin, "averaged_steps": avg, "mixed_vs_fp64": err(a, b),
+            "noise_floor_fp64_seed": err(c, b)}
+
+
 def e2e(cfg, steps, device):
     """Per step through the C-ABI with host buffers: import the state from host
     arrays, one step, read W back to host memory."""
@@ -643,6 +674,7 @@ def main():
                        "kernels_ms_per_step": {k: v / args.steps for k, v in k64.items()}, "launch_cfg": cfg64}
         out["mixed_over_fp64"] = out["value"] / out["fp64"]["value"]
         out["field_error"] = guarded(lambda: field_error((1, 10, 20), device))
+        out["field_error_time_averaged"] = guarded(lambda: field_error_averaged(device))
         out["e2e"] = e2e(cfg, 3, device)
 
         def both():
