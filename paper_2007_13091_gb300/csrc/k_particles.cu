@@ -430,18 +430,22 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
     const double dt = s.dt[0];
     const Real dtR = (Real)dt;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ int sh_cnt[8], sh_scnt[8];
-    __shared__ long long sh_base, sh_sbase, sh_tile;
+    // slot bookkeeping in two sets, alternating between tiles, so that no
+    // barrier is needed after a tile's stores: a set is rewritten two tiles
+    // later, after two barriers every warp has passed
+    __shared__ int sh_cnt[2][8], sh_scnt[2][8];
+    __shared__ long long sh_base[2], sh_sbase[2], sh_tile[2];
+    int par = 0;
     __shared__ unsigned long long sh_red[8][8];
     // per-thread counters, reduced once per block at the end
     unsigned c_valid = 0, c_coll = 0, c_exit = 0, c_lost = 0, c_cross = 0, c_wall = 0;
     // tiles of blockDim.x particles are taken from a global counter, so that
     // blocks that start late (or walk short paths) take fewer tiles
     if (threadIdx.x == 0)
-        sh_tile = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_TILE]), 1ULL) * blockDim.x;
+        sh_tile[0] = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_TILE]), 1ULL) * blockDim.x;
     __syncthreads();
     for (;;) {
-        const long long bb = sh_tile;  // block-uniform
+        const long long bb = sh_tile[par];  // block-uniform
         if (bb >= n) break;
         const long long i = bb + threadIdx.x;
         const bool valid = i < n;
@@ -622,31 +626,33 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
         const unsigned mmask = __ballot_sync(FULL, mover);
         const unsigned smask = __ballot_sync(FULL, survivor);
         if (lane == 0) {
-            sh_cnt[warp] = __popc(mmask);
-            sh_scnt[warp] = __popc(smask);
+            sh_cnt[par][warp] = __popc(mmask);
+            sh_scnt[par][warp] = __popc(smask);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             int tot = 0, stot = 0;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                const int c = sh_cnt[w], sc = sh_scnt[w];
-                sh_cnt[w] = tot;
-                sh_scnt[w] = stot;
+                const int c = sh_cnt[par][w], sc = sh_scnt[par][w];
+                sh_cnt[par][w] = tot;
+                sh_scnt[par][w] = stot;
                 tot += c;
                 stot += sc;
             }
-            sh_base = tot ? (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_MOVERS]),
-                                                 (unsigned long long)tot)
-                          : 0LL;
-            sh_sbase = stot ? (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_ALIVE]),
-                                                   (unsigned long long)stot)
-                            : 0LL;
-            // the next tile (every thread has read sh_tile before the barrier above)
-            sh_tile = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_TILE]), 1ULL) * blockDim.x;
+            sh_base[par] = tot ? (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_MOVERS]),
+                                                      (unsigned long long)tot)
+                               : 0LL;
+            sh_sbase[par] = stot ? (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_ALIVE]),
+                                                        (unsigned long long)stot)
+                                 : 0LL;
+            // the next tile, in the other set (its last readers read it before
+            // the barrier above)
+            sh_tile[par ^ 1] =
+                (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_TILE]), 1ULL) * blockDim.x;
         }
         __syncthreads();
         if (survivor) {
-            const long long j = sh_sbase + sh_scnt[warp] + __popc(smask & ((1u << lane) - 1u));
+            const long long j = sh_sbase[par] + sh_scnt[par][warp] + __popc(smask & ((1u << lane) - 1u));
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 nxt.x[c][j] = xe[c];
@@ -658,7 +664,7 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
             if constexpr (KE) nxt.e[j] = ee;
         }
         if (mover) {
-            const long long j = sh_base + sh_cnt[warp] + __popc(mmask & ((1u << lane) - 1u));
+            const long long j = sh_base[par] + sh_cnt[par][warp] + __popc(mmask & ((1u << lane) - 1u));
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 mv.x[c][j] = us[c];
@@ -672,7 +678,7 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
                 mv.e2[j] = ee;
             }
         }
-        __syncthreads();  // sh_cnt / sh_base / sh_tile are reused next iteration
+        par ^= 1;
     }
     // ---- counters: one atomic per block and counter (survivors were counted
     // by their slot reservations)
