@@ -458,14 +458,64 @@ def test_cube_full_size_sampled():
         assert np.array_equal(gsim.last(k), osim.last(k)), k
     assert st["n_sampled"] == int(osim.last("n_sam").sum()) > 2e8
     assert st["n_lost"] == 0
+    _check_sampled_cells(gsim, osim, cfg, rng_seed=13)
+    gsim.close()
+
+
+def test_blunt_vehicle_full_size_sampled():
+    """Full-size Ma 8 blunt vehicle (2,770,032 tets, N_ref 100, T_w = 3 T_inf,
+    snapped body surface), the method's first step from the GPU's own
+    gas-kinetic start-up field (300 local steps), imported into the oracle:
+    per-cell dt, tau, rho^h, N_sam, m_sam bit for bit, and the GPU's W^p of 24
+    random cells (and of 8 cells next to the body) reproduced exactly by the
+    oracle's own sampling and tracking of the particles around them."""
+    import torch
+    cfg = wl.blunt_vehicle(precision="mixed")
+    nc = len(cfg["mesh"]["tets"])
+    assert nc > 2_700_000
+    gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], stream=torch.cuda.Stream())
+    gsim.gks_steps(300, local_dt=True)
+    st0 = gsim.state()
+    assert st0["id"].size == 0
+    osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    osim.set_state(st0)
+    st = gsim.step(1, stats=True)
+    osim.prepare()
+    assert gsim.last("dt") == osim.last("dt")
+    for k in ("tau", "rho_h", "n_sam", "m_sam"):
+        assert np.array_equal(gsim.last(k), osim.last(k)), k
+    assert st["n_sampled"] == int(osim.last("n_sam").sum()) > 2e8
+    assert st["n_lost"] == 0
+    body = _body_cells(cfg)
+    _check_sampled_cells(gsim, osim, cfg, rng_seed=17, extra=np.random.default_rng(3).choice(body, 8, replace=False))
+    gsim.close()
+
+
+def _body_cells(cfg):
+    """Tets with a face on the body (boundary tag 2)."""
+    tets = np.asarray(cfg["mesh"]["tets"], dtype=np.int64)
+    bf = np.sort(np.asarray(cfg["mesh"]["bfaces"], dtype=np.int64)[cfg["mesh"]["btags"] == 2], axis=1)
+    n = int(tets.max()) + 1
+    f = np.sort(tets[:, [[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]]].reshape(-1, 3), axis=1)
+    key = (f[:, 0] * n + f[:, 1]) * n + f[:, 2]
+    bkey = (bf[:, 0] * n + bf[:, 1]) * n + bf[:, 2]
+    return np.unique(np.nonzero(np.isin(key, bkey))[0] // 4)
+
+
+def _check_sampled_cells(gsim, osim, cfg, rng_seed, n_cells=24, extra=()):
+    """For random cells (and `extra`), the oracle regenerates and tracks every
+    particle born within four neighbour rings in the first step and
+    reproduces the GPU's W^p of the cell exactly (fixed point)."""
+    nc = len(cfg["mesh"]["tets"])
     WP = gsim.moments(ugkwp.WP)
     dt, tau = osim.last("dt"), osim.last("tau")
     info = ugkwp.ugkwp_state_info(gsim.handle)
     exps = [int(v) for v in info.exps]
     vol = osim.geometry("vol")
     nb = _tet_neighbours(cfg["mesh"]["tets"])
-    rng = np.random.default_rng(13)
-    cells = rng.choice(nc, 24, replace=False)
+    rng = np.random.default_rng(rng_seed)
+    cells = list(rng.choice(nc, n_cells, replace=False)) + [int(v) for v in extra]
+    step = int(info.step) - 1
     for c in cells:
         dist = {int(c): 0}
         frontier = {int(c)}
@@ -476,7 +526,7 @@ def test_cube_full_size_sampled():
         for b, r in sorted(dist.items()):
             sp = osim.sample_cell(b)
             for k in range(sp["id"].size):
-                out = osim.track_one(sp["id"][k], b, sp["x"][:, k], sp["u"][:, k], tau[b], dt, 0)
+                out = osim.track_one(sp["id"][k], b, sp["x"][:, k], sp["u"][:, k], tau[b], dt, step)
                 if out["status"] & 3 or out["cell"] != c:
                     continue
                 assert r < 4, "a particle from the outermost ring reached the cell: widen the ring"
@@ -486,4 +536,3 @@ def test_cube_full_size_sampled():
                 acc += np.rint(np.ldexp(phi, -np.array(exps))).astype(np.int64)
         ref = (acc.astype(np.float64) * np.ldexp(1.0, np.array(exps))) / vol[c]
         np.testing.assert_array_equal(WP[:, c], ref)
-    gsim.close()
