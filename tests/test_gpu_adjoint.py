@@ -63,12 +63,19 @@ def test_adjoint_matches_gpu_finite_differences():
         assert abs(out[1 + k] - fd) <= 1e-6 * max(abs(out[1 + k]), 1e-3 * np.abs(out[1:]).max()), (k, out, fd)
 
 
-@pytest.mark.parametrize("precision,theta", [("fp64", None), ("mixed", None), ("mixed", (1.1, 0.7, 1.3))])
+@pytest.mark.parametrize("precision,theta,Pr", [("fp64", None, 0.0), ("mixed", None, 0.0),
+                                                ("mixed", (1.1, 0.7, 1.3), 0.0), ("mixed", None, 2.0 / 3.0)])
 @pytest.mark.parametrize("functional", [0, 1])
-def test_adjoint_o2_matches_oracle_reference(precision, theta, functional):
+def test_adjoint_o2_matches_oracle_reference(precision, theta, Pr, functional):
     """Second order: the limiter frozen at the call's theta on both sides; the
-    oracle's gradient by central differences of its own second-order map."""
-    cfg, g, st = _setup(precision, order=2)
+    oracle's gradient by central differences of its own second-order map
+    (also with the Prandtl fix of the heat flux, Pr = 2/3)."""
+    import torch
+    cfg = wl.wall_channel(precision=precision, order=2)
+    cfg["params"]["Pr"] = Pr
+    g = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], stream=torch.cuda.Stream())
+    g.step(2)
+    st = g.state()
     th = _theta0() if theta is None else np.array(theta)
     out = g.adjoint(functional, K, [1], th)
     o = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
