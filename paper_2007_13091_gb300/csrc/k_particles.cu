@@ -711,23 +711,48 @@ __global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams
     const long long n = s.cnt64[CNT_MOVERS];
     const int nc = m.nc;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        const Real us[3] = {mv.x[0][j], mv.x[1][j], mv.x[2][j]};
-        const Real ue[3] = {mv.u[0][j], mv.u[1][j], mv.u[2][j]};
-        const double mm = mv.m[j];
-        const int c0 = mv.cell[j];
-        const unsigned long long code = mv.id[j];
-        const int c1 = (int)(code >> 1);
-        const bool exited = code & 1ULL;
-        long long q0[5], q1[5];
-        const Real es = mv.e ? mv.e[j] : (Real)0, ee = mv.e2 ? mv.e2[j] : (Real)0;
-        bool ok = phi_q(us, es, mm, p, q0);
-        ok &= phi_q(ue, ee, mm, p, q1);
-        if (!ok) set_err(s, ERRB_FIXED_OVERFLOW);
+    const int lane = threadIdx.x & 31;
+    // whole warps per iteration: the start-cell sums are reduced over runs of
+    // equal start cells within the warp (the list is ordered by start cell
+    // within each tracking tile), one atomic per run and quantity
+    for (long long j0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); j0 < n; j0 += stride) {
+        const long long j = j0 + lane;
+        const bool valid = j < n;
+        Real us[3] = {(Real)0, (Real)0, (Real)0}, ue[3] = {(Real)0, (Real)0, (Real)0};
+        double mm = 0.0;
+        int c0 = -1, c1 = -1;
+        bool exited = true;
+        long long q0[5] = {0, 0, 0, 0, 0}, q1[5] = {0, 0, 0, 0, 0};
+        if (valid) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q)
-            atomicAdd(reinterpret_cast<unsigned long long*>(&s.pflux[(size_t)q * nc + c0]), (unsigned long long)(-q0[q]));
-        if (!exited) {
+            for (int c = 0; c < 3; ++c) { us[c] = mv.x[c][j]; ue[c] = mv.u[c][j]; }
+            mm = mv.m[j];
+            c0 = mv.cell[j];
+            const unsigned long long code = mv.id[j];
+            c1 = (int)(code >> 1);
+            exited = code & 1ULL;
+            const Real es = mv.e ? mv.e[j] : (Real)0, ee = mv.e2 ? mv.e2[j] : (Real)0;
+            bool ok = phi_q(us, es, mm, p, q0);
+            ok &= phi_q(ue, ee, mm, p, q1);
+            if (!ok) set_err(s, ERRB_FIXED_OVERFLOW);
+        }
+        const int prev = __shfl_up_sync(FULL, c0, 1);
+        const bool head = lane == 0 || prev != c0;
+        const unsigned heads = __ballot_sync(FULL, head);
+        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+        const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            long long v = -q0[q];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const long long o = __shfl_up_sync(FULL, v, d);
+                if (lane - d >= start) v += o;
+            }
+            if (tail && c0 >= 0)
+                atomicAdd(reinterpret_cast<unsigned long long*>(&s.pflux[(size_t)q * nc + c0]), (unsigned long long)v);
+        }
+        if (valid && !exited) {
 #pragma unroll
             for (int q = 0; q < 5; ++q)
                 atomicAdd(reinterpret_cast<unsigned long long*>(&s.pflux[(size_t)q * nc + c1]), (unsigned long long)q1[q]);
