@@ -261,7 +261,13 @@ int ugkwp_moments(ugkwp_sim* s, int32_t which, double* out, int32_t out_on_devic
 /* State image: ugkwp_state_info fills the scalar fields (n_particles, step,
  * t, exps); ugkwp_export_state also fills the arrays (which must hold
  * n_particles entries).  ugkwp_import_state replaces the simulation state
- * (W, particles, step, t, exps) from host arrays.  Synchronising.
+ * (W, particles, step, t, exps) from host arrays.  Synchronising.  The
+ * particles are validated and converted to the particle precision on the
+ * host (in parallel) before anything on the device changes; the converted
+ * positions and velocities go through a page-locked host staging buffer
+ * (6, or 7 with K > 0, times n_particles times the particle size in bytes)
+ * that the simulation keeps between imports and frees with ugkwp_free.
+ * Host arrays in page-locked memory copy fastest.
  * Errors: UGKWP_E_ARG, UGKWP_E_CAPACITY, UGKWP_E_STATE (particle outside the
  * mesh index range or not representable in the particle precision). */
 int ugkwp_state_info(ugkwp_sim* s, ugkwp_state* st);

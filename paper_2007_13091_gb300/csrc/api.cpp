@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ugkwp_internal.hpp"
@@ -33,6 +34,10 @@ struct ugkwp_sim {
     PartBufRaw A, B;   // A: the current particles (between steps: the survivors); B: the next survivors
     PartBufRaw Mv;     // the step's movers (particles whose counting flux is non-zero)
     cudaStream_t stream = nullptr;
+    // page-locked host staging of ugkwp_import_state (particle positions and
+    // velocities in the particle precision), kept between imports
+    void* pin = nullptr;
+    size_t pin_bytes = 0;
     int64_t step = 0;
     int32_t n_bc = 0;
     size_t real_size = 8;
@@ -69,6 +74,7 @@ struct ugkwp_sim {
         if (sampled) cudaEventDestroy(sampled);
         if (tracked) cudaEventDestroy(tracked);
         if (gp_ready) cudaEventDestroy(gp_ready);
+        if (pin) cudaFreeHost(pin);
         if (wave) cudaStreamDestroy(wave);
         if (aux) cudaStreamDestroy(aux);
     }
@@ -992,46 +998,76 @@ int ugkwp_import_state(ugkwp_sim* s, const ugkwp_state* st) {
     const int nc = s->M.nc;
     const size_t rs = s->real_size;
     if (s->A.e && n > 0 && !st->e) return fail(UGKWP_E_ARG, "internal energies (e) needed when K > 0");
-    std::vector<char> xs[3], us[3];
-    std::vector<char> es(s->A.e ? (size_t)n * rs : 0);
-    for (int d = 0; d < 3; ++d) {
-        xs[d].resize((size_t)n * rs);
-        us[d].resize((size_t)n * rs);
+    // validate and convert the particles on the host, in parallel, into the
+    // page-locked staging (x[3], u[3], e in the particle precision), before
+    // anything on the device changes
+    const int ncomp = s->A.e ? 7 : 6;
+    const size_t need = (size_t)ncomp * (size_t)n * rs;
+    if (need > s->pin_bytes) {
+        if (s->pin) cudaFreeHost(s->pin);
+        s->pin = nullptr;
+        s->pin_bytes = 0;
+        CU(cudaHostAlloc(&s->pin, need, cudaHostAllocDefault));
+        s->pin_bytes = need;
     }
-    for (int64_t i = 0; i < n; ++i) {
-        if (st->cell[i] < 0 || st->cell[i] >= nc) return fail(UGKWP_E_STATE, "particle cell out of range");
-        if (s->A.e) {
-            const double ev = st->e[i];
-            if (!(ev >= 0.0)) return fail(UGKWP_E_STATE, "negative internal energy");
-            if (rs == 4) {
-                const float ef = (float)ev;
-                if ((double)ef != ev) return fail(UGKWP_E_STATE, "internal energy not representable in binary32");
-                ((float*)es.data())[i] = ef;
-            } else {
-                ((double*)es.data())[i] = ev;
+    char* stage = static_cast<char*>(s->pin);
+    auto comp = [&](int c) { return stage + (size_t)c * (size_t)n * rs; };  // 0-2 x, 3-5 u, 6 e
+    // per range: 0 ok, else the first problem found (1 cell, 2 negative e,
+    // 3 e not binary32, 4 x or u not binary32)
+    auto convert = [&](int64_t lo, int64_t hi) -> int {
+        for (int64_t i = lo; i < hi; ++i) {
+            if (st->cell[i] < 0 || st->cell[i] >= nc) return 1;
+            if (s->A.e) {
+                const double ev = st->e[i];
+                if (!(ev >= 0.0)) return 2;
+                if (rs == 4) {
+                    const float ef = (float)ev;
+                    if ((double)ef != ev) return 3;
+                    ((float*)comp(6))[i] = ef;
+                } else {
+                    ((double*)comp(6))[i] = ev;
+                }
+            }
+            for (int d = 0; d < 3; ++d) {
+                const double xv = st->x[d * n + i], uv = st->u[d * n + i];
+                if (rs == 4) {
+                    const float xf = (float)xv, uf = (float)uv;
+                    if ((double)xf != xv || (double)uf != uv) return 4;
+                    ((float*)comp(d))[i] = xf;
+                    ((float*)comp(3 + d))[i] = uf;
+                } else {
+                    ((double*)comp(d))[i] = xv;
+                    ((double*)comp(3 + d))[i] = uv;
+                }
             }
         }
-        for (int d = 0; d < 3; ++d) {
-            const double xv = st->x[d * n + i], uv = st->u[d * n + i];
-            if (rs == 4) {
-                const float xf = (float)xv, uf = (float)uv;
-                if ((double)xf != xv || (double)uf != uv) return fail(UGKWP_E_STATE, "particle state not representable in binary32");
-                ((float*)xs[d].data())[i] = xf;
-                ((float*)us[d].data())[i] = uf;
-            } else {
-                ((double*)xs[d].data())[i] = xv;
-                ((double*)us[d].data())[i] = uv;
-            }
-        }
+        return 0;
+    };
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int nth = n < (1 << 16) ? 1 : (int)std::min<unsigned>(hw ? hw : 1, 16u);
+    std::vector<int> bad(nth, 0);
+    {
+        std::vector<std::thread> pool;
+        const int64_t per = (n + nth - 1) / nth;
+        for (int t = 1; t < nth; ++t)
+            pool.emplace_back([&, t] { bad[t] = convert(std::min<int64_t>(n, t * per), std::min<int64_t>(n, (t + 1) * per)); });
+        bad[0] = convert(0, std::min<int64_t>(n, per));
+        for (auto& th : pool) th.join();
+    }
+    for (int t = 0; t < nth; ++t) {
+        if (bad[t] == 1) return fail(UGKWP_E_STATE, "particle cell out of range");
+        if (bad[t] == 2) return fail(UGKWP_E_STATE, "negative internal energy");
+        if (bad[t] == 3) return fail(UGKWP_E_STATE, "internal energy not representable in binary32");
+        if (bad[t] == 4) return fail(UGKWP_E_STATE, "particle state not representable in binary32");
     }
     cudaStream_t q = s->stream;
     CU(cudaStreamSynchronize(q));
     for (int d = 0; d < 3; ++d)
         if (n) {
-            CU(cudaMemcpyAsync(s->A.x[d], xs[d].data(), (size_t)n * rs, cudaMemcpyHostToDevice, q));
-            CU(cudaMemcpyAsync(s->A.u[d], us[d].data(), (size_t)n * rs, cudaMemcpyHostToDevice, q));
+            CU(cudaMemcpyAsync(s->A.x[d], comp(d), (size_t)n * rs, cudaMemcpyHostToDevice, q));
+            CU(cudaMemcpyAsync(s->A.u[d], comp(3 + d), (size_t)n * rs, cudaMemcpyHostToDevice, q));
         }
-    if (n && s->A.e) CU(cudaMemcpyAsync(s->A.e, es.data(), (size_t)n * rs, cudaMemcpyHostToDevice, q));
+    if (n && s->A.e) CU(cudaMemcpyAsync(s->A.e, comp(6), (size_t)n * rs, cudaMemcpyHostToDevice, q));
     if (n) {
         CU(cudaMemcpyAsync(s->A.m, st->m, (size_t)n * 8, cudaMemcpyHostToDevice, q));
         CU(cudaMemcpyAsync(s->A.cell, st->cell, (size_t)n * 4, cudaMemcpyHostToDevice, q));
