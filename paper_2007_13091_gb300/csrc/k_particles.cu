@@ -294,10 +294,7 @@ template <> struct Trk<float> {
         const float4 v = m.trk_f[tet].pl[k];
         nx = v.x; ny = v.y; nz = v.z; d = v.w;
     }
-    __device__ static __forceinline__ int nb(const DevMesh& m, int tet, int k) {
-        const int4 v = m.trk_f[tet].nb;
-        return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
-    }
+    __device__ static __forceinline__ int4 nbv(const DevMesh& m, int tet) { return m.trk_f[tet].nb; }
     __device__ static __forceinline__ float tau(const DevState& s, int c) { return s.tauf[c]; }
     __device__ static __forceinline__ float tf(float tau, unsigned long long r) {
         return -(tau * dm::f_log(dm::u01f(r)));
@@ -309,10 +306,7 @@ template <> struct Trk<double> {
         const Dbl4 v = m.trk_d[tet].pl[k];
         nx = v.x; ny = v.y; nz = v.z; d = v.w;
     }
-    __device__ static __forceinline__ int nb(const DevMesh& m, int tet, int k) {
-        const int4 v = m.trk_d[tet].nb;
-        return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
-    }
+    __device__ static __forceinline__ int4 nbv(const DevMesh& m, int tet) { return m.trk_d[tet].nb; }
     __device__ static __forceinline__ double tau(const DevState& s, int c) { return s.tau[c]; }
     __device__ static __forceinline__ double tf(double tau, unsigned long long r) {
         return -(tau * dm::d_log(dm::u01d(r)));
@@ -486,6 +480,9 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
             int last = -1;
             Real t0 = (Real)0;
             for (;;) {
+                // the tet's neighbour codes, loaded with its planes (they sit in
+                // another sector of the tet's record)
+                const int4 nbv = Trk<Real>::nbv(m, tet);
                 // smallest crossing time (d - n.x0)/(u.n) over u.n > 0, compared
                 // by cross products (positive denominators), one division
                 int best = -1;
@@ -517,7 +514,7 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
                     for (int c = 0; c < 3; ++c) xe[c] = x0[c];
                     break;
                 }
-                const int code = Trk<Real>::nb(m, tet, best);
+                const int code = best == 0 ? nbv.x : best == 1 ? nbv.y : best == 2 ? nbv.z : nbv.w;
                 if (code >= 0) { tet = code >> 2; last = code & 3; continue; }
                 const int bi = -1 - code;
                 const DevBc& bc = p.bc[m.bf_tag[bi]];
