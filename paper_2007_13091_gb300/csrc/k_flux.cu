@@ -191,13 +191,16 @@ __device__ __forceinline__ void venkat_ratio(double d1, double d2, double eps2, 
 // Limited gradient of quantity q (0..4: W, 5: rho^h) of cell i.
 __device__ __forceinline__ void gradient_of(const DevMesh& m, const DevState& s, const DevParams& p, int i, int q) {
     const int nc = m.nc;
-    const int own = m.cfs[i];
     const double self = q < 5 ? s.W[(size_t)q * nc + i] : s.rhoh[i];
+    // the neighbour across each local face, from the tet's tracking record
+    // (neighbour << 2 | its local face, or -1 - boundary face): one load
+    // instead of a face index and then its cells
+    const int4 nbv = m.trk_f ? m.trk_f[i].nb : m.trk_d[i].nb;
     double val[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const int f = m.cf[k * nc + i];
-        const int other = ((own >> k) & 1) ? m.f_nbr[f] : m.f_own[f];
+        const int ck = k == 0 ? nbv.x : k == 1 ? nbv.y : k == 2 ? nbv.z : nbv.w;
+        const int other = ck >= 0 ? ck >> 2 : ck;
         if (other >= 0) {
             val[k] = q < 5 ? s.W[(size_t)q * nc + other] : s.rhoh[other];
         } else {
