@@ -92,6 +92,41 @@ def test_adjoint_o2_matches_oracle_reference(precision, theta, Pr, functional):
     assert (np.abs(r1[1:] - ref[1:]) / np.abs(ref[1:])).max() > 1e-3
 
 
+@pytest.mark.parametrize("order", [1, 2])
+def test_adjoint_with_specular_sides(order):
+    """The channel with its y sides specular (tag 2) and its z sides diffuse
+    walls (tag 1, listed): at second order the reconstruction's mirrored
+    momentum ghosts enter the reverse sweep; J and dJ/dtheta against the
+    oracle's reference (dual numbers at first order, central differences of
+    the second-order map with the limiter frozen)."""
+    import torch
+    cfg = wl.wall_channel(precision="mixed", order=order)
+    nodes, bf = cfg["mesh"]["nodes"], cfg["mesh"]["bfaces"]
+    y = nodes[bf][:, :, 1]
+    side_y = np.all(y == 0.0, axis=1) | np.all(y == 0.5, axis=1)
+    cfg["mesh"]["btags"] = np.where(side_y, 2, cfg["mesh"]["btags"]).astype(np.int32)
+    cfg["params"]["bc"] = list(cfg["params"]["bc"]) + [{"type": "specular"}]
+    g = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], stream=torch.cuda.Stream())
+    g.step(2)
+    st = g.state()
+    th = _theta0()
+    o = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    o.set_state(st)
+    fr = o.record_frozen(K)
+    for functional in (0, 1):
+        g.set_state(st)
+        out = g.adjoint(functional, K, [1], th)
+        if order == 1:
+            ref = o.frozen_objective(fr, th, functional=functional, tags=[1])
+        else:
+            ref = o.frozen_o2_gradient(fr, th, functional=functional, tags=[1])
+        assert out[0] == pytest.approx(ref[0], rel=1e-10)
+        scale = np.abs(ref[1:]).max()
+        for k in range(3):
+            assert abs(out[1 + k] - ref[1 + k]) <= 1e-6 * max(abs(ref[1 + k]), 1e-3 * scale), (k, out, ref)
+    assert side_y.any() and (cfg["mesh"]["btags"] == 1).any()
+
+
 def _teacher_forced_record(g, st, o, n_steps):
     """The frozen data of n_steps steps of the GPU simulation from state st,
     each step taken by the oracle from the GPU's state before it (so the
