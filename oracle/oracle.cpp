@@ -20,6 +20,14 @@
 //
 // Readings where the paper is silent are listed in the repository design
 // notes; each is marked "reading:" below.
+//
+// Parity unpinned (no pin independent of this code beyond conservation, the
+// free-molecular profile and the continuum limit): the upwind reading of the
+// wave's free transport in interior_flux, the far-field ghost of
+// boundary_flux (all hydrodynamic, emitting no particles), and the
+// least-squares weights and limiter constant of limited_gradients (pinned
+// only through properties any such choice has: exact gradients of linear
+// fields, the limiter's bounds and its relaxation as epsilon grows).
 #include "ugkwp_oracle.h"
 #include "omath.hpp"
 #include "dual.hpp"
