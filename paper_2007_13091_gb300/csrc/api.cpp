@@ -125,6 +125,7 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, bool with_e, Carver& c, 
     const size_t nc = mh.nc, nf = mh.nf, nbf = mh.nbf;
     M.nc = mh.nc; M.nf = mh.nf; M.nbf = mh.nbf; M.nif = mh.nf - mh.nbf;
     M.vol = c.take<double>(nc);
+    M.ivol = c.take<double>(nc);
     M.dS = c.take<double>(3 * nc);
     M.vtx = c.take<double>(12 * nc);
     M.cf = c.take<int32_t>(4 * nc);
@@ -544,6 +545,9 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     cudaError_t ce = cudaSuccess;
 #define UP(dst, src, bytes) if (ce == cudaSuccess) ce = up(dst, src, bytes)
     UP(s->M.vol, mh.vol.data(), nc * sizeof(double));
+    std::vector<double> ivol(nc);
+    for (int i = 0; i < nc; ++i) ivol[i] = 1.0 / mh.vol[i];
+    UP(s->M.ivol, ivol.data(), nc * sizeof(double));
     UP(s->M.dS, dS.data(), dS.size() * sizeof(double));
     UP(s->M.vtx, vtx.data(), vtx.size() * sizeof(double));
     UP(s->M.cf, cf.data(), cf.size() * sizeof(int32_t));

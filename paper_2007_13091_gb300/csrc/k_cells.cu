@@ -236,7 +236,9 @@ __global__ void k_cell_update(DevMesh m, DevState s, DevParams p) {
     const int own = m.cfs[i];
 #pragma unroll
     for (int k = 0; k < 4; ++k) f[k] = m.cf[k * nc + i];
-    const double vol = m.vol[i];
+    // 1/|Omega| once per cell (the factor of the update) instead of ten
+    // binary64 divisions
+    const double ivol = m.ivol[i];
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         double acc = 0.0;
@@ -247,7 +249,7 @@ __global__ void k_cell_update(DevMesh m, DevState s, DevParams p) {
         }
         const double fp = (double)s.pflux[(size_t)q * nc + i] * p.qscale[q];
         double& w = s.W[(size_t)q * nc + i];
-        w = (w - acc / vol) + fp / vol;
+        w = (w - acc * ivol) + fp * ivol;
         if (p.averaging) s.wsum[(size_t)q * nc + i] += s.dt[0] * w;
     }
 }

@@ -89,6 +89,7 @@ struct DevMesh {
     int32_t nc, nf, nbf;
     int32_t nif;             // interior faces (they lead face_order)
     const double* vol;       // [nc]
+    const double* ivol;      // [nc] 1 / vol
     const double* dS;        // [3][nc]
     const double* vtx;       // [12][nc]: vertex k coordinate c at [(3k+c) nc + i]
     const int32_t* cf;       // [4][nc] face of local face k
