@@ -51,8 +51,8 @@ TRACK_DRAM_BYTES = {"mixed": 963773184 + 981693184 + 27904, "fp64": None}
 # Binary64 flops per interior face of k_face_flux_o2 (the second-order wave flux):
 # ncu's executed dadd + dmul + 2 dfma per launch divided by the interior faces, on
 # this workload (profiles/); None until captured for the current kernel.
-FLUX_O2_FLOPS_PER_FACE = (29802880 + 80156800 + 2 * 146472960) / 162432
-FLUX_O2_DRAM_BYTES = 30781952 + 0
+FLUX_O2_FLOPS_PER_FACE = None
+FLUX_O2_DRAM_BYTES = None
 # FP64 peak: 2 FP64 FMA lanes per clock per SM (the nominal 1.25 TFLOP/s of this
 # part at 152 SMs and 2.07 GHz), 2 flops per FMA
 FP64_FMA_LANES_PER_SM = 2

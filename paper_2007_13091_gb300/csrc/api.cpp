@@ -680,11 +680,12 @@ int enqueue_step(ugkwp_sim* s) {
                 if (gp) launch_gp_coef(s->M, s->S, s->P, s->wave);
             });
         if (gp) CU(cudaEventRecord(s->gp_ready, s->wave));
-        if (s->P.order == 2 && s->M.nif > 0)
+        // order 2: one kernel, interior faces at second order then the boundary
+        // faces at first order; order 1: every face at first order
+        if (s->P.order == 2)
             timed(s, UGKWP_K_FLUX_O2, 1, s->wave, [&] { launch_face_flux_o2(s->M, s->S, s->P, s->lc.wave_blocks, s->wave); });
-        const int first = s->P.order == 2 ? s->M.nif : 0;
-        if (s->M.nf > first)
-            timed(s, UGKWP_K_FLUX, 1, s->wave, [&] { launch_face_flux(s->M, s->S, s->P, first, s->lc.wave_blocks, s->wave); });
+        else
+            timed(s, UGKWP_K_FLUX, 1, s->wave, [&] { launch_face_flux(s->M, s->S, s->P, 0, s->lc.wave_blocks, s->wave); });
         CU(cudaEventRecord(s->join, s->wave));
         timed(s, UGKWP_K_SCAN, 2, q, [&] { launch_scan(s->M, s->S, s->P, q); });
         if (gp) CU(cudaStreamWaitEvent(q, s->gp_ready, 0));  // the sampler reads the g_p coefficients
@@ -733,10 +734,10 @@ int enqueue_gks_step(ugkwp_sim* s, int32_t mode) {
     timed(s, UGKWP_K_SAMPLE_COUNT, 1, q, [&] { launch_sample_count(s->M, s->S, P, q); });
     if (P.order == 2)
         timed(s, UGKWP_K_GRADIENTS, 1, q, [&] { launch_gradients(s->M, s->S, P, q); });
-    if (P.order == 2 && s->M.nif > 0)
+    if (P.order == 2)
         timed(s, UGKWP_K_FLUX_O2, 1, q, [&] { launch_face_flux_o2(s->M, s->S, P, s->lc.wave_blocks, q); });
-    const int first = P.order == 2 ? s->M.nif : 0;
-    if (s->M.nf > first) timed(s, UGKWP_K_FLUX, 1, q, [&] { launch_face_flux(s->M, s->S, P, first, 0, q); });
+    else
+        timed(s, UGKWP_K_FLUX, 1, q, [&] { launch_face_flux(s->M, s->S, P, 0, 0, q); });
     timed(s, UGKWP_K_UPDATE, 1, q, [&] { launch_cell_update(s->M, s->S, P, q); });
     return UGKWP_OK;
 }

@@ -685,14 +685,21 @@ __global__ void __launch_bounds__(128) k_gp_coef(DevMesh m, DevState s, DevParam
     s.gpc[(size_t)13 * nc + i] = 1.0 + Phi;
 }
 
-// Second-order flux of the interior faces (the first nif entries of face_order).
+__device__ __forceinline__ void face_flux_o1(const DevMesh& m, const DevState& s, const DevParams& p, int t);
+
+// Second-order flux of the interior faces (the first nif entries of face_order),
+// then the first-order flux of the boundary faces that follow them.
 // With local time steps (GKS step) each face is integrated over the smaller
 // step of its cells and stores the mean flux rate F / dt_f.
 __global__ void __launch_bounds__(UGKWP_WAVE_THREADS, UGKWP_WAVE_MIN_BLOCKS) k_face_flux_o2(DevMesh m, DevState s, DevParams p) {
     const int nf = m.nf;
     const double dt = s.dt[0];
     const double inv_Tref = 1.0 / p.T_ref;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.nif; t += gridDim.x * blockDim.x) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+        if (t >= m.nif) {  // the boundary faces follow, at first order, in the same grid
+            face_flux_o1(m, s, p, t);
+            continue;
+        }
         const int f = m.face_order[t];
         const int o = m.f_own[f], nb = m.f_nbr[f];
         const double n[3] = {m.f_n[f], m.f_n[nf + f], m.f_n[2 * nf + f]};
@@ -788,7 +795,7 @@ void launch_gp_coef(const DevMesh& m, const DevState& s, const DevParams& p, cud
 }
 
 void launch_face_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p, int blocks, cudaStream_t st) {
-    k_face_flux_o2<<<wave_grid(m.nif, blocks), UGKWP_WAVE_THREADS, 0, st>>>(m, s, p);
+    k_face_flux_o2<<<wave_grid(m.nf, blocks), UGKWP_WAVE_THREADS, 0, st>>>(m, s, p);
 }
 
 int wave_threads() { return UGKWP_WAVE_THREADS; }
