@@ -47,12 +47,14 @@ TRACK_BYTES_PER_CELL = {"mixed": 80 + 8, "fp64": 144 + 8}
 # launches) on this workload, from the ncu capture summarised in
 # profiles/k_track_k_face_flux_o2_cavity24_mixed.md; set to None whenever the
 # kernel changes until it is captured again
-TRACK_DRAM_BYTES = {"mixed": 963773184 + 981693184 + 27904, "fp64": None}
+TRACK_DRAM_BYTES = {"mixed": 962697216 + 980654336 + 28416, "fp64": None}
 # Binary64 flops per interior face of k_face_flux_o2 (the second-order wave flux):
 # ncu's executed dadd + dmul + 2 dfma per launch divided by the interior faces, on
 # this workload (profiles/); None until captured for the current kernel.
-FLUX_O2_FLOPS_PER_FACE = None
-FLUX_O2_DRAM_BYTES = None
+# (the kernel also takes the boundary faces' first-order flux after the
+# interior faces: their flops are included, counted per interior face)
+FLUX_O2_FLOPS_PER_FACE = (29934208 + 80965504 + 2 * 148104192) / 162432
+FLUX_O2_DRAM_BYTES = 31148800 + 512
 # FP64 peak: 2 FP64 FMA lanes per clock per SM (the nominal 1.25 TFLOP/s of this
 # part at 152 SMs and 2.07 GHz), 2 flops per FMA
 FP64_FMA_LANES_PER_SM = 2
@@ -643,7 +645,8 @@ def main():
         n_if = sim.n_faces - sim.n_bfaces
         flops = FLUX_O2_FLOPS_PER_FACE * n_if if FLUX_O2_FLOPS_PER_FACE else None
         ach = flops / (flux_ms * 1e-3) / 1e12 if flops else None
-        roof_flux = {"kernel": "k_face_flux_o2 (a3-a4: second-order wave flux of the interior faces)",
+        roof_flux = {"kernel": "k_face_flux_o2 (a3-a4: second-order wave flux of the interior faces, then the "
+                               "first-order flux of the boundary faces)",
                      "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": ach / fp64_peak if ach else None,
                      "peak_kind": f"FP64 nominal: {props.multi_processor_count} SMs x {FP64_FMA_LANES_PER_SM} "
