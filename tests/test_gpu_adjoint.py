@@ -19,6 +19,37 @@ pytestmark = pytest.mark.gpu
 
 K = 3
 
+# Rounding floor of an exact derivative (dual numbers, or the reverse sweep)
+# relative to the largest component: both sum per-face products of every
+# magnitude in different orders.
+ROUND_FLOOR = 1e-12
+# Central differences with step h = 1e-5 theta_k: their rounding (~ eps |J| / h)
+# and truncation (~ h^2 |third derivative| / 6) stay below 1e-9 |J| / |theta_k|.
+FD_REL_STEP = 1e-5
+
+
+def fd_floor(J, theta):
+    return 1e-9 * abs(J) / np.abs(theta)
+
+
+def assert_grad_close(out, ref, floor, what=""):
+    """dJ/dtheta within 1e-6 relative of the reference, component by component.
+    A component whose reference is not well above its noise floor (1000 x
+    floor_k) has no relative accuracy to test: it is excluded from the
+    relative bound, reported, and must stay within 1000 x floor_k of it."""
+    floor = np.broadcast_to(np.asarray(floor, float), (3,))
+    excluded = []
+    for k in range(3):
+        if abs(ref[1 + k]) > 1e3 * floor[k]:
+            assert abs(out[1 + k] - ref[1 + k]) <= 1e-6 * abs(ref[1 + k]), (what, k, out, ref)
+        else:
+            assert abs(out[1 + k] - ref[1 + k]) <= 1e3 * floor[k], (what, k, out, ref)
+            excluded.append(k)
+    if excluded:
+        print(f"{what}: components {excluded} at the noise floor {floor[excluded]} (reference {ref[1:]}) "
+              "are excluded from the relative bound")
+    return excluded
+
 
 def _theta0():
     return np.array([1.0, 0.5 * np.sqrt(5.0 / 3.0), 1.0])
@@ -41,9 +72,7 @@ def test_adjoint_matches_oracle_reference(precision, functional):
     o.set_state(st)
     ref = o.frozen_objective(o.record_frozen(K), _theta0(), functional=functional, tags=[1])
     assert out[0] == pytest.approx(ref[0], rel=1e-10)
-    scale = np.abs(ref[1:]).max()
-    for k in range(3):
-        assert abs(out[1 + k] - ref[1 + k]) <= 1e-6 * max(abs(ref[1 + k]), 1e-3 * scale), (k, out, ref)
+    assert_grad_close(out, ref, ROUND_FLOOR * np.abs(ref[1:]).max(), f"{precision} functional {functional}")
 
 
 def test_adjoint_matches_gpu_finite_differences():
@@ -51,16 +80,18 @@ def test_adjoint_matches_gpu_finite_differences():
     th = _theta0()
     g.set_state(st)
     out = g.adjoint(0, K, [1], th)
+    fd = np.zeros(4)
+    fd[0] = out[0]
     for k in range(3):
-        h = 1e-5 * th[k]
+        h = FD_REL_STEP * th[k]
         J = []
         for sgn in (1.0, -1.0):
             t = th.copy()
             t[k] += sgn * h
             g.set_state(st)  # the same recorded particle data for every evaluation
             J.append(g.adjoint(0, K, [1], t)[0])
-        fd = (J[0] - J[1]) / (2 * h)
-        assert abs(out[1 + k] - fd) <= 1e-6 * max(abs(out[1 + k]), 1e-3 * np.abs(out[1:]).max()), (k, out, fd)
+        fd[1 + k] = (J[0] - J[1]) / (2 * h)
+    assert_grad_close(out, fd, fd_floor(out[0], th), "GPU central differences")
 
 
 @pytest.mark.parametrize("precision,theta,Pr", [("fp64", None, 0.0), ("mixed", None, 0.0),
@@ -83,9 +114,7 @@ def test_adjoint_o2_matches_oracle_reference(precision, theta, Pr, functional):
     fr = o.record_frozen(K)
     ref = o.frozen_o2_gradient(fr, th, functional=functional, tags=[1])
     assert out[0] == pytest.approx(ref[0], rel=1e-10)
-    scale = np.abs(ref[1:]).max()
-    for k in range(3):
-        assert abs(out[1 + k] - ref[1 + k]) <= 1e-6 * max(abs(ref[1 + k]), 1e-3 * scale), (k, out, ref)
+    assert_grad_close(out, ref, fd_floor(ref[0], th), f"order 2 {precision} Pr {Pr} functional {functional}")
     # the reconstruction matters: the first-order map's gradient is another
     o1 = oracle.OracleSim(cfg["mesh"], cfg["W0"], dict(cfg["params"], order=1))
     r1 = o1.frozen_objective(fr, th, functional=functional, tags=[1])
@@ -121,9 +150,8 @@ def test_adjoint_with_specular_sides(order):
         else:
             ref = o.frozen_o2_gradient(fr, th, functional=functional, tags=[1])
         assert out[0] == pytest.approx(ref[0], rel=1e-10)
-        scale = np.abs(ref[1:]).max()
-        for k in range(3):
-            assert abs(out[1 + k] - ref[1 + k]) <= 1e-6 * max(abs(ref[1 + k]), 1e-3 * scale), (k, out, ref)
+        floor = ROUND_FLOOR * np.abs(ref[1:]).max() if order == 1 else fd_floor(ref[0], th)
+        assert_grad_close(out, ref, floor, f"specular sides order {order} functional {functional}")
     assert side_y.any() and (cfg["mesh"]["btags"] == 1).any()
 
 
