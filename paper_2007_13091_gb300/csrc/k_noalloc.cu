@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(1024) k_dt_final(const double* __restrict__ pa
 }
 
 // Device address of g_dt_partial, looked up once per device (the host-side
-// name of the array is only a stand-in for it).
+// name of the array is only a stand-in for it) and kept for the life of the
+// process: a device reset makes it stale (documented in the header).
 std::mutex g_mu;
 double* g_ptr[256] = {};
 
