@@ -401,7 +401,7 @@ def gp1_sampling(device, steps, warmup, launch_cfg):
     cfg = workload("mixed")
     cfg["params"]["sampling"] = "gp1"
     sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=torch.cuda.Stream(device=device))
-    ugkwp.ugkwp_set_launch_cfg(sim.handle, launch_cfg["particle_blocks"], launch_cfg["wave_blocks"])
+    ugkwp.ugkwp_set_launch_cfg(sim.handle, **launch_cfg)
     sim.step(200)
     ms, moves, _, kms, _ = time_steps(sim, steps, warmup, 1)
     sim.close()
@@ -420,7 +420,7 @@ def diatomic(device, steps, warmup, launch_cfg):
     from paper_2007_13091_gb300 import workloads as wl
     cfg = wl.cavity(n=24, Kn=0.075, N_ref=100, precision="mixed", order=ORDER, K=2)
     sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=torch.cuda.Stream(device=device))
-    ugkwp.ugkwp_set_launch_cfg(sim.handle, launch_cfg["particle_blocks"], launch_cfg["wave_blocks"])
+    ugkwp.ugkwp_set_launch_cfg(sim.handle, **launch_cfg)
     sim.step(200)
     ms, moves, _, kms, _ = time_steps(sim, steps, warmup, 1)
     sim.close()

@@ -295,22 +295,34 @@ enum {
 };
 
 /* ---- launch configuration and autotuning -------------------------------
- * Grid sizes of the step kernels that loop over their work.  Results do not
- * depend on them (every particle draws from its own counter-based stream and
- * every sum over particles is fixed point), only the speed does. */
+ * Grid sizes and block shapes of the step kernels that loop over their work.
+ * Results do not depend on them (every particle draws from its own
+ * counter-based stream and every sum over particles is fixed point), only the
+ * speed does. */
 typedef struct {
     int32_t particle_blocks;     /* blocks of the sampling, tracking and movers kernels (> 0) */
     int32_t wave_blocks;         /* blocks of the persistent second-order wave kernels (> 0) */
+    int32_t track_threads;       /* particles per tracking tile, one per thread of a block: 128 or 256 */
+    int32_t track_stages;        /* 0: each thread loads its particle when its tile starts; 2 or 3:
+                                  * tiles are copied into shared memory by bulk copies (TMA),
+                                  * track_stages - 1 tiles ahead of the one being walked */
+    int32_t smem_carveout;       /* preferred shared-memory carveout of the step's kernels, percent of
+                                  * the largest (0..100), or -1 for the driver's choice.  A kernel
+                                  * attribute: it holds for every simulation of the process */
+    int32_t reserved;            /* 0 */
 } ugkwp_launch_cfg;
 
 int ugkwp_get_launch_cfg(const ugkwp_sim* s, ugkwp_launch_cfg* out);
 /* Takes effect at the next step (the step graphs are recaptured). */
 int ugkwp_set_launch_cfg(ugkwp_sim* s, const ugkwp_launch_cfg* cfg);
-/* Autotuner: for each candidate grid pair (particle blocks 1, 2, 4, 8 or 16 per
- * SM; wave blocks 1 or 2 per SM at order 2) runs 2 warm-up steps and
- * steps_per_trial timed steps (even, >= 2) on the bound stream, keeps the
- * fastest pair and returns it in *best (may be NULL).  The trial steps advance
- * the simulation like any other steps.  E_STATE while per-kernel timing is on. */
+/* Autotuner: for each candidate configuration -- tracking shape (128 threads
+ * with 0, 2 or 3 stages, 256 threads with 2 stages) x resident tracking threads
+ * per SM (1024 or 2048, the grid split in its two launches) x wave blocks (1 or
+ * 2 per SM at order 2) x carveout (driver's choice, 58% or 86% for every kernel
+ * of the step) -- runs 2 warm-up steps and steps_per_trial timed steps (even,
+ * >= 2) on the bound stream, keeps the fastest and returns it in *best (may be
+ * NULL).  The trial steps advance the simulation like any other steps.
+ * E_STATE while per-kernel timing is on. */
 int ugkwp_autotune(ugkwp_sim* s, int32_t steps_per_trial, ugkwp_launch_cfg* best);
 
 /* ---- batches of independent simulations --------------------------------
@@ -406,7 +418,10 @@ int ugkwp_adjoint_wave(ugkwp_sim* s, const ugkwp_adjoint_req* r, double* out);
  * the library holds until the process exits; n_cells above
  * UGKWP_NOALLOC_MAX_CELLS is rejected with UGKWP_E_ARG.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Every call
+ * device current; make that first call before any stream capture.  The address
+ * is kept for the life of the process: after cudaDeviceReset (or anything else
+ * that destroys the device's primary context) it is stale, so do not call this
+ * entry point on that device again in the same process.  Every call
  * shares the array and leaves its contents behind (each call writes every slot
  * it reads, so nothing needs clearing): calls whose work overlaps on the GPU,
  * on any streams, race and must be ordered by the caller.  The call returns

@@ -51,7 +51,7 @@ struct ugkwp_sim {
     cudaStream_t wave = nullptr, aux = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, sampled = nullptr, tracked = nullptr, gp_ready = nullptr;
     // grid sizes of the looping step kernels
-    LaunchCfg lc{0, 0};
+    LaunchCfg lc{0, 0, {128, 0}, -1};
     // two-step CUDA graphs, one per ping-pong parity (keyed by buffer A), with
     // the kernels each one launches per class
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -169,6 +169,8 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, bool with_e, Carver& c, 
     S.smass_next = c.take<int64_t>(nc);
     S.cnt = c.take<int32_t>(nc);
     S.soff = c.take<int32_t>(nc);
+    S.wcap = c.take<int32_t>(nc);
+    S.woff = c.take<int32_t>(nc);
     S.pflux = c.take<int64_t>(5 * nc);
     S.wacc = c.take<int64_t>(5 * nc);
     S.mom = c.take<double>(5 * nc);
@@ -179,14 +181,18 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, bool with_e, Carver& c, 
     S.t = c.take<double>(1);
     S.dt = c.take<double>(1);
     S.cnt64 = c.take<int64_t>(CNT_SLOTS);
+    // each particle array holds the capacity rounded up to whole tiles of the
+    // tracking kernel (TRACK_TILE_MAX particles), so that a tile's bulk copies
+    // into shared memory stay inside the array
+    const size_t capt = ((size_t)cap + TRACK_TILE_MAX - 1) / TRACK_TILE_MAX * TRACK_TILE_MAX;
     for (PartBufRaw* pb : {&A, &B, &Mv}) {
-        for (int d = 0; d < 3; ++d) pb->x[d] = c.take<char>(rs * (size_t)cap);
-        for (int d = 0; d < 3; ++d) pb->u[d] = c.take<char>(rs * (size_t)cap);
-        pb->m = c.take<double>((size_t)cap);
-        pb->cell = c.take<int32_t>((size_t)cap);
-        pb->id = c.take<uint64_t>((size_t)cap);
-        pb->e = with_e ? (void*)c.take<char>(rs * (size_t)cap) : nullptr;
-        pb->e2 = (with_e && pb == &Mv) ? (void*)c.take<char>(rs * (size_t)cap) : nullptr;
+        for (int d = 0; d < 3; ++d) pb->x[d] = c.take<char>(rs * capt);
+        for (int d = 0; d < 3; ++d) pb->u[d] = c.take<char>(rs * capt);
+        pb->m = c.take<double>(capt);
+        pb->cell = c.take<int32_t>(capt);
+        pb->id = c.take<uint64_t>(capt);
+        pb->e = with_e ? (void*)c.take<char>(rs * capt) : nullptr;
+        pb->e2 = (with_e && pb == &Mv) ? (void*)c.take<char>(rs * capt) : nullptr;
     }
 }
 
@@ -241,7 +247,8 @@ int ceil_log2(double b) {
 
 // Fixed-point quanta 2^e_q: e_q = ceil(log2 B_q) - 50 with B_mass the largest
 // cell mass, B_mom = B_mass c, B_E = B_mass c^2 / 2, c the largest |U| + 5 sqrt(RT)
-// over the cells and the wall / far-field states.
+// over the cells and the wall / far-field states, with p = (rho E - rho |U|^2 / 2)
+// / ((3 + K) / 2) for K internal degrees of freedom.
 void fixed_point_exponents(const MeshHost& mh, const ugkwp_params& p, const double* W, int32_t e[5]) {
     const int nc = mh.nc;
     double bm = 0.0, cmax = 0.0;
@@ -249,7 +256,7 @@ void fixed_point_exponents(const MeshHost& mh, const ugkwp_params& p, const doub
         const double rho = Wv[0];
         const double U[3] = {Wv[stride] / rho, Wv[2 * stride] / rho, Wv[3 * stride] / rho};
         const double U2 = (U[0] * U[0] + U[1] * U[1]) + U[2] * U[2];
-        const double pr = (Wv[4 * stride] - 0.5 * (rho * U2)) / 1.5;
+        const double pr = (Wv[4 * stride] - 0.5 * (rho * U2)) / (1.5 + 0.5 * (double)p.K);
         const double T = pr / (rho * p.R);
         return std::sqrt((U[0] * U[0] + U[1] * U[1]) + U[2] * U[2]) + 5.0 * std::sqrt(p.R * T);
     };
@@ -281,6 +288,14 @@ void set_exps(DevParams& P, const int32_t e[5]) {
     }
 }
 
+// Kernel attributes of a launch configuration (set outside stream capture).
+cudaError_t configure_kernels(const DevParams& P, const LaunchCfg& lc) {
+    cudaError_t e = configure_particle_kernels(P, lc.track, lc.carveout);
+    if (e == cudaSuccess) e = configure_wave_kernels(lc.carveout);
+    if (e == cudaSuccess) e = configure_cell_kernels(lc.carveout);
+    return e;
+}
+
 int read_error(ugkwp_sim* s) {
     int64_t h[CNT_SLOTS];
     CU(cudaMemcpyAsync(h, s->S.cnt64, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
@@ -295,6 +310,11 @@ int read_error(ugkwp_sim* s) {
     if (e & ERRB_TRACK_LIMIT) return fail(UGKWP_E_TRACK_LIMIT, std::to_string(h[CNT_LOST]) + " particles exceeded max_crossings");
     if (e & ERRB_FIXED_OVERFLOW) return fail(UGKWP_E_FIXED_OVERFLOW, "fixed-point particle flux overflow");
     if (e & ERRB_SAMPLE_LIMIT) return fail(UGKWP_E_CAPACITY, "more than 65534 particles sampled in one cell");
+    if (e & ERRB_SORT)
+        return fail(UGKWP_E_STATE, "survivor counts per cell disagree with the survivors: the particle state is not valid");
+    if (e & ERRB_STAGE_WAIT)
+        return fail(UGKWP_E_CUDA, "a bulk copy of particles into shared memory did not complete within its wait "
+                                  "limit: the step's particle state is not valid");
     return fail(UGKWP_E_STATE, "device error word " + std::to_string(e));
 }
 
@@ -591,6 +611,13 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     }
     s->lc.particle_blocks = particle_grid();
     s->lc.wave_blocks = sm_count();
+    s->lc.track = TrackShape{128, 0};
+    s->lc.carveout = -1;
+    ce = configure_kernels(s->P, s->lc);
+    if (ce != cudaSuccess) {
+        delete s;
+        return cuda_fail(ce, "ugkwp_init kernel attributes");
+    }
     *out = s;
     return UGKWP_OK;
 }
@@ -702,18 +729,19 @@ int enqueue_step(ugkwp_sim* s) {
         const int first_half = (s->lc.particle_blocks + 1) / 2;
         timed(s, UGKWP_K_TRACK, s->lc.particle_blocks > first_half ? 2 : 1, q, [&] {
             ce = cudaEventRecord(s->sampled, q);
-            launch_track(s->M, s->S, s->P, s->A, s->B, s->Mv, first_half, q);
+            launch_track(s->M, s->S, s->P, s->A, s->B, s->Mv, s->lc.track, first_half, q);
             if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s->aux, s->sampled, 0);
             if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s->aux, s->join, 0);
             if (s->lc.particle_blocks > first_half)
-                launch_track(s->M, s->S, s->P, s->A, s->B, s->Mv, s->lc.particle_blocks - first_half, s->aux);
+                launch_track(s->M, s->S, s->P, s->A, s->B, s->Mv, s->lc.track, s->lc.particle_blocks - first_half,
+                             s->aux);
             if (ce == cudaSuccess) ce = cudaEventRecord(s->tracked, s->aux);
             if (ce == cudaSuccess) ce = cudaStreamWaitEvent(q, s->tracked, 0);
         });
         if (ce != cudaSuccess) return cuda_fail(ce, "tracking launch order");
         timed(s, UGKWP_K_MOVERS, 1, q, [&] { launch_movers(s->M, s->S, s->P, s->Mv, s->lc.particle_blocks, q); });
         CU(cudaStreamWaitEvent(q, s->join, 0));  // join before the update reads F (already joined via aux)
-        timed(s, UGKWP_K_UPDATE, 1, q, [&] { launch_cell_update(s->M, s->S, s->P, q); });
+        timed(s, UGKWP_K_UPDATE, 1, q, [&] { launch_cell_update(s->M, s->S, s->P, s->B.cell, q); });
         std::swap(s->A, s->B);
         std::swap(s->S.nleft, s->S.nleft_next);
         std::swap(s->S.smass, s->S.smass_next);
@@ -738,7 +766,7 @@ int enqueue_gks_step(ugkwp_sim* s, int32_t mode) {
         timed(s, UGKWP_K_FLUX_O2, 1, q, [&] { launch_face_flux_o2(s->M, s->S, P, s->lc.wave_blocks, q); });
     else
         timed(s, UGKWP_K_FLUX, 1, q, [&] { launch_face_flux(s->M, s->S, P, 0, 0, q); });
-    timed(s, UGKWP_K_UPDATE, 1, q, [&] { launch_cell_update(s->M, s->S, P, q); });
+    timed(s, UGKWP_K_UPDATE, 1, q, [&] { launch_cell_update(s->M, s->S, P, nullptr, q); });
     return UGKWP_OK;
 }
 
@@ -746,7 +774,9 @@ int enqueue_gks_step(ugkwp_sim* s, int32_t mode) {
 int launch_step_pair(ugkwp_sim* s, bool& used) {
     used = false;
     if (!s->graphs_ok || s->timing || s->stream == nullptr) return UGKWP_OK;
-    void* key = s->A.x[0];
+    // the per-cell survivor counts swap every step: their pointer tells the
+    // step parity a captured pair starts from
+    void* key = s->S.nleft;
     int slot = s->graph_key[0] == key ? 0 : s->graph_key[1] == key ? 1 : -1;
     if (slot < 0) {
         slot = s->graph[0] ? 1 : 0;
@@ -819,7 +849,7 @@ int ugkwp_step(ugkwp_sim* s, int32_t n_steps, ugkwp_stats* st) {
         CU(cudaMemcpyAsync(&dt, s->S.dt, sizeof(double), cudaMemcpyDeviceToHost, q));
         CU(cudaStreamSynchronize(q));
         st->t = t; st->dt = dt; st->step = s->step;
-        st->n_particles = h[CNT_ALIVE]; st->n_tracked = h[CNT_TRACKED];
+        st->n_particles = h[CNT_SURV]; st->n_tracked = h[CNT_TRACKED];
         st->n_sampled = h[CNT_SAMPLED]; st->n_collided = h[CNT_COLLIDED]; st->n_exited = h[CNT_EXITED];
         st->n_lost = h[CNT_LOST]; st->n_crossings = h[CNT_CROSSINGS]; st->n_wall_hits = h[CNT_WALL];
         st->n_moves_total = h[CNT_MOVES];
@@ -933,8 +963,8 @@ int ugkwp_state_info(ugkwp_sim* s, ugkwp_state* st) {
     CU(cudaMemcpyAsync(h, s->S.cnt64, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
     CU(cudaMemcpyAsync(&t, s->S.t, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CU(cudaStreamSynchronize(s->stream));
-    // the current buffer holds exactly the N_A live particles
-    st->n_particles = h[CNT_N_A];
+    // the current buffer holds the live particles in N_A slots (the rest are holes)
+    st->n_particles = h[CNT_SURV];
     st->step = s->step;
     st->t = t;
     for (int q = 0; q < 5; ++q) st->exps[q] = s->P.exps[q];
@@ -1086,6 +1116,7 @@ int ugkwp_import_state(ugkwp_sim* s, const ugkwp_state* st) {
     std::memset(h, 0, sizeof(h));
     h[CNT_MOVES] = moves;
     h[CNT_N_A] = n;
+    h[CNT_SURV] = n;
     h[CNT_STEP] = st->step;
     CU(cudaMemcpyAsync(s->S.cnt64, h, sizeof(h), cudaMemcpyHostToDevice, q));
     CU(cudaMemcpyAsync(s->S.t, &st->t, sizeof(double), cudaMemcpyHostToDevice, q));
@@ -1282,6 +1313,10 @@ int ugkwp_get_launch_cfg(const ugkwp_sim* s, ugkwp_launch_cfg* out) {
     if (!s || !out) return fail(UGKWP_E_ARG, "NULL argument");
     out->particle_blocks = s->lc.particle_blocks;
     out->wave_blocks = s->lc.wave_blocks;
+    out->track_threads = s->lc.track.threads;
+    out->track_stages = s->lc.track.stages;
+    out->smem_carveout = s->lc.carveout;
+    out->reserved = 0;
     return UGKWP_OK;
 }
 
@@ -1290,9 +1325,19 @@ int ugkwp_set_launch_cfg(ugkwp_sim* s, const ugkwp_launch_cfg* cfg) {
     if (cfg->particle_blocks <= 0 || cfg->wave_blocks <= 0 || cfg->particle_blocks > (1 << 20) ||
         cfg->wave_blocks > (1 << 20))
         return fail(UGKWP_E_ARG, "grid sizes must be in [1, 2^20]");
-    if (cfg->particle_blocks != s->lc.particle_blocks || cfg->wave_blocks != s->lc.wave_blocks) {
-        s->lc.particle_blocks = cfg->particle_blocks;
-        s->lc.wave_blocks = cfg->wave_blocks;
+    if (cfg->track_threads != 128 && cfg->track_threads != 256)
+        return fail(UGKWP_E_ARG, "track_threads must be 128 or 256");
+    if (cfg->track_stages != 0 && cfg->track_stages != 2 && cfg->track_stages != 3)
+        return fail(UGKWP_E_ARG, "track_stages must be 0, 2 or 3");
+    if (cfg->smem_carveout < -1 || cfg->smem_carveout > 100)
+        return fail(UGKWP_E_ARG, "smem_carveout must be -1 or in [0, 100]");
+    LaunchCfg lc{cfg->particle_blocks, cfg->wave_blocks, TrackShape{cfg->track_threads, cfg->track_stages},
+                 cfg->smem_carveout};
+    if (lc.particle_blocks != s->lc.particle_blocks || lc.wave_blocks != s->lc.wave_blocks ||
+        lc.track.threads != s->lc.track.threads || lc.track.stages != s->lc.track.stages ||
+        lc.carveout != s->lc.carveout) {
+        CU(configure_kernels(s->P, lc));
+        s->lc = lc;
         s->drop_graphs();
     }
     return UGKWP_OK;
@@ -1302,16 +1347,42 @@ int ugkwp_set_launch_cfg(ugkwp_sim* s, const ugkwp_launch_cfg* cfg) {
 
 namespace {
 
-// Candidate grid pairs of the autotuner for a simulation of this order.
-std::vector<LaunchCfg> tune_candidates(int order) {
-    std::vector<LaunchCfg> c;
+ugkwp_launch_cfg to_public(const LaunchCfg& c) {
+    return ugkwp_launch_cfg{c.particle_blocks, c.wave_blocks, c.track.threads, c.track.stages, c.carveout, 0};
+}
+
+// The autotuner's search, in two stages: (1) tracking shape x carveout at
+// 1024 resident tracking threads per SM and one wave block per SM; (2) for the
+// fastest of those, resident tracking threads per SM (512, 1024, 2048) x wave
+// blocks per SM (1, 2 at order 2).  trial(c, ms) sets c, steps and returns the
+// time; the fastest configuration is returned in best.
+template <class Trial> int tune_search(int order, Trial&& trial, LaunchCfg& best) {
     const int sms = sm_count();
-    for (int pb : {1, 2, 4, 8, 16})
+    const TrackShape shapes[] = {{128, 0}, {128, 2}, {128, 3}, {256, 2}};
+    float best_ms = 0.0f;
+    bool have = false;
+    auto consider = [&](const LaunchCfg& c) {
+        float ms = 0.0f;
+        int rc = trial(c, ms);
+        if (rc) return rc;
+        if (!have || ms < best_ms) { best_ms = ms; best = c; have = true; }
+        return (int)UGKWP_OK;
+    };
+    for (const TrackShape& sh : shapes)
+        for (int carve : {-1, 58, 86}) {
+            int rc = consider(LaunchCfg{1024 / sh.threads * sms, sms, sh, carve});
+            if (rc) return rc;
+        }
+    const LaunchCfg stage1 = best;
+    for (int threads_per_sm : {512, 1024, 2048})
         for (int wb : {1, 2}) {
             if (order != 2 && wb != 1) continue;
-            c.push_back(LaunchCfg{pb * sms, wb * sms});
+            if (threads_per_sm == 1024 && wb == 1) continue;  // measured in the first stage
+            int rc = consider(LaunchCfg{threads_per_sm / stage1.track.threads * sms, wb * sms, stage1.track,
+                                        stage1.carveout});
+            if (rc) return rc;
         }
-    return c;
+    return UGKWP_OK;
 }
 
 // Device time of `steps` steps enqueued by `run` on stream q.
@@ -1341,24 +1412,20 @@ int ugkwp_autotune(ugkwp_sim* s, int32_t steps_per_trial, ugkwp_launch_cfg* best
     if (!s) return fail(UGKWP_E_ARG, "NULL simulation");
     if (steps_per_trial < 2 || (steps_per_trial & 1)) return fail(UGKWP_E_ARG, "steps_per_trial must be even and >= 2");
     if (s->timing) return fail(UGKWP_E_STATE, "per-kernel timing is enabled");
-    float best_ms = 0.0f;
     LaunchCfg best_lc = s->lc;
-    bool have = false;
-    for (const LaunchCfg& c : tune_candidates(s->P.order)) {
-        ugkwp_launch_cfg u{c.particle_blocks, c.wave_blocks};
-        int rc = ugkwp_set_launch_cfg(s, &u);
-        if (rc) return rc;
-        rc = ugkwp_step(s, 2, nullptr);
-        if (rc) return rc;
-        float ms = 0.0f;
-        rc = time_steps(s->stream, [&] { return ugkwp_step(s, steps_per_trial, nullptr); }, ms);
-        if (rc) return rc;
-        rc = read_error(s);
-        if (rc) return rc;
-        if (!have || ms < best_ms) { best_ms = ms; best_lc = c; have = true; }
-    }
-    ugkwp_launch_cfg u{best_lc.particle_blocks, best_lc.wave_blocks};
-    int rc = ugkwp_set_launch_cfg(s, &u);
+    int rc = tune_search(s->P.order, [&](const LaunchCfg& c, float& ms) {
+        ugkwp_launch_cfg u = to_public(c);
+        int r = ugkwp_set_launch_cfg(s, &u);
+        if (r) return r;
+        r = ugkwp_step(s, 2, nullptr);
+        if (r) return r;
+        r = time_steps(s->stream, [&] { return ugkwp_step(s, steps_per_trial, nullptr); }, ms);
+        if (r) return r;
+        return read_error(s);
+    }, best_lc);
+    if (rc) return rc;
+    ugkwp_launch_cfg u = to_public(best_lc);
+    rc = ugkwp_set_launch_cfg(s, &u);
     if (rc) return rc;
     if (best) *best = u;
     return UGKWP_OK;
@@ -1399,7 +1466,7 @@ namespace {
 std::vector<void*> batch_key(const ugkwp_batch* b) {
     std::vector<void*> k;
     k.reserve(b->sims.size());
-    for (auto* s : b->sims) k.push_back(s->A.x[0]);
+    for (auto* s : b->sims) k.push_back(s->S.nleft);
     return k;
 }
 
@@ -1553,26 +1620,22 @@ int ugkwp_batch_autotune(ugkwp_batch* b, int32_t steps_per_trial, ugkwp_launch_c
         if (s->timing) return fail(UGKWP_E_STATE, "per-kernel timing is enabled on a member");
         order = std::max(order, (int)s->P.order);
     }
-    float best_ms = 0.0f;
-    LaunchCfg best_lc{0, 0};
-    bool have = false;
-    for (const LaunchCfg& c : tune_candidates(order)) {
-        ugkwp_launch_cfg u{c.particle_blocks, c.wave_blocks};
+    LaunchCfg best_lc = b->sims.empty() ? LaunchCfg{1, 1, {128, 0}, -1} : b->sims[0]->lc;
+    int rc0 = tune_search(order, [&](const LaunchCfg& c, float& ms) {
+        ugkwp_launch_cfg u = to_public(c);
         for (auto* s : b->sims) {
-            int rc = ugkwp_set_launch_cfg(s, &u);
-            if (rc) return rc;
+            int r = ugkwp_set_launch_cfg(s, &u);
+            if (r) return r;
         }
         b->drop_graphs();
-        int rc = ugkwp_batch_step(b, 2);
-        if (rc) return rc;
-        float ms = 0.0f;
-        rc = time_steps(b->stream, [&] { return ugkwp_batch_step(b, steps_per_trial); }, ms);
-        if (rc) return rc;
-        rc = ugkwp_batch_sync(b);
-        if (rc) return rc;
-        if (!have || ms < best_ms) { best_ms = ms; best_lc = c; have = true; }
-    }
-    ugkwp_launch_cfg u{best_lc.particle_blocks, best_lc.wave_blocks};
+        int r = ugkwp_batch_step(b, 2);
+        if (r) return r;
+        r = time_steps(b->stream, [&] { return ugkwp_batch_step(b, steps_per_trial); }, ms);
+        if (r) return r;
+        return ugkwp_batch_sync(b);
+    }, best_lc);
+    if (rc0) return rc0;
+    ugkwp_launch_cfg u = to_public(best_lc);
     for (auto* s : b->sims) {
         int rc = ugkwp_set_launch_cfg(s, &u);
         if (rc) return rc;

@@ -59,11 +59,12 @@ __global__ void k_reset(DevMesh m, DevState s) {
         s.cnt64[CNT_LOST] = 0;
         s.cnt64[CNT_CROSSINGS] = 0;
         s.cnt64[CNT_WALL] = 0;
-        s.cnt64[CNT_ALIVE] = 0;
+        s.cnt64[CNT_RESV] = 0;
         s.cnt64[CNT_TRACKED] = 0;
         s.cnt64[CNT_DT_BITS] = 0x7ff0000000000000LL;  // +inf
-        s.cnt64[CNT_MOVERS] = 0;
         s.cnt64[CNT_TILE] = 0;
+        s.cnt64[CNT_OVF] = 0;
+        s.cnt64[CNT_SURV] = 0;
     }
 }
 
@@ -120,8 +121,10 @@ __global__ void k_cell_prep(DevMesh m, DevState s, DevParams p) {
 
 // a5 counts: rho^hp = e^{-dt/tau} rho^h, m_ref = (rho^p + rho^hp)|Omega|/N_ref,
 // N_sam = 2 ceil(rho^hp |Omega| / (2 m_ref)), N_sam >= N_min - N_left,
-// m_sam = rho^hp |Omega| / N_sam (Sec. 2.4 (b)).  Also the per-block sums of
-// the per-cell particle counts (survivors + samples) and of N_sam.
+// m_sam = rho^hp |Omega| / N_sam (Sec. 2.4 (b)).  Also the survivor bucket
+// the cell gets in the buffer this step's survivors are written to (a11:
+// sized from the particles that start the step in the cell), and the
+// per-block sums of the bucket sizes and of N_sam.
 __global__ void k_sample_count(DevMesh m, DevState s, DevParams p) {
     __shared__ int2 shw[32];
     const int nc = m.nc;
@@ -131,7 +134,7 @@ __global__ void k_sample_count(DevMesh m, DevState s, DevParams p) {
         if (i == 0) s.dt[0] = dt;
         return;
     }
-    int count = 0, nsam = 0;
+    int wcap = 0, nsam = 0;
     if (i < nc) {
         const double vol = m.vol[i];
         const double ex = dm::d_exp(-(dt / s.tau[i]));
@@ -155,16 +158,19 @@ __global__ void k_sample_count(DevMesh m, DevState s, DevParams p) {
         s.nsam[i] = (int)ns;
         s.msam[i] = ms;
         nsam = (int)ns;
-        count = s.nleft[i] + nsam;
+        const int count = s.nleft[i] + nsam;
         s.cnt[i] = count;
+        wcap = bucket_slots(count);
+        s.wcap[i] = wcap;
     }
-    const int2 incl = block_scan_incl2(make_int2(count, nsam), shw);
+    const int2 incl = block_scan_incl2(make_int2(wcap, nsam), shw);
     if (threadIdx.x == blockDim.x - 1) s.bsum[blockIdx.x] = incl;
     if (i == 0) s.dt[0] = dt;
 }
 
-// Exclusive scan of the block sums (one block): totals of the next buffer and
-// of the sampled particles, and the capacity check.
+// Exclusive scan of the block sums (one block): the slots of the survivor
+// buckets of the buffer written this step and the sampled particles (they
+// follow the N_A slots of the current buffer), and the capacity checks.
 __global__ void k_scan_bsum(DevState s, DevParams p, int nb) {
     __shared__ int2 shw[32];
     __shared__ long long carry_sh[2];
@@ -181,11 +187,12 @@ __global__ void k_scan_bsum(DevState s, DevParams p, int nb) {
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const long long total = carry_sh[0];
+        const long long total = s.cnt64[CNT_N_A] + carry_sh[1];
         s.cnt64[CNT_N_B] = total;
         s.cnt64[CNT_NSAM] = carry_sh[1];
         s.cnt64[CNT_SAMPLED] = carry_sh[1];
-        if (total > p.capacity) {
+        s.cnt64[CNT_WTOT] = carry_sh[0];
+        if (total > p.capacity || carry_sh[0] > p.capacity) {
             set_err(s, ERRB_CAPACITY);
             s.cnt64[CNT_N_B] = 0;
             s.cnt64[CNT_NSAM] = 0;
@@ -196,14 +203,17 @@ __global__ void k_scan_bsum(DevState s, DevParams p, int nb) {
 __global__ void k_scan_apply(DevMesh m, DevState s) {
     __shared__ int2 shw[32];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int2 v = i < m.nc ? make_int2(s.cnt[i], s.nsam[i]) : make_int2(0, 0);
+    const int2 v = i < m.nc ? make_int2(s.wcap[i], s.nsam[i]) : make_int2(0, 0);
     const int2 incl = block_scan_incl2(v, shw);
-    if (i < m.nc) s.soff[i] = s.bsum[blockIdx.x].y + incl.y - v.y;
+    if (i < m.nc) {
+        s.soff[i] = s.bsum[blockIdx.x].y + incl.y - v.y;
+        s.woff[i] = s.bsum[blockIdx.x].x + incl.x - v.x;
+    }
 }
 
 // a10: W^{n+1} = W^n - 1/|Omega| sum_k (+-F_k |S_k|) + F^{fr,p}/|Omega|, faces
 // gathered in local order 0..3 (Eq. update_macro_variables).
-__global__ void k_cell_update(DevMesh m, DevState s, DevParams p) {
+__global__ void k_cell_update(DevMesh m, DevState s, DevParams p, int32_t* wcell) {
     const int nc = m.nc, nf = m.nf;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (p.gks) {
@@ -229,9 +239,17 @@ __global__ void k_cell_update(DevMesh m, DevState s, DevParams p) {
         s.t[0] = s.t[0] + s.dt[0];
         if (p.averaging) s.tsum[0] += s.dt[0];
         s.cnt64[CNT_STEP] += 1;
-        s.cnt64[CNT_N_A] = s.cnt64[CNT_ALIVE];  // the compacted survivors become the current particles
+        // the survivor buckets and the overflow slots become the current buffer
+        const long long ovf = s.cnt64[CNT_OVF];
+        const long long room = p.capacity - s.cnt64[CNT_WTOT];
+        s.cnt64[CNT_N_A] = s.cnt64[CNT_WTOT] + (ovf < room ? ovf : room);
     }
     if (i >= nc) return;
+    // a11: the bucket slots no survivor took are holes
+    if (!(s.cnt64[CNT_ERR] & ERRB_CAPACITY)) {
+        const int cap = s.wcap[i], fill = s.nleft_next[i];
+        for (int k = fill < cap ? fill : cap; k < cap; ++k) wcell[(size_t)s.woff[i] + k] = -1;
+    }
     int f[4];
     const int own = m.cfs[i];
 #pragma unroll
@@ -373,6 +391,20 @@ int sm_count() {
 
 int particle_grid() { return sm_count() * 8; }
 
+cudaError_t configure_cell_kernels(int carveout) {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](auto f) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
+    };
+    set(k_reset);
+    set(k_cell_prep);
+    set(k_sample_count);
+    set(k_scan_bsum);
+    set(k_scan_apply);
+    set(k_cell_update);
+    return e;
+}
+
 void launch_reset(const DevMesh& m, const DevState& s, cudaStream_t st) {
     k_reset<<<cdiv(5LL * m.nc, 256) < 4096 ? cdiv(5LL * m.nc, 256) : 4096, 256, 0, st>>>(m, s);
 }
@@ -386,8 +418,8 @@ void launch_scan(const DevMesh& m, const DevState& s, const DevParams& p, cudaSt
     k_scan_bsum<<<1, SCAN_BLOCK, 0, st>>>(s, p, scan_blocks(m.nc));
     k_scan_apply<<<scan_blocks(m.nc), SCAN_BLOCK, 0, st>>>(m, s);
 }
-void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
-    k_cell_update<<<cdiv(m.nc, 256), 256, 0, st>>>(m, s, p);
+void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p, int32_t* wcell, cudaStream_t st) {
+    k_cell_update<<<cdiv(m.nc, 256), 256, 0, st>>>(m, s, p, wcell);
 }
 void launch_rebuild_survivors(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
                               cudaStream_t st) {

@@ -800,6 +800,18 @@ void launch_face_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p
 
 int wave_threads() { return UGKWP_WAVE_THREADS; }
 
+cudaError_t configure_wave_kernels(int carveout) {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](auto f) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
+    };
+    set(k_gradients);
+    set(k_gp_coef);
+    set(k_face_flux_o2);
+    set(k_face_flux);
+    return e;
+}
+
 // blocks > 0 bounds the grid (a step of the method: the flux shares the GPU
 // with the particle kernels launched beside it); 0: one thread per face.
 void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, int first, int blocks,

@@ -4,12 +4,15 @@
 //
 //   k_sample_write  a5: N_sam hydro particles per cell, in pairs U +/- sqrt(RT) X
 //                   with X ~ N(0, I) (Box-Muller), uniform in the tet.
-//   k_track         a6-a9, a11: t_f = min(-tau ln eta, dt), face-by-face
-//                   streaming, boundary interaction, particle flux (movers
-//                   listed for k_movers), removal; the survivors are written
-//                   compacted into the other buffer (block-level slot
-//                   reservation), where the next step's samples follow them.
-//                   Blocks take 128-particle tiles from a global counter.
+//   k_sort          a11: the survivors of the last step, compacted, sorted by
+//                   cell (counting sort on the scanned per-cell counts) into
+//                   the working buffer, where each cell's samples follow them.
+//   k_track         a6-a9: t_f = min(-tau ln eta, dt), face-by-face streaming
+//                   of the cell-sorted particles, boundary interaction,
+//                   particle flux (movers listed for k_movers), removal; the
+//                   survivors are written compacted into the survivor buffer
+//                   (block-level slot reservation).  Blocks take tiles of
+//                   128 or 256 particles from a global counter.
 #include "dmath.cuh"
 #include "ugkwp_internal.hpp"
 
@@ -19,14 +22,6 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-// Threads per block of k_track and the resident blocks per SM its register
-// budget is sized for.
-#ifndef UGKWP_TRACK_THREADS
-#define UGKWP_TRACK_THREADS 128
-#endif
-#ifndef UGKWP_TRACK_MIN_BLOCKS
-#define UGKWP_TRACK_MIN_BLOCKS (1024 / UGKWP_TRACK_THREADS)
-#endif
 enum : unsigned long long { TAG_TF = 1, TAG_SVEL = 2, TAG_SPOS = 3, TAG_WALL = 4, TAG_GP = 5, TAG_SINT = 6, TAG_WINT = 7 };
 
 __device__ __forceinline__ void set_err(const DevState& s, int32_t bits) {
@@ -209,7 +204,7 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
         const int cell = lo;
         const int k = (int)(g - s.soff[cell]);
         const int side = k & 1;
-        // the samples follow the survivors of the last step in cell order
+        // the samples follow the current buffer's survivor slots, in cell order
         const long long j = s.cnt64[CNT_N_A] + g;
         if constexpr (sizeof(Real) == 4) {
             // mixed mode: binary32 arithmetic from U, sqrt(RT) and the tet's
@@ -411,10 +406,96 @@ __device__ __forceinline__ bool fixed_of_mass(double m, int e, long long& q) {
     return true;
 }
 
-// KE: the particles carry an internal energy (K > 0)
-template <class Real, bool KE>
-__global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br,
-                                                                     PartBufRaw nr, PartBufRaw ar) {
+// ---- bulk copies of particle tiles into shared memory: the copy engine
+// (cp.async.bulk, TMA) writes a stage and completes the transaction count of
+// the stage's mbarrier; the block waits on the barrier's phase parity.
+__device__ __forceinline__ unsigned smem_addr(const void* ptr) { return (unsigned)__cvta_generic_to_shared(ptr); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned long long* bar, unsigned bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// Wait for the phase of the given parity to complete: at most MBAR_TRIES
+// tests (each may suspend the thread for a while), false if it did not.
+constexpr int MBAR_TRIES = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (int k = 0; k < MBAR_TRIES; ++k)
+        if (mbar_test(bar, parity)) return true;
+    return false;
+}
+
+// One stage of T particles in shared memory, structure of arrays like the
+// particle buffer: x[3], u[3] (particle precision), e (KE), m, id, cell.  Every
+// array starts on a 16-byte boundary (T RS is a multiple of 512).
+template <class Real, bool KE, int T> struct Stage {
+    static constexpr int RS = (int)sizeof(Real);
+    static constexpr int X = 0;
+    static constexpr int U = 3 * T * RS;
+    static constexpr int E = 6 * T * RS;
+    static constexpr int M = (KE ? 7 : 6) * T * RS;
+    static constexpr int ID = M + 8 * T;
+    static constexpr int CELL = ID + 8 * T;
+    static constexpr int BYTES = CELL + 4 * T;
+};
+
+// Thread 0: bulk copies of the tile of T particles from index t0 (a multiple
+// of T: every source starts 16-byte aligned, and the particle arrays hold
+// whole tiles) into stage `st`, completing on `bar`.
+template <class Real, bool KE, int T>
+__device__ __forceinline__ void stage_tile(char* st, unsigned long long* bar, const PartView<Real>& b, long long t0) {
+    using L = Stage<Real, KE, T>;
+    mbar_expect(bar, (unsigned)L::BYTES);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        bulk_load(st + L::X + c * T * L::RS, b.x[c] + t0, T * L::RS, bar);
+        bulk_load(st + L::U + c * T * L::RS, b.u[c] + t0, T * L::RS, bar);
+    }
+    if constexpr (KE) bulk_load(st + L::E, b.e + t0, T * L::RS, bar);
+    bulk_load(st + L::M, b.m + t0, 8 * T, bar);
+    bulk_load(st + L::ID, b.id + t0, 8 * T, bar);
+    bulk_load(st + L::CELL, b.cell + t0, 4 * T, bar);
+}
+
+// Thread 0's source of tiles: grabs of TILE_GRAB consecutive tiles from the
+// global counter (one atomic per grab), handed out in order, so the tiles a
+// block walks increase.  Returns the first particle index of the next tile.
+struct TileQueue {
+    long long next = 0, end = 0;
+};
+__device__ __forceinline__ long long next_tile(TileQueue& q, int64_t* ctr, int T) {
+    if (q.next == q.end) {
+        q.next = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(ctr), 1ULL) * TILE_GRAB;
+        q.end = q.next + TILE_GRAB;
+    }
+    return (q.next++) * T;
+}
+
+// KE: the particles carry an internal energy (K > 0).  THREADS: particles per
+// tile (one per thread).  STAGES = 0: each thread loads its particle from the
+// buffer when its tile starts; STAGES > 0: the tiles are staged in shared
+// memory by bulk copies, STAGES - 1 tiles ahead of the one being walked.
+template <class Real, bool KE, int THREADS, int STAGES>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br,
+                                                                  PartBufRaw nr, PartBufRaw ar) {
+    constexpr int NW = THREADS / 32;
+    using L = Stage<Real, KE, THREADS>;
     if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
     const PartView<Real> b = view<Real>(br);   // this step's particles: survivors, then samples
     const PartView<Real> nxt = view<Real>(nr);  // the next step's survivors, compacted
@@ -427,24 +508,49 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
     // slot bookkeeping in two sets, alternating between tiles, so that no
     // barrier is needed after a tile's stores: a set is rewritten two tiles
     // later, after two barriers every warp has passed
-    __shared__ int sh_cnt[2][8], sh_scnt[2][8];
-    __shared__ long long sh_base[2], sh_sbase[2], sh_tile[2];
+    __shared__ int sh_cnt[2][NW];
+    __shared__ long long sh_base[2], sh_tile[2];
+    const long long wtot = s.cnt64[CNT_WTOT];  // overflow slots start after the buckets
     int par = 0;
-    __shared__ unsigned long long sh_red[8][8];
+    __shared__ unsigned long long sh_red[NW][8];
+    // staged tiles: first particle index per stage, one mbarrier per stage
+    extern __shared__ __align__(16) char stg[];
+    __shared__ unsigned long long sh_bar[STAGES > 0 ? STAGES : 1];
+    __shared__ long long sh_stile[STAGES > 0 ? STAGES : 1];
     // per-thread counters, reduced once per block at the end
-    unsigned c_valid = 0, c_coll = 0, c_exit = 0, c_lost = 0, c_cross = 0, c_wall = 0;
-    // tiles of blockDim.x particles are taken from a global counter, so that
+    unsigned c_valid = 0, c_coll = 0, c_exit = 0, c_lost = 0, c_cross = 0, c_wall = 0, c_surv = 0;
+    // tiles of THREADS particles are taken from a global counter, so that
     // blocks that start late (or walk short paths) take fewer tiles
-    if (threadIdx.x == 0)
-        sh_tile[0] = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_TILE]), 1ULL) * blockDim.x;
+    TileQueue tq;  // thread 0's
+    if (threadIdx.x == 0) {
+        if constexpr (STAGES > 0) {
+            for (int k = 0; k < STAGES; ++k) mbar_init(&sh_bar[k]);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            for (int k = 0; k < STAGES; ++k) {
+                const long long t0 = next_tile(tq, &s.cnt64[CNT_TILE], THREADS);
+                sh_stile[k] = t0;
+                if (t0 < n) stage_tile<Real, KE, THREADS>(stg + k * L::BYTES, &sh_bar[k], b, t0);
+            }
+        } else {
+            sh_tile[0] = next_tile(tq, &s.cnt64[CNT_TILE], THREADS);
+        }
+    }
     __syncthreads();
+    int slot = 0;        // stage of this tile
+    unsigned phase = 0;  // parity of the stage's mbarrier phase this tile completes
     for (;;) {
-        const long long bb = sh_tile[par];  // block-uniform
+        const long long bb = STAGES > 0 ? sh_stile[slot] : sh_tile[par];  // block-uniform
         if (bb >= n) break;
         const long long i = bb + threadIdx.x;
-        const bool valid = i < n;
-        int status = 0, ncross = 0, nrefl = 0, nwall = 0;
+        // a stage whose copies did not complete within the wait's limit is
+        // not read; the block stops at the next barrier
+        const bool staged = STAGES == 0 || mbar_wait(&sh_bar[slot], phase);
+        // the slot's start cell; -1 marks a hole of a survivor bucket
         int c0 = -1, tet = -1;
+        if (i < n && staged)
+            c0 = STAGES > 0 ? reinterpret_cast<const int*>(stg + slot * L::BYTES + L::CELL)[threadIdx.x] : b.cell[i];
+        const bool valid = c0 >= 0;
+        int status = 0, ncross = 0, nrefl = 0, nwall = 0;
         long long qmass = 0;
         bool survivor = false, mover = false, exited = false;
         Real us[3] = {(Real)0, (Real)0, (Real)0}, ue[3] = {(Real)0, (Real)0, (Real)0};
@@ -453,15 +559,30 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
         double mm = 0.0;
         unsigned long long id = 0;
         if (valid) {
-            id = b.id[i];
-            c0 = b.cell[i];
             Real x0[3], u[3];
+            if constexpr (STAGES > 0) {
+                const char* st = stg + slot * L::BYTES;
+                const int k = threadIdx.x;
+                id = reinterpret_cast<const unsigned long long*>(st + L::ID)[k];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) { x0[c] = b.x[c][i]; u[c] = b.u[c][i]; }
-            mm = b.m[i];
-            if constexpr (KE) {
-                es = b.e[i];
-                ee = es;
+                for (int c = 0; c < 3; ++c) {
+                    x0[c] = reinterpret_cast<const Real*>(st + L::X + c * THREADS * L::RS)[k];
+                    u[c] = reinterpret_cast<const Real*>(st + L::U + c * THREADS * L::RS)[k];
+                }
+                mm = reinterpret_cast<const double*>(st + L::M)[k];
+                if constexpr (KE) {
+                    es = reinterpret_cast<const Real*>(st + L::E)[k];
+                    ee = es;
+                }
+            } else {
+                id = b.id[i];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) { x0[c] = b.x[c][i]; u[c] = b.u[c][i]; }
+                mm = b.m[i];
+                if constexpr (KE) {
+                    es = b.e[i];
+                    ee = es;
+                }
             }
 #pragma unroll
             for (int c = 0; c < 3; ++c) us[c] = u[c];
@@ -600,65 +721,104 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
             c_cross += ncross;
             c_wall += nwall;
         }
-        // ---- survivors per end cell (count, fixed-point mass): segmented
-        // reduction over lanes with equal keys in a row, one atomic per run
+        // ---- a11: each survivor goes to the bucket of its end cell in the
+        // next buffer, so the next step finds the particles sorted by cell.
+        // Lanes with the same end cell take consecutive slots from the cell's
+        // count (one atomic per group); the count is also the cell's survivor
+        // count N_left of the next step.  A survivor beyond its bucket takes an
+        // overflow slot after the buckets.
         const int key = survivor ? tet : -1;
-        long long v = survivor ? qmass : 0;
-        const int prev = __shfl_up_sync(FULL, key, 1);
-        const bool head = lane == 0 || prev != key;
-        const unsigned heads = __ballot_sync(FULL, head);
-        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+        int srank = 0;  // the survivor's slot in its bucket, written after the movers' barriers
+        {
+            const unsigned peers = __match_any_sync(FULL, key);
+            const int leader = __ffs(peers) - 1;
+            int rank = 0;
+            if (lane == leader && key >= 0) rank = atomicAdd(&s.nleft_next[key], __popc(peers));
+            rank = __shfl_sync(FULL, rank, leader) + __popc(peers & ((1u << lane) - 1u));
+            srank = rank;
+        }
+        // ---- survivors' fixed-point mass per end cell: segmented reduction
+        // over lanes with equal keys in a row, one atomic per run
+        {
+            long long v = survivor ? qmass : 0;
+            const int prev = __shfl_up_sync(FULL, key, 1);
+            const bool head = lane == 0 || prev != key;
+            const unsigned heads = __ballot_sync(FULL, head);
+            const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const long long o = __shfl_up_sync(FULL, v, d);
-            if (lane - d >= start) v += o;
-        }
-        const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
-        if (tail && key >= 0) {
-            atomicAdd(&s.nleft_next[key], lane - start + 1);
-            atomicAdd(reinterpret_cast<unsigned long long*>(&s.smass_next[key]), (unsigned long long)v);
-        }
-        // ---- survivors (compacted into the next buffer) and movers: one slot
-        // reservation of each per block and iteration
-        const unsigned mmask = __ballot_sync(FULL, mover);
-        const unsigned smask = __ballot_sync(FULL, survivor);
-        if (lane == 0) {
-            sh_cnt[par][warp] = __popc(mmask);
-            sh_scnt[par][warp] = __popc(smask);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int tot = 0, stot = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                const int c = sh_cnt[par][w], sc = sh_scnt[par][w];
-                sh_cnt[par][w] = tot;
-                sh_scnt[par][w] = stot;
-                tot += c;
-                stot += sc;
+            for (int d = 1; d < 32; d <<= 1) {
+                const long long o = __shfl_up_sync(FULL, v, d);
+                if (lane - d >= start) v += o;
             }
-            sh_base[par] = tot ? (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_MOVERS]),
-                                                      (unsigned long long)tot)
-                               : 0LL;
-            sh_sbase[par] = stot ? (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_ALIVE]),
-                                                        (unsigned long long)stot)
-                                 : 0LL;
-            // the next tile, in the other set (its last readers read it before
-            // the barrier above)
-            sh_tile[par ^ 1] =
-                (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_TILE]), 1ULL) * blockDim.x;
+            const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+            if (tail && key >= 0) atomicAdd(reinterpret_cast<unsigned long long*>(&s.smass_next[key]), (unsigned long long)v);
+        }
+        c_surv += survivor ? 1u : 0u;
+        // ---- movers: one slot reservation per block and iteration
+        const unsigned mmask = __ballot_sync(FULL, mover);
+        if (lane == 0) sh_cnt[par][warp] = __popc(mmask);
+        if (__syncthreads_or(!staged)) {
+            // a stage wait gave up: report it, give the copies still in flight
+            // a bounded wait (shared memory must not be released under them)
+            // and stop; the step's particle state is not valid
+            if (threadIdx.x == 0) {
+                set_err(s, ERRB_STAGE_WAIT);
+                if constexpr (STAGES > 0) {
+                    unsigned ph = phase;
+                    for (int k = 0, sl = slot; k < STAGES; ++k) {
+                        if (sh_stile[sl] < n) mbar_wait(&sh_bar[sl], ph);
+                        if (++sl == STAGES) { sl = 0; ph ^= 1u; }
+                    }
+                }
+            }
+            return;
+        }
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < NW; ++w) {
+                const int c = sh_cnt[par][w];
+                sh_cnt[par][w] = tot;
+                tot += c;
+            }
+            sh_base[par] =
+                tot ? (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_RESV]), (unsigned long long)tot)
+                    : 0LL;
+            if constexpr (STAGES > 0) {
+                // refill this tile's stage (every thread read its particle from
+                // it before the barrier above) with the tile STAGES ahead
+                const long long t0 = next_tile(tq, &s.cnt64[CNT_TILE], THREADS);
+                sh_stile[slot] = t0;
+                if (t0 < n) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    stage_tile<Real, KE, THREADS>(stg + slot * L::BYTES, &sh_bar[slot], b, t0);
+                }
+            } else {
+                // the next tile, in the other set (its last readers read it
+                // before the barrier above)
+                sh_tile[par ^ 1] = next_tile(tq, &s.cnt64[CNT_TILE], THREADS);
+            }
         }
         __syncthreads();
         if (survivor) {
-            const long long j = sh_sbase[par] + sh_scnt[par][warp] + __popc(smask & ((1u << lane) - 1u));
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                nxt.x[c][j] = xe[c];
-                nxt.u[c][j] = ue[c];
+            long long j = -1;
+            if (srank < s.wcap[tet]) {
+                j = (long long)s.woff[tet] + srank;
+            } else {
+                const long long o = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_OVF]), 1ULL);
+                if (o < p.capacity - wtot) j = wtot + o;
+                else set_err(s, ERRB_CAPACITY);
             }
-            nxt.m[j] = mm;
-            nxt.cell[j] = tet;
-            nxt.id[j] = id;
-            if constexpr (KE) nxt.e[j] = ee;
+            if (j >= 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    nxt.x[c][j] = xe[c];
+                    nxt.u[c][j] = ue[c];
+                }
+                nxt.m[j] = mm;
+                nxt.cell[j] = tet;
+                nxt.id[j] = id;
+                if constexpr (KE) nxt.e[j] = ee;
+            }
         }
         if (mover) {
             const long long j = sh_base[par] + sh_cnt[par][warp] + __popc(mmask & ((1u << lane) - 1u));
@@ -676,20 +836,24 @@ __global__ void __launch_bounds__(UGKWP_TRACK_THREADS, UGKWP_TRACK_MIN_BLOCKS) k
             }
         }
         par ^= 1;
+        if (STAGES > 0 && ++slot == STAGES) {
+            slot = 0;
+            phase ^= 1u;
+        }
     }
     // ---- counters: one atomic per block and counter (survivors were counted
     // by their slot reservations)
-    unsigned vals[6] = {c_valid, c_coll, c_exit, c_lost, c_cross, c_wall};
+    unsigned vals[7] = {c_valid, c_coll, c_exit, c_lost, c_cross, c_wall, c_surv};
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < 7; ++k) {
         const unsigned w = __reduce_add_sync(FULL, vals[k]);
         if (lane == 0) sh_red[warp][k] = w;
     }
     __syncthreads();
-    if (threadIdx.x < 6) {
+    if (threadIdx.x < 7) {
         unsigned long long t = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh_red[w][threadIdx.x];
-        const int slot[6] = {CNT_TRACKED, CNT_COLLIDED, CNT_EXITED, CNT_LOST, CNT_CROSSINGS, CNT_WALL};
+        for (int w = 0; w < NW; ++w) t += sh_red[w][threadIdx.x];
+        const int slot[7] = {CNT_TRACKED, CNT_COLLIDED, CNT_EXITED, CNT_LOST, CNT_CROSSINGS, CNT_WALL, CNT_SURV};
         if (t) {
             atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[slot[threadIdx.x]]), t);
             if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_MOVES]), t);
@@ -705,7 +869,7 @@ template <class Real>
 __global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams p, PartBufRaw ar) {
     if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
     const PartView<Real> mv = view<Real>(ar);
-    const long long n = s.cnt64[CNT_MOVERS];
+    const long long n = s.cnt64[CNT_RESV];
     const int nc = m.nc;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
@@ -771,15 +935,73 @@ void launch_sample_scale(const DevMesh& m, const DevState& s, const DevParams& p
     else k_sample_scale<double><<<(m.nc + 255) / 256, 256, 0, st>>>(m, s, p);
 }
 
-void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b, const PartBufRaw& nxt,
-                  const PartBufRaw& movers, int blocks, cudaStream_t st) {
-    if (p.precision == UGKWP_MIXED) {
-        if (p.K > 0) k_track<float, true><<<blocks, UGKWP_TRACK_THREADS, 0, st>>>(m, s, p, b, nxt, movers);
-        else k_track<float, false><<<blocks, UGKWP_TRACK_THREADS, 0, st>>>(m, s, p, b, nxt, movers);
+namespace {
+template <class Real, bool KE, int T, int S>
+void track_as(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b, const PartBufRaw& nxt,
+              const PartBufRaw& movers, int blocks, cudaStream_t st) {
+    const int smem = S > 0 ? S * Stage<Real, KE, T>::BYTES : 0;
+    k_track<Real, KE, T, S><<<blocks, T, smem, st>>>(m, s, p, b, nxt, movers);
+}
+template <class Real, bool KE>
+void track_shape(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b, const PartBufRaw& nxt,
+                 const PartBufRaw& movers, const TrackShape& sh, int blocks, cudaStream_t st) {
+    if (sh.threads == 256) {
+        if (sh.stages == 2) track_as<Real, KE, 256, 2>(m, s, p, b, nxt, movers, blocks, st);
+        else if (sh.stages == 3) track_as<Real, KE, 256, 3>(m, s, p, b, nxt, movers, blocks, st);
+        else track_as<Real, KE, 256, 0>(m, s, p, b, nxt, movers, blocks, st);
     } else {
-        if (p.K > 0) k_track<double, true><<<blocks, UGKWP_TRACK_THREADS, 0, st>>>(m, s, p, b, nxt, movers);
-        else k_track<double, false><<<blocks, UGKWP_TRACK_THREADS, 0, st>>>(m, s, p, b, nxt, movers);
+        if (sh.stages == 2) track_as<Real, KE, 128, 2>(m, s, p, b, nxt, movers, blocks, st);
+        else if (sh.stages == 3) track_as<Real, KE, 128, 3>(m, s, p, b, nxt, movers, blocks, st);
+        else track_as<Real, KE, 128, 0>(m, s, p, b, nxt, movers, blocks, st);
     }
+}
+}  // namespace
+
+void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b, const PartBufRaw& nxt,
+                  const PartBufRaw& movers, const TrackShape& sh, int blocks, cudaStream_t st) {
+    if (p.precision == UGKWP_MIXED) {
+        if (p.K > 0) track_shape<float, true>(m, s, p, b, nxt, movers, sh, blocks, st);
+        else track_shape<float, false>(m, s, p, b, nxt, movers, sh, blocks, st);
+    } else {
+        if (p.K > 0) track_shape<double, true>(m, s, p, b, nxt, movers, sh, blocks, st);
+        else track_shape<double, false>(m, s, p, b, nxt, movers, sh, blocks, st);
+    }
+}
+
+namespace {
+// Attributes of every tracking shape of one particle type: the dynamic shared
+// memory its stages take, and the preferred carveout; the carveout also for
+// the other particle kernels of that type.
+template <class Real, bool KE> cudaError_t configure_type(int carveout) {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](auto f, int smem) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
+    };
+    set(k_track<Real, KE, 128, 0>, 0);
+    set(k_track<Real, KE, 128, 2>, 2 * Stage<Real, KE, 128>::BYTES);
+    set(k_track<Real, KE, 128, 3>, 3 * Stage<Real, KE, 128>::BYTES);
+    set(k_track<Real, KE, 256, 0>, 0);
+    set(k_track<Real, KE, 256, 2>, 2 * Stage<Real, KE, 256>::BYTES);
+    set(k_track<Real, KE, 256, 3>, 3 * Stage<Real, KE, 256>::BYTES);
+    set(k_sample_write<Real>, 0);
+    set(k_sample_scale<Real>, 0);
+    set(k_movers<Real>, 0);
+    return e;
+}
+}  // namespace
+
+cudaError_t configure_particle_kernels(const DevParams& p, const TrackShape& sh, int carveout) {
+    (void)sh;
+    if (p.precision == UGKWP_MIXED) return p.K > 0 ? configure_type<float, true>(carveout) : configure_type<float, false>(carveout);
+    return p.K > 0 ? configure_type<double, true>(carveout) : configure_type<double, false>(carveout);
+}
+
+int track_smem_bytes(const DevParams& p, const TrackShape& sh) {
+    if (sh.stages <= 0) return 0;
+    const int rs = p.precision == UGKWP_MIXED ? 4 : 8;
+    const int arrays = 6 + (p.K > 0 ? 1 : 0);
+    return sh.stages * sh.threads * (arrays * rs + 8 + 8 + 4);
 }
 
 void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a, int blocks, cudaStream_t st) {

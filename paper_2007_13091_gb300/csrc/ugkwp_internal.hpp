@@ -18,13 +18,21 @@ enum : int32_t {
     ERRB_FIXED_OVERFLOW = 4,
     ERRB_NONFINITE = 8,
     ERRB_SAMPLE_LIMIT = 16,
+    ERRB_STAGE_WAIT = 32,   // a bulk copy into shared memory did not complete within its wait limit
+    ERRB_SORT = 64,         // a cell holds more survivors than its count (sort skipped them)
 };
 
-// Device counters (int64 slots).
+// Largest tile of the tracking kernel (particles per block and tile); the
+// particle arrays hold whole tiles of this size.
+constexpr int TRACK_TILE_MAX = 256;
+
+// Device counters (int64 slots).  The counters that tracking blocks update
+// with atomics sit on 128-byte lines of their own.
 enum : int {
-    CNT_N_A = 0,        // particles in the current buffer: the survivors of the last step
-    CNT_N_B = 1,        // particles tracked this step (survivors + samples), from the scan
-    CNT_ALIVE = 2,      // survivors of this step (the slot counter of the compacted next buffer)
+    CNT_N_A = 0,        // slots of the current buffer before the samples: the last step's
+                        // survivor buckets (holes marked by cell -1) and overflow slots
+    CNT_N_B = 1,        // slots tracked this step (N_A + samples), from the scan
+    CNT_SURV = 2,       // survivors of the last step (particles alive)
     CNT_SAMPLED = 3,
     CNT_COLLIDED = 4,
     CNT_EXITED = 5,
@@ -37,10 +45,14 @@ enum : int {
     CNT_ERR = 12,       // error bits
     CNT_MOVES = 13,     // particle moves since init (never reset by a step)
     CNT_NSAM = 14,      // particles sampled this step (from the scan)
-    CNT_MOVERS = 15,    // particles whose flux contribution is non-zero this step
-    CNT_TILE = 16,      // next 128-particle tile of the tracking kernel
-    CNT_SLOTS = 17,
+    CNT_WTOT = 15,      // slots of the survivor buckets of the buffer written this step (from the scan)
+    CNT_RESV = 16,      // mover slots reserved this step
+    CNT_TILE = 32,      // next grab of tracking tiles
+    CNT_OVF = 48,       // overflow slots (survivors whose bucket is full) taken this step
+    CNT_SLOTS = 64,
 };
+// Tiles taken from the tile counter per atomic.
+constexpr int TILE_GRAB = 4;
 
 struct DevBc {
     int32_t type;
@@ -155,6 +167,9 @@ struct DevState {
     int64_t* smass_next;  // [nc]
     int32_t* cnt;         // [nc] particles per cell after sampling
     int32_t* soff;        // [nc] exclusive scan of N_sam (sampled-particle index)
+    int32_t* wcap;        // [nc] slots of the cell's survivor bucket in the buffer written this step
+    int32_t* woff;        // [nc] first slot of that bucket (exclusive scan of wcap); the bucket's
+                          // fill count is nleft_next (the survivors that ended in the cell)
     int64_t* pflux;       // [5][nc] fixed-point particle flux
     int64_t* wacc;        // [5][nc] fixed-point scratch for W^p
     double* mom;          // [5][nc] staging of moments copied to the host
@@ -196,9 +211,17 @@ void launch_sample_count(const DevMesh& m, const DevState& s, const DevParams& p
 void launch_scan(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 // Grid sizes of the step kernels that loop over their work (any positive
 // value gives the same results; chosen for speed, e.g. by the autotuner).
+// Shape of the tracking kernel: threads (= particles) per block and tile,
+// and tiles staged ahead in shared memory by bulk copies (0: direct loads).
+struct TrackShape {
+    int threads;  // 128 or 256
+    int stages;   // 0, 2 or 3
+};
 struct LaunchCfg {
-    int particle_blocks;  // blocks of 256 threads for sampling, tracking, movers
+    int particle_blocks;  // blocks of the sampling, tracking and movers kernels
     int wave_blocks;      // blocks of the persistent second-order wave kernels
+    TrackShape track;     // tracking kernel shape
+    int carveout;         // preferred shared-memory carveout (percent) of the step's kernels, -1: driver default
 };
 
 void launch_sample_write(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b,
@@ -209,16 +232,30 @@ void launch_sample_scale(const DevMesh& m, const DevState& s, const DevParams& p
 // compacted to nxt, the particles whose counting flux is non-zero are listed in
 // movers and their flux added by launch_movers.
 void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b,
-                  const PartBufRaw& nxt, const PartBufRaw& movers, int blocks, cudaStream_t st);
+                  const PartBufRaw& nxt, const PartBufRaw& movers, const TrackShape& sh, int blocks, cudaStream_t st);
+// Dynamic shared memory of one tracking block of this shape.
+int track_smem_bytes(const DevParams& p, const TrackShape& sh);
+// Kernel attributes of the step's kernels for a launch configuration (dynamic
+// shared memory of the tracking kernel, the common preferred carveout): set
+// outside stream capture, before the configuration's first launch.
+cudaError_t configure_particle_kernels(const DevParams& p, const TrackShape& sh, int carveout);
+cudaError_t configure_wave_kernels(int carveout);
+cudaError_t configure_cell_kernels(int carveout);
 void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
                    int blocks, cudaStream_t st);
+
 // First-order flux of face_order[first..nf); second-order flux of the nif interior faces.
 void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, int first, int blocks,
                       cudaStream_t st);
 void launch_face_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p, int blocks, cudaStream_t st);
 void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 void launch_gp_coef(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
-void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
+// a10, and the end of a11: the unused slots of each survivor bucket of the
+// buffer written this step (cell array wcell) are marked as holes.
+void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p, int32_t* wcell, cudaStream_t st);
+// Survivor bucket of a cell that starts a step with `cnt` particles: the slots
+// the next buffer reserves for the survivors that end the step in it.
+__host__ __device__ inline int bucket_slots(int cnt) { return cnt + cnt / 32 + 4; }
 void launch_rebuild_survivors(const DevMesh& m, const DevState& s, const DevParams& p,
                               const PartBufRaw& a, cudaStream_t st);
 void launch_wp_moments(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,

@@ -63,7 +63,12 @@ SAMPLING = {"maxwell": 0, "energy_matched": 1, "gp1": 2}
 
 
 class LaunchCfg(ctypes.Structure):
-    _fields_ = [("particle_blocks", ctypes.c_int32), ("wave_blocks", ctypes.c_int32)]
+    _fields_ = [("particle_blocks", ctypes.c_int32), ("wave_blocks", ctypes.c_int32),
+                ("track_threads", ctypes.c_int32), ("track_stages", ctypes.c_int32),
+                ("smem_carveout", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class Stats(ctypes.Structure):
@@ -369,18 +374,24 @@ def ugkwp_kn_gll(sim, n_cells: int) -> np.ndarray:
 def ugkwp_get_launch_cfg(sim) -> dict:
     c = LaunchCfg()
     _check(lib().ugkwp_get_launch_cfg(sim, ctypes.byref(c)))
-    return {"particle_blocks": c.particle_blocks, "wave_blocks": c.wave_blocks}
+    return c.as_dict()
 
 
-def ugkwp_set_launch_cfg(sim, particle_blocks: int, wave_blocks: int):
-    c = LaunchCfg(int(particle_blocks), int(wave_blocks))
+def ugkwp_set_launch_cfg(sim, particle_blocks: int, wave_blocks: int, track_threads: int = None,
+                         track_stages: int = None, smem_carveout: int = None):
+    """Set the launch configuration; fields left None keep their current values."""
+    cur = ugkwp_get_launch_cfg(sim)
+    c = LaunchCfg(int(particle_blocks), int(wave_blocks),
+                  int(cur["track_threads"] if track_threads is None else track_threads),
+                  int(cur["track_stages"] if track_stages is None else track_stages),
+                  int(cur["smem_carveout"] if smem_carveout is None else smem_carveout), 0)
     _check(lib().ugkwp_set_launch_cfg(sim, ctypes.byref(c)))
 
 
 def ugkwp_autotune(sim, steps_per_trial: int = 2) -> dict:
     c = LaunchCfg()
     _check(lib().ugkwp_autotune(sim, int(steps_per_trial), ctypes.byref(c)))
-    return {"particle_blocks": c.particle_blocks, "wave_blocks": c.wave_blocks}
+    return c.as_dict()
 
 
 def ugkwp_batch_create(handles, stream: int):
@@ -401,7 +412,7 @@ def ugkwp_batch_sync(batch):
 def ugkwp_batch_autotune(batch, steps_per_trial: int = 2) -> dict:
     c = LaunchCfg()
     _check(lib().ugkwp_batch_autotune(batch, int(steps_per_trial), ctypes.byref(c)))
-    return {"particle_blocks": c.particle_blocks, "wave_blocks": c.wave_blocks}
+    return c.as_dict()
 
 
 def ugkwp_batch_free(batch):

@@ -143,7 +143,9 @@ def centroids(nodes, tets):
 
 def _params(Kn, omega, CFL, N_ref, precision, seed, bc, C2=0.0, N_min=0, capacity=None,
             n_cells=None, max_crossings=1000, order=1):
-    cap = capacity if capacity is not None else int(3 * N_ref * n_cells + 4096)
+    # room for ~2.6 N_ref particles per cell (the settled cavity) in survivor
+    # buckets of 17/16 of a cell's count plus 4 slots
+    cap = capacity if capacity is not None else int(3.3 * N_ref * n_cells + 8 * n_cells + 4096)
     return {"R": 1.0, "mu_ref": mu_ref_vhs(Kn, omega), "T_ref": 1.0, "omega": omega, "CFL": CFL,
             "C2": C2, "order": order, "venkat_K": 5.0, "N_ref": N_ref, "N_min": N_min, "precision": precision,
             "seed": seed, "max_crossings": max_crossings, "bc": bc, "particle_capacity": cap,
@@ -373,7 +375,8 @@ def batch_instances(n=64, seed=4, tets_lo=2000, tets_hi=60000, precision="mixed"
     [1e-4, 1], Mach uniform in [0.1, 3]; even instances are shock tubes (aspect
     25:1:1, both states moving at Mach times the left sound speed, N_ref 50),
     odd ones cavities (lid at that Mach, N_ref 100); instance k has seed
-    1000 seed + k.  Particle capacity cap_factor N_ref per cell (+4096).
+    1000 seed + k.  Particle capacity cap_factor N_ref per cell in survivor
+    buckets (17/16 of the count plus 4 slots per cell, +4096).
     Energy-matched sampling by default: with the printed sampling the
     rarefied shock tubes reach negative pressure within tens of steps at
     these particle numbers."""
@@ -395,7 +398,7 @@ def batch_instances(n=64, seed=4, tets_lo=2000, tets_hi=60000, precision="mixed"
             cfg = cavity(n=m, Kn=Kn, N_ref=100, precision=precision, seed=s_k, lid_mach=mach, order=order)
             N_ref = 100
         nc = len(cfg["mesh"]["tets"])
-        cfg["params"]["particle_capacity"] = int(cap_factor * N_ref * nc + 4096)
+        cfg["params"]["particle_capacity"] = int(cap_factor * N_ref * nc * 17 / 16 + 8 * nc + 4096)
         cfg["params"]["sampling"] = sampling
         cfg["name"] = f"instance{k}_" + cfg["name"]
         cfg["Kn"], cfg["mach"] = Kn, mach

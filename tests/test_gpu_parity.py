@@ -75,10 +75,15 @@ def compare_step(gsim, osim, check_flux=True):
     assert g["t"] == pytest.approx(o["t"], rel=1e-15)
 
 
-def run_teacher_forced(cfg, warm_steps):
+def run_teacher_forced(cfg, warm_steps, launch=None):
+    """One step of each side from the oracle's state after warm_steps steps;
+    launch: (particle_blocks, wave_blocks, track_threads, track_stages,
+    smem_carveout) for the GPU side, or None for the default configuration."""
     osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
     osim.step(warm_steps)
     gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    if launch is not None:
+        ugkwp.ugkwp_set_launch_cfg(gsim.handle, *launch)
     gsim.set_state(osim.state())
     g0 = gsim.state()
     assert_particles_equal(g0, osim.state())  # import/export round trip
@@ -106,6 +111,26 @@ def test_shock_tube_first_step_from_init(precision):
 def test_shock_tube_teacher_forced(precision):
     gsim, osim = run_teacher_forced(wl.shock_tube(precision=precision), warm_steps=3)
     assert osim.last("counters")["n_collided"] > 0
+
+
+@pytest.mark.parametrize("threads,stages", [(128, 2), (128, 3), (256, 2), (256, 3), (256, 0)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tracking_shapes_teacher_forced(precision, threads, stages):
+    """The tracking kernel with its tiles staged in shared memory by bulk copies
+    (or 256-particle tiles with direct loads) against the oracle, on a jittered
+    far-field mesh whose particle count leaves a ragged last tile, with an odd
+    grid so that blocks take unequal numbers of tiles."""
+    cfg = wl.cube_flow(h0=0.5, growth=2.0, N_ref=30, precision=precision, Kn=0.1)
+    gsim, osim = run_teacher_forced(cfg, warm_steps=2, launch=(37, 5, threads, stages, -1))
+    n = osim.state()["id"].size
+    assert n % threads != 0 and n > 50 * threads
+
+
+@pytest.mark.parametrize("stages", [0, 2])
+def test_tracking_shapes_internal_energy_teacher_forced(stages):
+    """Staged tiles carry the particles' internal energies (K = 2)."""
+    cfg = wl.cavity(n=6, N_ref=40, precision="mixed", order=1, K=2)
+    run_teacher_forced(cfg, warm_steps=3, launch=(19, 3, 128, stages, 58))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -244,6 +269,24 @@ def test_internal_degrees_of_freedom_teacher_forced(precision, order):
     gsim, osim = run_teacher_forced(cfg, warm_steps=3)
     c = osim.last("counters")
     assert c["n_wall_hits"] > 0 and c["n_sampled"] > 0
+    assert np.all(osim.state()["e"] > 0.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_internal_degrees_first_step_from_init(precision):
+    """K = 2 from the common initial state, with no state import: each side
+    derives its fixed-point quanta from W0 with p = (rho E - rho |U|^2/2) /
+    ((3 + K)/2) (on this tube a K = 0 pressure would give the momentum
+    quantum one binade too coarse), so the quanta, the first step's particles
+    and its fixed-point sums are equal bit for bit."""
+    cfg = wl.shock_tube(precision=precision, K=2)
+    osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+    gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    assert np.array_equal(gsim.state()["exps"], osim.state()["exps"])
+    osim.step()
+    gsim.step(1, stats=True)
+    compare_step(gsim, osim)
+    assert np.array_equal(gsim.state()["exps"], osim.state()["exps"])
     assert np.all(osim.state()["e"] > 0.0)
 
 
