@@ -303,26 +303,23 @@ typedef struct {
     int32_t particle_blocks;     /* blocks of the sampling, tracking and movers kernels (> 0) */
     int32_t wave_blocks;         /* blocks of the persistent second-order wave kernels (> 0) */
     int32_t track_threads;       /* particles per tracking tile, one per thread of a block: 128 or 256 */
-    int32_t track_stages;        /* 0: each thread loads its particle when its tile starts; 2 or 3:
-                                  * tiles are copied into shared memory by bulk copies (TMA),
-                                  * track_stages - 1 tiles ahead of the one being walked */
     int32_t smem_carveout;       /* preferred shared-memory carveout of the step's kernels, percent of
-                                  * the largest (0..100), or -1 for the driver's choice.  A kernel
-                                  * attribute: it holds for every simulation of the process */
-    int32_t reserved;            /* 0 */
+                                  * the largest (0..100), or -1 for the driver's choice (default 58).
+                                  * A kernel attribute: it holds for every simulation of the process */
 } ugkwp_launch_cfg;
 
 int ugkwp_get_launch_cfg(const ugkwp_sim* s, ugkwp_launch_cfg* out);
 /* Takes effect at the next step (the step graphs are recaptured). */
 int ugkwp_set_launch_cfg(ugkwp_sim* s, const ugkwp_launch_cfg* cfg);
-/* Autotuner: for each candidate configuration -- tracking shape (128 threads
- * with 0, 2 or 3 stages, 256 threads with 2 stages) x resident tracking threads
- * per SM (1024 or 2048, the grid split in its two launches) x wave blocks (1 or
- * 2 per SM at order 2) x carveout (driver's choice, 58% or 86% for every kernel
- * of the step) -- runs 2 warm-up steps and steps_per_trial timed steps (even,
- * >= 2) on the bound stream, keeps the fastest and returns it in *best (may be
- * NULL).  The trial steps advance the simulation like any other steps.
- * E_STATE while per-kernel timing is on. */
+/* Autotuner: two stages of trials, each trial 2 warm-up steps and
+ * steps_per_trial timed steps (even, >= 2) on the bound stream: (1) tracking
+ * block of 128 or 256 threads x carveout (the driver's choice, or 58% for every
+ * kernel of the step) at 1024 resident tracking threads per SM and one wave
+ * block per SM; (2) for the fastest, 512, 1024 or 2048 resident tracking threads
+ * per SM (the grid split in its two launches) x 1 or 2 wave blocks per SM (order
+ * 2).  Keeps the fastest and returns it in *best (may be NULL).  The trial
+ * steps advance the simulation like any other steps.  E_STATE while per-kernel
+ * timing is on. */
 int ugkwp_autotune(ugkwp_sim* s, int32_t steps_per_trial, ugkwp_launch_cfg* best);
 
 /* ---- batches of independent simulations --------------------------------

@@ -51,7 +51,7 @@ struct ugkwp_sim {
     cudaStream_t wave = nullptr, aux = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, sampled = nullptr, tracked = nullptr, gp_ready = nullptr;
     // grid sizes of the looping step kernels
-    LaunchCfg lc{0, 0, {128, 0}, -1};
+    LaunchCfg lc{0, 0, {128}, -1};
     // two-step CUDA graphs, one per ping-pong parity (keyed by buffer A), with
     // the kernels each one launches per class
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -290,7 +290,7 @@ void set_exps(DevParams& P, const int32_t e[5]) {
 
 // Kernel attributes of a launch configuration (set outside stream capture).
 cudaError_t configure_kernels(const DevParams& P, const LaunchCfg& lc) {
-    cudaError_t e = configure_particle_kernels(P, lc.track, lc.carveout);
+    cudaError_t e = configure_particle_kernels(P, lc.carveout);
     if (e == cudaSuccess) e = configure_wave_kernels(lc.carveout);
     if (e == cudaSuccess) e = configure_cell_kernels(lc.carveout);
     return e;
@@ -312,9 +312,9 @@ int read_error(ugkwp_sim* s) {
     if (e & ERRB_SAMPLE_LIMIT) return fail(UGKWP_E_CAPACITY, "more than 65534 particles sampled in one cell");
     if (e & ERRB_SORT)
         return fail(UGKWP_E_STATE, "survivor counts per cell disagree with the survivors: the particle state is not valid");
-    if (e & ERRB_STAGE_WAIT)
-        return fail(UGKWP_E_CUDA, "a bulk copy of particles into shared memory did not complete within its wait "
-                                  "limit: the step's particle state is not valid");
+    if (e & ERRB_CHECK)
+        return fail(UGKWP_E_STATE, "a kernel's bounds or alignment check failed (check " + std::to_string(h[CNT_CHECK] >> 48) +
+                                   ", value " + std::to_string(h[CNT_CHECK] & 0xffffffffffffLL) + "); the access was skipped");
     return fail(UGKWP_E_STATE, "device error word " + std::to_string(e));
 }
 
@@ -611,8 +611,10 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     }
     s->lc.particle_blocks = particle_grid();
     s->lc.wave_blocks = sm_count();
-    s->lc.track = TrackShape{128, 0};
-    s->lc.carveout = -1;
+    s->lc.track = TrackShape{128};
+    // the tracking blocks' walk queues and the wave flux share each SM's
+    // L1/shared memory; one common carveout lets them run side by side
+    s->lc.carveout = 58;
     ce = configure_kernels(s->P, s->lc);
     if (ce != cudaSuccess) {
         delete s;
@@ -1314,9 +1316,7 @@ int ugkwp_get_launch_cfg(const ugkwp_sim* s, ugkwp_launch_cfg* out) {
     out->particle_blocks = s->lc.particle_blocks;
     out->wave_blocks = s->lc.wave_blocks;
     out->track_threads = s->lc.track.threads;
-    out->track_stages = s->lc.track.stages;
     out->smem_carveout = s->lc.carveout;
-    out->reserved = 0;
     return UGKWP_OK;
 }
 
@@ -1327,15 +1327,11 @@ int ugkwp_set_launch_cfg(ugkwp_sim* s, const ugkwp_launch_cfg* cfg) {
         return fail(UGKWP_E_ARG, "grid sizes must be in [1, 2^20]");
     if (cfg->track_threads != 128 && cfg->track_threads != 256)
         return fail(UGKWP_E_ARG, "track_threads must be 128 or 256");
-    if (cfg->track_stages != 0 && cfg->track_stages != 2 && cfg->track_stages != 3)
-        return fail(UGKWP_E_ARG, "track_stages must be 0, 2 or 3");
     if (cfg->smem_carveout < -1 || cfg->smem_carveout > 100)
         return fail(UGKWP_E_ARG, "smem_carveout must be -1 or in [0, 100]");
-    LaunchCfg lc{cfg->particle_blocks, cfg->wave_blocks, TrackShape{cfg->track_threads, cfg->track_stages},
-                 cfg->smem_carveout};
+    LaunchCfg lc{cfg->particle_blocks, cfg->wave_blocks, TrackShape{cfg->track_threads}, cfg->smem_carveout};
     if (lc.particle_blocks != s->lc.particle_blocks || lc.wave_blocks != s->lc.wave_blocks ||
-        lc.track.threads != s->lc.track.threads || lc.track.stages != s->lc.track.stages ||
-        lc.carveout != s->lc.carveout) {
+        lc.track.threads != s->lc.track.threads || lc.carveout != s->lc.carveout) {
         CU(configure_kernels(s->P, lc));
         s->lc = lc;
         s->drop_graphs();
@@ -1348,17 +1344,17 @@ int ugkwp_set_launch_cfg(ugkwp_sim* s, const ugkwp_launch_cfg* cfg) {
 namespace {
 
 ugkwp_launch_cfg to_public(const LaunchCfg& c) {
-    return ugkwp_launch_cfg{c.particle_blocks, c.wave_blocks, c.track.threads, c.track.stages, c.carveout, 0};
+    return ugkwp_launch_cfg{c.particle_blocks, c.wave_blocks, c.track.threads, c.carveout};
 }
 
-// The autotuner's search, in two stages: (1) tracking shape x carveout at
-// 1024 resident tracking threads per SM and one wave block per SM; (2) for the
+// The autotuner's search, in two stages: (1) tracking block shape x carveout
+// at 1024 resident tracking threads per SM and one wave block per SM; (2) for the
 // fastest of those, resident tracking threads per SM (512, 1024, 2048) x wave
 // blocks per SM (1, 2 at order 2).  trial(c, ms) sets c, steps and returns the
 // time; the fastest configuration is returned in best.
 template <class Trial> int tune_search(int order, Trial&& trial, LaunchCfg& best) {
     const int sms = sm_count();
-    const TrackShape shapes[] = {{128, 0}, {128, 2}, {128, 3}, {256, 2}};
+    const TrackShape shapes[] = {{128}, {256}};
     float best_ms = 0.0f;
     bool have = false;
     auto consider = [&](const LaunchCfg& c) {
@@ -1369,7 +1365,7 @@ template <class Trial> int tune_search(int order, Trial&& trial, LaunchCfg& best
         return (int)UGKWP_OK;
     };
     for (const TrackShape& sh : shapes)
-        for (int carve : {-1, 58, 86}) {
+        for (int carve : {-1, 58}) {
             int rc = consider(LaunchCfg{1024 / sh.threads * sms, sms, sh, carve});
             if (rc) return rc;
         }
@@ -1620,7 +1616,7 @@ int ugkwp_batch_autotune(ugkwp_batch* b, int32_t steps_per_trial, ugkwp_launch_c
         if (s->timing) return fail(UGKWP_E_STATE, "per-kernel timing is enabled on a member");
         order = std::max(order, (int)s->P.order);
     }
-    LaunchCfg best_lc = b->sims.empty() ? LaunchCfg{1, 1, {128, 0}, -1} : b->sims[0]->lc;
+    LaunchCfg best_lc = b->sims.empty() ? LaunchCfg{1, 1, {128}, -1} : b->sims[0]->lc;
     int rc0 = tune_search(order, [&](const LaunchCfg& c, float& ms) {
         ugkwp_launch_cfg u = to_public(c);
         for (auto* s : b->sims) {

@@ -28,6 +28,14 @@ __device__ __forceinline__ void set_err(const DevState& s, int32_t bits) {
     atomicOr(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_ERR]), (unsigned long long)bits);
 }
 
+// A failed self-check of a kernel: the error bit, and the first failure's
+// check number and value (the access it guards is skipped).
+__device__ __forceinline__ void check_failed(const DevState& s, int check, unsigned long long value) {
+    atomicCAS(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_CHECK]), 0ULL,
+              ((unsigned long long)check << 48) | (value & 0xffffffffffffULL));
+    set_err(s, ERRB_CHECK);
+}
+
 __device__ __forceinline__ unsigned long long make_id(long long step, int cell, int k) {
     return ((unsigned long long)step << 40) | ((unsigned long long)cell << 16) | (unsigned long long)k;
 }
@@ -406,73 +414,6 @@ __device__ __forceinline__ bool fixed_of_mass(double m, int e, long long& q) {
     return true;
 }
 
-// ---- bulk copies of particle tiles into shared memory: the copy engine
-// (cp.async.bulk, TMA) writes a stage and completes the transaction count of
-// the stage's mbarrier; the block waits on the barrier's phase parity.
-__device__ __forceinline__ unsigned smem_addr(const void* ptr) { return (unsigned)__cvta_generic_to_shared(ptr); }
-__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect(unsigned long long* bar, unsigned bytes) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok)
-                 : "r"(smem_addr(bar)), "r"(parity)
-                 : "memory");
-    return ok != 0;
-}
-// Wait for the phase of the given parity to complete: at most MBAR_TRIES
-// tests (each may suspend the thread for a while), false if it did not.
-constexpr int MBAR_TRIES = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    for (int k = 0; k < MBAR_TRIES; ++k)
-        if (mbar_test(bar, parity)) return true;
-    return false;
-}
-
-// One stage of T particles in shared memory, structure of arrays like the
-// particle buffer: x[3], u[3] (particle precision), e (KE), m, id, cell.  Every
-// array starts on a 16-byte boundary (T RS is a multiple of 512).
-template <class Real, bool KE, int T> struct Stage {
-    static constexpr int RS = (int)sizeof(Real);
-    static constexpr int X = 0;
-    static constexpr int U = 3 * T * RS;
-    static constexpr int E = 6 * T * RS;
-    static constexpr int M = (KE ? 7 : 6) * T * RS;
-    static constexpr int ID = M + 8 * T;
-    static constexpr int CELL = ID + 8 * T;
-    static constexpr int BYTES = CELL + 4 * T;
-};
-
-// Thread 0: bulk copies of the tile of T particles from index t0 (a multiple
-// of T: every source starts 16-byte aligned, and the particle arrays hold
-// whole tiles) into stage `st`, completing on `bar`.
-template <class Real, bool KE, int T>
-__device__ __forceinline__ void stage_tile(char* st, unsigned long long* bar, const PartView<Real>& b, long long t0) {
-    using L = Stage<Real, KE, T>;
-    mbar_expect(bar, (unsigned)L::BYTES);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        bulk_load(st + L::X + c * T * L::RS, b.x[c] + t0, T * L::RS, bar);
-        bulk_load(st + L::U + c * T * L::RS, b.u[c] + t0, T * L::RS, bar);
-    }
-    if constexpr (KE) bulk_load(st + L::E, b.e + t0, T * L::RS, bar);
-    bulk_load(st + L::M, b.m + t0, 8 * T, bar);
-    bulk_load(st + L::ID, b.id + t0, 8 * T, bar);
-    bulk_load(st + L::CELL, b.cell + t0, 4 * T, bar);
-}
-
 // Thread 0's source of tiles: grabs of TILE_GRAB consecutive tiles from the
 // global counter (one atomic per grab), handed out in order, so the tiles a
 // block walks increase.  Returns the first particle index of the next tile.
@@ -487,260 +428,212 @@ __device__ __forceinline__ long long next_tile(TileQueue& q, int64_t* ctr, int T
     return (q.next++) * T;
 }
 
+// ---- the walk of one particle, one tet at a time
+// Walk state along x0 + u (t - t0): the tet it is in, the face it entered
+// through (or last reflected from, skipped in the exit test), its counters.
+template <class Real> struct Walk {
+    Real x0[3], u[3], t0, t_end;
+    int tet, last, ncross, nrefl, nwall, status;
+};
+
+// One tet of the face-by-face walk (Sec. 2.2 streaming): the exit face is the
+// one with u.n > 0 and the smallest crossing time (d - n.x0)/(u.n), compared
+// by cross products (positive denominators) with one division; ties keep the
+// lower local face.  Returns true when the walk goes on (into the neighbour,
+// or restarted at a wall); false when it ended: stopped inside the tet (xe the
+// end point), left the domain (status 2) or passed max_crossings (status 4).
+template <class Real, bool KE>
+__device__ __forceinline__ bool visit(const DevMesh& m, const DevParams& p, long long step, unsigned long long id,
+                                      Walk<Real>& w, Real xe[3], Real& ee) {
+    // the tet's neighbour codes, loaded with its planes (they sit in
+    // another sector of the tet's record)
+    const int4 nbv = Trk<Real>::nbv(m, w.tet);
+    int best = -1;
+    Real nbest = (Real)0, dbest = (Real)1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (k == w.last) continue;
+        Real nx, ny, nz, d;
+        Trk<Real>::plane(m, w.tet, k, nx, ny, nz, d);
+        const Real un = (w.u[0] * nx + w.u[1] * ny) + w.u[2] * nz;
+        if (un > (Real)0) {
+            const Real xn = (w.x0[0] * nx + w.x0[1] * ny) + w.x0[2] * nz;
+            const Real num = d - xn;
+            if (best < 0 || num * dbest < nbest * un) { best = k; nbest = num; dbest = un; }
+        }
+    }
+    Real sbest = best >= 0 ? nbest / dbest : (Real)0;
+    const Real rem = w.t_end - w.t0;
+    if (best < 0 || sbest >= rem) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xe[c] = w.x0[c] + w.u[c] * rem;
+        return false;
+    }
+    if (sbest < (Real)0) sbest = (Real)0;
+    ++w.ncross;
+    if (w.ncross > p.max_crossings) {
+        w.status |= 4;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xe[c] = w.x0[c];
+        return false;
+    }
+    const int code = best == 0 ? nbv.x : best == 1 ? nbv.y : best == 2 ? nbv.z : nbv.w;
+    if (code >= 0) {
+        w.tet = code >> 2;
+        w.last = code & 3;
+        return true;
+    }
+    const int bi = -1 - code;
+    const DevBc& bc = p.bc[m.bf_tag[bi]];
+    if (bc.type == UGKWP_BC_FARFIELD || bc.type == UGKWP_BC_OUTFLOW) {
+        w.status |= 2;
+        return false;
+    }
+    Real xh[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) xh[c] = w.x0[c] + w.u[c] * sbest;
+    if (bc.type == UGKWP_BC_SPECULAR) {
+        Real nx, ny, nz, d;
+        Trk<Real>::plane(m, w.tet, best, nx, ny, nz, d);
+        const Real un = (w.u[0] * nx + w.u[1] * ny) + w.u[2] * nz;
+        const Real two = un + un;
+        w.u[0] = w.u[0] - two * nx;
+        w.u[1] = w.u[1] - two * ny;
+        w.u[2] = w.u[2] - two * nz;
+    } else {
+        // diffuse re-emission, full accommodation: |u_n| = sqrt(-2 R T_w ln eta),
+        // tangential components U_w,t + sqrt(R T_w) N(0,1)
+        const dm::U4 r = dm::philox(id, (unsigned long long)step, TAG_WALL, (unsigned long long)w.nwall, p.seed, 0ULL);
+        if constexpr (sizeof(Real) == 4) {
+            // mixed mode: binary32 from the wall constants and the face frame
+            // rounded to binary32
+            const float vn = sqrtf(bc.c2rt_f * dm::f_log(dm::u01f(r.a)));
+            const float rad = sqrtf(-2.0f * dm::f_log(dm::u01f(r.b)));
+            float sn, cs;
+            dm::f_sincos2pi(dm::u01f(r.c), &sn, &cs);
+            const int nbf = m.nbf;
+            const float v1 = m.bf_f[(size_t)9 * nbf + bi] + bc.sw_f * (rad * cs);
+            const float v2 = m.bf_f[(size_t)10 * nbf + bi] + bc.sw_f * (rad * sn);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                w.u[c] = ((-vn) * m.bf_f[(size_t)c * nbf + bi] + v1 * m.bf_f[(size_t)(3 + c) * nbf + bi]) +
+                         v2 * m.bf_f[(size_t)(6 + c) * nbf + bi];
+            if constexpr (KE)
+                ee = internal_energy<float>(id, step, TAG_WINT, 2ULL * (unsigned long long)w.nwall, p.K, bc.sw_f, p.seed);
+        } else {
+            const double vn = sqrt(-2.0 * p.R * bc.T_w * dm::d_log(dm::u01d(r.a)));
+            const double rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.b)));
+            double sn, cs;
+            dm::d_sincos2pi(dm::u01d(r.c), &sn, &cs);
+            const double sw = sqrt(p.R * bc.T_w);
+            const int nbf = m.nbf;
+            double n3[3], t1[3], t2[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                n3[c] = m.bf_n[(size_t)c * nbf + bi];
+                t1[c] = m.bf_t1[(size_t)c * nbf + bi];
+                t2[c] = m.bf_t2[(size_t)c * nbf + bi];
+            }
+            const double v1 = ((bc.U_w[0] * t1[0] + bc.U_w[1] * t1[1]) + bc.U_w[2] * t1[2]) + sw * (rad * cs);
+            const double v2 = ((bc.U_w[0] * t2[0] + bc.U_w[1] * t2[1]) + bc.U_w[2] * t2[2]) + sw * (rad * sn);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) w.u[c] = (Real)(((-vn) * n3[c] + v1 * t1[c]) + v2 * t2[c]);
+            if constexpr (KE)
+                ee = (Real)internal_energy<double>(id, step, TAG_WINT, 2ULL * (unsigned long long)w.nwall, p.K, sw, p.seed);
+        }
+        ++w.nwall;
+    }
+    ++w.nrefl;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) w.x0[c] = xh[c];
+    w.t0 = w.t0 + sbest;
+    w.last = best;
+    return true;
+}
+
+// A particle whose walk ended, ready for the outputs.
+template <class Real> struct Ended {
+    bool active, survivor, mover, exited;
+    int tet, c0;
+    Real xe[3], ue[3], us[3], es, ee;
+    double mm;
+    unsigned long long id;
+};
+
+// Walks that did not end in their first tet wait in shared memory (structure
+// of arrays, QCAP entries per block) until half a block of them has gathered;
+// the block then walks them on in full warps.  An entry holds the walk state,
+// the particle's internal energy (KE) and its slot in the buffer, from which
+// the rest of the particle is read again when the walk ends.
+template <class Real, bool KE, int T> struct WalkQueue {
+    static constexpr int QCAP = T + T / 2;
+    Real x0[3][QCAP], u[3][QCAP], t0[QCAP], t_end[QCAP], ee[KE ? QCAP : 1];
+    int tet[QCAP], last[QCAP], ncross[QCAP], nrefl[QCAP], nwall[QCAP], flags[QCAP];  // flags: status | coll << 3
+    long long slot[QCAP];
+    int count;
+};
+
 // KE: the particles carry an internal energy (K > 0).  THREADS: particles per
-// tile (one per thread).  STAGES = 0: each thread loads its particle from the
-// buffer when its tile starts; STAGES > 0: the tiles are staged in shared
-// memory by bulk copies, STAGES - 1 tiles ahead of the one being walked.
-template <class Real, bool KE, int THREADS, int STAGES>
+// tile (one per thread).
+template <class Real, bool KE, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br,
                                                                   PartBufRaw nr, PartBufRaw ar) {
     constexpr int NW = THREADS / 32;
-    using L = Stage<Real, KE, THREADS>;
+    using Q = WalkQueue<Real, KE, THREADS>;
     if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
-    const PartView<Real> b = view<Real>(br);   // this step's particles: survivors, then samples
-    const PartView<Real> nxt = view<Real>(nr);  // the next step's survivors, compacted
+    const PartView<Real> b = view<Real>(br);   // this step's particles, sorted by cell (holes: cell -1)
+    const PartView<Real> nxt = view<Real>(nr);  // the next step's survivors, in their end cells' buckets
     const PartView<Real> mv = view<Real>(ar);  // mover list: x = u at start, u = u at end
     const long long n = s.cnt64[CNT_N_B];
     const long long step = s.cnt64[CNT_STEP];
     const double dt = s.dt[0];
     const Real dtR = (Real)dt;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // slot bookkeeping in two sets, alternating between tiles, so that no
-    // barrier is needed after a tile's stores: a set is rewritten two tiles
-    // later, after two barriers every warp has passed
+    // slot bookkeeping in two sets, alternating between output rounds, so
+    // that no barrier is needed after a round's stores: a set is rewritten
+    // two rounds later, after two barriers every warp has passed
     __shared__ int sh_cnt[2][NW];
     __shared__ long long sh_base[2], sh_tile[2];
     const long long wtot = s.cnt64[CNT_WTOT];  // overflow slots start after the buckets
     int par = 0;
     __shared__ unsigned long long sh_red[NW][8];
-    // staged tiles: first particle index per stage, one mbarrier per stage
-    extern __shared__ __align__(16) char stg[];
-    __shared__ unsigned long long sh_bar[STAGES > 0 ? STAGES : 1];
-    __shared__ long long sh_stile[STAGES > 0 ? STAGES : 1];
+    __shared__ Q q;
     // per-thread counters, reduced once per block at the end
     unsigned c_valid = 0, c_coll = 0, c_exit = 0, c_lost = 0, c_cross = 0, c_wall = 0, c_surv = 0;
     // tiles of THREADS particles are taken from a global counter, so that
     // blocks that start late (or walk short paths) take fewer tiles
     TileQueue tq;  // thread 0's
     if (threadIdx.x == 0) {
-        if constexpr (STAGES > 0) {
-            for (int k = 0; k < STAGES; ++k) mbar_init(&sh_bar[k]);
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            for (int k = 0; k < STAGES; ++k) {
-                const long long t0 = next_tile(tq, &s.cnt64[CNT_TILE], THREADS);
-                sh_stile[k] = t0;
-                if (t0 < n) stage_tile<Real, KE, THREADS>(stg + k * L::BYTES, &sh_bar[k], b, t0);
-            }
-        } else {
-            sh_tile[0] = next_tile(tq, &s.cnt64[CNT_TILE], THREADS);
-        }
+        q.count = 0;
+        sh_tile[0] = next_tile(tq, &s.cnt64[CNT_TILE], THREADS);
     }
     __syncthreads();
-    int slot = 0;        // stage of this tile
-    unsigned phase = 0;  // parity of the stage's mbarrier phase this tile completes
-    for (;;) {
-        const long long bb = STAGES > 0 ? sh_stile[slot] : sh_tile[par];  // block-uniform
-        if (bb >= n) break;
-        const long long i = bb + threadIdx.x;
-        // a stage whose copies did not complete within the wait's limit is
-        // not read; the block stops at the next barrier
-        const bool staged = STAGES == 0 || mbar_wait(&sh_bar[slot], phase);
-        // the slot's start cell; -1 marks a hole of a survivor bucket
-        int c0 = -1, tet = -1;
-        if (i < n && staged)
-            c0 = STAGES > 0 ? reinterpret_cast<const int*>(stg + slot * L::BYTES + L::CELL)[threadIdx.x] : b.cell[i];
-        const bool valid = c0 >= 0;
-        int status = 0, ncross = 0, nrefl = 0, nwall = 0;
-        long long qmass = 0;
-        bool survivor = false, mover = false, exited = false;
-        Real us[3] = {(Real)0, (Real)0, (Real)0}, ue[3] = {(Real)0, (Real)0, (Real)0};
-        Real xe[3] = {(Real)0, (Real)0, (Real)0};
-        Real es = (Real)0, ee = (Real)0;  // internal energy at start and end (KE)
-        double mm = 0.0;
-        unsigned long long id = 0;
-        if (valid) {
-            Real x0[3], u[3];
-            if constexpr (STAGES > 0) {
-                const char* st = stg + slot * L::BYTES;
-                const int k = threadIdx.x;
-                id = reinterpret_cast<const unsigned long long*>(st + L::ID)[k];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    x0[c] = reinterpret_cast<const Real*>(st + L::X + c * THREADS * L::RS)[k];
-                    u[c] = reinterpret_cast<const Real*>(st + L::U + c * THREADS * L::RS)[k];
-                }
-                mm = reinterpret_cast<const double*>(st + L::M)[k];
-                if constexpr (KE) {
-                    es = reinterpret_cast<const Real*>(st + L::E)[k];
-                    ee = es;
-                }
-            } else {
-                id = b.id[i];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) { x0[c] = b.x[c][i]; u[c] = b.u[c][i]; }
-                mm = b.m[i];
-                if constexpr (KE) {
-                    es = b.e[i];
-                    ee = es;
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) us[c] = u[c];
-            Real t_end = dtR;
-            bool coll = false;
-            if ((long long)(id >> 40) != step) {
-                // Philox4x32-10, counter (id low, id high, step, TAG_TF), key (seed low, seed high)
-                const unsigned long long r = dm::philox32_2((unsigned)id, (unsigned)(id >> 32), (unsigned)step,
-                                                            (unsigned)TAG_TF, (unsigned)p.seed,
-                                                            (unsigned)(p.seed >> 32));
-                const Real tf = Trk<Real>::tf(Trk<Real>::tau(s, c0), r);
-                if (tf < dtR) { coll = true; t_end = tf; }
-            }
-            // ---- face-by-face walk along x0 + u (t - t0)
-            tet = c0;
-            int last = -1;
-            Real t0 = (Real)0;
-            for (;;) {
-                // the tet's neighbour codes, loaded with its planes (they sit in
-                // another sector of the tet's record)
-                const int4 nbv = Trk<Real>::nbv(m, tet);
-                // smallest crossing time (d - n.x0)/(u.n) over u.n > 0, compared
-                // by cross products (positive denominators), one division
-                int best = -1;
-                Real nbest = (Real)0, dbest = (Real)1;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (k == last) continue;
-                    Real nx, ny, nz, d;
-                    Trk<Real>::plane(m, tet, k, nx, ny, nz, d);
-                    const Real un = (u[0] * nx + u[1] * ny) + u[2] * nz;
-                    if (un > (Real)0) {
-                        const Real xn = (x0[0] * nx + x0[1] * ny) + x0[2] * nz;
-                        const Real num = d - xn;
-                        if (best < 0 || num * dbest < nbest * un) { best = k; nbest = num; dbest = un; }
-                    }
-                }
-                Real sbest = best >= 0 ? nbest / dbest : (Real)0;
-                const Real rem = t_end - t0;
-                if (best < 0 || sbest >= rem) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) xe[c] = x0[c] + u[c] * rem;
-                    break;
-                }
-                if (sbest < (Real)0) sbest = (Real)0;
-                ++ncross;
-                if (ncross > p.max_crossings) {
-                    status |= 4;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) xe[c] = x0[c];
-                    break;
-                }
-                const int code = best == 0 ? nbv.x : best == 1 ? nbv.y : best == 2 ? nbv.z : nbv.w;
-                if (code >= 0) { tet = code >> 2; last = code & 3; continue; }
-                const int bi = -1 - code;
-                const DevBc& bc = p.bc[m.bf_tag[bi]];
-                if (bc.type == UGKWP_BC_FARFIELD || bc.type == UGKWP_BC_OUTFLOW) { status |= 2; break; }
-                Real xh[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) xh[c] = x0[c] + u[c] * sbest;
-                if (bc.type == UGKWP_BC_SPECULAR) {
-                    Real nx, ny, nz, d;
-                    Trk<Real>::plane(m, tet, best, nx, ny, nz, d);
-                    const Real un = (u[0] * nx + u[1] * ny) + u[2] * nz;
-                    const Real two = un + un;
-                    u[0] = u[0] - two * nx;
-                    u[1] = u[1] - two * ny;
-                    u[2] = u[2] - two * nz;
-                } else {
-                    // diffuse re-emission, full accommodation: |u_n| = sqrt(-2 R T_w ln eta),
-                    // tangential components U_w,t + sqrt(R T_w) N(0,1)
-                    const dm::U4 r = dm::philox(id, (unsigned long long)step, TAG_WALL, (unsigned long long)nwall,
-                                                p.seed, 0ULL);
-                    if constexpr (sizeof(Real) == 4) {
-                        // mixed mode: binary32 from the wall constants and the
-                        // face frame rounded to binary32
-                        const float vn = sqrtf(bc.c2rt_f * dm::f_log(dm::u01f(r.a)));
-                        const float rad = sqrtf(-2.0f * dm::f_log(dm::u01f(r.b)));
-                        float sn, cs;
-                        dm::f_sincos2pi(dm::u01f(r.c), &sn, &cs);
-                        const int nbf = m.nbf;
-                        const float v1 = m.bf_f[(size_t)9 * nbf + bi] + bc.sw_f * (rad * cs);
-                        const float v2 = m.bf_f[(size_t)10 * nbf + bi] + bc.sw_f * (rad * sn);
-#pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            u[c] = ((-vn) * m.bf_f[(size_t)c * nbf + bi] + v1 * m.bf_f[(size_t)(3 + c) * nbf + bi]) +
-                                   v2 * m.bf_f[(size_t)(6 + c) * nbf + bi];
-                        if constexpr (KE)
-                            ee = internal_energy<float>(id, step, TAG_WINT, 2ULL * (unsigned long long)nwall, p.K, bc.sw_f,
-                                                        p.seed);
-                    } else {
-                        const double vn = sqrt(-2.0 * p.R * bc.T_w * dm::d_log(dm::u01d(r.a)));
-                        const double rad = sqrt(-2.0 * dm::d_log(dm::u01d(r.b)));
-                        double sn, cs;
-                        dm::d_sincos2pi(dm::u01d(r.c), &sn, &cs);
-                        const double sw = sqrt(p.R * bc.T_w);
-                        const int nbf = m.nbf;
-                        double n3[3], t1[3], t2[3];
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            n3[c] = m.bf_n[(size_t)c * nbf + bi];
-                            t1[c] = m.bf_t1[(size_t)c * nbf + bi];
-                            t2[c] = m.bf_t2[(size_t)c * nbf + bi];
-                        }
-                        const double v1 = ((bc.U_w[0] * t1[0] + bc.U_w[1] * t1[1]) + bc.U_w[2] * t1[2]) + sw * (rad * cs);
-                        const double v2 = ((bc.U_w[0] * t2[0] + bc.U_w[1] * t2[1]) + bc.U_w[2] * t2[2]) + sw * (rad * sn);
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) u[c] = (Real)(((-vn) * n3[c] + v1 * t1[c]) + v2 * t2[c]);
-                        if constexpr (KE)
-                            ee = (Real)internal_energy<double>(id, step, TAG_WINT, 2ULL * (unsigned long long)nwall, p.K,
-                                                               sw, p.seed);
-                    }
-                    ++nwall;
-                }
-                ++nrefl;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) x0[c] = xh[c];
-                t0 = t0 + sbest;
-                last = best;
-            }
-            exited = status & 2;
-            const bool lost = status & 4;
-            survivor = !exited && (!coll || lost);
-            if (coll && !lost && !exited) status |= 1;
-            // ---- particle flux by counting: a particle that ends in its start
-            // cell with its velocity unchanged contributes nothing; the others
-            // are listed for the binary64 flux pass
-            mover = exited || tet != c0 || nrefl > 0;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) ue[c] = u[c];
-            if (survivor && !fixed_of_mass(mm, p.exps[0], qmass)) set_err(s, ERRB_FIXED_OVERFLOW);
-            c_valid += 1;
-            c_coll += status & 1;
-            c_exit += (status >> 1) & 1;
-            c_lost += (status >> 2) & 1;
-            c_cross += ncross;
-            c_wall += nwall;
-        }
-        // ---- a11: each survivor goes to the bucket of its end cell in the
-        // next buffer, so the next step finds the particles sorted by cell.
-        // Lanes with the same end cell take consecutive slots from the cell's
-        // count (one atomic per group); the count is also the cell's survivor
-        // count N_left of the next step.  A survivor beyond its bucket takes an
+
+    // ---- outputs of the particles whose walks ended this round (one per
+    // lane or none): the survivor's slot in its end cell's bucket, the
+    // survivors' mass per end cell, the counters, the mover record.  Contains
+    // the block's two barriers of the round; with `advance`, thread 0 also
+    // takes the next tile.
+    auto emit = [&](const Ended<Real>& e, bool advance, int qtake) {
+        // a11: each survivor goes to the bucket of its end cell in the next
+        // buffer, so the next step finds the particles sorted by cell.  Lanes
+        // with the same end cell take consecutive slots from the cell's count
+        // (one atomic per group); the count is also the cell's survivor count
+        // N_left of the next step.  A survivor beyond its bucket takes an
         // overflow slot after the buckets.
-        const int key = survivor ? tet : -1;
-        int srank = 0;  // the survivor's slot in its bucket, written after the movers' barriers
+        const int key = e.survivor ? e.tet : -1;
+        int srank = 0;
         {
             const unsigned peers = __match_any_sync(FULL, key);
             const int leader = __ffs(peers) - 1;
-            int rank = 0;
-            if (lane == leader && key >= 0) rank = atomicAdd(&s.nleft_next[key], __popc(peers));
-            rank = __shfl_sync(FULL, rank, leader) + __popc(peers & ((1u << lane) - 1u));
-            srank = rank;
+            if (lane == leader && key >= 0) srank = atomicAdd(&s.nleft_next[key], __popc(peers));
+            srank = __shfl_sync(FULL, srank, leader) + __popc(peers & ((1u << lane) - 1u));
         }
-        // ---- survivors' fixed-point mass per end cell: segmented reduction
-        // over lanes with equal keys in a row, one atomic per run
+        // survivors' fixed-point mass per end cell: segmented reduction over
+        // lanes with equal keys in a row, one atomic per run
         {
-            long long v = survivor ? qmass : 0;
+            long long v = 0;
+            if (e.survivor && !fixed_of_mass(e.mm, p.exps[0], v)) set_err(s, ERRB_FIXED_OVERFLOW);
             const int prev = __shfl_up_sync(FULL, key, 1);
             const bool head = lane == 0 || prev != key;
             const unsigned heads = __ballot_sync(FULL, head);
@@ -753,26 +646,11 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_track(DevMesh m, De
             const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
             if (tail && key >= 0) atomicAdd(reinterpret_cast<unsigned long long*>(&s.smass_next[key]), (unsigned long long)v);
         }
-        c_surv += survivor ? 1u : 0u;
-        // ---- movers: one slot reservation per block and iteration
-        const unsigned mmask = __ballot_sync(FULL, mover);
+        c_surv += e.survivor ? 1u : 0u;
+        // movers: one slot reservation per block and round
+        const unsigned mmask = __ballot_sync(FULL, e.mover);
         if (lane == 0) sh_cnt[par][warp] = __popc(mmask);
-        if (__syncthreads_or(!staged)) {
-            // a stage wait gave up: report it, give the copies still in flight
-            // a bounded wait (shared memory must not be released under them)
-            // and stop; the step's particle state is not valid
-            if (threadIdx.x == 0) {
-                set_err(s, ERRB_STAGE_WAIT);
-                if constexpr (STAGES > 0) {
-                    unsigned ph = phase;
-                    for (int k = 0, sl = slot; k < STAGES; ++k) {
-                        if (sh_stile[sl] < n) mbar_wait(&sh_bar[sl], ph);
-                        if (++sl == STAGES) { sl = 0; ph ^= 1u; }
-                    }
-                }
-            }
-            return;
-        }
+        __syncthreads();
         if (threadIdx.x == 0) {
             int tot = 0;
             for (int w = 0; w < NW; ++w) {
@@ -783,66 +661,205 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_track(DevMesh m, De
             sh_base[par] =
                 tot ? (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_RESV]), (unsigned long long)tot)
                     : 0LL;
-            if constexpr (STAGES > 0) {
-                // refill this tile's stage (every thread read its particle from
-                // it before the barrier above) with the tile STAGES ahead
-                const long long t0 = next_tile(tq, &s.cnt64[CNT_TILE], THREADS);
-                sh_stile[slot] = t0;
-                if (t0 < n) {
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    stage_tile<Real, KE, THREADS>(stg + slot * L::BYTES, &sh_bar[slot], b, t0);
-                }
-            } else {
-                // the next tile, in the other set (its last readers read it
-                // before the barrier above)
-                sh_tile[par ^ 1] = next_tile(tq, &s.cnt64[CNT_TILE], THREADS);
-            }
+            // the walks taken from the queue this round leave it (every
+            // thread read its entry before the barrier above)
+            q.count -= qtake;
+            // the next tile, in the other set (its last readers read it before
+            // the barrier above); a round without a new tile keeps the current one
+            sh_tile[par ^ 1] = advance ? next_tile(tq, &s.cnt64[CNT_TILE], THREADS) : sh_tile[par];
         }
         __syncthreads();
-        if (survivor) {
+        if (e.survivor) {
             long long j = -1;
-            if (srank < s.wcap[tet]) {
-                j = (long long)s.woff[tet] + srank;
+            if (srank < s.wcap[e.tet]) {
+                j = (long long)s.woff[e.tet] + srank;
             } else {
                 const long long o = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&s.cnt64[CNT_OVF]), 1ULL);
                 if (o < p.capacity - wtot) j = wtot + o;
                 else set_err(s, ERRB_CAPACITY);
             }
+            if (j >= p.capacity) {
+                check_failed(s, 6, (unsigned long long)j);
+                j = -1;
+            }
             if (j >= 0) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    nxt.x[c][j] = xe[c];
-                    nxt.u[c][j] = ue[c];
+                    nxt.x[c][j] = e.xe[c];
+                    nxt.u[c][j] = e.ue[c];
                 }
-                nxt.m[j] = mm;
-                nxt.cell[j] = tet;
-                nxt.id[j] = id;
-                if constexpr (KE) nxt.e[j] = ee;
+                nxt.m[j] = e.mm;
+                nxt.cell[j] = e.tet;
+                nxt.id[j] = e.id;
+                if constexpr (KE) nxt.e[j] = e.ee;
             }
         }
-        if (mover) {
-            const long long j = sh_base[par] + sh_cnt[par][warp] + __popc(mmask & ((1u << lane) - 1u));
+        const long long mj = sh_base[par] + sh_cnt[par][warp] + __popc(mmask & ((1u << lane) - 1u));
+        if (e.mover && mj >= p.capacity) check_failed(s, 7, (unsigned long long)mj);
+        if (e.mover && mj < p.capacity) {
+            const long long j = mj;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                mv.x[c][j] = us[c];
-                mv.u[c][j] = ue[c];
+                mv.x[c][j] = e.us[c];
+                mv.u[c][j] = e.ue[c];
             }
-            mv.m[j] = mm;
-            mv.cell[j] = c0;
-            mv.id[j] = ((unsigned long long)(unsigned)tet << 1) | (exited ? 1ULL : 0ULL);
+            mv.m[j] = e.mm;
+            mv.cell[j] = e.c0;
+            mv.id[j] = ((unsigned long long)(unsigned)e.tet << 1) | (e.exited ? 1ULL : 0ULL);
             if constexpr (KE) {
-                mv.e[j] = es;
-                mv.e2[j] = ee;
+                mv.e[j] = e.es;
+                mv.e2[j] = e.ee;
             }
         }
         par ^= 1;
-        if (STAGES > 0 && ++slot == STAGES) {
-            slot = 0;
-            phase ^= 1u;
+    };
+
+    // The end of a walk: removal (a9), counters, the mover flag (a8: a
+    // particle that ends in its start cell with its velocity unchanged
+    // contributes nothing to the counting flux; the others are listed for the
+    // binary64 flux pass).
+    auto finish = [&](const Walk<Real>& w, bool coll, Ended<Real>& e) {
+        e.active = true;
+        e.exited = w.status & 2;
+        const bool lost = w.status & 4;
+        e.survivor = !e.exited && (!coll || lost);
+        const int status = w.status | ((coll && !lost && !e.exited) ? 1 : 0);
+        e.tet = w.tet;
+        e.mover = e.exited || w.tet != e.c0 || w.nrefl > 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) e.ue[c] = w.u[c];
+        c_coll += status & 1;
+        c_exit += (status >> 1) & 1;
+        c_lost += (status >> 2) & 1;
+        c_cross += w.ncross;
+        c_wall += w.nwall;
+    };
+
+    for (;;) {
+        const long long bb = sh_tile[par];  // block-uniform
+        const bool have_tile = bb < n;
+        if (!have_tile && q.count == 0) break;
+        // ---- a new tile: load, t_f, the first tet of every walk
+        Ended<Real> e;
+        e.active = e.survivor = e.mover = e.exited = false;
+        e.tet = e.c0 = -1;
+        e.es = e.ee = (Real)0;
+        e.mm = 0.0;
+        e.id = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) e.xe[c] = e.ue[c] = e.us[c] = (Real)0;
+        if (have_tile) {
+            const long long i = bb + threadIdx.x;
+            // the slot's start cell; -1 marks a hole of a survivor bucket
+            const int c0 = i < n ? b.cell[i] : -1;
+            if (c0 >= 0) {
+                Walk<Real> w;
+                e.id = b.id[i];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    w.x0[c] = b.x[c][i];
+                    w.u[c] = b.u[c][i];
+                }
+                e.mm = b.m[i];
+                if constexpr (KE) e.es = b.e[i];
+                e.ee = e.es;
+                e.c0 = c0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) e.us[c] = w.u[c];
+                c_valid += 1;
+                // a6: t_f = min(-tau ln eta, dt) for the particles left from the last step
+                w.t_end = dtR;
+                bool coll = false;
+                if ((long long)(e.id >> 40) != step) {
+                    // Philox4x32-10, counter (id low, id high, step, TAG_TF), key (seed low, seed high)
+                    const unsigned long long r = dm::philox32_2((unsigned)e.id, (unsigned)(e.id >> 32), (unsigned)step,
+                                                                (unsigned)TAG_TF, (unsigned)p.seed,
+                                                                (unsigned)(p.seed >> 32));
+                    const Real tf = Trk<Real>::tf(Trk<Real>::tau(s, c0), r);
+                    if (tf < dtR) { coll = true; w.t_end = tf; }
+                }
+                // a7: the walk's first tet
+                w.t0 = (Real)0;
+                w.tet = c0;
+                w.last = -1;
+                w.ncross = w.nrefl = w.nwall = w.status = 0;
+                if (visit<Real, KE>(m, p, step, e.id, w, e.xe, e.ee)) {
+                    // the walk goes on: it waits in the queue
+                    const int k = atomicAdd(&q.count, 1);
+                    if (k >= Q::QCAP) check_failed(s, 5, (unsigned long long)k);
+                    else {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        q.x0[c][k] = w.x0[c];
+                        q.u[c][k] = w.u[c];
+                    }
+                    q.t0[k] = w.t0;
+                    q.t_end[k] = w.t_end;
+                    if constexpr (KE) q.ee[k] = e.ee;
+                    q.tet[k] = w.tet;
+                    q.last[k] = w.last;
+                    q.ncross[k] = w.ncross;
+                    q.nrefl[k] = w.nrefl;
+                    q.nwall[k] = w.nwall;
+                    q.flags[k] = w.status | (coll ? 8 : 0);
+                    q.slot[k] = i;
+                    }
+                } else {
+                    finish(w, coll, e);
+                }
+            }
+        }
+        emit(e, have_tile, 0);
+        // ---- the queued walks, in full warps once half a block of them has
+        // gathered (or once the tiles are done)
+        const int qc = q.count;  // block-uniform: the pushes came before emit's barriers
+        if (qc >= THREADS / 2 || (!have_tile && qc > 0)) {
+            const int take = qc < THREADS ? qc : THREADS;
+            Ended<Real> f;
+            f.active = f.survivor = f.mover = f.exited = false;
+            f.tet = f.c0 = -1;
+            f.es = f.ee = (Real)0;
+            f.mm = 0.0;
+            f.id = 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) f.xe[c] = f.ue[c] = f.us[c] = (Real)0;
+            if ((int)threadIdx.x < take) {
+                const int k = qc - take + threadIdx.x;
+                Walk<Real> w;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    w.x0[c] = q.x0[c][k];
+                    w.u[c] = q.u[c][k];
+                }
+                w.t0 = q.t0[k];
+                w.t_end = q.t_end[k];
+                w.tet = q.tet[k];
+                w.last = q.last[k];
+                w.ncross = q.ncross[k];
+                w.nrefl = q.nrefl[k];
+                w.nwall = q.nwall[k];
+                const int fl = q.flags[k];
+                w.status = fl & 7;
+                const bool coll = fl & 8;
+                const long long i = q.slot[k];
+                // the rest of the particle, read again from its slot
+                f.id = b.id[i];
+                f.c0 = b.cell[i];
+                f.mm = b.m[i];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) f.us[c] = b.u[c][i];
+                if constexpr (KE) {
+                    f.es = b.e[i];
+                    f.ee = q.ee[k];
+                }
+                while (visit<Real, KE>(m, p, step, f.id, w, f.xe, f.ee)) {
+                }
+                finish(w, coll, f);
+            }
+            emit(f, false, take);
         }
     }
-    // ---- counters: one atomic per block and counter (survivors were counted
-    // by their slot reservations)
+    // ---- counters: one atomic per block and counter
     unsigned vals[7] = {c_valid, c_coll, c_exit, c_lost, c_cross, c_wall, c_surv};
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
@@ -936,24 +953,11 @@ void launch_sample_scale(const DevMesh& m, const DevState& s, const DevParams& p
 }
 
 namespace {
-template <class Real, bool KE, int T, int S>
-void track_as(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b, const PartBufRaw& nxt,
-              const PartBufRaw& movers, int blocks, cudaStream_t st) {
-    const int smem = S > 0 ? S * Stage<Real, KE, T>::BYTES : 0;
-    k_track<Real, KE, T, S><<<blocks, T, smem, st>>>(m, s, p, b, nxt, movers);
-}
 template <class Real, bool KE>
 void track_shape(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b, const PartBufRaw& nxt,
                  const PartBufRaw& movers, const TrackShape& sh, int blocks, cudaStream_t st) {
-    if (sh.threads == 256) {
-        if (sh.stages == 2) track_as<Real, KE, 256, 2>(m, s, p, b, nxt, movers, blocks, st);
-        else if (sh.stages == 3) track_as<Real, KE, 256, 3>(m, s, p, b, nxt, movers, blocks, st);
-        else track_as<Real, KE, 256, 0>(m, s, p, b, nxt, movers, blocks, st);
-    } else {
-        if (sh.stages == 2) track_as<Real, KE, 128, 2>(m, s, p, b, nxt, movers, blocks, st);
-        else if (sh.stages == 3) track_as<Real, KE, 128, 3>(m, s, p, b, nxt, movers, blocks, st);
-        else track_as<Real, KE, 128, 0>(m, s, p, b, nxt, movers, blocks, st);
-    }
+    if (sh.threads == 256) k_track<Real, KE, 256><<<blocks, 256, 0, st>>>(m, s, p, b, nxt, movers);
+    else k_track<Real, KE, 128><<<blocks, 128, 0, st>>>(m, s, p, b, nxt, movers);
 }
 }  // namespace
 
@@ -969,39 +973,24 @@ void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const
 }
 
 namespace {
-// Attributes of every tracking shape of one particle type: the dynamic shared
-// memory its stages take, and the preferred carveout; the carveout also for
-// the other particle kernels of that type.
+// The preferred carveout of the particle kernels of one particle type.
 template <class Real, bool KE> cudaError_t configure_type(int carveout) {
     cudaError_t e = cudaSuccess;
-    auto set = [&](auto f, int smem) {
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto set = [&](auto f) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
     };
-    set(k_track<Real, KE, 128, 0>, 0);
-    set(k_track<Real, KE, 128, 2>, 2 * Stage<Real, KE, 128>::BYTES);
-    set(k_track<Real, KE, 128, 3>, 3 * Stage<Real, KE, 128>::BYTES);
-    set(k_track<Real, KE, 256, 0>, 0);
-    set(k_track<Real, KE, 256, 2>, 2 * Stage<Real, KE, 256>::BYTES);
-    set(k_track<Real, KE, 256, 3>, 3 * Stage<Real, KE, 256>::BYTES);
-    set(k_sample_write<Real>, 0);
-    set(k_sample_scale<Real>, 0);
-    set(k_movers<Real>, 0);
+    set(k_track<Real, KE, 128>);
+    set(k_track<Real, KE, 256>);
+    set(k_sample_write<Real>);
+    set(k_sample_scale<Real>);
+    set(k_movers<Real>);
     return e;
 }
 }  // namespace
 
-cudaError_t configure_particle_kernels(const DevParams& p, const TrackShape& sh, int carveout) {
-    (void)sh;
+cudaError_t configure_particle_kernels(const DevParams& p, int carveout) {
     if (p.precision == UGKWP_MIXED) return p.K > 0 ? configure_type<float, true>(carveout) : configure_type<float, false>(carveout);
     return p.K > 0 ? configure_type<double, true>(carveout) : configure_type<double, false>(carveout);
-}
-
-int track_smem_bytes(const DevParams& p, const TrackShape& sh) {
-    if (sh.stages <= 0) return 0;
-    const int rs = p.precision == UGKWP_MIXED ? 4 : 8;
-    const int arrays = 6 + (p.K > 0 ? 1 : 0);
-    return sh.stages * sh.threads * (arrays * rs + 8 + 8 + 4);
 }
 
 void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a, int blocks, cudaStream_t st) {

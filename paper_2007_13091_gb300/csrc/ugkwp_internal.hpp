@@ -18,8 +18,9 @@ enum : int32_t {
     ERRB_FIXED_OVERFLOW = 4,
     ERRB_NONFINITE = 8,
     ERRB_SAMPLE_LIMIT = 16,
-    ERRB_STAGE_WAIT = 32,   // a bulk copy into shared memory did not complete within its wait limit
     ERRB_SORT = 64,         // a cell holds more survivors than its count (sort skipped them)
+    ERRB_CHECK = 128,       // a kernel's own bounds or alignment check failed (the access was skipped;
+                            // CNT_CHECK holds the check and the value)
 };
 
 // Largest tile of the tracking kernel (particles per block and tile); the
@@ -49,6 +50,7 @@ enum : int {
     CNT_RESV = 16,      // mover slots reserved this step
     CNT_TILE = 32,      // next grab of tracking tiles
     CNT_OVF = 48,       // overflow slots (survivors whose bucket is full) taken this step
+    CNT_CHECK = 56,     // the first failed self-check: (check << 48) | value
     CNT_SLOTS = 64,
 };
 // Tiles taken from the tile counter per atomic.
@@ -211,11 +213,9 @@ void launch_sample_count(const DevMesh& m, const DevState& s, const DevParams& p
 void launch_scan(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
 // Grid sizes of the step kernels that loop over their work (any positive
 // value gives the same results; chosen for speed, e.g. by the autotuner).
-// Shape of the tracking kernel: threads (= particles) per block and tile,
-// and tiles staged ahead in shared memory by bulk copies (0: direct loads).
+// Shape of the tracking kernel: threads (= particles) per block and tile.
 struct TrackShape {
     int threads;  // 128 or 256
-    int stages;   // 0, 2 or 3
 };
 struct LaunchCfg {
     int particle_blocks;  // blocks of the sampling, tracking and movers kernels
@@ -233,12 +233,10 @@ void launch_sample_scale(const DevMesh& m, const DevState& s, const DevParams& p
 // movers and their flux added by launch_movers.
 void launch_track(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& b,
                   const PartBufRaw& nxt, const PartBufRaw& movers, const TrackShape& sh, int blocks, cudaStream_t st);
-// Dynamic shared memory of one tracking block of this shape.
-int track_smem_bytes(const DevParams& p, const TrackShape& sh);
-// Kernel attributes of the step's kernels for a launch configuration (dynamic
-// shared memory of the tracking kernel, the common preferred carveout): set
-// outside stream capture, before the configuration's first launch.
-cudaError_t configure_particle_kernels(const DevParams& p, const TrackShape& sh, int carveout);
+// The common preferred shared-memory carveout of the step's kernels (a
+// kernel attribute): set outside stream capture, before the configuration's
+// first launch.
+cudaError_t configure_particle_kernels(const DevParams& p, int carveout);
 cudaError_t configure_wave_kernels(int carveout);
 cudaError_t configure_cell_kernels(int carveout);
 void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,

@@ -64,11 +64,10 @@ SAMPLING = {"maxwell": 0, "energy_matched": 1, "gp1": 2}
 
 class LaunchCfg(ctypes.Structure):
     _fields_ = [("particle_blocks", ctypes.c_int32), ("wave_blocks", ctypes.c_int32),
-                ("track_threads", ctypes.c_int32), ("track_stages", ctypes.c_int32),
-                ("smem_carveout", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("track_threads", ctypes.c_int32), ("smem_carveout", ctypes.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Stats(ctypes.Structure):
@@ -378,13 +377,12 @@ def ugkwp_get_launch_cfg(sim) -> dict:
 
 
 def ugkwp_set_launch_cfg(sim, particle_blocks: int, wave_blocks: int, track_threads: int = None,
-                         track_stages: int = None, smem_carveout: int = None):
+                         smem_carveout: int = None):
     """Set the launch configuration; fields left None keep their current values."""
     cur = ugkwp_get_launch_cfg(sim)
     c = LaunchCfg(int(particle_blocks), int(wave_blocks),
                   int(cur["track_threads"] if track_threads is None else track_threads),
-                  int(cur["track_stages"] if track_stages is None else track_stages),
-                  int(cur["smem_carveout"] if smem_carveout is None else smem_carveout), 0)
+                  int(cur["smem_carveout"] if smem_carveout is None else smem_carveout))
     _check(lib().ugkwp_set_launch_cfg(sim, ctypes.byref(c)))
 
 

@@ -74,33 +74,32 @@ def test_batched_step_matches_oracle():
     b.close()
 
 
-# tracking shapes (threads per tile, staged tiles) and carveouts that must give
-# the results of the default configuration bit for bit
-SHAPES = [(128, 2, -1), (128, 3, 58), (256, 0, -1), (256, 2, 86), (256, 3, 58)]
+# tracking blocks (threads per tile) and carveouts that must give the results
+# of the default configuration bit for bit
+SHAPES = [(128, 58), (256, -1), (256, 86)]
 
 
 @pytest.mark.parametrize("precision,K", [("mixed", 0), ("fp64", 0), ("mixed", 2)])
 def test_launch_cfg_changes_only_speed(precision, K):
-    """Odd grid sizes and every tracking shape (direct loads or tiles staged in
-    shared memory by bulk copies, 128 or 256 particles per tile) and carveout:
+    """Odd grid sizes, tracking tiles of 128 or 256 particles and carveouts:
     the same states bit for bit as the default configuration."""
     import torch
     cfg = wl.cavity(n=6, N_ref=60, precision=precision, order=2, K=K)
     c = _sim(cfg, torch.cuda.Stream())
     c.step(4)
-    for threads, stages, carve in SHAPES:
+    for threads, carve in SHAPES:
         a = _sim(cfg, torch.cuda.Stream())
         d = ugkwp.ugkwp_get_launch_cfg(a.handle)
         assert d["particle_blocks"] > 0 and d["wave_blocks"] > 0
-        ugkwp.ugkwp_set_launch_cfg(a.handle, 7, 3, threads, stages, carve)   # odd grids on purpose
+        ugkwp.ugkwp_set_launch_cfg(a.handle, 7, 3, threads, carve)   # odd grids on purpose
         assert ugkwp.ugkwp_get_launch_cfg(a.handle) == {"particle_blocks": 7, "wave_blocks": 3, "track_threads": threads,
-                                                       "track_stages": stages, "smem_carveout": carve}
+                                                       "smem_carveout": carve}
         a.step(4)
         _assert_same(a, c)
         a.close()
     with pytest.raises(ugkwp.UgkwpError):
         ugkwp.ugkwp_set_launch_cfg(c.handle, 0, 1)
-    for bad in ((8, 8, 64, 0, -1), (8, 8, 128, 1, -1), (8, 8, 128, 2, 101)):
+    for bad in ((8, 8, 64, -1), (8, 8, 128, 101), (8, 8, 128, -2)):
         with pytest.raises(ugkwp.UgkwpError):
             ugkwp.ugkwp_set_launch_cfg(c.handle, *bad)
 
@@ -112,11 +111,11 @@ def test_autotuner_picks_a_candidate_and_keeps_results():
     best = ugkwp.ugkwp_autotune(a.handle, 2)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     assert best["particle_blocks"] % sms == 0 and best["wave_blocks"] % sms == 0
-    assert (best["track_threads"], best["track_stages"]) in {(128, 0), (128, 2), (128, 3), (256, 2)}
+    assert best["track_threads"] in (128, 256) and best["smem_carveout"] in (-1, 58)
     assert ugkwp.ugkwp_get_launch_cfg(a.handle) == best
     n = a.step(0, stats=True)["step"]
-    # 12 shape x carveout trials, then 5 grid trials at order 2; 2 warm-up + 2 timed steps each
-    assert n == 17 * 4
+    # 4 block x carveout trials, then 5 grid trials at order 2; 2 warm-up + 2 timed steps each
+    assert n == 9 * 4
     c.step(n)
     _assert_same(a, c)
 
@@ -124,7 +123,7 @@ def test_autotuner_picks_a_candidate_and_keeps_results():
 def test_batch_autotune_and_member_errors():
     import torch
     cfgs = [wl.shock_tube(nx=40, ny=2, nz=2, precision="mixed", U=0.8, N_ref=100), _members()[1]]
-    for c in cfgs:  # 70 steps: keep the tube physical (N_ref 100, energy-matched sampling)
+    for c in cfgs:  # 38 steps: keep the tube physical (N_ref 100, energy-matched sampling)
         c["params"]["sampling"] = "energy_matched"
     sims = [_sim(c, torch.cuda.Stream()) for c in cfgs]
     b = ugkwp.Batch(sims)

@@ -77,8 +77,8 @@ def compare_step(gsim, osim, check_flux=True):
 
 def run_teacher_forced(cfg, warm_steps, launch=None):
     """One step of each side from the oracle's state after warm_steps steps;
-    launch: (particle_blocks, wave_blocks, track_threads, track_stages,
-    smem_carveout) for the GPU side, or None for the default configuration."""
+    launch: (particle_blocks, wave_blocks, track_threads, smem_carveout) for
+    the GPU side, or None for the default configuration."""
     osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
     osim.step(warm_steps)
     gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
@@ -113,24 +113,24 @@ def test_shock_tube_teacher_forced(precision):
     assert osim.last("counters")["n_collided"] > 0
 
 
-@pytest.mark.parametrize("threads,stages", [(128, 2), (128, 3), (256, 2), (256, 3), (256, 0)])
+@pytest.mark.parametrize("threads", [128, 256])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_tracking_shapes_teacher_forced(precision, threads, stages):
-    """The tracking kernel with its tiles staged in shared memory by bulk copies
-    (or 256-particle tiles with direct loads) against the oracle, on a jittered
-    far-field mesh whose particle count leaves a ragged last tile, with an odd
-    grid so that blocks take unequal numbers of tiles."""
+def test_tracking_tiles_teacher_forced(precision, threads):
+    """The tracking kernel with 128- or 256-particle tiles against the oracle,
+    on a jittered far-field mesh whose particle count leaves a ragged last
+    tile, with an odd grid so that blocks take unequal numbers of tiles and
+    walks that leave their first tet wait in the blocks' queues."""
     cfg = wl.cube_flow(h0=0.5, growth=2.0, N_ref=30, precision=precision, Kn=0.1)
-    gsim, osim = run_teacher_forced(cfg, warm_steps=2, launch=(37, 5, threads, stages, -1))
+    gsim, osim = run_teacher_forced(cfg, warm_steps=2, launch=(37, 5, threads, -1))
     n = osim.state()["id"].size
     assert n % threads != 0 and n > 50 * threads
+    assert osim.last("counters")["n_crossings"] > 0
 
 
-@pytest.mark.parametrize("stages", [0, 2])
-def test_tracking_shapes_internal_energy_teacher_forced(stages):
-    """Staged tiles carry the particles' internal energies (K = 2)."""
+def test_tracking_tiles_internal_energy_teacher_forced():
+    """Queued walks carry the particles' internal energies (K = 2)."""
     cfg = wl.cavity(n=6, N_ref=40, precision="mixed", order=1, K=2)
-    run_teacher_forced(cfg, warm_steps=3, launch=(19, 3, 128, stages, 58))
+    run_teacher_forced(cfg, warm_steps=3, launch=(19, 3, 128, 58))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
