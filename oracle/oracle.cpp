@@ -937,12 +937,35 @@ static Real internal_energy(uint64_t seed, uint64_t id, uint64_t step, uint64_t 
     return e;
 }
 
+// Tracking planes of every tet.  In the mixed mode (binary32 particles, reading)
+// a particle's position is stored relative to the anchor of its tet: vertex 0
+// rounded to the grid 2^-q with q = 22 - r, 2^r bounding the coordinates, so
+// that anchors and their differences are exact in binary32 while offsets stay
+// within about a cell of zero; the planes of a tet are written in its frame.
+// In binary64 the anchors are 0 (global coordinates).
 template <class Real> struct Planes {
     std::vector<Real> n;  // [4*nc][3]
     std::vector<Real> d;  // [4*nc]
     std::vector<int32_t> nb;  // [4*nc]: (tet << 2 | local face) or -1 - face for boundary
+    std::vector<double> A;    // [3*nc] anchor of each tet
+    std::vector<float> Af;    // [3*nc] the same, binary32 (exact)
     void build(const Geom& g) {
         n.resize(12 * (size_t)g.nc); d.resize(4 * (size_t)g.nc); nb.resize(4 * (size_t)g.nc);
+        A.assign(3 * (size_t)g.nc, 0.0);
+        Af.assign(3 * (size_t)g.nc, 0.0f);
+        if (std::is_same<Real, float>::value) {
+            double mx = 0.0;
+            for (double v : g.xyz) mx = std::max(mx, std::fabs(v));
+            int r = 0;
+            while (std::ldexp(1.0, r) <= mx) ++r;
+            const int q = 22 - r;
+            for (int i = 0; i < g.nc; ++i)
+                for (int c = 0; c < 3; ++c) {
+                    const double v = g.xyz[3 * (size_t)g.tet[4 * i] + c];
+                    A[3 * (size_t)i + c] = std::ldexp(std::nearbyint(std::ldexp(v, q)), -q);
+                    Af[3 * (size_t)i + c] = (float)A[3 * (size_t)i + c];
+                }
+        }
         for (int i = 0; i < g.nc; ++i)
             for (int k = 0; k < 4; ++k) {
                 int f = g.tet_face[4 * i + k];
@@ -951,7 +974,11 @@ template <class Real> struct Planes {
                     Real v = (Real)g.f_n[3 * (size_t)f + c];
                     n[12 * (size_t)i + 3 * k + c] = sg > 0 ? v : -v;
                 }
-                Real dv = (Real)g.f_d[f];
+                // the plane offset in the tet's frame: d - n.A in binary64
+                const double* fn = &g.f_n[3 * (size_t)f];
+                const double* Ai = &A[3 * (size_t)i];
+                const double dl = g.f_d[f] - ((fn[0] * Ai[0] + fn[1] * Ai[1]) + fn[2] * Ai[2]);
+                Real dv = (Real)dl;
                 d[4 * (size_t)i + k] = sg > 0 ? dv : -dv;
                 if (g.f_nbr[f] < 0) nb[4 * (size_t)i + k] = -1 - f;
                 else if (sg > 0) nb[4 * (size_t)i + k] = (g.f_nbr[f] << 2) | g.f_nbr_k[f];
@@ -967,7 +994,8 @@ enum { ST_COLL = 1, ST_EXIT = 2, ST_LOST = 4 };
 // follows the ray x0 + u (t - t0); in its tet the exit face is the one with
 // u.n > 0 and the smallest crossing time (ties: lowest local face; the face it
 // entered through, or last reflected from, is skipped).  Interior faces hand
-// the ray to the neighbour unchanged; walls restart it at the hit point.
+// the ray to the neighbour unchanged (in the mixed mode moved into the
+// neighbour's frame); walls restart it at the hit point.
 template <class Real>
 static TrackOut track(const Geom& g, const Planes<Real>& pl, const orc_params& P,
                       Part<Real>& pt, Real t_end, uint64_t step) {
@@ -1007,7 +1035,17 @@ static TrackOut track(const Geom& g, const Planes<Real>& pl, const orc_params& P
             break;
         }
         int code = pl.nb[4 * (size_t)tet + best];
-        if (code >= 0) { tet = code >> 2; last = code & 3; continue; }
+        if (code >= 0) {
+            const int nt = code >> 2;
+            // mixed mode: the segment start moves into the frame of the next tet
+            // (the anchor difference is exact in binary32)
+            if (std::is_same<Real, float>::value)
+                for (int c = 0; c < 3; ++c)
+                    x0[c] = x0[c] + (Real)(pl.Af[3 * (size_t)tet + c] - pl.Af[3 * (size_t)nt + c]);
+            tet = nt;
+            last = code & 3;
+            continue;
+        }
         int f = -1 - code;
         const orc_bc& bc = P.bc[g.f_bc[f]];
         if (bc.type == ORC_BC_INFLOW || bc.type == ORC_BC_OUTFLOW) { o.status |= ST_EXIT; break; }
@@ -1282,8 +1320,10 @@ template <class Real> struct Sim : SimBase {
         return 0;
     }
 
+    // The particle draws of a5 are made in binary64 in both modes (in the mixed
+    // mode the drawn particle is then rounded to binary32, reading).
     void gp_normals(const double* c, uint64_t id, double Xout[3]) const {
-        gp_draw<Real>(P.seed, (uint64_t)step, c, id, Xout);
+        gp_draw<double>(P.seed, (uint64_t)step, c, id, Xout);
     }
 
     // The three normals X of the pair whose first member has id `ida`, by
@@ -1310,7 +1350,9 @@ template <class Real> struct Sim : SimBase {
     }
 
     // a5: the N_sam particles of cell i, in pairs u = U +/- sqrt(RT) X with
-    // X ~ N(0, I) (Box-Muller), x uniform in the tet (needs prepare()).
+    // X ~ N(0, I) (Box-Muller), x uniform in the tet (needs prepare()).  The
+    // draw is binary64 arithmetic in both modes; the mixed mode rounds the
+    // particle to binary32, its position as the offset from the tet's anchor.
     void sample_cell(int i, std::vector<Part<Real>>& out) const {
         const orc_params& p = P;
         const int64_t ns = nsam[i];
@@ -1325,58 +1367,10 @@ template <class Real> struct Sim : SimBase {
             double S = 0.0;
             for (int64_t j = 0; j < ns / 2; ++j) {
                 double X[3];
-                normals_of_pair(p.seed, (uint64_t)step, make_id((uint64_t)step, (uint64_t)i, (uint64_t)(2 * j)), X);
+                Sim<double>::normals_of_pair(p.seed, (uint64_t)step, make_id((uint64_t)step, (uint64_t)i, (uint64_t)(2 * j)), X);
                 S = S + ((X[0] * X[0] + X[1] * X[1]) + X[2] * X[2]);
             }
             if (S > 0.0) sig = sig * std::sqrt((double)(3 * (ns / 2)) / S);
-        }
-        if constexpr (std::is_same<Real, float>::value) {
-            // Mixed precision (reading): the particle arithmetic is binary32,
-            // from U and sqrt(RT) of the cell and the tet's first vertex and
-            // edge vectors rounded to binary32.
-            const float Uf[3] = {(float)pr[i].U[0], (float)pr[i].U[1], (float)pr[i].U[2]};
-            const float sigf = (float)sig;
-            float P0[3], E[3][3];
-            for (int c = 0; c < 3; ++c) {
-                P0[c] = (float)p0[c];
-                E[0][c] = (float)(p1[c] - p0[c]);
-                E[1][c] = (float)(p2[c] - p0[c]);
-                E[2][c] = (float)(p3[c] - p0[c]);
-            }
-            for (int64_t j = 0; j < ns / 2; ++j) {
-                uint64_t ida = make_id((uint64_t)step, (uint64_t)i, (uint64_t)(2 * j));
-                Ctr4 r = draw(p.seed, ida, (uint64_t)step, TAG_SVEL, 0);
-                float X[3], sn, cs;
-                float rad = std::sqrt(-2.0f * log_f(u01_f(r.v[0])));
-                sincos2pi_f(u01_f(r.v[1]), &sn, &cs);
-                X[0] = rad * cs; X[1] = rad * sn;
-                rad = std::sqrt(-2.0f * log_f(u01_f(r.v[2])));
-                sincos2pi_f(u01_f(r.v[3]), &sn, &cs);
-                X[2] = rad * cs;
-                for (int side = 0; side < 2; ++side) {
-                    Part<Real> pt;
-                    pt.id = ida + (uint64_t)side;
-                    pt.cell = i;
-                    pt.m = ms;
-                    if (p.sampling == 2) {
-                        // first-order g_p: every particle drawn on its own
-                        double Xg[3];
-                        gp_normals(&gpc[GP_NC * (size_t)i], pt.id, Xg);
-                        for (int c = 0; c < 3; ++c) pt.u[c] = Uf[c] + sigf * (float)Xg[c];
-                    } else {
-                        for (int c = 0; c < 3; ++c) pt.u[c] = side == 0 ? Uf[c] + sigf * X[c] : Uf[c] - sigf * X[c];
-                    }
-                    if (p.K > 0) pt.e = internal_energy<float>(p.seed, pt.id, (uint64_t)step, TAG_SINT, 0, p.K, sigf);
-                    Ctr4 rp = draw(p.seed, pt.id, (uint64_t)step, TAG_SPOS, 0);
-                    float a = u01_f(rp.v[0]), b = u01_f(rp.v[1]), cc = u01_f(rp.v[2]);
-                    if (a + b > 1.0f) { a = 1.0f - a; b = 1.0f - b; }
-                    if (b + cc > 1.0f) { float tmp = cc; cc = 1.0f - a - b; b = 1.0f - tmp; }
-                    else if (a + b + cc > 1.0f) { float tmp = cc; cc = a + b + cc - 1.0f; a = 1.0f - b - tmp; }
-                    for (int c = 0; c < 3; ++c) pt.x[c] = P0[c] + ((a * E[0][c] + b * E[1][c]) + cc * E[2][c]);
-                    out.push_back(pt);
-                }
-            }
-            return;
         }
         for (int64_t j = 0; j < ns / 2; ++j) {
                 uint64_t ida = make_id((uint64_t)step, (uint64_t)i, (uint64_t)(2 * j));
@@ -1411,7 +1405,8 @@ template <class Real> struct Sim : SimBase {
                     else if (a + b + cc > 1.0) { double tmp = cc; cc = a + b + cc - 1.0; a = 1.0 - b - tmp; }
                     for (int c = 0; c < 3; ++c) {
                         double e1 = p1[c] - p0[c], e2 = p2[c] - p0[c], e3 = p3[c] - p0[c];
-                        pt.x[c] = (Real)(p0[c] + ((a * e1 + b * e2) + cc * e3));
+                        // mixed mode: the offset from the tet's anchor (0 in binary64)
+                        pt.x[c] = (Real)((p0[c] - pl.A[3 * (size_t)i + c]) + ((a * e1 + b * e2) + cc * e3));
                     }
                     out.push_back(pt);
                 }
@@ -1509,7 +1504,10 @@ template <class Real> struct Sim : SimBase {
             id[k] = v[k].id;
             m[k] = v[k].m;
             if (e) e[k] = (double)v[k].e;
-            for (int c = 0; c < 3; ++c) { x[3 * k + c] = (double)v[k].x[c]; u[3 * k + c] = (double)v[k].u[c]; }
+            for (int c = 0; c < 3; ++c) {
+                x[3 * k + c] = pl.A[3 * (size_t)cell + c] + (double)v[k].x[c];
+                u[3 * k + c] = (double)v[k].u[c];
+            }
         }
         return n;
     }
@@ -1520,8 +1518,9 @@ template <class Real> struct Sim : SimBase {
             const auto& pt = parts[k];
             if (id) id[k] = pt.id;
             if (cell) cell[k] = pt.cell;
+            // positions: anchor + offset (exact in binary64)
             for (int c = 0; c < 3; ++c) {
-                if (x) x[c * n + k] = (double)pt.x[c];
+                if (x) x[c * n + k] = pl.A[3 * (size_t)pt.cell + c] + (double)pt.x[c];
                 if (u) u[c * n + k] = (double)pt.u[c];
             }
             if (m) m[k] = pt.m;
@@ -1537,9 +1536,11 @@ template <class Real> struct Sim : SimBase {
             pt.id = id[k]; pt.cell = cell[k]; pt.m = m[k];
             if (pt.cell < 0 || pt.cell >= g.nc) { err = "particle cell out of range"; return false; }
             for (int c = 0; c < 3; ++c) {
-                pt.x[c] = (Real)x[c * n + k];
+                const double xl = x[c * n + k] - pl.A[3 * (size_t)pt.cell + c];
+                pt.x[c] = (Real)xl;
                 pt.u[c] = (Real)u[c * n + k];
-                if ((double)pt.x[c] != x[c * n + k] || (double)pt.u[c] != u[c * n + k]) {
+                if ((double)pt.x[c] != xl || pl.A[3 * (size_t)pt.cell + c] + xl != x[c * n + k] ||
+                    (double)pt.u[c] != u[c * n + k]) {
                     err = "particle state not representable in the particle precision"; return false;
                 }
             }
@@ -1558,7 +1559,10 @@ template <class Real> struct Sim : SimBase {
                   int64_t stp, int32_t* cell_out, int32_t* nc_out) const override {
         Part<Real> pt;
         pt.id = id; pt.cell = cell; pt.m = 1.0;
-        for (int c = 0; c < 3; ++c) { pt.x[c] = (Real)io_x[c]; pt.u[c] = (Real)io_u[c]; }
+        for (int c = 0; c < 3; ++c) {
+            pt.x[c] = (Real)(io_x[c] - pl.A[3 * (size_t)cell + c]);
+            pt.u[c] = (Real)io_u[c];
+        }
         if (io_e) pt.e = (Real)*io_e;
         const Real dtR = (Real)dtv;
         Real t_end = dtR;
@@ -1571,7 +1575,10 @@ template <class Real> struct Sim : SimBase {
             if (tf < dtR) { st |= ST_COLL; t_end = tf; }
         }
         TrackOut o = track<Real>(g, pl, P, pt, t_end, (uint64_t)stp);
-        for (int c = 0; c < 3; ++c) { io_x[c] = (double)pt.x[c]; io_u[c] = (double)pt.u[c]; }
+        for (int c = 0; c < 3; ++c) {
+            io_x[c] = pl.A[3 * (size_t)o.cell + c] + (double)pt.x[c];
+            io_u[c] = (double)pt.u[c];
+        }
         if (io_e) *io_e = (double)pt.e;
         *cell_out = o.cell;
         *nc_out = o.ncross;

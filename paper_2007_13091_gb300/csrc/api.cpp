@@ -33,6 +33,7 @@ struct ugkwp_sim {
     DevState S;
     PartBufRaw A, B;   // A: the current particles (between steps: the survivors); B: the next survivors
     PartBufRaw Mv;     // the step's movers (particles whose counting flux is non-zero)
+    std::vector<double> anchor;  // [3*nc] anchors of the tets (mixed mode; 0 in binary64)
     cudaStream_t stream = nullptr;
     // page-locked host staging of ugkwp_import_state (particle positions and
     // velocities in the particle precision), kept between imports
@@ -136,6 +137,8 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, bool with_e, Carver& c, 
     else M.trk_d = c.take<TrkD>(nc);
     M.face_order = c.take<int32_t>(nf);
     M.vtx_f = c.take<float>(12 * nc);
+    M.anc_f = c.take<float4>(nc);
+    M.anc_d = c.take<double>(3 * nc);
     M.bf_f = c.take<float>(11 * (nbf ? nbf : 1));
     M.lsq_c = c.take<double>(12 * nc);
     M.lsq_dxf = c.take<double>(12 * nc);
@@ -534,7 +537,31 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
             bt2[(size_t)d * nbf + b] = mh.f_t2[3 * (size_t)f + d];
         }
     }
-    // tracking records: planes (+-n, +-d) per local face, neighbour codes
+    // mixed mode: each tet's anchor, vertex 0 rounded to the grid 2^-q with
+    // q = 22 - r (2^r bounds the coordinates): anchors and their differences
+    // are exact in binary32, and a particle's position is stored as its
+    // binary32 offset from the anchor of its tet (binary64: anchors 0)
+    s->anchor.assign(3 * (size_t)nc, 0.0);
+    std::vector<float4> ancf(nc, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+    std::vector<double> ancd(3 * (size_t)nc, 0.0);
+    if (s->real_size == 4) {
+        double mx = 0.0;
+        for (double v : mh.xyz) mx = std::max(mx, std::fabs(v));
+        int r = 0;
+        while (std::ldexp(1.0, r) <= mx) ++r;
+        const int q = 22 - r;
+        for (int i = 0; i < nc; ++i) {
+            double a[3];
+            for (int d = 0; d < 3; ++d) {
+                a[d] = std::ldexp(std::nearbyint(std::ldexp(mh.xyz[3 * (size_t)mh.tet[4 * (size_t)i] + d], q)), -q);
+                s->anchor[3 * (size_t)i + d] = a[d];
+                ancd[(size_t)d * nc + i] = a[d];
+            }
+            ancf[i] = make_float4((float)a[0], (float)a[1], (float)a[2], 0.0f);
+        }
+    }
+    // tracking records: planes (+-n, +-d) per local face (mixed mode: d in the
+    // tet's frame, d - n.A), neighbour codes
     std::vector<TrkF> tf;
     std::vector<TrkD> td;
     if (s->real_size == 4) tf.resize(nc); else td.resize(nc);
@@ -546,7 +573,9 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
             const double* n = &mh.f_n[3 * (size_t)f];
             const double d = mh.f_d[f];
             if (s->real_size == 4) {
-                const float nx = (float)n[0], ny = (float)n[1], nz = (float)n[2], dd = (float)d;
+                const double* Ai = &s->anchor[3 * (size_t)i];
+                const double dl = d - ((n[0] * Ai[0] + n[1] * Ai[1]) + n[2] * Ai[2]);
+                const float nx = (float)n[0], ny = (float)n[1], nz = (float)n[2], dd = (float)dl;
                 tf[i].pl[k] = own ? make_float4(nx, ny, nz, dd) : make_float4(-nx, -ny, -nz, -dd);
             } else {
                 td[i].pl[k] = own ? Dbl4{n[0], n[1], n[2], d} : Dbl4{-n[0], -n[1], -n[2], -d};
@@ -563,7 +592,10 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
         return cudaMemcpyAsync(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice, st);
     };
     cudaError_t ce = cudaSuccess;
-#define UP(dst, src, bytes) if (ce == cudaSuccess) ce = up(dst, src, bytes)
+#define UP(dst, src, bytes)                     \
+    do {                                         \
+        if (ce == cudaSuccess) ce = up(dst, src, bytes); \
+    } while (0)
     UP(s->M.vol, mh.vol.data(), nc * sizeof(double));
     std::vector<double> ivol(nc);
     for (int i = 0; i < nc; ++i) ivol[i] = 1.0 / mh.vol[i];
@@ -572,8 +604,13 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     UP(s->M.vtx, vtx.data(), vtx.size() * sizeof(double));
     UP(s->M.cf, cf.data(), cf.size() * sizeof(int32_t));
     UP(s->M.cfs, cfs.data(), cfs.size() * sizeof(int32_t));
-    if (s->real_size == 4) { UP(s->M.trk_f, tf.data(), tf.size() * sizeof(TrkF)); }
-    else { UP(s->M.trk_d, td.data(), td.size() * sizeof(TrkD)); }
+    if (s->real_size == 4) {
+        UP(s->M.trk_f, tf.data(), tf.size() * sizeof(TrkF));
+    } else {
+        UP(s->M.trk_d, td.data(), td.size() * sizeof(TrkD));
+    }
+    UP(s->M.anc_f, ancf.data(), ancf.size() * sizeof(float4));
+    UP(s->M.anc_d, ancd.data(), ancd.size() * sizeof(double));
     UP(s->M.face_order, forder.data(), nf * sizeof(int32_t));
     UP(s->M.vtx_f, vtxf.data(), vtxf.size() * sizeof(float));
     UP(s->M.bf_f, bff.data(), bff.size() * sizeof(float));
@@ -1016,7 +1053,11 @@ int ugkwp_export_state(ugkwp_sim* s, ugkwp_state* st) {
         if (st->e) st->e[k] = !s->A.e ? 0.0 : rs == 4 ? (double)((const float*)es.data())[i] : ((const double*)es.data())[i];
         for (int d = 0; d < 3; ++d) {
             double xv, uv;
-            if (rs == 4) { xv = ((const float*)xs[d].data())[i]; uv = ((const float*)us[d].data())[i]; }
+            if (rs == 4) {
+                // mixed mode: anchor of the tet + offset, exact in binary64
+                xv = s->anchor[3 * (size_t)cell[i] + d] + (double)((const float*)xs[d].data())[i];
+                uv = ((const float*)us[d].data())[i];
+            }
             else { xv = ((const double*)xs[d].data())[i]; uv = ((const double*)us[d].data())[i]; }
             if (st->x) st->x[d * np + k] = xv;
             if (st->u) st->u[d * np + k] = uv;
@@ -1068,8 +1109,11 @@ int ugkwp_import_state(ugkwp_sim* s, const ugkwp_state* st) {
             for (int d = 0; d < 3; ++d) {
                 const double xv = st->x[d * n + i], uv = st->u[d * n + i];
                 if (rs == 4) {
-                    const float xf = (float)xv, uf = (float)uv;
-                    if ((double)xf != xv || (double)uf != uv) return 4;
+                    // mixed mode: the offset from the anchor of the particle's tet
+                    const double A = s->anchor[3 * (size_t)st->cell[i] + d];
+                    const double xl = xv - A;
+                    const float xf = (float)xl, uf = (float)uv;
+                    if ((double)xf != xl || A + xl != xv || (double)uf != uv) return 4;
                     ((float*)comp(d))[i] = xf;
                     ((float*)comp(3 + d))[i] = uf;
                 } else {

@@ -248,7 +248,8 @@ __global__ void k_cell_update(DevMesh m, DevState s, DevParams p, int32_t* wcell
     // a11: the bucket slots no survivor took are holes
     if (!(s.cnt64[CNT_ERR] & ERRB_CAPACITY)) {
         const int cap = s.wcap[i], fill = s.nleft_next[i];
-        for (int k = fill < cap ? fill : cap; k < cap; ++k) wcell[(size_t)s.woff[i] + k] = -1;
+        if ((long long)s.woff[i] + cap <= p.capacity)
+            for (int k = fill < cap ? fill : cap; k < cap; ++k) wcell[(size_t)s.woff[i] + k] = -1;
     }
     int f[4];
     const int own = m.cfs[i];

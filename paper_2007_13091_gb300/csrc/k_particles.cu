@@ -182,9 +182,9 @@ __global__ void __launch_bounds__(256) k_sample_scale(DevMesh m, DevState s, Dev
     if (ns >= 2) {
         double S = 0.0;
         for (int j = 0; j < ns / 2; ++j) {
-            Real X[3];
-            pair_normals<Real>(make_id(step, cell, 2 * j), step, p.seed, X);
-            const double x0 = (double)X[0], x1 = (double)X[1], x2 = (double)X[2];
+            double X[3];
+            pair_normals<double>(make_id(step, cell, 2 * j), step, p.seed, X);
+            const double x0 = X[0], x1 = X[1], x2 = X[2];
             S = S + ((x0 * x0 + x1 * x1) + x2 * x2);
         }
         if (S > 0.0) sig = sig * sqrt((double)(3 * (ns / 2)) / S);
@@ -214,42 +214,8 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
         const int side = k & 1;
         // the samples follow the current buffer's survivor slots, in cell order
         const long long j = s.cnt64[CNT_N_A] + g;
-        if constexpr (sizeof(Real) == 4) {
-            // mixed mode: binary32 arithmetic from U, sqrt(RT) and the tet's
-            // vertex and edges rounded to binary32
-            const float4 us = s.usig[cell];
-            const unsigned long long ida = make_id(step, cell, k - side);
-            const unsigned long long id = ida + (unsigned long long)side;
-            const bool gp = p.sampling == UGKWP_SAMPLE_GP1;
-            float X[3];
-            if (gp) gp_normals<float>(s.gpc, nc, cell, id, step, p.seed, X);  // every particle on its own
-            else pair_normals<float>(ida, step, p.seed, X);
-            const dm::U4 rp = dm::philox(id, (unsigned long long)step, TAG_SPOS, 0ULL, p.seed, 0ULL);
-            float a = dm::u01f(rp.a), bb = dm::u01f(rp.b), cc = dm::u01f(rp.c);
-            if (a + bb > 1.0f) { a = 1.0f - a; bb = 1.0f - bb; }
-            if (bb + cc > 1.0f) {
-                const float t = cc;
-                cc = 1.0f - a - bb;
-                bb = 1.0f - t;
-            } else if (a + bb + cc > 1.0f) {
-                const float t = cc;
-                cc = a + bb + cc - 1.0f;
-                a = 1.0f - bb - t;
-            }
-            const float U[3] = {us.x, us.y, us.z};
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float P0 = m.vtx_f[(size_t)c * nc + cell];
-                const float E1 = m.vtx_f[(size_t)(3 + c) * nc + cell];
-                const float E2 = m.vtx_f[(size_t)(6 + c) * nc + cell];
-                const float E3 = m.vtx_f[(size_t)(9 + c) * nc + cell];
-                b.x[c][j] = P0 + ((a * E1 + bb * E2) + cc * E3);
-                b.u[c][j] = (gp || side == 0) ? U[c] + us.w * X[c] : U[c] - us.w * X[c];
-            }
-            b.m[j] = s.msam[cell];
-            b.cell[j] = cell;
-            b.id[j] = id;
-            if (p.K > 0) b.e[j] = internal_energy<float>(id, step, TAG_SINT, 0ULL, p.K, us.w, p.seed);
+        if (j >= p.capacity || cell < 0 || cell >= nc) {
+            check_failed(s, 9, (unsigned long long)j);
             continue;
         }
         const double U[3] = {s.prim[nc + cell], s.prim[2 * nc + cell], s.prim[3 * nc + cell]};
@@ -279,7 +245,8 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
             const double E1 = m.vtx[(size_t)(3 + c) * nc + cell] - P0;
             const double E2 = m.vtx[(size_t)(6 + c) * nc + cell] - P0;
             const double E3 = m.vtx[(size_t)(9 + c) * nc + cell] - P0;
-            b.x[c][j] = (Real)(P0 + ((a * E1 + bb * E2) + cc * E3));
+            // the offset from the tet's anchor (the anchor is 0 in binary64)
+            b.x[c][j] = (Real)((P0 - m.anc_d[(size_t)c * nc + cell]) + ((a * E1 + bb * E2) + cc * E3));
             b.u[c][j] = (Real)((gp || side == 0) ? U[c] + sig * X[c] : U[c] - sig * X[c]);
         }
         b.m[j] = s.msam[cell];
@@ -479,7 +446,16 @@ __device__ __forceinline__ bool visit(const DevMesh& m, const DevParams& p, long
     }
     const int code = best == 0 ? nbv.x : best == 1 ? nbv.y : best == 2 ? nbv.z : nbv.w;
     if (code >= 0) {
-        w.tet = code >> 2;
+        const int nt = code >> 2;
+        if constexpr (sizeof(Real) == 4) {
+            // mixed mode: the segment start moves into the next tet's frame
+            // (the anchors' difference is exact in binary32)
+            const float4 a0 = m.anc_f[w.tet], a1 = m.anc_f[nt];
+            w.x0[0] = w.x0[0] + (a0.x - a1.x);
+            w.x0[1] = w.x0[1] + (a0.y - a1.y);
+            w.x0[2] = w.x0[2] + (a0.z - a1.z);
+        }
+        w.tet = nt;
         w.last = code & 3;
         return true;
     }
@@ -909,6 +885,12 @@ __global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams
             const unsigned long long code = mv.id[j];
             c1 = (int)(code >> 1);
             exited = code & 1ULL;
+            // a record outside the mesh is reported and skipped
+            if (c0 < 0 || c0 >= nc || (!exited && (c1 < 0 || c1 >= nc))) {
+                check_failed(s, 8, (unsigned long long)j);
+                c0 = -1;
+                exited = true;
+            }
             const Real es = mv.e ? mv.e[j] : (Real)0, ee = mv.e2 ? mv.e2[j] : (Real)0;
             bool ok = phi_q(us, es, mm, p, q0);
             ok &= phi_q(ue, ee, mm, p, q1);

@@ -111,6 +111,8 @@ struct DevMesh {
     const TrkF* trk_f;       // [nc]
     const TrkD* trk_d;       // [nc]
     const float* vtx_f;      // [12][nc] mixed mode: vertex 0, then edges p_k - p_0 (k = 1..3), binary32
+    const float4* anc_f;     // [nc] mixed mode: anchor of the tet (x, y, z, 0), exact in binary32
+    const double* anc_d;     // [3][nc] the same anchors, binary64 (0 in the binary64 mode)
     const float* bf_f;       // [11][nbf] mixed mode: n, t1, t2, U_w.t1, U_w.t2 of each boundary face, binary32
     // second-order reconstruction (order 2)
     const double* lsq_c;     // [12][nc]: gradient = sum_k c_k (v_k - v_i), c_k at [(3k+d) nc + i]
