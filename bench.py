@@ -47,7 +47,12 @@ TRACK_BYTES_PER_CELL = {"mixed": 80 + 8, "fp64": 144 + 8}
 # launches) on this workload, from the ncu capture summarised in
 # profiles/k_track_k_face_flux_o2_cavity24_mixed.md; set to None whenever the
 # kernel changes until it is captured again
-TRACK_DRAM_BYTES = {"mixed": 962697216 + 980654336 + 28416, "fp64": None}
+TRACK_DRAM_BYTES = {"mixed": None, "fp64": None}
+# bytes the movers' flux kernel reads per mover (start and end velocity, mass,
+# start cell, end cell and exit flag), MIXED / FP64
+MOVER_BYTES = {"mixed": 12 + 12 + 8 + 4 + 8, "fp64": 24 + 24 + 8 + 4 + 8}
+# int64 atomic additions per mover: -phi at the start cell, +phi at the end cell
+MOVER_ATOMICS = 10
 # Binary64 flops per interior face of k_face_flux_o2 (the second-order wave flux):
 # ncu's executed dadd + dmul + 2 dfma per launch divided by the interior faces, on
 # this workload (profiles/); None until captured for the current kernel.
@@ -67,6 +72,28 @@ def guarded(fn):
         return fn()
     except Exception as e:  # noqa: BLE001 - reported, not hidden
         return {"error": f"{type(e).__name__}: {e}"[:300]}
+
+
+def fp64_peak_measured(n=8192, reps=5):
+    """Binary64 throughput of this GPU measured as a cuBLAS DGEMM (2 n^3 flops)
+    timed with CUDA events, best of `reps` (TFLOP/s)."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b
+    torch.cuda.empty_cache()
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
 def peaks():
@@ -430,6 +457,62 @@ def diatomic(device, steps, warmup, launch_cfg):
             "workload": "cavity 24^3, MIXED, order 2, K = 2 (diatomic), 200 spin-up steps"}
 
 
+def shock_tube(device, steps=20, warmup=3, seeds=(1, 1001), oracle_steps=20):
+    """The 3D shock tube at full size (100x4x4 hexes x 6 = 9,600 tets, Sod
+    states, Kn 1e-2, N_ref 50, specular side walls, CFL 0.5, first order,
+    seed 1): `steps` steps in FP64 and in MIXED, device time over the whole
+    run from the initial state (the workload is those 20 steps, so nothing is
+    spun up; `warmup` steps of a separate simulation come first to load the
+    library's kernels and graphs), the per-field relative L2 of MIXED vs FP64
+    after the run with the FP64 seed-to-seed floor, and the CPU oracle over the
+    same `oracle_steps` steps."""
+    import torch
+    from paper_2007_13091_gb300 import ugkwp
+    from paper_2007_13091_gb300 import workloads as wl
+    out = {"workload": "3D shock tube [0,1]x[0,0.04]^2, 100x4x4 hexes x 6 = 9,600 tets, Sod states, Kn 1e-2, "
+                       "N_ref 50, specular side walls, CFL 0.5, first order, seed 1", "steps": steps}
+    fields = {}
+    for precision, seed in (("fp64", seeds[0]), ("mixed", seeds[0]), ("fp64", seeds[1])):
+        cfg = wl.shock_tube(precision=precision, seed=seed)
+        stream = torch.cuda.Stream(device=device)
+        w = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=stream)
+        w.step(warmup)
+        w.sync()
+        w.close()
+        sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=stream)
+        st0 = sim.step(0, stats=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(steps)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        st1 = sim.step(0, stats=True)
+        P = sim.moments(ugkwp.PRIM)
+        fields[(precision, seed)] = {"rho": P[0], "U": P[1:4], "T": P[4], "p": P[0] * P[4]}
+        moves = st1["n_moves_total"] - st0["n_moves_total"]
+        if seed == seeds[0]:
+            out[precision] = {"value": moves / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+                              "cell_steps_per_s": sim.n_cells * steps / (ms * 1e-3),
+                              "particles_per_step": moves / steps}
+        sim.close()
+    ref, mix, other = fields[("fp64", seeds[0])], fields[("mixed", seeds[0])], fields[("fp64", seeds[1])]
+    # velocity relative to the sound speed of the left state (the tube starts at rest)
+    c_left = math.sqrt(5.0 / 3.0)
+
+    def err(x, y):
+        e = {k: float(np.linalg.norm(x[k] - y[k]) / np.linalg.norm(y[k])) for k in ("rho", "T", "p")}
+        e["U"] = float(np.linalg.norm(x["U"] - y["U"]) / (c_left * math.sqrt(y["U"].shape[1])))
+        return e
+    out["field_error"] = {"after_steps": steps, "mixed_vs_fp64": err(mix, ref), "noise_floor_fp64_seed": err(other, ref),
+                          "U_scale": "sound speed of the left state"}
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    out["cpu_baseline"] = guarded(lambda: cpu_oracle_run(wl.shock_tube(precision="fp64", seed=seeds[0]), 0,
+                                                         oracle_steps, "3D shock tube 9,600 tets, FP64, the "
+                                                         f"whole {oracle_steps}-step run from the initial state"))
+    return out
+
+
 def gks_start_up(device, steps=20, warmup=3):
     """Start-up steps of the gas-kinetic scheme (the method without particles,
     Sec. 3.2; the initial fields of the steady cases, Sec. 4.3, 4.4) on the
@@ -524,23 +607,53 @@ def hypersonic(device, which, steps, warmup, gks_steps, spin_up=5, adjoint_K=0, 
     return out
 
 
-def cpu_baseline(steps):
-    """The CPU oracle (single thread) on the same workload: one untimed step
-    samples the particle population, then `steps` timed steps."""
+def host_cores():
+    """Host cores this process may run on (the oracle itself uses one)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count()
+
+
+def cpu_oracle_run(cfg, untimed, steps, sample):
+    """The CPU oracle (single thread) on `cfg`: `untimed` steps, then `steps`
+    timed steps; particle-moves/s and cell-steps/s."""
     import oracle
-    cfg = workload("mixed")
     s = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
-    s.step()
+    if untimed:
+        s.step(untimed)
     moves = 0
     t0 = time.perf_counter()
     for _ in range(steps):
         s.step()
         moves += s.last("counters")["n_tracked"]
     t1 = time.perf_counter()
-    return {"value": moves / (t1 - t0), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"cavity 24^3x6 tets, N_ref 100, MIXED, order {ORDER}: {steps} oracle steps after one sampling step "
-                      f"({moves} particle moves, {t1 - t0:.1f} s)",
-            "cell_steps_per_s": len(cfg["mesh"]["tets"]) * steps / (t1 - t0)}
+    n = len(cfg["mesh"]["tets"])
+    return {"value": moves / (t1 - t0), "unit": UNIT, "cores": 1, "host_cores_available": host_cores(),
+            "kind": "oracle", "sample": f"{sample} ({steps} timed steps, {moves} particle moves, {t1 - t0:.1f} s)",
+            "cell_steps_per_s": n * steps / (t1 - t0), "n_cells": n}
+
+
+def cpu_baseline(steps):
+    """The CPU oracle (single thread) on the bench workload: one untimed step
+    samples the particle population, then `steps` timed steps.  The oracle
+    starts from the initial state, where the cavity holds ~N_ref particles per
+    cell, not from the settled ~2.6 N_ref the GPU line is timed on: its rate
+    is per move, which the population size hardly changes."""
+    cfg = workload("mixed")
+    return cpu_oracle_run(cfg, 1, steps, f"cavity 24^3x6 tets, N_ref 100, MIXED, order {ORDER}: oracle steps after "
+                                         "one sampling step, from the unsettled initial population")
+
+
+def cpu_not_timed(line, start_up):
+    """Why a hypersonic case has no CPU line: one oracle step moves as many
+    particles as the GPU line's step (minutes on one core at the cavity's
+    oracle rate) after hundreds of gas-kinetic start-up steps, which does not
+    fit the bench's few minutes; the oracle's rate per move is the cavity's."""
+    ppm = line.get("particles_per_step") if isinstance(line, dict) else None
+    return {"timed": False, "reason": f"one oracle step moves ~{ppm:.3g} particles after {start_up} gas-kinetic "
+                                      "start-up steps: minutes per step on one core, beyond the bench's few minutes"
+            if ppm else "the GPU line did not run", "cores": 1, "host_cores_available": host_cores()}
 
 
 def run_reference(args, ws, rank):
@@ -565,8 +678,13 @@ def run_reference(args, ws, rank):
             "config": {"workload": "lid-driven cavity 24^3 hexes x 6 = 82944 tets, Kn 0.075, N_ref 100, MIXED",
                        "order": ORDER,
                        "sample": f"{steps} of the requested {args.steps} steps (CPU oracle, single thread)"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "host_cores_available": host_cores(),
+                             "kind": "oracle",
                              "sample": f"{steps} oracle steps after {warm} warm-up step(s), {moves} moves"},
+            "population": "the oracle starts from the initial state (~N_ref particles per cell) and runs only "
+                          f"{warm + steps} steps, while the GPU line is timed on the settled population "
+                          f"(~2.6 N_ref per cell after {SPIN_UP} steps): the rate is per particle move, which "
+                          "the population size hardly changes, but the two lines do not time the same steps",
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -631,6 +749,20 @@ def main():
                             "two k_track launches: the second starts when the wave flux is done) over "
                             f"{args.steps} further steps of the same run (direct launches, wave flux "
                             "overlapping on the second stream)"}
+    # the movers' flux pass (a8): the mover records it reads, and its int64 atomics
+    movers_ms = kms.get("movers", 0.0) / args.steps
+    n_movers = int(st["n_movers"])
+    roof_movers = None
+    if movers_ms > 0.0:
+        mb = MOVER_BYTES[args.precision] * n_movers
+        ach_m = mb / (movers_ms * 1e-3) / 1e9
+        roof_movers = {"kernel": "k_movers (a8: binary64 counting flux of the particles that changed cell, met a "
+                                 "wall or left)", "bound": "hbm", "achieved": ach_m, "peak": peak, "unit": "GB/s",
+                       "frac": ach_m / peak, "peak_kind": f"{peak_kind} HBM copy", "traffic": None,
+                       "algorithmic_bytes_per_launch": mb, "bytes_per_mover": MOVER_BYTES[args.precision],
+                       "movers_per_launch": n_movers, "ms_per_launch": movers_ms,
+                       "int64_atomics_per_s": MOVER_ATOMICS * n_movers / (movers_ms * 1e-3),
+                       "timing": "CUDA events on the library's stream around each launch"}
     roof_flux = None
     if ORDER == 2 and kms.get("flux_o2", 0.0) > 0.0:
         props = torch.cuda.get_device_properties(local)
@@ -640,7 +772,9 @@ def main():
                 sm_mhz = float(json.load(f).get("sm_max_mhz", sm_mhz))
         except OSError:
             pass
-        fp64_peak = props.multi_processor_count * FP64_FMA_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        fp64_nominal = props.multi_processor_count * FP64_FMA_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        fp64_meas = guarded(fp64_peak_measured)
+        fp64_peak = fp64_meas if isinstance(fp64_meas, float) else fp64_nominal
         flux_ms = kms["flux_o2"] / args.steps
         n_if = sim.n_faces - sim.n_bfaces
         flops = FLUX_O2_FLOPS_PER_FACE * n_if if FLUX_O2_FLOPS_PER_FACE else None
@@ -649,15 +783,21 @@ def main():
                                "first-order flux of the boundary faces)",
                      "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": ach / fp64_peak if ach else None,
-                     "peak_kind": f"FP64 nominal: {props.multi_processor_count} SMs x {FP64_FMA_LANES_PER_SM} "
-                                  f"FMA lanes/clk x 2 flop x {sm_mhz:.0f} MHz",
+                     "peak_kind": ("measured: cuBLAS DGEMM 8192^3 on this GPU (binary64 runs on the FMA pipes; "
+                                   "there is no FP64 entry in the measured peaks)"
+                                   if isinstance(fp64_meas, float) else "FP64 nominal (the DGEMM probe failed)"),
+                     "fp64_nominal_tflops": fp64_nominal,
+                     "fp64_nominal_kind": f"{props.multi_processor_count} SMs x {FP64_FMA_LANES_PER_SM} "
+                                          f"FMA lanes/clk x 2 flop x {sm_mhz:.0f} MHz",
+                     "frac_of_nominal": ach / fp64_nominal if ach else None,
                      "traffic": FLUX_O2_DRAM_BYTES, "traffic_unit": "bytes per launch (ncu)",
                      "flops_per_face": FLUX_O2_FLOPS_PER_FACE, "faces_per_launch": n_if,
                      "ms_per_launch": flux_ms,
                      "timing": "CUDA events on the library's wave stream around each launch, overlapping the "
                                "particle kernels"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "ms_per_step": ms_max / args.steps, "field_error": None, "mixed_over_fp64": None,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 particles / f64 cells / int64 flux" if args.precision == "mixed" else "f64",
            "data": "synthetic",
            "config": {"workload": "lid-driven cavity 24^3 hexes x 6 = 82944 tets, argon-like VHS gas, Kn 0.075, "
@@ -668,7 +808,7 @@ def main():
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "cell_steps_per_s": cell_steps,
            "roofline": roof_track,
-           "roofline_track": roof_track, "roofline_flux_o2": roof_flux,
+           "roofline_track": roof_track, "roofline_movers": roof_movers, "roofline_flux_o2": roof_flux,
            "kernels_ms_per_step": {k: v / args.steps for k, v in kms.items()},
            "step_launch": "two-step CUDA graphs replayed on the caller's stream",
            "launch_cfg": launch_cfg,
@@ -700,10 +840,15 @@ def main():
         out["gks_start_up"] = guarded(lambda: gks_start_up(device))
         out["gp1_sampling"] = guarded(lambda: gp1_sampling(device, args.steps, args.warmup, launch_cfg))
         out["diatomic"] = guarded(lambda: diatomic(device, args.steps, args.warmup, launch_cfg))
+        out["shock_tube"] = guarded(lambda: shock_tube(device))
         out["cube_ma4"] = guarded(lambda: hypersonic(device, "cube", 10, 3, 300))
         out["blunt_vehicle"] = guarded(lambda: hypersonic(device, "vehicle", 5, 3, 1200, spin_up=2, adjoint_K=16,
                                                           kernel_times=False))
         out["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+        out["cpu_baseline_by_config"] = {
+            "cavity": out["cpu_baseline"],
+            "shock_tube": out["shock_tube"].get("cpu_baseline") if isinstance(out["shock_tube"], dict) else None,
+            "cube_ma4": cpu_not_timed(out["cube_ma4"], 300), "blunt_vehicle": cpu_not_timed(out["blunt_vehicle"], 1200)}
     elif rank == 0:
         out["e2e"] = None
         out["cpu_baseline"] = None

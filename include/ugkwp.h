@@ -163,6 +163,8 @@ typedef struct {
     int64_t n_tracked;           /* particles moved in the last step (old + sampled) */
     int64_t n_sampled, n_collided, n_exited, n_lost, n_crossings, n_wall_hits;
     int64_t n_moves_total;       /* particle moves summed over every step since init */
+    int64_t n_movers;            /* particles of the last step whose counting flux is not zero (they
+                                  * left their start cell, met a wall or left the domain) */
 } ugkwp_stats;
 
 /* Host-side image of the simulation state for checkpoint/restart and for

@@ -892,6 +892,7 @@ int ugkwp_step(ugkwp_sim* s, int32_t n_steps, ugkwp_stats* st) {
         st->n_sampled = h[CNT_SAMPLED]; st->n_collided = h[CNT_COLLIDED]; st->n_exited = h[CNT_EXITED];
         st->n_lost = h[CNT_LOST]; st->n_crossings = h[CNT_CROSSINGS]; st->n_wall_hits = h[CNT_WALL];
         st->n_moves_total = h[CNT_MOVES];
+        st->n_movers = h[CNT_RESV];
         return read_error(s);
     }
     return UGKWP_OK;

@@ -74,7 +74,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("dt", ctypes.c_double), ("step", ctypes.c_int64),
                 ("n_particles", ctypes.c_int64), ("n_tracked", ctypes.c_int64), ("n_sampled", ctypes.c_int64),
                 ("n_collided", ctypes.c_int64), ("n_exited", ctypes.c_int64), ("n_lost", ctypes.c_int64),
-                ("n_crossings", ctypes.c_int64), ("n_wall_hits", ctypes.c_int64), ("n_moves_total", ctypes.c_int64)]
+                ("n_crossings", ctypes.c_int64), ("n_wall_hits", ctypes.c_int64), ("n_moves_total", ctypes.c_int64),
+                ("n_movers", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
