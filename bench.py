@@ -261,6 +261,8 @@ def field_error(horizons, device):
     the same initial state and seed, and the FP64 seed-to-seed noise floor."""
     from paper_2007_13091_gb300 import ugkwp
 
+    first = {}
+
     def prims(precision, seed):
         cfg = workload(precision, seed)
         sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device)
@@ -271,6 +273,9 @@ def field_error(horizons, device):
             P = sim.moments(ugkwp.PRIM)
             rho, U, T = P[0], P[1:4], P[4]
             out[h] = {"rho": rho, "U": U, "T": T, "p": rho * T}
+            if h == 1 and seed == 2:
+                st = sim.state()
+                first[precision] = (st["id"], st["cell"])
         sim.close()
         return out
 
@@ -288,7 +293,20 @@ def field_error(horizons, device):
         floor = {k: rel(c[h][k], b[h][k]) for k in ("rho", "T", "p")}
         floor["U"] = uerr(c[h]["U"], b[h]["U"])
         res[str(h)] = {"mixed_vs_fp64": err, "noise_floor_fp64_seed": floor}
-    return {"horizons": list(horizons), "by_horizon": res}
+    out = {"horizons": list(horizons), "by_horizon": res}
+    if "mixed" in first and "fp64" in first:
+        # the discrete decisions behind the error: after one step from the same
+        # state and seed, particles whose cell differs between the two
+        # precisions, and particles that exist in one only (t_f or exit decisions)
+        (ia, ca), (ib, cb) = first["mixed"], first["fp64"]
+        common, ja, jb = np.intersect1d(ia, ib, assume_unique=True, return_indices=True)
+        moved = int((ca[ja] != cb[jb]).sum())
+        out["after_1_step_particles"] = {"fp64": int(ib.size), "mixed": int(ia.size), "common_ids": int(common.size),
+                                         "cell_differs": moved, "only_in_fp64": int(ib.size - common.size),
+                                         "only_in_mixed": int(ia.size - common.size),
+                                         "differing_per_particle": (moved + (ib.size - common.size) +
+                                                                    (ia.size - common.size)) / max(ib.size, 1)}
+    return out
 
 
 def field_error_averaged(device, spin=300, avg=600):
@@ -457,7 +475,7 @@ def diatomic(device, steps, warmup, launch_cfg):
             "workload": "cavity 24^3, MIXED, order 2, K = 2 (diatomic), 200 spin-up steps"}
 
 
-def shock_tube(device, steps=20, warmup=3, seeds=(1, 1001), oracle_steps=20):
+def shock_tube(device, steps=20, warmup=3, seeds=(1, 1002), oracle_steps=20):
     """The 3D shock tube at full size (100x4x4 hexes x 6 = 9,600 tets, Sod
     states, Kn 1e-2, N_ref 50, specular side walls, CFL 0.5, first order,
     seed 1): `steps` steps in FP64 and in MIXED, device time over the whole

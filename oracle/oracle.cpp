@@ -1320,10 +1320,65 @@ template <class Real> struct Sim : SimBase {
         return 0;
     }
 
-    // The particle draws of a5 are made in binary64 in both modes (in the mixed
-    // mode the drawn particle is then rounded to binary32, reading).
+    // First-order g_p draws in the particle precision, widened.
     void gp_normals(const double* c, uint64_t id, double Xout[3]) const {
-        gp_draw<double>(P.seed, (uint64_t)step, c, id, Xout);
+        gp_draw<Real>(P.seed, (uint64_t)step, c, id, Xout);
+    }
+
+    // a5 positions (reading): three uniforms N_k 2^-48 with N_k odd and below
+    // 2^48 (the top 47 bits of a Philox word, doubled, plus one), folded from
+    // the cube to the prism to the tet (Rocchini and Cignoni, J. Graphics Tools
+    // 5(4), 2000) on the integers N_k, so that both modes place the particle
+    // with the same exact barycentric weights.
+    static void fold_weights(const Ctr4& r, int64_t N[3]) {
+        const int64_t one = (int64_t)1 << 48;
+        int64_t a = (int64_t)(((r.v[0] >> 17) << 1) | 1), b = (int64_t)(((r.v[1] >> 17) << 1) | 1);
+        int64_t c = (int64_t)(((r.v[2] >> 17) << 1) | 1);
+        if (a + b > one) { a = one - a; b = one - b; }
+        if (b + c > one) { int64_t t = c; c = one - a - b; b = one - t; }
+        else if (a + b + c > one) { int64_t t = c; c = a + b + c - one; a = one - b - t; }
+        N[0] = a; N[1] = b; N[2] = c;
+    }
+
+    // a binary64 value as the binary32 pair (value rounded, remainder rounded)
+    static void split32(double v, float& hi, float& lo) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    }
+
+    // Knuth's exact sum: s + e equals a + b
+    static void exact_sum(float a, float b, float& s, float& e) {
+        s = a + b;
+        float v = s - a;
+        e = (a - (s - v)) + (b - v);
+    }
+
+    // Mixed mode: one coordinate of the position offset from the tet's anchor,
+    // (p0 - A) + ((w1 e1 + w2 e2) + w3 e3) carried on binary32 pairs and
+    // rounded to binary32 at the end.  A product w e keeps its high parts'
+    // rounding error exactly (fused multiply-add) plus the two cross terms;
+    // each sum keeps its exact error in the low part.
+    static float offset_on_pairs(double p0A, const double e[3], const int64_t N[3]) {
+        float ph[3], pe[3];
+        for (int k = 0; k < 3; ++k) {
+            const float wh = (float)(N[k] >> 24) * 0x1p-24f, wl = (float)(N[k] & 0xffffff) * 0x1p-48f;
+            float eh, el;
+            split32(e[k], eh, el);
+            ph[k] = wh * eh;
+            pe[k] = std::fmaf(wh, eh, -ph[k]) + (wh * el + wl * eh);
+        }
+        float s, r;
+        exact_sum(ph[0], ph[1], s, r);
+        float low = r + (pe[0] + pe[1]);
+        float s2, r2;
+        exact_sum(s, ph[2], s2, r2);
+        low = r2 + (low + pe[2]);
+        float ah, al;
+        split32(p0A, ah, al);
+        float s3, r3;
+        exact_sum(ah, s2, s3, r3);
+        low = r3 + (low + al);
+        return s3 + low;
     }
 
     // The three normals X of the pair whose first member has id `ida`, by
@@ -1351,8 +1406,9 @@ template <class Real> struct Sim : SimBase {
 
     // a5: the N_sam particles of cell i, in pairs u = U +/- sqrt(RT) X with
     // X ~ N(0, I) (Box-Muller), x uniform in the tet (needs prepare()).  The
-    // draw is binary64 arithmetic in both modes; the mixed mode rounds the
-    // particle to binary32, its position as the offset from the tet's anchor.
+    // binary64 mode draws in binary64.  The mixed mode (reading) draws the
+    // velocities in binary32 from U and sqrt(RT) rounded to binary32, and the
+    // position offset from the tet's anchor on binary32 pairs, rounded once.
     void sample_cell(int i, std::vector<Part<Real>>& out) const {
         const orc_params& p = P;
         const int64_t ns = nsam[i];
@@ -1360,56 +1416,59 @@ template <class Real> struct Sim : SimBase {
         double sig = std::sqrt(p.R * pr[i].T);
         const double *p0 = &g.xyz[3 * (size_t)g.tet[4 * i]], *p1 = &g.xyz[3 * (size_t)g.tet[4 * i + 1]];
         const double *p2 = &g.xyz[3 * (size_t)g.tet[4 * i + 2]], *p3 = &g.xyz[3 * (size_t)g.tet[4 * i + 3]];
+        constexpr bool mixed = std::is_same<Real, float>::value;
         // Energy-matched sampling (option): one factor s for all pairs of the
         // cell so that the sampled thermal energy sum_j m (s sqrt(RT))^2 |X_j|^2
-        // equals N_sam m (3/2) R T exactly, i.e. s^2 sum_j |X_j|^2 = 3 N_sam / 2.
+        // equals N_sam m (3/2) R T exactly, i.e. s^2 sum_j |X_j|^2 = 3 N_sam / 2
+        // (the X of the particle precision, summed in binary64).
         if (p.sampling == 1 && ns >= 2) {
             double S = 0.0;
             for (int64_t j = 0; j < ns / 2; ++j) {
                 double X[3];
-                Sim<double>::normals_of_pair(p.seed, (uint64_t)step, make_id((uint64_t)step, (uint64_t)i, (uint64_t)(2 * j)), X);
+                normals_of_pair(p.seed, (uint64_t)step, make_id((uint64_t)step, (uint64_t)i, (uint64_t)(2 * j)), X);
                 S = S + ((X[0] * X[0] + X[1] * X[1]) + X[2] * X[2]);
             }
             if (S > 0.0) sig = sig * std::sqrt((double)(3 * (ns / 2)) / S);
         }
+        const float Uf[3] = {(float)pr[i].U[0], (float)pr[i].U[1], (float)pr[i].U[2]};
+        const float sigf = (float)sig;
         for (int64_t j = 0; j < ns / 2; ++j) {
-                uint64_t ida = make_id((uint64_t)step, (uint64_t)i, (uint64_t)(2 * j));
-                Ctr4 r = draw(p.seed, ida, (uint64_t)step, TAG_SVEL, 0);
-                double X[3], sn, cs;
-                double rad = std::sqrt(-2.0 * log_d(u01_d(r.v[0])));
-                sincos2pi_d(u01_d(r.v[1]), &sn, &cs);
-                X[0] = rad * cs; X[1] = rad * sn;
-                rad = std::sqrt(-2.0 * log_d(u01_d(r.v[2])));
-                sincos2pi_d(u01_d(r.v[3]), &sn, &cs);
-                X[2] = rad * cs;
-                for (int side = 0; side < 2; ++side) {
-                    Part<Real> pt;
-                    pt.id = ida + (uint64_t)side;
-                    pt.cell = i;
-                    pt.m = ms;
-                    if (p.sampling == 2) {
-                        double Xg[3];
-                        gp_normals(&gpc[GP_NC * (size_t)i], pt.id, Xg);
-                        for (int c = 0; c < 3; ++c) pt.u[c] = (Real)(pr[i].U[c] + sig * Xg[c]);
+            uint64_t ida = make_id((uint64_t)step, (uint64_t)i, (uint64_t)(2 * j));
+            double X[3];
+            normals_of_pair(p.seed, (uint64_t)step, ida, X);
+            for (int side = 0; side < 2; ++side) {
+                Part<Real> pt;
+                pt.id = ida + (uint64_t)side;
+                pt.cell = i;
+                pt.m = ms;
+                double Xs[3] = {X[0], X[1], X[2]};
+                if (p.sampling == 2) gp_normals(&gpc[GP_NC * (size_t)i], pt.id, Xs);  // every particle on its own
+                const bool plus = p.sampling == 2 || side == 0;
+                for (int c = 0; c < 3; ++c) {
+                    if constexpr (mixed) {
+                        const float xs = (float)Xs[c];
+                        pt.u[c] = plus ? Uf[c] + sigf * xs : Uf[c] - sigf * xs;
                     } else {
-                        for (int c = 0; c < 3; ++c)
-                            pt.u[c] = (Real)(side == 0 ? pr[i].U[c] + sig * X[c] : pr[i].U[c] - sig * X[c]);
+                        pt.u[c] = plus ? pr[i].U[c] + sig * Xs[c] : pr[i].U[c] - sig * Xs[c];
                     }
-                    if (p.K > 0) pt.e = (Real)internal_energy<double>(p.seed, pt.id, (uint64_t)step, TAG_SINT, 0, p.K, sig);
-                    // Uniform point in the tet: cube -> prism -> tet folding
-                    // (Rocchini and Cignoni, J. Graphics Tools 5(4), 2000).
-                    Ctr4 rp = draw(p.seed, pt.id, (uint64_t)step, TAG_SPOS, 0);
-                    double a = u01_d(rp.v[0]), b = u01_d(rp.v[1]), cc = u01_d(rp.v[2]);
-                    if (a + b > 1.0) { a = 1.0 - a; b = 1.0 - b; }
-                    if (b + cc > 1.0) { double tmp = cc; cc = 1.0 - a - b; b = 1.0 - tmp; }
-                    else if (a + b + cc > 1.0) { double tmp = cc; cc = a + b + cc - 1.0; a = 1.0 - b - tmp; }
-                    for (int c = 0; c < 3; ++c) {
-                        double e1 = p1[c] - p0[c], e2 = p2[c] - p0[c], e3 = p3[c] - p0[c];
-                        // mixed mode: the offset from the tet's anchor (0 in binary64)
-                        pt.x[c] = (Real)((p0[c] - pl.A[3 * (size_t)i + c]) + ((a * e1 + b * e2) + cc * e3));
-                    }
-                    out.push_back(pt);
                 }
+                if (p.K > 0) {
+                    if constexpr (mixed) pt.e = internal_energy<float>(p.seed, pt.id, (uint64_t)step, TAG_SINT, 0, p.K, sigf);
+                    else pt.e = internal_energy<double>(p.seed, pt.id, (uint64_t)step, TAG_SINT, 0, p.K, sig);
+                }
+                int64_t N[3];
+                fold_weights(draw(p.seed, pt.id, (uint64_t)step, TAG_SPOS, 0), N);
+                for (int c = 0; c < 3; ++c) {
+                    const double e[3] = {p1[c] - p0[c], p2[c] - p0[c], p3[c] - p0[c]};
+                    if constexpr (mixed) {
+                        pt.x[c] = offset_on_pairs(p0[c] - pl.A[3 * (size_t)i + c], e, N);
+                    } else {
+                        const double a = (double)N[0] * 0x1p-48, b = (double)N[1] * 0x1p-48, cc = (double)N[2] * 0x1p-48;
+                        pt.x[c] = p0[c] + ((a * e[0] + b * e[1]) + cc * e[2]);
+                    }
+                }
+                out.push_back(pt);
+            }
         }
     }
 

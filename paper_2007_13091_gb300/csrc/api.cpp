@@ -136,9 +136,7 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, bool with_e, Carver& c, 
     if (rs == 4) M.trk_f = c.take<TrkF>(nc);
     else M.trk_d = c.take<TrkD>(nc);
     M.face_order = c.take<int32_t>(nf);
-    M.vtx_f = c.take<float>(12 * nc);
-    M.anc_f = c.take<float4>(nc);
-    M.anc_d = c.take<double>(3 * nc);
+    M.smp_f = c.take<float>(24 * nc);
     M.bf_f = c.take<float>(11 * (nbf ? nbf : 1));
     M.lsq_c = c.take<double>(12 * nc);
     M.lsq_dxf = c.take<double>(12 * nc);
@@ -504,17 +502,8 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     for (int type = 1; type <= 4; ++type)
         for (int f = 0; f < nf; ++f)
             if (mh.f_nbr[f] < 0 && p->bc[mh.f_tag[f]].type == type) forder.push_back(f);
-    // binary32 images for the mixed mode: tet vertex 0 and edges (double
-    // differences rounded once), boundary-face frames and U_w.t (Sec. 2.4 (b), (e))
-    std::vector<float> vtxf(12 * (size_t)nc), bff(11 * (size_t)std::max(nbf, 1), 0.0f);
-    for (int i = 0; i < nc; ++i) {
-        const double* p0 = &mh.xyz[3 * (size_t)mh.tet[4 * (size_t)i]];
-        for (int d = 0; d < 3; ++d) vtxf[(size_t)d * nc + i] = (float)p0[d];
-        for (int k = 1; k < 4; ++k) {
-            const double* pk = &mh.xyz[3 * (size_t)mh.tet[4 * (size_t)i + k]];
-            for (int d = 0; d < 3; ++d) vtxf[(size_t)(3 * k + d) * nc + i] = (float)(pk[d] - p0[d]);
-        }
-    }
+    // binary32 images for the mixed mode: boundary-face frames and U_w.t (Sec. 2.4 (e))
+    std::vector<float> bff(11 * (size_t)std::max(nbf, 1), 0.0f);
     for (int b = 0; b < nbf; ++b) {
         const int f = mh.face_of_bf[b];
         const double* t1 = &mh.f_t1[3 * (size_t)f];
@@ -543,7 +532,6 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     // binary32 offset from the anchor of its tet (binary64: anchors 0)
     s->anchor.assign(3 * (size_t)nc, 0.0);
     std::vector<float4> ancf(nc, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
-    std::vector<double> ancd(3 * (size_t)nc, 0.0);
     if (s->real_size == 4) {
         double mx = 0.0;
         for (double v : mh.xyz) mx = std::max(mx, std::fabs(v));
@@ -555,9 +543,27 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
             for (int d = 0; d < 3; ++d) {
                 a[d] = std::ldexp(std::nearbyint(std::ldexp(mh.xyz[3 * (size_t)mh.tet[4 * (size_t)i] + d], q)), -q);
                 s->anchor[3 * (size_t)i + d] = a[d];
-                ancd[(size_t)d * nc + i] = a[d];
             }
             ancf[i] = make_float4((float)a[0], (float)a[1], (float)a[2], 0.0f);
+        }
+    }
+    // mixed-mode sampling frame (Sec. 2.4 (b)): vertex 0 minus the anchor and
+    // the edges p_k - p_0, binary64 values each split into a binary32 pair
+    // (high = the value rounded, low = the rest rounded)
+    std::vector<float> smpf;
+    if (s->real_size == 4) {
+        smpf.assign(24 * (size_t)nc, 0.0f);
+        auto put = [&](int c, int j, int i, double v) {
+            const float h = (float)v;
+            smpf[(size_t)(8 * c + j) * nc + i] = h;
+            smpf[(size_t)(8 * c + j + 1) * nc + i] = (float)(v - (double)h);
+        };
+        for (int i = 0; i < nc; ++i) {
+            const double* p0 = &mh.xyz[3 * (size_t)mh.tet[4 * (size_t)i]];
+            for (int c = 0; c < 3; ++c) {
+                put(c, 0, i, p0[c] - s->anchor[3 * (size_t)i + c]);
+                for (int k = 1; k < 4; ++k) put(c, 2 * k, i, mh.xyz[3 * (size_t)mh.tet[4 * (size_t)i + k] + c] - p0[c]);
+            }
         }
     }
     // tracking records: planes (+-n, +-d) per local face (mixed mode: d in the
@@ -585,7 +591,18 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
             else nbv[k] = (mh.f_own[f] << 2) | mh.f_own_k[f];
         }
         const int4 nb4 = make_int4(nbv[0], nbv[1], nbv[2], nbv[3]);
-        if (s->real_size == 4) tf[i].nb = nb4; else td[i].nb = nb4;
+        if (s->real_size == 4) {
+            tf[i].nb = nb4;
+            // anchor differences to the neighbours (exact in binary32)
+            for (int k = 0; k < 4; ++k) {
+                const float4 a0 = ancf[i], a1 = nbv[k] >= 0 ? ancf[nbv[k] >> 2] : ancf[i];
+                tf[i].da[3 * k] = a0.x - a1.x;
+                tf[i].da[3 * k + 1] = a0.y - a1.y;
+                tf[i].da[3 * k + 2] = a0.z - a1.z;
+            }
+        } else {
+            td[i].nb = nb4;
+        }
     }
     cudaStream_t st = s->stream;
     auto up = [&](const void* dst, const void* src, size_t bytes) {
@@ -609,10 +626,8 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     } else {
         UP(s->M.trk_d, td.data(), td.size() * sizeof(TrkD));
     }
-    UP(s->M.anc_f, ancf.data(), ancf.size() * sizeof(float4));
-    UP(s->M.anc_d, ancd.data(), ancd.size() * sizeof(double));
     UP(s->M.face_order, forder.data(), nf * sizeof(int32_t));
-    UP(s->M.vtx_f, vtxf.data(), vtxf.size() * sizeof(float));
+    UP(s->M.smp_f, smpf.data(), smpf.size() * sizeof(float));
     UP(s->M.bf_f, bff.data(), bff.size() * sizeof(float));
     UP(s->M.lsq_c, lsq_c.data(), lsq_c.size() * sizeof(double));
     UP(s->M.lsq_dxf, lsq_dxf.data(), lsq_dxf.size() * sizeof(double));

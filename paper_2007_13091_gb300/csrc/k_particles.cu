@@ -182,15 +182,69 @@ __global__ void __launch_bounds__(256) k_sample_scale(DevMesh m, DevState s, Dev
     if (ns >= 2) {
         double S = 0.0;
         for (int j = 0; j < ns / 2; ++j) {
-            double X[3];
-            pair_normals<double>(make_id(step, cell, 2 * j), step, p.seed, X);
-            const double x0 = X[0], x1 = X[1], x2 = X[2];
+            Real X[3];
+            pair_normals<Real>(make_id(step, cell, 2 * j), step, p.seed, X);
+            const double x0 = (double)X[0], x1 = (double)X[1], x2 = (double)X[2];
             S = S + ((x0 * x0 + x1 * x1) + x2 * x2);
         }
         if (S > 0.0) sig = sig * sqrt((double)(3 * (ns / 2)) / S);
     }
     s.sig[cell] = sig;
     if constexpr (sizeof(Real) == 4) s.usig[cell].w = (float)sig;
+}
+
+// a5 positions: a uniform point in the tet from three uniforms folded cube ->
+// prism -> tet (Rocchini & Cignoni, J. Graphics Tools 5(4), 2000).  The
+// uniforms are odd multiples of 2^-48 (47 bits of one Philox draw each) and
+// the folding runs on their integer numerators, so both precisions start from
+// the same exact barycentric weights w_k = N_k 2^-48.
+__device__ __forceinline__ void tet_weights(const dm::U4& r, long long N[3]) {
+    constexpr long long ONE = 1LL << 48;
+    long long a = (long long)(((r.a >> 17) << 1) | 1ULL), b = (long long)(((r.b >> 17) << 1) | 1ULL),
+              c = (long long)(((r.c >> 17) << 1) | 1ULL);
+    if (a + b > ONE) { a = ONE - a; b = ONE - b; }
+    if (b + c > ONE) {
+        const long long t = c;
+        c = ONE - a - b;
+        b = ONE - t;
+    } else if (a + b + c > ONE) {
+        const long long t = c;
+        c = a + b + c - ONE;
+        a = ONE - b - t;
+    }
+    N[0] = a; N[1] = b; N[2] = c;
+}
+
+// Error-free sum of two binary32 numbers: s + e = a + b exactly (Knuth).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Mixed-mode position coordinate: (p0 - A) + ((w1 E1 + w2 E2) + w3 E3) in
+// binary32 pairs (high + low, about 44 bits), then rounded to binary32.  f
+// points at the coordinate's 8 table entries (stride nc): p0 - A, E1, E2, E3
+// as (high, low).  Each product keeps the exact error of its high parts (FMA)
+// and the two cross terms; the sums carry their exact errors in the low part.
+__device__ __forceinline__ float ff_position(const float* f, int nc, const float wh[3], const float wl[3]) {
+    float p[3], e[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float eh = f[(size_t)(2 + 2 * k) * nc], el = f[(size_t)(3 + 2 * k) * nc];
+        p[k] = wh[k] * eh;
+        e[k] = __fmaf_rn(wh[k], eh, -p[k]) + (wh[k] * el + wl[k] * eh);
+    }
+    float s1, r1;
+    two_sum(p[0], p[1], s1, r1);
+    float lo = r1 + (e[0] + e[1]);
+    float s2, r2;
+    two_sum(s1, p[2], s2, r2);
+    lo = r2 + (lo + e[2]);
+    float s3, r3;
+    two_sum(f[0], s2, s3, r3);
+    lo = r3 + (lo + f[nc]);
+    return s3 + lo;
 }
 
 template <class Real>
@@ -218,41 +272,54 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
             check_failed(s, 9, (unsigned long long)j);
             continue;
         }
-        const double U[3] = {s.prim[nc + cell], s.prim[2 * nc + cell], s.prim[3 * nc + cell]};
-        const double sig = p.sampling == UGKWP_SAMPLE_ENERGY_MATCHED ? s.sig[cell] : sqrt(p.R * s.prim[4 * nc + cell]);
         const unsigned long long ida = make_id(step, cell, k - side);
         const unsigned long long id = ida + (unsigned long long)side;
         const bool gp = p.sampling == UGKWP_SAMPLE_GP1;
-        double X[3];
-        if (gp) gp_normals<double>(s.gpc, nc, cell, id, step, p.seed, X);
-        else pair_normals<double>(ida, step, p.seed, X);
-        const dm::U4 rp = dm::philox(id, (unsigned long long)step, TAG_SPOS, 0ULL, p.seed, 0ULL);
-        double a = dm::u01d(rp.a), bb = dm::u01d(rp.b), cc = dm::u01d(rp.c);
-        // cube -> prism -> tet folding of a uniform point (Rocchini & Cignoni 2000)
-        if (a + bb > 1.0) { a = 1.0 - a; bb = 1.0 - bb; }
-        if (bb + cc > 1.0) {
-            const double t = cc;
-            cc = 1.0 - a - bb;
-            bb = 1.0 - t;
-        } else if (a + bb + cc > 1.0) {
-            const double t = cc;
-            cc = a + bb + cc - 1.0;
-            a = 1.0 - bb - t;
-        }
+        long long N[3];
+        tet_weights(dm::philox(id, (unsigned long long)step, TAG_SPOS, 0ULL, p.seed, 0ULL), N);
+        if constexpr (sizeof(Real) == 4) {
+            // mixed mode: velocities in binary32 from U and the spread rounded
+            // to binary32; the position offset from the tet's anchor in
+            // binary32 pairs, rounded once
+            const float4 us = s.usig[cell];
+            float X[3];
+            if (gp) gp_normals<float>(s.gpc, nc, cell, id, step, p.seed, X);  // every particle on its own
+            else pair_normals<float>(ida, step, p.seed, X);
+            float wh[3], wl[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const double P0 = m.vtx[(size_t)c * nc + cell];
-            const double E1 = m.vtx[(size_t)(3 + c) * nc + cell] - P0;
-            const double E2 = m.vtx[(size_t)(6 + c) * nc + cell] - P0;
-            const double E3 = m.vtx[(size_t)(9 + c) * nc + cell] - P0;
-            // the offset from the tet's anchor (the anchor is 0 in binary64)
-            b.x[c][j] = (Real)((P0 - m.anc_d[(size_t)c * nc + cell]) + ((a * E1 + bb * E2) + cc * E3));
-            b.u[c][j] = (Real)((gp || side == 0) ? U[c] + sig * X[c] : U[c] - sig * X[c]);
+            for (int q = 0; q < 3; ++q) {
+                wh[q] = (float)(N[q] >> 24) * 0x1p-24f;
+                wl[q] = (float)(N[q] & 0xffffffLL) * 0x1p-48f;
+            }
+            const float U[3] = {us.x, us.y, us.z};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                b.x[c][j] = ff_position(m.smp_f + (size_t)(8 * c) * nc + cell, nc, wh, wl);
+                b.u[c][j] = (gp || side == 0) ? U[c] + us.w * X[c] : U[c] - us.w * X[c];
+            }
+            if (p.K > 0) b.e[j] = internal_energy<float>(id, step, TAG_SINT, 0ULL, p.K, us.w, p.seed);
+        } else {
+            const double U[3] = {s.prim[nc + cell], s.prim[2 * nc + cell], s.prim[3 * nc + cell]};
+            const double sig =
+                p.sampling == UGKWP_SAMPLE_ENERGY_MATCHED ? s.sig[cell] : sqrt(p.R * s.prim[4 * nc + cell]);
+            double X[3];
+            if (gp) gp_normals<double>(s.gpc, nc, cell, id, step, p.seed, X);
+            else pair_normals<double>(ida, step, p.seed, X);
+            const double a = (double)N[0] * 0x1p-48, bb = (double)N[1] * 0x1p-48, cc = (double)N[2] * 0x1p-48;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double P0 = m.vtx[(size_t)c * nc + cell];
+                const double E1 = m.vtx[(size_t)(3 + c) * nc + cell] - P0;
+                const double E2 = m.vtx[(size_t)(6 + c) * nc + cell] - P0;
+                const double E3 = m.vtx[(size_t)(9 + c) * nc + cell] - P0;
+                b.x[c][j] = P0 + ((a * E1 + bb * E2) + cc * E3);
+                b.u[c][j] = (gp || side == 0) ? U[c] + sig * X[c] : U[c] - sig * X[c];
+            }
+            if (p.K > 0) b.e[j] = internal_energy<double>(id, step, TAG_SINT, 0ULL, p.K, sig, p.seed);
         }
         b.m[j] = s.msam[cell];
         b.cell[j] = cell;
         b.id[j] = id;
-        if (p.K > 0) b.e[j] = (Real)internal_energy<double>(id, step, TAG_SINT, 0ULL, p.K, sig, p.seed);
     }
 }
 
@@ -449,11 +516,12 @@ __device__ __forceinline__ bool visit(const DevMesh& m, const DevParams& p, long
         const int nt = code >> 2;
         if constexpr (sizeof(Real) == 4) {
             // mixed mode: the segment start moves into the next tet's frame
-            // (the anchors' difference is exact in binary32)
-            const float4 a0 = m.anc_f[w.tet], a1 = m.anc_f[nt];
-            w.x0[0] = w.x0[0] + (a0.x - a1.x);
-            w.x0[1] = w.x0[1] + (a0.y - a1.y);
-            w.x0[2] = w.x0[2] + (a0.z - a1.z);
+            // (the anchors' difference, exact in binary32, sits in the
+            // record's line loaded for the planes)
+            const float* da = m.trk_f[w.tet].da + 3 * best;
+            w.x0[0] = w.x0[0] + da[0];
+            w.x0[1] = w.x0[1] + da[1];
+            w.x0[2] = w.x0[2] + da[2];
         }
         w.tet = nt;
         w.last = code & 3;
@@ -858,6 +926,48 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_track(DevMesh m, De
 // Counting flux of the listed movers: -phi(u_start) at the start cell and, unless
 // the particle left the domain, +phi(u_end) at the end cell (full warps of
 // binary64 work, kept out of the tracking kernel).
+// Sum of the int64 x over the lanes with pred set, exact modulo 2^64, by
+// 32-bit warp reductions of three parts (22, 22 and 20 signed bits): 32
+// lanes' part sums stay below 2^27 in magnitude, so none wraps.
+__device__ __forceinline__ unsigned long long warp_sum_i64(bool pred, long long x) {
+    const unsigned long long v = pred ? (unsigned long long)x : 0ULL;
+    const unsigned s0 = __reduce_add_sync(FULL, (unsigned)(v & 0x3fffffULL));
+    const unsigned s1 = __reduce_add_sync(FULL, (unsigned)((v >> 22) & 0x3fffffULL));
+    const unsigned s2 = __reduce_add_sync(FULL, (unsigned)(int)((long long)v >> 44));
+    return (unsigned long long)s0 + ((unsigned long long)s1 << 22) +
+           ((unsigned long long)(long long)(int)s2 << 44);
+}
+
+// Adds (or, with neg, subtracts) q[0..4] of every lane with key >= 0 to
+// pflux[q nc + key].  Lanes with equal keys are summed first and one of them
+// adds the sum -- one atomic per distinct cell and quantity -- unless the warp
+// holds more than GROUP_MAX distinct keys, where each lane adds its own.
+// Integer sums: the result does not depend on the grouping.
+constexpr int GROUP_MAX = 8;
+__device__ __forceinline__ void add_grouped(int key, const long long (&q)[5], bool neg, unsigned long long* pflux,
+                                            int nc, int lane) {
+    const unsigned grp = __match_any_sync(FULL, key);
+    unsigned leaders = __ballot_sync(FULL, key >= 0 && (__ffs(grp) - 1) == lane);
+    if (__popc(leaders) > GROUP_MAX) {
+        if (key >= 0) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c)
+                atomicAdd(&pflux[(size_t)c * nc + key], neg ? 0ULL - (unsigned long long)q[c] : (unsigned long long)q[c]);
+        }
+        return;
+    }
+    while (leaders) {
+        const int l = __ffs(leaders) - 1;
+        leaders &= leaders - 1u;
+        const bool mine = (grp >> l) & 1u;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const unsigned long long sum = warp_sum_i64(mine, q[c]);
+            if (lane == l) atomicAdd(&pflux[(size_t)c * nc + key], neg ? 0ULL - sum : sum);
+        }
+    }
+}
+
 template <class Real>
 __global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams p, PartBufRaw ar) {
     if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
@@ -866,9 +976,9 @@ __global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams
     const int nc = m.nc;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
-    // whole warps per iteration: the start-cell sums are reduced over runs of
-    // equal start cells within the warp (the list is ordered by start cell
-    // within each tracking tile), one atomic per run and quantity
+    // whole warps per iteration: the movers of a warp come from one tracking
+    // tile, whose particles sit in one or a few cells after the step's sort,
+    // so their start cells and end cells repeat within the warp
     for (long long j0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); j0 < n; j0 += stride) {
         const long long j = j0 + lane;
         const bool valid = j < n;
@@ -896,27 +1006,11 @@ __global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams
             ok &= phi_q(ue, ee, mm, p, q1);
             if (!ok) set_err(s, ERRB_FIXED_OVERFLOW);
         }
-        const int prev = __shfl_up_sync(FULL, c0, 1);
-        const bool head = lane == 0 || prev != c0;
-        const unsigned heads = __ballot_sync(FULL, head);
-        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
-        const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            long long v = -q0[q];
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const long long o = __shfl_up_sync(FULL, v, d);
-                if (lane - d >= start) v += o;
-            }
-            if (tail && c0 >= 0)
-                atomicAdd(reinterpret_cast<unsigned long long*>(&s.pflux[(size_t)q * nc + c0]), (unsigned long long)v);
-        }
-        if (valid && !exited) {
-#pragma unroll
-            for (int q = 0; q < 5; ++q)
-                atomicAdd(reinterpret_cast<unsigned long long*>(&s.pflux[(size_t)q * nc + c1]), (unsigned long long)q1[q]);
-        }
+        // -phi at the start cell of every record, +phi at the end cell of
+        // the ones still inside
+        unsigned long long* pf = reinterpret_cast<unsigned long long*>(s.pflux);
+        add_grouped(c0, q0, true, pf, nc, lane);
+        add_grouped(valid && !exited ? c1 : -1, q1, false, pf, nc, lane);
     }
 }
 

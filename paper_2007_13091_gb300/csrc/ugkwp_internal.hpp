@@ -86,10 +86,15 @@ struct DevParams {
 };
 
 // Tracking record of one tet: outward face planes (n, d) and neighbour codes
-// (tet << 2 | local face in the neighbour, or -1 - boundary-face index).
-struct __align__(16) TrkF {
+// (tet << 2 | local face in the neighbour, or -1 - boundary-face index).  The
+// binary32 record (mixed mode, positions relative to the tet's anchor) adds,
+// per local face k, the anchor of this tet minus the anchor of the neighbour
+// across k at da[3k..3k+2] (exact in binary32; 0 at boundary faces): one
+// 128-byte line per tet.
+struct __align__(128) TrkF {
     float4 pl[4];
     int4 nb;
+    float da[12];
 };
 struct __align__(16) Dbl4 {
     double x, y, z, w;
@@ -110,9 +115,9 @@ struct DevMesh {
     const int32_t* cfs;      // [nc] bit k set if the cell owns local face k
     const TrkF* trk_f;       // [nc]
     const TrkD* trk_d;       // [nc]
-    const float* vtx_f;      // [12][nc] mixed mode: vertex 0, then edges p_k - p_0 (k = 1..3), binary32
-    const float4* anc_f;     // [nc] mixed mode: anchor of the tet (x, y, z, 0), exact in binary32
-    const double* anc_d;     // [3][nc] the same anchors, binary64 (0 in the binary64 mode)
+    const float* smp_f;      // [24][nc] mixed mode: for coordinate c at [(8c + j) nc + i], j = 0, 1: vertex 0
+                             // minus the tet's anchor, j = 2k, 2k + 1 (k = 1..3): edge p_k - p_0, each
+                             // binary64 value split into a binary32 pair (high, low)
     const float* bf_f;       // [11][nbf] mixed mode: n, t1, t2, U_w.t1, U_w.t2 of each boundary face, binary32
     // second-order reconstruction (order 2)
     const double* lsq_c;     // [12][nc]: gradient = sum_k c_k (v_k - v_i), c_k at [(3k+d) nc + i]

@@ -256,3 +256,45 @@ def test_energy_matched_sampling_keeps_a_rarefied_box_physical():
         return n
     assert run("maxwell", 60) < 60
     assert run("energy_matched", 100) == 100
+
+
+def _anchors(nodes, tets):
+    """Mixed-mode anchors: vertex 0 of each tet on the grid 2^-q, q = 22 - r,
+    2^r the smallest power of two above the largest coordinate magnitude."""
+    r = 0
+    while 2.0 ** r <= np.abs(nodes).max():
+        r += 1
+    q = 22 - r
+    return np.ldexp(np.rint(np.ldexp(nodes[tets[:, 0]], q)), -q)
+
+
+def test_mixed_positions_are_binary64_positions_rounded():
+    """The mixed mode places a sampled particle on binary32 pairs: its offset
+    from the tet's anchor must be the binary64 mode's position of the same
+    particle (same id, same weights) minus the anchor, rounded to binary32 --
+    exactly for all but a few particles in a million (the pairs carry ~44
+    bits), and never more than one binary32 ulp away."""
+    out = {}
+    for precision in ("fp64", "mixed"):
+        cfg = wl.cavity(n=6, N_ref=60, precision=precision, seed=11)
+        s = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
+        s.prepare()
+        xs, ids = [], []
+        for c in range(len(cfg["mesh"]["tets"])):
+            d = s.sample_cell(c)
+            xs.append(d["x"])
+            ids.append(d["id"])
+        out[precision] = (np.concatenate(ids), np.concatenate(xs, axis=1))
+    ia, xa = out["fp64"]
+    ib, xb = out["mixed"]
+    np.testing.assert_array_equal(ia, ib)
+    cell = ((ia.astype(np.int64) >> 16) & 0xFFFFFF).astype(np.int64)
+    A = _anchors(cfg["mesh"]["nodes"], cfg["mesh"]["tets"])[cell].T
+    off32 = (xb - A).astype(np.float32)
+    assert np.array_equal((xb - A), off32.astype(np.float64))  # the stored offset is binary32
+    want = (xa - A).astype(np.float32)  # binary64 position, offset rounded once
+    same = off32 == want
+    assert same.mean() > 1 - 1e-5, same.mean()
+    ulp = np.spacing(np.abs(want))
+    assert np.all(np.abs(off32.astype(np.float64) - want.astype(np.float64)) <= ulp)
+    assert xa.shape[1] > 20000
