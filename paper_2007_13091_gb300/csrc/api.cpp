@@ -183,8 +183,8 @@ void layout(const MeshHost& mh, int64_t cap, size_t rs, bool with_e, Carver& c, 
     S.dt = c.take<double>(1);
     S.cnt64 = c.take<int64_t>(CNT_SLOTS);
     // each particle array holds the capacity rounded up to whole tiles of the
-    // tracking kernel (TRACK_TILE_MAX particles), so that a tile's bulk copies
-    // into shared memory stay inside the array
+    // tracking kernel (TRACK_TILE_MAX particles), so that a tile's loads of
+    // its whole slots stay inside the array
     const size_t capt = ((size_t)cap + TRACK_TILE_MAX - 1) / TRACK_TILE_MAX * TRACK_TILE_MAX;
     for (PartBufRaw* pb : {&A, &B, &Mv}) {
         for (int d = 0; d < 3; ++d) pb->x[d] = c.take<char>(rs * capt);

@@ -454,6 +454,7 @@ __device__ __forceinline__ bool fixed_of_mass(double m, int e, long long& q) {
 struct TileQueue {
     long long next = 0, end = 0;
 };
+
 __device__ __forceinline__ long long next_tile(TileQueue& q, int64_t* ctr, int T) {
     if (q.next == q.end) {
         q.next = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(ctr), 1ULL) * TILE_GRAB;
@@ -794,18 +795,25 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_track(DevMesh m, De
         for (int c = 0; c < 3; ++c) e.xe[c] = e.ue[c] = e.us[c] = (Real)0;
         if (have_tile) {
             const long long i = bb + threadIdx.x;
-            // the slot's start cell; -1 marks a hole of a survivor bucket
-            const int c0 = i < n ? b.cell[i] : -1;
-            if (c0 >= 0) {
-                Walk<Real> w;
-                e.id = b.id[i];
+            // the whole slot is read at once (one round trip; the arrays hold
+            // whole tiles, so slots past n are inside them and ignored); the
+            // slot's start cell -1 marks a hole of a survivor bucket
+            Walk<Real> w;
+            const int cell_i = b.cell[i];
+            const unsigned long long id_i = b.id[i];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    w.x0[c] = b.x[c][i];
-                    w.u[c] = b.u[c][i];
-                }
-                e.mm = b.m[i];
-                if constexpr (KE) e.es = b.e[i];
+            for (int c = 0; c < 3; ++c) {
+                w.x0[c] = b.x[c][i];
+                w.u[c] = b.u[c][i];
+            }
+            const double m_i = b.m[i];
+            Real e_i = (Real)0;
+            if constexpr (KE) e_i = b.e[i];
+            const int c0 = i < n ? cell_i : -1;
+            if (c0 >= 0) {
+                e.id = id_i;
+                e.mm = m_i;
+                e.es = e_i;
                 e.ee = e.es;
                 e.c0 = c0;
 #pragma unroll
@@ -923,50 +931,17 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_track(DevMesh m, De
     }
 }
 
-// Counting flux of the listed movers: -phi(u_start) at the start cell and, unless
-// the particle left the domain, +phi(u_end) at the end cell (full warps of
-// binary64 work, kept out of the tracking kernel).
-// Sum of the int64 x over the lanes with pred set, exact modulo 2^64, by
-// 32-bit warp reductions of three parts (22, 22 and 20 signed bits): 32
-// lanes' part sums stay below 2^27 in magnitude, so none wraps.
-__device__ __forceinline__ unsigned long long warp_sum_i64(bool pred, long long x) {
-    const unsigned long long v = pred ? (unsigned long long)x : 0ULL;
-    const unsigned s0 = __reduce_add_sync(FULL, (unsigned)(v & 0x3fffffULL));
-    const unsigned s1 = __reduce_add_sync(FULL, (unsigned)((v >> 22) & 0x3fffffULL));
-    const unsigned s2 = __reduce_add_sync(FULL, (unsigned)(int)((long long)v >> 44));
-    return (unsigned long long)s0 + ((unsigned long long)s1 << 22) +
-           ((unsigned long long)(long long)(int)s2 << 44);
+// Same bits (a particle's velocity and internal energy are unchanged unless it
+// met a wall).
+__device__ __forceinline__ bool same_bits(float a, float b) { return __float_as_uint(a) == __float_as_uint(b); }
+__device__ __forceinline__ bool same_bits(double a, double b) {
+    return __double_as_longlong(a) == __double_as_longlong(b);
 }
 
-// Adds (or, with neg, subtracts) q[0..4] of every lane with key >= 0 to
-// pflux[q nc + key].  Lanes with equal keys are summed first and one of them
-// adds the sum -- one atomic per distinct cell and quantity -- unless the warp
-// holds more than GROUP_MAX distinct keys, where each lane adds its own.
-// Integer sums: the result does not depend on the grouping.
-constexpr int GROUP_MAX = 8;
-__device__ __forceinline__ void add_grouped(int key, const long long (&q)[5], bool neg, unsigned long long* pflux,
-                                            int nc, int lane) {
-    const unsigned grp = __match_any_sync(FULL, key);
-    unsigned leaders = __ballot_sync(FULL, key >= 0 && (__ffs(grp) - 1) == lane);
-    if (__popc(leaders) > GROUP_MAX) {
-        if (key >= 0) {
-#pragma unroll
-            for (int c = 0; c < 5; ++c)
-                atomicAdd(&pflux[(size_t)c * nc + key], neg ? 0ULL - (unsigned long long)q[c] : (unsigned long long)q[c]);
-        }
-        return;
-    }
-    while (leaders) {
-        const int l = __ffs(leaders) - 1;
-        leaders &= leaders - 1u;
-        const bool mine = (grp >> l) & 1u;
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-            const unsigned long long sum = warp_sum_i64(mine, q[c]);
-            if (lane == l) atomicAdd(&pflux[(size_t)c * nc + key], neg ? 0ULL - sum : sum);
-        }
-    }
-}
+// Counting flux of the listed movers: -phi(u_start) at the start cell and, unless
+// the particle left the domain, +phi(u_end) at the end cell (full warps of
+// binary64 work, kept out of the tracking kernel).  phi(u_end) is phi(u_start)
+// for the movers that met no wall.
 
 template <class Real>
 __global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams p, PartBufRaw ar) {
@@ -974,20 +949,25 @@ __global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams
     const PartView<Real> mv = view<Real>(ar);
     const long long n = s.cnt64[CNT_RESV];
     const int nc = m.nc;
-    const long long stride = (long long)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
-    // whole warps per iteration: the movers of a warp come from one tracking
-    // tile, whose particles sit in one or a few cells after the step's sort,
-    // so their start cells and end cells repeat within the warp
-    for (long long j0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); j0 < n; j0 += stride) {
-        const long long j = j0 + lane;
+    unsigned long long* pf = reinterpret_cast<unsigned long long*>(s.pflux);
+    // movers whose end velocity differs from their start velocity (they met
+    // a wall): their end phi is taken after the block's pass, packed into
+    // whole warps, since binary64 work costs a warp its full issue time
+    __shared__ int wall_j[256];
+    __shared__ int n_wall;
+    for (long long base = (long long)blockIdx.x * 256; base < n; base += (long long)gridDim.x * 256) {
+        if (threadIdx.x == 0) n_wall = 0;
+        __syncthreads();
+        const long long j = base + threadIdx.x;
         const bool valid = j < n;
-        Real us[3] = {(Real)0, (Real)0, (Real)0}, ue[3] = {(Real)0, (Real)0, (Real)0};
+        Real us[3] = {(Real)0, (Real)0, (Real)0};
         double mm = 0.0;
         int c0 = -1, c1 = -1;
         bool exited = true;
-        long long q0[5] = {0, 0, 0, 0, 0}, q1[5] = {0, 0, 0, 0, 0};
+        long long q0[5] = {0, 0, 0, 0, 0};
         if (valid) {
+            Real ue[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) { us[c] = mv.x[c][j]; ue[c] = mv.u[c][j]; }
             mm = mv.m[j];
@@ -1002,15 +982,49 @@ __global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams
                 exited = true;
             }
             const Real es = mv.e ? mv.e[j] : (Real)0, ee = mv.e2 ? mv.e2[j] : (Real)0;
-            bool ok = phi_q(us, es, mm, p, q0);
-            ok &= phi_q(ue, ee, mm, p, q1);
-            if (!ok) set_err(s, ERRB_FIXED_OVERFLOW);
+            if (!phi_q(us, es, mm, p, q0)) set_err(s, ERRB_FIXED_OVERFLOW);
+            const bool same = same_bits(us[0], ue[0]) && same_bits(us[1], ue[1]) && same_bits(us[2], ue[2]) &&
+                              same_bits(es, ee);
+            if (!exited && !same) wall_j[atomicAdd(&n_wall, 1)] = threadIdx.x;
+            if (!exited && same) {
+                // +phi at the end cell: the start's phi
+#pragma unroll
+                for (int q = 0; q < 5; ++q) atomicAdd(&pf[(size_t)q * nc + c1], (unsigned long long)q0[q]);
+            }
         }
-        // -phi at the start cell of every record, +phi at the end cell of
-        // the ones still inside
-        unsigned long long* pf = reinterpret_cast<unsigned long long*>(s.pflux);
-        add_grouped(c0, q0, true, pf, nc, lane);
-        add_grouped(valid && !exited ? c1 : -1, q1, false, pf, nc, lane);
+        // -phi at the start cell, summed over runs of equal start cells within
+        // the warp (the list is ordered by start cell within each tracking
+        // tile), one atomic per run and quantity
+        const int prev = __shfl_up_sync(FULL, c0, 1);
+        const bool head = lane == 0 || prev != c0;
+        const unsigned heads = __ballot_sync(FULL, head);
+        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+        const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            long long v = -q0[q];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const long long o = __shfl_up_sync(FULL, v, d);
+                if (lane - d >= start) v += o;
+            }
+            if (tail && c0 >= 0) atomicAdd(&pf[(size_t)q * nc + c0], (unsigned long long)v);
+        }
+        __syncthreads();
+        // the block's wall movers: +phi(u_end) at the end cell
+        for (int t = threadIdx.x; t < n_wall; t += 256) {
+            const long long jw = base + wall_j[t];
+            Real ue[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ue[c] = mv.u[c][jw];
+            const Real ee = mv.e2 ? mv.e2[jw] : (Real)0;
+            long long q1[5];
+            if (!phi_q(ue, ee, mv.m[jw], p, q1)) set_err(s, ERRB_FIXED_OVERFLOW);
+            const int cw = (int)(mv.id[jw] >> 1);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) atomicAdd(&pf[(size_t)q * nc + cw], (unsigned long long)q1[q]);
+        }
+        __syncthreads();
     }
 }
 

@@ -450,16 +450,19 @@ def test_graph_replay_matches_direct_launches():
 def test_cavity_full_size_teacher_forced(precision):
     """The bench workload at full size (24^3 x 6 = 82,944 tets, ~8.4e6 particles,
     second-order reconstruction) on a side stream as the bench runs it: one step from the oracle's state
-    after its sampling step (graph replay equals direct launches, tested above)."""
+    after its sampling step (graph replay equals direct launches, tested above), taken three times
+    from the same state (the buffers alternate, so each reads memory the previous one wrote)."""
     import torch
     cfg = wl.cavity(n=24, N_ref=100, precision=precision, order=2)
     osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
     osim.step(1)
+    st = osim.state()
     gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], stream=torch.cuda.Stream())
-    gsim.set_state(osim.state())
     osim.step(1)
-    gsim.step(1)
-    compare_step(gsim, osim)
+    for _ in range(3):
+        gsim.set_state(st)
+        gsim.step(1)
+        compare_step(gsim, osim)
     assert osim.sizes()["n_particles"] > 8_000_000
 
 
