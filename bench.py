@@ -562,6 +562,169 @@ def gks_start_up(device, steps=20, warmup=3):
 
 
 def hypersonic(device, which, steps, warmup, gks_steps, spin_up=5, adjoint_K=0, kernel_times=True):
+    """The hypersonic configurations at full size, MIXED, first order, with the
+    paper's particle setting N_min = N_ref (Sec. 4.3, 4.4) and energy-matched
+    sampling: Ma 4 past the unit cube (1,152,912 tets, Kn 0.1, N_ref 200) or
+    Ma 8 past the blunt vehicle (2,770,032 tets, Kn 1e-3, T_w = 3 T_inf,
+    N_ref 100).  Each starts with `gks_steps` gas-kinetic steps with local
+    time steps from the free stream (the start-up of the steady cases), then
+    takes `spin_up` steps of the method and times `steps` more like the main
+    line.  With adjoint_K > 0 each functional (drag and wall heat flux of the
+    body, theta = the free stream and the wall) gets an adjoint call of
+    adjoint_K steps on a simulation of its own, right after its own start-up.
+
+    With N_ref particles per cell the method runs about 140 steps on the cube
+    and about 50 on the vehicle after the start-up before some cell's pressure
+    falls through zero (the base region behind the cube, the bow shock ahead
+    of the nose), so the cube times 100 steps after 20 and the vehicle 5
+    after 2, and each vehicle adjoint call (46 steps: the far field, 44 tets
+    from the body, reaches the functional after 46) starts from a fresh
+    start-up."""
+    import torch
+    from paper_2007_13091_gb300 import ugkwp
+    from paper_2007_13091_gb300 import workloads as wl
+
+    def config():
+        cfg = wl.cube_flow() if which == "cube" else wl.blunt_vehicle()
+        cfg["params"]["sampling"] = "energy_matched"
+        cfg["params"]["N_min"] = cfg["params"]["N_ref"]
+        return cfg
+
+    def started(cfg, stream):
+        sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.gks_steps(gks_steps, local_dt=True)
+        b.record(stream)
+        b.synchronize()
+        return sim, a.elapsed_time(b)
+
+    t0 = time.perf_counter()
+    cfg = config()
+    stream = torch.cuda.Stream(device=device)
+    out = {"workload": cfg["name"], "n_cells": len(cfg["mesh"]["tets"]), "N_ref": cfg["params"]["N_ref"],
+           "N_min": cfg["params"]["N_min"], "Kn": cfg["params"]["Kn"], "sampling": cfg["params"]["sampling"],
+           "setup_s": time.perf_counter() - t0}
+    sim, ms = started(cfg, stream)
+    n = sim.n_cells
+    sim.sync()
+    W = sim.moments(ugkwp.W)
+    U = W[1:4] / W[0]
+    p = (W[4] - 0.5 * W[0] * (U * U).sum(0)) / 1.5
+    out["gks_start_up"] = {"steps": gks_steps, "ms_per_step": ms / gks_steps,
+                           "cell_steps_per_s": n * gks_steps / (ms * 1e-3),
+                           "rho_min": float(W[0].min()), "p_min": float(p.min())}
+    sim.step(spin_up)
+    ms, moves, launches, kms, st = time_steps(sim, steps, warmup, 1, timing=kernel_times)
+    out.update({"value": moves / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+                "spin_up_steps": spin_up, "warmup_steps": warmup,
+                "method_steps_after_start_up": spin_up + warmup + steps + (steps if kernel_times else 0),
+                "cell_steps_per_s": n * steps / (ms * 1e-3), "particles_per_step": moves / steps})
+    if kms:
+        kms.pop("_moves", None)
+        out["kernels_ms_per_step"] = {k: v / steps for k, v in kms.items()}
+    sim.close()
+    if adjoint_K:
+        adj = {}
+        for functional, name in ((0, "drag"), (1, "wall_heat_flux")):
+            sim, _ = started(config(), stream)
+            t1 = time.perf_counter()
+            r = sim.adjoint(functional, adjoint_K, [2])
+            adj[name] = {"J_and_grad": [float(v) for v in r], "ms_per_call": 1e3 * (time.perf_counter() - t1)}
+            sim.close()
+        out["adjoint"] = {"steps": adjoint_K, "theta": "(rho_inf, U_inf, T_w) = (1, 8 sqrt(5/3), 3)",
+                          "grad_order": "dJ/drho_inf, dJ/dU_inf, dJ/dT_w",
+                          "cell_steps_per_s": n * adjoint_K / (1e-3 * adj["drag"]["ms_per_call"]), **adj}
+    return out
+
+
+def shock_tube(device, steps=20, warmup=3, seeds=(1, 1002), oracle_steps=20):
+    """The 3D shock tube at full size (100x4x4 hexes x 6 = 9,600 tets, Sod
+    states, Kn 1e-2, N_ref 50, specular side walls, CFL 0.5, first order,
+    seed 1): `steps` steps in FP64 and in MIXED, device time over the whole
+    run from the initial state (the workload is those 20 steps, so nothing is
+    spun up; `warmup` steps of a separate simulation come first to load the
+    library's kernels and graphs), the per-field relative L2 of MIXED vs FP64
+    after the run with the FP64 seed-to-seed floor, and the CPU oracle over the
+    same `oracle_steps` steps."""
+    import torch
+    from paper_2007_13091_gb300 import ugkwp
+    from paper_2007_13091_gb300 import workloads as wl
+    out = {"workload": "3D shock tube [0,1]x[0,0.04]^2, 100x4x4 hexes x 6 = 9,600 tets, Sod states, Kn 1e-2, "
+                       "N_ref 50, specular side walls, CFL 0.5, first order, seed 1", "steps": steps}
+    fields = {}
+    for precision, seed in (("fp64", seeds[0]), ("mixed", seeds[0]), ("fp64", seeds[1])):
+        cfg = wl.shock_tube(precision=precision, seed=seed)
+        stream = torch.cuda.Stream(device=device)
+        w = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=stream)
+        w.step(warmup)
+        w.sync()
+        w.close()
+        sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=stream)
+        st0 = sim.step(0, stats=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(steps)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        st1 = sim.step(0, stats=True)
+        P = sim.moments(ugkwp.PRIM)
+        fields[(precision, seed)] = {"rho": P[0], "U": P[1:4], "T": P[4], "p": P[0] * P[4]}
+        moves = st1["n_moves_total"] - st0["n_moves_total"]
+        if seed == seeds[0]:
+            out[precision] = {"value": moves / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+                              "cell_steps_per_s": sim.n_cells * steps / (ms * 1e-3),
+                              "particles_per_step": moves / steps}
+        sim.close()
+    ref, mix, other = fields[("fp64", seeds[0])], fields[("mixed", seeds[0])], fields[("fp64", seeds[1])]
+    # velocity relative to the sound speed of the left state (the tube starts at rest)
+    c_left = math.sqrt(5.0 / 3.0)
+
+    def err(x, y):
+        e = {k: float(np.linalg.norm(x[k] - y[k]) / np.linalg.norm(y[k])) for k in ("rho", "T", "p")}
+        e["U"] = float(np.linalg.norm(x["U"] - y["U"]) / (c_left * math.sqrt(y["U"].shape[1])))
+        return e
+    out["field_error"] = {"after_steps": steps, "mixed_vs_fp64": err(mix, ref), "noise_floor_fp64_seed": err(other, ref),
+                          "U_scale": "sound speed of the left state"}
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    out["cpu_baseline"] = guarded(lambda: cpu_oracle_run(wl.shock_tube(precision="fp64", seed=seeds[0]), 0,
+                                                         oracle_steps, "3D shock tube 9,600 tets, FP64, the "
+                                                         f"whole {oracle_steps}-step run from the initial state"))
+    return out
+
+
+def gks_start_up(device, steps=20, warmup=3):
+    """Start-up steps of the gas-kinetic scheme (the method without particles,
+    Sec. 3.2; the initial fields of the steady cases, Sec. 4.3, 4.4) on the
+    cavity 24^3 at second order with the Prandtl fix at Pr = 2/3: cell-steps/s
+    with the global time step and with local time steps, CUDA events on the
+    simulation's stream around `steps` direct-launch steps."""
+    import torch
+    from paper_2007_13091_gb300 import ugkwp
+    from paper_2007_13091_gb300 import workloads as wl
+    cfg = wl.cavity(n=24, Kn=0.075, N_ref=100, precision="mixed", order=2)
+    cfg["params"]["Pr"] = 2.0 / 3.0
+    stream = torch.cuda.Stream(device=device)
+    sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=stream)
+    n = sim.n_cells
+    out = {"workload": "cavity 24^3 hexes x 6 = 82,944 tets, Kn 0.075, order 2, Pr 2/3, no particles", "n_cells": n}
+    for local in (False, True):
+        sim.gks_steps(warmup, local_dt=local)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.gks_steps(steps, local_dt=local)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        out["local_dt" if local else "global_dt"] = {"ms_per_step": ms / steps,
+                                                      "cell_steps_per_s": n * steps / (ms * 1e-3)}
+    sim.sync()
+    sim.close()
+    return out
+
+
+def hypersonic(device, which, steps, warmup, gks_steps, spin_up=5, adjoint_K=0, kernel_times=True):
     """The hypersonic configurations at full size, MIXED, first order: Ma 4 past
     the unit cube (1,152,912 tets, Kn 0.1, N_ref 200) or Ma 8 past the blunt
     vehicle (2,770,032 tets, Kn 1e-3, T_w = 3 T_inf, N_ref 100, energy-matched
@@ -859,8 +1022,8 @@ def main():
         out["gp1_sampling"] = guarded(lambda: gp1_sampling(device, args.steps, args.warmup, launch_cfg))
         out["diatomic"] = guarded(lambda: diatomic(device, args.steps, args.warmup, launch_cfg))
         out["shock_tube"] = guarded(lambda: shock_tube(device))
-        out["cube_ma4"] = guarded(lambda: hypersonic(device, "cube", 10, 3, 300))
-        out["blunt_vehicle"] = guarded(lambda: hypersonic(device, "vehicle", 5, 3, 1200, spin_up=2, adjoint_K=16,
+        out["cube_ma4"] = guarded(lambda: hypersonic(device, "cube", 100, 3, 300, spin_up=17, kernel_times=False))
+        out["blunt_vehicle"] = guarded(lambda: hypersonic(device, "vehicle", 5, 3, 1200, spin_up=2, adjoint_K=46,
                                                           kernel_times=False))
         out["cpu_baseline"] = cpu_baseline(args.cpu_steps)
         out["cpu_baseline_by_config"] = {
