@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <thread>
 #include <vector>
@@ -59,7 +60,11 @@ struct ugkwp_sim {
     void* graph_key[2] = {nullptr, nullptr};
     int64_t graph_launches[2][UGKWP_N_KERNELS] = {};
     bool graphs_ok = true;
+    // counts the changes of the structures the kernels receive by value
+    // (parameters, launch configuration, buffers): a batch's graphs check it
+    uint64_t gen = 0;
     void drop_graphs() {
+        ++gen;
         for (int k = 0; k < 2; ++k) {
             if (graph[k]) cudaGraphExecDestroy(graph[k]);
             graph[k] = nullptr;
@@ -1490,12 +1495,31 @@ int ugkwp_autotune(ugkwp_sim* s, int32_t steps_per_trial, ugkwp_launch_cfg* best
 }  // extern "C"
 
 // ------------------------------------------------------------------ batches
+// Members of a batch that share precision, order, K > 0 and sampling form
+// fused chunks of up to BATCH_CHUNK members: each kernel of the step is one
+// launch for the whole chunk, on the chunk's own streams.
+struct FusedChunk {
+    std::vector<int> idx;  // members (indices into the batch)
+    int precision = 0, order = 1, sampling = 0;
+    bool ke = false;
+    cudaStream_t lane = nullptr, wave = nullptr, aux = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, sampled = nullptr, tracked = nullptr, gp_ready = nullptr,
+                done = nullptr;
+    ~FusedChunk() {
+        for (cudaEvent_t e : {fork, join, sampled, tracked, gp_ready, done})
+            if (e) cudaEventDestroy(e);
+        for (cudaStream_t q : {lane, wave, aux})
+            if (q) cudaStreamDestroy(q);
+    }
+};
+
 struct ugkwp_batch {
     std::vector<ugkwp_sim*> sims;
     cudaStream_t stream = nullptr;
     std::vector<cudaStream_t> lanes;
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> join;
+    std::vector<std::unique_ptr<FusedChunk>> chunks;
     // two-step graphs keyed by every member's buffer A (ping-pong parities)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::vector<void*> key[2];
@@ -1519,11 +1543,102 @@ struct ugkwp_batch {
 
 namespace {
 
+// A batch graph holds every member's structures as they were at capture: it
+// is valid while each member's step parity and structure generation match.
 std::vector<void*> batch_key(const ugkwp_batch* b) {
     std::vector<void*> k;
-    k.reserve(b->sims.size());
-    for (auto* s : b->sims) k.push_back(s->S.nleft);
+    k.reserve(2 * b->sims.size());
+    for (auto* s : b->sims) {
+        k.push_back(s->S.nleft);
+        k.push_back(reinterpret_cast<void*>(static_cast<uintptr_t>(s->gen)));
+    }
     return k;
+}
+
+// Proportional split of `total` blocks over members of work w[i] (at least one
+// block each, at most need[i]).
+std::vector<int> split_blocks(int total, const std::vector<long long>& w, const std::vector<int>& need) {
+    long long W = 0;
+    for (long long v : w) W += v;
+    std::vector<int> out(w.size(), 1);
+    for (size_t i = 0; i < w.size(); ++i) {
+        long long v = W > 0 ? (long long)total * w[i] / W : 1;
+        if (v < 1) v = 1;
+        if (v > need[i]) v = need[i];
+        out[i] = (int)v;
+    }
+    return out;
+}
+
+// One step of a fused chunk, enqueued like enqueue_step for a single
+// simulation: the same kernels in the same stream order, each one launch
+// for all members of the chunk.
+int enqueue_chunk_step(FusedChunk& ch, const std::vector<ugkwp_sim*>& sims) {
+    BatchChunk c;
+    std::memset(&c, 0, sizeof(c));
+    c.n = (int32_t)ch.idx.size();
+    const LaunchCfg lc = sims[ch.idx[0]]->lc;
+    const int sms = sm_count();
+    std::vector<long long> w6(c.n), wf(c.n);
+    std::vector<int> need_grad(c.n), need_o2(c.n), need_o1(c.n);
+    for (int i = 0; i < c.n; ++i) {
+        ugkwp_sim* s = sims[ch.idx[i]];
+        c.mem[i] = BatchMember{s->M, s->S, s->P, s->A, s->B, s->Mv};
+        w6[i] = 6LL * s->M.nc;
+        wf[i] = s->M.nf;
+        need_grad[i] = (int)((6LL * s->M.nc + gradient_threads() - 1) / gradient_threads());
+        need_o2[i] = (s->M.nf + wave_threads() - 1) / wave_threads();
+        need_o1[i] = (s->M.nf + 255) / 256;
+    }
+    const std::vector<int> b_grad = split_blocks(4 * sms, w6, need_grad);
+    const std::vector<int> b_o2 = split_blocks(lc.wave_blocks, wf, need_o2);
+    const std::vector<int> b_o1 = split_blocks(lc.wave_blocks, wf, need_o1);
+    for (int k = 0; k < BCL_N; ++k) c.off[k][0] = 0;
+    for (int i = 0; i < c.n; ++i) {
+        const int nc = c.mem[i].m.nc;
+        const int per[BCL_N] = {blocks_reset(nc), blocks_cells(nc), scan_blocks(nc), b_grad[i], blocks_gp_coef(nc),
+                                b_o2[i], b_o1[i]};
+        for (int k = 0; k < BCL_N; ++k) c.off[k][i + 1] = c.off[k][i] + per[k];
+    }
+    auto blocks = [&](int k) { return c.off[k][c.n]; };
+    cudaStream_t q = ch.lane;
+    launch_reset_batch(c, blocks(BCL_RESET), q);
+    launch_cell_prep_batch(c, blocks(BCL_CELLS), q);
+    launch_sample_count_batch(c, blocks(BCL_SCAN), q);
+    CU(cudaEventRecord(ch.fork, q));
+    CU(cudaStreamWaitEvent(ch.wave, ch.fork, 0));
+    const bool gp = ch.sampling == UGKWP_SAMPLE_GP1;
+    if (ch.order == 2) {
+        launch_gradients_batch(c, blocks(BCL_GRAD), ch.wave);
+        if (gp) launch_gp_coef_batch(c, blocks(BCL_GPC), ch.wave);
+    }
+    if (gp) CU(cudaEventRecord(ch.gp_ready, ch.wave));
+    if (ch.order == 2) launch_face_flux_o2_batch(c, blocks(BCL_FLUX_O2), ch.wave);
+    else launch_face_flux_batch(c, blocks(BCL_FLUX), ch.wave);
+    CU(cudaEventRecord(ch.join, ch.wave));
+    launch_scan_batch(c, blocks(BCL_SCAN), q);
+    if (gp) CU(cudaStreamWaitEvent(q, ch.gp_ready, 0));
+    if (ch.sampling == UGKWP_SAMPLE_ENERGY_MATCHED) launch_sample_scale_batch(c, blocks(BCL_CELLS), ch.precision, q);
+    launch_sample_write_batch(c, lc.particle_blocks, ch.precision, q);
+    const int first_half = (lc.particle_blocks + 1) / 2;
+    CU(cudaEventRecord(ch.sampled, q));
+    launch_track_batch(c, ch.precision, ch.ke, lc.track, first_half, q);
+    CU(cudaStreamWaitEvent(ch.aux, ch.sampled, 0));
+    CU(cudaStreamWaitEvent(ch.aux, ch.join, 0));
+    if (lc.particle_blocks > first_half)
+        launch_track_batch(c, ch.precision, ch.ke, lc.track, lc.particle_blocks - first_half, ch.aux);
+    CU(cudaEventRecord(ch.tracked, ch.aux));
+    CU(cudaStreamWaitEvent(q, ch.tracked, 0));
+    launch_movers_batch(c, lc.particle_blocks, ch.precision, q);
+    CU(cudaStreamWaitEvent(q, ch.join, 0));
+    launch_cell_update_batch(c, blocks(BCL_CELLS), q);
+    for (int i = 0; i < c.n; ++i) {
+        ugkwp_sim* s = sims[ch.idx[i]];
+        std::swap(s->A, s->B);
+        std::swap(s->S.nleft, s->S.nleft_next);
+        std::swap(s->S.smass, s->S.smass_next);
+    }
+    return UGKWP_OK;
 }
 
 bool batch_graphs_allowed(const ugkwp_batch* b) {
@@ -1533,9 +1648,24 @@ bool batch_graphs_allowed(const ugkwp_batch* b) {
 }
 
 // Enqueue `n` (1 or 2) steps of every member on the batch's lanes, forked from
-// and joined back into the batch stream.
+// and joined back into the batch stream: as fused chunks, or (while a member
+// records per-kernel times) as each member's own kernels.
 int batch_enqueue(ugkwp_batch* b, int n) {
     CU(cudaEventRecord(b->fork, b->stream));
+    bool timing = false;
+    for (auto* s : b->sims) timing = timing || s->timing;
+    if (!timing && !b->chunks.empty()) {
+        for (auto& ch : b->chunks) {
+            CU(cudaStreamWaitEvent(ch->lane, b->fork, 0));
+            for (int k = 0; k < n; ++k) {
+                int rc = enqueue_chunk_step(*ch, b->sims);
+                if (rc) return rc;
+            }
+            CU(cudaEventRecord(ch->done, ch->lane));
+            CU(cudaStreamWaitEvent(b->stream, ch->done, 0));
+        }
+        return UGKWP_OK;
+    }
     const size_t L = b->lanes.size();
     for (size_t i = 0; i < b->sims.size(); ++i) {
         ugkwp_sim* s = b->sims[i];
@@ -1625,6 +1755,29 @@ int ugkwp_batch_create(ugkwp_sim* const* sims, int32_t n_sims, void* cuda_stream
     }
     b->join.assign(v.size(), nullptr);
     for (size_t i = 0; i < v.size() && ce == cudaSuccess; ++i) ce = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    // fused chunks: members grouped by precision, order, K > 0 and sampling,
+    // in batch order, at most BATCH_CHUNK per chunk
+    for (size_t i = 0; i < v.size() && ce == cudaSuccess; ++i) {
+        const DevParams& P = v[i]->P;
+        FusedChunk* into = nullptr;
+        for (auto& ch : b->chunks)
+            if (ch->precision == P.precision && ch->order == P.order && ch->ke == (P.K > 0) &&
+                ch->sampling == P.sampling && (int)ch->idx.size() < BATCH_CHUNK)
+                into = ch.get();
+        if (!into) {
+            b->chunks.emplace_back(new FusedChunk);
+            into = b->chunks.back().get();
+            into->precision = P.precision;
+            into->order = P.order;
+            into->ke = P.K > 0;
+            into->sampling = P.sampling;
+            for (cudaStream_t* q : {&into->lane, &into->wave, &into->aux})
+                if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(q, cudaStreamNonBlocking);
+            for (cudaEvent_t* e : {&into->fork, &into->join, &into->sampled, &into->tracked, &into->gp_ready, &into->done})
+                if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+        }
+        into->idx.push_back((int)i);
+    }
     if (ce != cudaSuccess) {
         delete b;
         return cuda_fail(ce, "ugkwp_batch_create");

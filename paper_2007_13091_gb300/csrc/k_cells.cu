@@ -42,17 +42,17 @@ __device__ __forceinline__ int2 block_scan_incl2(int2 v, int2* sh_warp) {
     return v;
 }
 
-__global__ void k_reset(DevMesh m, DevState s) {
+__device__ __forceinline__ void reset_body(const DevMesh& m, const DevState& s, Blk bk) {
     const int nc = m.nc;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 5LL * nc; i += stride) {
+    const long long stride = (long long)bk.n * blockDim.x;
+    for (long long i = (long long)bk.id * blockDim.x + threadIdx.x; i < 5LL * nc; i += stride) {
         s.pflux[i] = 0;
         if (i < nc) {
             s.nleft_next[i] = 0;
             s.smass_next[i] = 0;
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (bk.id == 0 && threadIdx.x == 0) {
         s.cnt64[CNT_SAMPLED] = 0;
         s.cnt64[CNT_COLLIDED] = 0;
         s.cnt64[CNT_EXITED] = 0;
@@ -67,12 +67,15 @@ __global__ void k_reset(DevMesh m, DevState s) {
         s.cnt64[CNT_SURV] = 0;
     }
 }
+__global__ void k_reset(DevMesh m, DevState s) {
+    reset_body(m, s, Blk{(int)blockIdx.x, (int)gridDim.x});
+}
 
 // a1 + a2: primitives, tau = mu_ref/p (T/T_ref)^omega, rho^p from the survivors'
 // fixed-point mass, rho^h = rho - rho^p, and min_i |Omega_i| / sum_d Lambda_i^d.
-__global__ void k_cell_prep(DevMesh m, DevState s, DevParams p) {
+__device__ __forceinline__ void cell_prep_body(const DevMesh& m, const DevState& s, const DevParams& p, Blk bk) {
     const int nc = m.nc;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bk.id * blockDim.x + threadIdx.x;
     double r = __longlong_as_double(0x7ff0000000000000LL);
     if (i < nc) {
         const double rho = s.W[i];
@@ -118,6 +121,9 @@ __global__ void k_cell_prep(DevMesh m, DevState s, DevParams p) {
                       (unsigned long long)__double_as_longlong(v));
     }
 }
+__global__ void k_cell_prep(DevMesh m, DevState s, DevParams p) {
+    cell_prep_body(m, s, p, Blk{(int)blockIdx.x, (int)gridDim.x});
+}
 
 // a5 counts: rho^hp = e^{-dt/tau} rho^h, m_ref = (rho^p + rho^hp)|Omega|/N_ref,
 // N_sam = 2 ceil(rho^hp |Omega| / (2 m_ref)), N_sam >= N_min - N_left,
@@ -125,10 +131,10 @@ __global__ void k_cell_prep(DevMesh m, DevState s, DevParams p) {
 // the cell gets in the buffer this step's survivors are written to (a11:
 // sized from the particles that start the step in the cell), and the
 // per-block sums of the bucket sizes and of N_sam.
-__global__ void k_sample_count(DevMesh m, DevState s, DevParams p) {
+__device__ __forceinline__ void sample_count_body(const DevMesh& m, const DevState& s, const DevParams& p, Blk bk) {
     __shared__ int2 shw[32];
     const int nc = m.nc;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bk.id * blockDim.x + threadIdx.x;
     const double dt = p.CFL * __longlong_as_double(s.cnt64[CNT_DT_BITS]);
     if (p.gks) {  // GKS step: the time step only, nothing is sampled
         if (i == 0) s.dt[0] = dt;
@@ -164,14 +170,17 @@ __global__ void k_sample_count(DevMesh m, DevState s, DevParams p) {
         s.wcap[i] = wcap;
     }
     const int2 incl = block_scan_incl2(make_int2(wcap, nsam), shw);
-    if (threadIdx.x == blockDim.x - 1) s.bsum[blockIdx.x] = incl;
+    if (threadIdx.x == blockDim.x - 1) s.bsum[bk.id] = incl;
     if (i == 0) s.dt[0] = dt;
+}
+__global__ void k_sample_count(DevMesh m, DevState s, DevParams p) {
+    sample_count_body(m, s, p, Blk{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // Exclusive scan of the block sums (one block): the slots of the survivor
 // buckets of the buffer written this step and the sampled particles (they
 // follow the N_A slots of the current buffer), and the capacity checks.
-__global__ void k_scan_bsum(DevState s, DevParams p, int nb) {
+__device__ __forceinline__ void scan_bsum_body(const DevState& s, const DevParams& p, int nb) {
     __shared__ int2 shw[32];
     __shared__ long long carry_sh[2];
     if (threadIdx.x == 0) { carry_sh[0] = 0; carry_sh[1] = 0; }
@@ -199,23 +208,29 @@ __global__ void k_scan_bsum(DevState s, DevParams p, int nb) {
         }
     }
 }
+__global__ void k_scan_bsum(DevState s, DevParams p, int nb) {
+    scan_bsum_body(s, p, nb);
+}
 
-__global__ void k_scan_apply(DevMesh m, DevState s) {
+__device__ __forceinline__ void scan_apply_body(const DevMesh& m, const DevState& s, Blk bk) {
     __shared__ int2 shw[32];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bk.id * blockDim.x + threadIdx.x;
     const int2 v = i < m.nc ? make_int2(s.wcap[i], s.nsam[i]) : make_int2(0, 0);
     const int2 incl = block_scan_incl2(v, shw);
     if (i < m.nc) {
-        s.soff[i] = s.bsum[blockIdx.x].y + incl.y - v.y;
-        s.woff[i] = s.bsum[blockIdx.x].x + incl.x - v.x;
+        s.soff[i] = s.bsum[bk.id].y + incl.y - v.y;
+        s.woff[i] = s.bsum[bk.id].x + incl.x - v.x;
     }
+}
+__global__ void k_scan_apply(DevMesh m, DevState s) {
+    scan_apply_body(m, s, Blk{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // a10: W^{n+1} = W^n - 1/|Omega| sum_k (+-F_k |S_k|) + F^{fr,p}/|Omega|, faces
 // gathered in local order 0..3 (Eq. update_macro_variables).
-__global__ void k_cell_update(DevMesh m, DevState s, DevParams p, int32_t* wcell) {
+__device__ __forceinline__ void cell_update_body(const DevMesh& m, const DevState& s, const DevParams& p, int32_t* wcell, Blk bk) {
     const int nc = m.nc, nf = m.nf;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bk.id * blockDim.x + threadIdx.x;
     if (p.gks) {
         // GKS step (no particles): W -= sum_k (+-F_k |S_k|) / |Omega|; with local
         // steps F_k holds the flux rate and the cell advances by its own dt
@@ -271,6 +286,50 @@ __global__ void k_cell_update(DevMesh m, DevState s, DevParams p, int32_t* wcell
         w = (w - acc * ivol) + fp * ivol;
         if (p.averaging) s.wsum[(size_t)q * nc + i] += s.dt[0] * w;
     }
+}
+__global__ void k_cell_update(DevMesh m, DevState s, DevParams p, int32_t* wcell) {
+    cell_update_body(m, s, p, wcell, Blk{(int)blockIdx.x, (int)gridDim.x});
+}
+
+// ---- fused batches: member i of the chunk runs on the blocks
+// off[cls][i] .. off[cls][i + 1] - 1, the grid its own launch would have.
+__device__ __forceinline__ int member_of(const int32_t* off, int n) {
+    int lo = 0, hi = n;  // off[lo] <= blockIdx.x < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ Blk member_blk(const int32_t* off, int i) {
+    return Blk{(int)blockIdx.x - off[i], off[i + 1] - off[i]};
+}
+
+__global__ void k_reset_b(const __grid_constant__ BatchChunk c) {
+    const int i = member_of(c.off[BCL_RESET], c.n);
+    reset_body(c.mem[i].m, c.mem[i].s, member_blk(c.off[BCL_RESET], i));
+}
+__global__ void k_cell_prep_b(const __grid_constant__ BatchChunk c) {
+    const int i = member_of(c.off[BCL_CELLS], c.n);
+    cell_prep_body(c.mem[i].m, c.mem[i].s, c.mem[i].p, member_blk(c.off[BCL_CELLS], i));
+}
+__global__ void k_sample_count_b(const __grid_constant__ BatchChunk c) {
+    const int i = member_of(c.off[BCL_SCAN], c.n);
+    sample_count_body(c.mem[i].m, c.mem[i].s, c.mem[i].p, member_blk(c.off[BCL_SCAN], i));
+}
+// one block per member
+__global__ void k_scan_bsum_b(const __grid_constant__ BatchChunk c) {
+    const BatchMember& e = c.mem[blockIdx.x];
+    scan_bsum_body(e.s, e.p, scan_blocks(e.m.nc));
+}
+__global__ void k_scan_apply_b(const __grid_constant__ BatchChunk c) {
+    const int i = member_of(c.off[BCL_SCAN], c.n);
+    scan_apply_body(c.mem[i].m, c.mem[i].s, member_blk(c.off[BCL_SCAN], i));
+}
+__global__ void k_cell_update_b(const __grid_constant__ BatchChunk c) {
+    const int i = member_of(c.off[BCL_CELLS], c.n);
+    cell_update_body(c.mem[i].m, c.mem[i].s, c.mem[i].p, c.mem[i].b.cell, member_blk(c.off[BCL_CELLS], i));
 }
 
 // Time average W-bar = sum dt^n W^n / sum dt^n (Sec. 2.4 (c)).
@@ -403,11 +462,17 @@ cudaError_t configure_cell_kernels(int carveout) {
     set(k_scan_bsum);
     set(k_scan_apply);
     set(k_cell_update);
+    set(k_reset_b);
+    set(k_cell_prep_b);
+    set(k_sample_count_b);
+    set(k_scan_bsum_b);
+    set(k_scan_apply_b);
+    set(k_cell_update_b);
     return e;
 }
 
 void launch_reset(const DevMesh& m, const DevState& s, cudaStream_t st) {
-    k_reset<<<cdiv(5LL * m.nc, 256) < 4096 ? cdiv(5LL * m.nc, 256) : 4096, 256, 0, st>>>(m, s);
+    k_reset<<<blocks_reset(m.nc), 256, 0, st>>>(m, s);
 }
 void launch_cell_prep(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
     k_cell_prep<<<cdiv(m.nc, 256), 256, 0, st>>>(m, s, p);
@@ -421,6 +486,23 @@ void launch_scan(const DevMesh& m, const DevState& s, const DevParams& p, cudaSt
 }
 void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p, int32_t* wcell, cudaStream_t st) {
     k_cell_update<<<cdiv(m.nc, 256), 256, 0, st>>>(m, s, p, wcell);
+}
+int blocks_reset(int nc) { return cdiv(5LL * nc, 256) < 4096 ? cdiv(5LL * nc, 256) : 4096; }
+int blocks_cells(int nc) { return cdiv(nc, 256); }
+
+void launch_reset_batch(const BatchChunk& c, int blocks, cudaStream_t st) { k_reset_b<<<blocks, 256, 0, st>>>(c); }
+void launch_cell_prep_batch(const BatchChunk& c, int blocks, cudaStream_t st) {
+    k_cell_prep_b<<<blocks, 256, 0, st>>>(c);
+}
+void launch_sample_count_batch(const BatchChunk& c, int blocks, cudaStream_t st) {
+    k_sample_count_b<<<blocks, SCAN_BLOCK, 0, st>>>(c);
+}
+void launch_scan_batch(const BatchChunk& c, int blocks, cudaStream_t st) {
+    k_scan_bsum_b<<<c.n, SCAN_BLOCK, 0, st>>>(c);
+    k_scan_apply_b<<<blocks, SCAN_BLOCK, 0, st>>>(c);
+}
+void launch_cell_update_batch(const BatchChunk& c, int blocks, cudaStream_t st) {
+    k_cell_update_b<<<blocks, 256, 0, st>>>(c);
 }
 void launch_rebuild_survivors(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
                               cudaStream_t st) {

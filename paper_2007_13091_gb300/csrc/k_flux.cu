@@ -247,13 +247,16 @@ __device__ __forceinline__ void gradient_of(const DevMesh& m, const DevState& s,
 
 // One thread per (quantity, cell), quantity-major so that neighbouring threads
 // read neighbouring cells of one array.
-__global__ void __launch_bounds__(128) k_gradients(DevMesh m, DevState s, DevParams p) {
+__device__ __forceinline__ void gradients_body(const DevMesh& m, const DevState& s, const DevParams& p, Blk bk) {
     const int nc = m.nc;
     const long long n = 6LL * nc;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    for (long long t = (long long)bk.id * blockDim.x + threadIdx.x; t < n; t += (long long)bk.n * blockDim.x) {
         const int q = (int)(t / nc);
         gradient_of(m, s, p, (int)(t - (long long)q * nc), q);
     }
+}
+__global__ void __launch_bounds__(128) k_gradients(DevMesh m, DevState s, DevParams p) {
+    gradients_body(m, s, p, Blk{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // Moment tables of a unit Maxwellian in a face frame: <u^k> (normal, over the
@@ -608,9 +611,9 @@ __device__ void interior_flux_o2(const DevMesh& m, const DevState& s, const DevP
 // gradient and g_t from W_t = -sum_d dF_d/dx_d; as a polynomial phi of
 // X = (u - U)/sqrt(RT) in g_p = rho N(X)(1 + phi), bounded over |X| <= 5 and
 // scaled down where that bound Phi exceeds 1; stores GP_NC values per cell.
-__global__ void __launch_bounds__(128) k_gp_coef(DevMesh m, DevState s, DevParams p) {
+__device__ __forceinline__ void gp_coef_body(const DevMesh& m, const DevState& s, const DevParams& p, Blk bk) {
     const int nc = m.nc;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bk.id * blockDim.x + threadIdx.x;
     if (i >= nc) return;
     const double rho = s.prim[i];
     const double U[3] = {s.prim[nc + i], s.prim[2 * nc + i], s.prim[3 * nc + i]};
@@ -684,6 +687,9 @@ __global__ void __launch_bounds__(128) k_gp_coef(DevMesh m, DevState s, DevParam
     for (int k = 0; k < 13; ++k) s.gpc[(size_t)k * nc + i] = co[k];
     s.gpc[(size_t)13 * nc + i] = 1.0 + Phi;
 }
+__global__ void __launch_bounds__(128) k_gp_coef(DevMesh m, DevState s, DevParams p) {
+    gp_coef_body(m, s, p, Blk{(int)blockIdx.x, (int)gridDim.x});
+}
 
 __device__ __forceinline__ void face_flux_o1(const DevMesh& m, const DevState& s, const DevParams& p, int t);
 
@@ -691,11 +697,11 @@ __device__ __forceinline__ void face_flux_o1(const DevMesh& m, const DevState& s
 // then the first-order flux of the boundary faces that follow them.
 // With local time steps (GKS step) each face is integrated over the smaller
 // step of its cells and stores the mean flux rate F / dt_f.
-__global__ void __launch_bounds__(UGKWP_WAVE_THREADS, UGKWP_WAVE_MIN_BLOCKS) k_face_flux_o2(DevMesh m, DevState s, DevParams p) {
+__device__ __forceinline__ void face_flux_o2_body(const DevMesh& m, const DevState& s, const DevParams& p, Blk bk) {
     const int nf = m.nf;
     const double dt = s.dt[0];
     const double inv_Tref = 1.0 / p.T_ref;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+    for (int t = bk.id * blockDim.x + threadIdx.x; t < nf; t += bk.n * blockDim.x) {
         if (t >= m.nif) {  // the boundary faces follow, at first order, in the same grid
             face_flux_o1(m, s, p, t);
             continue;
@@ -710,6 +716,9 @@ __global__ void __launch_bounds__(UGKWP_WAVE_THREADS, UGKWP_WAVE_MIN_BLOCKS) k_f
             for (int q = 0; q < 5; ++q) F[q] = F[q] / dtf;
         for (int q = 0; q < 5; ++q) s.F[(size_t)q * nf + f] = F[q];
     }
+}
+__global__ void __launch_bounds__(UGKWP_WAVE_THREADS, UGKWP_WAVE_MIN_BLOCKS) k_face_flux_o2(DevMesh m, DevState s, DevParams p) {
+    face_flux_o2_body(m, s, p, Blk{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // First-order flux of face face_order[t].
@@ -769,9 +778,44 @@ __device__ __forceinline__ void face_flux_o1(const DevMesh& m, const DevState& s
 }
 
 // First-order flux of the faces face_order[first..nf), grid-stride.
-__global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevParams p, int first) {
-    for (int t = first + blockIdx.x * blockDim.x + threadIdx.x; t < m.nf; t += gridDim.x * blockDim.x)
+__device__ __forceinline__ void face_flux_body(const DevMesh& m, const DevState& s, const DevParams& p, int first, Blk bk) {
+    for (int t = first + bk.id * blockDim.x + threadIdx.x; t < m.nf; t += bk.n * blockDim.x)
         face_flux_o1(m, s, p, t);
+}
+__global__ void __launch_bounds__(256) k_face_flux(DevMesh m, DevState s, DevParams p, int first) {
+    face_flux_body(m, s, p, first, Blk{(int)blockIdx.x, (int)gridDim.x});
+}
+
+// ---- fused batches: member i of the chunk runs on the blocks
+// off[cls][i] .. off[cls][i + 1] - 1.
+__device__ __forceinline__ int member_of(const int32_t* off, int n) {
+    int lo = 0, hi = n;  // off[lo] <= blockIdx.x < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ Blk member_blk(const int32_t* off, int i) {
+    return Blk{(int)blockIdx.x - off[i], off[i + 1] - off[i]};
+}
+__global__ void __launch_bounds__(128) k_gradients_b(const __grid_constant__ BatchChunk c) {
+    const int i = member_of(c.off[BCL_GRAD], c.n);
+    gradients_body(c.mem[i].m, c.mem[i].s, c.mem[i].p, member_blk(c.off[BCL_GRAD], i));
+}
+__global__ void __launch_bounds__(128) k_gp_coef_b(const __grid_constant__ BatchChunk c) {
+    const int i = member_of(c.off[BCL_GPC], c.n);
+    gp_coef_body(c.mem[i].m, c.mem[i].s, c.mem[i].p, member_blk(c.off[BCL_GPC], i));
+}
+__global__ void __launch_bounds__(UGKWP_WAVE_THREADS, UGKWP_WAVE_MIN_BLOCKS)
+    k_face_flux_o2_b(const __grid_constant__ BatchChunk c) {
+    const int i = member_of(c.off[BCL_FLUX_O2], c.n);
+    face_flux_o2_body(c.mem[i].m, c.mem[i].s, c.mem[i].p, member_blk(c.off[BCL_FLUX_O2], i));
+}
+__global__ void __launch_bounds__(256) k_face_flux_b(const __grid_constant__ BatchChunk c) {
+    const int i = member_of(c.off[BCL_FLUX], c.n);
+    face_flux_body(c.mem[i].m, c.mem[i].s, c.mem[i].p, 0, member_blk(c.off[BCL_FLUX], i));
 }
 
 }  // namespace
@@ -791,7 +835,7 @@ void launch_gradients(const DevMesh& m, const DevState& s, const DevParams& p, c
 }
 
 void launch_gp_coef(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
-    k_gp_coef<<<(m.nc + 127) / 128, 128, 0, st>>>(m, s, p);
+    k_gp_coef<<<blocks_gp_coef(m.nc), 128, 0, st>>>(m, s, p);
 }
 
 void launch_face_flux_o2(const DevMesh& m, const DevState& s, const DevParams& p, int blocks, cudaStream_t st) {
@@ -809,6 +853,10 @@ cudaError_t configure_wave_kernels(int carveout) {
     set(k_gp_coef);
     set(k_face_flux_o2);
     set(k_face_flux);
+    set(k_gradients_b);
+    set(k_gp_coef_b);
+    set(k_face_flux_o2_b);
+    set(k_face_flux_b);
     return e;
 }
 
@@ -818,6 +866,20 @@ void launch_face_flux(const DevMesh& m, const DevState& s, const DevParams& p, i
                       cudaStream_t st) {
     const int need = (m.nf - first + 255) / 256;
     k_face_flux<<<blocks > 0 && blocks < need ? blocks : need, 256, 0, st>>>(m, s, p, first);
+}
+
+int blocks_gp_coef(int nc) { return (nc + 127) / 128; }
+int gradient_threads() { return 128; }
+
+void launch_gradients_batch(const BatchChunk& c, int blocks, cudaStream_t st) {
+    k_gradients_b<<<blocks, 128, 0, st>>>(c);
+}
+void launch_gp_coef_batch(const BatchChunk& c, int blocks, cudaStream_t st) { k_gp_coef_b<<<blocks, 128, 0, st>>>(c); }
+void launch_face_flux_o2_batch(const BatchChunk& c, int blocks, cudaStream_t st) {
+    k_face_flux_o2_b<<<blocks, UGKWP_WAVE_THREADS, 0, st>>>(c);
+}
+void launch_face_flux_batch(const BatchChunk& c, int blocks, cudaStream_t st) {
+    k_face_flux_b<<<blocks, 256, 0, st>>>(c);
 }
 
 }  // namespace ugkwp

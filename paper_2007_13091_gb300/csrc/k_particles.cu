@@ -172,9 +172,10 @@ __device__ __forceinline__ void gp_normals(const double* gpc, int nc, int cell, 
 // so the pairs' thermal energy is exactly rho^hp |Omega| (3/2) R T.  The sum
 // runs over the cell's pairs in order in binary64; spread = s sqrt(RT).
 template <class Real>
-__global__ void __launch_bounds__(256) k_sample_scale(DevMesh m, DevState s, DevParams p) {
+__device__ __forceinline__ void sample_scale_body(const DevMesh& m, const DevState& s, const DevParams& p,
+                                                  Blk bk) {
     const int nc = m.nc;
-    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cell = bk.id * blockDim.x + threadIdx.x;
     if (cell >= nc) return;
     const long long step = s.cnt64[CNT_STEP];
     const int ns = s.nsam[cell];
@@ -191,6 +192,10 @@ __global__ void __launch_bounds__(256) k_sample_scale(DevMesh m, DevState s, Dev
     }
     s.sig[cell] = sig;
     if constexpr (sizeof(Real) == 4) s.usig[cell].w = (float)sig;
+}
+template <class Real>
+__global__ void __launch_bounds__(256) k_sample_scale(DevMesh m, DevState s, DevParams p) {
+    sample_scale_body<Real>(m, s, p, Blk{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // a5 positions: a uniform point in the tet from three uniforms folded cube ->
@@ -248,14 +253,15 @@ __device__ __forceinline__ float ff_position(const float* f, int nc, const float
 }
 
 template <class Real>
-__global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, DevParams p, PartBufRaw br) {
+__device__ __forceinline__ void sample_write_body(const DevMesh& m, const DevState& s, const DevParams& p,
+                                                  const PartBufRaw& br, Blk bk) {
     if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
     const PartView<Real> b = view<Real>(br);
     const int nc = m.nc;
     const long long total = s.cnt64[CNT_NSAM];
     const long long step = s.cnt64[CNT_STEP];
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+    const long long stride = (long long)bk.n * blockDim.x;
+    for (long long g = (long long)bk.id * blockDim.x + threadIdx.x; g < total; g += stride) {
         // owning cell: the last c with soff[c] <= g (cells with N_sam = 0 share
         // the offset of the next cell and are never the last such c)
         int lo = 0, hi = nc;  // invariant: soff[lo] <= g < soff[hi] (soff[nc] = +inf)
@@ -321,6 +327,10 @@ __global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, Dev
         b.cell[j] = cell;
         b.id[j] = id;
     }
+}
+template <class Real>
+__global__ void __launch_bounds__(256) k_sample_write(DevMesh m, DevState s, DevParams p, PartBufRaw br) {
+    sample_write_body<Real>(m, s, p, br, Blk{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // ------------------------------------------------------------------ tracking
@@ -621,11 +631,12 @@ template <class Real, bool KE, int T> struct WalkQueue {
 // KE: the particles carry an internal energy (K > 0).  THREADS: particles per
 // tile (one per thread).
 template <class Real, bool KE, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br,
-                                                                  PartBufRaw nr, PartBufRaw ar) {
+__device__ __forceinline__ void track_body(const DevMesh& m, const DevState& s, const DevParams& p,
+                                           const PartBufRaw& br, const PartBufRaw& nr, const PartBufRaw& ar) {
     constexpr int NW = THREADS / 32;
     using Q = WalkQueue<Real, KE, THREADS>;
-    if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
+    // (block-uniform: another block may set the bit while this one starts)
+    if (__syncthreads_or(threadIdx.x == 0 && (s.cnt64[CNT_ERR] & ERRB_CAPACITY))) return;
     const PartView<Real> b = view<Real>(br);   // this step's particles, sorted by cell (holes: cell -1)
     const PartView<Real> nxt = view<Real>(nr);  // the next step's survivors, in their end cells' buckets
     const PartView<Real> mv = view<Real>(ar);  // mover list: x = u at start, u = u at end
@@ -639,6 +650,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_track(DevMesh m, De
     // two rounds later, after two barriers every warp has passed
     __shared__ int sh_cnt[2][NW];
     __shared__ long long sh_base[2], sh_tile[2];
+    __shared__ int sh_qc;  // queue size after the last output round
     const long long wtot = s.cnt64[CNT_WTOT];  // overflow slots start after the buckets
     int par = 0;
     __shared__ unsigned long long sh_red[NW][8];
@@ -650,6 +662,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_track(DevMesh m, De
     TileQueue tq;  // thread 0's
     if (threadIdx.x == 0) {
         q.count = 0;
+        sh_qc = 0;
         sh_tile[0] = next_tile(tq, &s.cnt64[CNT_TILE], THREADS);
     }
     __syncthreads();
@@ -709,6 +722,10 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_track(DevMesh m, De
             // the walks taken from the queue this round leave it (every
             // thread read its entry before the barrier above)
             q.count -= qtake;
+            // the queue's size as every warp must see it after this round: a
+            // warp that leaves the round early may already push the next
+            // tile's walks into q.count before a slower warp reads it
+            sh_qc = q.count;
             // the next tile, in the other set (its last readers read it before
             // the barrier above); a round without a new tile keeps the current one
             sh_tile[par ^ 1] = advance ? next_tile(tq, &s.cnt64[CNT_TILE], THREADS) : sh_tile[par];
@@ -783,7 +800,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_track(DevMesh m, De
     for (;;) {
         const long long bb = sh_tile[par];  // block-uniform
         const bool have_tile = bb < n;
-        if (!have_tile && q.count == 0) break;
+        if (!have_tile && sh_qc == 0) break;
         // ---- a new tile: load, t_f, the first tet of every walk
         Ended<Real> e;
         e.active = e.survivor = e.mover = e.exited = false;
@@ -864,7 +881,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_track(DevMesh m, De
         emit(e, have_tile, 0);
         // ---- the queued walks, in full warps once half a block of them has
         // gathered (or once the tiles are done)
-        const int qc = q.count;  // block-uniform: the pushes came before emit's barriers
+        const int qc = sh_qc;  // block-uniform: set between the round's barriers
         if (qc >= THREADS / 2 || (!have_tile && qc > 0)) {
             const int take = qc < THREADS ? qc : THREADS;
             Ended<Real> f;
@@ -930,6 +947,11 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_track(DevMesh m, De
         }
     }
 }
+template <class Real, bool KE, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_track(DevMesh m, DevState s, DevParams p, PartBufRaw br,
+                                                                  PartBufRaw nr, PartBufRaw ar) {
+    track_body<Real, KE, THREADS>(m, s, p, br, nr, ar);
+}
 
 // Same bits (a particle's velocity and internal energy are unchanged unless it
 // met a wall).
@@ -944,8 +966,9 @@ __device__ __forceinline__ bool same_bits(double a, double b) {
 // for the movers that met no wall.
 
 template <class Real>
-__global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams p, PartBufRaw ar) {
-    if (s.cnt64[CNT_ERR] & ERRB_CAPACITY) return;
+__device__ __forceinline__ void movers_body(const DevMesh& m, const DevState& s, const DevParams& p,
+                                            const PartBufRaw& ar, Blk bk) {
+    if (__syncthreads_or(threadIdx.x == 0 && (s.cnt64[CNT_ERR] & ERRB_CAPACITY))) return;
     const PartView<Real> mv = view<Real>(ar);
     const long long n = s.cnt64[CNT_RESV];
     const int nc = m.nc;
@@ -956,7 +979,7 @@ __global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams
     // whole warps, since binary64 work costs a warp its full issue time
     __shared__ int wall_j[256];
     __shared__ int n_wall;
-    for (long long base = (long long)blockIdx.x * 256; base < n; base += (long long)gridDim.x * 256) {
+    for (long long base = (long long)bk.id * 256; base < n; base += (long long)bk.n * 256) {
         if (threadIdx.x == 0) n_wall = 0;
         __syncthreads();
         const long long j = base + threadIdx.x;
@@ -1027,6 +1050,48 @@ __global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams
         __syncthreads();
     }
 }
+template <class Real>
+__global__ void __launch_bounds__(256) k_movers(DevMesh m, DevState s, DevParams p, PartBufRaw ar) {
+    movers_body<Real>(m, s, p, ar, Blk{(int)blockIdx.x, (int)gridDim.x});
+}
+
+// ---- fused batches
+__device__ __forceinline__ int member_of(const int32_t* off, int n) {
+    int lo = 0, hi = n;  // off[lo] <= blockIdx.x < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+template <class Real>
+__global__ void __launch_bounds__(256) k_sample_scale_b(const __grid_constant__ BatchChunk c) {
+    const int32_t* off = c.off[BCL_CELLS];
+    const int i = member_of(off, c.n);
+    sample_scale_body<Real>(c.mem[i].m, c.mem[i].s, c.mem[i].p, Blk{(int)blockIdx.x - off[i], off[i + 1] - off[i]});
+}
+// The particle kernels take every member of the chunk in turn on the whole grid.
+template <class Real>
+__global__ void __launch_bounds__(256) k_sample_write_b(const __grid_constant__ BatchChunk c) {
+    for (int k = 0; k < c.n; ++k)
+        sample_write_body<Real>(c.mem[k].m, c.mem[k].s, c.mem[k].p, c.mem[k].a, Blk{(int)blockIdx.x, (int)gridDim.x});
+}
+// Tiles come from each member's own counter; a block starts at member
+// blockIdx.x mod n, so that the blocks spread over the members' counters.
+template <class Real, bool KE, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_track_b(const __grid_constant__ BatchChunk c) {
+    for (int k = 0; k < c.n; ++k) {
+        const BatchMember& e = c.mem[((int)blockIdx.x + k) % c.n];
+        track_body<Real, KE, THREADS>(e.m, e.s, e.p, e.a, e.b, e.mv);
+        __syncthreads();
+    }
+}
+template <class Real>
+__global__ void __launch_bounds__(256) k_movers_b(const __grid_constant__ BatchChunk c) {
+    for (int k = 0; k < c.n; ++k)
+        movers_body<Real>(c.mem[k].m, c.mem[k].s, c.mem[k].p, c.mem[k].mv, Blk{(int)blockIdx.x, (int)gridDim.x});
+}
 
 }  // namespace
 
@@ -1074,6 +1139,11 @@ template <class Real, bool KE> cudaError_t configure_type(int carveout) {
     set(k_sample_write<Real>);
     set(k_sample_scale<Real>);
     set(k_movers<Real>);
+    set(k_track_b<Real, KE, 128>);
+    set(k_track_b<Real, KE, 256>);
+    set(k_sample_write_b<Real>);
+    set(k_sample_scale_b<Real>);
+    set(k_movers_b<Real>);
     return e;
 }
 }  // namespace
@@ -1086,6 +1156,36 @@ cudaError_t configure_particle_kernels(const DevParams& p, int carveout) {
 void launch_movers(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a, int blocks, cudaStream_t st) {
     if (p.precision == UGKWP_MIXED) k_movers<float><<<blocks, 256, 0, st>>>(m, s, p, a);
     else k_movers<double><<<blocks, 256, 0, st>>>(m, s, p, a);
+}
+
+void launch_sample_scale_batch(const BatchChunk& c, int blocks, int precision, cudaStream_t st) {
+    if (precision == UGKWP_MIXED) k_sample_scale_b<float><<<blocks, 256, 0, st>>>(c);
+    else k_sample_scale_b<double><<<blocks, 256, 0, st>>>(c);
+}
+void launch_sample_write_batch(const BatchChunk& c, int blocks, int precision, cudaStream_t st) {
+    if (precision == UGKWP_MIXED) k_sample_write_b<float><<<blocks, 256, 0, st>>>(c);
+    else k_sample_write_b<double><<<blocks, 256, 0, st>>>(c);
+}
+namespace {
+template <class Real, bool KE>
+void track_batch_shape(const BatchChunk& c, const TrackShape& sh, int blocks, cudaStream_t st) {
+    if (sh.threads == 256) k_track_b<Real, KE, 256><<<blocks, 256, 0, st>>>(c);
+    else k_track_b<Real, KE, 128><<<blocks, 128, 0, st>>>(c);
+}
+}  // namespace
+void launch_track_batch(const BatchChunk& c, int precision, bool ke, const TrackShape& sh, int blocks,
+                        cudaStream_t st) {
+    if (precision == UGKWP_MIXED) {
+        if (ke) track_batch_shape<float, true>(c, sh, blocks, st);
+        else track_batch_shape<float, false>(c, sh, blocks, st);
+    } else {
+        if (ke) track_batch_shape<double, true>(c, sh, blocks, st);
+        else track_batch_shape<double, false>(c, sh, blocks, st);
+    }
+}
+void launch_movers_batch(const BatchChunk& c, int blocks, int precision, cudaStream_t st) {
+    if (precision == UGKWP_MIXED) k_movers_b<float><<<blocks, 256, 0, st>>>(c);
+    else k_movers_b<double><<<blocks, 256, 0, st>>>(c);
 }
 
 }  // namespace ugkwp

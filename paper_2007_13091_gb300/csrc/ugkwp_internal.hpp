@@ -191,6 +191,24 @@ struct DevState {
     int64_t* cnt64;       // [CNT_SLOTS]
 };
 
+// One member of a fused batch: a simulation's device structures for one step,
+// with its particle buffers in this step's roles.
+struct BatchMember {
+    DevMesh m;
+    DevState s;
+    DevParams p;
+    PartBufRaw a;   // this step's particles
+    PartBufRaw b;   // the buffer the survivors are written to
+    PartBufRaw mv;  // the movers
+};
+
+// The block a kernel body runs as: its index among the blocks that work on
+// the same simulation, and their number (blockIdx.x and gridDim.x of a launch
+// for one simulation).
+struct Blk {
+    int id, n;
+};
+
 struct MeshHost {
     int32_t nn = 0, nc = 0, nf = 0, nbf = 0;
     std::vector<double> xyz;
@@ -212,7 +230,7 @@ constexpr int GP_ATTEMPTS = 64;
 
 // Kernel launchers (stream-ordered, no synchronisation).
 constexpr int SCAN_BLOCK = 1024;
-inline int scan_blocks(int nc) { return (nc + SCAN_BLOCK - 1) / SCAN_BLOCK; }
+__host__ __device__ inline int scan_blocks(int nc) { return (nc + SCAN_BLOCK - 1) / SCAN_BLOCK; }
 
 void launch_reset(const DevMesh& m, const DevState& s, cudaStream_t st);
 void launch_cell_prep(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st);
@@ -269,6 +287,40 @@ void launch_prim_moments(const DevMesh& m, const DevState& s, const DevParams& p
                          double* out, cudaStream_t st);
 void launch_wbar(const DevMesh& m, const DevState& s, double* out, cudaStream_t st);
 void launch_kn_gll(const DevMesh& m, const DevState& s, const DevParams& p, double* out, cudaStream_t st);
+
+// ---- fused batches: one launch of each step kernel for a chunk of up to
+// BATCH_CHUNK members of a batch that share precision, order, K and sampling.
+// The chunk travels as the launch's parameter (read-only, like a single
+// simulation's structures).  Kernels over cells or faces give member i the
+// blocks off[cls][i] .. off[cls][i + 1] - 1 of the grid, on which it runs the
+// body its own launch would run; the particle kernels (sampling, tracking,
+// movers) take every member in turn on the whole grid.
+constexpr int BATCH_CHUNK = 13;
+enum BatchClass { BCL_RESET, BCL_CELLS, BCL_SCAN, BCL_GRAD, BCL_GPC, BCL_FLUX_O2, BCL_FLUX, BCL_N };
+struct BatchChunk {
+    int32_t n;
+    int32_t off[BCL_N][BATCH_CHUNK + 1];
+    BatchMember mem[BATCH_CHUNK];
+};
+static_assert(sizeof(BatchChunk) <= 32764, "a chunk must fit a launch's parameter space");
+int blocks_reset(int nc);        // grid of one simulation's reset launch
+int blocks_cells(int nc);        // one thread per cell, 256 per block
+int blocks_gp_coef(int nc);      // one thread per cell, 128 per block
+int gradient_threads();          // threads per block of the gradient kernel
+void launch_reset_batch(const BatchChunk& c, int blocks, cudaStream_t st);
+void launch_cell_prep_batch(const BatchChunk& c, int blocks, cudaStream_t st);
+void launch_sample_count_batch(const BatchChunk& c, int blocks, cudaStream_t st);
+void launch_scan_batch(const BatchChunk& c, int blocks, cudaStream_t st);
+void launch_cell_update_batch(const BatchChunk& c, int blocks, cudaStream_t st);
+void launch_gradients_batch(const BatchChunk& c, int blocks, cudaStream_t st);
+void launch_gp_coef_batch(const BatchChunk& c, int blocks, cudaStream_t st);
+void launch_face_flux_o2_batch(const BatchChunk& c, int blocks, cudaStream_t st);
+void launch_face_flux_batch(const BatchChunk& c, int blocks, cudaStream_t st);
+void launch_sample_scale_batch(const BatchChunk& c, int blocks, int precision, cudaStream_t st);
+void launch_sample_write_batch(const BatchChunk& c, int blocks, int precision, cudaStream_t st);
+void launch_track_batch(const BatchChunk& c, int precision, bool ke, const TrackShape& sh, int blocks,
+                        cudaStream_t st);
+void launch_movers_batch(const BatchChunk& c, int blocks, int precision, cudaStream_t st);
 
 // ---- adjoint of the frozen-particle wave map (first order)
 struct AdjBc {

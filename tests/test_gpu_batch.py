@@ -141,3 +141,31 @@ def test_batch_autotune_and_member_errors():
     with pytest.raises(ugkwp.UgkwpError, match="batch member 1"):
         b2.sync()
     b2.close()
+
+
+def test_fused_chunks_equal_members_stepped_alone():
+    """Fifteen members of one kind (MIXED, second order): two fused chunks
+    (13 and 2 members), each kernel one launch per chunk.  Uneven sizes and
+    Knudsen numbers; every member ends bit for bit where it ends alone, after
+    a graph-replayed pair and a direct step."""
+    import torch
+    cfgs = []
+    for k in range(15):
+        if k % 2:
+            cfgs.append(wl.cavity(n=4 + k % 4, N_ref=40 + 5 * k, Kn=0.02 * (1 + k), precision="mixed", order=2,
+                                  seed=100 + k))
+        else:
+            cfgs.append(wl.shock_tube(nx=12 + 3 * k, ny=2, nz=2, precision="mixed", order=2, U=0.1 * k,
+                                      Kn=10.0 ** (-3 + k / 5), N_ref=60, seed=100 + k))
+    for c in cfgs:
+        c["params"]["sampling"] = "energy_matched"
+    batched = [_sim(c, torch.cuda.Stream()) for c in cfgs]
+    alone = [_sim(c, torch.cuda.Stream()) for c in cfgs]
+    b = ugkwp.Batch(batched)
+    b.step(3)
+    b.sync()
+    for s in alone:
+        s.step(3)
+    for x, y in zip(batched, alone):
+        _assert_same(x, y)
+    b.close()
