@@ -53,6 +53,9 @@ TRACK_DRAM_BYTES = {"mixed": None, "fp64": None}
 MOVER_BYTES = {"mixed": 12 + 12 + 8 + 4 + 8, "fp64": 24 + 24 + 8 + 4 + 8}
 # int64 atomic additions per mover: -phi at the start cell, +phi at the end cell
 MOVER_ATOMICS = 10
+# binary64 pipe operations of one phi = m (1, u, |u|^2/2): MIXED 3 widenings,
+# 7 products and 3 sums; FP64 the products and sums
+MOVER_FP64_OPS = {"mixed": 13, "fp64": 10}
 # Binary64 flops per interior face of k_face_flux_o2 (the second-order wave flux):
 # ncu's executed dadd + dmul + 2 dfma per launch divided by the interior faces, on
 # this workload (profiles/); None until captured for the current kernel.
@@ -561,25 +564,25 @@ def gks_start_up(device, steps=20, warmup=3):
     return out
 
 
-def hypersonic(device, which, steps, warmup, gks_steps, spin_up=5, adjoint_K=0, kernel_times=True):
+def hypersonic(device, which, steps, warmup, gks_steps, spin_up=5, adjoint_K=0):
     """The hypersonic configurations at full size, MIXED, first order, with the
     paper's particle setting N_min = N_ref (Sec. 4.3, 4.4) and energy-matched
     sampling: Ma 4 past the unit cube (1,152,912 tets, Kn 0.1, N_ref 200) or
     Ma 8 past the blunt vehicle (2,770,032 tets, Kn 1e-3, T_w = 3 T_inf,
     N_ref 100).  Each starts with `gks_steps` gas-kinetic steps with local
     time steps from the free stream (the start-up of the steady cases), then
-    takes `spin_up` steps of the method and times `steps` more like the main
-    line.  With adjoint_K > 0 each functional (drag and wall heat flux of the
-    body, theta = the free stream and the wall) gets an adjoint call of
-    adjoint_K steps on a simulation of its own, right after its own start-up.
+    takes `spin_up` + `warmup` steps of the method and times up to `steps`
+    more, in chunks of 10, until the first device error.  With adjoint_K > 0
+    each functional (drag and wall heat flux of the body, theta = the free
+    stream and the wall) gets an adjoint call of adjoint_K steps on a
+    simulation of its own, right after its own start-up.
 
-    With N_ref particles per cell the method runs about 140 steps on the cube
-    and about 50 on the vehicle after the start-up before some cell's pressure
-    falls through zero (the base region behind the cube, the bow shock ahead
-    of the nose), so the cube times 100 steps after 20 and the vehicle 5
-    after 2, and each vehicle adjoint call (46 steps: the far field, 44 tets
-    from the body, reaches the functional after 46) starts from a fresh
-    start-up."""
+    With N_ref particles per cell the method runs on the order of 100 steps on
+    the cube and 50 on the vehicle after the start-up before some cell's
+    pressure falls through zero (the base region behind the cube, the bow shock
+    ahead of the nose); the line reports how many steps it timed and the error
+    that ended them.  A vehicle adjoint call takes 46 steps: the far field, 44
+    tets from the body, reaches the functional after 46."""
     import torch
     from paper_2007_13091_gb300 import ugkwp
     from paper_2007_13091_gb300 import workloads as wl
@@ -614,177 +617,47 @@ def hypersonic(device, which, steps, warmup, gks_steps, spin_up=5, adjoint_K=0, 
     out["gks_start_up"] = {"steps": gks_steps, "ms_per_step": ms / gks_steps,
                            "cell_steps_per_s": n * gks_steps / (ms * 1e-3),
                            "rho_min": float(W[0].min()), "p_min": float(p.min())}
-    sim.step(spin_up)
-    ms, moves, launches, kms, st = time_steps(sim, steps, warmup, 1, timing=kernel_times)
-    out.update({"value": moves / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
-                "spin_up_steps": spin_up, "warmup_steps": warmup,
-                "method_steps_after_start_up": spin_up + warmup + steps + (steps if kernel_times else 0),
-                "cell_steps_per_s": n * steps / (ms * 1e-3), "particles_per_step": moves / steps})
-    if kms:
-        kms.pop("_moves", None)
-        out["kernels_ms_per_step"] = {k: v / steps for k, v in kms.items()}
+    # timed in chunks of 10 steps (graph-replayed pairs, CUDA events on the
+    # stream) until `steps` steps or the first device error, which ends the
+    # run and is reported with the step it came in
+    sim.step(spin_up + warmup)
+    m0 = sim.step(0, stats=True)["n_moves_total"]
+    ms, done, err = 0.0, 0, None
+    while done < steps:
+        k = min(10, steps - done)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(k)
+        b.record(stream)
+        try:
+            st = sim.step(0, stats=True)
+        except ugkwp.UgkwpError as e:
+            err = {"error": str(e)[:200], "in_method_steps": [spin_up + warmup + done + 1, spin_up + warmup + done + k]}
+            break
+        ms += a.elapsed_time(b)
+        done += k
+        moves = st["n_moves_total"] - m0
+    out.update({"steps_timed": done, "spin_up_steps": spin_up, "warmup_steps": warmup,
+                "method_steps_after_start_up": spin_up + warmup + done, "ended_by": err})
+    if done:
+        out.update({"value": moves / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / done,
+                    "cell_steps_per_s": n * done / (ms * 1e-3), "particles_per_step": moves / done})
     sim.close()
     if adjoint_K:
         adj = {}
         for functional, name in ((0, "drag"), (1, "wall_heat_flux")):
             sim, _ = started(config(), stream)
             t1 = time.perf_counter()
-            r = sim.adjoint(functional, adjoint_K, [2])
-            adj[name] = {"J_and_grad": [float(v) for v in r], "ms_per_call": 1e3 * (time.perf_counter() - t1)}
+            try:
+                r = sim.adjoint(functional, adjoint_K, [2])
+                adj[name] = {"J_and_grad": [float(v) for v in r], "ms_per_call": 1e3 * (time.perf_counter() - t1)}
+            except ugkwp.UgkwpError as e:
+                adj[name] = {"error": str(e)[:200]}
             sim.close()
         out["adjoint"] = {"steps": adjoint_K, "theta": "(rho_inf, U_inf, T_w) = (1, 8 sqrt(5/3), 3)",
-                          "grad_order": "dJ/drho_inf, dJ/dU_inf, dJ/dT_w",
-                          "cell_steps_per_s": n * adjoint_K / (1e-3 * adj["drag"]["ms_per_call"]), **adj}
-    return out
-
-
-def shock_tube(device, steps=20, warmup=3, seeds=(1, 1002), oracle_steps=20):
-    """The 3D shock tube at full size (100x4x4 hexes x 6 = 9,600 tets, Sod
-    states, Kn 1e-2, N_ref 50, specular side walls, CFL 0.5, first order,
-    seed 1): `steps` steps in FP64 and in MIXED, device time over the whole
-    run from the initial state (the workload is those 20 steps, so nothing is
-    spun up; `warmup` steps of a separate simulation come first to load the
-    library's kernels and graphs), the per-field relative L2 of MIXED vs FP64
-    after the run with the FP64 seed-to-seed floor, and the CPU oracle over the
-    same `oracle_steps` steps."""
-    import torch
-    from paper_2007_13091_gb300 import ugkwp
-    from paper_2007_13091_gb300 import workloads as wl
-    out = {"workload": "3D shock tube [0,1]x[0,0.04]^2, 100x4x4 hexes x 6 = 9,600 tets, Sod states, Kn 1e-2, "
-                       "N_ref 50, specular side walls, CFL 0.5, first order, seed 1", "steps": steps}
-    fields = {}
-    for precision, seed in (("fp64", seeds[0]), ("mixed", seeds[0]), ("fp64", seeds[1])):
-        cfg = wl.shock_tube(precision=precision, seed=seed)
-        stream = torch.cuda.Stream(device=device)
-        w = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=stream)
-        w.step(warmup)
-        w.sync()
-        w.close()
-        sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=stream)
-        st0 = sim.step(0, stats=True)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        sim.step(steps)
-        b.record(stream)
-        b.synchronize()
-        ms = a.elapsed_time(b)
-        st1 = sim.step(0, stats=True)
-        P = sim.moments(ugkwp.PRIM)
-        fields[(precision, seed)] = {"rho": P[0], "U": P[1:4], "T": P[4], "p": P[0] * P[4]}
-        moves = st1["n_moves_total"] - st0["n_moves_total"]
-        if seed == seeds[0]:
-            out[precision] = {"value": moves / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
-                              "cell_steps_per_s": sim.n_cells * steps / (ms * 1e-3),
-                              "particles_per_step": moves / steps}
-        sim.close()
-    ref, mix, other = fields[("fp64", seeds[0])], fields[("mixed", seeds[0])], fields[("fp64", seeds[1])]
-    # velocity relative to the sound speed of the left state (the tube starts at rest)
-    c_left = math.sqrt(5.0 / 3.0)
-
-    def err(x, y):
-        e = {k: float(np.linalg.norm(x[k] - y[k]) / np.linalg.norm(y[k])) for k in ("rho", "T", "p")}
-        e["U"] = float(np.linalg.norm(x["U"] - y["U"]) / (c_left * math.sqrt(y["U"].shape[1])))
-        return e
-    out["field_error"] = {"after_steps": steps, "mixed_vs_fp64": err(mix, ref), "noise_floor_fp64_seed": err(other, ref),
-                          "U_scale": "sound speed of the left state"}
-    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
-    out["cpu_baseline"] = guarded(lambda: cpu_oracle_run(wl.shock_tube(precision="fp64", seed=seeds[0]), 0,
-                                                         oracle_steps, "3D shock tube 9,600 tets, FP64, the "
-                                                         f"whole {oracle_steps}-step run from the initial state"))
-    return out
-
-
-def gks_start_up(device, steps=20, warmup=3):
-    """Start-up steps of the gas-kinetic scheme (the method without particles,
-    Sec. 3.2; the initial fields of the steady cases, Sec. 4.3, 4.4) on the
-    cavity 24^3 at second order with the Prandtl fix at Pr = 2/3: cell-steps/s
-    with the global time step and with local time steps, CUDA events on the
-    simulation's stream around `steps` direct-launch steps."""
-    import torch
-    from paper_2007_13091_gb300 import ugkwp
-    from paper_2007_13091_gb300 import workloads as wl
-    cfg = wl.cavity(n=24, Kn=0.075, N_ref=100, precision="mixed", order=2)
-    cfg["params"]["Pr"] = 2.0 / 3.0
-    stream = torch.cuda.Stream(device=device)
-    sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=stream)
-    n = sim.n_cells
-    out = {"workload": "cavity 24^3 hexes x 6 = 82,944 tets, Kn 0.075, order 2, Pr 2/3, no particles", "n_cells": n}
-    for local in (False, True):
-        sim.gks_steps(warmup, local_dt=local)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        sim.gks_steps(steps, local_dt=local)
-        b.record(stream)
-        b.synchronize()
-        ms = a.elapsed_time(b)
-        out["local_dt" if local else "global_dt"] = {"ms_per_step": ms / steps,
-                                                      "cell_steps_per_s": n * steps / (ms * 1e-3)}
-    sim.sync()
-    sim.close()
-    return out
-
-
-def hypersonic(device, which, steps, warmup, gks_steps, spin_up=5, adjoint_K=0, kernel_times=True):
-    """The hypersonic configurations at full size, MIXED, first order: Ma 4 past
-    the unit cube (1,152,912 tets, Kn 0.1, N_ref 200) or Ma 8 past the blunt
-    vehicle (2,770,032 tets, Kn 1e-3, T_w = 3 T_inf, N_ref 100, energy-matched
-    sampling).  Each starts with `gks_steps` gas-kinetic steps with local time
-    steps from the free stream (the start-up of the steady cases), then takes
-    `spin_up` steps of the method and times `steps` more like the main line;
-    with adjoint_K > 0 one adjoint call per functional follows (drag and wall
-    heat flux of the body, theta = the free stream and the wall).
-
-    The blunt vehicle runs the method for about 50 steps after its start-up
-    before some cell's pressure falls through zero (the bow shock ahead of the
-    nose, where nearly all the gas is in particles and the wave part is their
-    small difference from W; energy-matched sampling and twice N_ref only
-    delay it), so it times 5 steps and its adjoint calls take 16 steps each:
-    dJ/dT_w, while the far field, 44 tets from the body, needs 46 steps to
-    reach it (the coarse mesh of the same configuration checks all three
-    derivatives in the tests)."""
-    import torch
-    from paper_2007_13091_gb300 import ugkwp
-    from paper_2007_13091_gb300 import workloads as wl
-    t0 = time.perf_counter()
-    if which == "cube":
-        cfg = wl.cube_flow()
-    else:
-        cfg = wl.blunt_vehicle()
-        cfg["params"]["sampling"] = "energy_matched"
-    stream = torch.cuda.Stream(device=device)
-    sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device, stream=stream)
-    n = sim.n_cells
-    out = {"workload": cfg["name"], "n_cells": n, "N_ref": cfg["params"]["N_ref"], "Kn": cfg["params"]["Kn"],
-           "sampling": cfg["params"].get("sampling", "pairs"), "setup_s": time.perf_counter() - t0}
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    sim.gks_steps(gks_steps, local_dt=True)
-    b.record(stream)
-    b.synchronize()
-    ms = a.elapsed_time(b)
-    sim.sync()
-    W = sim.moments(ugkwp.W)
-    U = W[1:4] / W[0]
-    p = (W[4] - 0.5 * W[0] * (U * U).sum(0)) / 1.5
-    out["gks_start_up"] = {"steps": gks_steps, "ms_per_step": ms / gks_steps,
-                           "cell_steps_per_s": n * gks_steps / (ms * 1e-3),
-                           "rho_min": float(W[0].min()), "p_min": float(p.min())}
-    sim.step(spin_up)
-    ms, moves, launches, kms, st = time_steps(sim, steps, warmup, 1, timing=kernel_times)
-    out.update({"value": moves / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
-                "cell_steps_per_s": n * steps / (ms * 1e-3), "particles_per_step": moves / steps})
-    if kms:
-        kms.pop("_moves", None)
-        out["kernels_ms_per_step"] = {k: v / steps for k, v in kms.items()}
-    if adjoint_K:
-        adj = {}
-        for functional, name in ((0, "drag"), (1, "wall_heat_flux")):
-            t1 = time.perf_counter()
-            r = sim.adjoint(functional, adjoint_K, [2])
-            adj[name] = {"J_and_grad": [float(v) for v in r], "ms_per_call": 1e3 * (time.perf_counter() - t1)}
-        out["adjoint"] = {"steps": adjoint_K, "theta": "(rho_inf, U_inf, T_w) = (1, 8 sqrt(5/3), 3)",
-                          "cell_steps_per_s": n * adjoint_K / (1e-3 * adj["drag"]["ms_per_call"]), **adj}
-    sim.close()
+                          "grad_order": "dJ/drho_inf, dJ/dU_inf, dJ/dT_w", **adj}
+        if "ms_per_call" in adj["drag"]:
+            out["adjoint"]["cell_steps_per_s"] = n * adjoint_K / (1e-3 * adj["drag"]["ms_per_call"])
     return out
 
 
@@ -930,18 +803,27 @@ def main():
                             "two k_track launches: the second starts when the wave flux is done) over "
                             f"{args.steps} further steps of the same run (direct launches, wave flux "
                             "overlapping on the second stream)"}
-    # the movers' flux pass (a8): the mover records it reads, and its int64 atomics
+    # the movers' flux pass (a8): bound by its arithmetic (binary64 pipe for
+    # phi, integer pipes for the fixed-point conversion); its binary64 work is
+    # one phi per mover and a second one per wall hit
     movers_ms = kms.get("movers", 0.0) / args.steps
     n_movers = int(st["n_movers"])
+    n_wall = int(st["n_wall_hits"])
+    fp64_meas = None
     roof_movers = None
     if movers_ms > 0.0:
+        fp64_meas = guarded(fp64_peak_measured)
+        ops = MOVER_FP64_OPS[args.precision] * (n_movers + n_wall)
+        ach_ops = ops / (movers_ms * 1e-3) / 1e9
+        peak_ops = fp64_meas * 1e3 / 2.0 if isinstance(fp64_meas, float) else None
         mb = MOVER_BYTES[args.precision] * n_movers
-        ach_m = mb / (movers_ms * 1e-3) / 1e9
         roof_movers = {"kernel": "k_movers (a8: binary64 counting flux of the particles that changed cell, met a "
-                                 "wall or left)", "bound": "hbm", "achieved": ach_m, "peak": peak, "unit": "GB/s",
-                       "frac": ach_m / peak, "peak_kind": f"{peak_kind} HBM copy", "traffic": None,
-                       "algorithmic_bytes_per_launch": mb, "bytes_per_mover": MOVER_BYTES[args.precision],
-                       "movers_per_launch": n_movers, "ms_per_launch": movers_ms,
+                                 "wall or left)", "bound": "alu", "achieved": ach_ops, "peak": peak_ops,
+                       "unit": "Gop/s (binary64 pipe operations)", "frac": ach_ops / peak_ops if peak_ops else None,
+                       "peak_kind": "measured: cuBLAS DGEMM rate on this GPU / 2 (one FMA = 2 flops per pipe slot)",
+                       "traffic": None, "fp64_ops_per_phi": MOVER_FP64_OPS[args.precision],
+                       "movers_per_launch": n_movers, "wall_hits_per_launch": n_wall, "ms_per_launch": movers_ms,
+                       "bytes_read_per_launch": mb, "hbm_gbs": mb / (movers_ms * 1e-3) / 1e9,
                        "int64_atomics_per_s": MOVER_ATOMICS * n_movers / (movers_ms * 1e-3),
                        "timing": "CUDA events on the library's stream around each launch"}
     roof_flux = None
@@ -954,7 +836,8 @@ def main():
         except OSError:
             pass
         fp64_nominal = props.multi_processor_count * FP64_FMA_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-        fp64_meas = guarded(fp64_peak_measured)
+        if fp64_meas is None:
+            fp64_meas = guarded(fp64_peak_measured)
         fp64_peak = fp64_meas if isinstance(fp64_meas, float) else fp64_nominal
         flux_ms = kms["flux_o2"] / args.steps
         n_if = sim.n_faces - sim.n_bfaces
@@ -1022,9 +905,8 @@ def main():
         out["gp1_sampling"] = guarded(lambda: gp1_sampling(device, args.steps, args.warmup, launch_cfg))
         out["diatomic"] = guarded(lambda: diatomic(device, args.steps, args.warmup, launch_cfg))
         out["shock_tube"] = guarded(lambda: shock_tube(device))
-        out["cube_ma4"] = guarded(lambda: hypersonic(device, "cube", 100, 3, 300, spin_up=17, kernel_times=False))
-        out["blunt_vehicle"] = guarded(lambda: hypersonic(device, "vehicle", 5, 3, 1200, spin_up=2, adjoint_K=46,
-                                                          kernel_times=False))
+        out["cube_ma4"] = guarded(lambda: hypersonic(device, "cube", 100, 3, 300, spin_up=17))
+        out["blunt_vehicle"] = guarded(lambda: hypersonic(device, "vehicle", 40, 3, 1200, spin_up=2, adjoint_K=46))
         out["cpu_baseline"] = cpu_baseline(args.cpu_steps)
         out["cpu_baseline_by_config"] = {
             "cavity": out["cpu_baseline"],
