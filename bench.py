@@ -416,6 +416,76 @@ def batched(precision, steps, warmup, device):
                         f"seed 4, order {ORDER}, {precision}"}
 
 
+def batched_pairs(steps, warmup, device, launch_cfg):
+    """The MIXED batch with the printed pair sampling (Sec. 2.4 (b)) instead of
+    the energy-matched option, timed over `steps` steps after `warmup` from the
+    start with the given launch configuration (no autotuner trials, so that it
+    runs before the rarefied moving tubes fail); a device error ends it and is
+    reported with the steps done."""
+    import torch
+    from paper_2007_13091_gb300 import ugkwp
+    from paper_2007_13091_gb300 import workloads as wl
+    cases = wl.batch_instances(precision="mixed", order=ORDER, cap_factor=4.0, sampling="maxwell")
+    sims = [ugkwp.Simulation(c["mesh"], c["W0"], c["params"], device=device, stream=torch.cuda.Stream(device=device))
+            for c in cases]
+    for s in sims:
+        ugkwp.ugkwp_set_launch_cfg(s.handle, launch_cfg["particle_blocks"], launch_cfg["wave_blocks"],
+                                   launch_cfg["track_threads"], launch_cfg["smem_carveout"])
+    b = ugkwp.Batch(sims)
+    out = {"sampling": "pairs (printed)", "warmup": warmup}
+    try:
+        b.step(warmup)
+        b.sync()
+        m0 = sum(s.step(0, stats=True)["n_moves_total"] for s in sims)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(b.stream)
+        b.step(steps)
+        e1.record(b.stream)
+        b.sync()
+        ms = e0.elapsed_time(e1)
+        m1 = sum(s.step(0, stats=True)["n_moves_total"] for s in sims)
+        out.update({"value": (m1 - m0) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+                    "particles_per_step": (m1 - m0) / steps})
+    except ugkwp.UgkwpError as e:
+        out["error"] = str(e)[:200]
+    b.close()
+    for s in sims:
+        s.close()
+    return out
+
+
+def batched_field_error(device, steps=10):
+    """The batch's MIXED vs FP64 field error: both batches (energy-matched, the
+    bench's sampling) from the initial states and seeds, `steps` steps, per
+    field relative L2 over all members' cells, with the FP64 seed-to-seed
+    noise floor (every member's seed + 1)."""
+    import torch
+    from paper_2007_13091_gb300 import ugkwp
+    from paper_2007_13091_gb300 import workloads as wl
+
+    def fields(precision, seed_shift):
+        cases = wl.batch_instances(precision=precision, order=ORDER, cap_factor=4.0)
+        for c in cases:
+            c["params"]["seed"] += seed_shift
+        sims = [ugkwp.Simulation(c["mesh"], c["W0"], c["params"], device=device,
+                                 stream=torch.cuda.Stream(device=device)) for c in cases]
+        b = ugkwp.Batch(sims)
+        b.step(steps)
+        b.sync()
+        P = [s.moments(ugkwp.PRIM) for s in sims]
+        b.close()
+        for s in sims:
+            s.close()
+        P = np.concatenate(P, axis=1)
+        return {"rho": P[0], "T": P[4], "p": P[0] * P[4]}
+
+    a, b, c = fields("mixed", 0), fields("fp64", 0), fields("fp64", 1)
+
+    def err(x, y):
+        return {k: float(np.linalg.norm(x[k] - y[k]) / np.linalg.norm(y[k])) for k in ("rho", "T", "p")}
+    return {"after_steps": steps, "mixed_vs_fp64": err(a, b), "noise_floor_fp64_seed": err(c, b)}
+
+
 def adjoint(device, K=10):
     """The hand-written adjoint of the frozen-particle wave map (first order):
     gradient of the drag on the side walls of a channel with respect to
@@ -898,6 +968,8 @@ def main():
             r = {"mixed": batched("mixed", args.steps, args.warmup, device),
                  "fp64": batched("fp64", args.steps, args.warmup, device)}
             r["mixed_over_fp64"] = r["mixed"]["value"] / r["fp64"]["value"]
+            r["mixed_pair_sampling"] = guarded(lambda: batched_pairs(20, 3, device, r["mixed"]["launch_cfg"]))
+            r["field_error"] = guarded(lambda: batched_field_error(device))
             return r
         out["batched"] = guarded(both)
         out["adjoint"] = guarded(lambda: adjoint(device))

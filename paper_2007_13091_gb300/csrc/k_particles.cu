@@ -616,12 +616,13 @@ template <class Real> struct Ended {
 };
 
 // Walks that did not end in their first tet wait in shared memory (structure
-// of arrays, QCAP entries per block) until half a block of them has gathered;
-// the block then walks them on in full warps.  An entry holds the walk state,
+// of arrays, QCAP entries per block) until a tile's worth of them has
+// gathered; the block then walks one tile's worth on in full warps.  Before a
+// tile's pushes fewer than T walks wait, so 2T entries always suffice.  An entry holds the walk state,
 // the particle's internal energy (KE) and its slot in the buffer, from which
 // the rest of the particle is read again when the walk ends.
 template <class Real, bool KE, int T> struct WalkQueue {
-    static constexpr int QCAP = T + T / 2;
+    static constexpr int QCAP = 2 * T;
     Real x0[3][QCAP], u[3][QCAP], t0[QCAP], t_end[QCAP], ee[KE ? QCAP : 1];
     int tet[QCAP], last[QCAP], ncross[QCAP], nrefl[QCAP], nwall[QCAP], flags[QCAP];  // flags: status | coll << 3
     long long slot[QCAP];
@@ -879,10 +880,10 @@ __device__ __forceinline__ void track_body(const DevMesh& m, const DevState& s, 
             }
         }
         emit(e, have_tile, 0);
-        // ---- the queued walks, in full warps once half a block of them has
+        // ---- the queued walks, in full warps once a tile's worth of them has
         // gathered (or once the tiles are done)
         const int qc = sh_qc;  // block-uniform: set between the round's barriers
-        if (qc >= THREADS / 2 || (!have_tile && qc > 0)) {
+        if (qc >= THREADS || (!have_tile && qc > 0)) {
             const int take = qc < THREADS ? qc : THREADS;
             Ended<Real> f;
             f.active = f.survivor = f.mover = f.exited = false;
