@@ -47,7 +47,7 @@ TRACK_BYTES_PER_CELL = {"mixed": 80 + 8, "fp64": 144 + 8}
 # launches) on this workload, from the ncu capture summarised in
 # profiles/k_track_cavity24_mixed.md; set to None whenever the
 # kernel changes until it is captured again
-TRACK_DRAM_BYTES = {"mixed": 1230374656 + 1073810176 + 47872, "fp64": None}
+TRACK_DRAM_BYTES = {"mixed": 1229627648 + 1073300224 + 48128, "fp64": None}
 # bytes the movers' flux kernel reads per mover (start and end velocity, mass,
 # start cell, end cell and exit flag), MIXED / FP64
 MOVER_BYTES = {"mixed": 12 + 12 + 8 + 4 + 8, "fp64": 24 + 24 + 8 + 4 + 8}

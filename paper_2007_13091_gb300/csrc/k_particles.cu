@@ -342,6 +342,10 @@ template <> struct Trk<float> {
         nx = v.x; ny = v.y; nz = v.z; d = v.w;
     }
     __device__ static __forceinline__ int4 nbv(const DevMesh& m, int tet) { return m.trk_f[tet].nb; }
+    // the record is one 128-byte line
+    __device__ static __forceinline__ void prefetch(const DevMesh& m, int tet) {
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(m.trk_f + tet));
+    }
     __device__ static __forceinline__ float tau(const DevState& s, int c) { return s.tauf[c]; }
     __device__ static __forceinline__ float tf(float tau, unsigned long long r) {
         return -(tau * dm::f_log(dm::u01f(r)));
@@ -354,6 +358,12 @@ template <> struct Trk<double> {
         nx = v.x; ny = v.y; nz = v.z; d = v.w;
     }
     __device__ static __forceinline__ int4 nbv(const DevMesh& m, int tet) { return m.trk_d[tet].nb; }
+    // the 144-byte record starts on a 16-byte boundary, so it spans two lines
+    __device__ static __forceinline__ void prefetch(const DevMesh& m, int tet) {
+        const char* r = reinterpret_cast<const char*>(m.trk_d + tet);
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(r));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(r + sizeof(TrkD) - 1));
+    }
     __device__ static __forceinline__ double tau(const DevState& s, int c) { return s.tau[c]; }
     __device__ static __forceinline__ double tf(double tau, unsigned long long r) {
         return -(tau * dm::d_log(dm::u01d(r)));
@@ -460,15 +470,22 @@ __device__ __forceinline__ bool fixed_of_mass(double m, int e, long long& q) {
 
 // Thread 0's source of tiles: grabs of TILE_GRAB consecutive tiles from the
 // global counter (one atomic per grab), handed out in order, so the tiles a
-// block walks increase.  Returns the first particle index of the next tile.
+// block walks increase.  The grab after the current one is reserved when the
+// current one starts, so its atomic completes while the current grab's tiles
+// are walked (a block stops at its first tile past the end, and every grab it
+// still holds then lies past the end too).  Returns the first particle index
+// of the next tile.
 struct TileQueue {
-    long long next = 0, end = 0;
+    long long next = 0, end = 0, ahead = -1;
 };
 
 __device__ __forceinline__ long long next_tile(TileQueue& q, int64_t* ctr, int T) {
     if (q.next == q.end) {
-        q.next = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(ctr), 1ULL) * TILE_GRAB;
+        const long long g =
+            q.ahead >= 0 ? q.ahead : (long long)atomicAdd(reinterpret_cast<unsigned long long*>(ctr), 1ULL);
+        q.next = g * TILE_GRAB;
         q.end = q.next + TILE_GRAB;
+        q.ahead = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(ctr), 1ULL);
     }
     return (q.next++) * T;
 }
@@ -679,15 +696,13 @@ __device__ __forceinline__ void track_body(const DevMesh& m, const DevState& s, 
         // with the same end cell take consecutive slots from the cell's count
         // (one atomic per group); the count is also the cell's survivor count
         // N_left of the next step.  A survivor beyond its bucket takes an
-        // overflow slot after the buckets.
+        // overflow slot after the buckets.  The group's first slot is read
+        // after the round's barriers, so the atomic's round trip overlaps them.
         const int key = e.survivor ? e.tet : -1;
-        int srank = 0;
-        {
-            const unsigned peers = __match_any_sync(FULL, key);
-            const int leader = __ffs(peers) - 1;
-            if (lane == leader && key >= 0) srank = atomicAdd(&s.nleft_next[key], __popc(peers));
-            srank = __shfl_sync(FULL, srank, leader) + __popc(peers & ((1u << lane) - 1u));
-        }
+        const unsigned peers = __match_any_sync(FULL, key);
+        const int leader = __ffs(peers) - 1;
+        int sfirst = 0;
+        if (lane == leader && key >= 0) sfirst = atomicAdd(&s.nleft_next[key], __popc(peers));
         // survivors' fixed-point mass per end cell: segmented reduction over
         // lanes with equal keys in a row, one atomic per run
         {
@@ -732,6 +747,7 @@ __device__ __forceinline__ void track_body(const DevMesh& m, const DevState& s, 
             sh_tile[par ^ 1] = advance ? next_tile(tq, &s.cnt64[CNT_TILE], THREADS) : sh_tile[par];
         }
         __syncthreads();
+        const int srank = __shfl_sync(FULL, sfirst, leader) + __popc(peers & ((1u << lane) - 1u));
         if (e.survivor) {
             long long j = -1;
             if (srank < s.wcap[e.tet]) {
@@ -829,6 +845,8 @@ __device__ __forceinline__ void track_body(const DevMesh& m, const DevState& s, 
             if constexpr (KE) e_i = b.e[i];
             const int c0 = i < n ? cell_i : -1;
             if (c0 >= 0) {
+                // the start tet's record is on its way to L1 during the t_f draw
+                Trk<Real>::prefetch(m, c0);
                 e.id = id_i;
                 e.mm = m_i;
                 e.es = e_i;
