@@ -11,7 +11,8 @@ int64 fixed-point particle flux).  A step is one full UGKWP time step.
   field_error MIXED vs FP64 after a fixed number of steps, with the Monte-Carlo
              noise floor (two FP64 runs with different seeds)
   e2e        per step: state import from host buffers, step, W back to host
-  batched    64 independent instances in one graph, MIXED and FP64
+  batched    64 independent instances in one graph, MIXED and FP64; 8 copies of
+             the cavity as one batch against one of them stepped alone
   adjoint    the frozen-particle wave adjoint on a channel
   gks_start_up the particle-free start-up steps, global and local time steps
   gp1_sampling the workload with first-order g_p sampling
@@ -414,6 +415,55 @@ def batched(precision, steps, warmup, device):
             "workload": "64 instances (even: shock tubes moving at Mach M, N_ref 50; odd: cavities with lid "
                         "Mach M, N_ref 100), 2k-60k tets each, Kn log-uniform [1e-4, 1], M uniform [0.1, 3], "
                         f"seed 4, order {ORDER}, {precision}"}
+
+
+def batched_cavities(steps, warmup, device, members=8, n=24, spin_up=500):
+    """The batch with the single instance's work per member: `members` copies
+    of the bench's cavity (n^3 x 6 tets, Kn 0.075, N_ref 100, MIXED, the
+    printed pair sampling of Sec. 2.4 (b)) with seeds 2, 3, ...; stepped as one
+    batch for `spin_up` steps (the population settles), autotuned and timed.
+    Beside it, member 0 stepped alone from the state the batch left it in,
+    autotuned and timed the same way: the batch's moves/s over its members'
+    own."""
+    import torch
+    from paper_2007_13091_gb300 import ugkwp
+    from paper_2007_13091_gb300 import workloads as wl
+    cases = [wl.cavity(n=n, N_ref=100, precision="mixed", order=ORDER, seed=2 + k) for k in range(members)]
+    sims = [ugkwp.Simulation(c["mesh"], c["W0"], c["params"], device=device, stream=torch.cuda.Stream(device=device))
+            for c in cases]
+    b = ugkwp.Batch(sims)
+    b.step(spin_up)
+    b.sync()
+    best = b.autotune(2)
+    b.step(warmup)
+    b.sync()
+    m0 = sum(s.step(0, stats=True)["n_moves_total"] for s in sims)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.step(steps)
+    e1.record(b.stream)
+    b.sync()
+    ms = e0.elapsed_time(e1)
+    m1 = sum(s.step(0, stats=True)["n_moves_total"] for s in sims)
+    n_cells = sum(s.n_cells for s in sims)
+    b.close()
+    for s in sims[1:]:
+        s.close()
+    solo = sims[0]
+    cfg1 = ugkwp.ugkwp_autotune(solo.handle, 4)
+    ms1, mv1, _, _, _ = time_steps(solo, steps, warmup, 1, timing=False)
+    solo.close()
+    value = (m1 - m0) / (ms * 1e-3)
+    one = mv1 / (ms1 * 1e-3)
+    return {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "instances": members, "n_cells": n_cells,
+            "particles_per_step": (m1 - m0) / steps, "cell_steps_per_s": n_cells * steps / (ms * 1e-3),
+            "launch_cfg": best, "sampling": "pairs (printed)",
+            "member_alone": {"value": one, "unit": UNIT, "ms_per_step": ms1 / steps,
+                             "particles_per_step": mv1 / steps, "launch_cfg": cfg1},
+            "batch_over_member_alone": value / one,
+            "workload": f"{members} lid-driven cavities {n}^3 hexes x 6 = {6 * n ** 3} tets each "
+                        f"({n_cells} tets in all), Kn 0.075, N_ref 100, lid Mach 0.16, order {ORDER}, MIXED, "
+                        f"printed pair sampling, seeds 2-{1 + members}, timed after {spin_up} spin-up steps"}
 
 
 def batched_pairs(steps, warmup, device, launch_cfg):
@@ -970,6 +1020,7 @@ def main():
             r["mixed_over_fp64"] = r["mixed"]["value"] / r["fp64"]["value"]
             r["mixed_pair_sampling"] = guarded(lambda: batched_pairs(20, 3, device, r["mixed"]["launch_cfg"]))
             r["field_error"] = guarded(lambda: batched_field_error(device))
+            r["equal_work_cavities"] = guarded(lambda: batched_cavities(args.steps, args.warmup, device))
             return r
         out["batched"] = guarded(both)
         out["adjoint"] = guarded(lambda: adjoint(device))

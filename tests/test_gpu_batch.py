@@ -169,3 +169,22 @@ def test_fused_chunks_equal_members_stepped_alone():
     for x, y in zip(batched, alone):
         _assert_same(x, y)
     b.close()
+
+
+def test_fused_chunk_with_pair_sampling_equals_members_stepped_alone():
+    """Five cavities with the printed pair sampling (Sec. 2.4 (b)), one fused
+    chunk: every member ends bit for bit where it ends alone, after two
+    graph-replayed pairs and a direct step."""
+    import torch
+    cfgs = [wl.cavity(n=5 + k, N_ref=50 + 10 * k, Kn=0.075 * (1 + k), precision="mixed", order=2, seed=200 + k)
+            for k in range(5)]
+    batched = [_sim(c, torch.cuda.Stream()) for c in cfgs]
+    alone = [_sim(c, torch.cuda.Stream()) for c in cfgs]
+    b = ugkwp.Batch(batched)
+    b.step(5)
+    b.sync()
+    for s in alone:
+        s.step(5)
+    for x, y in zip(batched, alone):
+        _assert_same(x, y)
+    b.close()
