@@ -344,12 +344,16 @@ def field_error_averaged(device, spin=300, avg=600):
             "noise_floor_fp64_seed": err(c, b)}
 
 
-def e2e(cfg, steps, device):
+def e2e(cfg, steps, device, launch_cfg=None):
     """Per step through the C-ABI with host buffers: import the state from host
-    arrays, one step, read W back to host memory."""
+    arrays, one step, read W back to host memory (at `launch_cfg`, the launch
+    configuration a user sets once, if given)."""
     import torch
     from paper_2007_13091_gb300 import ugkwp
     sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device)
+    if launch_cfg is not None:
+        ugkwp.ugkwp_set_launch_cfg(sim.handle, launch_cfg["particle_blocks"], launch_cfg["wave_blocks"],
+                                   launch_cfg["track_threads"], launch_cfg["smem_carveout"])
     sim.step(SPIN_UP)
     state = sim.state()
 
@@ -375,9 +379,10 @@ def e2e(cfg, steps, device):
     t1 = time.perf_counter()
     sim.close()
     return {"value": moves / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "steps": steps, "particles": int(n),
-            "per_step": "ugkwp_import_state of the whole state from page-locked host arrays (validated and "
-                        "converted to the particle precision on the host), one step, W read back to host memory"}
+            "steps": steps, "particles": int(n), "ms_per_step": (t1 - t0) * 1e3 / steps, "launch_cfg": launch_cfg,
+            "per_step": "ugkwp_import_state of the whole state from page-locked host arrays (copied as they "
+                        "are, checked and converted to the particle precision on the device), one step, W read "
+                        "back to host memory"}
 
 
 def batched(precision, steps, warmup, device):
@@ -1012,7 +1017,7 @@ def main():
         out["mixed_over_fp64"] = out["value"] / out["fp64"]["value"]
         out["field_error"] = guarded(lambda: field_error((1, 10, 20), device))
         out["field_error_time_averaged"] = guarded(lambda: field_error_averaged(device))
-        out["e2e"] = e2e(cfg, 3, device)
+        out["e2e"] = e2e(cfg, 5, device, launch_cfg)
 
         def both():
             r = {"mixed": batched("mixed", args.steps, args.warmup, device),

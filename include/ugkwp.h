@@ -264,12 +264,14 @@ int ugkwp_moments(ugkwp_sim* s, int32_t which, double* out, int32_t out_on_devic
  * t, exps); ugkwp_export_state also fills the arrays (which must hold
  * n_particles entries).  ugkwp_import_state replaces the simulation state
  * (W, particles, step, t, exps) from host arrays.  Synchronising.  The
- * particles are validated and converted to the particle precision on the
- * host (in parallel) before anything on the device changes; the converted
- * positions and velocities go through a page-locked host staging buffer
- * (6, or 7 with K > 0, times n_particles times the particle size in bytes)
- * that the simulation keeps between imports and frees with ugkwp_free.
- * Host arrays in page-locked memory copy fastest.
+ * arrays are copied to the device as they are and every particle is checked
+ * and converted to the particle precision there, into the simulation's spare
+ * particle buffer, before its state changes: a rejected image leaves the
+ * simulation as it was.  In mixed precision the binary64 positions,
+ * velocities and internal energies pass through a device staging buffer
+ * (3 n_cells + 6 n_particles doubles, 7 n_particles with K > 0, plus 256
+ * bytes) allocated by the call, kept between imports and freed with
+ * ugkwp_free.  Host arrays in page-locked memory copy fastest.
  * Errors: UGKWP_E_ARG, UGKWP_E_CAPACITY, UGKWP_E_STATE (particle outside the
  * mesh index range or not representable in the particle precision). */
 int ugkwp_state_info(ugkwp_sim* s, ugkwp_state* st);

@@ -36,10 +36,11 @@ struct ugkwp_sim {
     PartBufRaw Mv;     // the step's movers (particles whose counting flux is non-zero)
     std::vector<double> anchor;  // [3*nc] anchors of the tets (mixed mode; 0 in binary64)
     cudaStream_t stream = nullptr;
-    // page-locked host staging of ugkwp_import_state (particle positions and
-    // velocities in the particle precision), kept between imports
-    void* pin = nullptr;
-    size_t pin_bytes = 0;
+    // device staging of ugkwp_import_state (an error word, the tets' anchors
+    // and the image's binary64 positions, velocities and internal energies in
+    // mixed mode), kept between imports
+    void* imp = nullptr;
+    size_t imp_bytes = 0;
     int64_t step = 0;
     int32_t n_bc = 0;
     size_t real_size = 8;
@@ -80,7 +81,7 @@ struct ugkwp_sim {
         if (sampled) cudaEventDestroy(sampled);
         if (tracked) cudaEventDestroy(tracked);
         if (gp_ready) cudaEventDestroy(gp_ready);
-        if (pin) cudaFreeHost(pin);
+        if (imp) cudaFree(imp);
         if (wave) cudaStreamDestroy(wave);
         if (aux) cudaStreamDestroy(aux);
     }
@@ -1097,88 +1098,66 @@ int ugkwp_import_state(ugkwp_sim* s, const ugkwp_state* st) {
     const int nc = s->M.nc;
     const size_t rs = s->real_size;
     if (s->A.e && n > 0 && !st->e) return fail(UGKWP_E_ARG, "internal energies (e) needed when K > 0");
-    // validate and convert the particles on the host, in parallel, into the
-    // page-locked staging (x[3], u[3], e in the particle precision), before
-    // anything on the device changes
-    const int ncomp = s->A.e ? 7 : 6;
-    const size_t need = (size_t)ncomp * (size_t)n * rs;
-    if (need > s->pin_bytes) {
-        if (s->pin) cudaFreeHost(s->pin);
-        s->pin = nullptr;
-        s->pin_bytes = 0;
-        CU(cudaHostAlloc(&s->pin, need, cudaHostAllocDefault));
-        s->pin_bytes = need;
+    // The image goes to the device as the caller holds it: cell, m and id into
+    // the spare buffer B; x, u and e into B as well with binary64 particles,
+    // else into a device staging buffer (binary64, with the tets' anchors),
+    // from which k_import checks every particle and converts it into B.  The
+    // buffers swap only when every particle passed, so a rejected image
+    // leaves the simulation as it was.
+    const bool mixed = rs == 4;
+    const bool ke = s->A.e != nullptr;
+    const size_t hdr = 256;  // the error word
+    const size_t need =
+        hdr + (mixed ? (3 * (size_t)nc + (size_t)(ke ? 7 : 6) * (size_t)n) * sizeof(double) : 0);
+    if (need > s->imp_bytes) {
+        if (s->imp) cudaFree(s->imp);
+        s->imp = nullptr;
+        s->imp_bytes = 0;
+        CU(cudaMalloc(&s->imp, need));
+        s->imp_bytes = need;
     }
-    char* stage = static_cast<char*>(s->pin);
-    auto comp = [&](int c) { return stage + (size_t)c * (size_t)n * rs; };  // 0-2 x, 3-5 u, 6 e
-    // per range: 0 ok, else the first problem found (1 cell, 2 negative e,
-    // 3 e not binary32, 4 x or u not binary32)
-    auto convert = [&](int64_t lo, int64_t hi) -> int {
-        for (int64_t i = lo; i < hi; ++i) {
-            if (st->cell[i] < 0 || st->cell[i] >= nc) return 1;
-            if (s->A.e) {
-                const double ev = st->e[i];
-                if (!(ev >= 0.0)) return 2;
-                if (rs == 4) {
-                    const float ef = (float)ev;
-                    if ((double)ef != ev) return 3;
-                    ((float*)comp(6))[i] = ef;
-                } else {
-                    ((double*)comp(6))[i] = ev;
-                }
-            }
-            for (int d = 0; d < 3; ++d) {
-                const double xv = st->x[d * n + i], uv = st->u[d * n + i];
-                if (rs == 4) {
-                    // mixed mode: the offset from the anchor of the particle's tet
-                    const double A = s->anchor[3 * (size_t)st->cell[i] + d];
-                    const double xl = xv - A;
-                    const float xf = (float)xl, uf = (float)uv;
-                    if ((double)xf != xl || A + xl != xv || (double)uf != uv) return 4;
-                    ((float*)comp(d))[i] = xf;
-                    ((float*)comp(3 + d))[i] = uf;
-                } else {
-                    ((double*)comp(d))[i] = xv;
-                    ((double*)comp(3 + d))[i] = uv;
-                }
-            }
-        }
-        return 0;
-    };
-    const unsigned hw = std::thread::hardware_concurrency();
-    const int nth = n < (1 << 16) ? 1 : (int)std::min<unsigned>(hw ? hw : 1, 16u);
-    std::vector<int> bad(nth, 0);
-    {
-        std::vector<std::thread> pool;
-        const int64_t per = (n + nth - 1) / nth;
-        for (int t = 1; t < nth; ++t)
-            pool.emplace_back([&, t] { bad[t] = convert(std::min<int64_t>(n, t * per), std::min<int64_t>(n, (t + 1) * per)); });
-        bad[0] = convert(0, std::min<int64_t>(n, per));
-        for (auto& th : pool) th.join();
-    }
-    for (int t = 0; t < nth; ++t) {
-        if (bad[t] == 1) return fail(UGKWP_E_STATE, "particle cell out of range");
-        if (bad[t] == 2) return fail(UGKWP_E_STATE, "negative internal energy");
-        if (bad[t] == 3) return fail(UGKWP_E_STATE, "internal energy not representable in binary32");
-        if (bad[t] == 4) return fail(UGKWP_E_STATE, "particle state not representable in binary32");
-    }
+    char* base = static_cast<char*>(s->imp);
+    unsigned long long* err = reinterpret_cast<unsigned long long*>(base);
+    double* anc = reinterpret_cast<double*>(base + hdr);
+    double* xs = anc + 3 * (size_t)nc;
+    double* us = xs + 3 * (size_t)n;
+    double* es = (mixed && ke) ? us + 3 * (size_t)n : nullptr;
     cudaStream_t q = s->stream;
-    CU(cudaStreamSynchronize(q));
-    for (int d = 0; d < 3; ++d)
-        if (n) {
-            CU(cudaMemcpyAsync(s->A.x[d], comp(d), (size_t)n * rs, cudaMemcpyHostToDevice, q));
-            CU(cudaMemcpyAsync(s->A.u[d], comp(3 + d), (size_t)n * rs, cudaMemcpyHostToDevice, q));
-        }
-    if (n && s->A.e) CU(cudaMemcpyAsync(s->A.e, comp(6), (size_t)n * rs, cudaMemcpyHostToDevice, q));
+    CU(cudaStreamSynchronize(q));  // B is free once the bound stream's steps are done
+    CU(cudaMemsetAsync(err, 0xff, sizeof(unsigned long long), q));
     if (n) {
-        CU(cudaMemcpyAsync(s->A.m, st->m, (size_t)n * 8, cudaMemcpyHostToDevice, q));
-        CU(cudaMemcpyAsync(s->A.cell, st->cell, (size_t)n * 4, cudaMemcpyHostToDevice, q));
-        CU(cudaMemcpyAsync(s->A.id, st->id, (size_t)n * 8, cudaMemcpyHostToDevice, q));
+        CU(cudaMemcpyAsync(s->B.m, st->m, (size_t)n * 8, cudaMemcpyHostToDevice, q));
+        CU(cudaMemcpyAsync(s->B.cell, st->cell, (size_t)n * 4, cudaMemcpyHostToDevice, q));
+        CU(cudaMemcpyAsync(s->B.id, st->id, (size_t)n * 8, cudaMemcpyHostToDevice, q));
+        if (mixed) {
+            CU(cudaMemcpyAsync(anc, s->anchor.data(), 3 * (size_t)nc * sizeof(double), cudaMemcpyHostToDevice, q));
+            CU(cudaMemcpyAsync(xs, st->x, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, q));
+            CU(cudaMemcpyAsync(us, st->u, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, q));
+            if (ke) CU(cudaMemcpyAsync(es, st->e, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, q));
+        } else {
+            for (int d = 0; d < 3; ++d) {
+                CU(cudaMemcpyAsync(s->B.x[d], st->x + (size_t)d * n, (size_t)n * 8, cudaMemcpyHostToDevice, q));
+                CU(cudaMemcpyAsync(s->B.u[d], st->u + (size_t)d * n, (size_t)n * 8, cudaMemcpyHostToDevice, q));
+            }
+            if (ke) CU(cudaMemcpyAsync(s->B.e, st->e, (size_t)n * 8, cudaMemcpyHostToDevice, q));
+        }
+        launch_import(nc, n, mixed, anc, xs, us, es, s->B, err, q);
+        CU(cudaGetLastError());
     }
-    CU(cudaMemcpyAsync(s->S.W, st->W, 5 * (size_t)nc * sizeof(double), cudaMemcpyHostToDevice, q));
+    unsigned long long bad = 0;
     int64_t h[CNT_SLOTS];
+    CU(cudaMemcpyAsync(&bad, err, sizeof(bad), cudaMemcpyDeviceToHost, q));
     CU(cudaMemcpyAsync(h, s->S.cnt64, sizeof(h), cudaMemcpyDeviceToHost, q));
     CU(cudaStreamSynchronize(q));
+    switch (bad == ~0ULL ? 0 : (int)(bad & 7)) {
+        case 0: break;
+        case 1: return fail(UGKWP_E_STATE, "particle cell out of range");
+        case 2: return fail(UGKWP_E_STATE, "negative internal energy");
+        case 3: return fail(UGKWP_E_STATE, "internal energy not representable in binary32");
+        default: return fail(UGKWP_E_STATE, "particle state not representable in binary32");
+    }
+    std::swap(s->A, s->B);
+    CU(cudaMemcpyAsync(s->S.W, st->W, 5 * (size_t)nc * sizeof(double), cudaMemcpyHostToDevice, q));
     const int64_t moves = h[CNT_MOVES];
     std::memset(h, 0, sizeof(h));
     h[CNT_MOVES] = moves;

@@ -281,6 +281,10 @@ void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p,
 __host__ __device__ inline int bucket_slots(int cnt) { return cnt + cnt / 32 + 4; }
 void launch_rebuild_survivors(const DevMesh& m, const DevState& s, const DevParams& p,
                               const PartBufRaw& a, cudaStream_t st);
+// checks a state image's particles and converts them into the spare buffer b
+// (mixed: x, u, e from the binary64 staging xs, us, es; anchors anc [nc][3])
+void launch_import(int nc, long long n, bool mixed, const double* anc, const double* xs, const double* us,
+                   const double* es, const PartBufRaw& b, unsigned long long* err, cudaStream_t st);
 void launch_wp_moments(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
                        double* out, cudaStream_t st);
 void launch_prim_moments(const DevMesh& m, const DevState& s, const DevParams& p, int which,

@@ -400,19 +400,51 @@ def test_crossing_limit_is_reported():
     compare_step(gsim, osim)
 
 
-def test_import_rejects_bad_state():
-    cfg = wl.shock_tube(nx=10, ny=2, nz=2, precision="mixed")
+def _one_changed(a, i, v):
+    b = np.array(a, copy=True)
+    b.reshape(-1)[i] = v
+    return b
+
+
+@pytest.mark.parametrize("precision,K", [("mixed", 0), ("mixed", 2), ("fp64", 2)])
+def test_import_rejects_bad_state(precision, K):
+    """Every particle is checked on the device before the state changes: a
+    rejected image names the first bad particle's problem and leaves the
+    simulation where it was; a good image after it is taken as usual."""
+    cfg = wl.shock_tube(nx=10, ny=2, nz=2, precision=precision, K=K)
     osim = oracle.OracleSim(cfg["mesh"], cfg["W0"], cfg["params"])
     osim.step()
     st = osim.state()
     gsim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
-    bad = dict(st, x=st["x"] + 1e-12)  # not representable in binary32
-    with pytest.raises(ugkwp.UgkwpError) as e:
-        gsim.set_state(bad)
-    assert e.value.code == ugkwp.E_STATE
-    bad = dict(st, cell=np.where(np.arange(st["cell"].size) == 0, 10 ** 6, st["cell"]).astype(np.int32))
-    with pytest.raises(ugkwp.UgkwpError):
-        gsim.set_state(bad)
+    gsim.step(2)
+    before = gsim.state()
+    n = st["cell"].size
+    cases = [(dict(st, cell=_one_changed(st["cell"], n // 2, 10 ** 6).astype(np.int32)), "cell out of range"),
+             (dict(st, cell=_one_changed(st["cell"], 3, -1).astype(np.int32)), "cell out of range")]
+    if precision == "mixed":
+        cases += [(dict(st, x=st["x"] + 1e-12), "not representable"),
+                  (dict(st, u=_one_changed(st["u"], 2 * n + 5, 0.1)), "not representable")]
+    if K:
+        cases += [(dict(st, e=_one_changed(st["e"], 7, -1.0)), "negative internal energy"),
+                  (dict(st, e=_one_changed(st["e"], 7, np.nan)), "negative internal energy")]
+        if precision == "mixed":
+            cases += [(dict(st, e=_one_changed(st["e"], 9, 0.1)), "internal energy not representable")]
+    # the first bad particle decides the message: a bad cell after a bad position
+    if precision == "mixed":
+        cases += [(dict(st, x=_one_changed(st["x"], 1, 1e-9), cell=_one_changed(st["cell"], 4, -1).astype(np.int32)),
+                   "not representable")]
+    for bad, msg in cases:
+        with pytest.raises(ugkwp.UgkwpError, match=msg) as e:
+            gsim.set_state(bad)
+        assert e.value.code == ugkwp.E_STATE
+        after = gsim.state()
+        assert after["step"] == before["step"]
+        np.testing.assert_array_equal(after["W"], before["W"])
+        assert_particles_equal(after, before)
+    gsim.set_state(st)
+    gsim.step(1)
+    osim.step()
+    compare_step(gsim, osim)
 
 
 def test_graph_replay_matches_direct_launches():
