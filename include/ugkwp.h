@@ -269,14 +269,48 @@ int ugkwp_moments(ugkwp_sim* s, int32_t which, double* out, int32_t out_on_devic
  * particle buffer, before its state changes: a rejected image leaves the
  * simulation as it was.  In mixed precision the binary64 positions,
  * velocities and internal energies pass through a device staging buffer
- * (3 n_cells + 6 n_particles doubles, 7 n_particles with K > 0, plus 256
- * bytes) allocated by the call, kept between imports and freed with
- * ugkwp_free.  Host arrays in page-locked memory copy fastest.
+ * (3 n_cells + 6 n_particles doubles, 7 n_particles with K > 0) allocated by
+ * the call, kept between imports and freed with ugkwp_free; the native image
+ * below needs none.  Host arrays in page-locked memory copy fastest.
  * Errors: UGKWP_E_ARG, UGKWP_E_CAPACITY, UGKWP_E_STATE (particle outside the
  * mesh index range or not representable in the particle precision). */
 int ugkwp_state_info(ugkwp_sim* s, ugkwp_state* st);
 int ugkwp_export_state(ugkwp_sim* s, ugkwp_state* st);
 int ugkwp_import_state(ugkwp_sim* s, const ugkwp_state* st);
+
+/* Native image of the simulation state, for checkpoint and restart of the
+ * same mesh and precision: the particles as the simulation stores them, so
+ * that no conversion is needed either way.  Like ugkwp_state, except that x,
+ * u and e hold real_size bytes per value (4 in MIXED, 8 in FP64; set by the
+ * export, checked by the import): in MIXED x is the binary32 offset of the
+ * particle from the anchor of its tet (a point of the tet fixed by
+ * ugkwp_init: the position is anchor + offset, exactly, in binary64), u and e
+ * the binary32 velocity and internal energy; in FP64 the binary64 values.
+ * e may be NULL when K = 0 (the export then writes zeros into it if given).
+ * The export holds the live particles in buffer order (the arrays must hold
+ * n_particles entries; with n_particles too small it reports UGKWP_E_ARG and
+ * fills only the scalar fields).  The import copies the arrays as they are
+ * into the simulation's spare particle buffer and checks there every
+ * particle's cell (in [0, n_cells)) and internal energy (>= 0) before the
+ * state changes; a rejected image leaves the simulation as it was.
+ * Synchronising.  Errors: UGKWP_E_ARG (NULL argument, real_size of another
+ * precision, e missing with K > 0), UGKWP_E_CAPACITY, UGKWP_E_STATE. */
+typedef struct {
+    int64_t n_particles;
+    int64_t step;
+    double t;
+    int32_t exps[5];
+    int32_t real_size;
+    double* W;
+    uint64_t* id;
+    int32_t* cell;
+    void* x;
+    void* u;
+    double* m;
+    void* e;
+} ugkwp_state_native;
+int ugkwp_export_state_native(ugkwp_sim* s, ugkwp_state_native* st);
+int ugkwp_import_state_native(ugkwp_sim* s, const ugkwp_state_native* st);
 
 /* Diagnostics of the last step, copied to host memory (synchronising):
  *  0 dt (1 double), 1 tau [n_cells], 2 rho^h before sampling [n_cells],

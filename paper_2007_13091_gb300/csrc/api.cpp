@@ -36,9 +36,9 @@ struct ugkwp_sim {
     PartBufRaw Mv;     // the step's movers (particles whose counting flux is non-zero)
     std::vector<double> anchor;  // [3*nc] anchors of the tets (mixed mode; 0 in binary64)
     cudaStream_t stream = nullptr;
-    // device staging of ugkwp_import_state (an error word, the tets' anchors
-    // and the image's binary64 positions, velocities and internal energies in
-    // mixed mode), kept between imports
+    // device staging of ugkwp_import_state in mixed mode (the tets' anchors
+    // and the image's binary64 positions, velocities and internal energies),
+    // kept between imports
     void* imp = nullptr;
     size_t imp_bytes = 0;
     int64_t step = 0;
@@ -1089,6 +1089,69 @@ int ugkwp_export_state(ugkwp_sim* s, ugkwp_state* st) {
     return read_error(s);
 }
 
+}  // extern "C"
+
+namespace {
+
+// The end of an import: reads the check kernel's error word; when every
+// particle passed, the spare buffer B (which holds the image's particles)
+// becomes the current one and W, the counters, t, the quanta and the
+// survivors' counts and mass per cell are set from the image.
+int import_commit(ugkwp_sim* s, int64_t n, int64_t step, double t, const int32_t* exps, const double* W,
+                  const unsigned long long* err) {
+    const int nc = s->M.nc;
+    cudaStream_t q = s->stream;
+    unsigned long long bad = 0;
+    int64_t h[CNT_SLOTS];
+    CU(cudaMemcpyAsync(&bad, err, sizeof(bad), cudaMemcpyDeviceToHost, q));
+    CU(cudaMemcpyAsync(h, s->S.cnt64, sizeof(h), cudaMemcpyDeviceToHost, q));
+    CU(cudaStreamSynchronize(q));
+    switch (bad == ~0ULL ? 0 : (int)(bad & 7)) {
+        case 0: break;
+        case 1: return fail(UGKWP_E_STATE, "particle cell out of range");
+        case 2: return fail(UGKWP_E_STATE, "negative internal energy");
+        case 3: return fail(UGKWP_E_STATE, "internal energy not representable in binary32");
+        default: return fail(UGKWP_E_STATE, "particle state not representable in binary32");
+    }
+    std::swap(s->A, s->B);
+    CU(cudaMemcpyAsync(s->S.W, W, 5 * (size_t)nc * sizeof(double), cudaMemcpyHostToDevice, q));
+    const int64_t moves = h[CNT_MOVES];
+    std::memset(h, 0, sizeof(h));
+    h[CNT_MOVES] = moves;
+    h[CNT_N_A] = n;
+    h[CNT_SURV] = n;
+    h[CNT_STEP] = step;
+    CU(cudaMemcpyAsync(s->S.cnt64, h, sizeof(h), cudaMemcpyHostToDevice, q));
+    CU(cudaMemcpyAsync(s->S.t, &t, sizeof(double), cudaMemcpyHostToDevice, q));
+    CU(cudaMemsetAsync(s->S.nleft, 0, nc * sizeof(int32_t), q));
+    CU(cudaMemsetAsync(s->S.smass, 0, nc * sizeof(int64_t), q));
+    set_exps(s->P, exps);
+    s->drop_graphs();  // the graphs carry the parameters by value
+    launch_rebuild_survivors(s->M, s->S, s->P, s->A, q);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(q));
+    s->step = step;
+    return UGKWP_OK;
+}
+
+// The device staging of a binary64 image in mixed precision (`need` bytes),
+// allocated on first use and kept until ugkwp_free.
+int import_staging(ugkwp_sim* s, size_t need, char*& base) {
+    if (need > s->imp_bytes) {
+        if (s->imp) cudaFree(s->imp);
+        s->imp = nullptr;
+        s->imp_bytes = 0;
+        CU(cudaMalloc(&s->imp, need));
+        s->imp_bytes = need;
+    }
+    base = static_cast<char*>(s->imp);
+    return UGKWP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int ugkwp_import_state(ugkwp_sim* s, const ugkwp_state* st) {
     if (!s || !st || !st->W || (st->n_particles > 0 && (!st->id || !st->cell || !st->x || !st->u || !st->m)))
         return fail(UGKWP_E_ARG, "NULL argument");
@@ -1103,24 +1166,20 @@ int ugkwp_import_state(ugkwp_sim* s, const ugkwp_state* st) {
     // else into a device staging buffer (binary64, with the tets' anchors),
     // from which k_import checks every particle and converts it into B.  The
     // buffers swap only when every particle passed, so a rejected image
-    // leaves the simulation as it was.
+    // leaves the simulation as it was.  The first failed particle is reported
+    // in a counter slot that no step uses.
     const bool mixed = rs == 4;
     const bool ke = s->A.e != nullptr;
-    const size_t hdr = 256;  // the error word
-    const size_t need =
-        hdr + (mixed ? (3 * (size_t)nc + (size_t)(ke ? 7 : 6) * (size_t)n) * sizeof(double) : 0);
-    if (need > s->imp_bytes) {
-        if (s->imp) cudaFree(s->imp);
-        s->imp = nullptr;
-        s->imp_bytes = 0;
-        CU(cudaMalloc(&s->imp, need));
-        s->imp_bytes = need;
+    unsigned long long* err = reinterpret_cast<unsigned long long*>(&s->S.cnt64[CNT_IMPORT]);
+    double* anc = nullptr;
+    if (mixed) {
+        char* base = nullptr;
+        int rc = import_staging(s, (3 * (size_t)nc + (size_t)(ke ? 7 : 6) * (size_t)n) * sizeof(double), base);
+        if (rc) return rc;
+        anc = reinterpret_cast<double*>(base);
     }
-    char* base = static_cast<char*>(s->imp);
-    unsigned long long* err = reinterpret_cast<unsigned long long*>(base);
-    double* anc = reinterpret_cast<double*>(base + hdr);
-    double* xs = anc + 3 * (size_t)nc;
-    double* us = xs + 3 * (size_t)n;
+    double* xs = mixed ? anc + 3 * (size_t)nc : nullptr;
+    double* us = mixed ? xs + 3 * (size_t)n : nullptr;
     double* es = (mixed && ke) ? us + 3 * (size_t)n : nullptr;
     cudaStream_t q = s->stream;
     CU(cudaStreamSynchronize(q));  // B is free once the bound stream's steps are done
@@ -1141,40 +1200,106 @@ int ugkwp_import_state(ugkwp_sim* s, const ugkwp_state* st) {
             }
             if (ke) CU(cudaMemcpyAsync(s->B.e, st->e, (size_t)n * 8, cudaMemcpyHostToDevice, q));
         }
-        launch_import(nc, n, mixed, anc, xs, us, es, s->B, err, q);
+        launch_import(nc, n, mixed, mixed, anc, xs, us, es, s->B, err, q);
         CU(cudaGetLastError());
     }
-    unsigned long long bad = 0;
+    return import_commit(s, n, st->step, st->t, st->exps, st->W, err);
+}
+
+int ugkwp_export_state_native(ugkwp_sim* s, ugkwp_state_native* st) {
+    if (!s || !st) return fail(UGKWP_E_ARG, "NULL argument");
+    const int64_t want = st->n_particles;
+    ugkwp_state info{};
+    int rc = ugkwp_state_info(s, &info);
+    if (rc) return rc;
+    st->n_particles = info.n_particles;
+    st->step = info.step;
+    st->t = info.t;
+    for (int q = 0; q < 5; ++q) st->exps[q] = info.exps[q];
+    st->real_size = (int32_t)s->real_size;
+    if (want < st->n_particles) return fail(UGKWP_E_ARG, "n_particles of the state is smaller than the particle count");
+    const int nc = s->M.nc;
+    cudaStream_t q = s->stream;
+    if (st->W) CU(cudaMemcpyAsync(st->W, s->S.W, 5 * (size_t)nc * sizeof(double), cudaMemcpyDeviceToHost, q));
     int64_t h[CNT_SLOTS];
-    CU(cudaMemcpyAsync(&bad, err, sizeof(bad), cudaMemcpyDeviceToHost, q));
     CU(cudaMemcpyAsync(h, s->S.cnt64, sizeof(h), cudaMemcpyDeviceToHost, q));
     CU(cudaStreamSynchronize(q));
-    switch (bad == ~0ULL ? 0 : (int)(bad & 7)) {
-        case 0: break;
-        case 1: return fail(UGKWP_E_STATE, "particle cell out of range");
-        case 2: return fail(UGKWP_E_STATE, "negative internal energy");
-        case 3: return fail(UGKWP_E_STATE, "internal energy not representable in binary32");
-        default: return fail(UGKWP_E_STATE, "particle state not representable in binary32");
+    // the N_A slots of the current buffer, then the live ones (cell >= 0) in
+    // buffer order into the caller's arrays
+    const size_t n = (size_t)h[CNT_N_A], rs = s->real_size;
+    std::vector<char> xs[3], us[3];
+    std::vector<double> m(n);
+    std::vector<int32_t> cell(n);
+    std::vector<uint64_t> id(n);
+    std::vector<char> es(s->A.e ? n * rs : 0);
+    if (s->A.e && n) CU(cudaMemcpyAsync(es.data(), s->A.e, n * rs, cudaMemcpyDeviceToHost, q));
+    for (int d = 0; d < 3; ++d) {
+        xs[d].resize(n * rs);
+        us[d].resize(n * rs);
+        if (n) {
+            CU(cudaMemcpyAsync(xs[d].data(), s->A.x[d], n * rs, cudaMemcpyDeviceToHost, q));
+            CU(cudaMemcpyAsync(us[d].data(), s->A.u[d], n * rs, cudaMemcpyDeviceToHost, q));
+        }
     }
-    std::swap(s->A, s->B);
-    CU(cudaMemcpyAsync(s->S.W, st->W, 5 * (size_t)nc * sizeof(double), cudaMemcpyHostToDevice, q));
-    const int64_t moves = h[CNT_MOVES];
-    std::memset(h, 0, sizeof(h));
-    h[CNT_MOVES] = moves;
-    h[CNT_N_A] = n;
-    h[CNT_SURV] = n;
-    h[CNT_STEP] = st->step;
-    CU(cudaMemcpyAsync(s->S.cnt64, h, sizeof(h), cudaMemcpyHostToDevice, q));
-    CU(cudaMemcpyAsync(s->S.t, &st->t, sizeof(double), cudaMemcpyHostToDevice, q));
-    CU(cudaMemsetAsync(s->S.nleft, 0, nc * sizeof(int32_t), q));
-    CU(cudaMemsetAsync(s->S.smass, 0, nc * sizeof(int64_t), q));
-    set_exps(s->P, st->exps);
-    s->drop_graphs();  // the graphs carry the parameters by value
-    launch_rebuild_survivors(s->M, s->S, s->P, s->A, q);
-    CU(cudaGetLastError());
+    if (n) {
+        CU(cudaMemcpyAsync(m.data(), s->A.m, n * 8, cudaMemcpyDeviceToHost, q));
+        CU(cudaMemcpyAsync(cell.data(), s->A.cell, n * 4, cudaMemcpyDeviceToHost, q));
+        CU(cudaMemcpyAsync(id.data(), s->A.id, n * 8, cudaMemcpyDeviceToHost, q));
+    }
     CU(cudaStreamSynchronize(q));
-    s->step = st->step;
-    return UGKWP_OK;
+    const size_t np = (size_t)st->n_particles;
+    char* xo = static_cast<char*>(st->x);
+    char* uo = static_cast<char*>(st->u);
+    char* eo = static_cast<char*>(st->e);
+    size_t k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        if (cell[i] < 0) continue;
+        if (st->id) st->id[k] = id[i];
+        if (st->cell) st->cell[k] = cell[i];
+        if (st->m) st->m[k] = m[i];
+        if (eo) {
+            if (s->A.e) std::memcpy(eo + k * rs, es.data() + i * rs, rs);
+            else std::memset(eo + k * rs, 0, rs);
+        }
+        for (int d = 0; d < 3; ++d) {
+            if (xo) std::memcpy(xo + (d * np + k) * rs, xs[d].data() + i * rs, rs);
+            if (uo) std::memcpy(uo + (d * np + k) * rs, us[d].data() + i * rs, rs);
+        }
+        ++k;
+    }
+    return read_error(s);
+}
+
+int ugkwp_import_state_native(ugkwp_sim* s, const ugkwp_state_native* st) {
+    if (!s || !st || !st->W || (st->n_particles > 0 && (!st->id || !st->cell || !st->x || !st->u || !st->m)))
+        return fail(UGKWP_E_ARG, "NULL argument");
+    const int64_t n = st->n_particles;
+    if (n < 0 || n > s->capacity) return fail(UGKWP_E_CAPACITY, "imported particles exceed the capacity");
+    if (st->step < 0 || st->step >= ((int64_t)1 << 24) - 1) return fail(UGKWP_E_STATE, "step out of range");
+    const size_t rs = s->real_size;
+    if (st->real_size != (int32_t)rs) return fail(UGKWP_E_ARG, "real_size differs from the simulation's particle precision");
+    const bool ke = s->A.e != nullptr;
+    if (ke && n > 0 && !st->e) return fail(UGKWP_E_ARG, "internal energies (e) needed when K > 0");
+    unsigned long long* err = reinterpret_cast<unsigned long long*>(&s->S.cnt64[CNT_IMPORT]);
+    cudaStream_t q = s->stream;
+    CU(cudaStreamSynchronize(q));  // B is free once the bound stream's steps are done
+    CU(cudaMemsetAsync(err, 0xff, sizeof(unsigned long long), q));
+    if (n) {
+        // the image as it is into the spare buffer B, checked there
+        const char* xi = static_cast<const char*>(st->x);
+        const char* ui = static_cast<const char*>(st->u);
+        CU(cudaMemcpyAsync(s->B.m, st->m, (size_t)n * 8, cudaMemcpyHostToDevice, q));
+        CU(cudaMemcpyAsync(s->B.cell, st->cell, (size_t)n * 4, cudaMemcpyHostToDevice, q));
+        CU(cudaMemcpyAsync(s->B.id, st->id, (size_t)n * 8, cudaMemcpyHostToDevice, q));
+        for (int d = 0; d < 3; ++d) {
+            CU(cudaMemcpyAsync(s->B.x[d], xi + (size_t)d * n * rs, (size_t)n * rs, cudaMemcpyHostToDevice, q));
+            CU(cudaMemcpyAsync(s->B.u[d], ui + (size_t)d * n * rs, (size_t)n * rs, cudaMemcpyHostToDevice, q));
+        }
+        if (ke) CU(cudaMemcpyAsync(s->B.e, st->e, (size_t)n * rs, cudaMemcpyHostToDevice, q));
+        launch_import(s->M.nc, n, rs == 4, false, nullptr, nullptr, nullptr, nullptr, s->B, err, q);
+        CU(cudaGetLastError());
+    }
+    return import_commit(s, n, st->step, st->t, st->exps, st->W, err);
 }
 
 int ugkwp_last(ugkwp_sim* s, int32_t which, void* host_out) {

@@ -382,16 +382,16 @@ __global__ void k_rebuild(DevMesh m, DevState s, DevParams p, PartBufRaw a) {
 
 // A state image's particles, checked and brought into the particle
 // precision in the spare buffer b (its cell, m and id arrays already hold the
-// image's; with binary64 particles so do x, u and e).  Mixed mode: x, u and e
-// come in binary64 (staged [3][n], [3][n], [n]); a position becomes its offset
-// from the anchor of its tet, which must be exact in binary32 and give back
-// the position when added to the anchor, and the velocity and internal energy
-// must be binary32 values.  *err receives the smallest i << 3 | kind over the
-// particles that fail, kind being the first failed check of particle i: 1
-// cell outside [0, nc), 2 internal energy negative or not a number, 3
-// internal energy not a binary32 value, 4 position or velocity not
-// representable.
-template <class Real>
+// image's; so do x, u and e when they come in the particle precision).
+// CONVERT (mixed mode, binary64 image): x, u and e come in binary64 (staged
+// [3][n], [3][n], [n]); a position becomes its offset from the anchor of its
+// tet, which must be exact in binary32 and give back the position when added
+// to the anchor, and the velocity and internal energy must be binary32
+// values.  *err receives the smallest i << 3 | kind over the particles that
+// fail, kind being the first failed check of particle i: 1 cell outside
+// [0, nc), 2 internal energy negative or not a number, 3 internal energy not
+// a binary32 value, 4 position or velocity not representable.
+template <class Real, bool CONVERT>
 __global__ void k_import(int nc, long long n, const double* anc, const double* xs, const double* us,
                          const double* es, PartBufRaw b, unsigned long long* err) {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -400,7 +400,7 @@ __global__ void k_import(int nc, long long n, const double* anc, const double* x
         unsigned kind = 0;
         if (c < 0 || c >= nc) {
             kind = 1;
-        } else if constexpr (sizeof(Real) == 4) {
+        } else if constexpr (CONVERT) {
             if (es) {
                 const double ev = es[i];
                 const float ef = __double2float_rn(ev);
@@ -419,7 +419,7 @@ __global__ void k_import(int nc, long long n, const double* anc, const double* x
                 static_cast<float*>(b.u[d])[i] = uf;
             }
         } else {
-            if (b.e && !(static_cast<const double*>(b.e)[i] >= 0.0)) kind = 2;
+            if (b.e && !(static_cast<const Real*>(b.e)[i] >= (Real)0)) kind = 2;
         }
         if (kind) atomicMin(err, ((unsigned long long)i << 3) | kind);
     }
@@ -554,11 +554,13 @@ void launch_rebuild_survivors(const DevMesh& m, const DevState& s, const DevPara
     if (p.precision == UGKWP_MIXED) k_rebuild<float><<<particle_grid(), 256, 0, st>>>(m, s, p, a);
     else k_rebuild<double><<<particle_grid(), 256, 0, st>>>(m, s, p, a);
 }
-void launch_import(int nc, long long n, bool mixed, const double* anc, const double* xs, const double* us,
-                   const double* es, const PartBufRaw& b, unsigned long long* err, cudaStream_t st) {
+void launch_import(int nc, long long n, bool mixed, bool convert, const double* anc, const double* xs,
+                   const double* us, const double* es, const PartBufRaw& b, unsigned long long* err,
+                   cudaStream_t st) {
     if (n <= 0) return;
-    if (mixed) k_import<float><<<particle_grid(), 256, 0, st>>>(nc, n, anc, xs, us, es, b, err);
-    else k_import<double><<<particle_grid(), 256, 0, st>>>(nc, n, anc, xs, us, es, b, err);
+    if (mixed && convert) k_import<float, true><<<particle_grid(), 256, 0, st>>>(nc, n, anc, xs, us, es, b, err);
+    else if (mixed) k_import<float, false><<<particle_grid(), 256, 0, st>>>(nc, n, anc, xs, us, es, b, err);
+    else k_import<double, false><<<particle_grid(), 256, 0, st>>>(nc, n, anc, xs, us, es, b, err);
 }
 void launch_wp_moments(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
                        double* out, cudaStream_t st) {

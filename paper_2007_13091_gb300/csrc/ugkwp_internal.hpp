@@ -49,6 +49,7 @@ enum : int {
     CNT_WTOT = 15,      // slots of the survivor buckets of the buffer written this step (from the scan)
     CNT_RESV = 16,      // mover slots reserved this step
     CNT_TILE = 32,      // next grab of tracking tiles
+    CNT_IMPORT = 40,    // a state import's first failed particle: (index << 3) | problem
     CNT_OVF = 48,       // overflow slots (survivors whose bucket is full) taken this step
     CNT_CHECK = 56,     // the first failed self-check: (check << 48) | value
     CNT_SLOTS = 64,
@@ -281,10 +282,12 @@ void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p,
 __host__ __device__ inline int bucket_slots(int cnt) { return cnt + cnt / 32 + 4; }
 void launch_rebuild_survivors(const DevMesh& m, const DevState& s, const DevParams& p,
                               const PartBufRaw& a, cudaStream_t st);
-// checks a state image's particles and converts them into the spare buffer b
-// (mixed: x, u, e from the binary64 staging xs, us, es; anchors anc [nc][3])
-void launch_import(int nc, long long n, bool mixed, const double* anc, const double* xs, const double* us,
-                   const double* es, const PartBufRaw& b, unsigned long long* err, cudaStream_t st);
+// checks a state image's particles in the spare buffer b and, with convert
+// (mixed mode, binary64 image), converts x, u, e from the binary64 staging
+// xs, us, es into it (anchors anc [nc][3])
+void launch_import(int nc, long long n, bool mixed, bool convert, const double* anc, const double* xs,
+                   const double* us, const double* es, const PartBufRaw& b, unsigned long long* err,
+                   cudaStream_t st);
 void launch_wp_moments(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
                        double* out, cudaStream_t st);
 void launch_prim_moments(const DevMesh& m, const DevState& s, const DevParams& p, int which,

@@ -88,6 +88,13 @@ class State(ctypes.Structure):
                 ("u", ctypes.c_void_p), ("m", ctypes.c_void_p), ("e", ctypes.c_void_p)]
 
 
+class StateNative(ctypes.Structure):
+    _fields_ = [("n_particles", ctypes.c_int64), ("step", ctypes.c_int64), ("t", ctypes.c_double),
+                ("exps", ctypes.c_int32 * 5), ("real_size", ctypes.c_int32), ("W", ctypes.c_void_p),
+                ("id", ctypes.c_void_p), ("cell", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("u", ctypes.c_void_p), ("m", ctypes.c_void_p), ("e", ctypes.c_void_p)]
+
+
 class AdjointReq(ctypes.Structure):
     _fields_ = [("functional", ctypes.c_int32), ("n_steps", ctypes.c_int32), ("wall_tags", ctypes.c_void_p),
                 ("n_wall_tags", ctypes.c_int32), ("reserved_", ctypes.c_int32), ("theta", ctypes.c_void_p),
@@ -100,6 +107,7 @@ EXPORTED = ["ugkwp_gks_steps", "ugkwp_average", "ugkwp_average_time", "ugkwp_kn_
             "ugkwp_batch_step", "ugkwp_batch_sync", "ugkwp_batch_autotune", "ugkwp_batch_free",
             "ugkwp_time_step_noalloc", "ugkwp_timing_enable", "ugkwp_timing_read", "ugkwp_mesh_load", "ugkwp_mesh_free", "ugkwp_query_sizes", "ugkwp_init", "ugkwp_free", "ugkwp_step",
             "ugkwp_sync", "ugkwp_moments", "ugkwp_state_info", "ugkwp_export_state", "ugkwp_import_state",
+            "ugkwp_export_state_native", "ugkwp_import_state_native",
             "ugkwp_last", "ugkwp_adjoint_wave", "ugkwp_last_error"]
 
 _LIB = None
@@ -129,6 +137,8 @@ def lib():
             "ugkwp_state_info": [vp, P(State)],
             "ugkwp_export_state": [vp, P(State)],
             "ugkwp_import_state": [vp, P(State)],
+            "ugkwp_export_state_native": [vp, P(StateNative)],
+            "ugkwp_import_state_native": [vp, P(StateNative)],
             "ugkwp_last": [vp, i32, vp],
             "ugkwp_adjoint_wave": [vp, P(AdjointReq), vp],
             "ugkwp_adjoint_query": [vp, i32, P(sz)],
@@ -299,6 +309,51 @@ def ugkwp_import_state(sim, state: dict):
     for k, a in arrs.items():
         setattr(st, k, a.ctypes.data)
     _check(lib().ugkwp_import_state(sim, ctypes.byref(st)))
+
+
+def ugkwp_export_state_native(sim, n_cells: int) -> dict:
+    """The native state image (see include/ugkwp.h): x, u, e in the particle
+    precision (float32 in MIXED, x the offsets from the tets' anchors)."""
+    probe = StateNative()
+    probe.n_particles = -1  # too small on purpose: fills the scalar fields only
+    rc = lib().ugkwp_export_state_native(sim, ctypes.byref(probe))
+    if rc not in (0, E_ARG):
+        _check(rc)
+    n = probe.n_particles
+    dt = np.float32 if probe.real_size == 4 else np.float64
+    out = {"W": np.empty((5, n_cells)), "id": np.empty(n, dtype=np.uint64), "cell": np.empty(n, dtype=np.int32),
+           "x": np.empty((3, n), dtype=dt), "u": np.empty((3, n), dtype=dt), "m": np.empty(n),
+           "e": np.empty(n, dtype=dt)}
+    st = StateNative()
+    st.n_particles = n
+    for k in ("W", "id", "cell", "x", "u", "m", "e"):
+        setattr(st, k, out[k].ctypes.data)
+    _check(lib().ugkwp_export_state_native(sim, ctypes.byref(st)))
+    out.update(step=int(st.step), t=float(st.t), exps=np.array(list(st.exps), dtype=np.int64),
+               real_size=int(st.real_size))
+    return out
+
+
+def ugkwp_import_state_native(sim, state: dict):
+    dt = np.float32 if int(state["real_size"]) == 4 else np.float64
+    arrs = {"W": np.ascontiguousarray(state["W"], dtype=np.float64),
+            "id": np.ascontiguousarray(state["id"], dtype=np.uint64),
+            "cell": np.ascontiguousarray(state["cell"], dtype=np.int32),
+            "x": np.ascontiguousarray(state["x"], dtype=dt),
+            "u": np.ascontiguousarray(state["u"], dtype=dt),
+            "m": np.ascontiguousarray(state["m"], dtype=np.float64)}
+    if state.get("e") is not None:
+        arrs["e"] = np.ascontiguousarray(state["e"], dtype=dt)
+    st = StateNative()
+    st.n_particles = arrs["id"].size
+    st.step = int(state["step"])
+    st.t = float(state["t"])
+    st.real_size = int(state["real_size"])
+    for q in range(5):
+        st.exps[q] = int(state["exps"][q])
+    for k, a in arrs.items():
+        setattr(st, k, a.ctypes.data)
+    _check(lib().ugkwp_import_state_native(sim, ctypes.byref(st)))
 
 
 def ugkwp_last(sim, which: str, n_cells: int, n_faces: int):
@@ -475,6 +530,13 @@ class Simulation:
 
     def set_state(self, st: dict):
         ugkwp_import_state(self.handle, st)
+
+    def state_native(self):
+        """The native image (checkpoint of this mesh and precision)."""
+        return ugkwp_export_state_native(self.handle, self.n_cells)
+
+    def set_state_native(self, st: dict):
+        ugkwp_import_state_native(self.handle, st)
 
     def last(self, which: str):
         return ugkwp_last(self.handle, which, self.n_cells, self.n_faces)

@@ -37,6 +37,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(ugkwp.Params) == 8 * 8 + 8 * 4 + 8 + 8 + 16 * 80
     assert ctypes.sizeof(ugkwp.MeshDesc) == 16 + 4 * 8
     assert ctypes.sizeof(ugkwp.State) == 8 + 8 + 8 + 20 + 4 + 7 * 8
+    assert ctypes.sizeof(ugkwp.StateNative) == 8 + 8 + 8 + 20 + 4 + 7 * 8
     assert ctypes.sizeof(ugkwp.LaunchCfg) == 4 * 4
 
 

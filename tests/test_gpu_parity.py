@@ -447,6 +447,47 @@ def test_import_rejects_bad_state(precision, K):
     compare_step(gsim, osim)
 
 
+@pytest.mark.parametrize("precision,K", [("mixed", 0), ("mixed", 2), ("fp64", 0)])
+def test_native_image_round_trip(precision, K):
+    """The native image (particles in the simulation's own precision) restores
+    a simulation bit for bit: a copy restored from it steps on exactly like
+    the original; its velocities, cells, masses and ids are those of the
+    binary64 image; a bad image is rejected and changes nothing."""
+    cfg = wl.cavity(n=5, N_ref=40, precision=precision, order=2, K=K, seed=31)
+    a = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    a.step(3)
+    nat = a.state_native()
+    wide = a.state()
+    assert nat["real_size"] == (4 if precision == "mixed" else 8)
+    assert nat["x"].dtype == (np.float32 if precision == "mixed" else np.float64)
+    for k in ("id", "cell", "m", "W"):
+        np.testing.assert_array_equal(nat[k], wide[k])
+    np.testing.assert_array_equal(nat["u"].astype(np.float64), wide["u"])
+    if K:
+        np.testing.assert_array_equal(nat["e"].astype(np.float64), wide["e"])
+    if precision == "fp64":
+        np.testing.assert_array_equal(nat["x"], wide["x"])
+    b = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    b.step(1)
+    before = b.state()
+    bad = dict(nat, cell=_one_changed(nat["cell"], 2, cfg["mesh"]["tets"].shape[0]).astype(np.int32))
+    with pytest.raises(ugkwp.UgkwpError, match="cell out of range"):
+        b.set_state_native(bad)
+    with pytest.raises(ugkwp.UgkwpError) as e:
+        b.set_state_native(dict(nat, real_size=12 - nat["real_size"]))
+    assert e.value.code == ugkwp.E_ARG
+    after = b.state()
+    np.testing.assert_array_equal(after["W"], before["W"])
+    assert_particles_equal(after, before)
+    b.set_state_native(nat)
+    a.step(2)
+    b.step(2)
+    sa, sb = a.state(), b.state()
+    assert sa["step"] == sb["step"]
+    np.testing.assert_array_equal(sa["W"], sb["W"])
+    assert_particles_equal(sa, sb)
+
+
 def test_graph_replay_matches_direct_launches():
     """ugkwp_step(n >= 2) replays two-step CUDA graphs; the state must equal that
     of single-step launches bit for bit (all sums are order-independent)."""
