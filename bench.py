@@ -352,7 +352,8 @@ def e2e(cfg, steps, device, launch_cfg=None):
     form) and, in a second loop, as the binary64 image."""
     import torch
     from paper_2007_13091_gb300 import ugkwp
-    sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device)
+    sim = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"], device=device,
+                           stream=torch.cuda.Stream(device=device))
     if launch_cfg is not None:
         ugkwp.ugkwp_set_launch_cfg(sim.handle, launch_cfg["particle_blocks"], launch_cfg["wave_blocks"],
                                    launch_cfg["track_threads"], launch_cfg["smem_carveout"])

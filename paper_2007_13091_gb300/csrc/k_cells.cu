@@ -366,17 +366,39 @@ __global__ void k_kn_gll(DevMesh m, DevState s, DevParams p, double* out) {
     out[i] = l * sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) / rho;
 }
 
+// The survivors' count and fixed-point mass per cell of an imported buffer.
+// Imported particles mostly come sorted by cell, so each warp sums over runs
+// of equal cells in its 32 slots and adds once per run (integer sums: the
+// result does not depend on how they are grouped).
 template <class Real>
 __global__ void k_rebuild(DevMesh m, DevState s, DevParams p, PartBufRaw a) {
     const long long n = s.cnt64[CNT_N_A];
     const int32_t* cell = a.cell;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int c = cell[i];
-        if (c < 0) continue;
-        atomicAdd(&s.nleft[c], 1);
-        const long long q = __double2ll_rn(a.m[i] * p.qinv[0]);
-        atomicAdd(reinterpret_cast<unsigned long long*>(&s.smass[c]), (unsigned long long)q);
+    // warp-uniform bounds: every lane takes part in the run sums
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const long long i = base + lane;
+        int c = -1;
+        long long q = 0;
+        if (i < n) {
+            c = cell[i];
+            if (c >= 0) q = __double2ll_rn(a.m[i] * p.qinv[0]);
+        }
+        const int prev = __shfl_up_sync(FULL, c, 1);
+        const unsigned heads = __ballot_sync(FULL, lane == 0 || prev != c);
+        const int start = 31 - __clz(heads & (FULL >> (31 - lane)));
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const long long o = __shfl_up_sync(FULL, q, d);
+            if (lane - d >= start) q += o;
+        }
+        const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+        if (tail && c >= 0) {
+            atomicAdd(&s.nleft[c], lane - start + 1);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&s.smass[c]), (unsigned long long)q);
+        }
     }
 }
 

@@ -476,7 +476,9 @@ def ugkwp_batch_free(batch):
 # ------------------------------------------------------------ convenience
 class Simulation:
     """A UGKWP simulation on one GPU: workspace from the PyTorch allocator,
-    work enqueued on a PyTorch stream (the current one by default)."""
+    work enqueued on a PyTorch stream (the current one by default; a stream of
+    its own, e.g. torch.cuda.Stream(), steps faster than the legacy default
+    stream, with which the step's concurrent kernels serialise in part)."""
 
     def __init__(self, mesh: dict, W0, params: dict, device: str = "cuda", stream=None):
         import torch
