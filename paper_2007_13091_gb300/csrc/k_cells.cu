@@ -548,7 +548,7 @@ void launch_sample_count(const DevMesh& m, const DevState& s, const DevParams& p
     k_sample_count<<<scan_blocks(m.nc), SCAN_BLOCK, 0, st>>>(m, s, p);
 }
 void launch_scan(const DevMesh& m, const DevState& s, const DevParams& p, cudaStream_t st) {
-    k_scan_bsum<<<1, SCAN_BLOCK, 0, st>>>(s, p, scan_blocks(m.nc));
+    k_scan_bsum<<<1, SCAN_SUM_THREADS, 0, st>>>(s, p, scan_blocks(m.nc));
     k_scan_apply<<<scan_blocks(m.nc), SCAN_BLOCK, 0, st>>>(m, s);
 }
 void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p, int32_t* wcell, cudaStream_t st) {
@@ -565,7 +565,7 @@ void launch_sample_count_batch(const BatchChunk& c, int blocks, cudaStream_t st)
     k_sample_count_b<<<blocks, SCAN_BLOCK, 0, st>>>(c);
 }
 void launch_scan_batch(const BatchChunk& c, int blocks, cudaStream_t st) {
-    k_scan_bsum_b<<<c.n, SCAN_BLOCK, 0, st>>>(c);
+    k_scan_bsum_b<<<c.n, SCAN_SUM_THREADS, 0, st>>>(c);
     k_scan_apply_b<<<blocks, SCAN_BLOCK, 0, st>>>(c);
 }
 void launch_cell_update_batch(const BatchChunk& c, int blocks, cudaStream_t st) {

@@ -230,7 +230,11 @@ constexpr int GP_NC = 14;
 constexpr int GP_ATTEMPTS = 64;
 
 // Kernel launchers (stream-ordered, no synchronisation).
-constexpr int SCAN_BLOCK = 1024;
+// cells per block of the counting and offset kernels (256: every SM takes
+// blocks on a ~1e5-cell mesh), and threads of the one-block scan of their
+// block sums
+constexpr int SCAN_BLOCK = 256;
+constexpr int SCAN_SUM_THREADS = 1024;
 __host__ __device__ inline int scan_blocks(int nc) { return (nc + SCAN_BLOCK - 1) / SCAN_BLOCK; }
 
 void launch_reset(const DevMesh& m, const DevState& s, cudaStream_t st);
