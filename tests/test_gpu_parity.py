@@ -488,6 +488,32 @@ def test_native_image_round_trip(precision, K):
     assert_particles_equal(sa, sb)
 
 
+def test_import_of_an_image_without_particles():
+    """An image with no particles is taken in both forms: the next step starts
+    from W alone and samples every cell, as the first step does."""
+    cfg = wl.cavity(n=4, N_ref=30, precision="mixed", order=2, seed=41)
+    a = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    a.step(2)
+    wide, nat = a.state(), a.state_native()
+    empty_wide = dict(wide, id=wide["id"][:0], cell=wide["cell"][:0], m=wide["m"][:0], e=wide["e"][:0],
+                      x=wide["x"][:, :0], u=wide["u"][:, :0])
+    empty_nat = dict(nat, id=nat["id"][:0], cell=nat["cell"][:0], m=nat["m"][:0], e=nat["e"][:0],
+                     x=nat["x"][:, :0], u=nat["u"][:, :0])
+    b = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    c = ugkwp.Simulation(cfg["mesh"], cfg["W0"], cfg["params"])
+    b.set_state(empty_wide)
+    c.set_state_native(empty_nat)
+    for sim in (b, c):
+        st = sim.state()
+        assert st["id"].size == 0 and st["step"] == wide["step"]
+        np.testing.assert_array_equal(st["W"], wide["W"])
+        stats = sim.step(1, stats=True)
+        assert stats["n_particles"] > 0 and stats["n_sampled"] == stats["n_tracked"]
+    sb, sc = b.state(), c.state()
+    np.testing.assert_array_equal(sb["W"], sc["W"])
+    assert_particles_equal(sb, sc)
+
+
 def test_graph_replay_matches_direct_launches():
     """ugkwp_step(n >= 2) replays two-step CUDA graphs; the state must equal that
     of single-step launches bit for bit (all sums are order-independent)."""
