@@ -52,7 +52,8 @@ struct ugkwp_sim {
     // the wave flux (binary64-bound) runs beside the particle kernels; the
     // second half of the tracking grid joins from `aux` once the wave is done
     cudaStream_t wave = nullptr, aux = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr, sampled = nullptr, tracked = nullptr, gp_ready = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, sampled = nullptr, tracked = nullptr, gp_ready = nullptr,
+                waved = nullptr;
     // grid sizes of the looping step kernels
     LaunchCfg lc{0, 0, {128}, -1};
     // two-step CUDA graphs, one per ping-pong parity (keyed by buffer A), with
@@ -81,6 +82,7 @@ struct ugkwp_sim {
         if (sampled) cudaEventDestroy(sampled);
         if (tracked) cudaEventDestroy(tracked);
         if (gp_ready) cudaEventDestroy(gp_ready);
+        if (waved) cudaEventDestroy(waved);
         if (imp) cudaFree(imp);
         if (wave) cudaStreamDestroy(wave);
         if (aux) cudaStreamDestroy(aux);
@@ -667,6 +669,7 @@ int ugkwp_init(const ugkwp_mesh* m, const ugkwp_params* p, const double* W0, voi
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s->sampled, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s->tracked, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s->gp_ready, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s->waved, cudaEventDisableTiming);
     if (ce != cudaSuccess) {
         delete s;
         return cuda_fail(ce, "ugkwp_init upload");
@@ -778,6 +781,10 @@ int enqueue_step(ugkwp_sim* s) {
         else
             timed(s, UGKWP_K_FLUX, 1, s->wave, [&] { launch_face_flux(s->M, s->S, s->P, 0, s->lc.wave_blocks, s->wave); });
         CU(cudaEventRecord(s->join, s->wave));
+        // the wave part of the update follows the flux on the wave stream,
+        // beside the tracking; the particle part waits for it
+        timed(s, UGKWP_K_UPDATE, 1, s->wave, [&] { launch_wave_update(s->M, s->S, s->wave); });
+        CU(cudaEventRecord(s->waved, s->wave));
         timed(s, UGKWP_K_SCAN, 2, q, [&] { launch_scan(s->M, s->S, s->P, q); });
         if (gp) CU(cudaStreamWaitEvent(q, s->gp_ready, 0));  // the sampler reads the g_p coefficients
         const bool matched = s->P.sampling == UGKWP_SAMPLE_ENERGY_MATCHED;
@@ -804,7 +811,7 @@ int enqueue_step(ugkwp_sim* s) {
         });
         if (ce != cudaSuccess) return cuda_fail(ce, "tracking launch order");
         timed(s, UGKWP_K_MOVERS, 1, q, [&] { launch_movers(s->M, s->S, s->P, s->Mv, s->lc.particle_blocks, q); });
-        CU(cudaStreamWaitEvent(q, s->join, 0));  // join before the update reads F (already joined via aux)
+        CU(cudaStreamWaitEvent(q, s->waved, 0));  // the wave part of the update is done
         timed(s, UGKWP_K_UPDATE, 1, q, [&] { launch_cell_update(s->M, s->S, s->P, s->B.cell, q); });
         std::swap(s->A, s->B);
         std::swap(s->S.nleft, s->S.nleft_next);
@@ -1612,9 +1619,9 @@ struct FusedChunk {
     bool ke = false;
     cudaStream_t lane = nullptr, wave = nullptr, aux = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, sampled = nullptr, tracked = nullptr, gp_ready = nullptr,
-                done = nullptr;
+                done = nullptr, waved = nullptr;
     ~FusedChunk() {
-        for (cudaEvent_t e : {fork, join, sampled, tracked, gp_ready, done})
+        for (cudaEvent_t e : {fork, join, sampled, tracked, gp_ready, done, waved})
             if (e) cudaEventDestroy(e);
         for (cudaStream_t q : {lane, wave, aux})
             if (q) cudaStreamDestroy(q);
@@ -1724,6 +1731,8 @@ int enqueue_chunk_step(FusedChunk& ch, const std::vector<ugkwp_sim*>& sims) {
     if (ch.order == 2) launch_face_flux_o2_batch(c, blocks(BCL_FLUX_O2), ch.wave);
     else launch_face_flux_batch(c, blocks(BCL_FLUX), ch.wave);
     CU(cudaEventRecord(ch.join, ch.wave));
+    launch_wave_update_batch(c, blocks(BCL_CELLS), ch.wave);
+    CU(cudaEventRecord(ch.waved, ch.wave));
     launch_scan_batch(c, blocks(BCL_SCAN), q);
     if (gp) CU(cudaStreamWaitEvent(q, ch.gp_ready, 0));
     if (ch.sampling == UGKWP_SAMPLE_ENERGY_MATCHED) launch_sample_scale_batch(c, blocks(BCL_CELLS), ch.precision, q);
@@ -1738,7 +1747,7 @@ int enqueue_chunk_step(FusedChunk& ch, const std::vector<ugkwp_sim*>& sims) {
     CU(cudaEventRecord(ch.tracked, ch.aux));
     CU(cudaStreamWaitEvent(q, ch.tracked, 0));
     launch_movers_batch(c, lc.particle_blocks, ch.precision, q);
-    CU(cudaStreamWaitEvent(q, ch.join, 0));
+    CU(cudaStreamWaitEvent(q, ch.waved, 0));
     launch_cell_update_batch(c, blocks(BCL_CELLS), q);
     for (int i = 0; i < c.n; ++i) {
         ugkwp_sim* s = sims[ch.idx[i]];
@@ -1883,7 +1892,7 @@ int ugkwp_batch_create(ugkwp_sim* const* sims, int32_t n_sims, void* cuda_stream
                 if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(q, cudaStreamNonBlocking);
             // the fork is a timing event, as a single simulation's is
             if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&into->fork, cudaEventDefault);
-            for (cudaEvent_t* e : {&into->join, &into->sampled, &into->tracked, &into->gp_ready, &into->done})
+            for (cudaEvent_t* e : {&into->join, &into->sampled, &into->tracked, &into->gp_ready, &into->done, &into->waved})
                 if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
         }
         into->idx.push_back((int)i);

@@ -266,6 +266,26 @@ __device__ __forceinline__ void cell_update_body(const DevMesh& m, const DevStat
         if ((long long)s.woff[i] + cap <= p.capacity)
             for (int k = fill < cap ? fill : cap; k < cap; ++k) wcell[(size_t)s.woff[i] + k] = -1;
     }
+    // the particle part, added to W - sum_k (+-F_k |S_k|) / |Omega| that
+    // k_wave_update left in W: (W - acc/|Omega|) + F^{fr,p}/|Omega|
+    const double ivol = m.ivol[i];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const double fp = (double)s.pflux[(size_t)q * nc + i] * p.qscale[q];
+        double& w = s.W[(size_t)q * nc + i];
+        w = w + fp * ivol;
+        if (p.averaging) s.wsum[(size_t)q * nc + i] += s.dt[0] * w;
+    }
+}
+
+// a10, the wave part of a step with particles: W <- W - sum_k (+-F_k |S_k|)
+// |Omega|^-1, faces gathered in local order 0..3.  It runs as soon as the
+// wave flux is done, beside the tracking (no particle kernel reads W);
+// k_cell_update adds the particle part once the movers' flux is summed.
+__device__ __forceinline__ void wave_update_body(const DevMesh& m, const DevState& s, Blk bk) {
+    const int nc = m.nc, nf = m.nf;
+    const int i = bk.id * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
     int f[4];
     const int own = m.cfs[i];
 #pragma unroll
@@ -281,11 +301,12 @@ __device__ __forceinline__ void cell_update_body(const DevMesh& m, const DevStat
             const double v = s.F[(size_t)q * nf + f[k]] * m.f_area[f[k]];
             acc = acc + (((own >> k) & 1) ? v : -v);
         }
-        const double fp = (double)s.pflux[(size_t)q * nc + i] * p.qscale[q];
         double& w = s.W[(size_t)q * nc + i];
-        w = (w - acc * ivol) + fp * ivol;
-        if (p.averaging) s.wsum[(size_t)q * nc + i] += s.dt[0] * w;
+        w = w - acc * ivol;
     }
+}
+__global__ void k_wave_update(DevMesh m, DevState s) {
+    wave_update_body(m, s, Blk{(int)blockIdx.x, (int)gridDim.x});
 }
 __global__ void k_cell_update(DevMesh m, DevState s, DevParams p, int32_t* wcell) {
     cell_update_body(m, s, p, wcell, Blk{(int)blockIdx.x, (int)gridDim.x});
@@ -330,6 +351,10 @@ __global__ void k_scan_apply_b(const __grid_constant__ BatchChunk c) {
 __global__ void k_cell_update_b(const __grid_constant__ BatchChunk c) {
     const int i = member_of(c.off[BCL_CELLS], c.n);
     cell_update_body(c.mem[i].m, c.mem[i].s, c.mem[i].p, c.mem[i].b.cell, member_blk(c.off[BCL_CELLS], i));
+}
+__global__ void k_wave_update_b(const __grid_constant__ BatchChunk c) {
+    const int i = member_of(c.off[BCL_CELLS], c.n);
+    wave_update_body(c.mem[i].m, c.mem[i].s, member_blk(c.off[BCL_CELLS], i));
 }
 
 // Time average W-bar = sum dt^n W^n / sum dt^n (Sec. 2.4 (c)).
@@ -535,6 +560,8 @@ cudaError_t configure_cell_kernels(int carveout) {
     set(k_scan_bsum_b);
     set(k_scan_apply_b);
     set(k_cell_update_b);
+    set(k_wave_update);
+    set(k_wave_update_b);
     return e;
 }
 
@@ -554,6 +581,9 @@ void launch_scan(const DevMesh& m, const DevState& s, const DevParams& p, cudaSt
 void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p, int32_t* wcell, cudaStream_t st) {
     k_cell_update<<<cdiv(m.nc, 256), 256, 0, st>>>(m, s, p, wcell);
 }
+void launch_wave_update(const DevMesh& m, const DevState& s, cudaStream_t st) {
+    k_wave_update<<<cdiv(m.nc, 256), 256, 0, st>>>(m, s);
+}
 int blocks_reset(int nc) { return cdiv(5LL * nc, 256) < 4096 ? cdiv(5LL * nc, 256) : 4096; }
 int blocks_cells(int nc) { return cdiv(nc, 256); }
 
@@ -570,6 +600,9 @@ void launch_scan_batch(const BatchChunk& c, int blocks, cudaStream_t st) {
 }
 void launch_cell_update_batch(const BatchChunk& c, int blocks, cudaStream_t st) {
     k_cell_update_b<<<blocks, 256, 0, st>>>(c);
+}
+void launch_wave_update_batch(const BatchChunk& c, int blocks, cudaStream_t st) {
+    k_wave_update_b<<<blocks, 256, 0, st>>>(c);
 }
 void launch_rebuild_survivors(const DevMesh& m, const DevState& s, const DevParams& p, const PartBufRaw& a,
                               cudaStream_t st) {

@@ -281,6 +281,8 @@ void launch_gp_coef(const DevMesh& m, const DevState& s, const DevParams& p, cud
 // a10, and the end of a11: the unused slots of each survivor bucket of the
 // buffer written this step (cell array wcell) are marked as holes.
 void launch_cell_update(const DevMesh& m, const DevState& s, const DevParams& p, int32_t* wcell, cudaStream_t st);
+// the wave part of a step's update (before the particle part of launch_cell_update)
+void launch_wave_update(const DevMesh& m, const DevState& s, cudaStream_t st);
 // Survivor bucket of a cell that starts a step with `cnt` particles: the slots
 // the next buffer reserves for the survivors that end the step in it.
 __host__ __device__ inline int bucket_slots(int cnt) { return cnt + cnt / 32 + 4; }
@@ -323,6 +325,7 @@ void launch_cell_prep_batch(const BatchChunk& c, int blocks, cudaStream_t st);
 void launch_sample_count_batch(const BatchChunk& c, int blocks, cudaStream_t st);
 void launch_scan_batch(const BatchChunk& c, int blocks, cudaStream_t st);
 void launch_cell_update_batch(const BatchChunk& c, int blocks, cudaStream_t st);
+void launch_wave_update_batch(const BatchChunk& c, int blocks, cudaStream_t st);
 void launch_gradients_batch(const BatchChunk& c, int blocks, cudaStream_t st);
 void launch_gp_coef_batch(const BatchChunk& c, int blocks, cudaStream_t st);
 void launch_face_flux_o2_batch(const BatchChunk& c, int blocks, cudaStream_t st);
