@@ -374,28 +374,32 @@ def e2e(cfg, steps, device, launch_cfg=None):
         sim.step(1)
         torch.cuda.synchronize()
         moves = 0
+        t_load = 0.0
         t0 = time.perf_counter()
         for _ in range(steps):
+            a = time.perf_counter()
             load(state)
+            t_load += time.perf_counter() - a
             st = sim.step(1, stats=True)
             moves += st["n_tracked"]
             sim.moments(ugkwp.W)
         t1 = time.perf_counter()
-        return moves / (t1 - t0), (t1 - t0) * 1e3 / steps, h2d, state["id"].size
+        return moves / (t1 - t0), (t1 - t0) * 1e3 / steps, h2d, state["id"].size, t_load * 1e3 / steps
 
     native = sim.state_native()
     wide = sim.state()
-    v_nat, ms_nat, h2d_nat, n = loop(native, sim.set_state_native)
-    v_wide, ms_wide, h2d_wide, _ = loop(wide, sim.set_state)
+    v_nat, ms_nat, h2d_nat, n, imp_nat = loop(native, sim.set_state_native)
+    v_wide, ms_wide, h2d_wide, _, imp_wide = loop(wide, sim.set_state)
     d2h = 5 * sim.n_cells * 8
     sim.close()
     return {"value": v_nat, "unit": UNIT, "h2d_bytes_per_step": int(h2d_nat), "d2h_bytes_per_step": int(d2h),
-            "steps": steps, "particles": int(n), "ms_per_step": ms_nat, "launch_cfg": launch_cfg,
+            "steps": steps, "particles": int(n), "ms_per_step": ms_nat, "import_ms_per_step": imp_nat,
+            "launch_cfg": launch_cfg,
             "per_step": "ugkwp_import_state_native of the whole state from page-locked host arrays (particles "
                         "in the simulation's precision: binary32 offsets from the tets' anchors, binary32 "
                         "velocities; copied as they are and checked on the device), one step, W read back to "
                         "host memory",
-            "binary64_image": {"value": v_wide, "unit": UNIT, "ms_per_step": ms_wide,
+            "binary64_image": {"value": v_wide, "unit": UNIT, "ms_per_step": ms_wide, "import_ms_per_step": imp_wide,
                                "h2d_bytes_per_step": int(h2d_wide), "d2h_bytes_per_step": int(d2h),
                                "per_step": "ugkwp_import_state of the binary64 image (copied as it is, checked "
                                            "and converted to the particle precision on the device), one step, "
